@@ -1,0 +1,401 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle (or the shared event simulation) against a closed
+form, an invariant of the method, a hand-derived case or a brute-force
+computation in a different formulation -- never against a retyped copy of its
+own formulas.  All run on the CPU.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_7556_gb300 import eventgen as eg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+GEOM = eg.Geometry()
+
+
+def _event(r, phi, z, layer):
+    return eg.Event(np.asarray(r, np.float32), np.asarray(phi, np.float32), np.asarray(z, np.float32),
+                    np.asarray(layer, np.uint8), np.zeros(len(r), np.int32))
+
+
+def _centres(bn, i, j, m=None, n=None):
+    k = bn.qpt_min + (i + 0.5) * (bn.qpt_max - bn.qpt_min) / bn.n_qpt
+    phi0 = -math.pi + (j + 0.5) * 2.0 * math.pi / bn.n_phi
+    cot = z0 = 0.0
+    if m is not None:
+        cot = bn.cot_min + (m + 0.5) * (bn.cot_max - bn.cot_min) / bn.n_cot
+        z0 = bn.z0_min + (n + 0.5) * (bn.z0_max - bn.z0_min) / bn.n_z0
+    return k, phi0, cot, z0
+
+
+def _popcount(a):
+    a = np.asarray(a, dtype=np.uint32)
+    return np.unpackbits(a.view(np.uint8)).reshape(a.shape + (32,)).sum(-1)
+
+
+# --------------------------------------------------------------------------------------------
+# The event simulation, pinned to plane geometry (Sec. 4: tracks are circles in the transverse
+# plane of a barrel detector).
+# --------------------------------------------------------------------------------------------
+
+def test_simulated_hits_lie_on_the_track_circle():
+    """Noiseless hits sit on a circle of radius R = pT / (0.3 B) through the beam line whose
+    tangent there points along phi0, and z advances with the arc length R * (subtended angle)."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        q = rng.choice([-1.0, 1.0])
+        pt = math.exp(rng.uniform(math.log(0.5), math.log(100.0)))
+        phi0, cot, z0 = rng.uniform(-math.pi, math.pi), rng.uniform(-6, 6), rng.normal(0, 5)
+        r, phi, z, layer, _ = eg.helix_hits(GEOM, [q / pt], [phi0], [cot], [z0])
+        R = 100.0 * pt / (0.3 * GEOM.b_tesla)                 # cm
+        centre = q * R * np.array([-math.sin(phi0), math.cos(phi0)])
+        pts = np.stack([r * np.cos(phi), r * np.sin(phi)], axis=1)
+        assert np.allclose(np.linalg.norm(pts - centre, axis=1), R, rtol=1e-12, atol=1e-9)
+        # every layer closer than the diameter is reached, no other
+        assert sorted(layer.tolist()) == [l for l, rl in enumerate(GEOM.radii_cm) if rl <= 2 * R]
+        # arc length from the subtended angle at the centre, computed with atan2
+        a0 = np.arctan2(-centre[1], -centre[0])
+        ah = np.arctan2(pts[:, 1] - centre[1], pts[:, 0] - centre[0])
+        alpha = np.abs((ah - a0 + math.pi) % (2 * math.pi) - math.pi)
+        assert np.allclose(z, z0 + cot * R * alpha, rtol=1e-10, atol=1e-9)
+
+
+# --------------------------------------------------------------------------------------------
+# Stage-1 vote
+# --------------------------------------------------------------------------------------------
+
+def test_golden_single_helix_fixtures():
+    """Hand-derived worked examples (tests/golden/single_helix.json)."""
+    with open(os.path.join(GOLDEN, "single_helix.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        bn = eg.Binning(**c["binning"])
+        k, phi0, cot, z0 = _centres(bn, *c["generating_bin"], *c["generating_stage2_bin"])
+        r, phi, z, layer, _ = eg.helix_hits(GEOM, [k], [phi0], [cot], [z0])
+        b = oracle.make_binning(GEOM, bn)
+        M, votes, flags = oracle.vote(b, _event(r, phi, z, layer))
+        i, j = c["generating_bin"]
+        assert int(M[i, j]) == c["expected_mask"]
+        assert int(votes.sum()) == c["expected_votes"]
+        cands = oracle.peaks(b, M)
+        assert [(int(x["iq"]), int(x["jphi"]), int(x["mask"])) for x in cands] == \
+            [tuple(x) for x in c["expected_candidates"]]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_single_noiseless_helix_generating_bin_holds_all_layers(seed):
+    """A noiseless helix with q/pT and phi0 on bin centres puts every reached layer in its own bin
+    (closed form: the vote inverts the hit position exactly), and the peak search returns exactly
+    one candidate, in the generating column, on the generating row or the row above it (the first
+    row of the q/pT plateau under the raster tie-break)."""
+    rng = np.random.default_rng(100 + seed)
+    for bn in (eg.BINNING_SMALL, eg.BINNING_PILEUP, eg.BINNING_FINE):
+        i = int(rng.integers(2, bn.n_qpt - 2))
+        j = int(rng.integers(0, bn.n_phi))
+        k, phi0, _, _ = _centres(bn, i, j)
+        r, phi, z, layer, _ = eg.helix_hits(GEOM, [k], [phi0], [0.0], [0.0])
+        b = oracle.make_binning(GEOM, bn)
+        M, votes, flags = oracle.vote(b, _event(r, phi, z, layer))
+        reached = sum(1 << int(l) for l in layer)
+        assert int(M[i, j]) == reached
+        assert not np.any(flags["row"] == i)      # votes at the generating row sit on bin centres
+        if len(layer) >= bn.threshold:
+            cands = oracle.peaks(b, M)
+            assert len(cands) == 1
+            assert int(cands[0]["jphi"]) == j and int(cands[0]["iq"]) in (i - 1, i)
+            assert int(cands[0]["mask"]) == reached
+
+
+def _exact_vote_count(b, r):
+    """Number of q/pT bin centres k_i with |0.15 B (r/100) k_i| <= 1, by exact rational arithmetic."""
+    c = Fraction(0.15) * Fraction(b.b_tesla) * Fraction(float(r)) / 100
+    dk = (Fraction(b.qpt_max) - Fraction(b.qpt_min)) / b.n_qpt
+    lim = 1 / c
+    # i ranges over integers with -lim <= qpt_min + (i + 1/2) dk <= lim
+    lo = math.ceil((-lim - Fraction(b.qpt_min)) / dk - Fraction(1, 2))
+    hi = math.floor((lim - Fraction(b.qpt_min)) / dk - Fraction(1, 2))
+    lo, hi = max(lo, 0), min(hi, b.n_qpt - 1)
+    return max(0, hi - lo + 1)
+
+
+@pytest.mark.parametrize("name", ["single_50trk", "pileup_100k"])
+def test_vote_count_conservation(name):
+    """Votes per layer equal the closed-form count of rows inside the |x| <= 1 domain (up to
+    domain-flagged votes), and the masks never hold more layer bits than votes were cast."""
+    w = eg.WORKLOADS[name]
+    ev = w.event(3)
+    if ev.n_hits > 20000:
+        ev = ev.subset(np.arange(20000))
+    b = oracle.make_binning(w.geometry, w.binning)
+    M, votes, flags = oracle.vote(b, ev)
+    n_domain = int((flags["kind"] == 2).sum())
+    for l in range(w.geometry.n_layers):
+        radii = ev.r[ev.layer == l]
+        uniq, cnt = np.unique(radii, return_counts=True)
+        expect = sum(int(n) * _exact_vote_count(b, rr) for rr, n in zip(uniq, cnt))
+        assert abs(int(votes[l]) - expect) <= n_domain
+        assert int(((M >> l) & 1).sum()) <= int(votes[l])
+    assert int(_popcount(M).sum()) <= int(votes.sum())
+
+
+def test_cyclic_phi_rotation_shifts_accumulator():
+    """Rotating every hit by m bin widths shifts the accumulator by m columns.  Bins may differ
+    only where a vote of either event lies within the flag window of an edge (the FP32 inputs
+    are rounded after rotation, moving votes by < 1e-4 bin)."""
+    w = eg.WORKLOADS["single_50trk"]
+    b = oracle.make_binning(w.geometry, w.binning)
+    ev = w.event(1)
+    M, _, fl = oracle.vote(b, ev)
+    for m in (1, 37, -5, w.binning.n_phi // 2):
+        rot = (ev.phi.astype(np.float64) + m * 2.0 * math.pi / b.n_phi)
+        rot = np.mod(rot + math.pi, 2 * math.pi) - math.pi
+        ev2 = eg.Event(ev.r, rot.astype(np.float32), ev.z, ev.layer, ev.track)
+        M2, _, fl2 = oracle.vote(b, ev2)
+        shifted = np.roll(M, m, axis=1)
+        diff = np.argwhere(shifted != M2)
+        allowed = set()
+        for f in fl:
+            for jj in (f["bin"], f["alt"]):
+                if jj >= 0:
+                    allowed.add((int(f["row"]), int((jj + m) % b.n_phi)))
+        for f in fl2:
+            for jj in (f["bin"], f["alt"]):
+                if jj >= 0:
+                    allowed.add((int(f["row"]), int(jj)))
+        assert all((int(i), int(j)) in allowed for i, j in diff)
+        assert len(diff) <= len(fl) + len(fl2)
+        # candidates rotate with the accumulator where their neighbourhood is untouched by flags
+        c1 = {(int(c["iq"]), int((c["jphi"] + m) % b.n_phi)) for c in oracle.peaks(b, M)}
+        c2 = {(int(c["iq"]), int(c["jphi"])) for c in oracle.peaks(b, M2)}
+        near = {(i + di, (j + dj) % b.n_phi) for (i, j) in allowed for di in (-1, 0, 1) for dj in (-1, 0, 1)}
+        assert {c for c in c1 ^ c2 if c not in near} == set()
+
+
+def _brute_force_votes(b, r, phi, layer, mp):
+    """Bin-major brute force with a different predicate: bin (i, j) receives hit h when
+    f(d) = sin(d) - x changes sign across the bin, d = phi - phi0 on the branch |d| <= pi/2
+    where f increases; evaluated at 40 significant digits.  No arcsine is used."""
+    mp.mp.dps = 40
+    M = np.zeros((b.n_qpt, b.n_phi), np.uint16)
+    two_pi = 2 * mp.pi
+    w = two_pi / b.n_phi
+    half_pi = mp.pi / 2
+    dk = (mp.mpf(b.qpt_max) - mp.mpf(b.qpt_min)) / b.n_qpt
+    for h in range(len(r)):
+        rr, ph = mp.mpf(float(r[h])), mp.mpf(float(phi[h]))
+        for i in range(b.n_qpt):
+            k = mp.mpf(b.qpt_min) + (i + mp.mpf(1) / 2) * dk
+            x = mp.mpf(15) / 100 * mp.mpf(b.b_tesla) * rr / 100 * k
+            if abs(x) > 1:
+                continue
+            for j in range(b.n_phi):
+                edge = -mp.pi + j * w
+                hi = ph - edge
+                hi = hi - two_pi * mp.floor((hi + mp.pi) / two_pi)     # into [-pi, pi)
+                lo = hi - w
+                if hi < -half_pi or lo >= half_pi:
+                    continue
+                ok_lo = lo < -half_pi or mp.sin(lo) < x      # the root lies above lo
+                ok_hi = hi >= half_pi or mp.sin(hi) >= x     # ... and not above hi
+                if ok_lo and ok_hi:
+                    M[i, j] |= 1 << int(layer[h])
+    return M
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_vote_matches_brute_force_sign_change(seed):
+    """Tiny random events: the oracle's hit-major FP64 vote equals a bin-major high-precision
+    sign-change search, except at votes the oracle flags as edge votes."""
+    mp = pytest.importorskip("mpmath")
+    rng = np.random.default_rng(seed)
+    bn = eg.Binning(n_qpt=24, qpt_min=-2.0, qpt_max=2.0, n_phi=48, threshold=3)
+    b = oracle.make_binning(GEOM, bn)
+    n = 12
+    layer = rng.integers(0, 10, n).astype(np.uint8)
+    r = np.asarray(GEOM.radii_cm, np.float32)[layer]
+    phi = rng.uniform(-math.pi, math.pi, n).astype(np.float32)
+    M, _, flags = oracle.vote(b, _event(r, phi, np.zeros(n), layer))
+    Mb = _brute_force_votes(b, r, phi, layer, mp)
+    diff = np.argwhere(M != Mb)
+    allowed = {(int(f["row"]), int(jj)) for f in flags for jj in (f["bin"], f["alt"]) if jj >= 0}
+    assert all((int(i), int(j)) in allowed for i, j in diff)
+
+
+def test_vote_matches_high_precision_arithmetic():
+    """Every unflagged FP64 vote lands in the bin of the exact (40-digit) computation."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    rng = np.random.default_rng(11)
+    bn = eg.BINNING_FINE
+    b = oracle.make_binning(GEOM, bn)
+    n = 6
+    layer = rng.integers(0, 10, n).astype(np.uint8)
+    r = np.asarray(GEOM.radii_cm, np.float32)[layer]
+    phi = rng.uniform(-math.pi, math.pi, n).astype(np.float32)
+    M, _, flags = oracle.vote(b, _event(r, phi, np.zeros(n), layer))
+    flagged = {(int(f["hit"]), int(f["row"])) for f in flags}
+    dk = (mp.mpf(bn.qpt_max) - mp.mpf(bn.qpt_min)) / bn.n_qpt
+    checked = 0
+    for h in range(n):
+        for i in range(0, bn.n_qpt, 7):
+            k = mp.mpf(bn.qpt_min) + (i + mp.mpf(1) / 2) * dk
+            x = mp.mpf(15) / 100 * mp.mpf(GEOM.b_tesla) * mp.mpf(float(r[h])) / 100 * k
+            if abs(x) > 1 or (h, i) in flagged:
+                continue
+            u = bn.n_phi * (mp.mpf(float(phi[h])) - mp.asin(x) + mp.pi) / (2 * mp.pi)
+            j = int(mp.floor(u)) % bn.n_phi
+            assert (int(M[i, j]) >> int(layer[h])) & 1
+            checked += 1
+    assert checked > 200
+
+
+def test_missing_layers_tolerated():
+    """The Hough transform tolerates missing hits (Sec. 4): removing up to L - k layers of a
+    noiseless helix keeps one candidate at the generating column, holding the remaining layers."""
+    bn = eg.BINNING_SMALL
+    b = oracle.make_binning(GEOM, bn)
+    i, j = 70, 33
+    k, phi0, _, _ = _centres(bn, i, j)
+    r, phi, z, layer, _ = eg.helix_hits(GEOM, [k], [phi0], [0.0], [0.0])
+    rng = np.random.default_rng(5)
+    for drop in range(0, GEOM.n_layers - bn.threshold + 1):
+        keep = np.sort(rng.permutation(len(r))[drop:])
+        M, _, _ = oracle.vote(b, _event(r[keep], phi[keep], z[keep], layer[keep]))
+        cands = oracle.peaks(b, M)
+        assert len(cands) == 1 and int(cands[0]["jphi"]) == j
+        assert int(cands[0]["mask"]) == sum(1 << int(l) for l in layer[keep])
+    keep = np.arange(bn.threshold - 1)
+    M, _, _ = oracle.vote(b, _event(r[keep], phi[keep], z[keep], layer[keep]))
+    assert len(oracle.peaks(b, M)) == 0
+
+
+# --------------------------------------------------------------------------------------------
+# Peak search: hand-derived accumulators (tests/golden/peak_cases.json)
+# --------------------------------------------------------------------------------------------
+
+def test_golden_peak_cases():
+    with open(os.path.join(GOLDEN, "peak_cases.json")) as f:
+        spec = json.load(f)
+    for case in spec["cases"]:
+        nq, nphi = case["shape"]
+        M = np.zeros((nq, nphi), np.uint16)
+        for i, j, mask in case["cells"]:
+            M[i, j] = mask
+        bn = eg.Binning(n_qpt=nq, qpt_min=-1, qpt_max=1, n_phi=nphi, threshold=case["threshold"])
+        got = [(int(c["iq"]), int(c["jphi"])) for c in oracle.peaks(oracle.make_binning(GEOM, bn), M)]
+        assert got == [tuple(x) for x in case["expected"]], case["name"]
+
+
+def test_peaks_invariants_on_random_accumulators():
+    """Candidates are never 8-neighbours of one another, each reaches the threshold and dominates
+    its 3 x 3 block, and every strict maximum of its 3 x 3 block above threshold is found."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        nq, nphi = 9, 16
+        M = rng.integers(0, 1 << 6, (nq, nphi)).astype(np.uint16)
+        bn = eg.Binning(n_qpt=nq, qpt_min=-1, qpt_max=1, n_phi=nphi, threshold=3)
+        cands = {(int(c["iq"]), int(c["jphi"])) for c in oracle.peaks(oracle.make_binning(GEOM, bn), M)}
+        p = _popcount(M)
+        padded = np.zeros((nq + 2, nphi), int)
+        padded[1:-1] = p
+        for i in range(nq):
+            for j in range(nphi):
+                block = [padded[i + 1 + di, (j + dj) % nphi] for di in (-1, 0, 1) for dj in (-1, 0, 1)
+                         if (di, dj) != (0, 0)]
+                strict = p[i, j] >= 3 and all(v < p[i, j] for v in block)
+                if strict:
+                    assert (i, j) in cands
+                if (i, j) in cands:
+                    assert p[i, j] >= 3 and all(v <= p[i, j] for v in block)
+        for (i, j) in cands:
+            for di in (-1, 0, 1):
+                for dj in (-1, 0, 1):
+                    if (di, dj) != (0, 0):
+                        assert (i + di, (j + dj) % nphi) not in cands
+
+
+# --------------------------------------------------------------------------------------------
+# Membership and the second-stage vote
+# --------------------------------------------------------------------------------------------
+
+def test_member_layers_reproduce_candidate_mask():
+    """A cell's mask is the OR of the layer bits of the hits that voted into it, so the members
+    found by re-deriving the votes must OR to exactly the candidate's mask."""
+    w = eg.WORKLOADS["single_50trk"]
+    b = oracle.make_binning(w.geometry, w.binning)
+    ev = w.event(2)
+    M, _, _ = oracle.vote(b, ev)
+    cands = oracle.peaks(b, M)
+    offsets, mem, _ = oracle.members(b, ev, cands)
+    assert len(cands) > 10
+    for q, c in enumerate(cands):
+        hits = mem[offsets[q]:offsets[q + 1]]
+        assert np.all(np.diff(hits) > 0)
+        acc = 0
+        for h in hits:
+            acc |= 1 << int(ev.layer[h])
+        assert acc == int(c["mask"])
+
+
+def test_stage2_single_helix_closed_form():
+    """Member hits of a noiseless helix with cot(theta) and z0 on stage-2 bin centres all vote for
+    the generating (cot, z0) cell, which is then the stage-2 maximum with every layer."""
+    bn = eg.BINNING_PILEUP
+    b = oracle.make_binning(GEOM, bn)
+    rng = np.random.default_rng(9)
+    for _ in range(8):
+        i, j = int(rng.integers(0, bn.n_qpt)), int(rng.integers(0, bn.n_phi))
+        m, n = int(rng.integers(0, bn.n_cot)), int(rng.integers(0, bn.n_z0))
+        k, phi0, cot, z0 = _centres(bn, i, j, m, n)
+        r, phi, z, layer, _ = eg.helix_hits(GEOM, [k], [phi0], [cot], [z0])
+        ev = _event(r, phi, z, layer)
+        cand = np.zeros(1, oracle.CAND_DTYPE)
+        cand["iq"], cand["jphi"] = i, j
+        offsets = np.array([0, len(r)], np.int64)
+        res, _ = oracle.stage2(b, ev, cand, offsets, np.arange(len(r), dtype=np.int64))
+        assert (int(res[0]["icot"]), int(res[0]["jz0"])) == (m, n)
+        assert int(res[0]["mask2"]) == sum(1 << int(l) for l in layer)
+        assert int(res[0]["n_votes"]) <= len(r) * bn.n_cot
+
+
+def test_stage2_matches_geometric_brute_force():
+    """Stage-2 cells from a separate computation: z0 from the arc length R * alpha, alpha the
+    angle the chord subtends at the circle's centre (atan2 geometry, no arcsine)."""
+    w = eg.WORKLOADS["single_50trk"]
+    bn = w.binning
+    b = oracle.make_binning(w.geometry, bn)
+    ev = w.event(4)
+    M, _, _ = oracle.vote(b, ev)
+    cands = oracle.peaks(b, M)[:12]
+    offsets, mem, _ = oracle.members(b, ev, cands)
+    res, zflags = oracle.stage2(b, ev, cands, offsets, mem)
+    flagged = {int(f["cand"]) for f in zflags}
+    dt = (bn.cot_max - bn.cot_min) / bn.n_cot
+    for q, c in enumerate(cands):
+        if q in flagged:
+            continue
+        k = bn.qpt_min + (int(c["iq"]) + 0.5) * (bn.qpt_max - bn.qpt_min) / bn.n_qpt
+        R = 100.0 / (0.3 * w.geometry.b_tesla * abs(k))          # cm
+        M2 = np.zeros((bn.n_cot, bn.n_z0), np.uint16)
+        for h in mem[offsets[q]:offsets[q + 1]]:
+            rr = float(ev.r[h])
+            # chord of length rr from the beam line; the centre sits at distance R from both ends
+            half = rr / 2.0
+            alpha = 2.0 * math.atan2(half, math.sqrt(max(R * R - half * half, 0.0)))
+            s = R * alpha
+            for m in range(bn.n_cot):
+                t = bn.cot_min + (m + 0.5) * dt
+                u = bn.n_z0 * (float(ev.z[h]) - s * t - bn.z0_min) / (bn.z0_max - bn.z0_min)
+                if 0 <= u < bn.n_z0:
+                    M2[m, int(math.floor(u))] |= 1 << int(ev.layer[h])
+        p = _popcount(M2)
+        best = int(np.argmax(p))
+        assert (int(res[q]["icot"]), int(res[q]["jz0"])) == divmod(best, bn.n_z0)
+        assert int(res[q]["mask2"]) == int(M2.flat[best])
