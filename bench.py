@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 Hough-transform track finder on a seeded synthetic workload.
+
+One step = one event through the whole hot path on the GPU: hit staging, stage-1 vote, peak
+search, membership and the stage-2 vote.  Default workload: the single high-pileup event
+(5,000 helices + 50,000 noise hits, 512 q/pT x 2048 phi0 layer masks, >= 7 layers, 64 x 64
+stage 2).  Inputs are resident in HBM before the timed region; L2 is flushed (a 256 MiB write)
+before every timed step and each step is bracketed by CUDA events on the launching stream.
+
+`e2e` repeats the measurement through the public one-call entry point (hough_process) from
+pinned host buffers: host->device copy of the hits, the path, and the device->host read of the
+candidate list, timed on the host around each call.
+
+`--impl reference` times the FP64 CPU oracle (the plain restatement of the method the CUDA path is
+checked against) on this machine's host cores, on the same workload and metric.
+
+Launch: `python bench.py [--gpus 1] [--steps K] [--warmup W]`; for N > 1 under
+`python -m torch.distributed.run --nproc-per-node N ... bench.py --gpus N`: every rank processes
+its own events (events are independent; no collective on the data path) and the timing is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1310_7556_gb300 import eventgen as eg  # noqa: E402
+
+METRIC = "Hough votes/s and events/s on 1 GB300 (batched vs plain); p50/p99 event latency"
+WORKLOAD_TEXT = {
+    "pileup_100k": "single high-pileup event: 5000 helices (q=+-1, pT log-uniform 0.5-100 GeV, eta +-2.5, "
+                   "z0~N(0,5cm)) + 50000 uniform noise hits on 10 barrel layers r=4..110 cm, B=3.8 T; "
+                   "512 q/pT x 2048 phi0 uint16 layer masks, threshold >=7, 64 cot x 64 z0 stage 2",
+    "single_50trk": "single event: 50 helices pT 1-50 GeV, no noise; 128 q/pT x 256 phi0, threshold >=8",
+    "fine_4m": "fine binning: 20000 helices + 200000 noise hits; 1024 q/pT x 4096 phi0, threshold >=7",
+}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="pileup_100k", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline(workload, n_events: int = 4):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload."""
+    import oracle
+    w = eg.WORKLOADS[workload]
+    events = [w.event(i) for i in range(n_events)]
+    oracle.build()
+    t0 = time.perf_counter()
+    votes = 0
+    for ev in events:
+        res = oracle.run(w.geometry, w.binning, ev)
+        votes += int(res["votes_by_layer"].sum())
+    dt = time.perf_counter() - t0
+    return {"value": n_events / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_events} full {workload} events (seeds 0..{n_events - 1}), whole path, FP64, 1 thread",
+            "votes_per_s": votes / dt, "seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, one event (or a bounded sample) per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = eg.WORKLOADS[args.workload]
+    ev = w.event(0)
+    # keep the whole run within a few minutes: above 60 steps a step is a prefix sample of the hits
+    frac = min(1.0, 60.0 / max(1, args.steps + args.warmup))
+    sample = ev if frac >= 1.0 else ev.subset(np.arange(int(ev.n_hits * frac)))
+    for _ in range(args.warmup):
+        oracle.run(w.geometry, w.binning, sample)
+    t0 = time.perf_counter()
+    votes = 0
+    for _ in range(args.steps):
+        votes += int(oracle.run(w.geometry, w.binning, sample)["votes_by_layer"].sum())
+    dt = time.perf_counter() - t0
+    value = args.steps * frac / dt
+    desc = ("one full event per step" if frac >= 1.0 else
+            f"per step the first {sample.n_hits} of {ev.n_hits} hits; events/s scaled by that fraction "
+            "(the vote is linear in the hits)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": int(ev.n_hits)},
+            "votes_per_s": votes / frac / dt if frac > 0 else None,
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1310_7556_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    binding.load()
+
+    w = eg.WORKLOADS[args.workload]
+    ev = w.event(rank)     # each rank its own event
+    n = ev.n_hits
+    tens = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
+    ctx = binding.HoughContext(w.geometry, w.binning, max_hits=n, max_candidates=1 << 18,
+                               max_members=1 << 23, device=local)
+    ctx.enable_timing(True)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.vote(*tens, n_hits=n, where=binding.DEVICE, stream=stream)
+        ctx.peaks(stream=stream)
+        ctx.stage2(stream=stream)
+
+    # measured shared-atomic ceiling (conflict-free 32-lane atomicOr), before anything is timed
+    smem_peak = binding.smem_or_throughput(local, 0, 30.0)
+    smem_peak_rand = binding.smem_or_throughput(local, 1, 30.0)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    votes = int(st.votes)
+    n_cand = int(st.n_candidates)
+
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    lib_t = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = binding.kernel_launches()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            e0[k].record(stream)
+            step()
+            e1[k].record(stream)
+            lib_t.append(ctx.timing())
+        torch.cuda.synchronize()
+    launches = binding.kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    events_per_s = world * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    vote_ms = statistics.mean(t["vote_ms"] for t in lib_t)
+    stage_ms = statistics.mean(t["stage_ms"] for t in lib_t)
+    peaks_ms = statistics.mean(t["peaks_ms"] for t in lib_t)
+    stage2_ms = statistics.mean(t["stage2_ms"] for t in lib_t)
+
+    # end to end through hough_process from pinned host buffers
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (ev.r, ev.phi, ev.z, ev.layer)]
+    out = np.zeros(1 << 18, dtype=binding.CANDIDATE_DTYPE)
+    for _ in range(3):
+        ctx.process(*pinned, n_hits=n, out=out, stream=stream)
+    if world > 1:
+        dist.barrier()
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = ctx.process(*pinned, n_hits=n, out=out, stream=stream)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_s)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * args.steps / e2e_total
+    h2d = n * (4 + 4 + 4 + 1)
+    d2h = len(got) * 32 + 160
+
+    peaks, peaks_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # vote kernel: one shared atomicOr per vote (before the duplicate skip) is the algorithmic work
+    achieved_atomics = votes / (vote_ms * 1e-3)
+    # algorithmic bytes of the vote launch: 13 B per hit read (r, phi, z, layer) + 2 B per cell written
+    vote_bytes = 13 * n + 2 * w.binning.n_qpt * w.binning.n_phi
+
+    line = {
+        "metric": METRIC,
+        "value": events_per_s,
+        "unit": "events/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": n, "votes_per_event": votes,
+                   "candidates_per_event": n_cand, "mode": "plain: one event per step, one launch sequence",
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "tiling": list(ctx.get_tiling())},
+        "votes_per_s": votes * events_per_s,
+        "stage_ms": {"staging": stage_ms, "vote": vote_ms, "peaks": peaks_ms, "stage2": stage2_ms},
+        "roofline": {"bound": "smem_atomic", "kernel": "vote_kernel", "achieved": achieved_atomics / 1e9,
+                     "peak": smem_peak / 1e9, "unit": "Gatomic/s", "frac": achieved_atomics / smem_peak,
+                     "peak_kind": "measured by hough_microbench_smem_or (conflict-free 32-lane atomicOr)",
+                     "peak_random_pattern": smem_peak_rand / 1e9,
+                     "traffic": None,
+                     "hbm": {"achieved": vote_bytes / (vote_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": vote_bytes / (vote_ms * 1e-3) / 1e9 / hbm_peak,
+                             "peak_kind": f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)"}},
+        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

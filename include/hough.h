@@ -1,0 +1,247 @@
+/*
+ * hough.h -- C ABI of the GB300 Hough-transform track finder.
+ *
+ * The method (Halyo et al., "First Evaluation of the CPU, GPGPU and MIC
+ * Architectures for Real Time Particle Tracking based on Hough Transform at
+ * the LHC", Sec. 4): every hit of an event votes into a discrete grid of track
+ * parameters -- curvature q/pT by azimuth phi0 at the beam line -- and local
+ * maxima of the grid are the track candidates; candidates are then confirmed by
+ * a second, more expensive computation (Sec. 4), here a (cot theta, z0) vote of
+ * each candidate's member hits.  Each grid cell holds a 16-bit mask of the
+ * detector layers that voted for it.
+ *
+ * Formulas (the paper gives the steps in prose; these are the helix relations
+ * of a track from the beam line in a solenoid field B):
+ *   x    = 0.15 * B * (r / 100) * k_i             k_i = qpt_min + (i + 1/2) dk,  r in cm
+ *   phi0 = phi - asin(x)                          a vote exists when |x| <= 1
+ *   j    = floor(n_phi * (phi0 + pi) / (2 pi)) mod n_phi
+ *   s    = r * asin(|x|) / |x|                    transverse arc length (s = r at x = 0)
+ *   z0   = z - s * t_m                            t_m = cot_min + (m + 1/2) dt
+ *
+ * Conventions for every entry point:
+ *   - Returns HOUGH_OK (0) or a negative HOUGH_E* status; hough_last_error()
+ *     gives a message for the calling thread's last failure.
+ *   - `where` says where caller buffers live: HOUGH_HOST (pageable or pinned
+ *     host memory) or HOUGH_DEVICE (device memory of the context's GPU).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls that only enqueue work return before it runs; calls that
+ *     return results to host memory synchronise the stream first.
+ *   - The library owns every context and its device buffers (allocated once by
+ *     hough_create, sized by hough_limits).  Caller buffers stay owned by the
+ *     caller and must stay valid until the call that reads them has finished
+ *     on the stream.
+ *   - A context is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef HOUGH_H
+#define HOUGH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HOUGH_OK          0
+#define HOUGH_EINVAL     (-1)   /* an argument is out of its documented range */
+#define HOUGH_ENOMEM     (-2)   /* a device or pinned-host allocation failed */
+#define HOUGH_ECUDA      (-3)   /* the CUDA runtime reported an error */
+#define HOUGH_ETRUNC     (-4)   /* more results than the caller's capacity; the first cap were written */
+#define HOUGH_ECAPACITY  (-5)   /* the input exceeds the limits the context was created with */
+#define HOUGH_EBUSY      (-6)   /* serving: no free slot for a new event */
+#define HOUGH_ETIMEDOUT  (-7)   /* a bounded wait expired */
+#define HOUGH_EDEVICE    (-8)   /* a device-side check failed (see hough_stats.device_error) */
+#define HOUGH_ENOTREADY  (-9)   /* the requested result has not been produced yet */
+
+#define HOUGH_HOST   0
+#define HOUGH_DEVICE 1
+
+#define HOUGH_MAX_LAYERS 16
+
+/* Device-side error bits reported in hough_stats.device_error. */
+#define HOUGH_DEVERR_LAYER     1u   /* a hit had layer >= n_layers; it cast no vote */
+#define HOUGH_DEVERR_RADIUS    2u   /* a hit had r <= 0 or a non-finite coordinate; it cast no vote */
+#define HOUGH_DEVERR_CAND      4u   /* more candidates than max_candidates; the first ones were kept */
+#define HOUGH_DEVERR_MEMBERS   8u   /* more member hits than max_members; stage 2 skipped the rest */
+
+/* Barrel detector: number of layers and the solenoid field. */
+typedef struct hough_geometry {
+    int32_t n_layers;   /* 1..16; a hit's layer index must be < n_layers */
+    int32_t reserved;   /* must be 0 */
+    double  b_tesla;    /* field in tesla, > 0 */
+} hough_geometry;
+
+/*
+ * Accumulator axes (Sec. 4: "a discrete grid in the parameter space").
+ * Stage 1: n_qpt rows of q/pT over [qpt_min, qpt_max] (c/GeV) by n_phi columns
+ * of phi0 over [-pi, pi), cyclic.  A cell is a candidate when popcount(mask) >=
+ * threshold and it is a local maximum (see hough_peaks).  Stage 2: n_cot rows
+ * of cot(theta) over [cot_min, cot_max] by n_z0 columns of z0 over
+ * [z0_min_cm, z0_max_cm), not cyclic.
+ * Limits: 1 <= n_qpt <= 65535; 64 <= n_phi <= 32768 and n_phi % 64 == 0;
+ * 1 <= threshold <= 16; 1 <= n_cot, n_z0 <= 256 and n_cot * n_z0 <= 16384;
+ * qpt_min < qpt_max, cot_min < cot_max, z0_min_cm < z0_max_cm.
+ */
+typedef struct hough_binning {
+    int32_t n_qpt, n_phi, threshold, n_cot, n_z0, reserved;
+    double  qpt_min, qpt_max;
+    double  cot_min, cot_max;
+    double  z0_min_cm, z0_max_cm;
+} hough_binning;
+
+/* Capacities fixed at creation; every device buffer is sized from them. */
+typedef struct hough_limits {
+    int64_t max_hits;         /* hits per event, >= 1 */
+    int32_t max_candidates;   /* stage-1 candidates kept per event, >= 1 */
+    int32_t max_members;      /* member hits kept per event over all candidates, >= 1 */
+} hough_limits;
+
+/*
+ * One track candidate.  (iq, jphi) is the stage-1 cell, mask its layer mask;
+ * n_members the hits whose stage-1 vote fell in the cell; (icot, jz0) the
+ * stage-2 maximum (most layers, lowest row-major index on ties) and mask2 its
+ * layer mask.  flags: bit 0 set when popcount(mask2) >= threshold (confirmed),
+ * bit 1 when the member list was cut by max_members.  The stage-2 fields are 0
+ * until hough_stage2 has run.
+ */
+typedef struct hough_candidate {
+    uint32_t iq, jphi, mask, n_members;
+    uint32_t icot, jz0, mask2, flags;
+} hough_candidate;
+
+/* Counters of the last processed event (filled by hough_get_stats). */
+typedef struct hough_stats {
+    uint64_t votes;                              /* stage-1 votes cast */
+    uint64_t votes_by_layer[HOUGH_MAX_LAYERS];
+    uint64_t general_votes;                      /* votes on layers whose hits do not share one radius */
+    uint64_t refined_votes;                      /* of those, votes recomputed in FP64 near a bin edge */
+    uint64_t stage2_votes;                       /* stage-2 votes cast */
+    int64_t  n_hits;                             /* hits accepted */
+    int64_t  n_candidates;                       /* candidates found (may exceed max_candidates) */
+    int64_t  n_members;                          /* member hits found (may exceed max_members) */
+    uint32_t device_error;                       /* HOUGH_DEVERR_* bits */
+    uint32_t uniform_layers;                     /* bit l: all hits of layer l share one radius */
+} hough_stats;
+
+typedef struct hough_ctx hough_ctx;
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char *hough_last_error(void);
+
+/* Library version, "major.minor.patch". */
+const char *hough_version(void);
+
+/*
+ * Create a context on CUDA device `device`: validates the arguments (HOUGH_EINVAL),
+ * allocates every device buffer (HOUGH_ENOMEM) and returns it in *out.
+ */
+int hough_create(const hough_geometry *geometry, const hough_binning *binning,
+                 const hough_limits *limits, int device, hough_ctx **out);
+
+/* Release a context and all its buffers.  NULL is accepted.  Synchronises the device first. */
+void hough_destroy(hough_ctx *ctx);
+
+/*
+ * Stage-1 vote of one event (Sec. 4, first step).  Hits are four parallel
+ * arrays of n_hits entries: r (cm, > 0), phi (rad, |phi| <= 1000; it is reduced
+ * modulo 2 pi), z (cm, finite), layer (< n_layers).  With HOUGH_HOST the arrays
+ * are checked on the host (HOUGH_EINVAL on a bad hit) and copied; with
+ * HOUGH_DEVICE a bad hit is dropped on the device and reported through
+ * hough_stats.device_error.  n_hits may be 0.  Replaces the context's previous
+ * event.  HOUGH_ECAPACITY when n_hits > max_hits.  Asynchronous on `stream`.
+ */
+int hough_vote(hough_ctx *ctx, const float *r, const float *phi, const float *z,
+               const uint8_t *layer, int64_t n_hits, int where, void *stream);
+
+/*
+ * Peak search (Sec. 4, second step) on the accumulator of the last vote: cell
+ * (i, j) with layer count p = popcount(mask) is a candidate when p >= threshold,
+ * no 3 x 3 neighbour has a larger count and the neighbours at offsets (-1,-1),
+ * (-1,0), (-1,+1), (0,-1) have strictly smaller counts.  phi0 wraps; rows
+ * outside the grid count as empty.  Candidates are kept in raster order.
+ * Asynchronous on `stream`.
+ */
+int hough_peaks(hough_ctx *ctx, void *stream);
+
+/*
+ * Confirmation step (Sec. 4: "more expensive computations ... to confirm"):
+ * finds each candidate's member hits (hits whose stage-1 vote on the
+ * candidate's row fell in its cell) and votes them into the (cot theta, z0)
+ * grid; fills n_members, icot, jz0, mask2 and flags.  Asynchronous on `stream`.
+ */
+int hough_stage2(hough_ctx *ctx, void *stream);
+
+/*
+ * Copy the candidates of the last event (raster order) to `out` (cap entries,
+ * HOUGH_HOST or HOUGH_DEVICE); *n_out receives the number found.  HOUGH_ETRUNC
+ * when that exceeds cap.  Synchronises `stream`.
+ */
+int hough_get_candidates(hough_ctx *ctx, hough_candidate *out, int32_t cap, int32_t *n_out,
+                         int where, void *stream);
+
+/* Copy the n_qpt x n_phi row-major accumulator of the last vote.  Synchronises `stream`. */
+int hough_get_accumulator(hough_ctx *ctx, uint16_t *out, int where, void *stream);
+
+/*
+ * Copy the member lists of the last stage 2: offsets[n_cand + 1] (int64) and
+ * hits[offsets[n_cand]] (int32 hit indices of the event, increasing within each
+ * candidate).  `hit_cap` bounds `hits`; HOUGH_ETRUNC when it is too small.
+ * Synchronises `stream`.
+ */
+int hough_get_members(hough_ctx *ctx, int64_t *offsets, int32_t *hits, int64_t hit_cap,
+                      int where, void *stream);
+
+/* Counters of the last event.  Synchronises `stream`.  HOUGH_EDEVICE if device_error != 0. */
+int hough_get_stats(hough_ctx *ctx, hough_stats *out, void *stream);
+
+/*
+ * Whole path on one event: hough_vote, hough_peaks, hough_stage2 and
+ * hough_get_candidates in one call (hits and candidates both in `where` memory).
+ * Synchronises `stream`.
+ */
+int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float *z,
+                  const uint8_t *layer, int64_t n_hits, hough_candidate *out, int32_t cap,
+                  int32_t *n_out, int where, void *stream);
+
+/*
+ * Vote-kernel tiling: each CTA owns a tile of tile_qpt rows by tile_phi columns
+ * of the accumulator in shared memory.  tile_phi must divide n_phi and be a
+ * multiple of 64; tile_qpt in 1..256; threads in {128, 256, 512, 1024};
+ * tile_qpt * tile_phi * 2 bytes must fit in shared memory.  HOUGH_EINVAL otherwise.
+ */
+typedef struct hough_tiling {
+    int32_t tile_qpt, tile_phi, threads, reserved;
+} hough_tiling;
+
+int hough_set_tiling(hough_ctx *ctx, const hough_tiling *tiling);
+int hough_get_tiling(const hough_ctx *ctx, hough_tiling *tiling);
+
+/*
+ * Per-step device time of the last event, measured with CUDA events recorded on the stream each
+ * call was given (enabled by hough_enable_timing; off by default).  stage_ms covers the hit
+ * staging kernels, vote_ms the vote kernel alone, peaks_ms the peak search, stage2_ms membership
+ * and the stage-2 vote.  hough_get_timing synchronises; HOUGH_ENOTREADY before a timed event.
+ */
+typedef struct hough_timing {
+    float stage_ms, vote_ms, peaks_ms, stage2_ms;
+} hough_timing;
+
+int hough_enable_timing(hough_ctx *ctx, int on);
+int hough_get_timing(hough_ctx *ctx, hough_timing *out);
+
+/* Kernels this library has launched in the process so far (all contexts). */
+uint64_t hough_kernel_launches(void);
+
+/*
+ * Throughput of 32-bit shared-memory atomicOr on device `device`, the ceiling of the vote step
+ * (the vote is one shared atomic per cell update, Sec. 6.1).  pattern 0: the 32 lanes of a warp
+ * hit 32 different banks; pattern 1: lanes hit words of a random permutation of a 16 KB tile
+ * (the access pattern of the vote).  Runs a persistent grid of 152-multiple CTAs for about `ms`
+ * milliseconds and returns lane-atomics per second in *atomics_per_s.  Synchronises the device.
+ */
+int hough_microbench_smem_or(int device, int pattern, double ms, double *atomics_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOUGH_H */

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of the hough C ABI (``include/hough.h``): argument marshalling only.
+
+Every step of the path runs in the CUDA library.  There is no fallback: when the library is
+missing, loading it raises.  Device buffers are passed as raw pointers (anything with a
+``data_ptr()`` method, e.g. a CUDA torch tensor, or an integer), host buffers as numpy arrays,
+and a stream as a ``cudaStream_t`` value (e.g. ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HOST, DEVICE = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, ETRUNC, ECAPACITY, EBUSY, ETIMEDOUT, EDEVICE, ENOTREADY = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+MAX_LAYERS = 16
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhough.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class HoughError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hough error {code}: {msg}")
+        self.code = code
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int32), ("reserved", ctypes.c_int32), ("b_tesla", ctypes.c_double)]
+
+
+class Binning(ctypes.Structure):
+    _fields_ = [("n_qpt", ctypes.c_int32), ("n_phi", ctypes.c_int32), ("threshold", ctypes.c_int32),
+                ("n_cot", ctypes.c_int32), ("n_z0", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("qpt_min", ctypes.c_double), ("qpt_max", ctypes.c_double),
+                ("cot_min", ctypes.c_double), ("cot_max", ctypes.c_double),
+                ("z0_min_cm", ctypes.c_double), ("z0_max_cm", ctypes.c_double)]
+
+
+class Limits(ctypes.Structure):
+    _fields_ = [("max_hits", ctypes.c_int64), ("max_candidates", ctypes.c_int32),
+                ("max_members", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("votes", ctypes.c_uint64), ("votes_by_layer", ctypes.c_uint64 * MAX_LAYERS),
+                ("general_votes", ctypes.c_uint64), ("refined_votes", ctypes.c_uint64),
+                ("stage2_votes", ctypes.c_uint64), ("n_hits", ctypes.c_int64),
+                ("n_candidates", ctypes.c_int64), ("n_members", ctypes.c_int64),
+                ("device_error", ctypes.c_uint32), ("uniform_layers", ctypes.c_uint32)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("stage_ms", ctypes.c_float), ("vote_ms", ctypes.c_float), ("peaks_ms", ctypes.c_float),
+                ("stage2_ms", ctypes.c_float)]
+
+
+class Tiling(ctypes.Structure):
+    _fields_ = [("tile_qpt", ctypes.c_int32), ("tile_phi", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+CANDIDATE_DTYPE = np.dtype([("iq", np.uint32), ("jphi", np.uint32), ("mask", np.uint32),
+                            ("n_members", np.uint32), ("icot", np.uint32), ("jz0", np.uint32),
+                            ("mask2", np.uint32), ("flags", np.uint32)])
+assert CANDIDATE_DTYPE.itemsize == 32
+
+# Every entry point the header declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_I32, _I64 = ctypes.c_int32, ctypes.c_int64
+_SIGNATURES = {
+    "hough_last_error": ([], ctypes.c_char_p),
+    "hough_version": ([], ctypes.c_char_p),
+    "hough_create": ([ctypes.POINTER(Geometry), ctypes.POINTER(Binning), ctypes.POINTER(Limits), ctypes.c_int,
+                      ctypes.POINTER(_P)], ctypes.c_int),
+    "hough_destroy": ([_P], None),
+    "hough_vote": ([_P, _P, _P, _P, _P, _I64, ctypes.c_int, _P], ctypes.c_int),
+    "hough_peaks": ([_P, _P], ctypes.c_int),
+    "hough_stage2": ([_P, _P], ctypes.c_int),
+    "hough_get_candidates": ([_P, _P, _I32, ctypes.POINTER(_I32), ctypes.c_int, _P], ctypes.c_int),
+    "hough_get_accumulator": ([_P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "hough_get_members": ([_P, _P, _P, _I64, ctypes.c_int, _P], ctypes.c_int),
+    "hough_get_stats": ([_P, ctypes.POINTER(Stats), _P], ctypes.c_int),
+    "hough_process": ([_P, _P, _P, _P, _P, _I64, _P, _I32, ctypes.POINTER(_I32), ctypes.c_int, _P], ctypes.c_int),
+    "hough_set_tiling": ([_P, ctypes.POINTER(Tiling)], ctypes.c_int),
+    "hough_get_tiling": ([_P, ctypes.POINTER(Tiling)], ctypes.c_int),
+    "hough_enable_timing": ([_P, ctypes.c_int], ctypes.c_int),
+    "hough_get_timing": ([_P, ctypes.POINTER(Timing)], ctypes.c_int),
+    "hough_kernel_launches": ([], ctypes.c_uint64),
+    "hough_microbench_smem_or": ([ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+                                 ctypes.c_int),
+}
+
+
+def kernel_launches() -> int:
+    return int(load().hough_kernel_launches())
+
+
+def smem_or_throughput(device: int = 0, pattern: int = 0, ms: float = 50.0) -> float:
+    """Measured shared-memory atomicOr lane-operations per second on the device."""
+    out = ctypes.c_double(0.0)
+    _check(load().hough_microbench_smem_or(device, pattern, ms, ctypes.byref(out)))
+    return out.value
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Open the CUDA library (raises when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"hough CUDA library missing at {_LIB_PATH}; build it with "
+                                   "python -c 'import __graft_entry__ as g; g.build()'")
+            lib = ctypes.CDLL(_LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, allow=()):
+    if rc != OK and rc not in allow:
+        raise HoughError(rc, load().hough_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """Raw address of a buffer: numpy array, object with data_ptr(), integer or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def make_geometry(geometry) -> Geometry:
+    return Geometry(n_layers=geometry.n_layers, reserved=0, b_tesla=geometry.b_tesla)
+
+
+def make_binning(binning) -> Binning:
+    return Binning(n_qpt=binning.n_qpt, n_phi=binning.n_phi, threshold=binning.threshold,
+                   n_cot=binning.n_cot, n_z0=binning.n_z0, reserved=0,
+                   qpt_min=binning.qpt_min, qpt_max=binning.qpt_max,
+                   cot_min=binning.cot_min, cot_max=binning.cot_max,
+                   z0_min_cm=binning.z0_min, z0_max_cm=binning.z0_max)
+
+
+class HoughContext:
+    """One hough_ctx: a GPU, a set of axes and the device buffers sized by the limits."""
+
+    def __init__(self, geometry, binning, max_hits: int, max_candidates: int = 65536,
+                 max_members: int = 1 << 22, device: int = 0):
+        lib = load()
+        self._lib = lib
+        self.binning = binning
+        self.geometry = geometry
+        g, b = make_geometry(geometry), make_binning(binning)
+        lim = Limits(max_hits=max_hits, max_candidates=max_candidates, max_members=max_members)
+        h = _P()
+        _check(lib.hough_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(lim), device, ctypes.byref(h)))
+        self._h = h
+        self.max_candidates = max_candidates
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hough_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the path -----------------------------------------------------------------------------
+    def vote(self, r, phi, z, layer, n_hits=None, where=HOST, stream=None):
+        if where == HOST:
+            r, phi, z = (np.ascontiguousarray(a, dtype=np.float32) for a in (r, phi, z))
+            layer = np.ascontiguousarray(layer, dtype=np.uint8)
+            n_hits = r.shape[0]
+        self._keep = (r, phi, z, layer)
+        _check(self._lib.hough_vote(self._h, _ptr(r), _ptr(phi), _ptr(z), _ptr(layer), int(n_hits), where,
+                                    _stream(stream)))
+
+    def peaks(self, stream=None):
+        _check(self._lib.hough_peaks(self._h, _stream(stream)))
+
+    def stage2(self, stream=None):
+        _check(self._lib.hough_stage2(self._h, _stream(stream)))
+
+    def vote_event(self, event, stream=None):
+        self.vote(event.r, event.phi, event.z, event.layer, stream=stream)
+
+    # -- results ------------------------------------------------------------------------------
+    def candidates(self, cap=None, stream=None) -> np.ndarray:
+        cap = self.max_candidates if cap is None else cap
+        out = np.zeros(max(cap, 1), dtype=CANDIDATE_DTYPE)
+        n = _I32(0)
+        _check(self._lib.hough_get_candidates(self._h, _ptr(out), cap, ctypes.byref(n), HOST, _stream(stream)))
+        return out[: n.value].copy()
+
+    def accumulator(self, stream=None) -> np.ndarray:
+        out = np.zeros((self.binning.n_qpt, self.binning.n_phi), dtype=np.uint16)
+        _check(self._lib.hough_get_accumulator(self._h, _ptr(out), HOST, _stream(stream)))
+        return out
+
+    def members(self, n_candidates: int, hit_cap: int = 1 << 22, stream=None):
+        offsets = np.zeros(n_candidates + 1, dtype=np.int64)
+        hits = np.zeros(max(hit_cap, 1), dtype=np.int32)
+        _check(self._lib.hough_get_members(self._h, _ptr(offsets), _ptr(hits), hit_cap, HOST, _stream(stream)))
+        return offsets, hits[: offsets[-1]].copy()
+
+    def stats(self, stream=None, allow_device_error=False) -> Stats:
+        st = Stats()
+        _check(self._lib.hough_get_stats(self._h, ctypes.byref(st), _stream(stream)),
+               allow=(EDEVICE,) if allow_device_error else ())
+        return st
+
+    def process(self, r, phi, z, layer, n_hits=None, cap=None, out=None, stream=None) -> np.ndarray:
+        """Whole path on host-resident hits (numpy arrays, or pinned buffers with data_ptr())."""
+        cap = self.max_candidates if cap is None else cap
+        if isinstance(r, np.ndarray):
+            r, phi, z = (np.ascontiguousarray(a, dtype=np.float32) for a in (r, phi, z))
+            layer = np.ascontiguousarray(layer, dtype=np.uint8)
+            n_hits = r.shape[0]
+        if out is None:
+            out = np.zeros(max(cap, 1), dtype=CANDIDATE_DTYPE)
+        n = _I32(0)
+        _check(self._lib.hough_process(self._h, _ptr(r), _ptr(phi), _ptr(z), _ptr(layer), int(n_hits), _ptr(out),
+                                       cap, ctypes.byref(n), HOST, _stream(stream)))
+        return out[: n.value]
+
+    # -- timing -------------------------------------------------------------------------------
+    def enable_timing(self, on=True):
+        _check(self._lib.hough_enable_timing(self._h, 1 if on else 0))
+
+    def timing(self) -> dict:
+        t = Timing()
+        _check(self._lib.hough_get_timing(self._h, ctypes.byref(t)))
+        return dict(stage_ms=t.stage_ms, vote_ms=t.vote_ms, peaks_ms=t.peaks_ms, stage2_ms=t.stage2_ms)
+
+    # -- tiling -------------------------------------------------------------------------------
+    def set_tiling(self, tile_qpt: int, tile_phi: int, threads: int):
+        t = Tiling(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, reserved=0)
+        _check(self._lib.hough_set_tiling(self._h, ctypes.byref(t)))
+
+    def get_tiling(self):
+        t = Tiling()
+        _check(self._lib.hough_get_tiling(self._h, ctypes.byref(t)))
+        return (t.tile_qpt, t.tile_phi, t.threads)

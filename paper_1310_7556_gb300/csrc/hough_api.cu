@@ -1,0 +1,485 @@
+// C ABI of the hough library (declared in include/hough.h): argument checks, the context and its
+// device buffers, and the order in which the kernels of the path are enqueued.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hough_internal.cuh"
+
+using namespace hough;
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<uint64_t> g_launches{0};
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? HOUGH_ENOMEM : HOUGH_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+}  // namespace
+
+struct hough_ctx {
+    int device = 0;
+    int sms = 0;
+    hough_geometry geometry{};
+    hough_binning binning{};
+    hough_limits limits{};
+    Axes ax{};
+    Tiling tiling{};
+    float refine_eps = 0.f;
+    // device buffers
+    std::vector<void *> allocations;
+    Workspace w{};
+    int64_t *hit_start = nullptr;        // device, 2 entries, zero
+    float *in_r = nullptr, *in_phi = nullptr, *in_z = nullptr;
+    uint8_t *in_layer = nullptr;
+    int32_t *mem_idx = nullptr;
+    DevStats *stats_host = nullptr;      // pinned
+    int64_t n_hits = 0;
+    int stage = 0;                       // 0 nothing, 1 voted, 2 peaks, 3 stage 2
+    bool timing = false;
+    cudaEvent_t ev[5] = {};              // before staging, before vote, after vote, after peaks, after stage 2
+    int timed = 0;                       // bit k: ev[k] recorded for the current event
+
+    ~hough_ctx()
+    {
+        cudaSetDevice(device);
+        cudaDeviceSynchronize();
+        for (void *p : allocations) cudaFree(p);
+        if (stats_host) cudaFreeHost(stats_host);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    template <typename T>
+    cudaError_t alloc(T **p, size_t count)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) allocations.push_back(q);
+        *p = static_cast<T *>(q);
+        return e;
+    }
+};
+
+namespace {
+
+int check_binning(const hough_geometry *g, const hough_binning *b)
+{
+    if (!g || !b) return fail(HOUGH_EINVAL, "geometry and binning are required");
+    if (g->n_layers < 1 || g->n_layers > HOUGH_MAX_LAYERS) return fail(HOUGH_EINVAL, "n_layers must be 1..16");
+    if (g->reserved != 0 || b->reserved != 0) return fail(HOUGH_EINVAL, "reserved fields must be 0");
+    if (!(g->b_tesla > 0.0) || !std::isfinite(g->b_tesla)) return fail(HOUGH_EINVAL, "b_tesla must be > 0");
+    if (b->n_qpt < 1 || b->n_qpt > 65535) return fail(HOUGH_EINVAL, "n_qpt must be 1..65535");
+    if (b->n_phi < 64 || b->n_phi > 32768 || b->n_phi % 64) return fail(HOUGH_EINVAL, "n_phi must be a multiple of 64 in 64..32768");
+    if (b->threshold < 1 || b->threshold > 16) return fail(HOUGH_EINVAL, "threshold must be 1..16");
+    if (b->n_cot < 1 || b->n_cot > 256 || b->n_z0 < 1 || b->n_z0 > 256 || b->n_cot * b->n_z0 > 16384)
+        return fail(HOUGH_EINVAL, "n_cot and n_z0 must be 1..256 with n_cot * n_z0 <= 16384");
+    if (!(b->qpt_min < b->qpt_max) || !(b->cot_min < b->cot_max) || !(b->z0_min_cm < b->z0_max_cm))
+        return fail(HOUGH_EINVAL, "axis minimum must be below its maximum");
+    if (!std::isfinite(b->qpt_min) || !std::isfinite(b->qpt_max) || !std::isfinite(b->cot_min) ||
+        !std::isfinite(b->cot_max) || !std::isfinite(b->z0_min_cm) || !std::isfinite(b->z0_max_cm))
+        return fail(HOUGH_EINVAL, "axis bounds must be finite");
+    return HOUGH_OK;
+}
+
+Axes make_axes(const hough_geometry *g, const hough_binning *b)
+{
+    Axes ax;
+    ax.n_layers = g->n_layers;
+    ax.n_qpt = b->n_qpt;
+    ax.n_phi = b->n_phi;
+    ax.threshold = b->threshold;
+    ax.n_cot = b->n_cot;
+    ax.n_z0 = b->n_z0;
+    ax.b = g->b_tesla;
+    ax.qpt_min = b->qpt_min;
+    ax.qpt_max = b->qpt_max;
+    ax.dk = (b->qpt_max - b->qpt_min) / b->n_qpt;
+    ax.cot_min = b->cot_min;
+    ax.cot_max = b->cot_max;
+    ax.dt = (b->cot_max - b->cot_min) / b->n_cot;
+    ax.z0_min = b->z0_min_cm;
+    ax.z0_max = b->z0_max_cm;
+    return ax;
+}
+
+int check_tiling(const hough_ctx *c, const hough_tiling *t)
+{
+    if (!t) return fail(HOUGH_EINVAL, "tiling is required");
+    if (t->tile_qpt < 1 || t->tile_qpt > 256) return fail(HOUGH_EINVAL, "tile_qpt must be 1..256");
+    if (t->tile_phi < 64 || t->tile_phi % 64 || c->ax.n_phi % t->tile_phi)
+        return fail(HOUGH_EINVAL, "tile_phi must be a multiple of 64 dividing n_phi");
+    if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
+        return fail(HOUGH_EINVAL, "threads must be 128, 256, 512 or 1024");
+    Tiling tt{t->tile_qpt, t->tile_phi, t->threads};
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (vote_smem_bytes(c->ax, tt) + 1024 > (size_t)max_smem)
+        return fail(HOUGH_EINVAL, "tile needs %zu bytes of shared memory, the device allows %d",
+                    vote_smem_bytes(c->ax, tt), max_smem);
+    return HOUGH_OK;
+}
+
+Tiling default_tiling(const Axes &ax)
+{
+    Tiling t;
+    t.tile_phi = std::min(ax.n_phi, 256);
+    while (ax.n_phi % t.tile_phi) t.tile_phi -= 64;
+    t.tile_qpt = std::min(ax.n_qpt, 16);
+    t.threads = 256;
+    return t;
+}
+
+int check_host_hits(const hough_ctx *c, const float *r, const float *phi, const float *z,
+                    const uint8_t *layer, int64_t n)
+{
+    for (int64_t h = 0; h < n; ++h) {
+        if (layer[h] >= c->ax.n_layers) return fail(HOUGH_EINVAL, "hit %lld: layer %d >= n_layers", (long long)h, layer[h]);
+        if (!(r[h] > 0.f) || !std::isfinite(r[h])) return fail(HOUGH_EINVAL, "hit %lld: r must be finite and > 0", (long long)h);
+        if (!(std::fabs(phi[h]) <= 1000.f)) return fail(HOUGH_EINVAL, "hit %lld: phi must be finite, |phi| <= 1000", (long long)h);
+        if (!std::isfinite(z[h])) return fail(HOUGH_EINVAL, "hit %lld: z must be finite", (long long)h);
+    }
+    return HOUGH_OK;
+}
+
+int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                 int64_t n, int where, cudaStream_t s)
+{
+    if (n < 0) return fail(HOUGH_EINVAL, "n_hits must be >= 0");
+    if (n > c->limits.max_hits) return fail(HOUGH_ECAPACITY, "n_hits %lld exceeds max_hits %lld", (long long)n, (long long)c->limits.max_hits);
+    if (where != HOUGH_HOST && where != HOUGH_DEVICE) return fail(HOUGH_EINVAL, "where must be HOUGH_HOST or HOUGH_DEVICE");
+    if (n > 0 && (!r || !phi || !z || !layer)) return fail(HOUGH_EINVAL, "hit arrays are required");
+    if (where == HOUGH_HOST) {
+        int rc = check_host_hits(c, r, phi, z, layer, n);
+        if (rc) return rc;
+        if (n > 0) {
+            CU(cudaMemcpyAsync(c->in_r, r, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy r");
+            CU(cudaMemcpyAsync(c->in_phi, phi, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy phi");
+            CU(cudaMemcpyAsync(c->in_z, z, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy z");
+            CU(cudaMemcpyAsync(c->in_layer, layer, n, cudaMemcpyHostToDevice, s), "copy layer");
+        }
+        c->w.r = c->in_r; c->w.phi = c->in_phi; c->w.z = c->in_z; c->w.layer = c->in_layer;
+    } else {
+        c->w.r = r; c->w.phi = phi; c->w.z = z; c->w.layer = layer;
+    }
+    // one event: its hits start at 0 (hit_start holds {0, 0} from creation; the kernels read
+    // only the start of an event and take the total by value)
+    c->w.n_hits_total = n;
+    c->n_hits = n;
+    c->timed = 0;
+    if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1; }
+    CU(launch_stage(c->ax, c->w, s), "stage kernels");
+    if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
+    CU(launch_vote(c->ax, c->w, c->tiling, c->refine_eps, s), "vote kernel");
+    if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
+    g_launches += kStageLaunches + kVoteLaunches;
+    c->stage = 1;
+    return HOUGH_OK;
+}
+
+int read_stats(hough_ctx *c, cudaStream_t s)
+{
+    CU(cudaMemcpyAsync(c->stats_host, c->w.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "copy stats");
+    CU(cudaStreamSynchronize(s), "synchronise");
+    return HOUGH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hough_last_error(void) { return g_err; }
+
+const char *hough_version(void) { return "0.1.0"; }
+
+int hough_create(const hough_geometry *geometry, const hough_binning *binning, const hough_limits *limits,
+                 int device, hough_ctx **out)
+{
+    if (!out) return fail(HOUGH_EINVAL, "out is required");
+    *out = nullptr;
+    int rc = check_binning(geometry, binning);
+    if (rc) return rc;
+    if (!limits || limits->max_hits < 1 || limits->max_hits > (1LL << 30) || limits->max_candidates < 1 ||
+        limits->max_members < 1)
+        return fail(HOUGH_EINVAL, "limits: max_hits in 1..2^30, max_candidates >= 1, max_members >= 1");
+    int ndev = 0;
+    CU(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(HOUGH_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    CU(cudaSetDevice(device), "cudaSetDevice");
+    hough_ctx *c = new (std::nothrow) hough_ctx();
+    if (!c) return fail(HOUGH_ENOMEM, "host allocation");
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    c->geometry = *geometry;
+    c->binning = *binning;
+    c->limits = *limits;
+    c->ax = make_axes(geometry, binning);
+    c->tiling = default_tiling(c->ax);
+    c->refine_eps = refine_eps_for(c->ax);
+    const Axes &ax = c->ax;
+    const int64_t n = limits->max_hits;
+    const int nkeys = n_keys(ax);
+    Workspace &w = c->w;
+    w.n_events = 1;
+    w.max_cand = limits->max_candidates;
+    w.max_members = limits->max_members;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(c->alloc(&c->hit_start, 2));
+    A(c->alloc(&c->in_r, n)); A(c->alloc(&c->in_phi, n)); A(c->alloc(&c->in_z, n)); A(c->alloc(&c->in_layer, n));
+    A(c->alloc(&w.key, n)); A(c->alloc(&w.rank, n)); A(c->alloc(&w.hot_tmp, n));
+    A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1));
+    A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n));
+    A(c->alloc(&w.radii, 1)); A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
+    A(c->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(c->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
+    A(c->alloc(&w.kq32, ax.n_qpt));
+    A(c->alloc(&w.M, (size_t)ax.n_qpt * ax.n_phi));
+    A(c->alloc(&w.cands, w.max_cand));
+    A(c->alloc(&w.band_counts, n_bands(ax))); A(c->alloc(&w.band_offs, n_bands(ax)));
+    A(c->alloc(&w.mem_counts, w.max_cand)); A(c->alloc(&w.mem_offs, (size_t)w.max_cand + 1));
+    A(c->alloc(&w.mem_pos, w.max_members)); A(c->alloc(&c->mem_idx, w.max_members));
+    A(c->alloc(&w.stats, 1));
+    A(cudaMallocHost(&c->stats_host, sizeof(DevStats)));
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "hough_create allocation");
+    }
+    w.hit_start = c->hit_start;
+    // FP32 q/pT bin centres: the FP64 centre rounded once
+    std::vector<float> kq(ax.n_qpt);
+    for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i + 0.5) * ax.dk);
+    A(cudaMemcpy(w.kq32, kq.data(), sizeof(float) * ax.n_qpt, cudaMemcpyHostToDevice));
+    A(cudaMemset(c->hit_start, 0, 2 * sizeof(int64_t)));
+    A(cudaMemset(w.memo, 0, sizeof(TableMemo)));
+    A(cudaMemset(w.stats, 0, sizeof(DevStats)));
+    A(cudaDeviceSynchronize());
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "hough_create initialisation");
+    }
+    *out = c;
+    return HOUGH_OK;
+}
+
+void hough_destroy(hough_ctx *ctx) { delete ctx; }
+
+int hough_vote(hough_ctx *c, const float *r, const float *phi, const float *z, const uint8_t *layer,
+               int64_t n_hits, int where, void *stream)
+{
+    if (!c) return fail(HOUGH_EINVAL, "ctx is required");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    return enqueue_vote(c, r, phi, z, layer, n_hits, where, (cudaStream_t)stream);
+}
+
+int hough_peaks(hough_ctx *c, void *stream)
+{
+    if (!c) return fail(HOUGH_EINVAL, "ctx is required");
+    if (c->stage < 1) return fail(HOUGH_ENOTREADY, "hough_vote has not run");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    CU(launch_peaks(c->ax, c->w, (cudaStream_t)stream), "peak kernels");
+    if (c->timing) { CU(cudaEventRecord(c->ev[3], (cudaStream_t)stream), "event"); c->timed |= 8; }
+    g_launches += kPeakLaunches;
+    c->stage = 2;
+    return HOUGH_OK;
+}
+
+int hough_stage2(hough_ctx *c, void *stream)
+{
+    if (!c) return fail(HOUGH_EINVAL, "ctx is required");
+    if (c->stage < 2) return fail(HOUGH_ENOTREADY, "hough_peaks has not run");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    CU(launch_stage2(c->ax, c->w, c->sms, (cudaStream_t)stream), "stage-2 kernels");
+    if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
+    g_launches += kStage2Launches;
+    c->stage = 3;
+    return HOUGH_OK;
+}
+
+int hough_get_candidates(hough_ctx *c, hough_candidate *out, int32_t cap, int32_t *n_out, int where, void *stream)
+{
+    if (!c || !n_out || cap < 0 || (cap > 0 && !out)) return fail(HOUGH_EINVAL, "bad arguments");
+    if (where != HOUGH_HOST && where != HOUGH_DEVICE) return fail(HOUGH_EINVAL, "bad where");
+    if (c->stage < 2) return fail(HOUGH_ENOTREADY, "hough_peaks has not run");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = read_stats(c, s);
+    if (rc) return rc;
+    const int64_t found = c->stats_host->n_candidates;
+    const int64_t kept = std::min<int64_t>(found, c->w.max_cand);
+    const int64_t ncopy = std::min<int64_t>(kept, cap);
+    *n_out = (int32_t)std::min<int64_t>(found, INT32_MAX);
+    if (ncopy > 0) {
+        CU(cudaMemcpyAsync(out, c->w.cands, sizeof(hough_candidate) * ncopy,
+                           where == HOUGH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s),
+           "copy candidates");
+        CU(cudaStreamSynchronize(s), "synchronise");
+    }
+    if (found > cap) return fail(HOUGH_ETRUNC, "%lld candidates, capacity %d", (long long)found, cap);
+    if (found > kept) return fail(HOUGH_ETRUNC, "%lld candidates, max_candidates %d", (long long)found, c->w.max_cand);
+    return HOUGH_OK;
+}
+
+int hough_get_accumulator(hough_ctx *c, uint16_t *out, int where, void *stream)
+{
+    if (!c || !out) return fail(HOUGH_EINVAL, "bad arguments");
+    if (where != HOUGH_HOST && where != HOUGH_DEVICE) return fail(HOUGH_EINVAL, "bad where");
+    if (c->stage < 1) return fail(HOUGH_ENOTREADY, "hough_vote has not run");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(out, c->w.M, sizeof(uint16_t) * (size_t)c->ax.n_qpt * c->ax.n_phi,
+                       where == HOUGH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s),
+       "copy accumulator");
+    CU(cudaStreamSynchronize(s), "synchronise");
+    return HOUGH_OK;
+}
+
+int hough_get_members(hough_ctx *c, int64_t *offsets, int32_t *hits, int64_t hit_cap, int where, void *stream)
+{
+    if (!c || !offsets || hit_cap < 0 || (hit_cap > 0 && !hits)) return fail(HOUGH_EINVAL, "bad arguments");
+    if (where != HOUGH_HOST) return fail(HOUGH_EINVAL, "member lists are returned to host memory only");
+    if (c->stage < 3) return fail(HOUGH_ENOTREADY, "hough_stage2 has not run");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = read_stats(c, s);
+    if (rc) return rc;
+    const int64_t ncand = std::min<int64_t>(c->stats_host->n_candidates, c->w.max_cand);
+    CU(cudaMemcpyAsync(offsets, c->w.mem_offs, sizeof(int64_t) * (ncand + 1), cudaMemcpyDeviceToHost, s), "copy offsets");
+    CU(cudaStreamSynchronize(s), "synchronise");
+    const int64_t total = std::min<int64_t>(offsets[ncand], c->w.max_members);
+    const int64_t ncopy = std::min(total, hit_cap);
+    CU(launch_member_index(c->w, c->mem_idx, ncopy, s), "member index kernel");
+    if (ncopy > 0) CU(cudaMemcpyAsync(hits, c->mem_idx, sizeof(int32_t) * ncopy, cudaMemcpyDeviceToHost, s), "copy members");
+    CU(cudaStreamSynchronize(s), "synchronise");
+    for (int64_t q = 0; q < ncand; ++q) {
+        const int64_t a = std::min(offsets[q], ncopy), b = std::min(offsets[q + 1], ncopy);
+        if (b > a) std::sort(hits + a, hits + b);
+    }
+    if (offsets[ncand] > hit_cap || offsets[ncand] > c->w.max_members)
+        return fail(HOUGH_ETRUNC, "%lld member hits, capacity %lld", (long long)offsets[ncand], (long long)std::min<int64_t>(hit_cap, c->w.max_members));
+    return HOUGH_OK;
+}
+
+int hough_get_stats(hough_ctx *c, hough_stats *out, void *stream)
+{
+    if (!c || !out) return fail(HOUGH_EINVAL, "bad arguments");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = read_stats(c, s);
+    if (rc) return rc;
+    LayerInfo info[HOUGH_MAX_LAYERS];
+    CU(cudaMemcpy(info, c->w.info, sizeof(info), cudaMemcpyDeviceToHost), "copy layer info");
+    const DevStats &d = *c->stats_host;
+    std::memset(out, 0, sizeof(*out));
+    for (int l = 0; l < HOUGH_MAX_LAYERS; ++l) {
+        out->votes_by_layer[l] = d.votes_by_layer[l];
+        out->votes += d.votes_by_layer[l];
+        if (l < c->ax.n_layers && info[l].uniform) out->uniform_layers |= 1u << l;
+        else out->general_votes += d.votes_by_layer[l];
+    }
+    out->refined_votes = d.refined_votes;
+    out->stage2_votes = d.stage2_votes;
+    out->n_hits = (int64_t)d.n_hits;
+    out->n_candidates = d.n_candidates;
+    out->n_members = d.n_members;
+    out->device_error = d.device_error;
+    if (d.device_error) return fail(HOUGH_EDEVICE, "device-side check failed: bits 0x%x", d.device_error);
+    return HOUGH_OK;
+}
+
+int hough_process(hough_ctx *c, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                  int64_t n_hits, hough_candidate *out, int32_t cap, int32_t *n_out, int where, void *stream)
+{
+    int rc = hough_vote(c, r, phi, z, layer, n_hits, where, stream);
+    if (rc) return rc;
+    if ((rc = hough_peaks(c, stream))) return rc;
+    if ((rc = hough_stage2(c, stream))) return rc;
+    return hough_get_candidates(c, out, cap, n_out, where, stream);
+}
+
+int hough_set_tiling(hough_ctx *c, const hough_tiling *t)
+{
+    if (!c) return fail(HOUGH_EINVAL, "ctx is required");
+    int rc = check_tiling(c, t);
+    if (rc) return rc;
+    c->tiling = Tiling{t->tile_qpt, t->tile_phi, t->threads};
+    return HOUGH_OK;
+}
+
+int hough_enable_timing(hough_ctx *c, int on)
+{
+    if (!c) return fail(HOUGH_EINVAL, "ctx is required");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    if (on && !c->ev[0])
+        for (cudaEvent_t &e : c->ev) CU(cudaEventCreate(&e), "cudaEventCreate");
+    c->timing = on != 0;
+    c->timed = 0;
+    return HOUGH_OK;
+}
+
+int hough_get_timing(hough_ctx *c, hough_timing *out)
+{
+    if (!c || !out) return fail(HOUGH_EINVAL, "bad arguments");
+    if (!(c->timed & 7)) return fail(HOUGH_ENOTREADY, "no timed event");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    float ms[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < 4; ++k) {
+        if ((c->timed >> (k + 1)) & 1) {
+            CU(cudaEventSynchronize(c->ev[k + 1]), "event synchronise");
+            CU(cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]), "event elapsed");
+        }
+    }
+    out->stage_ms = ms[0];
+    out->vote_ms = ms[1];
+    out->peaks_ms = ms[2];
+    out->stage2_ms = ms[3];
+    return HOUGH_OK;
+}
+
+uint64_t hough_kernel_launches(void) { return g_launches.load(); }
+
+int hough_microbench_smem_or(int device, int pattern, double ms, double *atomics_per_s)
+{
+    if (!atomics_per_s || (pattern != 0 && pattern != 1) || !(ms > 0.0) || ms > 10000.0)
+        return fail(HOUGH_EINVAL, "bad arguments");
+    uint64_t n = 0;
+    cudaError_t e = run_smem_or_bench(device, pattern, ms, atomics_per_s, &n);
+    g_launches += n;
+    if (e) return cuda_fail(e, "shared-atomic microbenchmark");
+    return HOUGH_OK;
+}
+
+int hough_get_tiling(const hough_ctx *c, hough_tiling *t)
+{
+    if (!c || !t) return fail(HOUGH_EINVAL, "bad arguments");
+    t->tile_qpt = c->tiling.tile_qpt;
+    t->tile_phi = c->tiling.tile_phi;
+    t->threads = c->tiling.threads;
+    t->reserved = 0;
+    return HOUGH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+"""Comparison of the CUDA path with the FP64 oracle under the parity rule.
+
+Rule: the integer layer masks and the candidate list are bit-exact, except where a vote the
+oracle flags (its bin coordinate within 1e-4 bin of an edge, or |x| within 1e-6 of 1) may
+legitimately land on the other side in FP32; the number of mismatched (cell, layer) pairs must
+not exceed the number of flagged votes, and each must be explained by one.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _allowed_cells(flags, n_phi):
+    """(row, bin, layer) triples a flagged vote may touch; a domain-edge flag with no bin on the
+    oracle side allows any bin of the row for that layer (stored with bin -1)."""
+    allowed = set()
+    for f in flags:
+        row, lay = int(f["row"]), int(f["layer"])
+        for b in (f["bin"], f["alt"]):
+            if b >= 0:
+                allowed.add((row, int(b) % n_phi, lay))
+        if int(f["kind"]) == 2:
+            allowed.add((row, -1, lay))
+    return allowed
+
+
+def accumulator_mismatches(M_gpu: np.ndarray, M_ref: np.ndarray, flags) -> tuple[list, list]:
+    """Returns (all mismatched (i, j, layer) triples, those no flagged vote explains)."""
+    n_phi = M_ref.shape[1]
+    allowed = _allowed_cells(flags, n_phi)
+    diff = np.argwhere(M_gpu != M_ref)
+    mism, unexplained = [], []
+    for i, j in diff:
+        x = int(M_gpu[i, j]) ^ int(M_ref[i, j])
+        for l in range(16):
+            if (x >> l) & 1:
+                t = (int(i), int(j), l)
+                mism.append(t)
+                if t not in allowed and (int(i), -1, l) not in allowed:
+                    unexplained.append(t)
+    return mism, unexplained
+
+
+def assert_accumulator_parity(M_gpu, M_ref, flags):
+    mism, unexplained = accumulator_mismatches(M_gpu, M_ref, flags)
+    assert not unexplained, f"{len(unexplained)} accumulator bits differ at unflagged votes: {unexplained[:8]}"
+    assert len(mism) <= len(flags), f"{len(mism)} mismatched bits > {len(flags)} flagged votes"
+    return len(mism)
+
+
+def _touched(flags, n_phi):
+    cells = set()
+    for f in flags:
+        for b in (f["bin"], f["alt"]):
+            if b >= 0:
+                cells.add((int(f["row"]), int(b) % n_phi))
+        if int(f["kind"]) == 2:
+            cells.add((int(f["row"]), -1))
+    return cells
+
+
+def assert_candidate_parity(c_gpu, c_ref, flags, n_phi):
+    """Candidate lists equal, except candidates whose 3 x 3 block holds a cell a flagged vote touched."""
+    touched = _touched(flags, n_phi)
+    rows_any = {i for (i, j) in touched if j == -1}
+
+    def near(i, j):
+        for di in (-1, 0, 1):
+            if i + di in rows_any:
+                return True
+            for dj in (-1, 0, 1):
+                if (i + di, (j + dj) % n_phi) in touched:
+                    return True
+        return False
+
+    g = {(int(c["iq"]), int(c["jphi"])): int(c["mask"]) for c in c_gpu}
+    r = {(int(c["iq"]), int(c["jphi"])): int(c["mask"]) for c in c_ref}
+    bad = [k for k in set(g) ^ set(r) if not near(*k)]
+    bad += [k for k in set(g) & set(r) if g[k] != r[k] and not near(*k)]
+    assert not bad, f"{len(bad)} candidates differ away from flagged votes: {sorted(bad)[:8]}"
+    # order: raster
+    keys = [(int(c["iq"]), int(c["jphi"])) for c in c_gpu]
+    assert keys == sorted(keys), "GPU candidates are not in raster order"
+    return len(set(g) ^ set(r))
+
+
+def assert_members_and_stage2_parity(c_gpu, off_gpu, mem_gpu, ref, threshold):
+    """Member lists and stage-2 results of candidates present on both sides.
+
+    A member list may differ only by hits whose vote on that row the oracle flags; a stage-2
+    result may differ only for such candidates or where the oracle flags a z0 vote."""
+    c_ref = ref["candidates"]
+    index_ref = {(int(c["iq"]), int(c["jphi"])): q for q, c in enumerate(c_ref)}
+    mflag_hits = {}
+    for f in ref["member_flags"]:
+        mflag_hits.setdefault(int(f["cand"]), set()).add(int(f["hit"]))
+    zflag_cands = {int(f["cand"]) for f in ref["stage2_flags"]}
+    checked = 0
+    for q, c in enumerate(c_gpu):
+        key = (int(c["iq"]), int(c["jphi"]))
+        if key not in index_ref:
+            continue
+        p = index_ref[key]
+        mg = set(mem_gpu[off_gpu[q]:off_gpu[q + 1]].tolist())
+        mr = set(ref["members"][ref["member_offsets"][p]:ref["member_offsets"][p + 1]].tolist())
+        assert list(mem_gpu[off_gpu[q]:off_gpu[q + 1]]) == sorted(mg), "member list not sorted"
+        diff = mg ^ mr
+        assert diff <= mflag_hits.get(p, set()), f"candidate {key}: members differ at unflagged hits {sorted(diff)[:8]}"
+        assert int(c["n_members"]) == len(mg)
+        if diff or p in zflag_cands:
+            continue
+        s = ref["stage2"][p]
+        assert (int(c["icot"]), int(c["jz0"]), int(c["mask2"])) == (int(s["icot"]), int(s["jz0"]), int(s["mask2"])), \
+            f"candidate {key}: stage 2 {(int(c['icot']), int(c['jz0']), int(c['mask2']))} vs oracle {tuple(int(v) for v in s)[:3]}"
+        assert (int(c["flags"]) & 1) == (1 if bin(int(s["mask2"])).count("1") >= threshold else 0)
+        checked += 1
+    return checked

@@ -1,0 +1,225 @@
+"""Parity of the CUDA path with the FP64 oracle, called through the C ABI (needs a GPU).
+
+Element by element: the accumulator's layer masks, the vote count, the candidate list (raster
+order), member lists and stage-2 results, bit-exact except where the oracle flags a vote within
+its edge window (see tests/parity.py for the rule)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_7556_gb300 import eventgen as eg
+
+from parity import (assert_accumulator_parity, assert_candidate_parity,
+                    assert_members_and_stage2_parity)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def binding():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1310_7556_gb300 import binding as b
+    b.load()
+    return b
+
+
+def run_gpu(binding, geometry, binning, ev, tiling=None, where="host", max_candidates=1 << 18):
+    with binding.HoughContext(geometry, binning, max_hits=max(ev.n_hits, 1), max_candidates=max_candidates) as ctx:
+        if tiling:
+            ctx.set_tiling(*tiling)
+        if where == "host":
+            ctx.vote_event(ev)
+        else:
+            import torch
+            t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (ev.r, ev.phi, ev.z, ev.layer)]
+            torch.cuda.synchronize()
+            ctx.vote(*t, n_hits=ev.n_hits, where=binding.DEVICE)
+        ctx.peaks()
+        ctx.stage2()
+        M = ctx.accumulator()
+        cands = ctx.candidates()
+        st = ctx.stats()
+        off, mem = ctx.members(len(cands))
+    return dict(M=M, candidates=cands, stats=st, member_offsets=off, members=mem)
+
+
+def check_event(binding, geometry, binning, ev, **kw):
+    ref = oracle.run(geometry, binning, ev)
+    got = run_gpu(binding, geometry, binning, ev, **kw)
+    n_bits = assert_accumulator_parity(got["M"], ref["M"], ref["vote_flags"])
+    assert int(got["stats"].votes) == int(ref["votes_by_layer"].sum())
+    for l in range(geometry.n_layers):
+        assert int(got["stats"].votes_by_layer[l]) == int(ref["votes_by_layer"][l])
+    n_c = assert_candidate_parity(got["candidates"], ref["candidates"], ref["vote_flags"], binning.n_phi)
+    checked = assert_members_and_stage2_parity(got["candidates"], got["member_offsets"], got["members"], ref,
+                                               binning.threshold)
+    return dict(ref=ref, got=got, mismatched_bits=n_bits, mismatched_cands=n_c, stage2_checked=checked)
+
+
+@pytest.mark.parametrize("index", range(4))
+def test_single_event_50_tracks(binding, index):
+    w = eg.WORKLOADS["single_50trk"]
+    r = check_event(binding, w.geometry, w.binning, w.event(index))
+    assert r["stage2_checked"] > 0
+
+
+def test_pileup_event_full_size(binding):
+    """The 100k-hit pileup event at its full 512 x 2048 binning, every cell compared."""
+    w = eg.WORKLOADS["pileup_100k"]
+    r = check_event(binding, w.geometry, w.binning, w.event(0))
+    assert r["got"]["stats"].uniform_layers == (1 << 10) - 1
+    assert r["got"]["stats"].refined_votes == 0
+
+
+def test_fine_binning_event_full_size(binding):
+    """The 400k-hit, 1024 x 4096 event, every cell compared."""
+    w = eg.WORKLOADS["fine_4m"]
+    check_event(binding, w.geometry, w.binning, w.event(0))
+
+
+def test_device_pointers_match_host_path(binding):
+    w = eg.WORKLOADS["pileup_100k"]
+    ev = w.event(5).subset(np.arange(30000))
+    a = run_gpu(binding, w.geometry, w.binning, ev, where="host")
+    b = run_gpu(binding, w.geometry, w.binning, ev, where="device")
+    assert np.array_equal(a["M"], b["M"])
+    assert np.array_equal(a["candidates"], b["candidates"])
+
+
+@pytest.mark.parametrize("tiling", [(1, 64, 128), (7, 128, 256), (16, 256, 256), (32, 512, 512),
+                                    (64, 1024, 1024), (3, 2048, 128)])
+def test_tilings_agree_bit_for_bit(binding, tiling):
+    """Every tile shape, including ragged last slabs (512 rows by 7 or 3), gives the same result."""
+    w = eg.WORKLOADS["pileup_100k"]
+    ev = w.event(2).subset(np.arange(40000))
+    base = run_gpu(binding, w.geometry, w.binning, ev)
+    other = run_gpu(binding, w.geometry, w.binning, ev, tiling=tiling)
+    assert np.array_equal(base["M"], other["M"])
+    assert np.array_equal(base["candidates"], other["candidates"])
+
+
+def test_per_vote_path_for_non_uniform_radii(binding):
+    """Hits of a layer at different radii take the FP32 asinf path with FP64 edge refinement."""
+    w = eg.WORKLOADS["pileup_100k"]
+    ev = w.event(3).subset(np.arange(20000))
+    rng = np.random.default_rng(1)
+    ev.r = (ev.r + rng.uniform(-0.5, 0.5, ev.n_hits)).astype(np.float32)
+    r = check_event(binding, w.geometry, w.binning, ev)
+    st = r["got"]["stats"]
+    assert st.uniform_layers == 0 and st.general_votes == st.votes and st.refined_votes > 0
+
+
+def test_mixed_uniform_and_non_uniform_layers(binding):
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(7)
+    jitter = ev.layer % 2 == 1
+    ev.r = np.where(jitter, ev.r * np.float32(1.003), ev.r).astype(np.float32)
+    ev.r[np.nonzero(jitter)[0][::2]] *= np.float32(0.999)
+    r = check_event(binding, w.geometry, w.binning, ev)
+    assert r["got"]["stats"].uniform_layers == 0b0101010101
+
+
+# ---------------------------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------------------------
+
+def _event(r, phi, z, layer):
+    return eg.Event(np.asarray(r, np.float32), np.asarray(phi, np.float32), np.asarray(z, np.float32),
+                    np.asarray(layer, np.uint8), np.zeros(len(r), np.int32))
+
+
+def test_empty_event(binding):
+    w = eg.WORKLOADS["single_50trk"]
+    got = run_gpu(binding, w.geometry, w.binning, _event([], [], [], []))
+    assert not got["M"].any() and len(got["candidates"]) == 0 and got["stats"].votes == 0
+
+
+def test_single_hit_and_extreme_azimuths(binding):
+    w = eg.WORKLOADS["pileup_100k"]
+    pi32 = np.float32(math.pi)
+    phis = [0.0, pi32, -pi32, np.nextafter(pi32, np.float32(0)), 3.1415926, -3.1415926, 999.0, -999.0, 1e-30]
+    for phi in phis:
+        check_event(binding, w.geometry, w.binning, _event([110.0], [phi], [0.0], [9]))
+
+
+def test_all_hits_at_one_azimuth(binding):
+    """Degenerate pileup: every hit of every layer at the same phi (hot-spot atomics, one bucket)."""
+    w = eg.WORKLOADS["pileup_100k"]
+    n = 5000
+    layer = np.arange(n) % 10
+    r = np.asarray(w.geometry.radii_cm, np.float32)[layer]
+    check_event(binding, w.geometry, w.binning, _event(r, np.full(n, 0.7), np.zeros(n), layer))
+
+
+def test_one_row_grid_and_narrow_phi(binding):
+    g = eg.Geometry()
+    bn = eg.Binning(n_qpt=1, qpt_min=-0.3, qpt_max=0.1, n_phi=64, threshold=2)
+    check_event(binding, g, bn, eg.WORKLOADS["single_50trk"].event(3))
+
+
+def test_odd_sizes_and_few_layers(binding):
+    """3 layers, 77 rows, 192 columns: ragged slabs and a non-power-of-two phi axis."""
+    g = eg.Geometry(radii_cm=(5.0, 30.0, 90.0), b_tesla=2.0)
+    bn = eg.Binning(n_qpt=77, qpt_min=-1.3, qpt_max=0.9, n_phi=192, threshold=2, n_cot=17, n_z0=23,
+                    cot_min=-3.0, cot_max=2.0, z0_min=-20.0, z0_max=10.0)
+    ev = eg.simulate_event(g, 40, (0.7, 20.0), 30, seed=99)
+    check_event(binding, g, bn, ev, tiling=(5, 64, 128))
+    check_event(binding, g, bn, ev)
+
+
+def test_candidate_capacity_truncates_in_raster_order(binding):
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(0)
+    ref = oracle.run(w.geometry, w.binning, ev)
+    n = len(ref["candidates"])
+    assert n > 10
+    with binding.HoughContext(w.geometry, w.binning, max_hits=ev.n_hits, max_candidates=10) as ctx:
+        ctx.vote_event(ev)
+        ctx.peaks()
+        ctx.stage2()
+        with pytest.raises(binding.HoughError) as e:
+            ctx.candidates(cap=10)
+        assert e.value.code == binding.ETRUNC
+        st = ctx.stats(allow_device_error=True)
+        assert st.device_error & 4 and st.n_candidates == n
+        out = np.zeros(10, dtype=binding.CANDIDATE_DTYPE)
+        import ctypes
+        nn = ctypes.c_int32(0)
+        rc = binding.load().hough_get_candidates(ctx._h, out.ctypes.data, 10, ctypes.byref(nn), binding.HOST, None)
+        assert rc == binding.ETRUNC and nn.value == n
+        assert [(int(c["iq"]), int(c["jphi"])) for c in out] == \
+            [(int(c["iq"]), int(c["jphi"])) for c in ref["candidates"][:10]]
+
+
+def test_bad_hits(binding):
+    """Host buffers: a bad hit is rejected with HOUGH_EINVAL before any work.  Device buffers: it
+    is dropped on the device, flagged in device_error, and the other hits vote as usual."""
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(1)
+    bad = _event(np.r_[ev.r, 30.0, -1.0], np.r_[ev.phi, 0.1, 0.2], np.r_[ev.z, 0, 0], np.r_[ev.layer, 12, 3])
+    with binding.HoughContext(w.geometry, w.binning, max_hits=bad.n_hits) as ctx:
+        with pytest.raises(binding.HoughError) as e:
+            ctx.vote_event(bad)
+        assert e.value.code == binding.EINVAL
+        import torch
+        t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (bad.r, bad.phi, bad.z, bad.layer)]
+        ctx.vote(*t, n_hits=bad.n_hits, where=binding.DEVICE)
+        ctx.peaks()
+        st = ctx.stats(allow_device_error=True)
+        assert st.device_error == 1 | 2 and st.n_hits == ev.n_hits
+        M = ctx.accumulator()
+    ref = oracle.run(w.geometry, w.binning, ev)
+    assert_accumulator_parity(M, ref["M"], ref["vote_flags"])
+
+
+def test_capacity_error(binding):
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(0)
+    with binding.HoughContext(w.geometry, w.binning, max_hits=ev.n_hits - 1) as ctx:
+        with pytest.raises(binding.HoughError) as e:
+            ctx.vote_event(ev)
+        assert e.value.code == binding.ECAPACITY
