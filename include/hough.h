@@ -240,6 +240,31 @@ uint64_t hough_kernel_launches(void);
  */
 int hough_microbench_smem_or(int device, int pattern, double ms, double *atomics_per_s);
 
+/*
+ * Stage-1 vote of one event with no allocation at all.  The paper has no counterpart: this exists
+ * for callers that may not allocate device memory while they run -- a trigger's real-time event
+ * loop, where cudaMalloc and cudaFree can synchronise the whole device and take unbounded time, or
+ * a framework that has handed all device memory to its own pool -- and therefore cannot create a
+ * hough_ctx.
+ *
+ * Runs the staging and vote kernels of hough_vote on the hits r, phi, z, layer (device pointers,
+ * n_hits entries, same meaning and checks as hough_vote with HOUGH_DEVICE) and writes the
+ * n_qpt x n_phi row-major layer masks to `accumulator` (device, caller-owned).  If `device_error`
+ * is not NULL it receives (device memory, asynchronously) the HOUGH_DEVERR_* bits of dropped hits.
+ * The geometry and binning are read at each call; the stage-2 fields of the binning are ignored.
+ *
+ * Scratch: one fixed 8 MiB array in device memory, reserved by the CUDA runtime on every GPU that
+ * loads this library and held until the process exits.  Limits: n_hits <= 131072, n_qpt <= 1024,
+ * n_phi <= 4096; larger inputs return HOUGH_ECAPACITY before any work.  The first call on a device
+ * (with that device current) looks up the array's device address; make that first call before
+ * any stream capture.  Every call reuses the same array and clears what must start empty, so calls
+ * whose work may overlap on the GPU race: issue them on one stream or synchronise between them.
+ * Asynchronous on `stream` (a cudaStream_t of the current device, NULL for the legacy stream).
+ */
+int hough_vote_static(const hough_geometry *geometry, const hough_binning *binning, const float *r,
+                      const float *phi, const float *z, const uint8_t *layer, int64_t n_hits,
+                      uint16_t *accumulator, uint32_t *device_error, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

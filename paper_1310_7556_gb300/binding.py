@@ -93,6 +93,8 @@ _SIGNATURES = {
     "hough_kernel_launches": ([], ctypes.c_uint64),
     "hough_microbench_smem_or": ([ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
                                  ctypes.c_int),
+    "hough_vote_static": ([ctypes.POINTER(Geometry), ctypes.POINTER(Binning), _P, _P, _P, _P, _I64, _P, _P, _P],
+                          ctypes.c_int),
 }
 
 
@@ -105,6 +107,14 @@ def smem_or_throughput(device: int = 0, pattern: int = 0, ms: float = 50.0) -> f
     out = ctypes.c_double(0.0)
     _check(load().hough_microbench_smem_or(device, pattern, ms, ctypes.byref(out)))
     return out.value
+
+
+def vote_static(geometry, binning, r, phi, z, layer, n_hits, accumulator, device_error=None, stream=None):
+    """hough_vote_static: the vote of one event into a caller-owned device accumulator, for callers
+    that may not allocate device memory while running (device pointers only; see include/hough.h)."""
+    g, b = make_geometry(geometry), make_binning(binning)
+    _check(load().hough_vote_static(ctypes.byref(g), ctypes.byref(b), _ptr(r), _ptr(phi), _ptr(z), _ptr(layer),
+                                    int(n_hits), _ptr(accumulator), _ptr(device_error), _stream(stream)))
 
 
 def library_path() -> str:

@@ -41,6 +41,10 @@ int cuda_fail(cudaError_t e, const char *what)
 
 }  // namespace
 
+int hough::set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+void hough::note_launches(uint64_t n) { g_launches += n; }
+
 struct hough_ctx {
     int device = 0;
     int sms = 0;

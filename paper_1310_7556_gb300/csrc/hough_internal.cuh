@@ -139,6 +139,10 @@ cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t to
 
 cudaError_t run_smem_or_bench(int device, int pattern, double ms, double *atomics_per_s, uint64_t *launches);
 
+// Record a failure for hough_last_error (returns code), and count launches for hough_kernel_launches.
+int set_last_error(int code, const char *msg);
+void note_launches(uint64_t n);
+
 // Kernels launched by each enqueue function (for hough_kernel_launches).
 constexpr int kStageLaunches = 5;
 constexpr int kVoteLaunches = 1;
