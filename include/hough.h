@@ -61,7 +61,7 @@ extern "C" {
 #define HOUGH_DEVERR_LAYER     1u   /* a hit had layer >= n_layers; it cast no vote */
 #define HOUGH_DEVERR_RADIUS    2u   /* a hit had r <= 0 or a non-finite coordinate; it cast no vote */
 #define HOUGH_DEVERR_CAND      4u   /* more candidates than max_candidates; the first ones were kept */
-#define HOUGH_DEVERR_MEMBERS   8u   /* more member hits than max_members; stage 2 skipped the rest */
+#define HOUGH_DEVERR_MEMBERS   8u   /* more member hits than max_members; the member lists were cut (stage 2 still saw every member) */
 
 /* Barrel detector: number of layers and the solenoid field. */
 typedef struct hough_geometry {
@@ -203,13 +203,27 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
                   int32_t *n_out, int where, void *stream);
 
 /*
- * Vote-kernel tiling: each CTA owns a tile of tile_qpt rows by tile_phi columns
- * of the accumulator in shared memory.  tile_phi must divide n_phi and be a
- * multiple of 64; tile_qpt in 1..256; threads in {128, 256, 512, 1024};
- * tile_qpt * tile_phi * 2 bytes must fit in shared memory.  HOUGH_EINVAL otherwise.
+ * Kernel configuration of a context.
+ *
+ * vote_mode HOUGH_VOTE_GATHER (default): for every layer whose hits share one radius the
+ * accumulator is computed cell by cell from the per-bucket extrema of the hits' azimuth fraction
+ * (identical result, no atomics), in bands of band_rows rows with the peak search fused; layers
+ * whose hits lie at several radii are added by the shared-atomic scatter kernel.
+ * vote_mode HOUGH_VOTE_SCATTER: every layer by the shared-atomic scatter kernel (Sec. 6.1), each
+ * CTA owning a tile of tile_qpt rows x tile_phi columns in shared memory.
+ *
+ * tile_phi must divide n_phi and be a multiple of 64; tile_qpt in 1..256; threads in
+ * {128, 256, 512, 1024}; tile_qpt * tile_phi * 2 bytes must fit in shared memory; band_rows in
+ * 1..16 with (band_rows + 2) * n_phi bytes of shared memory.  HOUGH_EINVAL otherwise.
  */
+#define HOUGH_VOTE_GATHER  0
+#define HOUGH_VOTE_SCATTER 1
+
 typedef struct hough_tiling {
-    int32_t tile_qpt, tile_phi, threads, reserved;
+    int32_t tile_qpt, tile_phi, threads;
+    int32_t vote_mode;
+    int32_t band_rows;
+    int32_t reserved[3];   /* must be 0 */
 } hough_tiling;
 
 int hough_set_tiling(hough_ctx *ctx, const hough_tiling *tiling);

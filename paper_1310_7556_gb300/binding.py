@@ -61,7 +61,10 @@ class Timing(ctypes.Structure):
 
 class Tiling(ctypes.Structure):
     _fields_ = [("tile_qpt", ctypes.c_int32), ("tile_phi", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("vote_mode", ctypes.c_int32), ("band_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+VOTE_GATHER, VOTE_SCATTER = 0, 1
 
 
 CANDIDATE_DTYPE = np.dtype([("iq", np.uint32), ("jphi", np.uint32), ("mask", np.uint32),
@@ -272,11 +275,20 @@ class HoughContext:
         return dict(stage_ms=t.stage_ms, vote_ms=t.vote_ms, peaks_ms=t.peaks_ms, stage2_ms=t.stage2_ms)
 
     # -- tiling -------------------------------------------------------------------------------
-    def set_tiling(self, tile_qpt: int, tile_phi: int, threads: int):
-        t = Tiling(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, reserved=0)
+    def set_tiling(self, tile_qpt: int = None, tile_phi: int = None, threads: int = None,
+                   vote_mode: int = None, band_rows: int = None):
+        """Change the kernel configuration; unspecified fields keep their current value."""
+        cur = self.get_tiling()
+        new = dict(cur)
+        for k, v in dict(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, vote_mode=vote_mode,
+                         band_rows=band_rows).items():
+            if v is not None:
+                new[k] = v
+        t = Tiling(**new)
         _check(self._lib.hough_set_tiling(self._h, ctypes.byref(t)))
 
-    def get_tiling(self):
+    def get_tiling(self) -> dict:
         t = Tiling()
         _check(self._lib.hough_get_tiling(self._h, ctypes.byref(t)))
-        return (t.tile_qpt, t.tile_phi, t.threads)
+        return dict(tile_qpt=t.tile_qpt, tile_phi=t.tile_phi, threads=t.threads, vote_mode=t.vote_mode,
+                    band_rows=t.band_rows)

@@ -134,17 +134,24 @@ Axes make_axes(const hough_geometry *g, const hough_binning *b)
 int check_tiling(const hough_ctx *c, const hough_tiling *t)
 {
     if (!t) return fail(HOUGH_EINVAL, "tiling is required");
+    if (t->reserved[0] || t->reserved[1] || t->reserved[2]) return fail(HOUGH_EINVAL, "reserved fields must be 0");
     if (t->tile_qpt < 1 || t->tile_qpt > 256) return fail(HOUGH_EINVAL, "tile_qpt must be 1..256");
     if (t->tile_phi < 64 || t->tile_phi % 64 || c->ax.n_phi % t->tile_phi)
         return fail(HOUGH_EINVAL, "tile_phi must be a multiple of 64 dividing n_phi");
     if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
         return fail(HOUGH_EINVAL, "threads must be 128, 256, 512 or 1024");
-    Tiling tt{t->tile_qpt, t->tile_phi, t->threads};
+    if (t->vote_mode != HOUGH_VOTE_GATHER && t->vote_mode != HOUGH_VOTE_SCATTER)
+        return fail(HOUGH_EINVAL, "vote_mode must be HOUGH_VOTE_GATHER or HOUGH_VOTE_SCATTER");
+    if (t->band_rows < 1 || t->band_rows > 16) return fail(HOUGH_EINVAL, "band_rows must be 1..16");
+    Tiling tt{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows};
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (vote_smem_bytes(c->ax, tt) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "tile needs %zu bytes of shared memory, the device allows %d",
                     vote_smem_bytes(c->ax, tt), max_smem);
+    if (gather_smem_bytes(c->ax, t->band_rows) + 1024 > (size_t)max_smem)
+        return fail(HOUGH_EINVAL, "band of %d rows needs %zu bytes of shared memory, the device allows %d",
+                    t->band_rows, gather_smem_bytes(c->ax, t->band_rows), max_smem);
     return HOUGH_OK;
 }
 
@@ -155,7 +162,18 @@ Tiling default_tiling(const Axes &ax)
     while (ax.n_phi % t.tile_phi) t.tile_phi -= 64;
     t.tile_qpt = std::min(ax.n_qpt, 16);
     t.threads = 256;
+    t.vote_mode = HOUGH_VOTE_GATHER;
+    t.band_rows = 4;
     return t;
+}
+
+// Largest band-list storage over every allowed band height.
+size_t band_list_entries(const Axes &ax)
+{
+    size_t best = 0;
+    for (int r = 1; r <= 16; ++r)
+        best = std::max(best, (size_t)n_bands(ax, r) * (size_t)band_capacity(ax, r));
+    return best;
 }
 
 int check_host_hits(const hough_ctx *c, const float *r, const float *phi, const float *z,
@@ -195,12 +213,14 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     c->w.n_hits_total = n;
     c->n_hits = n;
     c->timed = 0;
+    c->w.band_rows = c->tiling.band_rows;
+    c->w.band_cap = band_capacity(c->ax, c->tiling.band_rows);
     if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1; }
     CU(launch_stage(c->ax, c->w, s), "stage kernels");
     if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
     CU(launch_vote(c->ax, c->w, c->tiling, c->refine_eps, s), "vote kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
-    g_launches += kStageLaunches + kVoteLaunches;
+    g_launches += kStageLaunches + (c->tiling.vote_mode == HOUGH_VOTE_SCATTER ? 1 : kVoteLaunches);
     c->stage = 1;
     return HOUGH_OK;
 }
@@ -256,16 +276,17 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&c->hit_start, 2));
     A(c->alloc(&c->in_r, n)); A(c->alloc(&c->in_phi, n)); A(c->alloc(&c->in_z, n)); A(c->alloc(&c->in_layer, n));
     A(c->alloc(&w.key, n)); A(c->alloc(&w.rank, n)); A(c->alloc(&w.hot_tmp, n));
-    A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1));
+    A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1)); A(c->alloc(&w.prof, nkeys));
     A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n));
     A(c->alloc(&w.radii, 1)); A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
     A(c->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(c->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
     A(c->alloc(&w.kq32, ax.n_qpt));
     A(c->alloc(&w.M, (size_t)ax.n_qpt * ax.n_phi));
     A(c->alloc(&w.cands, w.max_cand));
-    A(c->alloc(&w.band_counts, n_bands(ax))); A(c->alloc(&w.band_offs, n_bands(ax)));
-    A(c->alloc(&w.mem_counts, w.max_cand)); A(c->alloc(&w.mem_offs, (size_t)w.max_cand + 1));
-    A(c->alloc(&w.mem_pos, w.max_members)); A(c->alloc(&c->mem_idx, w.max_members));
+    A(c->alloc(&w.band_cands, band_list_entries(ax)));
+    A(c->alloc(&w.band_counts, n_bands(ax, 1))); A(c->alloc(&w.band_offs, n_bands(ax, 1)));
+    A(c->alloc(&w.mem_start, w.max_cand)); A(c->alloc(&w.mem_count, w.max_cand));
+    A(c->alloc(&w.mem_pool, w.max_members)); A(c->alloc(&c->mem_idx, w.max_members));
     A(c->alloc(&w.stats, 1));
     A(cudaMallocHost(&c->stats_host, sizeof(DevStats)));
     if (e != cudaSuccess) {
@@ -273,6 +294,8 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
         return cuda_fail(e, "hough_create allocation");
     }
     w.hit_start = c->hit_start;
+    w.band_rows = c->tiling.band_rows;
+    w.band_cap = band_capacity(ax, c->tiling.band_rows);
     // FP32 q/pT bin centres: the FP64 centre rounded once
     std::vector<float> kq(ax.n_qpt);
     for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i + 0.5) * ax.dk);
@@ -304,7 +327,7 @@ int hough_peaks(hough_ctx *c, void *stream)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     if (c->stage < 1) return fail(HOUGH_ENOTREADY, "hough_vote has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    CU(launch_peaks(c->ax, c->w, (cudaStream_t)stream), "peak kernels");
+    CU(launch_peaks(c->ax, c->w, c->tiling, (cudaStream_t)stream), "peak kernels");
     if (c->timing) { CU(cudaEventRecord(c->ev[3], (cudaStream_t)stream), "event"); c->timed |= 8; }
     g_launches += kPeakLaunches;
     c->stage = 2;
@@ -316,7 +339,7 @@ int hough_stage2(hough_ctx *c, void *stream)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     if (c->stage < 2) return fail(HOUGH_ENOTREADY, "hough_peaks has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    CU(launch_stage2(c->ax, c->w, c->sms, (cudaStream_t)stream), "stage-2 kernels");
+    CU(launch_stage2(c->ax, c->w, c->sms, c->refine_eps, (cudaStream_t)stream), "stage-2 kernels");
     if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
     g_launches += kStage2Launches;
     c->stage = 3;
@@ -371,19 +394,29 @@ int hough_get_members(hough_ctx *c, int64_t *offsets, int32_t *hits, int64_t hit
     int rc = read_stats(c, s);
     if (rc) return rc;
     const int64_t ncand = std::min<int64_t>(c->stats_host->n_candidates, c->w.max_cand);
-    CU(cudaMemcpyAsync(offsets, c->w.mem_offs, sizeof(int64_t) * (ncand + 1), cudaMemcpyDeviceToHost, s), "copy offsets");
-    CU(cudaStreamSynchronize(s), "synchronise");
-    const int64_t total = std::min<int64_t>(offsets[ncand], c->w.max_members);
-    const int64_t ncopy = std::min(total, hit_cap);
-    CU(launch_member_index(c->w, c->mem_idx, ncopy, s), "member index kernel");
-    if (ncopy > 0) CU(cudaMemcpyAsync(hits, c->mem_idx, sizeof(int32_t) * ncopy, cudaMemcpyDeviceToHost, s), "copy members");
-    CU(cudaStreamSynchronize(s), "synchronise");
-    for (int64_t q = 0; q < ncand; ++q) {
-        const int64_t a = std::min(offsets[q], ncopy), b = std::min(offsets[q + 1], ncopy);
-        if (b > a) std::sort(hits + a, hits + b);
+    const int64_t pooled = std::min<int64_t>(c->stats_host->pool_used, c->w.max_members);
+    std::vector<int32_t> start(ncand), count(ncand), pool(pooled);
+    if (ncand > 0) {
+        CU(cudaMemcpyAsync(start.data(), c->w.mem_start, sizeof(int32_t) * ncand, cudaMemcpyDeviceToHost, s), "copy member starts");
+        CU(cudaMemcpyAsync(count.data(), c->w.mem_count, sizeof(int32_t) * ncand, cudaMemcpyDeviceToHost, s), "copy member counts");
     }
-    if (offsets[ncand] > hit_cap || offsets[ncand] > c->w.max_members)
-        return fail(HOUGH_ETRUNC, "%lld member hits, capacity %lld", (long long)offsets[ncand], (long long)std::min<int64_t>(hit_cap, c->w.max_members));
+    CU(launch_member_index(c->w, c->mem_idx, pooled, s), "member index kernel");
+    if (pooled > 0) CU(cudaMemcpyAsync(pool.data(), c->mem_idx, sizeof(int32_t) * pooled, cudaMemcpyDeviceToHost, s), "copy members");
+    CU(cudaStreamSynchronize(s), "synchronise");
+    // lists in candidate order, each sorted by hit index
+    offsets[0] = 0;
+    bool cut = c->stats_host->pool_used > (unsigned)c->w.max_members;
+    for (int64_t q = 0; q < ncand; ++q) {
+        const int64_t a = offsets[q];
+        int64_t n = count[q];
+        if (a + n > hit_cap) { n = std::max<int64_t>(0, hit_cap - a); cut = true; }
+        if (n > 0) {
+            std::copy(pool.begin() + start[q], pool.begin() + start[q] + n, hits + a);
+            std::sort(hits + a, hits + a + n);
+        }
+        offsets[q + 1] = a + n;
+    }
+    if (cut) return fail(HOUGH_ETRUNC, "member lists were cut (max_members %d, capacity %lld)", c->w.max_members, (long long)hit_cap);
     return HOUGH_OK;
 }
 
@@ -401,8 +434,8 @@ int hough_get_stats(hough_ctx *c, hough_stats *out, void *stream)
     for (int l = 0; l < HOUGH_MAX_LAYERS; ++l) {
         out->votes_by_layer[l] = d.votes_by_layer[l];
         out->votes += d.votes_by_layer[l];
-        if (l < c->ax.n_layers && info[l].uniform) out->uniform_layers |= 1u << l;
-        else out->general_votes += d.votes_by_layer[l];
+        if (l < c->ax.n_layers && info[l].present && info[l].uniform) out->uniform_layers |= 1u << l;
+        else if (l < c->ax.n_layers) out->general_votes += d.votes_by_layer[l];
     }
     out->refined_votes = d.refined_votes;
     out->stage2_votes = d.stage2_votes;
@@ -429,7 +462,7 @@ int hough_set_tiling(hough_ctx *c, const hough_tiling *t)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     int rc = check_tiling(c, t);
     if (rc) return rc;
-    c->tiling = Tiling{t->tile_qpt, t->tile_phi, t->threads};
+    c->tiling = Tiling{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows};
     return HOUGH_OK;
 }
 
@@ -482,7 +515,9 @@ int hough_get_tiling(const hough_ctx *c, hough_tiling *t)
     t->tile_qpt = c->tiling.tile_qpt;
     t->tile_phi = c->tiling.tile_phi;
     t->threads = c->tiling.threads;
-    t->reserved = 0;
+    t->vote_mode = c->tiling.vote_mode;
+    t->band_rows = c->tiling.band_rows;
+    t->reserved[0] = t->reserved[1] = t->reserved[2] = 0;
     return HOUGH_OK;
 }
 

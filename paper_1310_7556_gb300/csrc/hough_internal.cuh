@@ -1,15 +1,20 @@
 // Internal declarations shared by the CUDA translation units of the hough library.
 //
-// Data layout in device memory for one event (n hits, L layers, Nq x Nphi grid):
-//   key[n], rank[n]          counting-sort key (layer * Nphi + J) and the hit's rank in its bucket
-//   counts[L*Nphi]           bucket sizes; offs[L*Nphi + 1] their exclusive prefix sum
-//   hot[n]   (16 B)          staged hit, sorted by (layer, J): fraction f, FP32 c, J | layer, row range
-//   cold[n]  (16 B)          the same hit's r, phi, z and input index, same order
-//   tab[L*Nq] (8 B)          per (layer, q/pT row): Nphi * asin(x) / (2 pi) = I + g  (uniform-radius layers)
-//   arc[L*Nq] (8 B)          per (layer, q/pT row): arc length s in FP64         (uniform-radius layers)
-//   M[Nq*Nphi] (uint16)      stage-1 accumulator, row-major layer masks
-//   cands[max_cand] (32 B)   hough_candidate records in raster order
-//   mem_pos[max_members]     member hits (staged positions), grouped per candidate
+// Device layout of a batch of events that share one set of axes (L layers, Nq x Nphi grid).
+// Hits of event e occupy [hit_start[e], hit_start[e+1]) of the concatenated hit arrays; every
+// other per-event array has a fixed stride:
+//   key[n], rank[n]           counting-sort key (layer * Nphi + J) and the hit's rank in its bucket
+//   hot_tmp[n]                the hit's 16-byte staged record, input order
+//   counts[L*Nphi]            bucket sizes; offs[L*Nphi + 1] their exclusive prefix sum (event-local)
+//   prof[L*Nphi]  (8 B)       per (layer, bucket J): .x = max over the bucket of bits(f) + 1,
+//                             .y = max over bucket J+1 of ~bits(f) (0 when the bucket is empty)
+//   hot[n], cold[n] (16 B)    staged hits sorted by (layer, J); cold holds r, phi, z, input index
+//   tab[L*Nq] (8 B)           per (layer, q/pT row): Nphi asin(x) / (2 pi) = I + g, for layers whose
+//                             hits share one radius; arc[L*Nq] the arc length s (FP64)
+//   M[Nq*Nphi] (uint16)       stage-1 accumulator, row-major layer masks
+//   band_cands[n_bands*band_cap] (8 B)  peak candidates of each row band: cell index, mask
+//   cands[max_cand] (32 B)    hough_candidate records in raster order
+//   mem_pool[max_members]     member hits (staged positions); mem_start/mem_count per candidate
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,7 +25,7 @@
 namespace hough {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr double kTwoPi = 6.283185307179586;   // 2 * kPi, exactly the double product
+constexpr double kTwoPi = 6.283185307179586;       // 2 * kPi, exactly the double product
 constexpr double kInvTwoPi = 0.15915494309189535;  // 1 / (2 pi) rounded to double
 
 // Axes of the two grids, by value into every kernel.
@@ -30,9 +35,9 @@ struct Axes {
     double cot_min, cot_max, dt, z0_min, z0_max;
 };
 
-// Staged hit, the record the vote kernel streams (16 bytes, one vector load).
+// Staged hit, the record the vote and membership kernels stream (16 bytes, one vector load).
 struct __align__(16) HotHit {
-    float f;          // fractional part of the hit's phi0 bin coordinate u_h = Nphi (phi + pi) / (2 pi)
+    float f;          // fractional part of the hit's own bin coordinate u_h = Nphi (phi + pi) / (2 pi)
     float c;          // FP32 sagitta coefficient 0.15 B r / 100 (per-vote path)
     uint32_t jl;      // J = floor(u_h) mod Nphi in bits 0..15, layer in bits 16..19
     uint32_t rows;    // first voting row in bits 0..15, last in bits 16..31 (first > last: none)
@@ -59,7 +64,7 @@ struct DevStats {
     unsigned int n_candidates;
     unsigned int n_members;
     unsigned int device_error;
-    unsigned int pad;
+    unsigned int pool_used;     // member-pool entries handed out
 };
 
 // Per-layer radius range: min and max of the hit radii as float bits (radii are > 0).
@@ -70,9 +75,11 @@ struct LayerRadii {
 
 // Per-layer facts of the current batch, written by the layer-info kernel.
 struct LayerInfo {
-    int32_t uniform;    // all hits of the layer share one radius: the table path applies
+    int32_t present;    // the layer has hits
+    int32_t uniform;    // all its hits share one radius (or it has none): the table path applies
     int32_t lo, hi;     // voting rows of that radius (lo > hi: none)
     uint32_t r_bits;    // the radius (float bits)
+    int32_t pad[3];
 };
 
 // Memo of the per-(layer, row) table: the radius each layer's rows were computed for.
@@ -82,9 +89,7 @@ struct TableMemo {
     int32_t dirty[HOUGH_MAX_LAYERS];
 };
 
-// Device buffers of a batch of events that share one set of axes.  Hits of event e occupy
-// [hit_start[e], hit_start[e+1]) of the concatenated arrays; every other per-event array
-// has a fixed stride.
+// Device buffers of a batch of events that share one set of axes.
 struct Workspace {
     int n_events;
     int64_t n_hits_total;
@@ -94,8 +99,9 @@ struct Workspace {
     int32_t *key, *rank;          // per hit
     HotHit *hot_tmp;              // per hit, input order
     int32_t *counts;              // n_events * nkeys
-    int32_t *offs;                // n_events * (nkeys + 1), event-local
-    HotHit *hot;                  // per hit, staged order within each event's range
+    int32_t *offs;                // n_events * (nkeys + 1)
+    uint2 *prof;                  // n_events * nkeys
+    HotHit *hot;                  // per hit, sorted within each event's range
     ColdHit *cold;
     LayerRadii *radii;            // batch-wide
     LayerInfo *info;              // HOUGH_MAX_LAYERS
@@ -104,40 +110,58 @@ struct Workspace {
     double *arc;                  // n_layers * n_qpt
     float *kq32;                  // n_qpt: FP32 q/pT bin centres
     uint16_t *M;                  // n_events * n_qpt * n_phi
-    hough_candidate *cands;       // n_events * max_cand
+    uint2 *band_cands;            // n_events * n_bands * band_cap
     int32_t *band_counts;         // n_events * n_bands
     int32_t *band_offs;           // n_events * n_bands
-    int32_t *mem_counts;          // n_events * max_cand
-    int64_t *mem_offs;            // n_events * (max_cand + 1)
-    int32_t *mem_pos;             // n_events * max_members: event-local staged positions
+    hough_candidate *cands;       // n_events * max_cand
+    int32_t *mem_pool;            // n_events * max_members: event-local staged positions
+    int32_t *mem_start;           // n_events * max_cand
+    int32_t *mem_count;           // n_events * max_cand: entries written to the pool
     DevStats *stats;              // n_events
     int max_cand, max_members;
+    int band_rows, band_cap;
 };
 
+// Vote-kernel configuration.
 struct Tiling {
     int tile_qpt, tile_phi, threads;
+    int vote_mode;                // HOUGH_VOTE_GATHER or HOUGH_VOTE_SCATTER
+    int band_rows;                // rows per band of the peak search (and of the gather kernel)
 };
 
-// Row band of the peak kernels.
-constexpr int kPeakRows = 4;
 constexpr int kPeakThreads = 256;
 
-// Refinement of the per-vote FP32 path: votes whose FP32 bin coordinate lies within
-// the refine window of an edge, or whose |x| exceeds kRefineXLim, are recomputed in FP64.
+// Refinement of the per-vote FP32 path: votes whose FP32 bin coordinate lies within the refine
+// window of an edge, or whose |x| exceeds kRefineXLim, are recomputed in FP64.
 constexpr float kRefineXLim = 0.99f;
 // Stage-2 FP32 window: a (member, cot) vote within this distance of a z0 edge is recomputed in FP64.
 constexpr float kStage2Eps = 2e-4f;
+
+__host__ __device__ inline int n_keys(const Axes &ax) { return ax.n_layers * ax.n_phi; }
+__host__ __device__ inline int n_bands(const Axes &ax, int band_rows) { return (ax.n_qpt + band_rows - 1) / band_rows; }
+// Candidates are never 8-neighbours, so a band holds at most one per 2 x 2 block.
+__host__ __device__ inline int band_capacity(const Axes &ax, int band_rows)
+{
+    return ((band_rows + 1) / 2) * ((ax.n_phi + 1) / 2);
+}
+
+// Refine window (in bins) of the per-vote FP32 path.  Its error is bounded by the asinf error,
+// the FP32 rounding of x = c k propagated through asin up to |x| = kRefineXLim, and the rounding
+// of the bin coordinate; the sum grows with Nphi / (2 pi).
+inline float refine_eps_for(const Axes &ax) { return (float)(ax.n_phi * 5e-7 + 1e-4); }
 
 // Kernel launchers (each enqueues on `stream` and returns the launch status).
 cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream);
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
                         cudaStream_t stream);
-cudaError_t launch_peaks(const Axes &ax, const Workspace &w, cudaStream_t stream);
-cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, cudaStream_t stream);
-
+cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
+cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream);
 cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t total, cudaStream_t stream);
-
 cudaError_t run_smem_or_bench(int device, int pattern, double ms, double *atomics_per_s, uint64_t *launches);
+
+size_t vote_smem_bytes(const Axes &ax, const Tiling &t);
+size_t gather_smem_bytes(const Axes &ax, int band_rows);
+size_t stage2_smem_bytes(const Axes &ax);
 
 // Record a failure for hough_last_error (returns code), and count launches for hough_kernel_launches.
 int set_last_error(int code, const char *msg);
@@ -145,19 +169,9 @@ void note_launches(uint64_t n);
 
 // Kernels launched by each enqueue function (for hough_kernel_launches).
 constexpr int kStageLaunches = 5;
-constexpr int kVoteLaunches = 1;
-constexpr int kPeakLaunches = 3;
-constexpr int kStage2Launches = 4;
-
-size_t vote_smem_bytes(const Axes &ax, const Tiling &t);
-size_t stage2_smem_bytes(const Axes &ax);
-
-// Refine window (in bins) of the per-vote FP32 path.  Its error is bounded by the asinf error,
-// the FP32 rounding of x = c k propagated through asin up to |x| = kRefineXLim, and the rounding
-// of the bin coordinate; the sum grows with Nphi / (2 pi).
-inline float refine_eps_for(const Axes &ax) { return (float)(ax.n_phi * 5e-7 + 1e-4); }
-__host__ __device__ inline int n_bands(const Axes &ax) { return (ax.n_qpt + kPeakRows - 1) / kPeakRows; }
-__host__ __device__ inline int n_keys(const Axes &ax) { return ax.n_layers * ax.n_phi; }
+constexpr int kVoteLaunches = 2;
+constexpr int kPeakLaunches = 2;
+constexpr int kStage2Launches = 1;
 
 // Exact FP64 helpers used by the staging, table and refinement code.  They evaluate the
 // definitions in the order of the method's formulas with explicitly rounded operations,
@@ -212,6 +226,65 @@ __device__ __forceinline__ int exact_bin(const Axes &ax, double phi, double x)
     double u = __ddiv_rn(__dmul_rn((double)ax.n_phi, __dadd_rn(phi0, kPi)), kTwoPi);
     long long j = (long long)floor(u) % ax.n_phi;
     return (int)(j < 0 ? j + ax.n_phi : j);
+}
+
+__device__ __forceinline__ int wrap_col(int j, int n)
+{
+    j += j < 0 ? n : 0;
+    return j >= n ? j - n : j;
+}
+
+// Peak test of the cells of rows 1..nrows of a band held as layer counts in shared memory
+// (`pc`, (nrows + 2) rows of Nphi bytes, row 0 and row nrows + 1 the halo), in raster order.
+// A cell with count p is a candidate when p >= threshold, the neighbours at (-1,-1), (-1,0),
+// (-1,+1), (0,-1) are below p and the other four are not above it; phi0 wraps.  Candidates go
+// to `out` (cell index i * Nphi + j, mask read from M) in raster order; returns their number.
+// Called by all kPeakThreads threads of the block.
+__device__ __forceinline__ int band_peak_search(const unsigned char *pc, int nrows, int i0, int nphi, int threshold,
+                                                const uint16_t *M, uint2 *out, int cap)
+{
+    __shared__ int s_warp[kPeakThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncell = nrows * nphi;
+    int running = 0;
+    for (int base = 0; base < ncell; base += kPeakThreads) {
+        const int cell = base + threadIdx.x;
+        bool is_peak = false;
+        int rr = 0, j = 0;
+        if (cell < ncell) {
+            rr = cell / nphi;
+            j = cell - rr * nphi;
+            const unsigned char *row = pc + (rr + 1) * nphi;
+            const int p = row[j];
+            if (p >= threshold) {
+                const int jm = wrap_col(j - 1, nphi), jp = wrap_col(j + 1, nphi);
+                const unsigned char *up = row - nphi, *dn = row + nphi;
+                is_peak = up[jm] < p && up[j] < p && up[jp] < p && row[jm] < p &&
+                          row[jp] <= p && dn[jm] <= p && dn[j] <= p && dn[jp] <= p;
+            }
+        }
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, is_peak);
+        // skip the block-wide prefix when no thread of the block found a candidate
+        const int any = __syncthreads_or(ball != 0u);
+        if (!any) continue;
+        if (lane == 0) s_warp[warp] = __popc(ball);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int q = 0; q < kPeakThreads / 32; ++q) {
+            const int c = s_warp[q];
+            before += q < warp ? c : 0;
+            total += c;
+        }
+        if (is_peak) {
+            const int idx = running + before + __popc(ball & ((1u << lane) - 1u));
+            const int cellg = (i0 + rr) * nphi + j;
+            if (idx < cap) out[idx] = make_uint2((unsigned)cellg, (unsigned)M[cellg]);
+        }
+        running += total;
+        __syncthreads();
+    }
+    return running;
 }
 
 }  // namespace hough

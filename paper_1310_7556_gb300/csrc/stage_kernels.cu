@@ -10,7 +10,9 @@
 // radius and the row, not on its azimuth (the paper's GPU optimisation of cutting the
 // trigonometric work, Sec. 6.1).  When every hit of a layer shares one radius the table
 // holds that value per (layer, row) in FP64, and a vote reduces to an integer subtraction
-// and one FP32 comparison.
+// and one FP32 comparison.  The staging also records, per (layer, phi bucket), the largest
+// and smallest fraction f of the hits in it: with the table they decide every cell of the
+// accumulator directly (see vote_kernel.cu).
 #include "hough_internal.cuh"
 
 namespace hough {
@@ -60,6 +62,14 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
         const int k = l * ax.n_phi + (int)J;
         w.key[h] = k;
         w.rank[h] = atomicAdd(&w.counts[(int64_t)e * nkeys + k], 1);
+        // bucket extrema of f as ordered bit patterns (f >= 0): .x of bucket J keeps the maximum
+        // (offset by one so an empty bucket, 0, is below every hit), .y of bucket J-1 keeps the
+        // maximum of the complement, i.e. the minimum of bucket J
+        if (w.prof) {
+            uint2 *prof = w.prof + (int64_t)e * nkeys + l * ax.n_phi;
+            atomicMax(&prof[J].x, __float_as_uint(f) + 1u);
+            atomicMax(&prof[J == 0 ? ax.n_phi - 1 : J - 1].y, ~__float_as_uint(f));
+        }
         HotHit hh;
         hh.f = f;
         hh.c = __fmul_rn(cscale, rr);
@@ -84,13 +94,15 @@ __global__ void layer_info_kernel(Axes ax, Workspace w)
     if (l >= HOUGH_MAX_LAYERS) return;
     LayerInfo li;
     const unsigned rmin = w.radii->rmin[l], rmax = w.radii->rmax[l];
-    li.uniform = (l < ax.n_layers) && rmax != 0u && rmin == rmax;
+    li.present = (l < ax.n_layers) && rmax != 0u;
+    li.uniform = !li.present || rmin == rmax;   // a layer without hits is trivially uniform
     li.lo = 1;
     li.hi = 0;
     li.r_bits = rmin;
-    if (li.uniform) row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
+    li.pad[0] = li.pad[1] = li.pad[2] = 0;
+    if (li.present && li.uniform) row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
     w.info[l] = li;
-    const int dirty = li.uniform && !(w.memo->valid[l] && w.memo->r_bits[l] == rmin);
+    const int dirty = li.present && li.uniform && !(w.memo->valid[l] && w.memo->r_bits[l] == rmin);
     w.memo->dirty[l] = dirty;
     if (dirty) {
         w.memo->r_bits[l] = rmin;
@@ -129,55 +141,53 @@ __global__ void table_kernel(Axes ax, Workspace w)
     w.arc[q] = s;
 }
 
-// One CTA per event: exclusive scan of the bucket sizes, and the vote count of uniform layers.
+// One CTA per event: exclusive scan of the bucket sizes (each thread owns a contiguous chunk),
+// and the vote count of uniform layers.
 __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Workspace w)
 {
     __shared__ int s_warp[kScanThreads / 32];
-    __shared__ int s_carry;
     const int e = blockIdx.x;
     const int nkeys = n_keys(ax);
     const int32_t *counts = w.counts + (int64_t)e * nkeys;
     int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
+    const int chunk = (nkeys + kScanThreads - 1) / kScanThreads;
+    const int k0 = min(nkeys, threadIdx.x * chunk), k1 = min(nkeys, k0 + chunk);
+    int sum = 0;
+    for (int k = k0; k < k1; ++k) sum += counts[k];
+    int incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    for (int base = 0; base < nkeys; base += kScanThreads) {
-        const int k = base + threadIdx.x;
-        const int v = k < nkeys ? counts[k] : 0;
-        int incl = v;
+    if (warp == 0) {
+        int wv = s_warp[lane];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane >= d) incl += t;
+            const int t = __shfl_up_sync(0xFFFFFFFFu, wv, d);
+            if (lane >= d) wv += t;
         }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int wv = s_warp[lane];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xFFFFFFFFu, wv, d);
-                if (lane >= d) wv += t;
-            }
-            s_warp[lane] = wv;   // inclusive over warps
-        }
-        __syncthreads();
-        const int carry = s_carry;
-        const int excl = carry + (warp > 0 ? s_warp[warp - 1] : 0) + incl - v;
-        if (k < nkeys) offs[k] = excl;
-        __syncthreads();
-        if (threadIdx.x == kScanThreads - 1) s_carry = excl + v;
-        __syncthreads();
+        s_warp[lane] = wv;   // inclusive over warps
     }
+    __syncthreads();
+    int run = (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
+    for (int k = k0; k < k1; ++k) {
+        offs[k] = run;
+        run += counts[k];
+    }
+    const int total = s_warp[kScanThreads / 32 - 1];
     if (threadIdx.x == 0) {
-        offs[nkeys] = s_carry;
-        w.stats[e].n_hits = (unsigned long long)s_carry;
+        offs[nkeys] = total;
+        w.stats[e].n_hits = (unsigned long long)total;
     }
     __syncthreads();
     if (threadIdx.x < ax.n_layers) {
         const int l = threadIdx.x;
         const LayerInfo li = w.info[l];
-        if (li.uniform && li.hi >= li.lo) {
+        if (li.present && li.uniform && li.hi >= li.lo) {
             const long long n_l = offs[(l + 1) * ax.n_phi] - offs[l * ax.n_phi];
             w.stats[e].votes_by_layer[l] += (unsigned long long)(n_l * (li.hi - li.lo + 1));
         }
@@ -232,6 +242,7 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
     const int nkeys = n_keys(ax);
     cudaError_t err;
     if ((err = cudaMemsetAsync(w.counts, 0, sizeof(int32_t) * (size_t)w.n_events * nkeys, stream))) return err;
+    if (w.prof && (err = cudaMemsetAsync(w.prof, 0, sizeof(uint2) * (size_t)w.n_events * nkeys, stream))) return err;
     if ((err = cudaMemsetAsync(w.stats, 0, sizeof(DevStats) * (size_t)w.n_events, stream))) return err;
     if ((err = cudaMemsetAsync(w.radii->rmin, 0xFF, sizeof(w.radii->rmin), stream))) return err;
     if ((err = cudaMemsetAsync(w.radii->rmax, 0, sizeof(w.radii->rmax), stream))) return err;

@@ -150,6 +150,8 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
     while (b->n_phi % t.tile_phi) t.tile_phi -= 64;
     t.tile_qpt = b->n_qpt < 16 ? b->n_qpt : 16;
     t.threads = 256;
+    t.vote_mode = HOUGH_VOTE_SCATTER;   // the shared-atomic vote kernel alone: no bucket profile needed
+    t.band_rows = 4;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The array keeps the previous call's contents: reset what the kernels expect to start at zero.

@@ -1,22 +1,32 @@
-// Stage-1 vote (Sec. 4, first step; the A[B[i]] += 1 scatter of Sec. 8) with the paper's GPU
-// remedy for it: every update goes to an accumulator tile in on-chip shared memory with shared
-// atomics (Sec. 6.1), and the tile reaches HBM once, with coalesced 16-byte stores and no
-// separate clearing pass.
+// Stage-1 vote (Sec. 4, first step; the A[B[i]] += 1 scatter of Sec. 8), accumulator flush and
+// the peak search over row bands (Sec. 4, second step).
 //
-// Work decomposition: one CTA per (event, tile) where a tile is tile_qpt rows of q/pT by
-// tile_phi columns of phi0.  The CTA reads only the hits that can vote into its tile -- per
-// layer a contiguous range (two when it wraps) of the (layer, phi bin)-sorted hits -- lane by
-// lane, and loops over the tile's rows in lockstep, so that at each row the 32 lanes of a warp
-// (hits of one layer, sorted by azimuth) vote into neighbouring cells of one row.  A lane whose
-// (word, bits) equals its left neighbour's skips its atomic: sorted hits of one layer often
-// land in the same cell.
+// Two ways to fill the accumulator, selected per layer on the device:
 //
-// Per-vote arithmetic.  For a layer whose hits share one radius the table gives
-// Nphi asin(x_i) / (2 pi) = I + g exactly (FP64, rounded once to FP32 in g), the hit carries its
-// own bin coordinate as J + f, and the vote's bin is J - I - (f < g): no transcendental and an
-// error below 1e-7 bin.  Other layers take FP32 asinf per vote; a vote whose FP32 bin coordinate
-// lies within `refine_eps` of an edge, or whose |x| > kRefineXLim, is recomputed in FP64 from the
-// hit's coordinates exactly as the definition reads.
+// 1. Gather (layers whose hits share one radius; every configured workload).  On row i every
+//    hit of such a layer votes at J - I_i - (f < g_i): its own bin coordinate J + f shifted by the
+//    table's Nphi asin(x_i) / (2 pi) = I_i + g_i.  So layer l's bit of cell (i, j) is set exactly
+//    when bucket J' = (j + I_i) mod Nphi holds a hit with f >= g_i, or bucket J' + 1 holds one with
+//    f < g_i -- a test of the buckets' largest and smallest f, which the staging recorded.  The
+//    gather kernel evaluates that test for every (cell, layer) of a band of rows: no atomics,
+//    each accumulator word written once with a coalesced store, and the band's layer counts kept
+//    in shared memory for the peak search of the same CTA.  Same FP32 comparisons as the per-vote
+//    form, so the same accumulator bit for bit.
+//
+// 2. Scatter (the paper's remedy, Sec. 6.1: shared-memory atomics instead of global ones).  One CTA
+//    per (event, tile of tile_qpt rows x tile_phi columns) in shared memory.  The CTA reads only the
+//    hits that can vote into its tile -- per layer one or two contiguous ranges of the
+//    (layer, phi bin)-sorted hits -- lane by lane, and loops over the tile's rows in lockstep, so a
+//    warp's 32 same-layer, azimuth-sorted hits update neighbouring words of one row; a lane whose
+//    (word, bit) equals its left neighbour's skips its atomicOr.  Table layers vote at
+//    J - I - (f < g); other layers take FP32 asinf per vote, and a vote within `refine_eps` of an
+//    edge (or with |x| > kRefineXLim) is recomputed in FP64 in the definition's order.  In the
+//    default (gather) mode this kernel handles only the layers whose radii differ and ORs its tile
+//    into the accumulator; in scatter mode it handles every layer and stores its tile.
+//
+// Peaks: candidates of each band of band_rows rows go to a band list in raster order (fused into
+// the gather kernel when every layer took the gather, else a standalone pass over the
+// accumulator); a per-event scan then concatenates the band lists into the raster-ordered list.
 #include "hough_internal.cuh"
 
 namespace hough {
@@ -32,15 +42,29 @@ struct VoteParams {
 };
 
 constexpr int kMaxRanges = 2 * HOUGH_MAX_LAYERS;
+constexpr int kCompactThreads = 1024;
 
-template <int TPB>
-__global__ void __launch_bounds__(TPB) vote_kernel(VoteParams p)
+// Layers of the batch: bit l of *uniform_out is set when layer l takes the table path; bit l of
+// *general_out when it has hits at more than one radius.  Called by warp 0.
+__device__ __forceinline__ void layer_masks(const Workspace &w, int L, unsigned *uniform_out, unsigned *general_out)
+{
+    const int l = threadIdx.x;
+    LayerInfo li;
+    li.present = 0;
+    li.uniform = 1;
+    if (l < L) li = w.info[l];
+    *uniform_out = __ballot_sync(0xFFFFFFFFu, l < L && li.uniform);
+    *general_out = __ballot_sync(0xFFFFFFFFu, l < L && li.present && !li.uniform);
+}
+
+template <int TPB, bool GENERAL_ONLY>
+__global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_start[kMaxRanges];
     __shared__ int s_pre[kMaxRanges + 1];
     __shared__ unsigned long long s_refined;
-    __shared__ unsigned s_umask;
+    __shared__ unsigned s_umask, s_gmask;
 
     const Axes &ax = p.ax;
     const int R = p.R, W = p.W, Wh = W >> 1, L = ax.n_layers, nphi = ax.n_phi;
@@ -60,16 +84,18 @@ __global__ void __launch_bounds__(TPB) vote_kernel(VoteParams p)
     const ColdHit *cold = p.w.cold + hstart;
     const int32_t *offs = p.w.offs + (int64_t)e * (nkeys + 1);
 
-    // layers whose hits share one radius take the table path
     if (threadIdx.x < 32) {
-        const int l = threadIdx.x;
-        const unsigned u = __ballot_sync(0xFFFFFFFFu, l < L && p.w.info[l < HOUGH_MAX_LAYERS ? l : 0].uniform);
-        if (l == 0) {
-            s_umask = u;
+        unsigned u, g;
+        layer_masks(p.w, L, &u, &g);
+        if (threadIdx.x == 0) {
+            s_umask = GENERAL_ONLY ? ~g : u;   // layers this kernel treats with the table
+            s_gmask = g;
             s_refined = 0ull;
         }
     }
     __syncthreads();
+    // in gather mode there is nothing to do unless some layer has hits at several radii
+    if (GENERAL_ONLY && s_gmask == 0u) return;
     const unsigned umask = s_umask;
 
     // clear the tile; stage this slab's table rows and FP32 q/pT centres
@@ -80,7 +106,7 @@ __global__ void __launch_bounds__(TPB) vote_kernel(VoteParams p)
         TabEntry te;
         te.I = 0;
         te.g = 0.f;
-        if (rr < nrows && ((umask >> l) & 1u)) te = p.w.tab[l * ax.n_qpt + i0 + rr];
+        if (!GENERAL_ONLY && rr < nrows && ((umask >> l) & 1u)) te = p.w.tab[l * ax.n_qpt + i0 + rr];
         tab[q] = te;
     }
     for (int q = threadIdx.x; q < R; q += TPB) kq[q] = q < nrows ? p.w.kq32[i0 + q] : 0.f;
@@ -92,17 +118,21 @@ __global__ void __launch_bounds__(TPB) vote_kernel(VoteParams p)
         if (l < L) {
             const int lstart = offs[l * nphi], lend = offs[(l + 1) * nphi];
             int ja = 0, jb = -1;   // inclusive J window, possibly beyond [0, nphi)
-            bool all = false, none = lend == lstart;
+            bool none = lend == lstart;
             if (!none && ((umask >> l) & 1u)) {
-                const LayerInfo li = p.w.info[l];
-                const int a = max(i0, li.lo), b = min(i0 + nrows - 1, li.hi);
-                if (a > b) {
-                    none = true;
+                if (GENERAL_ONLY) {
+                    none = true;   // the gather kernel votes for this layer
                 } else {
-                    // vote bin J - I - (f < g) lies in [J0, J0 + W) only for J in [J0 + I_a, J0 + W + I_b]
-                    const TabEntry ta = p.w.tab[l * ax.n_qpt + a], tb = p.w.tab[l * ax.n_qpt + b];
-                    ja = J0 + ta.I;
-                    jb = J0 + W + tb.I;
+                    const LayerInfo li = p.w.info[l];
+                    const int a = max(i0, li.lo), b = min(i0 + nrows - 1, li.hi);
+                    if (a > b) {
+                        none = true;
+                    } else {
+                        // vote bin J - I - (f < g) lies in [J0, J0 + W) only for J in [J0 + I_a, J0 + W + I_b]
+                        const TabEntry ta = p.w.tab[l * ax.n_qpt + a], tb = p.w.tab[l * ax.n_qpt + b];
+                        ja = J0 + ta.I;
+                        jb = J0 + W + tb.I;
+                    }
                 }
             } else if (!none) {
                 // per-vote layer: bound asin(c k) over the layer's radius range and the slab's rows
@@ -124,8 +154,7 @@ __global__ void __launch_bounds__(TPB) vote_kernel(VoteParams p)
                 jb = (int)floorf(J0 + W + p.s32 * amax) + 2;
             }
             if (!none) {
-                if (jb - ja + 1 >= nphi) all = true;
-                if (all) {
+                if (jb - ja + 1 >= nphi) {
                     nr = 1;
                     st[0] = lstart;
                     ln[0] = lend - lstart;
@@ -185,7 +214,7 @@ __global__ void __launch_bounds__(TPB) vote_kernel(VoteParams p)
         const int J = (int)(hh.jl & 0xFFFFu);
         const int l = (int)((hh.jl >> 16) & 0xFu);
         const int rlo = (int)(hh.rows & 0xFFFFu), rhi = (int)(hh.rows >> 16);
-        const bool uni = (umask >> l) & 1u;
+        const bool uni = !GENERAL_ONLY && ((umask >> l) & 1u);
         const uint32_t lbit = 1u << l;
         for (int rr = 0; rr < nrows; ++rr) {
             const int i = i0 + rr;
@@ -220,24 +249,240 @@ __global__ void __launch_bounds__(TPB) vote_kernel(VoteParams p)
     if (refined) atomicAdd(&s_refined, refined);
     __syncthreads();
 
-    // flush the tile: each row is W/8 16-byte vectors
+    // flush the tile: each row is W/8 16-byte vectors (ORed into the gathered layers' bits)
     uint16_t *M = p.w.M + (int64_t)e * ax.n_qpt * nphi;
     const int v8 = W >> 3;
     for (int q = threadIdx.x; q < nrows * v8; q += TPB) {
         const int rr = q / v8, c8 = q - rr * v8;
-        *reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + J0 + c8 * 8) = tile4[rr * v8 + c8];
+        uint4 *dst = reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + J0 + c8 * 8);
+        uint4 v = tile4[rr * v8 + c8];
+        if (GENERAL_ONLY) {
+            const uint4 old = *dst;
+            v.x |= old.x;
+            v.y |= old.y;
+            v.z |= old.z;
+            v.w |= old.w;
+        }
+        *dst = v;
     }
     if (threadIdx.x == 0 && s_refined) atomicAdd(&p.w.stats[e].refined_votes, s_refined);
 }
 
-template <int TPB>
-cudaError_t launch_tpb(const VoteParams &p, size_t smem, int grid, cudaStream_t stream)
+// Gather: the accumulator rows of one band (plus a halo row on each side for the peak test) from
+// the per-bucket f extrema and the table; fused peak search when every layer is a table layer.
+template <bool POW2>
+__global__ void __launch_bounds__(kPeakThreads) gather_kernel(Axes ax, Workspace w)
 {
-    cudaError_t err = cudaFuncSetAttribute(vote_kernel<TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    extern __shared__ __align__(16) unsigned char gsm[];
+    __shared__ unsigned s_general;
+    const int R = w.band_rows;
+    const int nb = n_bands(ax, R);
+    const int e = blockIdx.x / nb, band = blockIdx.x - e * nb;
+    const int L = ax.n_layers, nphi = ax.n_phi;
+    const int i0 = band * R;
+    const int nrows = min(R, ax.n_qpt - i0);
+    const int nkeys = L * nphi;
+    int *rowI = reinterpret_cast<int *>(gsm);                       // (R + 2) x 16
+    unsigned *rowG = reinterpret_cast<unsigned *>(rowI + (R + 2) * 16);
+    unsigned *rowMask = rowG + (R + 2) * 16;                        // R + 2 (+ padding to 4)
+    unsigned char *pc = reinterpret_cast<unsigned char *>(rowMask + ((R + 2 + 3) & ~3));
+
+    if (threadIdx.x < 32) {
+        unsigned u, g;
+        layer_masks(w, L, &u, &g);
+        if (threadIdx.x == 0) s_general = g;
+    }
+    // per (row, layer): the table entry and whether the layer votes on that row by the gather;
+    // the loop runs over whole warps so that every lane takes part in the ballot
+    const int nrl = (R + 2) * 16;
+    for (int q = threadIdx.x; q < ((nrl + 31) & ~31); q += kPeakThreads) {
+        const int rr = q >> 4, l = q & 15, i = i0 - 1 + rr;
+        int I = 0;
+        unsigned gb = 0u, valid = 0u;
+        if (q < nrl && l < L && rr < nrows + 2 && i >= 0 && i < ax.n_qpt) {
+            const LayerInfo li = w.info[l];
+            if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
+                const TabEntry te = w.tab[l * ax.n_qpt + i];
+                I = te.I;
+                gb = __float_as_uint(te.g);
+                valid = 1u;
+            }
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, valid) >> (threadIdx.x & 16);
+        if (q < nrl) {
+            rowI[q] = I;
+            rowG[q] = gb;
+            if ((threadIdx.x & 15) == 0) rowMask[rr] = m & 0xFFFFu;
+        }
+    }
+    __syncthreads();
+    const bool fused = s_general == 0u;
+    const uint2 *prof = w.prof + (int64_t)e * nkeys;
+    uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
+    const int half = nphi >> 1;
+    const int nq = (nrows + 2) * half;
+    for (int q = threadIdx.x; q < nq; q += kPeakThreads) {
+        const int rr = q / half;
+        const int j = (q - rr * half) * 2;
+        const int i = i0 - 1 + rr;
+        uint32_t word = 0u;
+        if (i >= 0 && i < ax.n_qpt) {
+            unsigned vm = rowMask[rr];
+            while (vm) {
+                const int l = __ffs(vm) - 1;
+                vm &= vm - 1u;
+                const int I = rowI[rr * 16 + l];
+                const unsigned gb = rowG[rr * 16 + l];
+                int J1 = j + I;
+                int J2 = J1 + 1;
+                if (POW2) {
+                    J1 &= nphi - 1;
+                    J2 &= nphi - 1;
+                } else {
+                    J1 = wrap_col(J1, nphi);
+                    J2 = wrap_col(J2, nphi);
+                }
+                const uint2 a = __ldg(&prof[l * nphi + J1]);
+                const uint2 b = __ldg(&prof[l * nphi + J2]);
+                const unsigned b0 = (a.x > gb) | (a.y > ~gb);
+                const unsigned b1 = (b.x > gb) | (b.y > ~gb);
+                word |= (b0 << l) | (b1 << (l + 16));
+            }
+            if (rr >= 1 && rr <= nrows) *reinterpret_cast<uint32_t *>(M + (int64_t)i * nphi + j) = word;
+        }
+        if (fused)
+            *reinterpret_cast<uint16_t *>(pc + rr * nphi + j) =
+                (uint16_t)(__popc(word & 0xFFFFu) | (__popc(word >> 16) << 8));
+    }
+    if (!fused) return;
+    __syncthreads();
+    uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
+    const int cnt = band_peak_search(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
+    if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+}
+
+// Peak search of one band straight from the accumulator (when the gather did not fuse it).
+__global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w, int gather_mode)
+{
+    extern __shared__ __align__(16) unsigned char pc[];
+    __shared__ unsigned s_general;
+    const int R = w.band_rows;
+    const int nb = n_bands(ax, R);
+    const int e = blockIdx.x / nb, band = blockIdx.x - e * nb;
+    const int nphi = ax.n_phi;
+    const int i0 = band * R;
+    const int nrows = min(R, ax.n_qpt - i0);
+    if (threadIdx.x < 32) {
+        unsigned u, g;
+        layer_masks(w, ax.n_layers, &u, &g);
+        if (threadIdx.x == 0) s_general = g;
+    }
+    __syncthreads();
+    if (gather_mode && s_general == 0u) return;   // the gather kernel found this band's peaks
+    const uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
+    const int v8 = nphi >> 3;
+    for (int q = threadIdx.x; q < (nrows + 2) * v8; q += kPeakThreads) {
+        const int rr = q / v8, c8 = q - rr * v8;
+        const int i = i0 - 1 + rr;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (i >= 0 && i < ax.n_qpt) v = *reinterpret_cast<const uint4 *>(M + (int64_t)i * nphi + c8 * 8);
+        const uint32_t words[4] = {v.x, v.y, v.z, v.w};
+        uint32_t packed[2] = {0u, 0u};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t lo = (uint32_t)__popc(words[u] & 0xFFFFu), hi = (uint32_t)__popc(words[u] >> 16);
+            packed[u >> 1] |= (lo | (hi << 8)) << ((u & 1) * 16);
+        }
+        *reinterpret_cast<uint2 *>(pc + rr * nphi + c8 * 8) = make_uint2(packed[0], packed[1]);
+    }
+    __syncthreads();
+    uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
+    const int cnt = band_peak_search(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
+    if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+}
+
+// One CTA per event: exclusive scan of the band counts, then the band lists concatenated into
+// the raster-ordered candidate list (the first max_cand of them).
+__global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w)
+{
+    __shared__ int s_warp[kCompactThreads / 32];
+    const int e = blockIdx.x;
+    const int nb = n_bands(ax, w.band_rows);
+    const int32_t *counts = w.band_counts + (int64_t)e * nb;
+    int32_t *offs = w.band_offs + (int64_t)e * nb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int chunk = (nb + kCompactThreads - 1) / kCompactThreads;
+    const int k0 = min(nb, threadIdx.x * chunk), k1 = min(nb, k0 + chunk);
+    int sum = 0;
+    for (int k = k0; k < k1; ++k) sum += counts[k];
+    int incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int wv = s_warp[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, wv, d);
+            if (lane >= d) wv += t;
+        }
+        s_warp[lane] = wv;
+    }
+    __syncthreads();
+    int run = (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
+    for (int k = k0; k < k1; ++k) {
+        offs[k] = run;
+        run += counts[k];
+    }
+    const int total = s_warp[kCompactThreads / 32 - 1];
+    if (threadIdx.x == 0) {
+        w.stats[e].n_candidates = (unsigned)total;
+        if (total > w.max_cand) atomicOr(&w.stats[e].device_error, HOUGH_DEVERR_CAND);
+    }
+    __syncthreads();
+    hough_candidate *cands = w.cands + (int64_t)e * w.max_cand;
+    const uint2 *lists = w.band_cands + (int64_t)e * nb * w.band_cap;
+    for (int b = warp; b < nb; b += kCompactThreads / 32) {
+        const int n = counts[b], o = offs[b];
+        for (int k = lane; k < n; k += 32) {
+            const int c = o + k;
+            if (c >= w.max_cand) break;
+            const uint2 v = lists[(int64_t)b * w.band_cap + k];
+            hough_candidate cd;
+            cd.iq = v.x / (unsigned)ax.n_phi;
+            cd.jphi = v.x % (unsigned)ax.n_phi;
+            cd.mask = v.y;
+            cd.n_members = 0u;
+            cd.icot = cd.jz0 = cd.mask2 = cd.flags = 0u;
+            cands[c] = cd;
+        }
+    }
+}
+
+template <int TPB, bool GENERAL_ONLY>
+cudaError_t launch_scatter(const VoteParams &p, size_t smem, int grid, cudaStream_t stream)
+{
+    cudaError_t err = cudaFuncSetAttribute(scatter_kernel<TPB, GENERAL_ONLY>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err) return err;
-    vote_kernel<TPB><<<grid, TPB, smem, stream>>>(p);
+    scatter_kernel<TPB, GENERAL_ONLY><<<grid, TPB, smem, stream>>>(p);
     return cudaGetLastError();
+}
+
+template <bool GENERAL_ONLY>
+cudaError_t launch_scatter_tpb(const VoteParams &p, int threads, size_t smem, int grid, cudaStream_t stream)
+{
+    switch (threads) {
+    case 128: return launch_scatter<128, GENERAL_ONLY>(p, smem, grid, stream);
+    case 256: return launch_scatter<256, GENERAL_ONLY>(p, smem, grid, stream);
+    case 512: return launch_scatter<512, GENERAL_ONLY>(p, smem, grid, stream);
+    case 1024: return launch_scatter<1024, GENERAL_ONLY>(p, smem, grid, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -246,6 +491,12 @@ size_t vote_smem_bytes(const Axes &ax, const Tiling &t)
 {
     return (size_t)t.tile_qpt * t.tile_phi * 2 + (size_t)ax.n_layers * t.tile_qpt * sizeof(TabEntry) +
            (size_t)t.tile_qpt * sizeof(float);
+}
+
+size_t gather_smem_bytes(const Axes &ax, int band_rows)
+{
+    const int rows = band_rows + 2;
+    return (size_t)rows * 16 * 8 + (size_t)((rows + 3) & ~3) * 4 + (size_t)rows * ax.n_phi;
 }
 
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
@@ -262,13 +513,32 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
     p.refine_eps = refine_eps;
     const size_t smem = vote_smem_bytes(ax, t);
     const int grid = w.n_events * p.tiles_per_event;
-    switch (t.threads) {
-    case 128: return launch_tpb<128>(p, smem, grid, stream);
-    case 256: return launch_tpb<256>(p, smem, grid, stream);
-    case 512: return launch_tpb<512>(p, smem, grid, stream);
-    case 1024: return launch_tpb<1024>(p, smem, grid, stream);
-    default: return cudaErrorInvalidValue;
+    if (t.vote_mode == HOUGH_VOTE_SCATTER) return launch_scatter_tpb<false>(p, t.threads, smem, grid, stream);
+    // gather every table layer, then let the scatter kernel add the layers whose radii differ
+    const size_t gsmem = gather_smem_bytes(ax, w.band_rows);
+    const int gblocks = w.n_events * n_bands(ax, w.band_rows);
+    const bool pow2 = (ax.n_phi & (ax.n_phi - 1)) == 0;
+    cudaError_t err;
+    if (pow2) {
+        if ((err = cudaFuncSetAttribute(gather_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem))) return err;
+        gather_kernel<true><<<gblocks, kPeakThreads, gsmem, stream>>>(ax, w);
+    } else {
+        if ((err = cudaFuncSetAttribute(gather_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem))) return err;
+        gather_kernel<false><<<gblocks, kPeakThreads, gsmem, stream>>>(ax, w);
     }
+    if ((err = cudaGetLastError())) return err;
+    return launch_scatter_tpb<true>(p, t.threads, smem, grid, stream);
+}
+
+cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
+{
+    const int nb = n_bands(ax, w.band_rows);
+    const size_t smem = (size_t)(w.band_rows + 2) * ax.n_phi;
+    cudaError_t err;
+    if ((err = cudaFuncSetAttribute(peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return err;
+    peaks_kernel<<<w.n_events * nb, kPeakThreads, smem, stream>>>(ax, w, t.vote_mode == HOUGH_VOTE_GATHER ? 1 : 0);
+    compact_kernel<<<w.n_events, kCompactThreads, 0, stream>>>(ax, w);
+    return cudaGetLastError();
 }
 
 }  // namespace hough

@@ -46,7 +46,7 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(binding.Binning) == 6 * 4 + 6 * 8
     assert ctypes.sizeof(binding.Limits) == 16
     assert binding.CANDIDATE_DTYPE.itemsize == 32
-    assert ctypes.sizeof(binding.Tiling) == 16
+    assert ctypes.sizeof(binding.Tiling) == 32
 
 
 def test_version_and_error_strings_without_gpu(lib):

@@ -30,7 +30,7 @@ def binding():
 def run_gpu(binding, geometry, binning, ev, tiling=None, where="host", max_candidates=1 << 18):
     with binding.HoughContext(geometry, binning, max_hits=max(ev.n_hits, 1), max_candidates=max_candidates) as ctx:
         if tiling:
-            ctx.set_tiling(*tiling)
+            ctx.set_tiling(**tiling) if isinstance(tiling, dict) else ctx.set_tiling(*tiling)
         if where == "host":
             ctx.vote_event(ev)
         else:
@@ -90,10 +90,13 @@ def test_device_pointers_match_host_path(binding):
     assert np.array_equal(a["candidates"], b["candidates"])
 
 
-@pytest.mark.parametrize("tiling", [(1, 64, 128), (7, 128, 256), (16, 256, 256), (32, 512, 512),
-                                    (64, 1024, 1024), (3, 2048, 128)])
+@pytest.mark.parametrize("tiling", [(1, 64, 128, 1), (7, 128, 256, 1), (16, 256, 256, 1), (32, 512, 512, 1),
+                                    (64, 1024, 1024, 1), (3, 2048, 128, 1), (16, 256, 256, 0, 1),
+                                    (16, 256, 256, 0, 3), (16, 256, 256, 0, 8), (16, 256, 256, 0, 16),
+                                    (16, 256, 256, 1, 5)])
 def test_tilings_agree_bit_for_bit(binding, tiling):
-    """Every tile shape, including ragged last slabs (512 rows by 7 or 3), gives the same result."""
+    """Every tile shape of the scatter kernel (ragged last slabs: 512 rows by 7 or 3), and every band
+    height of the gather kernel and of the peak search, gives the same result."""
     w = eg.WORKLOADS["pileup_100k"]
     ev = w.event(2).subset(np.arange(40000))
     base = run_gpu(binding, w.geometry, w.binning, ev)
@@ -167,7 +170,8 @@ def test_odd_sizes_and_few_layers(binding):
     bn = eg.Binning(n_qpt=77, qpt_min=-1.3, qpt_max=0.9, n_phi=192, threshold=2, n_cot=17, n_z0=23,
                     cot_min=-3.0, cot_max=2.0, z0_min=-20.0, z0_max=10.0)
     ev = eg.simulate_event(g, 40, (0.7, 20.0), 30, seed=99)
-    check_event(binding, g, bn, ev, tiling=(5, 64, 128))
+    check_event(binding, g, bn, ev, tiling=(5, 64, 128, 1, 3))
+    check_event(binding, g, bn, ev, tiling=(5, 64, 128, 0, 7))
     check_event(binding, g, bn, ev)
 
 
