@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="pileup_100k", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-events", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -218,23 +220,27 @@ def main():
     votes = int(st.votes)
     n_cand = int(st.n_candidates)
 
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    lib_t = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    launches0 = binding.kernel_launches()
-    with ClockSampler(local) as clocks:
-        for k in range(args.steps):
+    def timed_steps(steps):
+        """K steps, each after an L2 flush, bracketed by CUDA events on the launching stream."""
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        lib_t = []
+        for k in range(steps):
             flush.zero_()
             e0[k].record(stream)
             step()
             e1[k].record(stream)
             lib_t.append(ctx.timing())
         torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in zip(e0, e1)], lib_t
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = binding.kernel_launches()
+    with ClockSampler(local) as clocks:
+        step_ms, lib_t = timed_steps(args.steps)
     launches = binding.kernel_launches() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -244,10 +250,62 @@ def main():
     events_per_s = world * args.steps / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
 
-    vote_ms = statistics.mean(t["vote_ms"] for t in lib_t)
-    stage_ms = statistics.mean(t["stage_ms"] for t in lib_t)
-    peaks_ms = statistics.mean(t["peaks_ms"] for t in lib_t)
-    stage2_ms = statistics.mean(t["stage2_ms"] for t in lib_t)
+    stage_means = {k: statistics.mean(t[k] for t in lib_t) for k in lib_t[0]}
+    vote_ms = stage_means["vote_ms"]
+
+    # the same steps with the shared-atomic scatter vote (the paper's GPU design) for comparison
+    tiling0 = ctx.get_tiling()
+    ctx.set_tiling(vote_mode=binding.VOTE_SCATTER)
+    for _ in range(3):
+        step()
+    sc_ms, sc_t = timed_steps(min(args.steps, 20))
+    ctx.set_tiling(**tiling0)
+    scatter_vote_ms = statistics.mean(t["vote_ms"] for t in sc_t)
+    scatter = {"events_per_s": len(sc_ms) / (sum(sc_ms) * 1e-3), "ms_per_step": statistics.mean(sc_ms),
+               "vote_ms": scatter_vote_ms, "peaks_ms": statistics.mean(t["peaks_ms"] for t in sc_t),
+               "votes_per_s_in_vote_kernel": votes / (scatter_vote_ms * 1e-3),
+               "smem_atomic_frac": votes / (scatter_vote_ms * 1e-3) / smem_peak}
+
+    # batched: the batch workload (events of 100-10,000 tracks plus 0.5-2x noise), one replayed graph
+    # per step over all events
+    wb = eg.WORKLOADS["batch_256"]
+    bev = [wb.event(rank * args.batch_events + i) for i in range(args.batch_events)]
+    bhs = np.zeros(len(bev) + 1, dtype=np.int64)
+    bhs[1:] = np.cumsum([e.n_hits for e in bev])
+    bdev = [torch.from_numpy(np.concatenate([getattr(e, k) for e in bev])).to(dev) for k in ("r", "phi", "z", "layer")]
+    batch = binding.HoughBatch(wb.geometry, wb.binning, max_events=len(bev), max_hits=int(bhs[-1]),
+                               max_candidates=1 << 18, max_members=1 << 21, device=local)
+    for _ in range(3):
+        batch.run(*bdev, bhs, where=binding.DEVICE, stream=stream)
+    torch.cuda.synchronize()
+    bstats = [batch.stats(e) for e in range(len(bev))]
+    b_votes = sum(int(st.votes) for st in bstats)
+    b_cands = sum(int(st.n_candidates) for st in bstats)
+    b_members = sum(int(st.n_members) for st in bstats)
+    b0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
+    b1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
+    blaunch0 = binding.kernel_launches()
+    for k in range(args.batch_steps):
+        flush.zero_()
+        b0[k].record(stream)
+        batch.run(*bdev, bhs, where=binding.DEVICE, stream=stream)
+        b1[k].record(stream)
+    torch.cuda.synchronize()
+    blaunches = binding.kernel_launches() - blaunch0
+    batch_ms = [a.elapsed_time(b) for a, b in zip(b0, b1)]
+    b_total = sum(batch_ms)
+    if world > 1:
+        t = torch.tensor([b_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        b_total = float(t.item())
+    batched = {"events_per_s": world * len(bev) * args.batch_steps / (b_total * 1e-3),
+               "votes_per_s": world * b_votes * args.batch_steps / (b_total * 1e-3),
+               "ms_per_batch": b_total / args.batch_steps, "events_per_batch": len(bev), "hits_per_batch": int(bhs[-1]),
+               "votes_per_batch": b_votes, "candidates_per_batch": b_cands, "members_per_batch": b_members,
+               "steps": args.batch_steps, "gpu_launches": int(blaunches),
+               "mode": "one CUDA-graph replay per batch; kernels span all events"}
+    batch.close()
+    del bdev
 
     # end to end through hough_process from pinned host buffers
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (ev.r, ev.phi, ev.z, ev.layer)]
@@ -295,9 +353,11 @@ def main():
         "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": n, "votes_per_event": votes,
                    "candidates_per_event": n_cand, "mode": "plain: one event per step, one launch sequence",
                    "l2": "flushed before every timed step (256 MiB write)",
-                   "tiling": list(ctx.get_tiling())},
+                   "tiling": ctx.get_tiling()},
         "votes_per_s": votes * events_per_s,
-        "stage_ms": {"staging": stage_ms, "vote": vote_ms, "peaks": peaks_ms, "stage2": stage2_ms},
+        "stage_ms": stage_means,
+        "scatter_mode": scatter,
+        "batched": batched,
         "roofline": {"bound": "smem_atomic", "kernel": "vote_kernel", "achieved": achieved_atomics / 1e9,
                      "peak": smem_peak / 1e9, "unit": "Gatomic/s", "frac": achieved_atomics / smem_peak,
                      "peak_kind": "measured by hough_microbench_smem_or (conflict-free 32-lane atomicOr)",

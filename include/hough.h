@@ -230,13 +230,17 @@ int hough_set_tiling(hough_ctx *ctx, const hough_tiling *tiling);
 int hough_get_tiling(const hough_ctx *ctx, hough_tiling *tiling);
 
 /*
- * Per-step device time of the last event, measured with CUDA events recorded on the stream each
- * call was given (enabled by hough_enable_timing; off by default).  stage_ms covers the hit
- * staging kernels, vote_ms the vote kernel alone, peaks_ms the peak search, stage2_ms membership
- * and the stage-2 vote.  hough_get_timing synchronises; HOUGH_ENOTREADY before a timed event.
+ * Device time of the last event's steps, measured with CUDA events recorded on the stream each
+ * call was given (enabled by hough_enable_timing; off by default).  stage_ms: hit staging;
+ * vote_ms: the vote (= gather_ms + scatter_ms); peaks_ms: peak search (= band_peaks_ms +
+ * compact_ms); stage2_ms: membership and the stage-2 vote.  gather_ms covers the gather kernel
+ * (with the fused peak search); scatter_ms the shared-atomic kernel; band_peaks_ms the standalone
+ * peak kernel; compact_ms the candidate scan.  hough_get_timing synchronises; HOUGH_ENOTREADY
+ * before a timed event.
  */
 typedef struct hough_timing {
     float stage_ms, vote_ms, peaks_ms, stage2_ms;
+    float gather_ms, scatter_ms, band_peaks_ms, compact_ms;
 } hough_timing;
 
 int hough_enable_timing(hough_ctx *ctx, int on);
@@ -253,6 +257,56 @@ uint64_t hough_kernel_launches(void);
  * milliseconds and returns lane-atomics per second in *atomics_per_s.  Synchronises the device.
  */
 int hough_microbench_smem_or(int device, int pattern, double ms, double *atomics_per_s);
+
+/*
+ * Batched processing: many events of uneven size through the whole path (vote, peaks, membership,
+ * stage 2) in one launch sequence, captured into a CUDA graph on the first call for a given
+ * number of events and replayed afterwards.  Each event keeps its own accumulator, candidate list
+ * and member pool, with the limits below applying per event (max_hits: over the whole batch).
+ */
+typedef struct hough_batch_limits {
+    int32_t max_events;       /* events per batch, >= 1 */
+    int32_t max_candidates;   /* candidates kept per event, >= 1 */
+    int64_t max_hits;         /* hits per batch, 1 .. 2^31 - 1 */
+    int32_t max_members;      /* member hits kept per event, >= 1 */
+    int32_t reserved;         /* must be 0 */
+} hough_batch_limits;
+
+typedef struct hough_batch hough_batch;
+
+int hough_batch_create(const hough_geometry *geometry, const hough_binning *binning,
+                       const hough_batch_limits *limits, int device, hough_batch **out);
+void hough_batch_destroy(hough_batch *batch);
+
+/* Kernel configuration, as hough_set_tiling; drops the captured graphs. */
+int hough_batch_set_tiling(hough_batch *batch, const hough_tiling *tiling);
+
+/*
+ * Run the path on n_events events.  Hits of all events are concatenated in r, phi, z, layer
+ * (as for hough_vote, in `where` memory); event e owns hits [hit_start[e], hit_start[e+1]) --
+ * hit_start is a host array of n_events + 1 entries starting at 0.  With HOUGH_HOST the hits are
+ * checked and copied; with HOUGH_DEVICE bad hits are dropped on the device.  Asynchronous on
+ * `stream`: device-resident inputs must stay valid until the work has run.  HOUGH_ECAPACITY when
+ * n_events or the hit total exceeds the limits.
+ */
+int hough_batch_run(hough_batch *batch, const float *r, const float *phi, const float *z,
+                    const uint8_t *layer, const int64_t *hit_start, int32_t n_events, int where,
+                    void *stream);
+
+/*
+ * All events' candidates of the last run, concatenated in event order into `out` (cap entries,
+ * `where` memory); offsets (host, n_events + 1) receives each event's first index.  Each event's
+ * list is in raster order with stage-2 fields filled.  HOUGH_ETRUNC when the total exceeds cap.
+ * Synchronises `stream`.
+ */
+int hough_batch_candidates(hough_batch *batch, hough_candidate *out, int64_t cap, int64_t *offsets,
+                           int where, void *stream);
+
+/* Counters of one event of the last run.  Synchronises `stream`. */
+int hough_batch_stats(hough_batch *batch, int32_t event, hough_stats *out, void *stream);
+
+/* The accumulator of one event of the last run.  Synchronises `stream`. */
+int hough_batch_accumulator(hough_batch *batch, int32_t event, uint16_t *out, int where, void *stream);
 
 /*
  * Stage-1 vote of one event with no allocation at all.  The paper has no counterpart: this exists

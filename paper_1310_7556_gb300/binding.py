@@ -46,6 +46,11 @@ class Limits(ctypes.Structure):
                 ("max_members", ctypes.c_int32)]
 
 
+class BatchLimits(ctypes.Structure):
+    _fields_ = [("max_events", ctypes.c_int32), ("max_candidates", ctypes.c_int32), ("max_hits", ctypes.c_int64),
+                ("max_members", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("votes", ctypes.c_uint64), ("votes_by_layer", ctypes.c_uint64 * MAX_LAYERS),
                 ("general_votes", ctypes.c_uint64), ("refined_votes", ctypes.c_uint64),
@@ -55,8 +60,8 @@ class Stats(ctypes.Structure):
 
 
 class Timing(ctypes.Structure):
-    _fields_ = [("stage_ms", ctypes.c_float), ("vote_ms", ctypes.c_float), ("peaks_ms", ctypes.c_float),
-                ("stage2_ms", ctypes.c_float)]
+    _fields_ = [(n, ctypes.c_float) for n in ("stage_ms", "vote_ms", "peaks_ms", "stage2_ms", "gather_ms",
+                                              "scatter_ms", "band_peaks_ms", "compact_ms")]
 
 
 class Tiling(ctypes.Structure):
@@ -98,6 +103,14 @@ _SIGNATURES = {
                                  ctypes.c_int),
     "hough_vote_static": ([ctypes.POINTER(Geometry), ctypes.POINTER(Binning), _P, _P, _P, _P, _I64, _P, _P, _P],
                           ctypes.c_int),
+    "hough_batch_create": ([ctypes.POINTER(Geometry), ctypes.POINTER(Binning), ctypes.POINTER(BatchLimits),
+                            ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "hough_batch_destroy": ([_P], None),
+    "hough_batch_set_tiling": ([_P, ctypes.POINTER(Tiling)], ctypes.c_int),
+    "hough_batch_run": ([_P, _P, _P, _P, _P, _P, _I32, ctypes.c_int, _P], ctypes.c_int),
+    "hough_batch_candidates": ([_P, _P, _I64, _P, ctypes.c_int, _P], ctypes.c_int),
+    "hough_batch_stats": ([_P, _I32, ctypes.POINTER(Stats), _P], ctypes.c_int),
+    "hough_batch_accumulator": ([_P, _I32, _P, ctypes.c_int, _P], ctypes.c_int),
 }
 
 
@@ -272,7 +285,7 @@ class HoughContext:
     def timing(self) -> dict:
         t = Timing()
         _check(self._lib.hough_get_timing(self._h, ctypes.byref(t)))
-        return dict(stage_ms=t.stage_ms, vote_ms=t.vote_ms, peaks_ms=t.peaks_ms, stage2_ms=t.stage2_ms)
+        return {n: getattr(t, n) for n, _ in Timing._fields_}
 
     # -- tiling -------------------------------------------------------------------------------
     def set_tiling(self, tile_qpt: int = None, tile_phi: int = None, threads: int = None,
@@ -292,3 +305,77 @@ class HoughContext:
         _check(self._lib.hough_get_tiling(self._h, ctypes.byref(t)))
         return dict(tile_qpt=t.tile_qpt, tile_phi=t.tile_phi, threads=t.threads, vote_mode=t.vote_mode,
                     band_rows=t.band_rows)
+
+
+class HoughBatch:
+    """One hough_batch: many events through the whole path per call, as a replayed CUDA graph."""
+
+    def __init__(self, geometry, binning, max_events: int, max_hits: int, max_candidates: int = 1 << 17,
+                 max_members: int = 1 << 21, device: int = 0):
+        lib = load()
+        self._lib = lib
+        self.binning = binning
+        g, b = make_geometry(geometry), make_binning(binning)
+        lim = BatchLimits(max_events=max_events, max_candidates=max_candidates, max_hits=max_hits,
+                          max_members=max_members, reserved=0)
+        h = _P()
+        _check(lib.hough_batch_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(lim), device, ctypes.byref(h)))
+        self._h = h
+        self.max_events, self.max_candidates = max_events, max_candidates
+        self.n_events = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hough_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_tiling(self, tile_qpt=16, tile_phi=256, threads=256, vote_mode=VOTE_GATHER, band_rows=1):
+        t = Tiling(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, vote_mode=vote_mode, band_rows=band_rows)
+        _check(self._lib.hough_batch_set_tiling(self._h, ctypes.byref(t)))
+
+    def run(self, r, phi, z, layer, hit_start, where=HOST, stream=None):
+        """hit_start: int64 numpy array of n_events + 1 offsets (host)."""
+        hit_start = np.ascontiguousarray(hit_start, dtype=np.int64)
+        if where == HOST and isinstance(r, np.ndarray):
+            r, phi, z = (np.ascontiguousarray(a, dtype=np.float32) for a in (r, phi, z))
+            layer = np.ascontiguousarray(layer, dtype=np.uint8)
+        self._keep = (r, phi, z, layer, hit_start)
+        n_events = hit_start.shape[0] - 1
+        _check(self._lib.hough_batch_run(self._h, _ptr(r), _ptr(phi), _ptr(z), _ptr(layer), _ptr(hit_start),
+                                         n_events, where, _stream(stream)))
+        self.n_events = n_events
+
+    def run_events(self, events, stream=None):
+        """Concatenate Event objects (host) and run them."""
+        hs = np.zeros(len(events) + 1, dtype=np.int64)
+        hs[1:] = np.cumsum([e.n_hits for e in events])
+        cat = lambda name, dt: np.concatenate([getattr(e, name) for e in events]).astype(dt)
+        self.run(cat("r", np.float32), cat("phi", np.float32), cat("z", np.float32), cat("layer", np.uint8), hs,
+                 stream=stream)
+
+    def candidates(self, cap=None, stream=None):
+        """(candidates of all events concatenated, offsets[n_events + 1])."""
+        cap = self.max_events * self.max_candidates if cap is None else cap
+        out = np.zeros(max(cap, 1), dtype=CANDIDATE_DTYPE)
+        offs = np.zeros(self.n_events + 1, dtype=np.int64)
+        _check(self._lib.hough_batch_candidates(self._h, _ptr(out), cap, _ptr(offs), HOST, _stream(stream)))
+        return out[: offs[-1]].copy(), offs
+
+    def stats(self, event, stream=None, allow_device_error=False) -> Stats:
+        st = Stats()
+        _check(self._lib.hough_batch_stats(self._h, event, ctypes.byref(st), _stream(stream)),
+               allow=(EDEVICE,) if allow_device_error else ())
+        return st
+
+    def accumulator(self, event, stream=None) -> np.ndarray:
+        out = np.zeros((self.binning.n_qpt, self.binning.n_phi), dtype=np.uint16)
+        _check(self._lib.hough_batch_accumulator(self._h, event, _ptr(out), HOST, _stream(stream)))
+        return out

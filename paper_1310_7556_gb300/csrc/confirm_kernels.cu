@@ -2,28 +2,39 @@
 // expensive computations"): for each candidate, the hits whose stage-1 vote fell in its cell
 // (membership) and their vote in a (cot theta, z0) grid (stage 2), in one kernel.
 //
-// One CTA per candidate at a time.  Membership: only layers present in the candidate's mask can
-// hold members.  For a table layer the vote inverts exactly -- a hit of bucket J votes into column
-// j on row i when J = j + I_i + (f < g_i) -- so two buckets of the sorted hits hold all of that
-// layer's members; other layers scan the buckets their radius range allows and redo the vote per
-// hit (FP32 with FP64 refinement, as in the vote kernel).  Members are enumerated in a fixed order
-// (layer, bucket, position), so chunks of them can be re-enumerated when a candidate has more
-// members than shared memory holds.
+// Work scales with a candidate's votes, not with the size of the stage-2 grid: every warp owns a
+// private n_cot x n_z0 grid of layer masks in shared memory, clear between candidates.  A vote pass
+// ORs each (member, cot row) vote into it with a shared atomic; a collect pass revisits the same
+// votes, takes each touched word with atomicExch (reading and clearing it in one step) and keeps
+// the cell with the most layers, the lowest row-major index on ties.
 //
-// Stage 2: the n_cot x n_z0 grid of layer masks lives in shared memory.  For a member with arc
-// length s the z0 coordinate w(m) = n_z0 (z - s t_m - z0_min) / (z0_max - z0_min) is linear in the
-// cot row m; it is evaluated in FP32 around the member's own crossing row m_ref, and a vote within
-// kStage2Eps of a z0 edge is recomputed in FP64 exactly as the definition reads.  The result is the
-// cell with the most layers, the lowest row-major index on ties.
+// Events of moderate occupancy produce tens of thousands of candidates with a dozen members each,
+// saturated events a few hundred with fifty or more.  So a first kernel (a warp per candidate)
+// enumerates each candidate's members once, into the member pool, and files the candidate as
+// small (at most kSmallMembers members: stage 2 by one warp) or large (stage 2 by a whole CTA).
+//
+// Membership: only layers present in the candidate's mask can hold members.  For a table layer
+// the vote inverts exactly -- a hit of bucket J votes into column j on row i when
+// J = j + I_i + (f < g_i) -- so two buckets of the sorted hits hold all of that layer's members;
+// other layers scan the buckets their radius range allows and redo the vote per hit (FP32 with
+// FP64 refinement, as in the vote kernel).  Members are enumerated in a fixed order (layer, bucket,
+// position), so a candidate with more members than a warp's buffer is processed in chunks that
+// are re-enumerated.
+//
+// Stage-2 arithmetic: for a member with arc length s the z0 coordinate
+// w(m) = n_z0 (z - s t_m - z0_min) / (z0_max - z0_min) is linear in the cot row m; it is evaluated
+// in FP32 around the member's own crossing row m_ref, and a vote within kStage2Eps of a z0 edge is
+// recomputed in FP64 exactly as the definition reads.
 #include "hough_internal.cuh"
 
 namespace hough {
 
 namespace {
 
-constexpr int kConfirmThreads = 256;
-constexpr int kConfirmWarps = kConfirmThreads / 32;
-constexpr int kMemberChunk = 1024;
+constexpr int kConfirmWarpsMax = 8;
+constexpr int kMemberCap = 128;        // members a warp holds at a time
+constexpr int kSmallMembers = 32;      // candidates up to this size are finished by one warp
+constexpr int kLargeChunk = 1024;      // members a CTA holds at a time for a large candidate
 
 // The (up to two) ranges of staged hits of layer l that can hold members of candidate (i, j).
 struct LayerScan {
@@ -78,51 +89,65 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
     return sc;
 }
 
-// Members of one layer, enumerated by one warp in the fixed order.  Returns their number; when
-// `s_pos` is given, stores the member of rank (rank_base + local rank) in s_pos[rank - lo] if it
-// lies in [lo, hi), and in pool[rank] if rank < pool_n.
-__device__ int warp_layer_members(const Axes &ax, const Workspace &w, const HotHit *hot, const ColdHit *cold,
-                                  const LayerScan &sc, int i, int j, float s32, float refine_eps, int rank_base,
-                                  int lo, int hi, int *s_pos, int32_t *pool, int pool_n)
+// Members of candidate (i, j) enumerated by one warp in the fixed order.  Returns their number;
+// stores the staged position of each member of rank r in [lo, lo + cap) in pos[r - lo], and, when
+// pool is given, in pool[r] for r < pool_n.
+__device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t *offs, const HotHit *hot,
+                              const ColdHit *cold, uint32_t mask, int i, int j, float s32, float refine_eps,
+                              int lo, int cap, int *pos, int32_t *pool, int pool_n)
 {
     const int lane = threadIdx.x & 31;
     int count = 0;
-    for (int q = 0; q < sc.nr; ++q) {
-        for (int base = sc.st[q]; base < sc.en[q]; base += 32) {
-            const int pos = base + lane;
-            bool mem = false;
-            if (pos < sc.en[q]) {
-                const HotHit hh = hot[pos];
-                if (sc.table) {
-                    mem = q == 0 ? !(hh.f < sc.g) : (hh.f < sc.g);
-                } else {
-                    const int rlo = (int)(hh.rows & 0xFFFFu), rhi = (int)(hh.rows >> 16);
-                    if (i >= rlo && i <= rhi) {
-                        const float x = fminf(fmaxf(hh.c * w.kq32[i], -1.f), 1.f);
-                        const float vq = fmaf(-asinf(x), s32, hh.f);
-                        const float fl = floorf(vq);
-                        const float d = vq - fl;
-                        int jj = (int)(hh.jl & 0xFFFFu) + (int)fl;
-                        if (d < refine_eps || d > 1.f - refine_eps || fabsf(x) > kRefineXLim) {
-                            const ColdHit ch = cold[pos];
-                            jj = exact_bin(ax, (double)ch.phi, __dmul_rn(sagitta_coef(ax, (double)ch.r), qpt_centre(ax, i)));
+    while (mask) {
+        const int l = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        if (l >= ax.n_layers) break;
+        const LayerScan sc = layer_scan(ax, w, offs, l, i, j, s32);
+        for (int q = 0; q < sc.nr; ++q) {
+            for (int base = sc.st[q]; base < sc.en[q]; base += 32) {
+                const int p = base + lane;
+                bool mem = false;
+                if (p < sc.en[q]) {
+                    const HotHit hh = hot[p];
+                    if (sc.table) {
+                        mem = q == 0 ? !(hh.f < sc.g) : (hh.f < sc.g);
+                    } else {
+                        const int rlo = (int)(hh.rows & 0xFFFFu), rhi = (int)(hh.rows >> 16);
+                        if (i >= rlo && i <= rhi) {
+                            const float x = fminf(fmaxf(hh.c * w.kq32[i], -1.f), 1.f);
+                            const float vq = fmaf(-asinf(x), s32, hh.f);
+                            const float fl = floorf(vq);
+                            const float d = vq - fl;
+                            int jj = (int)(hh.jl & 0xFFFFu) + (int)fl;
+                            if (d < refine_eps || d > 1.f - refine_eps || fabsf(x) > kRefineXLim) {
+                                const ColdHit ch = cold[p];
+                                jj = exact_bin(ax, (double)ch.phi, __dmul_rn(sagitta_coef(ax, (double)ch.r), qpt_centre(ax, i)));
+                            }
+                            mem = wrap_col(jj, ax.n_phi) == j;
                         }
-                        mem = wrap_col(jj, ax.n_phi) == j;
                     }
                 }
-            }
-            const unsigned ball = __ballot_sync(0xFFFFFFFFu, mem);
-            if (s_pos && mem) {
-                const int r = rank_base + count + __popc(ball & ((1u << lane) - 1u));
-                if (r >= lo && r < hi) {
-                    s_pos[r - lo] = pos;
-                    if (r < pool_n) pool[r] = pos;
+                const unsigned ball = __ballot_sync(0xFFFFFFFFu, mem);
+                if (mem) {
+                    const int r = count + __popc(ball & ((1u << lane) - 1u));
+                    if (r >= lo && r < lo + cap) pos[r - lo] = p;
+                    if (pool && r < pool_n) pool[r] = p;
                 }
+                count += __popc(ball);
             }
-            count += __popc(ball);
         }
     }
     return count;
+}
+
+// Arc length of a member at row i: from the table for a uniform layer, else r asin(|x|) / |x| in FP64.
+__device__ __forceinline__ double member_arc(const Axes &ax, const Workspace &w, int l, int i, float r)
+{
+    const LayerInfo li = w.info[l];
+    if (li.uniform) return w.arc[l * ax.n_qpt + i];
+    const double rd = (double)r;
+    const double axv = fabs(__dmul_rn(sagitta_coef(ax, rd), qpt_centre(ax, i)));
+    return axv > 0.0 ? __ddiv_rn(__dmul_rn(rd, asin(axv)), axv) : rd;
 }
 
 // z0 coordinate of one stage-2 vote exactly as the definition reads (FP64, nothing fused).
@@ -133,163 +158,305 @@ __device__ __forceinline__ double exact_z0_coord(const Axes &ax, double z, doubl
     return __ddiv_rn(__dmul_rn((double)ax.n_z0, __dsub_rn(z0, ax.z0_min)), __dsub_rn(ax.z0_max, ax.z0_min));
 }
 
-__global__ void __launch_bounds__(kConfirmThreads) confirm_kernel(Axes ax, Workspace w, float s32, float refine_eps)
+// Stage-2 coefficients of one member at row i: z0 coordinate w(m) = a - (m - m_ref) b in FP32.
+__device__ __forceinline__ void member_coefficients(const Axes &ax, const Workspace &w, const HotHit *hot,
+                                                    const ColdHit *cold, int p, int i, double zscale, double t0,
+                                                    float *a_out, float *b_out, int *mrl_out)
+{
+    const int l = (int)((hot[p].jl >> 16) & 0xFu);
+    const ColdHit ch = cold[p];
+    const double s = member_arc(ax, w, l, i, ch.r);
+    const double A = __dmul_rn(zscale, __dsub_rn(__dsub_rn((double)ch.z, ax.z0_min), __dmul_rn(s, t0)));
+    const double B = __dmul_rn(zscale, __dmul_rn(s, ax.dt));
+    int mref = 0;
+    if (B > 0.0) mref = (int)fminf(fmaxf(rintf((float)A / (float)B), 0.f), (float)(ax.n_cot - 1));
+    *a_out = (float)(A - (double)mref * B);
+    *b_out = (float)B;
+    *mrl_out = mref | (l << 16);
+}
+
+// z0 bin of the vote of member p at cot row m (-1 outside the grid).
+__device__ __forceinline__ int stage2_bin(const Axes &ax, const Workspace &w, const ColdHit *cold, int p, int i,
+                                          float a, float b, int mrl, int m)
+{
+    const int mref = mrl & 0xFFFF;
+    const float wv = fmaf(-(float)(m - mref), b, a);
+    const float fl = floorf(wv);
+    const float d = wv - fl;
+    int nz;
+    if (d < kStage2Eps || d > 1.f - kStage2Eps) {
+        const ColdHit ch = cold[p];
+        nz = (int)floor(exact_z0_coord(ax, (double)ch.z, member_arc(ax, w, mrl >> 16, i, ch.r), m));
+    } else {
+        nz = (wv < -1.f || wv > (float)ax.n_z0 + 1.f) ? -1 : (int)fl;
+    }
+    return (nz >= 0 && nz < ax.n_z0) ? nz : -1;
+}
+
+struct Best {
+    unsigned cnt, cell, mask;
+};
+
+// Vote (pass 0) or collect (pass 1) of the (member, cot row) pair into `grid`.
+__device__ __forceinline__ void stage2_pair(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
+                                            int p, int i, float a, float b, int mrl, int m, int pass,
+                                            unsigned long long &votes, Best &best)
+{
+    const int nz = stage2_bin(ax, w, cold, p, i, a, b, mrl, m);
+    if (nz < 0) return;
+    const unsigned cell = (unsigned)(m * ax.n_z0 + nz);
+    if (pass == 0) {
+        atomicOr(&grid[cell >> 1], (1u << (mrl >> 16)) << ((cell & 1u) << 4));
+        ++votes;
+        return;
+    }
+    // both halves of a word are judged by whichever thread takes it
+    const uint32_t word = atomicExch(&grid[cell >> 1], 0u);
+    if (!word) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t m16 = (word >> (16 * h)) & 0xFFFFu;
+        const unsigned cc = (cell & ~1u) | (unsigned)h;
+        const unsigned cnt = (unsigned)__popc(m16);
+        if (m16 && (cnt > best.cnt || (cnt == best.cnt && cc < best.cell))) {
+            best.cnt = cnt;
+            best.cell = cc;
+            best.mask = m16;
+        }
+    }
+}
+
+__device__ __forceinline__ void warp_best(Best &best)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned oc = __shfl_xor_sync(0xFFFFFFFFu, best.cnt, d);
+        const unsigned ol = __shfl_xor_sync(0xFFFFFFFFu, best.cell, d);
+        const unsigned om = __shfl_xor_sync(0xFFFFFFFFu, best.mask, d);
+        if (oc > best.cnt || (oc == best.cnt && ol < best.cell)) {
+            best.cnt = oc;
+            best.cell = ol;
+            best.mask = om;
+        }
+    }
+}
+
+__device__ __forceinline__ hough_candidate finished(const Axes &ax, hough_candidate cd, int n, int written, const Best &b)
+{
+    cd.n_members = (uint32_t)n;
+    cd.icot = b.cell / (unsigned)ax.n_z0;
+    cd.jz0 = b.cell % (unsigned)ax.n_z0;
+    cd.mask2 = b.mask;
+    cd.flags = ((int)b.cnt >= ax.threshold ? 1u : 0u) | (written < n ? 2u : 0u);
+    return cd;
+}
+
+// Membership: one warp per candidate enumerates its members once, in the fixed order, straight into
+// the member pool, records the candidate's member count, and files the candidate under the small
+// or the large list for the stage-2 kernels.
+__global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, Workspace w, float s32, float refine_eps)
+{
+    __shared__ int s_pos[kConfirmWarpsMax][kMemberCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    int *pos = s_pos[warp];
+    const int nkeys = ax.n_layers * ax.n_phi;
+    const int total = (int)w.counters->total_cands;
+    for (int f = blockIdx.x * nwarps + warp; f < total; f += gridDim.x * nwarps) {
+        const int e = upper_index(w.cand_base, w.n_events, f);
+        const int c = f - w.cand_base[e];
+        const int64_t hstart = w.hit_start[e];
+        const HotHit *hot = w.hot + hstart;
+        const ColdHit *cold = w.cold + hstart;
+        const int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
+        int32_t *pool = w.mem_pool + (int64_t)e * w.max_members;
+        hough_candidate *cands = w.cands + (int64_t)e * w.max_cand;
+        const hough_candidate cd = cands[c];
+        const int n = warp_enumerate(ax, w, offs, hot, cold, cd.mask, (int)cd.iq, (int)cd.jphi, s32, refine_eps, 0,
+                                     kMemberCap, pos, nullptr, 0);
+        int base = 0, written = 0;
+        if (lane == 0) {
+            const unsigned b = n ? atomicAdd(&w.stats[e].pool_used, (unsigned)n) : 0u;
+            const long long room = (long long)w.max_members - (long long)b;
+            base = (int)min((long long)b, (long long)w.max_members);
+            written = n ? (int)max(0LL, min((long long)n, room)) : 0;
+            w.mem_start[(int64_t)e * w.max_cand + c] = base;
+            w.mem_count[(int64_t)e * w.max_cand + c] = written;
+            cands[c].n_members = (uint32_t)n;
+            if (n) atomicAdd(&w.stats[e].n_members, (unsigned)n);
+            int2 *list = n <= kSmallMembers ? w.small_list : w.large_list;
+            unsigned *cnt = n <= kSmallMembers ? &w.counters->n_small : &w.counters->n_large;
+            list[atomicAdd(cnt, 1u)] = make_int2(e, c);
+        }
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        written = __shfl_sync(0xFFFFFFFFu, written, 0);
+        __syncwarp();
+        if (n <= kMemberCap) {
+            for (int q = lane; q < written; q += 32) pool[base + q] = pos[q];
+        } else if (written > 0) {
+            warp_enumerate(ax, w, offs, hot, cold, cd.mask, (int)cd.iq, (int)cd.jphi, s32, refine_eps, 0, 0, pos,
+                           pool + base, written);
+        }
+        __syncwarp();
+    }
+}
+
+// Members [lo, lo + nm) of candidate c into pos: from the pool when all of them were stored there,
+// else re-enumerated (only when max_members was exceeded).  Called by one warp.
+__device__ __forceinline__ void load_members(const Axes &ax, const Workspace &w, const int32_t *offs, const HotHit *hot,
+                                             const ColdHit *cold, const int32_t *pool, const hough_candidate &cd,
+                                             int base, int written, int n, int lo, int nm, int cap, float s32,
+                                             float refine_eps, int *pos)
+{
+    const int lane = threadIdx.x & 31;
+    if (written == n) {
+        for (int q = lane; q < nm; q += 32) pos[q] = pool[base + lo + q];
+    } else {
+        warp_enumerate(ax, w, offs, hot, cold, cd.mask, (int)cd.iq, (int)cd.jphi, s32, refine_eps, lo, cap, pos,
+                       nullptr, 0);
+    }
+}
+
+struct Stage2Ctx {
+    const HotHit *hot;
+    const ColdHit *cold;
+    const int32_t *offs;
+    const int32_t *pool;
+    hough_candidate *cands;
+    double zscale, t0;
+};
+
+__device__ __forceinline__ Stage2Ctx stage2_ctx(const Axes &ax, const Workspace &w, int e)
+{
+    Stage2Ctx x;
+    const int64_t hstart = w.hit_start[e];
+    x.hot = w.hot + hstart;
+    x.cold = w.cold + hstart;
+    x.offs = w.offs + (int64_t)e * (ax.n_layers * ax.n_phi + 1);
+    x.pool = w.mem_pool + (int64_t)e * w.max_members;
+    x.cands = w.cands + (int64_t)e * w.max_cand;
+    x.zscale = __ddiv_rn((double)ax.n_z0, __dsub_rn(ax.z0_max, ax.z0_min));
+    x.t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
+    return x;
+}
+
+// Stage 2 of the small candidates: one warp each, in the warp's private grid.
+__global__ void __launch_bounds__(kConfirmWarpsMax * 32) stage2_small_kernel(Axes ax, Workspace w, float s32,
+                                                                              float refine_eps, int grid_words)
 {
     extern __shared__ __align__(16) unsigned char smem2[];
-    const int ncell = ax.n_cot * ax.n_z0;
-    const int nwords = (((ncell + 1) >> 1) + 1) & ~1;
-    uint32_t *grid2 = reinterpret_cast<uint32_t *>(smem2);           // n_cot x n_z0 masks, 2 per word
-    double *m_s = reinterpret_cast<double *>(grid2 + nwords);
-    float *m_z = reinterpret_cast<float *>(m_s + kMemberChunk);
-    float *m_a = m_z + kMemberChunk;
-    float *m_b = m_a + kMemberChunk;
-    int *m_ref = reinterpret_cast<int *>(m_b + kMemberChunk);
-    int *m_l = m_ref + kMemberChunk;
-    int *s_pos = m_l + kMemberChunk;
-    __shared__ int s_lcount[HOUGH_MAX_LAYERS], s_loff[HOUGH_MAX_LAYERS];
-    __shared__ int s_total, s_base, s_written;
-    __shared__ unsigned long long s_best[kConfirmWarps];
-    __shared__ unsigned long long s_votes;
-
-    const int e = blockIdx.y;
-    const int ncand = (int)min((unsigned)w.max_cand, w.stats[e].n_candidates);
-    const int nkeys = ax.n_layers * ax.n_phi;
-    const int64_t hstart = w.hit_start[e];
-    const HotHit *hot = w.hot + hstart;
-    const ColdHit *cold = w.cold + hstart;
-    const int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
-    int32_t *pool = w.mem_pool + (int64_t)e * w.max_members;
-    hough_candidate *cands = w.cands + (int64_t)e * w.max_cand;
-    const double zscale = __ddiv_rn((double)ax.n_z0, __dsub_rn(ax.z0_max, ax.z0_min));
-    const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
+    __shared__ int s_pos[kConfirmWarpsMax][kSmallMembers];
+    __shared__ float s_a[kConfirmWarpsMax][kSmallMembers], s_b[kConfirmWarpsMax][kSmallMembers];
+    __shared__ int s_mrl[kConfirmWarpsMax][kSmallMembers];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_votes = 0ull;
-    unsigned members_total = 0;
-
-    for (int c = blockIdx.x; c < ncand; c += gridDim.x) {
-        const hough_candidate cd = cands[c];
-        const int i = (int)cd.iq, j = (int)cd.jphi;
-        // count the members of each layer in the candidate's mask (warp w: layers w and w + 8)
-        for (int l = warp; l < HOUGH_MAX_LAYERS; l += kConfirmWarps) {
-            int n = 0;
-            if (l < ax.n_layers && ((cd.mask >> l) & 1u)) {
-                const LayerScan sc = layer_scan(ax, w, offs, l, i, j, s32);
-                n = warp_layer_members(ax, w, hot, cold, sc, i, j, s32, refine_eps, 0, 0, 0, nullptr, nullptr, 0);
+    const int nwarps = blockDim.x >> 5;
+    uint32_t *grid = reinterpret_cast<uint32_t *>(smem2) + warp * grid_words;
+    int *pos = s_pos[warp];
+    float *ma = s_a[warp], *mb = s_b[warp];
+    int *mrl = s_mrl[warp];
+    const int nsmall = (int)w.counters->n_small;
+    if (blockIdx.x * nwarps >= nsmall) return;
+    for (int q = lane; q < grid_words; q += 32) grid[q] = 0u;
+    __syncwarp();
+    const int ncot = ax.n_cot;
+    for (int idx = blockIdx.x * nwarps + warp; idx < nsmall; idx += gridDim.x * nwarps) {
+        unsigned long long votes = 0;
+        const int2 ec = w.small_list[idx];
+        const int e = ec.x, c = ec.y;
+        const Stage2Ctx x = stage2_ctx(ax, w, e);
+        const hough_candidate cd = x.cands[c];
+        const int i = (int)cd.iq, n = (int)cd.n_members;
+        const int base = w.mem_start[(int64_t)e * w.max_cand + c], written = w.mem_count[(int64_t)e * w.max_cand + c];
+        load_members(ax, w, x.offs, x.hot, x.cold, x.pool, cd, base, written, n, 0, n, kSmallMembers, s32, refine_eps,
+                     pos);
+        __syncwarp();
+        if (lane < n) member_coefficients(ax, w, x.hot, x.cold, pos[lane], i, x.zscale, x.t0, &ma[lane], &mb[lane], &mrl[lane]);
+        __syncwarp();
+        Best best = {0u, 0u, 0u};
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int q = 0; q < n; ++q) {
+                const float a = ma[q], b = mb[q];
+                const int r = mrl[q], p = pos[q];
+                for (int m = lane; m < ncot; m += 32) stage2_pair(ax, w, x.cold, grid, p, i, a, b, r, m, pass, votes, best);
             }
-            if (lane == 0) s_lcount[l] = n;
+            __syncwarp();
         }
-        for (int q = threadIdx.x; q < nwords; q += kConfirmThreads) grid2[q] = 0u;
+        warp_best(best);
+        if (lane == 0) x.cands[c] = finished(ax, cd, n, written, best);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
+        if (lane == 0 && votes) atomicAdd(&w.stats[e].stage2_votes, votes);
+        __syncwarp();
+    }
+}
+
+// Stage 2 of the large candidates: one CTA each, members in chunks of kLargeChunk.
+__global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(Axes ax, Workspace w, float s32,
+                                                                                 float refine_eps)
+{
+    extern __shared__ __align__(16) unsigned char smem2[];
+    __shared__ int s_pos[kLargeChunk];
+    __shared__ float s_a[kLargeChunk], s_b[kLargeChunk];
+    __shared__ int s_mrl[kLargeChunk];
+    __shared__ Best s_best[kConfirmWarpsMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    uint32_t *grid = reinterpret_cast<uint32_t *>(smem2);
+    const int nlarge = (int)w.counters->n_large;
+    if (blockIdx.x >= nlarge) return;
+    const int grid_words = (((ax.n_cot * ax.n_z0 + 1) >> 1) + 3) & ~3;
+    for (int q = threadIdx.x; q < grid_words; q += blockDim.x) grid[q] = 0u;
+    const int ncot = ax.n_cot;
+    for (int idx = blockIdx.x; idx < nlarge; idx += gridDim.x) {
+        unsigned long long votes = 0;
+        const int2 ec = w.large_list[idx];
+        const int e = ec.x, c = ec.y;
+        const Stage2Ctx x = stage2_ctx(ax, w, e);
+        const hough_candidate cd = x.cands[c];
+        const int i = (int)cd.iq, n = (int)cd.n_members;
+        const int base = w.mem_start[(int64_t)e * w.max_cand + c], written = w.mem_count[(int64_t)e * w.max_cand + c];
+        const int nchunks = (n + kLargeChunk - 1) / kLargeChunk;
+        Best best = {0u, 0u, 0u};
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k = 0; k < nchunks; ++k) {
+                const int lo = k * kLargeChunk;
+                const int nm = min(kLargeChunk, n - lo);
+                if (pass == 0 || nchunks > 1) {
+                    __syncthreads();
+                    if (written == n) {
+                        for (int q = threadIdx.x; q < nm; q += blockDim.x) s_pos[q] = x.pool[base + lo + q];
+                    } else if (warp == 0) {
+                        warp_enumerate(ax, w, x.offs, x.hot, x.cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, lo,
+                                       kLargeChunk, s_pos, nullptr, 0);
+                    }
+                    __syncthreads();
+                    for (int q = threadIdx.x; q < nm; q += blockDim.x)
+                        member_coefficients(ax, w, x.hot, x.cold, s_pos[q], i, x.zscale, x.t0, &s_a[q], &s_b[q], &s_mrl[q]);
+                    __syncthreads();
+                }
+                // (member, cot row) pairs spread over the CTA
+                for (int pq = threadIdx.x; pq < nm * ncot; pq += blockDim.x) {
+                    const int q = pq / ncot, m = pq - q * ncot;
+                    stage2_pair(ax, w, x.cold, grid, s_pos[q], i, s_a[q], s_b[q], s_mrl[q], m, pass, votes, best);
+                }
+                __syncthreads();
+            }
+        }
+        warp_best(best);
+        if (lane == 0) s_best[warp] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int l = 0; l < HOUGH_MAX_LAYERS; ++l) {
-                s_loff[l] = acc;
-                acc += s_lcount[l];
+            Best b = s_best[0];
+            for (int q = 1; q < nwarps; ++q) {
+                const Best o = s_best[q];
+                if (o.cnt > b.cnt || (o.cnt == b.cnt && o.cell < b.cell)) b = o;
             }
-            s_total = acc;
-            const unsigned base = acc ? atomicAdd(&w.stats[e].pool_used, (unsigned)acc) : 0u;
-            const long long room = (long long)w.max_members - (long long)base;
-            s_base = (int)min((long long)base, (long long)w.max_members);
-            s_written = (int)max(0LL, min((long long)acc, room));
-            w.mem_start[(int64_t)e * w.max_cand + c] = s_base;
-            w.mem_count[(int64_t)e * w.max_cand + c] = s_written;
-        }
-        __syncthreads();
-        const int n = s_total;
-        members_total += (unsigned)n;
-        unsigned long long votes = 0;
-        for (int lo = 0; lo < n; lo += kMemberChunk) {
-            const int hi = min(n, lo + kMemberChunk);
-            // the chunk's members, in the fixed order, into shared memory (and the pool)
-            for (int l = warp; l < HOUGH_MAX_LAYERS; l += kConfirmWarps) {
-                if (s_lcount[l] == 0) continue;
-                if (s_loff[l] >= hi || s_loff[l] + s_lcount[l] <= lo) continue;
-                const LayerScan sc = layer_scan(ax, w, offs, l, i, j, s32);
-                warp_layer_members(ax, w, hot, cold, sc, i, j, s32, refine_eps, s_loff[l], lo, hi, s_pos,
-                                   pool + s_base, s_written);
-            }
-            __syncthreads();
-            const int nm = hi - lo;
-            const double k = qpt_centre(ax, i);
-            // per member: arc length (FP64) and the linear z0 coordinate around its crossing row
-            for (int q = threadIdx.x; q < nm; q += kConfirmThreads) {
-                const int pos = s_pos[q];
-                const ColdHit ch = cold[pos];
-                const int l = (int)((hot[pos].jl >> 16) & 0xFu);
-                const LayerInfo li = w.info[l];
-                double s;
-                if (li.uniform) {
-                    s = w.arc[l * ax.n_qpt + i];
-                } else {
-                    const double r = (double)ch.r;
-                    const double axv = fabs(__dmul_rn(sagitta_coef(ax, r), k));
-                    s = axv > 0.0 ? __ddiv_rn(__dmul_rn(r, asin(axv)), axv) : r;
-                }
-                const double A = __dmul_rn(zscale, __dsub_rn(__dsub_rn((double)ch.z, ax.z0_min), __dmul_rn(s, t0)));
-                const double B = __dmul_rn(zscale, __dmul_rn(s, ax.dt));
-                int mref = 0;
-                if (B > 0.0) mref = (int)fminf(fmaxf(rintf((float)A / (float)B), 0.f), (float)(ax.n_cot - 1));
-                m_s[q] = s;
-                m_z[q] = ch.z;
-                m_a[q] = (float)(A - (double)mref * B);
-                m_b[q] = (float)B;
-                m_ref[q] = mref;
-                m_l[q] = l;
-            }
-            __syncthreads();
-            for (int pq = threadIdx.x; pq < nm * ax.n_cot; pq += kConfirmThreads) {
-                const int q = pq / ax.n_cot, m = pq - q * ax.n_cot;
-                const float wv = fmaf(-(float)(m - m_ref[q]), m_b[q], m_a[q]);
-                const float fl = floorf(wv);
-                const float d = wv - fl;
-                int nz;
-                if (d < kStage2Eps || d > 1.f - kStage2Eps) {
-                    nz = (int)floor(exact_z0_coord(ax, (double)m_z[q], m_s[q], m));
-                } else {
-                    nz = (int)fl;
-                    if (wv < -1.f || wv > (float)ax.n_z0 + 1.f) nz = -1;
-                }
-                if (nz >= 0 && nz < ax.n_z0) {
-                    const int cell = m * ax.n_z0 + nz;
-                    atomicOr(&grid2[cell >> 1], (1u << m_l[q]) << ((cell & 1) << 4));
-                    ++votes;
-                }
-            }
-            __syncthreads();
-        }
-        // the cell of most layers, lowest row-major index on ties: key = count << 32 | (ncell - cell)
-        unsigned long long best = 0ull;
-        for (int cell = threadIdx.x; cell < ncell; cell += kConfirmThreads) {
-            const uint32_t m16 = (grid2[cell >> 1] >> ((cell & 1) << 4)) & 0xFFFFu;
-            const unsigned long long key = ((unsigned long long)__popc(m16) << 32) | (unsigned)(ncell - cell);
-            best = key > best ? key : best;
+            x.cands[c] = finished(ax, cd, n, written, b);
         }
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, best, d);
-            best = o > best ? o : best;
-        }
-        if (lane == 0) s_best[warp] = best;
-        if (votes) atomicAdd(&s_votes, votes);
+        for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
+        if (lane == 0 && votes) atomicAdd(&w.stats[e].stage2_votes, votes);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long b = s_best[0];
-            for (int q = 1; q < kConfirmWarps; ++q) b = s_best[q] > b ? s_best[q] : b;
-            const int cell = ncell - (int)(b & 0xFFFFFFFFu);
-            const uint32_t m16 = (grid2[cell >> 1] >> ((cell & 1) << 4)) & 0xFFFFu;
-            hough_candidate out = cd;
-            out.n_members = (uint32_t)n;
-            out.icot = (uint32_t)(cell / ax.n_z0);
-            out.jz0 = (uint32_t)(cell % ax.n_z0);
-            out.mask2 = m16;
-            out.flags = (__popc(m16) >= ax.threshold ? 1u : 0u) | (s_written < n ? 2u : 0u);
-            cands[c] = out;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        if (s_votes) atomicAdd(&w.stats[e].stage2_votes, s_votes);
-        if (members_total) atomicAdd(&w.stats[e].n_members, members_total);
     }
 }
 
@@ -300,26 +467,35 @@ __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total
         idx_out[q] = cold[w.mem_pool[q]].idx;
 }
 
+int confirm_grid_words(const Axes &ax) { return (((ax.n_cot * ax.n_z0 + 1) >> 1) + 3) & ~3; }
+
+int small_warps(const Axes &ax)
+{
+    const size_t per_warp = (size_t)confirm_grid_words(ax) * 4;
+    int wpc = (int)((160u << 10) / per_warp);
+    return max(1, min(kConfirmWarpsMax, wpc));
+}
+
 }  // namespace
 
-size_t stage2_smem_bytes(const Axes &ax)
-{
-    const int ncell = ax.n_cot * ax.n_z0;
-    const int nwords = (((ncell + 1) >> 1) + 1) & ~1;
-    return (size_t)nwords * 4 + (size_t)kMemberChunk * (8 + 4 * 6);
-}
+size_t stage2_smem_bytes(const Axes &ax) { return (size_t)small_warps(ax) * confirm_grid_words(ax) * 4; }
 
 cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream)
 {
     const float s32 = (float)(ax.n_phi * kInvTwoPi);
-    const size_t smem = stage2_smem_bytes(ax);
-    cudaError_t err = cudaFuncSetAttribute(confirm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err) return err;
-    // candidates per event are known on the device only: size the grid for the device and let
-    // each CTA stride over its event's candidates
-    int y = (4 * sms + w.n_events - 1) / w.n_events;
-    y = max(1, min(y, w.max_cand));
-    confirm_kernel<<<dim3(y, w.n_events), kConfirmThreads, smem, stream>>>(ax, w, s32, refine_eps);
+    // the number of candidates is known on the device only: persistent grids sized for the device,
+    // each warp or CTA striding over the flattened (event, candidate) work
+    member_kernel<<<4 * sms, kConfirmWarpsMax * 32, 0, stream>>>(ax, w, s32, refine_eps);
+    cudaError_t err;
+    const int nw = small_warps(ax);
+    const size_t small_smem = stage2_smem_bytes(ax);
+    if ((err = cudaFuncSetAttribute(stage2_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem)))
+        return err;
+    stage2_small_kernel<<<2 * sms, nw * 32, small_smem, stream>>>(ax, w, s32, refine_eps, confirm_grid_words(ax));
+    const size_t large_smem = (size_t)confirm_grid_words(ax) * 4;
+    if ((err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem)))
+        return err;
+    stage2_large_kernel<<<4 * sms, kConfirmWarpsMax * 32, large_smem, stream>>>(ax, w, s32, refine_eps);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,8 @@ int cuda_fail(cudaError_t e, const char *what)
 
 int hough::set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+
+
 void hough::note_launches(uint64_t n) { g_launches += n; }
 
 struct hough_ctx {
@@ -65,7 +67,9 @@ struct hough_ctx {
     int64_t n_hits = 0;
     int stage = 0;                       // 0 nothing, 1 voted, 2 peaks, 3 stage 2
     bool timing = false;
-    cudaEvent_t ev[5] = {};              // before staging, before vote, after vote, after peaks, after stage 2
+    // 0 before staging, 1 after staging, 2 after the gather, 3 after the vote, 4 after the band
+    // peaks, 5 after the candidate scan, 6 after stage 2
+    cudaEvent_t ev[7] = {};
     int timed = 0;                       // bit k: ev[k] recorded for the current event
 
     ~hough_ctx()
@@ -110,7 +114,7 @@ int check_binning(const hough_geometry *g, const hough_binning *b)
     return HOUGH_OK;
 }
 
-Axes make_axes(const hough_geometry *g, const hough_binning *b)
+Axes make_axes_impl(const hough_geometry *g, const hough_binning *b)
 {
     Axes ax;
     ax.n_layers = g->n_layers;
@@ -131,12 +135,12 @@ Axes make_axes(const hough_geometry *g, const hough_binning *b)
     return ax;
 }
 
-int check_tiling(const hough_ctx *c, const hough_tiling *t)
+int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
 {
     if (!t) return fail(HOUGH_EINVAL, "tiling is required");
     if (t->reserved[0] || t->reserved[1] || t->reserved[2]) return fail(HOUGH_EINVAL, "reserved fields must be 0");
     if (t->tile_qpt < 1 || t->tile_qpt > 256) return fail(HOUGH_EINVAL, "tile_qpt must be 1..256");
-    if (t->tile_phi < 64 || t->tile_phi % 64 || c->ax.n_phi % t->tile_phi)
+    if (t->tile_phi < 64 || t->tile_phi % 64 || ax.n_phi % t->tile_phi)
         return fail(HOUGH_EINVAL, "tile_phi must be a multiple of 64 dividing n_phi");
     if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
         return fail(HOUGH_EINVAL, "threads must be 128, 256, 512 or 1024");
@@ -145,17 +149,17 @@ int check_tiling(const hough_ctx *c, const hough_tiling *t)
     if (t->band_rows < 1 || t->band_rows > 16) return fail(HOUGH_EINVAL, "band_rows must be 1..16");
     Tiling tt{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows};
     int max_smem = 0;
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    if (vote_smem_bytes(c->ax, tt) + 1024 > (size_t)max_smem)
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (vote_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "tile needs %zu bytes of shared memory, the device allows %d",
-                    vote_smem_bytes(c->ax, tt), max_smem);
-    if (gather_smem_bytes(c->ax, t->band_rows) + 1024 > (size_t)max_smem)
+                    vote_smem_bytes(ax, tt), max_smem);
+    if ((size_t)(t->band_rows + 2) * ax.n_phi + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "band of %d rows needs %zu bytes of shared memory, the device allows %d",
-                    t->band_rows, gather_smem_bytes(c->ax, t->band_rows), max_smem);
+                    t->band_rows, (size_t)(t->band_rows + 2) * ax.n_phi, max_smem);
     return HOUGH_OK;
 }
 
-Tiling default_tiling(const Axes &ax)
+Tiling default_tiling_impl(const Axes &ax)
 {
     Tiling t;
     t.tile_phi = std::min(ax.n_phi, 256);
@@ -163,12 +167,12 @@ Tiling default_tiling(const Axes &ax)
     t.tile_qpt = std::min(ax.n_qpt, 16);
     t.threads = 256;
     t.vote_mode = HOUGH_VOTE_GATHER;
-    t.band_rows = 4;
+    t.band_rows = 1;
     return t;
 }
 
 // Largest band-list storage over every allowed band height.
-size_t band_list_entries(const Axes &ax)
+size_t band_list_entries_impl(const Axes &ax)
 {
     size_t best = 0;
     for (int r = 1; r <= 16; ++r)
@@ -176,11 +180,11 @@ size_t band_list_entries(const Axes &ax)
     return best;
 }
 
-int check_host_hits(const hough_ctx *c, const float *r, const float *phi, const float *z,
-                    const uint8_t *layer, int64_t n)
+int check_host_hits_impl(const Axes &ax, const float *r, const float *phi, const float *z,
+                         const uint8_t *layer, int64_t n)
 {
     for (int64_t h = 0; h < n; ++h) {
-        if (layer[h] >= c->ax.n_layers) return fail(HOUGH_EINVAL, "hit %lld: layer %d >= n_layers", (long long)h, layer[h]);
+        if (layer[h] >= ax.n_layers) return fail(HOUGH_EINVAL, "hit %lld: layer %d >= n_layers", (long long)h, layer[h]);
         if (!(r[h] > 0.f) || !std::isfinite(r[h])) return fail(HOUGH_EINVAL, "hit %lld: r must be finite and > 0", (long long)h);
         if (!(std::fabs(phi[h]) <= 1000.f)) return fail(HOUGH_EINVAL, "hit %lld: phi must be finite, |phi| <= 1000", (long long)h);
         if (!std::isfinite(z[h])) return fail(HOUGH_EINVAL, "hit %lld: z must be finite", (long long)h);
@@ -196,7 +200,7 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     if (where != HOUGH_HOST && where != HOUGH_DEVICE) return fail(HOUGH_EINVAL, "where must be HOUGH_HOST or HOUGH_DEVICE");
     if (n > 0 && (!r || !phi || !z || !layer)) return fail(HOUGH_EINVAL, "hit arrays are required");
     if (where == HOUGH_HOST) {
-        int rc = check_host_hits(c, r, phi, z, layer, n);
+        int rc = check_host_hits_impl(c->ax, r, phi, z, layer, n);
         if (rc) return rc;
         if (n > 0) {
             CU(cudaMemcpyAsync(c->in_r, r, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy r");
@@ -218,8 +222,10 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1; }
     CU(launch_stage(c->ax, c->w, s), "stage kernels");
     if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
-    CU(launch_vote(c->ax, c->w, c->tiling, c->refine_eps, s), "vote kernel");
+    if (c->tiling.vote_mode == HOUGH_VOTE_GATHER) CU(launch_gather(c->ax, c->w, s), "gather kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
+    CU(launch_scatter(c->ax, c->w, c->tiling, c->refine_eps, c->tiling.vote_mode == HOUGH_VOTE_GATHER, s), "vote kernel");
+    if (c->timing) { CU(cudaEventRecord(c->ev[3], s), "event"); c->timed |= 8; }
     g_launches += kStageLaunches + (c->tiling.vote_mode == HOUGH_VOTE_SCATTER ? 1 : kVoteLaunches);
     c->stage = 1;
     return HOUGH_OK;
@@ -233,6 +239,34 @@ int read_stats(hough_ctx *c, cudaStream_t s)
 }
 
 }  // namespace
+
+Axes hough::make_axes(const hough_geometry *g, const hough_binning *b) { return make_axes_impl(g, b); }
+int hough::check_geometry_binning(const hough_geometry *g, const hough_binning *b) { return check_binning(g, b); }
+int hough::check_tiling_for(const Axes &ax, int device, const hough_tiling *t) { return check_tiling_impl(ax, device, t); }
+Tiling hough::default_tiling_for(const Axes &ax) { return default_tiling_impl(ax); }
+size_t hough::band_list_entries(const Axes &ax) { return band_list_entries_impl(ax); }
+int hough::check_host_hits_for(const Axes &ax, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                               int64_t n)
+{
+    return check_host_hits_impl(ax, r, phi, z, layer, n);
+}
+
+void hough::fill_stats(const DevStats &d, const LayerInfo *info, int n_layers, hough_stats *out)
+{
+    std::memset(out, 0, sizeof(*out));
+    for (int l = 0; l < HOUGH_MAX_LAYERS; ++l) {
+        out->votes_by_layer[l] = d.votes_by_layer[l];
+        out->votes += d.votes_by_layer[l];
+        if (l < n_layers && info[l].present && info[l].uniform) out->uniform_layers |= 1u << l;
+        else if (l < n_layers) out->general_votes += d.votes_by_layer[l];
+    }
+    out->refined_votes = d.refined_votes;
+    out->stage2_votes = d.stage2_votes;
+    out->n_hits = (int64_t)d.n_hits;
+    out->n_candidates = d.n_candidates;
+    out->n_members = d.n_members;
+    out->device_error = d.device_error;
+}
 
 extern "C" {
 
@@ -261,8 +295,8 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     c->geometry = *geometry;
     c->binning = *binning;
     c->limits = *limits;
-    c->ax = make_axes(geometry, binning);
-    c->tiling = default_tiling(c->ax);
+    c->ax = make_axes_impl(geometry, binning);
+    c->tiling = default_tiling_impl(c->ax);
     c->refine_eps = refine_eps_for(c->ax);
     const Axes &ax = c->ax;
     const int64_t n = limits->max_hits;
@@ -276,16 +310,18 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&c->hit_start, 2));
     A(c->alloc(&c->in_r, n)); A(c->alloc(&c->in_phi, n)); A(c->alloc(&c->in_z, n)); A(c->alloc(&c->in_layer, n));
     A(c->alloc(&w.key, n)); A(c->alloc(&w.rank, n)); A(c->alloc(&w.hot_tmp, n));
-    A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1)); A(c->alloc(&w.prof, nkeys));
+    A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1)); A(c->alloc(&w.prof, (size_t)prof_event_entries(ax)));
     A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n));
     A(c->alloc(&w.radii, 1)); A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
     A(c->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(c->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
     A(c->alloc(&w.kq32, ax.n_qpt));
     A(c->alloc(&w.M, (size_t)ax.n_qpt * ax.n_phi));
     A(c->alloc(&w.cands, w.max_cand));
-    A(c->alloc(&w.band_cands, band_list_entries(ax)));
+    A(c->alloc(&w.band_cands, band_list_entries_impl(ax)));
     A(c->alloc(&w.band_counts, n_bands(ax, 1))); A(c->alloc(&w.band_offs, n_bands(ax, 1)));
     A(c->alloc(&w.mem_start, w.max_cand)); A(c->alloc(&w.mem_count, w.max_cand));
+    A(c->alloc(&w.small_list, w.max_cand)); A(c->alloc(&w.large_list, w.max_cand));
+    A(c->alloc(&w.cand_base, 2)); A(c->alloc(&w.counters, 1));
     A(c->alloc(&w.mem_pool, w.max_members)); A(c->alloc(&c->mem_idx, w.max_members));
     A(c->alloc(&w.stats, 1));
     A(cudaMallocHost(&c->stats_host, sizeof(DevStats)));
@@ -294,6 +330,8 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
         return cuda_fail(e, "hough_create allocation");
     }
     w.hit_start = c->hit_start;
+    w.hit_capacity = n;
+    w.inputs = nullptr;
     w.band_rows = c->tiling.band_rows;
     w.band_cap = band_capacity(ax, c->tiling.band_rows);
     // FP32 q/pT bin centres: the FP64 centre rounded once
@@ -327,8 +365,10 @@ int hough_peaks(hough_ctx *c, void *stream)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     if (c->stage < 1) return fail(HOUGH_ENOTREADY, "hough_vote has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    CU(launch_peaks(c->ax, c->w, c->tiling, (cudaStream_t)stream), "peak kernels");
-    if (c->timing) { CU(cudaEventRecord(c->ev[3], (cudaStream_t)stream), "event"); c->timed |= 8; }
+    CU(launch_band_peaks(c->ax, c->w, c->tiling, (cudaStream_t)stream), "peak kernel");
+    if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
+    CU(launch_compact(c->ax, c->w, (cudaStream_t)stream), "candidate scan kernel");
+    if (c->timing) { CU(cudaEventRecord(c->ev[5], (cudaStream_t)stream), "event"); c->timed |= 32; }
     g_launches += kPeakLaunches;
     c->stage = 2;
     return HOUGH_OK;
@@ -340,7 +380,7 @@ int hough_stage2(hough_ctx *c, void *stream)
     if (c->stage < 2) return fail(HOUGH_ENOTREADY, "hough_peaks has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     CU(launch_stage2(c->ax, c->w, c->sms, c->refine_eps, (cudaStream_t)stream), "stage-2 kernels");
-    if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
+    if (c->timing) { CU(cudaEventRecord(c->ev[6], (cudaStream_t)stream), "event"); c->timed |= 64; }
     g_launches += kStage2Launches;
     c->stage = 3;
     return HOUGH_OK;
@@ -430,19 +470,7 @@ int hough_get_stats(hough_ctx *c, hough_stats *out, void *stream)
     LayerInfo info[HOUGH_MAX_LAYERS];
     CU(cudaMemcpy(info, c->w.info, sizeof(info), cudaMemcpyDeviceToHost), "copy layer info");
     const DevStats &d = *c->stats_host;
-    std::memset(out, 0, sizeof(*out));
-    for (int l = 0; l < HOUGH_MAX_LAYERS; ++l) {
-        out->votes_by_layer[l] = d.votes_by_layer[l];
-        out->votes += d.votes_by_layer[l];
-        if (l < c->ax.n_layers && info[l].present && info[l].uniform) out->uniform_layers |= 1u << l;
-        else if (l < c->ax.n_layers) out->general_votes += d.votes_by_layer[l];
-    }
-    out->refined_votes = d.refined_votes;
-    out->stage2_votes = d.stage2_votes;
-    out->n_hits = (int64_t)d.n_hits;
-    out->n_candidates = d.n_candidates;
-    out->n_members = d.n_members;
-    out->device_error = d.device_error;
+    fill_stats(d, info, c->ax.n_layers, out);
     if (d.device_error) return fail(HOUGH_EDEVICE, "device-side check failed: bits 0x%x", d.device_error);
     return HOUGH_OK;
 }
@@ -460,7 +488,7 @@ int hough_process(hough_ctx *c, const float *r, const float *phi, const float *z
 int hough_set_tiling(hough_ctx *c, const hough_tiling *t)
 {
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
-    int rc = check_tiling(c, t);
+    int rc = check_tiling_impl(c->ax, c->device, t);
     if (rc) return rc;
     c->tiling = Tiling{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows};
     return HOUGH_OK;
@@ -480,19 +508,22 @@ int hough_enable_timing(hough_ctx *c, int on)
 int hough_get_timing(hough_ctx *c, hough_timing *out)
 {
     if (!c || !out) return fail(HOUGH_EINVAL, "bad arguments");
-    if (!(c->timed & 7)) return fail(HOUGH_ENOTREADY, "no timed event");
+    if ((c->timed & 15) != 15) return fail(HOUGH_ENOTREADY, "no timed event");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    float ms[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = 0; k < 4; ++k) {
-        if ((c->timed >> (k + 1)) & 1) {
-            CU(cudaEventSynchronize(c->ev[k + 1]), "event synchronise");
-            CU(cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]), "event elapsed");
+    auto span = [&](int a, int b, float *ms) -> int {
+        *ms = 0.f;
+        if (((c->timed >> a) & 1) && ((c->timed >> b) & 1)) {
+            CU(cudaEventSynchronize(c->ev[b]), "event synchronise");
+            CU(cudaEventElapsedTime(ms, c->ev[a], c->ev[b]), "event elapsed");
         }
-    }
-    out->stage_ms = ms[0];
-    out->vote_ms = ms[1];
-    out->peaks_ms = ms[2];
-    out->stage2_ms = ms[3];
+        return HOUGH_OK;
+    };
+    int rc;
+    if ((rc = span(0, 1, &out->stage_ms)) || (rc = span(1, 3, &out->vote_ms)) || (rc = span(1, 2, &out->gather_ms)) ||
+        (rc = span(2, 3, &out->scatter_ms)) || (rc = span(3, 5, &out->peaks_ms)) ||
+        (rc = span(3, 4, &out->band_peaks_ms)) || (rc = span(4, 5, &out->compact_ms)) ||
+        (rc = span(5, 6, &out->stage2_ms)))
+        return rc;
     return HOUGH_OK;
 }
 

@@ -6,8 +6,10 @@
 //   key[n], rank[n]           counting-sort key (layer * Nphi + J) and the hit's rank in its bucket
 //   hot_tmp[n]                the hit's 16-byte staged record, input order
 //   counts[L*Nphi]            bucket sizes; offs[L*Nphi + 1] their exclusive prefix sum (event-local)
-//   prof[L*Nphi]  (8 B)       per (layer, bucket J): .x = max over the bucket of bits(f) + 1,
-//                             .y = max over bucket J+1 of ~bits(f) (0 when the bucket is empty)
+//   prof[16*(Nphi+16)] (8 B)  per (layer, bucket J): .x = max over the bucket of bits(f) + 1,
+//                             .y = max over bucket J+1 of ~bits(f) (0 when the bucket is empty);
+//                             entries Nphi..Nphi+15 of each layer repeat entries 0..15
+//                             (so a window of consecutive buckets never wraps), 16 layers always
 //   hot[n], cold[n] (16 B)    staged hits sorted by (layer, J); cold holds r, phi, z, input index
 //   tab[L*Nq] (8 B)           per (layer, q/pT row): Nphi asin(x) / (2 pi) = I + g, for layers whose
 //                             hits share one radius; arc[L*Nq] the arc length s (FP64)
@@ -65,6 +67,7 @@ struct DevStats {
     unsigned int n_members;
     unsigned int device_error;
     unsigned int pool_used;     // member-pool entries handed out
+    unsigned int pad;
 };
 
 // Per-layer radius range: min and max of the hit radii as float bits (radii are > 0).
@@ -87,20 +90,36 @@ struct TableMemo {
     uint32_t r_bits[HOUGH_MAX_LAYERS];
     int32_t valid[HOUGH_MAX_LAYERS];
     int32_t dirty[HOUGH_MAX_LAYERS];
+    int32_t lo[HOUGH_MAX_LAYERS], hi[HOUGH_MAX_LAYERS];   // voting rows of r_bits
+};
+
+// Device-resident hit pointers, for launch sequences captured once and replayed on new inputs.
+struct HitInputs {
+    const float *r, *phi, *z;
+    const uint8_t *layer;
+};
+
+// Counters of a whole batch.
+struct BatchCounters {
+    unsigned int total_cands;      // candidates kept over all events
+    unsigned int n_small, n_large; // entries of the stage-2 work lists
+    unsigned int pad;
 };
 
 // Device buffers of a batch of events that share one set of axes.
 struct Workspace {
     int n_events;
-    int64_t n_hits_total;
+    int64_t n_hits_total;         // < 0: read hit_start[n_events] on the device
+    int64_t hit_capacity;         // grid sizing when the total is read on the device
     const int64_t *hit_start;     // device, n_events + 1
     const float *r, *phi, *z;
     const uint8_t *layer;
+    const HitInputs *inputs;      // when set, the hit pointers are read from here on the device
     int32_t *key, *rank;          // per hit
     HotHit *hot_tmp;              // per hit, input order
     int32_t *counts;              // n_events * nkeys
     int32_t *offs;                // n_events * (nkeys + 1)
-    uint2 *prof;                  // n_events * nkeys
+    uint2 *prof;                  // n_events * prof_event_entries
     HotHit *hot;                  // per hit, sorted within each event's range
     ColdHit *cold;
     LayerRadii *radii;            // batch-wide
@@ -117,6 +136,10 @@ struct Workspace {
     int32_t *mem_pool;            // n_events * max_members: event-local staged positions
     int32_t *mem_start;           // n_events * max_cand
     int32_t *mem_count;           // n_events * max_cand: entries written to the pool
+    int2 *small_list;             // n_events * max_cand (event, candidate): for the warp stage-2 kernel
+    int2 *large_list;             // n_events * max_cand (event, candidate): for the CTA stage-2 kernel
+    int32_t *cand_base;           // n_events + 1: first flattened candidate index of each event
+    BatchCounters *counters;
     DevStats *stats;              // n_events
     int max_cand, max_members;
     int band_rows, band_cap;
@@ -138,6 +161,10 @@ constexpr float kRefineXLim = 0.99f;
 constexpr float kStage2Eps = 2e-4f;
 
 __host__ __device__ inline int n_keys(const Axes &ax) { return ax.n_layers * ax.n_phi; }
+// Bucket-profile stride per layer and per event (16 layers, each padded by 16 repeated buckets).
+constexpr int kProfPad = 16;
+__host__ __device__ inline int prof_stride(const Axes &ax) { return ax.n_phi + kProfPad; }
+__host__ __device__ inline int64_t prof_event_entries(const Axes &ax) { return (int64_t)HOUGH_MAX_LAYERS * prof_stride(ax); }
 __host__ __device__ inline int n_bands(const Axes &ax, int band_rows) { return (ax.n_qpt + band_rows - 1) / band_rows; }
 // Candidates are never 8-neighbours, so a band holds at most one per 2 x 2 block.
 __host__ __device__ inline int band_capacity(const Axes &ax, int band_rows)
@@ -155,13 +182,29 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
                         cudaStream_t stream);
 cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
+// The pieces of launch_vote and launch_peaks, for callers that time them separately.
+cudaError_t launch_gather(const Axes &ax, const Workspace &w, cudaStream_t stream);
+cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps, bool general_only,
+                           cudaStream_t stream);
+cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
+cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream);
+cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream);
 cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream);
 cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t total, cudaStream_t stream);
 cudaError_t run_smem_or_bench(int device, int pattern, double ms, double *atomics_per_s, uint64_t *launches);
 
 size_t vote_smem_bytes(const Axes &ax, const Tiling &t);
-size_t gather_smem_bytes(const Axes &ax, int band_rows);
 size_t stage2_smem_bytes(const Axes &ax);
+
+// Host helpers shared by the single-event and the batch entry points (hough_api.cu).
+Axes make_axes(const hough_geometry *g, const hough_binning *b);
+int check_geometry_binning(const hough_geometry *g, const hough_binning *b);
+int check_tiling_for(const Axes &ax, int device, const hough_tiling *t);
+Tiling default_tiling_for(const Axes &ax);
+size_t band_list_entries(const Axes &ax);
+int check_host_hits_for(const Axes &ax, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                        int64_t n);
+void fill_stats(const DevStats &d, const LayerInfo *info, int n_layers, hough_stats *out);
 
 // Record a failure for hough_last_error (returns code), and count launches for hough_kernel_launches.
 int set_last_error(int code, const char *msg);
@@ -170,8 +213,8 @@ void note_launches(uint64_t n);
 // Kernels launched by each enqueue function (for hough_kernel_launches).
 constexpr int kStageLaunches = 5;
 constexpr int kVoteLaunches = 2;
-constexpr int kPeakLaunches = 2;
-constexpr int kStage2Launches = 1;
+constexpr int kPeakLaunches = 3;
+constexpr int kStage2Launches = 3;
 
 // Exact FP64 helpers used by the staging, table and refinement code.  They evaluate the
 // definitions in the order of the method's formulas with explicitly rounded operations,
@@ -184,6 +227,35 @@ __device__ __forceinline__ double qpt_centre(const Axes &ax, int i)
 __device__ __forceinline__ double sagitta_coef(const Axes &ax, double r_cm)
 {
     return __dmul_rn(__dmul_rn(0.15, ax.b), __ddiv_rn(r_cm, 100.0));
+}
+
+// Hit total and hit arrays of the batch (from the device when the launch sequence is replayed).
+__device__ __forceinline__ int64_t hit_total(const Workspace &w)
+{
+    return w.n_hits_total >= 0 ? w.n_hits_total : w.hit_start[w.n_events];
+}
+
+__device__ __forceinline__ HitInputs hit_inputs(const Workspace &w)
+{
+    if (w.inputs) return *w.inputs;
+    HitInputs in;
+    in.r = w.r;
+    in.phi = w.phi;
+    in.z = w.z;
+    in.layer = w.layer;
+    return in;
+}
+
+// Last index e in [0, n) with base[e] <= f (base non-decreasing, base[0] = 0).
+template <typename T>
+__device__ __forceinline__ int upper_index(const T *base, int n, long long f)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long long)__ldg(&base[mid]) <= f) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Event index of hit h: the last e with hit_start[e] <= h.
@@ -237,51 +309,73 @@ __device__ __forceinline__ int wrap_col(int j, int n)
 // Peak test of the cells of rows 1..nrows of a band held as layer counts in shared memory
 // (`pc`, (nrows + 2) rows of Nphi bytes, row 0 and row nrows + 1 the halo), in raster order.
 // A cell with count p is a candidate when p >= threshold, the neighbours at (-1,-1), (-1,0),
-// (-1,+1), (0,-1) are below p and the other four are not above it; phi0 wraps.  Candidates go
-// to `out` (cell index i * Nphi + j, mask read from M) in raster order; returns their number.
-// Called by all kPeakThreads threads of the block.
+// (-1,+1), (0,-1) are below p and the other four are not above it; phi0 wraps.  Each thread tests
+// 8 consecutive cells per pass, so thread order is raster order and one block-wide scan of the
+// per-thread counts places every candidate.  Candidates go to `out` (cell index i * Nphi + j,
+// mask read from M) in raster order; returns their number.  Called by all TPB threads.
+template <int TPB>
 __device__ __forceinline__ int band_peak_search(const unsigned char *pc, int nrows, int i0, int nphi, int threshold,
                                                 const uint16_t *M, uint2 *out, int cap)
 {
-    __shared__ int s_warp[kPeakThreads / 32];
+    __shared__ int s_warp[TPB / 32];
+    __shared__ int s_total;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ncell = nrows * nphi;
+    const int eighth = nphi >> 3;
+    const int items = nrows * eighth;
     int running = 0;
-    for (int base = 0; base < ncell; base += kPeakThreads) {
-        const int cell = base + threadIdx.x;
-        bool is_peak = false;
-        int rr = 0, j = 0;
-        if (cell < ncell) {
-            rr = cell / nphi;
-            j = cell - rr * nphi;
+    for (int base = 0; base < items; base += TPB) {
+        const int it = base + threadIdx.x;
+        unsigned pk = 0u;
+        int rr = 0, j0 = 0;
+        if (it < items) {
+            rr = it / eighth;
+            j0 = (it - rr * eighth) * 8;
             const unsigned char *row = pc + (rr + 1) * nphi;
-            const int p = row[j];
-            if (p >= threshold) {
-                const int jm = wrap_col(j - 1, nphi), jp = wrap_col(j + 1, nphi);
-                const unsigned char *up = row - nphi, *dn = row + nphi;
-                is_peak = up[jm] < p && up[j] < p && up[jp] < p && row[jm] < p &&
-                          row[jp] <= p && dn[jm] <= p && dn[j] <= p && dn[jp] <= p;
+            const unsigned char *up = row - nphi, *dn = row + nphi;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = j0 + c;
+                const int p = row[j];
+                if (p >= threshold) {
+                    const int jm = wrap_col(j - 1, nphi), jp = wrap_col(j + 1, nphi);
+                    const bool peak = up[jm] < p && up[j] < p && up[jp] < p && row[jm] < p &&
+                                      row[jp] <= p && dn[jm] <= p && dn[j] <= p && dn[jp] <= p;
+                    pk |= (unsigned)peak << c;
+                }
             }
         }
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, is_peak);
-        // skip the block-wide prefix when no thread of the block found a candidate
-        const int any = __syncthreads_or(ball != 0u);
-        if (!any) continue;
-        if (lane == 0) s_warp[warp] = __popc(ball);
-        __syncthreads();
-        int before = 0, total = 0;
+        const int cnt = __popc(pk);
+        // skip the block-wide scan when no thread of the block found a candidate
+        if (!__syncthreads_or(cnt)) continue;
+        int incl = cnt;
 #pragma unroll
-        for (int q = 0; q < kPeakThreads / 32; ++q) {
-            const int c = s_warp[q];
-            before += q < warp ? c : 0;
-            total += c;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += t;
         }
-        if (is_peak) {
-            const int idx = running + before + __popc(ball & ((1u << lane) - 1u));
-            const int cellg = (i0 + rr) * nphi + j;
-            if (idx < cap) out[idx] = make_uint2((unsigned)cellg, (unsigned)M[cellg]);
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = lane < TPB / 32 ? s_warp[lane] : 0;
+            int wi = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+                if (lane >= d) wi += t;
+            }
+            if (lane < TPB / 32) s_warp[lane] = wi - v;
+            if (lane == 31) s_total = wi;
         }
-        running += total;
+        __syncthreads();
+        int idx = running + s_warp[warp] + incl - cnt;
+        while (pk) {
+            const int c = __ffs(pk) - 1;
+            pk &= pk - 1u;
+            const unsigned cellg = (unsigned)(i0 + rr) * (unsigned)nphi + (unsigned)(j0 + c);
+            if (idx < cap) out[idx] = make_uint2(cellg, (unsigned)M[cellg]);
+            ++idx;
+        }
+        running += s_total;
         __syncthreads();
     }
     return running;

@@ -33,13 +33,15 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
     const int nkeys = n_keys(ax);
     // FP32 sagitta coefficient of the per-vote path; its rounding is covered by the refine window
     const float cscale = (float)(0.15 * ax.b / 100.0);
-    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < w.n_hits_total;
+    const int64_t total = hit_total(w);
+    const HitInputs in = hit_inputs(w);
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total;
          h += (int64_t)gridDim.x * blockDim.x) {
         const int e = event_of(w.hit_start, w.n_events, h);
-        const float rr = __ldg(&w.r[h]);
-        const float ph = __ldg(&w.phi[h]);
-        const float zz = __ldg(&w.z[h]);
-        const int l = __ldg(&w.layer[h]);
+        const float rr = __ldg(&in.r[h]);
+        const float ph = __ldg(&in.phi[h]);
+        const float zz = __ldg(&in.z[h]);
+        const int l = __ldg(&in.layer[h]);
         unsigned bad = 0;
         if (l >= ax.n_layers) bad |= HOUGH_DEVERR_LAYER;
         if (!(rr > 0.f) || !isfinite(rr) || !(fabsf(ph) <= 1000.f) || !isfinite(zz))
@@ -66,9 +68,12 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
         // (offset by one so an empty bucket, 0, is below every hit), .y of bucket J-1 keeps the
         // maximum of the complement, i.e. the minimum of bucket J
         if (w.prof) {
-            uint2 *prof = w.prof + (int64_t)e * nkeys + l * ax.n_phi;
+            uint2 *prof = w.prof + (int64_t)e * prof_event_entries(ax) + (int64_t)l * prof_stride(ax);
+            const int Jm = J == 0 ? ax.n_phi - 1 : (int)J - 1;
             atomicMax(&prof[J].x, __float_as_uint(f) + 1u);
-            atomicMax(&prof[J == 0 ? ax.n_phi - 1 : J - 1].y, ~__float_as_uint(f));
+            atomicMax(&prof[Jm].y, ~__float_as_uint(f));
+            if (J < kProfPad) atomicMax(&prof[J + ax.n_phi].x, __float_as_uint(f) + 1u);   // the repeated copy
+            if (Jm < kProfPad) atomicMax(&prof[Jm + ax.n_phi].y, ~__float_as_uint(f));
         }
         HotHit hh;
         hh.f = f;
@@ -100,14 +105,21 @@ __global__ void layer_info_kernel(Axes ax, Workspace w)
     li.hi = 0;
     li.r_bits = rmin;
     li.pad[0] = li.pad[1] = li.pad[2] = 0;
-    if (li.present && li.uniform) row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
-    w.info[l] = li;
     const int dirty = li.present && li.uniform && !(w.memo->valid[l] && w.memo->r_bits[l] == rmin);
-    w.memo->dirty[l] = dirty;
-    if (dirty) {
-        w.memo->r_bits[l] = rmin;
-        w.memo->valid[l] = 1;
+    if (li.present && li.uniform) {
+        if (dirty) {
+            row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
+            w.memo->r_bits[l] = rmin;
+            w.memo->lo[l] = li.lo;
+            w.memo->hi[l] = li.hi;
+            w.memo->valid[l] = 1;
+        } else {
+            li.lo = w.memo->lo[l];   // the same radius as before: its rows are memoised
+            li.hi = w.memo->hi[l];
+        }
     }
+    w.info[l] = li;
+    w.memo->dirty[l] = dirty;
 }
 
 // Per (layer, row) of a uniform layer whose radius changed: T = Nphi asin(x) / (2 pi) split into
@@ -141,47 +153,71 @@ __global__ void table_kernel(Axes ax, Workspace w)
     w.arc[q] = s;
 }
 
-// One CTA per event: exclusive scan of the bucket sizes (each thread owns a contiguous chunk),
-// and the vote count of uniform layers.
+// One CTA per event: exclusive scan of the bucket sizes, in tiles of kScanTile counts staged
+// through shared memory with coalesced loads and stores; each warp scans 32 consecutive counts
+// per round with shuffles (no bank conflicts).  Then the vote count of uniform layers.
+constexpr int kScanRounds = 8;
+constexpr int kScanTile = kScanThreads * kScanRounds;
+
 __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Workspace w)
 {
+    __shared__ int s_tile[kScanTile];
     __shared__ int s_warp[kScanThreads / 32];
+    __shared__ int s_total;
     const int e = blockIdx.x;
     const int nkeys = n_keys(ax);
     const int32_t *counts = w.counts + (int64_t)e * nkeys;
     int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int chunk = (nkeys + kScanThreads - 1) / kScanThreads;
-    const int k0 = min(nkeys, threadIdx.x * chunk), k1 = min(nkeys, k0 + chunk);
-    int sum = 0;
-    for (int k = k0; k < k1; ++k) sum += counts[k];
-    int incl = sum;
+    int carry = 0;
+    for (int base = 0; base < nkeys; base += kScanTile) {
+        const int n = min(kScanTile, nkeys - base);
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int wv = s_warp[lane];
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(0xFFFFFFFFu, wv, d);
-            if (lane >= d) wv += t;
+        for (int r = 0; r < kScanRounds; ++r) {
+            const int k = r * kScanThreads + threadIdx.x;
+            s_tile[k] = k < n ? counts[base + k] : 0;
         }
-        s_warp[lane] = wv;   // inclusive over warps
+        __syncthreads();
+        // warp w owns entries [w * 32 * kScanRounds, (w + 1) * 32 * kScanRounds)
+        int run = 0;
+#pragma unroll
+        for (int r = 0; r < kScanRounds; ++r) {
+            const int k = warp * 32 * kScanRounds + r * 32 + lane;
+            const int v = s_tile[k];
+            int incl = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            s_tile[k] = run + incl - v;
+            run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+        if (lane == 0) s_warp[warp] = run;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = s_warp[lane];
+            int incl = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            s_warp[lane] = incl - v;   // exclusive over warps
+            if (lane == 31) s_total = incl;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kScanRounds; ++r) {
+            const int k = r * kScanThreads + threadIdx.x;
+            if (k < n) offs[base + k] = carry + s_warp[k / (32 * kScanRounds)] + s_tile[k];
+        }
+        carry += s_total;
+        __syncthreads();
     }
-    __syncthreads();
-    int run = (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
-    for (int k = k0; k < k1; ++k) {
-        offs[k] = run;
-        run += counts[k];
-    }
-    const int total = s_warp[kScanThreads / 32 - 1];
     if (threadIdx.x == 0) {
-        offs[nkeys] = total;
-        w.stats[e].n_hits = (unsigned long long)total;
+        offs[nkeys] = carry;
+        w.stats[e].n_hits = (unsigned long long)carry;
     }
     __syncthreads();
     if (threadIdx.x < ax.n_layers) {
@@ -198,7 +234,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Worksp
 __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspace w)
 {
     const int nkeys = n_keys(ax);
-    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < w.n_hits_total;
+    const int64_t total = hit_total(w);
+    const HitInputs in = hit_inputs(w);
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total;
          h += (int64_t)gridDim.x * blockDim.x) {
         const int k = w.key[h];
         if (k < 0) continue;
@@ -209,7 +247,7 @@ __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspa
         const int l = (hh.jl >> 16) & 0xF;
         const LayerInfo li = w.info[l];
         int lo = li.lo, hi = li.hi;
-        const float rr = w.r[h];
+        const float rr = in.r[h];
         if (!li.uniform) {
             row_range(ax, sagitta_coef(ax, (double)rr), &lo, &hi);
             if (hi >= lo)
@@ -220,8 +258,8 @@ __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspa
         w.hot[pos] = hh;
         ColdHit ch;
         ch.r = rr;
-        ch.phi = w.phi[h];
-        ch.z = w.z[h];
+        ch.phi = in.phi[h];
+        ch.z = in.z[h];
         ch.idx = (int32_t)(h - start);
         w.cold[pos] = ch;
     }
@@ -242,11 +280,13 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
     const int nkeys = n_keys(ax);
     cudaError_t err;
     if ((err = cudaMemsetAsync(w.counts, 0, sizeof(int32_t) * (size_t)w.n_events * nkeys, stream))) return err;
-    if (w.prof && (err = cudaMemsetAsync(w.prof, 0, sizeof(uint2) * (size_t)w.n_events * nkeys, stream))) return err;
+    if (w.prof && (err = cudaMemsetAsync(w.prof, 0, sizeof(uint2) * (size_t)w.n_events * prof_event_entries(ax), stream)))
+        return err;
     if ((err = cudaMemsetAsync(w.stats, 0, sizeof(DevStats) * (size_t)w.n_events, stream))) return err;
+    if (w.counters && (err = cudaMemsetAsync(w.counters, 0, sizeof(BatchCounters), stream))) return err;
     if ((err = cudaMemsetAsync(w.radii->rmin, 0xFF, sizeof(w.radii->rmin), stream))) return err;
     if ((err = cudaMemsetAsync(w.radii->rmax, 0, sizeof(w.radii->rmax), stream))) return err;
-    const int g = grid_for(w.n_hits_total, kStageThreads);
+    const int g = grid_for(w.n_hits_total >= 0 ? w.n_hits_total : w.hit_capacity, kStageThreads);
     stage_count_kernel<<<g, kStageThreads, 0, stream>>>(ax, w);
     layer_info_kernel<<<1, 32, 0, stream>>>(ax, w);
     const int nt = ax.n_layers * ax.n_qpt;

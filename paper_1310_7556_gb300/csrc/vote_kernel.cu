@@ -8,10 +8,9 @@
 //    table's Nphi asin(x_i) / (2 pi) = I_i + g_i.  So layer l's bit of cell (i, j) is set exactly
 //    when bucket J' = (j + I_i) mod Nphi holds a hit with f >= g_i, or bucket J' + 1 holds one with
 //    f < g_i -- a test of the buckets' largest and smallest f, which the staging recorded.  The
-//    gather kernel evaluates that test for every (cell, layer) of a band of rows: no atomics,
-//    each accumulator word written once with a coalesced store, and the band's layer counts kept
-//    in shared memory for the peak search of the same CTA.  Same FP32 comparisons as the per-vote
-//    form, so the same accumulator bit for bit.
+//    gather kernel evaluates that test for every (cell, layer) of a tile: no atomics, each
+//    accumulator word written once with a coalesced 16-byte store.  Same FP32 comparisons as the
+//    per-vote form, so the same accumulator bit for bit.
 //
 // 2. Scatter (the paper's remedy, Sec. 6.1: shared-memory atomics instead of global ones).  One CTA
 //    per (event, tile of tile_qpt rows x tile_phi columns) in shared memory.  The CTA reads only the
@@ -24,9 +23,10 @@
 //    default (gather) mode this kernel handles only the layers whose radii differ and ORs its tile
 //    into the accumulator; in scatter mode it handles every layer and stores its tile.
 //
-// Peaks: candidates of each band of band_rows rows go to a band list in raster order (fused into
-// the gather kernel when every layer took the gather, else a standalone pass over the
-// accumulator); a per-event scan then concatenates the band lists into the raster-ordered list.
+// Peaks: candidates of each band of band_rows rows (one row by default) go to a band list in
+// raster order; a per-event scan then concatenates the band lists into the raster-ordered list.
+#include <algorithm>
+
 #include "hough_internal.cuh"
 
 namespace hough {
@@ -42,6 +42,8 @@ struct VoteParams {
 };
 
 constexpr int kMaxRanges = 2 * HOUGH_MAX_LAYERS;
+constexpr int kGatherThreads = 512;
+constexpr int kGatherRows = 4;
 constexpr int kCompactThreads = 1024;
 
 // Layers of the batch: bit l of *uniform_out is set when layer l takes the table path; bit l of
@@ -268,38 +270,71 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     if (threadIdx.x == 0 && s_refined) atomicAdd(&p.w.stats[e].refined_votes, s_refined);
 }
 
-// Gather: the accumulator rows of one band (plus a halo row on each side for the peak test) from
-// the per-bucket f extrema and the table; fused peak search when every layer is a table layer.
-template <bool POW2>
-__global__ void __launch_bounds__(kPeakThreads) gather_kernel(Axes ax, Workspace w)
+// Layer bits of the 8 cells j0..j0+7 of one row for one layer: cell j0 + c takes bucket entry
+// J1 + c (J1 = (j0 + I) mod Nphi) and is set when .x > gb or .y > ~gb.  The 8 entries are read
+// as 16-byte vectors from the even-aligned window [J1 & ~1, (J1 & ~1) + 10), which the repeated
+// buckets at the end of each layer keep from wrapping.
+__device__ __forceinline__ unsigned gather8(const uint2 *prof_l, int J1, unsigned gb)
 {
-    extern __shared__ __align__(16) unsigned char gsm[];
-    __shared__ unsigned s_general;
-    const int R = w.band_rows;
-    const int nb = n_bands(ax, R);
-    const int e = blockIdx.x / nb, band = blockIdx.x - e * nb;
-    const int L = ax.n_layers, nphi = ax.n_phi;
-    const int i0 = band * R;
-    const int nrows = min(R, ax.n_qpt - i0);
-    const int nkeys = L * nphi;
-    int *rowI = reinterpret_cast<int *>(gsm);                       // (R + 2) x 16
-    unsigned *rowG = reinterpret_cast<unsigned *>(rowI + (R + 2) * 16);
-    unsigned *rowMask = rowG + (R + 2) * 16;                        // R + 2 (+ padding to 4)
-    unsigned char *pc = reinterpret_cast<unsigned char *>(rowMask + ((R + 2 + 3) & ~3));
-
-    if (threadIdx.x < 32) {
-        unsigned u, g;
-        layer_masks(w, L, &u, &g);
-        if (threadIdx.x == 0) s_general = g;
+    const uint4 *v = reinterpret_cast<const uint4 *>(prof_l + (J1 & ~1));
+    uint4 q[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] = __ldg(&v[k]);
+    // entries e[0..9]: e[2k] = (q[k].x, q[k].y), e[2k+1] = (q[k].z, q[k].w)
+    const unsigned ngb = ~gb;
+    unsigned bits = 0u;
+    if (J1 & 1) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int t = c + 1;
+            const unsigned x = (t & 1) ? q[t >> 1].z : q[t >> 1].x;
+            const unsigned y = (t & 1) ? q[t >> 1].w : q[t >> 1].y;
+            bits |= (unsigned)((x > gb) | (y > ngb)) << c;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const unsigned x = (c & 1) ? q[c >> 1].z : q[c >> 1].x;
+            const unsigned y = (c & 1) ? q[c >> 1].w : q[c >> 1].y;
+            bits |= (unsigned)((x > gb) | (y > ngb)) << c;
+        }
     }
+    return bits;
+}
+
+// Gather: one tile of kGatherRows rows x `cols` columns of the accumulator from the per-bucket f
+// extrema and the table.  Each thread owns 8 consecutive cells of one row (one 16-byte store); the
+// layer loop is unrolled over the NL layers with every layer's loads issued unconditionally (a
+// layer that does not vote on the row reads its zero-shift window and is masked off), so all of a
+// thread's loads can be in flight at once.
+struct GatherParams {
+    Axes ax;
+    Workspace w;
+    int cols, col_tiles, tiles_per_event;
+};
+
+template <int NL>
+__global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherParams p)
+{
+    __shared__ int rowI[kGatherRows * 16];
+    __shared__ unsigned rowG[kGatherRows * 16];
+    __shared__ unsigned rowMask[kGatherRows];
+    const Axes &ax = p.ax;
+    const Workspace &w = p.w;
+    const int e = blockIdx.x / p.tiles_per_event;
+    const int t = blockIdx.x - e * p.tiles_per_event;
+    const int rt = t / p.col_tiles, ct = t - rt * p.col_tiles;
+    const int i0 = rt * kGatherRows, c0 = ct * p.cols;
+    const int nrows = min(kGatherRows, ax.n_qpt - i0);
+    const int L = ax.n_layers, nphi = ax.n_phi;
+
     // per (row, layer): the table entry and whether the layer votes on that row by the gather;
-    // the loop runs over whole warps so that every lane takes part in the ballot
-    const int nrl = (R + 2) * 16;
-    for (int q = threadIdx.x; q < ((nrl + 31) & ~31); q += kPeakThreads) {
-        const int rr = q >> 4, l = q & 15, i = i0 - 1 + rr;
+    // whole warps take part in the ballot
+    for (int q = threadIdx.x; q < kGatherRows * 16; q += kGatherThreads) {
+        const int rr = q >> 4, l = q & 15, i = i0 + rr;
         int I = 0;
         unsigned gb = 0u, valid = 0u;
-        if (q < nrl && l < L && rr < nrows + 2 && i >= 0 && i < ax.n_qpt) {
+        if (l < L && rr < nrows) {
             const LayerInfo li = w.info[l];
             if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
                 const TabEntry te = w.tab[l * ax.n_qpt + i];
@@ -309,76 +344,52 @@ __global__ void __launch_bounds__(kPeakThreads) gather_kernel(Axes ax, Workspace
             }
         }
         const unsigned m = __ballot_sync(0xFFFFFFFFu, valid) >> (threadIdx.x & 16);
-        if (q < nrl) {
-            rowI[q] = I;
-            rowG[q] = gb;
-            if ((threadIdx.x & 15) == 0) rowMask[rr] = m & 0xFFFFu;
-        }
+        rowI[q] = I;
+        rowG[q] = gb;
+        if ((threadIdx.x & 15) == 0) rowMask[rr] = m & 0xFFFFu;
     }
     __syncthreads();
-    const bool fused = s_general == 0u;
-    const uint2 *prof = w.prof + (int64_t)e * nkeys;
+    const uint2 *prof = w.prof + (int64_t)e * prof_event_entries(ax);
+    const int pstride = prof_stride(ax);
     uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
-    const int half = nphi >> 1;
-    const int nq = (nrows + 2) * half;
-    for (int q = threadIdx.x; q < nq; q += kPeakThreads) {
-        const int rr = q / half;
-        const int j = (q - rr * half) * 2;
-        const int i = i0 - 1 + rr;
-        uint32_t word = 0u;
-        if (i >= 0 && i < ax.n_qpt) {
-            unsigned vm = rowMask[rr];
-            while (vm) {
-                const int l = __ffs(vm) - 1;
-                vm &= vm - 1u;
-                const int I = rowI[rr * 16 + l];
-                const unsigned gb = rowG[rr * 16 + l];
-                int J1 = j + I;
-                int J2 = J1 + 1;
-                if (POW2) {
-                    J1 &= nphi - 1;
-                    J2 &= nphi - 1;
-                } else {
-                    J1 = wrap_col(J1, nphi);
-                    J2 = wrap_col(J2, nphi);
-                }
-                const uint2 a = __ldg(&prof[l * nphi + J1]);
-                const uint2 b = __ldg(&prof[l * nphi + J2]);
-                const unsigned b0 = (a.x > gb) | (a.y > ~gb);
-                const unsigned b1 = (b.x > gb) | (b.y > ~gb);
-                word |= (b0 << l) | (b1 << (l + 16));
-            }
-            if (rr >= 1 && rr <= nrows) *reinterpret_cast<uint32_t *>(M + (int64_t)i * nphi + j) = word;
+    const int per_row = p.cols >> 3;
+    const int nq = nrows * per_row;
+    for (int q = threadIdx.x; q < nq; q += kGatherThreads) {
+        const int rr = q / per_row;
+        const int j0 = c0 + (q - rr * per_row) * 8;
+        const unsigned vm = rowMask[rr];
+        const int *rI = rowI + rr * 16;
+        const unsigned *rG = rowG + rr * 16;
+        unsigned bits[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const int J1 = wrap_col(j0 + rI[l], nphi);
+            bits[l] = gather8(prof + (int64_t)l * pstride, J1, rG[l]) & (0u - ((vm >> l) & 1u));
         }
-        if (fused)
-            *reinterpret_cast<uint16_t *>(pc + rr * nphi + j) =
-                (uint16_t)(__popc(word & 0xFFFFu) | (__popc(word >> 16) << 8));
+        unsigned lo[4] = {0u, 0u, 0u, 0u}, hi[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                lo[k] |= ((bits[l] >> (2 * k)) & 1u) << l;
+                hi[k] |= ((bits[l] >> (2 * k + 1)) & 1u) << l;
+            }
+        }
+        *reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + j0) =
+            make_uint4(lo[0] | (hi[0] << 16), lo[1] | (hi[1] << 16), lo[2] | (hi[2] << 16), lo[3] | (hi[3] << 16));
     }
-    if (!fused) return;
-    __syncthreads();
-    uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
-    const int cnt = band_peak_search(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
-    if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
 }
 
-// Peak search of one band straight from the accumulator (when the gather did not fuse it).
-__global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w, int gather_mode)
+// Peak search of one band of band_rows rows from the accumulator (plus a halo row on each side).
+__global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w)
 {
     extern __shared__ __align__(16) unsigned char pc[];
-    __shared__ unsigned s_general;
     const int R = w.band_rows;
     const int nb = n_bands(ax, R);
     const int e = blockIdx.x / nb, band = blockIdx.x - e * nb;
     const int nphi = ax.n_phi;
     const int i0 = band * R;
     const int nrows = min(R, ax.n_qpt - i0);
-    if (threadIdx.x < 32) {
-        unsigned u, g;
-        layer_masks(w, ax.n_layers, &u, &g);
-        if (threadIdx.x == 0) s_general = g;
-    }
-    __syncthreads();
-    if (gather_mode && s_general == 0u) return;   // the gather kernel found this band's peaks
     const uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
     const int v8 = nphi >> 3;
     for (int q = threadIdx.x; q < (nrows + 2) * v8; q += kPeakThreads) {
@@ -397,7 +408,7 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
     }
     __syncthreads();
     uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
-    const int cnt = band_peak_search(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
+    const int cnt = band_peak_search<kPeakThreads>(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
     if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
 }
 
@@ -463,6 +474,59 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
     }
 }
 
+// One CTA: the first flattened candidate index of every event (kept candidates only), so that
+// later kernels can spread all events' candidates over the whole device.
+__global__ void __launch_bounds__(kCompactThreads) cand_scan_kernel(Workspace w)
+{
+    __shared__ int s_warp[kCompactThreads / 32];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < w.n_events; base += kCompactThreads) {
+        const int e = base + threadIdx.x;
+        const int v = e < w.n_events ? (int)min((unsigned)w.max_cand, w.stats[e].n_candidates) : 0;
+        int incl = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int sv = s_warp[lane];
+            int si = sv;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, si, d);
+                if (lane >= d) si += t;
+            }
+            s_warp[lane] = si - sv;
+        }
+        __syncthreads();
+        const int excl = s_carry + s_warp[warp] + incl - v;
+        if (e < w.n_events) w.cand_base[e] = excl;
+        __syncthreads();
+        if (threadIdx.x == kCompactThreads - 1) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        w.cand_base[w.n_events] = s_carry;
+        w.counters->total_cands = (unsigned)s_carry;
+    }
+}
+
+// All events' candidate lists, concatenated in event order into `out` (positions from cand_base).
+__global__ void pack_candidates_kernel(Workspace w, hough_candidate *out)
+{
+    const int total = w.cand_base[w.n_events];
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < total; f += gridDim.x * blockDim.x) {
+        const int e = upper_index(w.cand_base, w.n_events, f);
+        out[f] = w.cands[(int64_t)e * w.max_cand + (f - w.cand_base[e])];
+    }
+}
+
 template <int TPB, bool GENERAL_ONLY>
 cudaError_t launch_scatter(const VoteParams &p, size_t smem, int grid, cudaStream_t stream)
 {
@@ -493,14 +557,8 @@ size_t vote_smem_bytes(const Axes &ax, const Tiling &t)
            (size_t)t.tile_qpt * sizeof(float);
 }
 
-size_t gather_smem_bytes(const Axes &ax, int band_rows)
-{
-    const int rows = band_rows + 2;
-    return (size_t)rows * 16 * 8 + (size_t)((rows + 3) & ~3) * 4 + (size_t)rows * ax.n_phi;
-}
 
-cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
-                        cudaStream_t stream)
+static VoteParams vote_params(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps)
 {
     VoteParams p;
     p.ax = ax;
@@ -511,34 +569,98 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
     p.tiles_per_event = ((ax.n_qpt + t.tile_qpt - 1) / t.tile_qpt) * p.n_spans;
     p.s32 = (float)(ax.n_phi * kInvTwoPi);
     p.refine_eps = refine_eps;
-    const size_t smem = vote_smem_bytes(ax, t);
-    const int grid = w.n_events * p.tiles_per_event;
-    if (t.vote_mode == HOUGH_VOTE_SCATTER) return launch_scatter_tpb<false>(p, t.threads, smem, grid, stream);
-    // gather every table layer, then let the scatter kernel add the layers whose radii differ
-    const size_t gsmem = gather_smem_bytes(ax, w.band_rows);
-    const int gblocks = w.n_events * n_bands(ax, w.band_rows);
-    const bool pow2 = (ax.n_phi & (ax.n_phi - 1)) == 0;
-    cudaError_t err;
-    if (pow2) {
-        if ((err = cudaFuncSetAttribute(gather_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem))) return err;
-        gather_kernel<true><<<gblocks, kPeakThreads, gsmem, stream>>>(ax, w);
-    } else {
-        if ((err = cudaFuncSetAttribute(gather_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem))) return err;
-        gather_kernel<false><<<gblocks, kPeakThreads, gsmem, stream>>>(ax, w);
-    }
-    if ((err = cudaGetLastError())) return err;
-    return launch_scatter_tpb<true>(p, t.threads, smem, grid, stream);
+    return p;
 }
 
-cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
+template <int NL>
+cudaError_t launch_gather_nl(const GatherParams &p, int blocks, cudaStream_t stream)
+{
+    gather_kernel<NL><<<blocks, kGatherThreads, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const Axes &ax, const Workspace &w, cudaStream_t stream)
+{
+    GatherParams p;
+    p.ax = ax;
+    p.w = w;
+    // the widest tile of at most 8 * kGatherThreads / kGatherRows cells per row that divides Nphi
+    int cols = std::min(ax.n_phi, 8 * kGatherThreads / kGatherRows);
+    cols -= cols % 64;
+    while (ax.n_phi % cols) cols -= 64;
+    p.cols = cols;
+    p.col_tiles = ax.n_phi / cols;
+    p.tiles_per_event = ((ax.n_qpt + kGatherRows - 1) / kGatherRows) * p.col_tiles;
+    const int blocks = w.n_events * p.tiles_per_event;
+    switch (ax.n_layers) {
+    case 1: return launch_gather_nl<1>(p, blocks, stream);
+    case 2: return launch_gather_nl<2>(p, blocks, stream);
+    case 3: return launch_gather_nl<3>(p, blocks, stream);
+    case 4: return launch_gather_nl<4>(p, blocks, stream);
+    case 5: return launch_gather_nl<5>(p, blocks, stream);
+    case 6: return launch_gather_nl<6>(p, blocks, stream);
+    case 7: return launch_gather_nl<7>(p, blocks, stream);
+    case 8: return launch_gather_nl<8>(p, blocks, stream);
+    case 9: return launch_gather_nl<9>(p, blocks, stream);
+    case 10: return launch_gather_nl<10>(p, blocks, stream);
+    case 11: return launch_gather_nl<11>(p, blocks, stream);
+    case 12: return launch_gather_nl<12>(p, blocks, stream);
+    case 13: return launch_gather_nl<13>(p, blocks, stream);
+    case 14: return launch_gather_nl<14>(p, blocks, stream);
+    case 15: return launch_gather_nl<15>(p, blocks, stream);
+    default: return launch_gather_nl<16>(p, blocks, stream);
+    }
+}
+
+cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps, bool general_only,
+                           cudaStream_t stream)
+{
+    const VoteParams p = vote_params(ax, w, t, refine_eps);
+    const size_t smem = vote_smem_bytes(ax, t);
+    const int grid = w.n_events * p.tiles_per_event;
+    return general_only ? launch_scatter_tpb<true>(p, t.threads, smem, grid, stream)
+                        : launch_scatter_tpb<false>(p, t.threads, smem, grid, stream);
+}
+
+cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
+                        cudaStream_t stream)
+{
+    if (t.vote_mode == HOUGH_VOTE_SCATTER) return launch_scatter(ax, w, t, refine_eps, false, stream);
+    // gather every table layer, then let the scatter kernel add the layers whose radii differ
+    cudaError_t err = launch_gather(ax, w, stream);
+    if (err) return err;
+    return launch_scatter(ax, w, t, refine_eps, true, stream);
+}
+
+cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
 {
     const int nb = n_bands(ax, w.band_rows);
     const size_t smem = (size_t)(w.band_rows + 2) * ax.n_phi;
     cudaError_t err;
     if ((err = cudaFuncSetAttribute(peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return err;
-    peaks_kernel<<<w.n_events * nb, kPeakThreads, smem, stream>>>(ax, w, t.vote_mode == HOUGH_VOTE_GATHER ? 1 : 0);
-    compact_kernel<<<w.n_events, kCompactThreads, 0, stream>>>(ax, w);
+    peaks_kernel<<<w.n_events * nb, kPeakThreads, smem, stream>>>(ax, w);
     return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream)
+{
+    compact_kernel<<<w.n_events, kCompactThreads, 0, stream>>>(ax, w);
+    cand_scan_kernel<<<1, kCompactThreads, 0, stream>>>(w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream)
+{
+    (void)ax;
+    pack_candidates_kernel<<<1216, 256, 0, stream>>>(w, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
+{
+    cudaError_t err = launch_band_peaks(ax, w, t, stream);
+    if (err) return err;
+    return launch_compact(ax, w, stream);
 }
 
 }  // namespace hough
