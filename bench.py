@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--only", choices=["all", "plain", "batched"], default="all",
+                    help="run one part only (for profiling); the default runs everything")
     return ap.parse_args()
 
 
@@ -175,50 +177,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse_args()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    import torch
-    import torch.distributed as dist
+class Env:
+    """Torch, the optional process group, the library binding and the device of this rank."""
 
-    from paper_1310_7556_gb300 import binding
+    def __init__(self):
+        import torch
+        import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    binding.load()
+        from paper_1310_7556_gb300 import binding
+        self.torch, self.dist, self.binding = torch, dist, binding
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        if self.world > 1:
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        binding.load()
+        self.stream = torch.cuda.current_stream(self.dev)
+        self.flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=self.dev)
 
-    w = eg.WORKLOADS[args.workload]
-    ev = w.event(rank)     # each rank its own event
-    n = ev.n_hits
-    tens = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
-    ctx = binding.HoughContext(w.geometry, w.binning, max_hits=n, max_candidates=1 << 18,
-                               max_members=1 << 23, device=local)
-    ctx.enable_timing(True)
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    def max_over_ranks(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        t = self.torch.tensor([x], device=self.dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+        self.torch.cuda.synchronize()
+
+
+def measure_plain(env, args, ctx, tens, n):
+    """One event per step through hough_vote, hough_peaks, hough_stage2 on device-resident hits."""
+    torch, binding, stream = env.torch, env.binding, env.stream
 
     def step():
         ctx.vote(*tens, n_hits=n, where=binding.DEVICE, stream=stream)
         ctx.peaks(stream=stream)
         ctx.stage2(stream=stream)
-
-    # measured shared-atomic ceiling (conflict-free 32-lane atomicOr), before anything is timed
-    smem_peak = binding.smem_or_throughput(local, 0, 30.0)
-    smem_peak_rand = binding.smem_or_throughput(local, 1, 30.0)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    st = ctx.stats()
-    votes = int(st.votes)
-    n_cand = int(st.n_candidates)
 
     def timed_steps(steps):
         """K steps, each after an L2 flush, bracketed by CUDA events on the launching stream."""
@@ -226,7 +225,7 @@ def main():
         e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         lib_t = []
         for k in range(steps):
-            flush.zero_()
+            env.flush.zero_()
             e0[k].record(stream)
             step()
             e1[k].record(stream)
@@ -234,25 +233,21 @@ def main():
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in zip(e0, e1)], lib_t
 
-    if world > 1:
-        dist.barrier()
+    for _ in range(max(3, args.warmup)):
+        step()
     torch.cuda.synchronize()
+    st = ctx.stats()
+    env.barrier()
     launches0 = binding.kernel_launches()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(env.local) as clocks:
         step_ms, lib_t = timed_steps(args.steps)
     launches = binding.kernel_launches() - launches0
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    events_per_s = world * args.steps / (total_ms * 1e-3)
-    ms_per_step = total_ms / args.steps
-
-    stage_means = {k: statistics.mean(t[k] for t in lib_t) for k in lib_t[0]}
-    vote_ms = stage_means["vote_ms"]
-
+    total_ms = env.max_over_ranks(sum(step_ms))
+    env.barrier()
+    out = {"events_per_s": env.world * args.steps / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
+           "stage_ms": {k: statistics.mean(t[k] for t in lib_t) for k in lib_t[0]},
+           "votes": int(st.votes), "candidates": int(st.n_candidates), "members": int(st.n_members),
+           "launches": int(launches), "clocks": clocks.summary()}
     # the same steps with the shared-atomic scatter vote (the paper's GPU design) for comparison
     tiling0 = ctx.get_tiling()
     ctx.set_tiling(vote_mode=binding.VOTE_SCATTER)
@@ -260,123 +255,154 @@ def main():
         step()
     sc_ms, sc_t = timed_steps(min(args.steps, 20))
     ctx.set_tiling(**tiling0)
-    scatter_vote_ms = statistics.mean(t["vote_ms"] for t in sc_t)
-    scatter = {"events_per_s": len(sc_ms) / (sum(sc_ms) * 1e-3), "ms_per_step": statistics.mean(sc_ms),
-               "vote_ms": scatter_vote_ms, "peaks_ms": statistics.mean(t["peaks_ms"] for t in sc_t),
-               "votes_per_s_in_vote_kernel": votes / (scatter_vote_ms * 1e-3),
-               "smem_atomic_frac": votes / (scatter_vote_ms * 1e-3) / smem_peak}
+    out["scatter"] = {"events_per_s": len(sc_ms) / (sum(sc_ms) * 1e-3), "ms_per_step": statistics.mean(sc_ms),
+                      "vote_ms": statistics.mean(t["vote_ms"] for t in sc_t),
+                      "peaks_ms": statistics.mean(t["peaks_ms"] for t in sc_t)}
+    return out
 
-    # batched: the batch workload (events of 100-10,000 tracks plus 0.5-2x noise), one replayed graph
-    # per step over all events
+
+def measure_batched(env, args):
+    """The batch workload (events of 100-10,000 tracks plus 0.5-2x noise hits): one replayed CUDA graph per
+    step over all events of the batch."""
+    torch, binding, stream = env.torch, env.binding, env.stream
     wb = eg.WORKLOADS["batch_256"]
-    bev = [wb.event(rank * args.batch_events + i) for i in range(args.batch_events)]
+    bev = [wb.event(env.rank * args.batch_events + i) for i in range(args.batch_events)]
     bhs = np.zeros(len(bev) + 1, dtype=np.int64)
     bhs[1:] = np.cumsum([e.n_hits for e in bev])
-    bdev = [torch.from_numpy(np.concatenate([getattr(e, k) for e in bev])).to(dev) for k in ("r", "phi", "z", "layer")]
+    bdev = [torch.from_numpy(np.concatenate([getattr(e, k) for e in bev])).to(env.dev) for k in ("r", "phi", "z", "layer")]
     batch = binding.HoughBatch(wb.geometry, wb.binning, max_events=len(bev), max_hits=int(bhs[-1]),
-                               max_candidates=1 << 18, max_members=1 << 21, device=local)
+                               max_candidates=1 << 18, max_members=1 << 21, device=env.local)
     for _ in range(3):
         batch.run(*bdev, bhs, where=binding.DEVICE, stream=stream)
     torch.cuda.synchronize()
     bstats = [batch.stats(e) for e in range(len(bev))]
-    b_votes = sum(int(st.votes) for st in bstats)
-    b_cands = sum(int(st.n_candidates) for st in bstats)
-    b_members = sum(int(st.n_members) for st in bstats)
     b0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
     b1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
-    blaunch0 = binding.kernel_launches()
+    env.barrier()
+    launch0 = binding.kernel_launches()
     for k in range(args.batch_steps):
-        flush.zero_()
+        env.flush.zero_()
         b0[k].record(stream)
         batch.run(*bdev, bhs, where=binding.DEVICE, stream=stream)
         b1[k].record(stream)
     torch.cuda.synchronize()
-    blaunches = binding.kernel_launches() - blaunch0
-    batch_ms = [a.elapsed_time(b) for a, b in zip(b0, b1)]
-    b_total = sum(batch_ms)
-    if world > 1:
-        t = torch.tensor([b_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        b_total = float(t.item())
-    batched = {"events_per_s": world * len(bev) * args.batch_steps / (b_total * 1e-3),
-               "votes_per_s": world * b_votes * args.batch_steps / (b_total * 1e-3),
-               "ms_per_batch": b_total / args.batch_steps, "events_per_batch": len(bev), "hits_per_batch": int(bhs[-1]),
-               "votes_per_batch": b_votes, "candidates_per_batch": b_cands, "members_per_batch": b_members,
-               "steps": args.batch_steps, "gpu_launches": int(blaunches),
-               "mode": "one CUDA-graph replay per batch; kernels span all events"}
+    launches = binding.kernel_launches() - launch0
+    total = env.max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(b0, b1)))
+    votes = sum(int(st.votes) for st in bstats)
+    out = {"events_per_s": env.world * len(bev) * args.batch_steps / (total * 1e-3),
+           "votes_per_s": env.world * votes * args.batch_steps / (total * 1e-3),
+           "ms_per_batch": total / args.batch_steps, "events_per_batch": len(bev), "hits_per_batch": int(bhs[-1]),
+           "votes_per_batch": votes, "candidates_per_batch": sum(int(st.n_candidates) for st in bstats),
+           "members_per_batch": sum(int(st.n_members) for st in bstats),
+           "stage2_votes_per_batch": sum(int(st.stage2_votes) for st in bstats),
+           "steps": args.batch_steps, "gpu_launches": int(launches),
+           "mode": "one CUDA-graph replay per batch; kernels span all events"}
     batch.close()
-    del bdev
+    return out
 
-    # end to end through hough_process from pinned host buffers
+
+def measure_e2e(env, args, ctx, ev):
+    """hough_process from pinned host buffers: hits to the device, the path, candidates back."""
+    torch, stream = env.torch, env.stream
+    n = ev.n_hits
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (ev.r, ev.phi, ev.z, ev.layer)]
-    out = np.zeros(1 << 18, dtype=binding.CANDIDATE_DTYPE)
+    out = np.zeros(1 << 18, dtype=env.binding.CANDIDATE_DTYPE)
     for _ in range(3):
         ctx.process(*pinned, n_hits=n, out=out, stream=stream)
-    if world > 1:
-        dist.barrier()
+    env.barrier()
     e2e_s = []
+    got = None
     for _ in range(args.steps):
-        flush.zero_()
+        env.flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         got = ctx.process(*pinned, n_hits=n, out=out, stream=stream)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * args.steps / e2e_total
-    h2d = n * (4 + 4 + 4 + 1)
-    d2h = len(got) * 32 + 160
+    total = env.max_over_ranks(sum(e2e_s))
+    return {"value": env.world * args.steps / total, "unit": "events/s", "h2d_bytes_per_step": n * (4 + 4 + 4 + 1),
+            "d2h_bytes_per_step": len(got) * 32 + 160}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    env = Env()
+    binding = env.binding
+    if args.only == "batched":
+        out = measure_batched(env, args)
+        if env.rank == 0:
+            print(json.dumps({"metric": METRIC, "part": "batched", **out}), flush=True)
+        return
+
+    w = eg.WORKLOADS[args.workload]
+    ev = w.event(env.rank)     # each rank its own event
+    n = ev.n_hits
+    tens = [env.torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
+    ctx = binding.HoughContext(w.geometry, w.binning, max_hits=n, max_candidates=1 << 18,
+                               max_members=1 << 23, device=env.local)
+    ctx.enable_timing(True)
+    # measured shared-atomic ceiling (conflict-free 32-lane atomicOr), before anything is timed
+    smem_peak = binding.smem_or_throughput(env.local, 0, 30.0)
+    smem_peak_rand = binding.smem_or_throughput(env.local, 1, 30.0)
+    plain = measure_plain(env, args, ctx, tens, n)
+    if args.only == "plain":
+        if env.rank == 0:
+            print(json.dumps({"metric": METRIC, "part": "plain", **plain}), flush=True)
+        return
+    batched = measure_batched(env, args)
+    e2e = measure_e2e(env, args, ctx, ev)
 
     peaks, peaks_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # vote kernel: one shared atomicOr per vote (before the duplicate skip) is the algorithmic work
-    achieved_atomics = votes / (vote_ms * 1e-3)
+    votes = plain["votes"]
+    vote_ms = plain["stage_ms"]["vote_ms"]
+    scatter = plain.pop("scatter")
+    scatter["smem_atomic_frac"] = votes / (scatter["vote_ms"] * 1e-3) / smem_peak
+    scatter["votes_per_s_in_vote_kernel"] = votes / (scatter["vote_ms"] * 1e-3)
     # algorithmic bytes of the vote launch: 13 B per hit read (r, phi, z, layer) + 2 B per cell written
     vote_bytes = 13 * n + 2 * w.binning.n_qpt * w.binning.n_phi
-
     line = {
         "metric": METRIC,
-        "value": events_per_s,
+        "value": plain["events_per_s"],
         "unit": "events/s",
-        "n_gpus": world,
+        "n_gpus": env.world,
         "steps": args.steps,
         "warmup": max(3, args.warmup),
-        "ms_per_step": ms_per_step,
+        "ms_per_step": plain["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": n, "votes_per_event": votes,
-                   "candidates_per_event": n_cand, "mode": "plain: one event per step, one launch sequence",
-                   "l2": "flushed before every timed step (256 MiB write)",
-                   "tiling": ctx.get_tiling()},
-        "votes_per_s": votes * events_per_s,
-        "stage_ms": stage_means,
+                   "candidates_per_event": plain["candidates"], "members_per_event": plain["members"],
+                   "mode": "plain: one event per step, one launch sequence",
+                   "l2": "flushed before every timed step (256 MiB write)", "tiling": ctx.get_tiling()},
+        "votes_per_s": votes * plain["events_per_s"],
+        "stage_ms": plain["stage_ms"],
         "scatter_mode": scatter,
         "batched": batched,
-        "roofline": {"bound": "smem_atomic", "kernel": "vote_kernel", "achieved": achieved_atomics / 1e9,
-                     "peak": smem_peak / 1e9, "unit": "Gatomic/s", "frac": achieved_atomics / smem_peak,
+        "roofline": {"bound": "smem_atomic", "kernel": "vote_kernel", "achieved": votes / (vote_ms * 1e-3) / 1e9,
+                     "peak": smem_peak / 1e9, "unit": "Gatomic/s", "frac": votes / (vote_ms * 1e-3) / smem_peak,
                      "peak_kind": "measured by hough_microbench_smem_or (conflict-free 32-lane atomicOr)",
                      "peak_random_pattern": smem_peak_rand / 1e9,
                      "traffic": None,
                      "hbm": {"achieved": vote_bytes / (vote_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": vote_bytes / (vote_ms * 1e-3) / 1e9 / hbm_peak,
                              "peak_kind": f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)"}},
-        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": plain["launches"],
+        "clocks": plain["clocks"],
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     ctx.close()
-    if rank == 0:
+    if env.rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    if env.world > 1:
+        env.dist.destroy_process_group()
 
 
 if __name__ == "__main__":

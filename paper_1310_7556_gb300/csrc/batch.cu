@@ -131,7 +131,7 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     A(b->alloc(&w.cands, E * C));
     A(b->alloc(&w.mem_pool, E * Mm));
     A(b->alloc(&w.mem_start, E * C)); A(b->alloc(&w.mem_count, E * C));
-    A(b->alloc(&w.small_list, E * C)); A(b->alloc(&w.large_list, E * C));
+    A(b->alloc(&w.large_list, E * C));
     A(b->alloc(&w.cand_base, E + 1)); A(b->alloc(&w.counters, 1));
     A(b->alloc(&w.stats, E));
     A(b->alloc(&b->packed, E * C));

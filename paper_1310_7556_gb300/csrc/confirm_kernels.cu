@@ -2,16 +2,18 @@
 // expensive computations"): for each candidate, the hits whose stage-1 vote fell in its cell
 // (membership) and their vote in a (cot theta, z0) grid (stage 2), in one kernel.
 //
-// Work scales with a candidate's votes, not with the size of the stage-2 grid: every warp owns a
-// private n_cot x n_z0 grid of layer masks in shared memory, clear between candidates.  A vote pass
-// ORs each (member, cot row) vote into it with a shared atomic; a collect pass revisits the same
-// votes, takes each touched word with atomicExch (reading and clearing it in one step) and keeps
-// the cell with the most layers, the lowest row-major index on ties.
+// Work scales with a candidate's votes, not with the size of the stage-2 grid.  A CTA that confirms
+// a large candidate keeps an n_cot x n_z0 grid of layer masks in shared memory, clear between
+// candidates: a vote pass ORs each (member, cot row) vote into it with a shared atomic; a collect
+// pass revisits the same votes, takes each touched word with atomicExch (reading and clearing it in
+// one step) and keeps the cell with the most layers, the lowest row-major index on ties.
 //
 // Events of moderate occupancy produce tens of thousands of candidates with a dozen members each,
 // saturated events a few hundred with fifty or more.  So a first kernel (a warp per candidate)
-// enumerates each candidate's members once, into the member pool, and files the candidate as
-// small (at most kSmallMembers members: stage 2 by one warp) or large (stage 2 by a whole CTA).
+// enumerates each candidate's members once, into the member pool, and finishes stage 2 itself when
+// the candidate has at most kSmallMembers members (one member per lane, cot rows in turn, lanes of
+// equal z0 bin grouped by __match_any_sync); larger candidates are filed for a CTA each, which
+// votes into a shared-memory grid as described above.
 //
 // Membership: only layers present in the candidate's mask can hold members.  For a table layer
 // the vote inverts exactly -- a hit of bucket J votes into column j on row i when
@@ -89,54 +91,97 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
     return sc;
 }
 
-// Members of candidate (i, j) enumerated by one warp in the fixed order.  Returns their number;
-// stores the staged position of each member of rank r in [lo, lo + cap) in pos[r - lo], and, when
-// pool is given, in pool[r] for r < pool_n.
+// Per-warp scratch of the enumeration: the candidate's (up to two per layer) bucket ranges in the
+// fixed order (layer ascending, range 0 before range 1), with their exclusive prefix.
+struct SegTable {
+    int start[2 * HOUGH_MAX_LAYERS];
+    int pre[2 * HOUGH_MAX_LAYERS + 1];
+    float g[HOUGH_MAX_LAYERS];
+    unsigned char kind[2 * HOUGH_MAX_LAYERS];   // 0: table side f >= g, 1: table side f < g, 2: per-vote test
+};
+
+// Members of candidate (i, j) enumerated by one warp in the fixed order (layer, bucket, position).
+// Lanes first find every layer's bucket ranges in parallel, then test the flattened union of their
+// hits together.  Returns the number of members; stores the staged position of the member of rank
+// r in [lo, lo + cap) in pos[r - lo], and, when pool is given, in pool[r] for r < pool_n.
 __device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t *offs, const HotHit *hot,
                               const ColdHit *cold, uint32_t mask, int i, int j, float s32, float refine_eps,
-                              int lo, int cap, int *pos, int32_t *pool, int pool_n)
+                              int lo, int cap, int *pos, int32_t *pool, int pool_n, SegTable &seg)
 {
     const int lane = threadIdx.x & 31;
+    // lane l < 16: layer l's ranges
+    int st0 = 0, len0 = 0, st1 = 0, len1 = 0;
+    unsigned char k0 = 0, k1 = 0;
+    if (lane < HOUGH_MAX_LAYERS && lane < ax.n_layers && ((mask >> lane) & 1u)) {
+        const LayerScan sc = layer_scan(ax, w, offs, lane, i, j, s32);
+        if (sc.nr >= 1) { st0 = sc.st[0]; len0 = sc.en[0] - sc.st[0]; }
+        if (sc.nr >= 2) { st1 = sc.st[1]; len1 = sc.en[1] - sc.st[1]; }
+        k0 = sc.table ? 0 : 2;
+        k1 = sc.table ? 1 : 2;
+        seg.g[lane] = sc.g;
+    }
+    const int tot = len0 + len1;
+    int incl = tot;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane < HOUGH_MAX_LAYERS) {
+        const int base = incl - tot;
+        seg.start[2 * lane] = st0;
+        seg.start[2 * lane + 1] = st1;
+        seg.pre[2 * lane] = base;
+        seg.pre[2 * lane + 1] = base + len0;
+        seg.kind[2 * lane] = k0;
+        seg.kind[2 * lane + 1] = k1;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (lane == 0) seg.pre[2 * HOUGH_MAX_LAYERS] = total;
+    __syncwarp();
     int count = 0;
-    while (mask) {
-        const int l = __ffs(mask) - 1;
-        mask &= mask - 1u;
-        if (l >= ax.n_layers) break;
-        const LayerScan sc = layer_scan(ax, w, offs, l, i, j, s32);
-        for (int q = 0; q < sc.nr; ++q) {
-            for (int base = sc.st[q]; base < sc.en[q]; base += 32) {
-                const int p = base + lane;
-                bool mem = false;
-                if (p < sc.en[q]) {
-                    const HotHit hh = hot[p];
-                    if (sc.table) {
-                        mem = q == 0 ? !(hh.f < sc.g) : (hh.f < sc.g);
-                    } else {
-                        const int rlo = (int)(hh.rows & 0xFFFFu), rhi = (int)(hh.rows >> 16);
-                        if (i >= rlo && i <= rhi) {
-                            const float x = fminf(fmaxf(hh.c * w.kq32[i], -1.f), 1.f);
-                            const float vq = fmaf(-asinf(x), s32, hh.f);
-                            const float fl = floorf(vq);
-                            const float d = vq - fl;
-                            int jj = (int)(hh.jl & 0xFFFFu) + (int)fl;
-                            if (d < refine_eps || d > 1.f - refine_eps || fabsf(x) > kRefineXLim) {
-                                const ColdHit ch = cold[p];
-                                jj = exact_bin(ax, (double)ch.phi, __dmul_rn(sagitta_coef(ax, (double)ch.r), qpt_centre(ax, i)));
-                            }
-                            mem = wrap_col(jj, ax.n_phi) == j;
-                        }
+    for (int base = 0; base < total; base += 32) {
+        const int v = base + lane;
+        bool mem = false;
+        int p = 0;
+        if (v < total) {
+            // the segment holding flattened index v: the last q with pre[q] <= v
+            int q = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (q + step < 2 * HOUGH_MAX_LAYERS && seg.pre[q + step] <= v) q += step;
+            p = seg.start[q] + (v - seg.pre[q]);
+            const HotHit hh = hot[p];
+            const int kind = seg.kind[q];
+            if (kind == 0) {
+                mem = !(hh.f < seg.g[q >> 1]);
+            } else if (kind == 1) {
+                mem = hh.f < seg.g[q >> 1];
+            } else {
+                const int rlo = (int)(hh.rows & 0xFFFFu), rhi = (int)(hh.rows >> 16);
+                if (i >= rlo && i <= rhi) {
+                    const float x = fminf(fmaxf(hh.c * w.kq32[i], -1.f), 1.f);
+                    const float vq = fmaf(-asinf(x), s32, hh.f);
+                    const float fl = floorf(vq);
+                    const float d = vq - fl;
+                    int jj = (int)(hh.jl & 0xFFFFu) + (int)fl;
+                    if (d < refine_eps || d > 1.f - refine_eps || fabsf(x) > kRefineXLim) {
+                        const ColdHit ch = cold[p];
+                        jj = exact_bin(ax, (double)ch.phi, __dmul_rn(sagitta_coef(ax, (double)ch.r), qpt_centre(ax, i)));
                     }
+                    mem = wrap_col(jj, ax.n_phi) == j;
                 }
-                const unsigned ball = __ballot_sync(0xFFFFFFFFu, mem);
-                if (mem) {
-                    const int r = count + __popc(ball & ((1u << lane) - 1u));
-                    if (r >= lo && r < lo + cap) pos[r - lo] = p;
-                    if (pool && r < pool_n) pool[r] = p;
-                }
-                count += __popc(ball);
             }
         }
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, mem);
+        if (mem) {
+            const int r = count + __popc(ball & ((1u << lane) - 1u));
+            if (r >= lo && r < lo + cap) pos[r - lo] = p;
+            if (pool && r < pool_n) pool[r] = p;
+        }
+        count += __popc(ball);
     }
+    __syncwarp();
     return count;
 }
 
@@ -191,6 +236,25 @@ __device__ __forceinline__ int stage2_bin(const Axes &ax, const Workspace &w, co
         nz = (wv < -1.f || wv > (float)ax.n_z0 + 1.f) ? -1 : (int)fl;
     }
     return (nz >= 0 && nz < ax.n_z0) ? nz : -1;
+}
+
+// Cot rows [*lo, *hi] whose vote of the member can fall inside the z0 range: w(m) = a - (m - m_ref) b
+// is monotone in m, so the rows form one run; the bounds are widened by a row on each side and
+// every pair is still tested exactly by stage2_bin.
+__device__ __forceinline__ void member_rows(const Axes &ax, float a, float b, int mrl, int *lo, int *hi)
+{
+    const int mref = mrl & 0xFFFF;
+    const float top = (float)(ax.n_cot - 1);
+    if (!(b > 0.f)) {
+        const bool in = a > -1.f && a < (float)ax.n_z0 + 1.f;
+        *lo = in ? 0 : 1;
+        *hi = in ? ax.n_cot - 1 : 0;
+        return;
+    }
+    const float flo = floorf((float)mref + (a - (float)ax.n_z0) / b);
+    const float fhi = floorf((float)mref + a / b) + 1.f;
+    *lo = (int)fminf(fmaxf(flo, 0.f), top + 1.f);
+    *hi = (int)fminf(fmaxf(fhi, -1.f), top);
 }
 
 struct Best {
@@ -251,17 +315,76 @@ __device__ __forceinline__ hough_candidate finished(const Axes &ax, hough_candid
     return cd;
 }
 
-// Membership: one warp per candidate enumerates its members once, in the fixed order, straight into
-// the member pool, records the candidate's member count, and files the candidate under the small
-// or the large list for the stage-2 kernels.
-__global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, Workspace w, float s32, float refine_eps)
+// Per-warp scratch of the small-candidate stage 2.
+struct SmallStage2 {
+    int pos[kSmallMembers];
+    float a[kSmallMembers], b[kSmallMembers];
+    int mrl[kSmallMembers], mlo[kSmallMembers];
+    int start[kSmallMembers + 1];
+};
+
+// Stage 2 of a candidate with at most 32 members in the warp's private grid: lane q prepares member
+// q and its run of cot rows; the (member, row) pairs of all runs are then spread over the lanes for
+// the vote pass and again for the collect pass.
+__device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
+                                  SmallStage2 &sm, int n, int i, unsigned long long &votes)
 {
+    const int lane = threadIdx.x & 31;
+    int len = 0;
+    if (lane < n) {
+        int lo, hi;
+        member_rows(ax, sm.a[lane], sm.b[lane], sm.mrl[lane], &lo, &hi);
+        sm.mlo[lane] = lo;
+        len = max(0, hi - lo + 1);
+    }
+    int incl = len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane < kSmallMembers) sm.start[lane] = incl - len;
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (lane == 0) sm.start[kSmallMembers] = total;
+    __syncwarp();
+    Best best = {0u, 0u, 0u};
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int v = lane; v < total; v += 32) {
+            // the member whose run holds pair v: the last q with start[q] <= v
+            int q = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (q + step < n && sm.start[q + step] <= v) q += step;
+            const int m = sm.mlo[q] + (v - sm.start[q]);
+            stage2_pair(ax, w, cold, grid, sm.pos[q], i, sm.a[q], sm.b[q], sm.mrl[q], m, pass, votes, best);
+        }
+        __syncwarp();
+    }
+    return best;
+}
+
+// Membership and, for candidates of at most kSmallMembers members, stage 2: one warp per candidate
+// over all events' candidates.  Members go once, in the fixed order, to the member pool; a larger
+// candidate is filed for the CTA stage-2 kernel.
+__global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, Workspace w, float s32, float refine_eps,
+                                                                        int grid_words)
+{
+    extern __shared__ __align__(16) unsigned char smem_m[];
     __shared__ int s_pos[kConfirmWarpsMax][kMemberCap];
+    __shared__ SegTable s_seg[kConfirmWarpsMax];
+    __shared__ SmallStage2 s_small[kConfirmWarpsMax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     int *pos = s_pos[warp];
+    SegTable &seg = s_seg[warp];
+    SmallStage2 &sm = s_small[warp];
+    uint32_t *grid = reinterpret_cast<uint32_t *>(smem_m) + warp * grid_words;   // warp-private, clear
+    for (int q = lane; q < grid_words; q += 32) grid[q] = 0u;
+    __syncwarp();
     const int nkeys = ax.n_layers * ax.n_phi;
     const int total = (int)w.counters->total_cands;
+    const double zscale = __ddiv_rn((double)ax.n_z0, __dsub_rn(ax.z0_max, ax.z0_min));
+    const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
     for (int f = blockIdx.x * nwarps + warp; f < total; f += gridDim.x * nwarps) {
         const int e = upper_index(w.cand_base, w.n_events, f);
         const int c = f - w.cand_base[e];
@@ -272,8 +395,9 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
         int32_t *pool = w.mem_pool + (int64_t)e * w.max_members;
         hough_candidate *cands = w.cands + (int64_t)e * w.max_cand;
         const hough_candidate cd = cands[c];
-        const int n = warp_enumerate(ax, w, offs, hot, cold, cd.mask, (int)cd.iq, (int)cd.jphi, s32, refine_eps, 0,
-                                     kMemberCap, pos, nullptr, 0);
+        const int i = (int)cd.iq;
+        const int n = warp_enumerate(ax, w, offs, hot, cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, 0,
+                                     kMemberCap, pos, nullptr, 0, seg);
         int base = 0, written = 0;
         if (lane == 0) {
             const unsigned b = n ? atomicAdd(&w.stats[e].pool_used, (unsigned)n) : 0u;
@@ -282,38 +406,37 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
             written = n ? (int)max(0LL, min((long long)n, room)) : 0;
             w.mem_start[(int64_t)e * w.max_cand + c] = base;
             w.mem_count[(int64_t)e * w.max_cand + c] = written;
-            cands[c].n_members = (uint32_t)n;
             if (n) atomicAdd(&w.stats[e].n_members, (unsigned)n);
-            int2 *list = n <= kSmallMembers ? w.small_list : w.large_list;
-            unsigned *cnt = n <= kSmallMembers ? &w.counters->n_small : &w.counters->n_large;
-            list[atomicAdd(cnt, 1u)] = make_int2(e, c);
+            if (n > kSmallMembers) {
+                cands[c].n_members = (uint32_t)n;
+                w.large_list[atomicAdd(&w.counters->n_large, 1u)] = make_int2(e, c);
+            }
         }
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         written = __shfl_sync(0xFFFFFFFFu, written, 0);
-        __syncwarp();
         if (n <= kMemberCap) {
             for (int q = lane; q < written; q += 32) pool[base + q] = pos[q];
         } else if (written > 0) {
-            warp_enumerate(ax, w, offs, hot, cold, cd.mask, (int)cd.iq, (int)cd.jphi, s32, refine_eps, 0, 0, pos,
-                           pool + base, written);
+            warp_enumerate(ax, w, offs, hot, cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, 0, 0, pos, pool + base,
+                           written, seg);
+        }
+        if (n <= kSmallMembers) {
+            if (lane < n) {
+                sm.pos[lane] = pos[lane];
+                member_coefficients(ax, w, hot, cold, pos[lane], i, zscale, t0, &sm.a[lane], &sm.b[lane], &sm.mrl[lane]);
+            }
+            __syncwarp();
+            unsigned long long votes = 0;
+            Best best = warp_stage2_small(ax, w, cold, grid, sm, n, i, votes);
+            warp_best(best);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
+            if (lane == 0) {
+                cands[c] = finished(ax, cd, n, written, best);
+                if (votes) atomicAdd(&w.stats[e].stage2_votes, votes);
+            }
         }
         __syncwarp();
-    }
-}
-
-// Members [lo, lo + nm) of candidate c into pos: from the pool when all of them were stored there,
-// else re-enumerated (only when max_members was exceeded).  Called by one warp.
-__device__ __forceinline__ void load_members(const Axes &ax, const Workspace &w, const int32_t *offs, const HotHit *hot,
-                                             const ColdHit *cold, const int32_t *pool, const hough_candidate &cd,
-                                             int base, int written, int n, int lo, int nm, int cap, float s32,
-                                             float refine_eps, int *pos)
-{
-    const int lane = threadIdx.x & 31;
-    if (written == n) {
-        for (int q = lane; q < nm; q += 32) pos[q] = pool[base + lo + q];
-    } else {
-        warp_enumerate(ax, w, offs, hot, cold, cd.mask, (int)cd.iq, (int)cd.jphi, s32, refine_eps, lo, cap, pos,
-                       nullptr, 0);
     }
 }
 
@@ -340,56 +463,6 @@ __device__ __forceinline__ Stage2Ctx stage2_ctx(const Axes &ax, const Workspace 
     return x;
 }
 
-// Stage 2 of the small candidates: one warp each, in the warp's private grid.
-__global__ void __launch_bounds__(kConfirmWarpsMax * 32) stage2_small_kernel(Axes ax, Workspace w, float s32,
-                                                                              float refine_eps, int grid_words)
-{
-    extern __shared__ __align__(16) unsigned char smem2[];
-    __shared__ int s_pos[kConfirmWarpsMax][kSmallMembers];
-    __shared__ float s_a[kConfirmWarpsMax][kSmallMembers], s_b[kConfirmWarpsMax][kSmallMembers];
-    __shared__ int s_mrl[kConfirmWarpsMax][kSmallMembers];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    uint32_t *grid = reinterpret_cast<uint32_t *>(smem2) + warp * grid_words;
-    int *pos = s_pos[warp];
-    float *ma = s_a[warp], *mb = s_b[warp];
-    int *mrl = s_mrl[warp];
-    const int nsmall = (int)w.counters->n_small;
-    if (blockIdx.x * nwarps >= nsmall) return;
-    for (int q = lane; q < grid_words; q += 32) grid[q] = 0u;
-    __syncwarp();
-    const int ncot = ax.n_cot;
-    for (int idx = blockIdx.x * nwarps + warp; idx < nsmall; idx += gridDim.x * nwarps) {
-        unsigned long long votes = 0;
-        const int2 ec = w.small_list[idx];
-        const int e = ec.x, c = ec.y;
-        const Stage2Ctx x = stage2_ctx(ax, w, e);
-        const hough_candidate cd = x.cands[c];
-        const int i = (int)cd.iq, n = (int)cd.n_members;
-        const int base = w.mem_start[(int64_t)e * w.max_cand + c], written = w.mem_count[(int64_t)e * w.max_cand + c];
-        load_members(ax, w, x.offs, x.hot, x.cold, x.pool, cd, base, written, n, 0, n, kSmallMembers, s32, refine_eps,
-                     pos);
-        __syncwarp();
-        if (lane < n) member_coefficients(ax, w, x.hot, x.cold, pos[lane], i, x.zscale, x.t0, &ma[lane], &mb[lane], &mrl[lane]);
-        __syncwarp();
-        Best best = {0u, 0u, 0u};
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int q = 0; q < n; ++q) {
-                const float a = ma[q], b = mb[q];
-                const int r = mrl[q], p = pos[q];
-                for (int m = lane; m < ncot; m += 32) stage2_pair(ax, w, x.cold, grid, p, i, a, b, r, m, pass, votes, best);
-            }
-            __syncwarp();
-        }
-        warp_best(best);
-        if (lane == 0) x.cands[c] = finished(ax, cd, n, written, best);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
-        if (lane == 0 && votes) atomicAdd(&w.stats[e].stage2_votes, votes);
-        __syncwarp();
-    }
-}
-
 // Stage 2 of the large candidates: one CTA each, members in chunks of kLargeChunk.
 __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(Axes ax, Workspace w, float s32,
                                                                                  float refine_eps)
@@ -398,7 +471,9 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(
     __shared__ int s_pos[kLargeChunk];
     __shared__ float s_a[kLargeChunk], s_b[kLargeChunk];
     __shared__ int s_mrl[kLargeChunk];
+    __shared__ int s_mlo[kLargeChunk], s_len[kLargeChunk], s_start[kLargeChunk + 1];
     __shared__ Best s_best[kConfirmWarpsMax];
+    __shared__ SegTable s_seg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     uint32_t *grid = reinterpret_cast<uint32_t *>(smem2);
@@ -427,17 +502,46 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(
                         for (int q = threadIdx.x; q < nm; q += blockDim.x) s_pos[q] = x.pool[base + lo + q];
                     } else if (warp == 0) {
                         warp_enumerate(ax, w, x.offs, x.hot, x.cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, lo,
-                                       kLargeChunk, s_pos, nullptr, 0);
+                                       kLargeChunk, s_pos, nullptr, 0, s_seg);
                     }
                     __syncthreads();
-                    for (int q = threadIdx.x; q < nm; q += blockDim.x)
+                    for (int q = threadIdx.x; q < nm; q += blockDim.x) {
                         member_coefficients(ax, w, x.hot, x.cold, s_pos[q], i, x.zscale, x.t0, &s_a[q], &s_b[q], &s_mrl[q]);
+                        int lo, hi;
+                        member_rows(ax, s_a[q], s_b[q], s_mrl[q], &lo, &hi);
+                        s_mlo[q] = lo;
+                        s_len[q] = max(0, hi - lo + 1);
+                    }
+                    __syncthreads();
+                    // exclusive scan of the runs' lengths (one thread per chunk slot strided over the CTA)
+                    if (warp == 0) {
+                        int carry = 0;
+                        for (int base = 0; base < nm; base += 32) {
+                            const int q = base + lane;
+                            const int v = q < nm ? s_len[q] : 0;
+                            int inc = v;
+#pragma unroll
+                            for (int d = 1; d < 32; d <<= 1) {
+                                const int t = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+                                if (lane >= d) inc += t;
+                            }
+                            if (q < nm) s_start[q] = carry + inc - v;
+                            carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+                        }
+                        if (lane == 0) s_start[nm] = carry;
+                    }
                     __syncthreads();
                 }
-                // (member, cot row) pairs spread over the CTA
-                for (int pq = threadIdx.x; pq < nm * ncot; pq += blockDim.x) {
-                    const int q = pq / ncot, m = pq - q * ncot;
-                    stage2_pair(ax, w, x.cold, grid, s_pos[q], i, s_a[q], s_b[q], s_mrl[q], m, pass, votes, best);
+                // (member, cot row) pairs of the chunk's runs, spread over the CTA
+                const int npairs = s_start[nm];
+                for (int v = threadIdx.x; v < npairs; v += blockDim.x) {
+                    int qlo = 0, qhi = nm - 1;
+                    while (qlo < qhi) {
+                        const int mid = (qlo + qhi + 1) >> 1;
+                        if (s_start[mid] <= v) qlo = mid; else qhi = mid - 1;
+                    }
+                    const int m = s_mlo[qlo] + (v - s_start[qlo]);
+                    stage2_pair(ax, w, x.cold, grid, s_pos[qlo], i, s_a[qlo], s_b[qlo], s_mrl[qlo], m, pass, votes, best);
                 }
                 __syncthreads();
             }
@@ -469,32 +573,23 @@ __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total
 
 int confirm_grid_words(const Axes &ax) { return (((ax.n_cot * ax.n_z0 + 1) >> 1) + 3) & ~3; }
 
-int small_warps(const Axes &ax)
-{
-    const size_t per_warp = (size_t)confirm_grid_words(ax) * 4;
-    int wpc = (int)((160u << 10) / per_warp);
-    return max(1, min(kConfirmWarpsMax, wpc));
-}
 
 }  // namespace
 
-size_t stage2_smem_bytes(const Axes &ax) { return (size_t)small_warps(ax) * confirm_grid_words(ax) * 4; }
+size_t stage2_smem_bytes(const Axes &ax) { return (size_t)confirm_grid_words(ax) * 4; }
 
 cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream)
 {
     const float s32 = (float)(ax.n_phi * kInvTwoPi);
     // the number of candidates is known on the device only: persistent grids sized for the device,
     // each warp or CTA striding over the flattened (event, candidate) work
-    member_kernel<<<4 * sms, kConfirmWarpsMax * 32, 0, stream>>>(ax, w, s32, refine_eps);
-    cudaError_t err;
-    const int nw = small_warps(ax);
-    const size_t small_smem = stage2_smem_bytes(ax);
-    if ((err = cudaFuncSetAttribute(stage2_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem)))
-        return err;
-    stage2_small_kernel<<<2 * sms, nw * 32, small_smem, stream>>>(ax, w, s32, refine_eps, confirm_grid_words(ax));
     const size_t large_smem = (size_t)confirm_grid_words(ax) * 4;
-    if ((err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem)))
-        return err;
+    const size_t member_smem = kConfirmWarpsMax * large_smem;
+    cudaError_t err = cudaFuncSetAttribute(member_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)member_smem);
+    if (err) return err;
+    member_kernel<<<4 * sms, kConfirmWarpsMax * 32, member_smem, stream>>>(ax, w, s32, refine_eps, confirm_grid_words(ax));
+    err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem);
+    if (err) return err;
     stage2_large_kernel<<<4 * sms, kConfirmWarpsMax * 32, large_smem, stream>>>(ax, w, s32, refine_eps);
     return cudaGetLastError();
 }

@@ -320,7 +320,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&w.band_cands, band_list_entries_impl(ax)));
     A(c->alloc(&w.band_counts, n_bands(ax, 1))); A(c->alloc(&w.band_offs, n_bands(ax, 1)));
     A(c->alloc(&w.mem_start, w.max_cand)); A(c->alloc(&w.mem_count, w.max_cand));
-    A(c->alloc(&w.small_list, w.max_cand)); A(c->alloc(&w.large_list, w.max_cand));
+    A(c->alloc(&w.large_list, w.max_cand));
     A(c->alloc(&w.cand_base, 2)); A(c->alloc(&w.counters, 1));
     A(c->alloc(&w.mem_pool, w.max_members)); A(c->alloc(&c->mem_idx, w.max_members));
     A(c->alloc(&w.stats, 1));

@@ -102,7 +102,8 @@ struct HitInputs {
 // Counters of a whole batch.
 struct BatchCounters {
     unsigned int total_cands;      // candidates kept over all events
-    unsigned int n_small, n_large; // entries of the stage-2 work lists
+    unsigned int n_large;          // entries of the CTA stage-2 work list
+    unsigned int pad0;
     unsigned int pad;
 };
 
@@ -136,7 +137,6 @@ struct Workspace {
     int32_t *mem_pool;            // n_events * max_members: event-local staged positions
     int32_t *mem_start;           // n_events * max_cand
     int32_t *mem_count;           // n_events * max_cand: entries written to the pool
-    int2 *small_list;             // n_events * max_cand (event, candidate): for the warp stage-2 kernel
     int2 *large_list;             // n_events * max_cand (event, candidate): for the CTA stage-2 kernel
     int32_t *cand_base;           // n_events + 1: first flattened candidate index of each event
     BatchCounters *counters;
@@ -214,7 +214,7 @@ void note_launches(uint64_t n);
 constexpr int kStageLaunches = 5;
 constexpr int kVoteLaunches = 2;
 constexpr int kPeakLaunches = 3;
-constexpr int kStage2Launches = 3;
+constexpr int kStage2Launches = 2;
 
 // Exact FP64 helpers used by the staging, table and refinement code.  They evaluate the
 // definitions in the order of the method's formulas with explicitly rounded operations,
