@@ -59,8 +59,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--only", choices=["all", "plain", "batched"], default="all",
+    ap.add_argument("--only", choices=["all", "plain", "batched", "served"], default="all",
                     help="run one part only (for profiling); the default runs everything")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="offered-load duration per served point")
+    ap.add_argument("--serve-loads", default=",".join(str(int(x)) for x in eg.SERVED_OFFERED_LOADS),
+                    help="offered loads (events/s), comma-separated")
     return ap.parse_args()
 
 
@@ -301,6 +304,121 @@ def measure_batched(env, args):
     return out
 
 
+def _percentiles(lat_ms):
+    if not lat_ms:
+        return {"p50_ms": None, "p99_ms": None, "p999_ms": None, "max_ms": None}
+    a = np.sort(np.asarray(lat_ms))
+    q = lambda p: float(a[min(len(a) - 1, int(math.ceil(p * len(a))) - 1)])
+    return {"p50_ms": q(0.50), "p99_ms": q(0.99), "p999_ms": q(0.999), "max_ms": float(a[-1])}
+
+
+def drive_server(env, srv, pool, rate, seconds, seed):
+    """Offer a Poisson stream of `rate` events/s for `seconds` to a server: a submitter thread
+    submits each event at its scheduled arrival (latency counts from that time, so a late
+    submission is charged to the server), a consumer thread polls every admitted ticket."""
+    import collections
+    binding = env.binding
+    n = max(1, int(rate * seconds))
+    arrivals = eg.poisson_arrivals(rate, n, seed)
+    admitted = collections.deque()
+    lat_ms, batch_sizes, statuses = [], [], collections.Counter()
+    done_ns = []
+    state = {"finished": False, "dropped": 0, "late_ns": []}
+    start = time.monotonic_ns() + 50_000_000
+    at = (start + arrivals * 1e9).astype(np.int64)
+
+    def submitter():
+        for i in range(n):
+            a = int(at[i])
+            now = time.monotonic_ns()
+            if a - now > 300_000:
+                time.sleep((a - now - 200_000) * 1e-9)
+            while time.monotonic_ns() < a:
+                pass
+            ev = pool[i % len(pool)]
+            state["late_ns"].append(time.monotonic_ns() - a)
+            t = srv.submit(ev[0], ev[1], ev[2], ev[3], ev[0].shape[0], arrival_ns=a)
+            if t is None:
+                state["dropped"] += 1
+            else:
+                admitted.append(t)
+        state["finished"] = True
+
+    def consumer():
+        while True:
+            if admitted:
+                t = admitted.popleft()
+                _, res = srv.poll(t, timeout_us=60_000_000, candidates=False,
+                                  allow=(binding.EDEVICE, binding.ENOMEM, binding.ETIMEDOUT))
+                statuses[int(res.status)] += 1
+                lat_ms.append((res.done_ns - res.arrival_ns) * 1e-6)
+                batch_sizes.append(res.batch_events)
+                done_ns.append(res.done_ns)
+            elif state["finished"]:
+                break
+            else:
+                time.sleep(50e-6)
+
+    st0 = srv.stats()
+    threads = [threading.Thread(target=submitter), threading.Thread(target=consumer)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    st1 = srv.stats()
+    span_s = (max(done_ns) - start) * 1e-9 if done_ns else float("nan")
+    out = {"offered_ev_s": rate, "seconds": seconds, "offered": n, "admitted": len(lat_ms),
+           "dropped": state["dropped"], "dropped_frac": state["dropped"] / n,
+           "completed_ev_s": len(lat_ms) / span_s if done_ns else 0.0,
+           **_percentiles(lat_ms),
+           "mean_batch_events": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+           "max_in_flight": int(st1.max_in_flight), "launches": int(st1.launches - st0.launches),
+           "submit_late_p99_us": float(np.percentile(state["late_ns"], 99)) * 1e-3,
+           "statuses": {str(k): v for k, v in statuses.items()}}
+    return out
+
+
+def measure_served(env, args):
+    """Trigger-style serving of batch-workload events arriving as Poisson streams: continuous
+    batching (events admitted while others run join the next launch; up to two launches overlap on
+    the device) against one launch per event through the same admission and lanes."""
+    import sys as _sys
+    binding = env.binding
+    _sys.setswitchinterval(1e-4)
+    wb = eg.WORKLOADS["batch_256"]
+    pool_events = [wb.event(1000 + env.rank * 64 + i) for i in range(64)]
+    pool = [tuple(np.ascontiguousarray(getattr(e, k)) for k in ("r", "phi", "z", "layer")) for e in pool_events]
+    max_event_hits = max(e.n_hits for e in pool_events)
+    loads = [float(x) for x in args.serve_loads.split(",") if x]
+    modes = {"continuous_batching": dict(lanes=3, max_in_flight=2, max_batch_events=64,
+                                         max_batch_hits=max(64 * 60_000, max_event_hits)),
+             "one_launch_per_event": dict(lanes=2, max_in_flight=1, max_batch_events=1,
+                                          max_batch_hits=max_event_hits)}
+    out = {"workload": "Poisson arrivals of batch-workload events (100-10,000 helices + 0.5-2x noise hits each; "
+                       "a pool of 64 seeded events reused cyclically)",
+           "latency": "result on the host minus scheduled arrival",
+           "memory_budget_bytes": 48 << 30}
+    launch0 = binding.kernel_launches()
+    for name, cfg in modes.items():
+        srv = binding.HoughServer(wb.geometry, wb.binning, max_candidates=1 << 17, max_members=1 << 21,
+                                  memory_budget=48 << 30, lane_timeout_us=30_000_000, device=env.local, **cfg)
+        # warm: one of each pool event through the server
+        for e in pool[:8]:
+            t = None
+            while t is None:
+                t = srv.submit(e[0], e[1], e[2], e[3], e[0].shape[0])
+            srv.poll(t, timeout_us=60_000_000, candidates=False)
+        res = []
+        for k, rate in enumerate(loads):
+            res.append(drive_server(env, srv, pool, rate, args.serve_seconds, seed=77 + k))
+        st = srv.stats()
+        out[name] = {"config": {**cfg, "lanes_in_service": int(st.lanes), "device_bytes": int(st.device_bytes)},
+                     "loads": res}
+        srv.close()
+    out["gpu_launches"] = int(binding.kernel_launches() - launch0)
+    return out
+
+
 def measure_e2e(env, args, ctx, ev):
     """hough_process from pinned host buffers: hits to the device, the path, candidates back."""
     torch, stream = env.torch, env.stream
@@ -330,10 +448,10 @@ def main():
         return
     env = Env()
     binding = env.binding
-    if args.only == "batched":
-        out = measure_batched(env, args)
+    if args.only in ("batched", "served"):
+        out = measure_batched(env, args) if args.only == "batched" else measure_served(env, args)
         if env.rank == 0:
-            print(json.dumps({"metric": METRIC, "part": "batched", **out}), flush=True)
+            print(json.dumps({"metric": METRIC, "part": args.only, **out}), flush=True)
         return
 
     w = eg.WORKLOADS[args.workload]
@@ -353,6 +471,7 @@ def main():
         return
     batched = measure_batched(env, args)
     e2e = measure_e2e(env, args, ctx, ev)
+    served = measure_served(env, args)
 
     peaks, peaks_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -384,6 +503,7 @@ def main():
         "stage_ms": plain["stage_ms"],
         "scatter_mode": scatter,
         "batched": batched,
+        "served": served,
         "roofline": {"bound": "smem_atomic", "kernel": "vote_kernel", "achieved": votes / (vote_ms * 1e-3) / 1e9,
                      "peak": smem_peak / 1e9, "unit": "Gatomic/s", "frac": votes / (vote_ms * 1e-3) / smem_peak,
                      "peak_kind": "measured by hough_microbench_smem_or (conflict-free 32-lane atomicOr)",

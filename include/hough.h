@@ -309,6 +309,116 @@ int hough_batch_stats(hough_batch *batch, int32_t event, hough_stats *out, void 
 int hough_batch_accumulator(hough_batch *batch, int32_t event, uint16_t *out, int where, void *stream);
 
 /*
+ * Served mode: a trigger-style request loop with continuous batching (the paper runs events one at
+ * a time, Sec. 6-7; it has no serving loop).  Events are submitted one by one as they arrive; a
+ * dispatcher thread owned by the server launches whatever has been admitted as one batch (the
+ * hough_batch path: one replayed graph) as soon as fewer than max_in_flight batches are on the
+ * GPU, so events that arrive while others run join the next launch, and launches of different
+ * lanes overlap on the device, one stream each.  A lane is one batch's device buffers
+ * (accumulators, candidate lists, member pools for max_batch_events events, allocated once and
+ * kept resident) plus pinned host staging for its hits and results.  Lanes are created within
+ * memory_budget; admission is bounded by them: when the filling batch is full and no lane is free,
+ * a new event is refused with HOUGH_EBUSY (dead time), never queued without bound.
+ *
+ * Each event's result -- its candidate list in raster order with stage-2 fields, its vote count
+ * and device-side error bits -- is the same as hough_process gives for that event alone.
+ */
+typedef struct hough_serve_config {
+    int32_t lanes;             /* device batch slots: 0 = as many as memory_budget holds, at most 4; else >= 2 */
+    int32_t max_in_flight;     /* batches on the GPU at once: 0 = lanes - 1; else 1 .. lanes - 1 */
+    int32_t max_batch_events;  /* events per launch, >= 1 */
+    int32_t max_candidates;    /* candidates kept per event, >= 1 */
+    int64_t max_batch_hits;    /* hits per launch (and per event), 1 .. 2^31 - 1 */
+    int32_t max_members;       /* member hits kept per event, >= 1 */
+    int32_t reserved;          /* must be 0 */
+    int64_t memory_budget;     /* device bytes all lanes may hold; 0 = no budget */
+    int64_t lane_timeout_us;   /* watchdog: a launch not finished after this fails with HOUGH_ETIMEDOUT and
+                                  its lane is retired; 0 = no watchdog */
+} hough_serve_config;
+
+/* Per-event result of hough_serve_poll.  Times are CLOCK_MONOTONIC nanoseconds (hough_serve_clock_ns). */
+typedef struct hough_serve_result {
+    uint64_t ticket;
+    int64_t  arrival_ns;      /* as given to hough_serve_submit (or its submission time) */
+    int64_t  submit_ns;       /* when hough_serve_submit was entered */
+    int64_t  launch_ns;       /* when its batch was launched */
+    int64_t  done_ns;         /* when its result reached host memory */
+    int64_t  n_candidates;
+    uint64_t votes;           /* stage-1 votes cast by the event */
+    int32_t  status;          /* HOUGH_OK, HOUGH_EDEVICE (device_error set), HOUGH_ENOMEM, HOUGH_ETIMEDOUT, ... */
+    int32_t  batch_events;    /* events that shared its launch */
+    uint32_t device_error;    /* HOUGH_DEVERR_* bits */
+    uint32_t reserved;
+} hough_serve_result;
+
+/* Server counters (hough_serve_get_stats). */
+typedef struct hough_serve_stats {
+    int64_t submitted;          /* hough_serve_submit calls with valid arguments */
+    int64_t admitted;           /* events given a ticket */
+    int64_t rejected_busy;      /* refused with HOUGH_EBUSY */
+    int64_t rejected_invalid;   /* refused as malformed (bad layer, radius or coordinate) */
+    int64_t completed;          /* events whose result reached the host */
+    int64_t failed;             /* events finished with an error status */
+    int64_t launches;           /* batches launched */
+    int64_t launched_events;    /* events over all launches */
+    int64_t max_in_flight;      /* most batches on the GPU at once */
+    int64_t timeouts;           /* launches failed by the watchdog */
+    int64_t alloc_failures;     /* result-buffer allocations that failed */
+    int64_t retired_lanes;
+    int64_t lanes;              /* lanes in service */
+    int64_t in_flight;          /* batches on the GPU now */
+    int64_t pending_tickets;    /* tickets not yet polled */
+    int64_t device_bytes;       /* device memory held by the lanes */
+} hough_serve_stats;
+
+typedef struct hough_server hough_server;
+
+/* Host-side fault injection for tests (no GPU fault is ever made): */
+#define HOUGH_SERVE_FAULT_HOLD  1   /* launch nothing while on (a stalled dispatcher) */
+#define HOUGH_SERVE_FAULT_STALL 2   /* treat every in-flight lane as never finishing while on (a stalled stream) */
+#define HOUGH_SERVE_FAULT_ALLOC 3   /* the next result-buffer acquisition fails with HOUGH_ENOMEM */
+
+/*
+ * Create a server on `device`: allocates the lanes (HOUGH_ENOMEM when fewer than two, or fewer than
+ * `lanes`, fit the budget), captures every batch size's graph, and starts the dispatcher thread.
+ */
+int hough_serve_create(const hough_geometry *geometry, const hough_binning *binning,
+                       const hough_serve_config *config, int device, hough_server **out);
+
+/* Stop the dispatcher, wait for the GPU work in flight, and free everything (unpolled results are dropped). */
+void hough_serve_destroy(hough_server *server);
+
+/* The server's clock: CLOCK_MONOTONIC in nanoseconds. */
+int64_t hough_serve_clock_ns(void);
+
+/*
+ * Admit one event: its hits (host memory, n_hits entries; checked as hough_vote does, a malformed
+ * event returns that check's status and is counted in rejected_invalid) are copied into the
+ * filling batch's pinned staging before the call returns.  arrival_ns (hough_serve_clock_ns time;
+ * 0 = now) is the event's arrival for latency.  *ticket identifies it for hough_serve_poll.
+ * HOUGH_EBUSY when no lane can take it.  Thread-safe.
+ */
+int hough_serve_submit(hough_server *server, const float *r, const float *phi, const float *z,
+                       const uint8_t *layer, int64_t n_hits, int64_t arrival_ns, uint64_t *ticket);
+
+/*
+ * Wait up to timeout_us (>= 0) for the event `ticket`; then copy up to cap of its candidates to
+ * `out` (host), fill *result (may be NULL) and release the ticket.  Returns HOUGH_ETIMEDOUT (ticket
+ * kept) if it has not finished, the event's status if that is an error, HOUGH_ETRUNC when out is
+ * given and holds fewer than its candidates, else HOUGH_OK.  Thread-safe.
+ */
+int hough_serve_poll(hough_server *server, uint64_t ticket, hough_candidate *out, int64_t cap,
+                     hough_serve_result *result, int64_t timeout_us);
+
+/* Wait up to timeout_us until every admitted event has finished (HOUGH_ETIMEDOUT otherwise). */
+int hough_serve_drain(hough_server *server, int64_t timeout_us);
+
+int hough_serve_get_stats(hough_server *server, hough_serve_stats *out);
+
+/* Switch a host-side fault (HOUGH_SERVE_FAULT_*) on (on != 0) or off. */
+int hough_serve_inject(hough_server *server, int fault, int on);
+
+/*
  * Stage-1 vote of one event with no allocation at all.  The paper has no counterpart: this exists
  * for callers that may not allocate device memory while they run -- a trigger's real-time event
  * loop, where cudaMalloc and cudaFree can synchronise the whole device and take unbounded time, or

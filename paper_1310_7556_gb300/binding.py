@@ -72,6 +72,30 @@ class Tiling(ctypes.Structure):
 VOTE_GATHER, VOTE_SCATTER = 0, 1
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("max_batch_events", ctypes.c_int32),
+                ("max_candidates", ctypes.c_int32), ("max_batch_hits", ctypes.c_int64),
+                ("max_members", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("lane_timeout_us", ctypes.c_int64)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("arrival_ns", ctypes.c_int64), ("submit_ns", ctypes.c_int64),
+                ("launch_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("votes", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_events", ctypes.c_int32),
+                ("device_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "submitted", "admitted", "rejected_busy", "rejected_invalid", "completed", "failed", "launches",
+        "launched_events", "max_in_flight", "timeouts", "alloc_failures", "retired_lanes", "lanes", "in_flight",
+        "pending_tickets", "device_bytes")]
+
+
+SERVE_FAULT_HOLD, SERVE_FAULT_STALL, SERVE_FAULT_ALLOC = 1, 2, 3
+
+
 CANDIDATE_DTYPE = np.dtype([("iq", np.uint32), ("jphi", np.uint32), ("mask", np.uint32),
                             ("n_members", np.uint32), ("icot", np.uint32), ("jz0", np.uint32),
                             ("mask2", np.uint32), ("flags", np.uint32)])
@@ -111,6 +135,15 @@ _SIGNATURES = {
     "hough_batch_candidates": ([_P, _P, _I64, _P, ctypes.c_int, _P], ctypes.c_int),
     "hough_batch_stats": ([_P, _I32, ctypes.POINTER(Stats), _P], ctypes.c_int),
     "hough_batch_accumulator": ([_P, _I32, _P, ctypes.c_int, _P], ctypes.c_int),
+    "hough_serve_create": ([ctypes.POINTER(Geometry), ctypes.POINTER(Binning), ctypes.POINTER(ServeConfig),
+                            ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "hough_serve_destroy": ([_P], None),
+    "hough_serve_clock_ns": ([], ctypes.c_int64),
+    "hough_serve_submit": ([_P, _P, _P, _P, _P, _I64, _I64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "hough_serve_poll": ([_P, ctypes.c_uint64, _P, _I64, ctypes.POINTER(ServeResult), _I64], ctypes.c_int),
+    "hough_serve_drain": ([_P, _I64], ctypes.c_int),
+    "hough_serve_get_stats": ([_P, ctypes.POINTER(ServeStats)], ctypes.c_int),
+    "hough_serve_inject": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
 }
 
 
@@ -379,3 +412,79 @@ class HoughBatch:
         out = np.zeros((self.binning.n_qpt, self.binning.n_phi), dtype=np.uint16)
         _check(self._lib.hough_batch_accumulator(self._h, event, _ptr(out), HOST, _stream(stream)))
         return out
+
+
+def serve_clock_ns() -> int:
+    """The server's clock (CLOCK_MONOTONIC nanoseconds, the clock of time.monotonic_ns)."""
+    return int(load().hough_serve_clock_ns())
+
+
+class HoughServer:
+    """One hough_server: events submitted one by one, continuously batched onto the GPU by the
+    library's dispatcher thread, results polled per ticket."""
+
+    def __init__(self, geometry, binning, max_batch_events: int, max_batch_hits: int, lanes: int = 3,
+                 max_in_flight: int = 0, max_candidates: int = 1 << 17, max_members: int = 1 << 21,
+                 memory_budget: int = 0, lane_timeout_us: int = 0, device: int = 0):
+        lib = load()
+        self._lib = lib
+        g, b = make_geometry(geometry), make_binning(binning)
+        cfg = ServeConfig(lanes=lanes, max_in_flight=max_in_flight, max_batch_events=max_batch_events,
+                          max_candidates=max_candidates, max_batch_hits=max_batch_hits, max_members=max_members,
+                          reserved=0, memory_budget=memory_budget, lane_timeout_us=lane_timeout_us)
+        h = _P()
+        _check(lib.hough_serve_create(ctypes.byref(g), ctypes.byref(b), ctypes.byref(cfg), device, ctypes.byref(h)))
+        self._h = h
+        self.max_candidates = max_candidates
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hough_serve_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, r, phi, z, layer, n_hits=None, arrival_ns: int = 0):
+        """Ticket of the admitted event, or None when the server is busy (HOUGH_EBUSY).  Host arrays
+        must be float32 / uint8 and contiguous."""
+        n = r.shape[0] if n_hits is None else n_hits
+        t = ctypes.c_uint64(0)
+        rc = _check(self._lib.hough_serve_submit(self._h, _ptr(r), _ptr(phi), _ptr(z), _ptr(layer), int(n),
+                                                 int(arrival_ns), ctypes.byref(t)), allow=(EBUSY,))
+        return None if rc == EBUSY else int(t.value)
+
+    def submit_event(self, event, arrival_ns: int = 0):
+        return self.submit(event.r, event.phi, event.z, event.layer, event.n_hits, arrival_ns)
+
+    def poll(self, ticket: int, timeout_us: int = 10_000_000, candidates: bool = True, allow=()):
+        """(candidates or None, ServeResult) of a finished event; raises HoughError on timeout or an
+        error status unless that status is in `allow` (the result is then still returned)."""
+        res = ServeResult()
+        if candidates:
+            out = np.zeros(self.max_candidates, dtype=CANDIDATE_DTYPE)
+            rc = self._lib.hough_serve_poll(self._h, ticket, _ptr(out), out.shape[0], ctypes.byref(res),
+                                            int(timeout_us))
+        else:
+            out = None
+            rc = self._lib.hough_serve_poll(self._h, ticket, None, 0, ctypes.byref(res), int(timeout_us))
+        _check(rc, allow=allow)
+        if rc == ETIMEDOUT and res.ticket == 0:
+            return None, None
+        return (out[: res.n_candidates].copy() if out is not None else None), res
+
+    def drain(self, timeout_us: int = 60_000_000):
+        _check(self._lib.hough_serve_drain(self._h, int(timeout_us)))
+
+    def stats(self) -> ServeStats:
+        st = ServeStats()
+        _check(self._lib.hough_serve_get_stats(self._h, ctypes.byref(st)))
+        return st
+
+    def inject(self, fault: int, on: bool = True):
+        _check(self._lib.hough_serve_inject(self._h, int(fault), int(bool(on))))

@@ -15,9 +15,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhough.so")
 
-SOURCES = ["hough_api.cu", "stage_kernels.cu", "vote_kernel.cu", "confirm_kernels.cu", "microbench.cu", "static_vote.cu", "batch.cu"]
+SOURCES = ["hough_api.cu", "stage_kernels.cu", "vote_kernel.cu", "confirm_kernels.cu", "microbench.cu", "static_vote.cu", "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread", "-I" + INCLUDE]
 
 
 def nvcc() -> str:
@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(lambda so: compile_one(*so), zip(srcs, objs)))
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

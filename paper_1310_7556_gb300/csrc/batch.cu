@@ -48,6 +48,7 @@ struct hough_batch {
     std::map<int, cudaGraphExec_t> graphs;   // by batch size
     int n_events = 0;                        // of the last run
     bool ran = false;
+    size_t device_bytes = 0;                 // everything allocated above
 
     ~hough_batch()
     {
@@ -62,8 +63,12 @@ struct hough_batch {
     cudaError_t alloc(T **p, size_t count)
     {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-        if (e == cudaSuccess) allocations.push_back(q);
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e == cudaSuccess) {
+            allocations.push_back(q);
+            device_bytes += bytes;
+        }
         *p = static_cast<T *>(q);
         return e;
     }
@@ -177,8 +182,10 @@ int hough_batch_set_tiling(hough_batch *b, const hough_tiling *t)
     return HOUGH_OK;
 }
 
-int hough_batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
-                    const int64_t *hit_start, int32_t n_events, int where, void *stream)
+}  // extern "C"
+
+int hough::batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                     const int64_t *hit_start, int32_t n_events, int where, cudaStream_t stream, bool check_hits)
 {
     if (!b || !hit_start) return bfail(HOUGH_EINVAL, "batch and hit_start are required");
     if (n_events < 1 || n_events > b->limits.max_events) return bfail(HOUGH_ECAPACITY, "n_events outside 1..max_events");
@@ -190,10 +197,12 @@ int hough_batch_run(hough_batch *b, const float *r, const float *phi, const floa
     if (n > b->limits.max_hits) return bfail(HOUGH_ECAPACITY, "the batch has more hits than max_hits");
     if (n > 0 && (!r || !phi || !z || !layer)) return bfail(HOUGH_EINVAL, "hit arrays are required");
     BCU(cudaSetDevice(b->device), "cudaSetDevice failed");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStream_t s = stream;
     if (where == HOUGH_HOST) {
-        int rc = check_host_hits_for(b->ax, r, phi, z, layer, n);
-        if (rc) return rc;
+        if (check_hits) {
+            int rc = check_host_hits_for(b->ax, r, phi, z, layer, n);
+            if (rc) return rc;
+        }
         if (n > 0) {
             BCU(cudaMemcpyAsync(b->in_r, r, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy r failed");
             BCU(cudaMemcpyAsync(b->in_phi, phi, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy phi failed");
@@ -237,6 +246,43 @@ int hough_batch_run(hough_batch *b, const float *r, const float *phi, const floa
     b->n_events = n_events;
     b->ran = true;
     return HOUGH_OK;
+}
+
+// Enqueue the concatenation of the last run's candidates into the batch's device buffer and the
+// copy of the per-event offsets (int32, n_events + 1) to `offsets_host`; no synchronisation.
+int hough::batch_enqueue_offsets(hough_batch *b, int32_t *offsets_host, cudaStream_t s)
+{
+    BCU(launch_pack_candidates(b->ax, b->w, b->packed, s), "pack kernel failed");
+    note_launches(1);
+    BCU(cudaMemcpyAsync(offsets_host, b->w.cand_base, sizeof(int32_t) * (b->n_events + 1), cudaMemcpyDeviceToHost, s),
+        "copy offsets failed");
+    return HOUGH_OK;
+}
+
+// Enqueue the copy of the first n events' counters to `stats_host`; no synchronisation.
+int hough::batch_enqueue_stats(hough_batch *b, DevStats *stats_host, int n, cudaStream_t s)
+{
+    BCU(cudaMemcpyAsync(stats_host, b->w.stats, sizeof(DevStats) * n, cudaMemcpyDeviceToHost, s), "copy stats failed");
+    return HOUGH_OK;
+}
+
+size_t hough::batch_device_bytes(const hough_batch *b) { return b->device_bytes; }
+
+// Enqueue the copy of the first n packed candidates to `out_host`; no synchronisation.
+int hough::batch_enqueue_candidates(hough_batch *b, hough_candidate *out_host, int64_t n, cudaStream_t s)
+{
+    if (n > 0)
+        BCU(cudaMemcpyAsync(out_host, b->packed, sizeof(hough_candidate) * n, cudaMemcpyDeviceToHost, s),
+            "copy candidates failed");
+    return HOUGH_OK;
+}
+
+extern "C" {
+
+int hough_batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                    const int64_t *hit_start, int32_t n_events, int where, void *stream)
+{
+    return batch_run(b, r, phi, z, layer, hit_start, n_events, where, static_cast<cudaStream_t>(stream), true);
 }
 
 int hough_batch_candidates(hough_batch *b, hough_candidate *out, int64_t cap, int64_t *offsets, int where, void *stream)

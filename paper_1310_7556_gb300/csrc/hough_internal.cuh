@@ -206,6 +206,15 @@ int check_host_hits_for(const Axes &ax, const float *r, const float *phi, const 
                         int64_t n);
 void fill_stats(const DevStats &d, const LayerInfo *info, int n_layers, hough_stats *out);
 
+// Batch internals used by the server: a run with or without the host-side hit checks, and the
+// asynchronous result copies (offsets first, then exactly the candidates they announce).
+int batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
+              const int64_t *hit_start, int32_t n_events, int where, cudaStream_t stream, bool check_hits);
+int batch_enqueue_offsets(hough_batch *b, int32_t *offsets_host, cudaStream_t s);
+int batch_enqueue_candidates(hough_batch *b, hough_candidate *out_host, int64_t n, cudaStream_t s);
+int batch_enqueue_stats(hough_batch *b, DevStats *stats_host, int n, cudaStream_t s);
+size_t batch_device_bytes(const hough_batch *b);
+
 // Record a failure for hough_last_error (returns code), and count launches for hough_kernel_launches.
 int set_last_error(int code, const char *msg);
 void note_launches(uint64_t n);
