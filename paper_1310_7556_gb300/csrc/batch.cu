@@ -129,6 +129,7 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     A(b->alloc(&w.prof, (size_t)(E * prof_event_entries(ax))));
     A(b->alloc(&w.radii, 1)); A(b->alloc(&w.info, HOUGH_MAX_LAYERS)); A(b->alloc(&w.memo, 1));
     A(b->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(b->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
+    A(b->alloc(&w.zco, (size_t)ax.n_layers * ax.n_qpt));
     A(b->alloc(&w.kq32, ax.n_qpt));
     A(b->alloc(&w.M, (size_t)E * ax.n_qpt * ax.n_phi));
     A(b->alloc(&w.band_cands, (size_t)E * band_list_entries(ax)));

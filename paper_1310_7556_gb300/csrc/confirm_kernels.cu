@@ -27,6 +27,8 @@
 // w(m) = n_z0 (z - s t_m - z0_min) / (z0_max - z0_min) is linear in the cot row m; it is evaluated
 // in FP32 around the member's own crossing row m_ref, and a vote within kStage2Eps of a z0 edge is
 // recomputed in FP64 exactly as the definition reads.
+#include <atomic>
+
 #include "hough_internal.cuh"
 
 namespace hough {
@@ -203,13 +205,53 @@ __device__ __forceinline__ double exact_z0_coord(const Axes &ax, double z, doubl
     return __ddiv_rn(__dmul_rn((double)ax.n_z0, __dsub_rn(z0, ax.z0_min)), __dsub_rn(ax.z0_max, ax.z0_min));
 }
 
+// Error-free transformations of FP32 arithmetic (Knuth's two-sum, and the product with its
+// rounding error from one fused multiply-add): a + b = s + e and a b = p + e exactly.
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return make_float2(p, fmaf(a, b, -p));
+}
+
 // Stage-2 coefficients of one member at row i: z0 coordinate w(m) = a - (m - m_ref) b in FP32.
+// For a layer of one radius the per-row terms S = zscale s t_0 and B = zscale s dt come from the
+// table and w(m_ref) = zscale (z - z0_min) - S - m_ref B is formed in two-float arithmetic (about
+// 2^-44 relative before the final rounding), which keeps a within a few 1e-6 bins of the exact
+// value -- far inside the FP64 recheck window of stage2_bin.  Other layers take the FP64 route.
 __device__ __forceinline__ void member_coefficients(const Axes &ax, const Workspace &w, const HotHit *hot,
                                                     const ColdHit *cold, int p, int i, double zscale, double t0,
                                                     float *a_out, float *b_out, int *mrl_out)
 {
     const int l = (int)((hot[p].jl >> 16) & 0xFu);
     const ColdHit ch = cold[p];
+    if (w.info[l].uniform) {
+        const float4 zc = w.zco[l * ax.n_qpt + i];
+        // d = z - z0_min and Z = zscale d as two-float values
+        float2 d = two_sum(ch.z, -ax.zmin_hi);
+        d.y = __fsub_rn(d.y, ax.zmin_lo);
+        const float2 zp = two_prod(d.x, ax.zs_hi);
+        const float zlo = zp.y + d.x * ax.zs_lo + d.y * ax.zs_hi;
+        // A = Z - S
+        float2 A = two_sum(zp.x, -zc.x);
+        A.y = A.y + (zlo - zc.y);
+        int mref = 0;
+        if (zc.z > 0.f) mref = (int)fminf(fmaxf(rintf(__fdividef(A.x, zc.z)), 0.f), (float)(ax.n_cot - 1));
+        // a = A - m_ref B; m_ref B.hi is exact as a two-float product
+        const float fm = (float)mref;
+        const float2 q = two_prod(fm, zc.z);
+        *a_out = __fsub_rn(A.x, q.x) + (A.y - q.y - fm * zc.w);
+        *b_out = zc.z;
+        *mrl_out = mref | (l << 16);
+        return;
+    }
     const double s = member_arc(ax, w, l, i, ch.r);
     const double A = __dmul_rn(zscale, __dsub_rn(__dsub_rn((double)ch.z, ax.z0_min), __dmul_rn(s, t0)));
     const double B = __dmul_rn(zscale, __dmul_rn(s, ax.dt));
@@ -315,19 +357,27 @@ __device__ __forceinline__ hough_candidate finished(const Axes &ax, hough_candid
     return cd;
 }
 
-// Per-warp scratch of the small-candidate stage 2.
+// Per-warp scratch of the small-candidate stage 2 (member positions stay in the warp's position
+// buffer).
 struct SmallStage2 {
-    int pos[kSmallMembers];
     float a[kSmallMembers], b[kSmallMembers];
     int mrl[kSmallMembers], mlo[kSmallMembers];
     int start[kSmallMembers + 1];
+};
+
+// The enumeration table and the small stage 2 are never live at the same time: a warp fills the
+// latter only after its enumeration has finished (and synchronised), and enumerates again only
+// after its stage 2 has.
+union WarpScratch {
+    SegTable seg;
+    SmallStage2 small;
 };
 
 // Stage 2 of a candidate with at most 32 members in the warp's private grid: lane q prepares member
 // q and its run of cot rows; the (member, row) pairs of all runs are then spread over the lanes for
 // the vote pass and again for the collect pass.
 __device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
-                                  SmallStage2 &sm, int n, int i, unsigned long long &votes)
+                                  SmallStage2 &sm, const int *pos, int n, int i, unsigned long long &votes)
 {
     const int lane = threadIdx.x & 31;
     int len = 0;
@@ -356,7 +406,7 @@ __device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
             for (int step = 16; step > 0; step >>= 1)
                 if (q + step < n && sm.start[q + step] <= v) q += step;
             const int m = sm.mlo[q] + (v - sm.start[q]);
-            stage2_pair(ax, w, cold, grid, sm.pos[q], i, sm.a[q], sm.b[q], sm.mrl[q], m, pass, votes, best);
+            stage2_pair(ax, w, cold, grid, pos[q], i, sm.a[q], sm.b[q], sm.mrl[q], m, pass, votes, best);
         }
         __syncwarp();
     }
@@ -371,13 +421,12 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
 {
     extern __shared__ __align__(16) unsigned char smem_m[];
     __shared__ int s_pos[kConfirmWarpsMax][kMemberCap];
-    __shared__ SegTable s_seg[kConfirmWarpsMax];
-    __shared__ SmallStage2 s_small[kConfirmWarpsMax];
+    __shared__ WarpScratch s_scratch[kConfirmWarpsMax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     int *pos = s_pos[warp];
-    SegTable &seg = s_seg[warp];
-    SmallStage2 &sm = s_small[warp];
+    SegTable &seg = s_scratch[warp].seg;
+    SmallStage2 &sm = s_scratch[warp].small;
     uint32_t *grid = reinterpret_cast<uint32_t *>(smem_m) + warp * grid_words;   // warp-private, clear
     for (int q = lane; q < grid_words; q += 32) grid[q] = 0u;
     __syncwarp();
@@ -421,13 +470,11 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
                            written, seg);
         }
         if (n <= kSmallMembers) {
-            if (lane < n) {
-                sm.pos[lane] = pos[lane];
+            if (lane < n)
                 member_coefficients(ax, w, hot, cold, pos[lane], i, zscale, t0, &sm.a[lane], &sm.b[lane], &sm.mrl[lane]);
-            }
             __syncwarp();
             unsigned long long votes = 0;
-            Best best = warp_stage2_small(ax, w, cold, grid, sm, n, i, votes);
+            Best best = warp_stage2_small(ax, w, cold, grid, sm, pos, n, i, votes);
             warp_best(best);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
@@ -578,19 +625,45 @@ int confirm_grid_words(const Axes &ax) { return (((ax.n_cot * ax.n_z0 + 1) >> 1)
 
 size_t stage2_smem_bytes(const Axes &ax) { return (size_t)confirm_grid_words(ax) * 4; }
 
+namespace {
+
+// Resident CTAs per SM of a kernel at a dynamic shared-memory size, asked once per size (the
+// answer depends on the kernel and the device only; the library drives one device model).
+template <typename K>
+int resident_ctas(K kernel, int threads, size_t smem, std::atomic<unsigned long long> &memo)
+{
+    const unsigned long long m = memo.load(std::memory_order_relaxed);
+    if (m && (m >> 32) == (unsigned long long)smem) return (int)(m & 0xFFFFFFFFull);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    memo.store(((unsigned long long)smem << 32) | (unsigned)n, std::memory_order_relaxed);
+    return n;
+}
+
+std::atomic<unsigned long long> g_member_ctas{0}, g_large_ctas{0};
+
+}  // namespace
+
 cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream)
 {
     const float s32 = (float)(ax.n_phi * kInvTwoPi);
-    // the number of candidates is known on the device only: persistent grids sized for the device,
-    // each warp or CTA striding over the flattened (event, candidate) work
+    // the number of candidates is known on the device only: persistent grids of exactly the
+    // resident CTAs, each warp or CTA striding over the flattened (event, candidate) work
     const size_t large_smem = (size_t)confirm_grid_words(ax) * 4;
     const size_t member_smem = kConfirmWarpsMax * large_smem;
     cudaError_t err = cudaFuncSetAttribute(member_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)member_smem);
+    if (!err) err = cudaFuncSetAttribute(member_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
     if (err) return err;
-    member_kernel<<<4 * sms, kConfirmWarpsMax * 32, member_smem, stream>>>(ax, w, s32, refine_eps, confirm_grid_words(ax));
+    const int threads = kConfirmWarpsMax * 32;
+    const int member_ctas = resident_ctas(member_kernel, threads, member_smem, g_member_ctas);
+    member_kernel<<<member_ctas * sms, threads, member_smem, stream>>>(ax, w, s32, refine_eps, confirm_grid_words(ax));
     err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem);
+    if (!err) err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
     if (err) return err;
-    stage2_large_kernel<<<4 * sms, kConfirmWarpsMax * 32, large_smem, stream>>>(ax, w, s32, refine_eps);
+    const int large_ctas = resident_ctas(stage2_large_kernel, threads, large_smem, g_large_ctas);
+    stage2_large_kernel<<<large_ctas * sms, threads, large_smem, stream>>>(ax, w, s32, refine_eps);
     return cudaGetLastError();
 }
 

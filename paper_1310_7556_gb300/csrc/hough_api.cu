@@ -132,6 +132,11 @@ Axes make_axes_impl(const hough_geometry *g, const hough_binning *b)
     ax.dt = (b->cot_max - b->cot_min) / b->n_cot;
     ax.z0_min = b->z0_min_cm;
     ax.z0_max = b->z0_max_cm;
+    ax.zscale = (double)b->n_z0 / (b->z0_max_cm - b->z0_min_cm);
+    ax.zs_hi = (float)ax.zscale;
+    ax.zs_lo = (float)(ax.zscale - (double)ax.zs_hi);
+    ax.zmin_hi = (float)ax.z0_min;
+    ax.zmin_lo = (float)(ax.z0_min - (double)ax.zmin_hi);
     return ax;
 }
 
@@ -314,6 +319,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n));
     A(c->alloc(&w.radii, 1)); A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
     A(c->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(c->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
+    A(c->alloc(&w.zco, (size_t)ax.n_layers * ax.n_qpt));
     A(c->alloc(&w.kq32, ax.n_qpt));
     A(c->alloc(&w.M, (size_t)ax.n_qpt * ax.n_phi));
     A(c->alloc(&w.cands, w.max_cand));

@@ -35,6 +35,9 @@ struct Axes {
     int n_layers, n_qpt, n_phi, threshold, n_cot, n_z0;
     double b, qpt_min, qpt_max, dk;
     double cot_min, cot_max, dt, z0_min, z0_max;
+    double zscale;                // n_z0 / (z0_max - z0_min): z0 bins per cm
+    float zs_hi, zs_lo;           // zscale as an unevaluated sum of two floats
+    float zmin_hi, zmin_lo;       // z0_min likewise
 };
 
 // Staged hit, the record the vote and membership kernels stream (16 bytes, one vector load).
@@ -128,6 +131,7 @@ struct Workspace {
     TableMemo *memo;
     TabEntry *tab;                // n_layers * n_qpt
     double *arc;                  // n_layers * n_qpt
+    float4 *zco;                  // n_layers * n_qpt stage-2 terms {S hi, S lo, B hi, B lo} (may be null)
     float *kq32;                  // n_qpt: FP32 q/pT bin centres
     uint16_t *M;                  // n_events * n_qpt * n_phi
     uint2 *band_cands;            // n_events * n_bands * band_cap

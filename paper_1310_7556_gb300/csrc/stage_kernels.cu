@@ -151,6 +151,15 @@ __global__ void table_kernel(Axes ax, Workspace w)
     }
     w.tab[q] = te;
     w.arc[q] = s;
+    if (w.zco) {
+        // stage-2 terms of the layer's members on this row: the z0 coordinate of cot row m is
+        // zscale (z - z0_min) - S - m B with S = zscale s t_0 and B = zscale s dt
+        const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
+        const double S = __dmul_rn(ax.zscale, __dmul_rn(s, t0));
+        const double B = __dmul_rn(ax.zscale, __dmul_rn(s, ax.dt));
+        const float sh = (float)S, bh = (float)B;
+        w.zco[q] = make_float4(sh, (float)(S - (double)sh), bh, (float)(B - (double)bh));
+    }
 }
 
 // One CTA per event: exclusive scan of the bucket sizes, in tiles of kScanTile counts staged
