@@ -227,8 +227,8 @@ __device__ __forceinline__ float2 two_prod(float a, float b)
 // 2^-44 relative before the final rounding), which keeps a within a few 1e-6 bins of the exact
 // value -- far inside the FP64 recheck window of stage2_bin.  Other layers take the FP64 route.
 __device__ __forceinline__ void member_coefficients(const Axes &ax, const Workspace &w, const HotHit *hot,
-                                                    const ColdHit *cold, int p, int i, double zscale, double t0,
-                                                    float *a_out, float *b_out, int *mrl_out)
+                                                    const ColdHit *cold, int p, int i, float *a_out, float *b_out,
+                                                    int *mrl_out)
 {
     const int l = (int)((hot[p].jl >> 16) & 0xFu);
     const ColdHit ch = cold[p];
@@ -253,8 +253,9 @@ __device__ __forceinline__ void member_coefficients(const Axes &ax, const Worksp
         return;
     }
     const double s = member_arc(ax, w, l, i, ch.r);
-    const double A = __dmul_rn(zscale, __dsub_rn(__dsub_rn((double)ch.z, ax.z0_min), __dmul_rn(s, t0)));
-    const double B = __dmul_rn(zscale, __dmul_rn(s, ax.dt));
+    const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
+    const double A = __dmul_rn(ax.zscale, __dsub_rn(__dsub_rn((double)ch.z, ax.z0_min), __dmul_rn(s, t0)));
+    const double B = __dmul_rn(ax.zscale, __dmul_rn(s, ax.dt));
     int mref = 0;
     if (B > 0.0) mref = (int)fminf(fmaxf(rintf((float)A / (float)B), 0.f), (float)(ax.n_cot - 1));
     *a_out = (float)(A - (double)mref * B);
@@ -303,33 +304,26 @@ struct Best {
     unsigned cnt, cell, mask;
 };
 
-// Vote (pass 0) or collect (pass 1) of the (member, cot row) pair into `grid`.
-__device__ __forceinline__ void stage2_pair(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
-                                            int p, int i, float a, float b, int mrl, int m, int pass,
-                                            unsigned long long &votes, Best &best)
+// One stage-2 vote: OR the member's layer bit into cell (m, nz) of `grid` and judge the cell by
+// the mask the OR produced.  The contributions to a cell are serialised by the atomic, so the last
+// one sees the cell's final mask; every other sees a subset of it.  Hence the largest popcount
+// seen over all votes is the grid's maximum, the cells seen with it are exactly the cells that
+// reach it, and the lowest of them -- with the mask seen there, which is its final mask -- is the
+// row-major-first arg-max.  No second pass over the votes is needed.  Returns the word index.
+__device__ __forceinline__ int stage2_vote(const Axes &ax, uint32_t *grid, int m, int nz, int layer, Best &best)
 {
-    const int nz = stage2_bin(ax, w, cold, p, i, a, b, mrl, m);
-    if (nz < 0) return;
     const unsigned cell = (unsigned)(m * ax.n_z0 + nz);
-    if (pass == 0) {
-        atomicOr(&grid[cell >> 1], (1u << (mrl >> 16)) << ((cell & 1u) << 4));
-        ++votes;
-        return;
+    const unsigned shift = (cell & 1u) << 4;
+    const uint32_t bit = 1u << layer;
+    const uint32_t old = atomicOr(&grid[cell >> 1], bit << shift);
+    const uint32_t m16 = ((old >> shift) & 0xFFFFu) | bit;
+    const unsigned cnt = (unsigned)__popc(m16);
+    if (cnt > best.cnt || (cnt == best.cnt && cell < best.cell)) {
+        best.cnt = cnt;
+        best.cell = cell;
+        best.mask = m16;
     }
-    // both halves of a word are judged by whichever thread takes it
-    const uint32_t word = atomicExch(&grid[cell >> 1], 0u);
-    if (!word) return;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const uint32_t m16 = (word >> (16 * h)) & 0xFFFFu;
-        const unsigned cc = (cell & ~1u) | (unsigned)h;
-        const unsigned cnt = (unsigned)__popc(m16);
-        if (m16 && (cnt > best.cnt || (cnt == best.cnt && cc < best.cell))) {
-            best.cnt = cnt;
-            best.cell = cc;
-            best.mask = m16;
-        }
-    }
+    return (int)(cell >> 1);
 }
 
 __device__ __forceinline__ void warp_best(Best &best)
@@ -374,8 +368,21 @@ union WarpScratch {
 };
 
 // Stage 2 of a candidate with at most 32 members in the warp's private grid: lane q prepares member
-// q and its run of cot rows; the (member, row) pairs of all runs are then spread over the lanes for
-// the vote pass and again for the collect pass.
+// q and its run of cot rows; the (member, row) pairs of all runs are then spread over the lanes and
+// voted in one pass (stage2_vote).  Each lane keeps the words its first kRecorded rounds touched and
+// clears them afterwards; pairs beyond those rounds are recomputed to clear theirs.
+constexpr int kRecorded = 6;
+
+__device__ __forceinline__ int small_pair_member(const SmallStage2 &sm, int n, int v)
+{
+    // the member whose run holds pair v: the last q with start[q] <= v
+    int q = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (q + step < n && sm.start[q + step] <= v) q += step;
+    return q;
+}
+
 __device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
                                   SmallStage2 &sm, const int *pos, int n, int i, unsigned long long &votes)
 {
@@ -398,25 +405,53 @@ __device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
     if (lane == 0) sm.start[kSmallMembers] = total;
     __syncwarp();
     Best best = {0u, 0u, 0u};
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int v = lane; v < total; v += 32) {
-            // the member whose run holds pair v: the last q with start[q] <= v
-            int q = 0;
+    int touched[kRecorded];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (q + step < n && sm.start[q + step] <= v) q += step;
+    for (int r = 0; r < kRecorded; ++r) touched[r] = -1;   // every slot, also those after an early exit
+#pragma unroll
+    for (int r = 0; r < kRecorded; ++r) {
+        const int v = lane + 32 * r;
+        if (32 * r >= total) break;
+        if (v < total) {
+            const int q = small_pair_member(sm, n, v);
             const int m = sm.mlo[q] + (v - sm.start[q]);
-            stage2_pair(ax, w, cold, grid, pos[q], i, sm.a[q], sm.b[q], sm.mrl[q], m, pass, votes, best);
+            const int mrl = sm.mrl[q];
+            const int nz = stage2_bin(ax, w, cold, pos[q], i, sm.a[q], sm.b[q], mrl, m);
+            if (nz >= 0) {
+                touched[r] = stage2_vote(ax, grid, m, nz, mrl >> 16, best);
+                ++votes;
+            }
         }
-        __syncwarp();
     }
+    for (int v = lane + 32 * kRecorded; v < total; v += 32) {
+        const int q = small_pair_member(sm, n, v);
+        const int m = sm.mlo[q] + (v - sm.start[q]);
+        const int mrl = sm.mrl[q];
+        const int nz = stage2_bin(ax, w, cold, pos[q], i, sm.a[q], sm.b[q], mrl, m);
+        if (nz >= 0) {
+            stage2_vote(ax, grid, m, nz, mrl >> 16, best);
+            ++votes;
+        }
+    }
+    __syncwarp();
+    // leave the grid clear for the warp's next candidate
+#pragma unroll
+    for (int r = 0; r < kRecorded; ++r)
+        if (touched[r] >= 0) grid[touched[r]] = 0u;
+    for (int v = lane + 32 * kRecorded; v < total; v += 32) {
+        const int q = small_pair_member(sm, n, v);
+        const int m = sm.mlo[q] + (v - sm.start[q]);
+        const int nz = stage2_bin(ax, w, cold, pos[q], i, sm.a[q], sm.b[q], sm.mrl[q], m);
+        if (nz >= 0) grid[(m * ax.n_z0 + nz) >> 1] = 0u;
+    }
+    __syncwarp();
     return best;
 }
 
 // Membership and, for candidates of at most kSmallMembers members, stage 2: one warp per candidate
 // over all events' candidates.  Members go once, in the fixed order, to the member pool; a larger
 // candidate is filed for the CTA stage-2 kernel.
-__global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, Workspace w, float s32, float refine_eps,
+__global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes ax, Workspace w, float s32, float refine_eps,
                                                                         int grid_words)
 {
     extern __shared__ __align__(16) unsigned char smem_m[];
@@ -432,8 +467,6 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
     __syncwarp();
     const int nkeys = ax.n_layers * ax.n_phi;
     const int total = (int)w.counters->total_cands;
-    const double zscale = __ddiv_rn((double)ax.n_z0, __dsub_rn(ax.z0_max, ax.z0_min));
-    const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
     for (int f = blockIdx.x * nwarps + warp; f < total; f += gridDim.x * nwarps) {
         const int e = upper_index(w.cand_base, w.n_events, f);
         const int c = f - w.cand_base[e];
@@ -447,11 +480,24 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
         const int i = (int)cd.iq;
         const int n = warp_enumerate(ax, w, offs, hot, cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, 0,
                                      kMemberCap, pos, nullptr, 0, seg);
+        // the event's member pool is shared by all its candidates: reserve the range now and use it
+        // after stage 2, so that the contended atomic's round trip overlaps the vote
+        unsigned reserved = 0u;
+        if (lane == 0 && n) reserved = atomicAdd(&w.stats[e].pool_used, (unsigned)n);
+        Best best = {0u, 0u, 0u};
+        unsigned long long votes = 0;
+        if (n <= kSmallMembers) {
+            if (lane < n) member_coefficients(ax, w, hot, cold, pos[lane], i, &sm.a[lane], &sm.b[lane], &sm.mrl[lane]);
+            __syncwarp();
+            best = warp_stage2_small(ax, w, cold, grid, sm, pos, n, i, votes);
+            warp_best(best);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
+        }
         int base = 0, written = 0;
         if (lane == 0) {
-            const unsigned b = n ? atomicAdd(&w.stats[e].pool_used, (unsigned)n) : 0u;
-            const long long room = (long long)w.max_members - (long long)b;
-            base = (int)min((long long)b, (long long)w.max_members);
+            const long long room = (long long)w.max_members - (long long)reserved;
+            base = (int)min((long long)reserved, (long long)w.max_members);
             written = n ? (int)max(0LL, min((long long)n, room)) : 0;
             w.mem_start[(int64_t)e * w.max_cand + c] = base;
             w.mem_count[(int64_t)e * w.max_cand + c] = written;
@@ -459,6 +505,9 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
             if (n > kSmallMembers) {
                 cands[c].n_members = (uint32_t)n;
                 w.large_list[atomicAdd(&w.counters->n_large, 1u)] = make_int2(e, c);
+            } else {
+                cands[c] = finished(ax, cd, n, written, best);
+                if (votes) atomicAdd(&w.stats[e].stage2_votes, votes);
             }
         }
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
@@ -468,20 +517,6 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32) member_kernel(Axes ax, 
         } else if (written > 0) {
             warp_enumerate(ax, w, offs, hot, cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, 0, 0, pos, pool + base,
                            written, seg);
-        }
-        if (n <= kSmallMembers) {
-            if (lane < n)
-                member_coefficients(ax, w, hot, cold, pos[lane], i, zscale, t0, &sm.a[lane], &sm.b[lane], &sm.mrl[lane]);
-            __syncwarp();
-            unsigned long long votes = 0;
-            Best best = warp_stage2_small(ax, w, cold, grid, sm, pos, n, i, votes);
-            warp_best(best);
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
-            if (lane == 0) {
-                cands[c] = finished(ax, cd, n, written, best);
-                if (votes) atomicAdd(&w.stats[e].stage2_votes, votes);
-            }
         }
         __syncwarp();
     }
@@ -493,7 +528,6 @@ struct Stage2Ctx {
     const int32_t *offs;
     const int32_t *pool;
     hough_candidate *cands;
-    double zscale, t0;
 };
 
 __device__ __forceinline__ Stage2Ctx stage2_ctx(const Axes &ax, const Workspace &w, int e)
@@ -505,12 +539,11 @@ __device__ __forceinline__ Stage2Ctx stage2_ctx(const Axes &ax, const Workspace 
     x.offs = w.offs + (int64_t)e * (ax.n_layers * ax.n_phi + 1);
     x.pool = w.mem_pool + (int64_t)e * w.max_members;
     x.cands = w.cands + (int64_t)e * w.max_cand;
-    x.zscale = __ddiv_rn((double)ax.n_z0, __dsub_rn(ax.z0_max, ax.z0_min));
-    x.t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
     return x;
 }
 
-// Stage 2 of the large candidates: one CTA each, members in chunks of kLargeChunk.
+// Stage 2 of the large candidates: one CTA each, members in chunks of kLargeChunk, every chunk's
+// (member, cot row) pairs voted in one pass (stage2_vote); the grid is cleared whole afterwards.
 __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(Axes ax, Workspace w, float s32,
                                                                                  float refine_eps)
 {
@@ -528,7 +561,6 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(
     if (blockIdx.x >= nlarge) return;
     const int grid_words = (((ax.n_cot * ax.n_z0 + 1) >> 1) + 3) & ~3;
     for (int q = threadIdx.x; q < grid_words; q += blockDim.x) grid[q] = 0u;
-    const int ncot = ax.n_cot;
     for (int idx = blockIdx.x; idx < nlarge; idx += gridDim.x) {
         unsigned long long votes = 0;
         const int2 ec = w.large_list[idx];
@@ -539,58 +571,58 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(
         const int base = w.mem_start[(int64_t)e * w.max_cand + c], written = w.mem_count[(int64_t)e * w.max_cand + c];
         const int nchunks = (n + kLargeChunk - 1) / kLargeChunk;
         Best best = {0u, 0u, 0u};
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int k = 0; k < nchunks; ++k) {
-                const int lo = k * kLargeChunk;
-                const int nm = min(kLargeChunk, n - lo);
-                if (pass == 0 || nchunks > 1) {
-                    __syncthreads();
-                    if (written == n) {
-                        for (int q = threadIdx.x; q < nm; q += blockDim.x) s_pos[q] = x.pool[base + lo + q];
-                    } else if (warp == 0) {
-                        warp_enumerate(ax, w, x.offs, x.hot, x.cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, lo,
-                                       kLargeChunk, s_pos, nullptr, 0, s_seg);
-                    }
-                    __syncthreads();
-                    for (int q = threadIdx.x; q < nm; q += blockDim.x) {
-                        member_coefficients(ax, w, x.hot, x.cold, s_pos[q], i, x.zscale, x.t0, &s_a[q], &s_b[q], &s_mrl[q]);
-                        int lo, hi;
-                        member_rows(ax, s_a[q], s_b[q], s_mrl[q], &lo, &hi);
-                        s_mlo[q] = lo;
-                        s_len[q] = max(0, hi - lo + 1);
-                    }
-                    __syncthreads();
-                    // exclusive scan of the runs' lengths (one thread per chunk slot strided over the CTA)
-                    if (warp == 0) {
-                        int carry = 0;
-                        for (int base = 0; base < nm; base += 32) {
-                            const int q = base + lane;
-                            const int v = q < nm ? s_len[q] : 0;
-                            int inc = v;
+        for (int k = 0; k < nchunks; ++k) {
+            const int lo = k * kLargeChunk;
+            const int nm = min(kLargeChunk, n - lo);
+            __syncthreads();
+            if (written == n) {
+                for (int q = threadIdx.x; q < nm; q += blockDim.x) s_pos[q] = x.pool[base + lo + q];
+            } else if (warp == 0) {
+                warp_enumerate(ax, w, x.offs, x.hot, x.cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, lo,
+                               kLargeChunk, s_pos, nullptr, 0, s_seg);
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+                member_coefficients(ax, w, x.hot, x.cold, s_pos[q], i, &s_a[q], &s_b[q], &s_mrl[q]);
+                int rlo, rhi;
+                member_rows(ax, s_a[q], s_b[q], s_mrl[q], &rlo, &rhi);
+                s_mlo[q] = rlo;
+                s_len[q] = max(0, rhi - rlo + 1);
+            }
+            __syncthreads();
+            // exclusive scan of the runs' lengths
+            if (warp == 0) {
+                int carry = 0;
+                for (int b0 = 0; b0 < nm; b0 += 32) {
+                    const int q = b0 + lane;
+                    const int v = q < nm ? s_len[q] : 0;
+                    int inc = v;
 #pragma unroll
-                            for (int d = 1; d < 32; d <<= 1) {
-                                const int t = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-                                if (lane >= d) inc += t;
-                            }
-                            if (q < nm) s_start[q] = carry + inc - v;
-                            carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
-                        }
-                        if (lane == 0) s_start[nm] = carry;
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int t = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+                        if (lane >= d) inc += t;
                     }
-                    __syncthreads();
+                    if (q < nm) s_start[q] = carry + inc - v;
+                    carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
                 }
-                // (member, cot row) pairs of the chunk's runs, spread over the CTA
-                const int npairs = s_start[nm];
-                for (int v = threadIdx.x; v < npairs; v += blockDim.x) {
-                    int qlo = 0, qhi = nm - 1;
-                    while (qlo < qhi) {
-                        const int mid = (qlo + qhi + 1) >> 1;
-                        if (s_start[mid] <= v) qlo = mid; else qhi = mid - 1;
-                    }
-                    const int m = s_mlo[qlo] + (v - s_start[qlo]);
-                    stage2_pair(ax, w, x.cold, grid, s_pos[qlo], i, s_a[qlo], s_b[qlo], s_mrl[qlo], m, pass, votes, best);
+                if (lane == 0) s_start[nm] = carry;
+            }
+            __syncthreads();
+            // (member, cot row) pairs of the chunk's runs, spread over the CTA
+            const int npairs = s_start[nm];
+            for (int v = threadIdx.x; v < npairs; v += blockDim.x) {
+                int qlo = 0, qhi = nm - 1;
+                while (qlo < qhi) {
+                    const int mid = (qlo + qhi + 1) >> 1;
+                    if (s_start[mid] <= v) qlo = mid; else qhi = mid - 1;
                 }
-                __syncthreads();
+                const int m = s_mlo[qlo] + (v - s_start[qlo]);
+                const int mrl = s_mrl[qlo];
+                const int nz = stage2_bin(ax, w, x.cold, s_pos[qlo], i, s_a[qlo], s_b[qlo], mrl, m);
+                if (nz >= 0) {
+                    stage2_vote(ax, grid, m, nz, mrl >> 16, best);
+                    ++votes;
+                }
             }
         }
         warp_best(best);
@@ -604,6 +636,7 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(
             }
             x.cands[c] = finished(ax, cd, n, written, b);
         }
+        for (int q = threadIdx.x; q < grid_words; q += blockDim.x) grid[q] = 0u;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
         if (lane == 0 && votes) atomicAdd(&w.stats[e].stage2_votes, votes);
