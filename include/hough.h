@@ -241,6 +241,7 @@ int hough_get_tiling(const hough_ctx *ctx, hough_tiling *tiling);
 typedef struct hough_timing {
     float stage_ms, vote_ms, peaks_ms, stage2_ms;
     float gather_ms, scatter_ms, band_peaks_ms, compact_ms;
+    float member_ms, large_ms;   /* stage2_ms = member_ms (membership, small candidates' stage 2) + large_ms */
 } hough_timing;
 
 int hough_enable_timing(hough_ctx *ctx, int on);

@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
 
 class Timing(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in ("stage_ms", "vote_ms", "peaks_ms", "stage2_ms", "gather_ms",
-                                              "scatter_ms", "band_peaks_ms", "compact_ms")]
+                                              "scatter_ms", "band_peaks_ms", "compact_ms", "member_ms", "large_ms")]
 
 
 class Tiling(ctypes.Structure):

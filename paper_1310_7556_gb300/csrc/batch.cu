@@ -243,7 +243,7 @@ int hough::batch_run(hough_batch *b, const float *r, const float *phi, const flo
         it = b->graphs.emplace(n_events, exec).first;
     }
     BCU(cudaGraphLaunch(it->second, s), "graph launch failed");
-    note_launches(kStageLaunches + kVoteLaunches + kPeakLaunches + kStage2Launches);
+    note_launches(kStageLaunches + kVoteLaunches + peak_launches(n_events) + kStage2Launches);
     b->n_events = n_events;
     b->ran = true;
     return HOUGH_OK;

@@ -1,32 +1,30 @@
 // Confirmation of the candidates (Sec. 4: candidates found as local maxima are confirmed by "more
 // expensive computations"): for each candidate, the hits whose stage-1 vote fell in its cell
-// (membership) and their vote in a (cot theta, z0) grid (stage 2), in one kernel.
+// (membership) and their vote in a (cot theta, z0) grid of layer masks (stage 2).
 //
-// Work scales with a candidate's votes, not with the size of the stage-2 grid.  A CTA that confirms
-// a large candidate keeps an n_cot x n_z0 grid of layer masks in shared memory, clear between
-// candidates: a vote pass ORs each (member, cot row) vote into it with a shared atomic; a collect
-// pass revisits the same votes, takes each touched word with atomicExch (reading and clearing it in
-// one step) and keeps the cell with the most layers, the lowest row-major index on ties.
+// Work scales with a candidate's votes, not with the size of the stage-2 grid.  Each confirming
+// warp owns a clear n_cot x n_z0 grid in shared memory.  A member's z0 coordinate is linear in the
+// cot row, so only a run of rows can vote inside the z0 range; the (member, row) pairs of all
+// runs are spread over the lanes and voted with a shared atomicOr, whose returned word also
+// judges the cell (stage2_vote): the arg-max falls out of the one pass.
 //
-// Events of moderate occupancy produce tens of thousands of candidates with a dozen members each,
-// saturated events a few hundred with fifty or more.  So a first kernel (a warp per candidate)
-// enumerates each candidate's members once, into the member pool, and finishes stage 2 itself when
-// the candidate has at most kSmallMembers members (one member per lane, cot rows in turn, lanes of
-// equal z0 bin grouped by __match_any_sync); larger candidates are filed for a CTA each, which
-// votes into a shared-memory grid as described above.
+// member_kernel (a warp per candidate, all events' candidates flattened) enumerates a candidate's
+// members once, in a fixed order, into the event's member pool, and finishes stage 2 itself for
+// candidates of up to kMemberCap members (in chunks of 32, one member per lane).  Larger
+// candidates -- the saturated cells of very dense events -- are filed for stage2_large_kernel,
+// a CTA each, which re-reads them from the pool (or re-enumerates them, when the pool overflowed)
+// in chunks of kLargeChunk.
 //
 // Membership: only layers present in the candidate's mask can hold members.  For a table layer
 // the vote inverts exactly -- a hit of bucket J votes into column j on row i when
 // J = j + I_i + (f < g_i) -- so two buckets of the sorted hits hold all of that layer's members;
 // other layers scan the buckets their radius range allows and redo the vote per hit (FP32 with
-// FP64 refinement, as in the vote kernel).  Members are enumerated in a fixed order (layer, bucket,
-// position), so a candidate with more members than a warp's buffer is processed in chunks that
-// are re-enumerated.
+// FP64 refinement, as in the vote kernel).
 //
 // Stage-2 arithmetic: for a member with arc length s the z0 coordinate
-// w(m) = n_z0 (z - s t_m - z0_min) / (z0_max - z0_min) is linear in the cot row m; it is evaluated
-// in FP32 around the member's own crossing row m_ref, and a vote within kStage2Eps of a z0 edge is
-// recomputed in FP64 exactly as the definition reads.
+// w(m) = n_z0 (z - s t_m - z0_min) / (z0_max - z0_min) is evaluated in FP32 around the row m_ref
+// where it crosses z0_min, from coefficients formed in two-float arithmetic (member_coefficients);
+// a vote within kStage2Eps of a z0 edge is recomputed in FP64 exactly as the definition reads.
 #include <atomic>
 
 #include "hough_internal.cuh"
@@ -205,22 +203,6 @@ __device__ __forceinline__ double exact_z0_coord(const Axes &ax, double z, doubl
     return __ddiv_rn(__dmul_rn((double)ax.n_z0, __dsub_rn(z0, ax.z0_min)), __dsub_rn(ax.z0_max, ax.z0_min));
 }
 
-// Error-free transformations of FP32 arithmetic (Knuth's two-sum, and the product with its
-// rounding error from one fused multiply-add): a + b = s + e and a b = p + e exactly.
-__device__ __forceinline__ float2 two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return make_float2(s, e);
-}
-
-__device__ __forceinline__ float2 two_prod(float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    return make_float2(p, fmaf(a, b, -p));
-}
-
 // Stage-2 coefficients of one member at row i: z0 coordinate w(m) = a - (m - m_ref) b in FP32.
 // For a layer of one radius the per-row terms S = zscale s t_0 and B = zscale s dt come from the
 // table and w(m_ref) = zscale (z - z0_min) - S - m_ref B is formed in two-float arithmetic (about
@@ -383,8 +365,9 @@ __device__ __forceinline__ int small_pair_member(const SmallStage2 &sm, int n, i
     return q;
 }
 
-__device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
-                                  SmallStage2 &sm, const int *pos, int n, int i, unsigned long long &votes)
+__device__ void warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
+                                  SmallStage2 &sm, const int *pos, int n, int i, bool clear, Best &best,
+                                  unsigned long long &votes)
 {
     const int lane = threadIdx.x & 31;
     int len = 0;
@@ -404,7 +387,6 @@ __device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (lane == 0) sm.start[kSmallMembers] = total;
     __syncwarp();
-    Best best = {0u, 0u, 0u};
     int touched[kRecorded];
 #pragma unroll
     for (int r = 0; r < kRecorded; ++r) touched[r] = -1;   // every slot, also those after an early exit
@@ -434,6 +416,7 @@ __device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
         }
     }
     __syncwarp();
+    if (!clear) return;
     // leave the grid clear for the warp's next candidate
 #pragma unroll
     for (int r = 0; r < kRecorded; ++r)
@@ -445,7 +428,6 @@ __device__ Best warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
         if (nz >= 0) grid[(m * ax.n_z0 + nz) >> 1] = 0u;
     }
     __syncwarp();
-    return best;
 }
 
 // Membership and, for candidates of at most kSmallMembers members, stage 2: one warp per candidate
@@ -486,10 +468,21 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
         if (lane == 0 && n) reserved = atomicAdd(&w.stats[e].pool_used, (unsigned)n);
         Best best = {0u, 0u, 0u};
         unsigned long long votes = 0;
-        if (n <= kSmallMembers) {
-            if (lane < n) member_coefficients(ax, w, hot, cold, pos[lane], i, &sm.a[lane], &sm.b[lane], &sm.mrl[lane]);
-            __syncwarp();
-            best = warp_stage2_small(ax, w, cold, grid, sm, pos, n, i, votes);
+        if (n <= kMemberCap) {
+            // members in chunks of 32 into the one grid; a single chunk clears what it touched,
+            // several clear the whole grid at the end
+            for (int c0 = 0; c0 < n; c0 += kSmallMembers) {
+                const int nc = min(kSmallMembers, n - c0);
+                if (lane < nc)
+                    member_coefficients(ax, w, hot, cold, pos[c0 + lane], i, &sm.a[lane], &sm.b[lane], &sm.mrl[lane]);
+                __syncwarp();
+                warp_stage2_small(ax, w, cold, grid, sm, pos + c0, nc, i, n <= kSmallMembers, best, votes);
+            }
+            if (n > kSmallMembers) {
+                uint4 *g4 = reinterpret_cast<uint4 *>(grid);
+                for (int q = lane; q < (grid_words >> 2); q += 32) g4[q] = make_uint4(0u, 0u, 0u, 0u);
+                __syncwarp();
+            }
             warp_best(best);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
@@ -502,7 +495,7 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
             w.mem_start[(int64_t)e * w.max_cand + c] = base;
             w.mem_count[(int64_t)e * w.max_cand + c] = written;
             if (n) atomicAdd(&w.stats[e].n_members, (unsigned)n);
-            if (n > kSmallMembers) {
+            if (n > kMemberCap) {
                 cands[c].n_members = (uint32_t)n;
                 w.large_list[atomicAdd(&w.counters->n_large, 1u)] = make_int2(e, c);
             } else {
@@ -677,7 +670,8 @@ std::atomic<unsigned long long> g_member_ctas{0}, g_large_ctas{0};
 
 }  // namespace
 
-cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream)
+cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream,
+                          cudaEvent_t between)
 {
     const float s32 = (float)(ax.n_phi * kInvTwoPi);
     // the number of candidates is known on the device only: persistent grids of exactly the
@@ -691,6 +685,7 @@ cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float ref
     const int threads = kConfirmWarpsMax * 32;
     const int member_ctas = resident_ctas(member_kernel, threads, member_smem, g_member_ctas);
     member_kernel<<<member_ctas * sms, threads, member_smem, stream>>>(ax, w, s32, refine_eps, confirm_grid_words(ax));
+    if (between && (err = cudaEventRecord(between, stream))) return err;
     err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem);
     if (!err) err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);

@@ -69,7 +69,7 @@ struct hough_ctx {
     bool timing = false;
     // 0 before staging, 1 after staging, 2 after the gather, 3 after the vote, 4 after the band
     // peaks, 5 after the candidate scan, 6 after stage 2
-    cudaEvent_t ev[7] = {};
+    cudaEvent_t ev[8] = {};
     int timed = 0;                       // bit k: ev[k] recorded for the current event
 
     ~hough_ctx()
@@ -137,6 +137,11 @@ Axes make_axes_impl(const hough_geometry *g, const hough_binning *b)
     ax.zs_lo = (float)(ax.zscale - (double)ax.zs_hi);
     ax.zmin_hi = (float)ax.z0_min;
     ax.zmin_lo = (float)(ax.z0_min - (double)ax.zmin_hi);
+    ax.pi_hi = (float)kPi;
+    ax.pi_lo = (float)(kPi - (double)ax.pi_hi);
+    const double upr = (double)b->n_phi / kTwoPi;
+    ax.u_hi = (float)upr;
+    ax.u_lo = (float)(upr - (double)ax.u_hi);
     return ax;
 }
 
@@ -375,7 +380,7 @@ int hough_peaks(hough_ctx *c, void *stream)
     if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
     CU(launch_compact(c->ax, c->w, (cudaStream_t)stream), "candidate scan kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[5], (cudaStream_t)stream), "event"); c->timed |= 32; }
-    g_launches += kPeakLaunches;
+    g_launches += peak_launches(1);
     c->stage = 2;
     return HOUGH_OK;
 }
@@ -385,8 +390,9 @@ int hough_stage2(hough_ctx *c, void *stream)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     if (c->stage < 2) return fail(HOUGH_ENOTREADY, "hough_peaks has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    CU(launch_stage2(c->ax, c->w, c->sms, c->refine_eps, (cudaStream_t)stream), "stage-2 kernels");
-    if (c->timing) { CU(cudaEventRecord(c->ev[6], (cudaStream_t)stream), "event"); c->timed |= 64; }
+    CU(launch_stage2(c->ax, c->w, c->sms, c->refine_eps, (cudaStream_t)stream, c->timing ? c->ev[7] : nullptr),
+       "stage-2 kernels");
+    if (c->timing) { CU(cudaEventRecord(c->ev[6], (cudaStream_t)stream), "event"); c->timed |= 64 | 128; }
     g_launches += kStage2Launches;
     c->stage = 3;
     return HOUGH_OK;
@@ -528,7 +534,7 @@ int hough_get_timing(hough_ctx *c, hough_timing *out)
     if ((rc = span(0, 1, &out->stage_ms)) || (rc = span(1, 3, &out->vote_ms)) || (rc = span(1, 2, &out->gather_ms)) ||
         (rc = span(2, 3, &out->scatter_ms)) || (rc = span(3, 5, &out->peaks_ms)) ||
         (rc = span(3, 4, &out->band_peaks_ms)) || (rc = span(4, 5, &out->compact_ms)) ||
-        (rc = span(5, 6, &out->stage2_ms)))
+        (rc = span(5, 6, &out->stage2_ms)) || (rc = span(5, 7, &out->member_ms)) || (rc = span(7, 6, &out->large_ms)))
         return rc;
     return HOUGH_OK;
 }

@@ -38,6 +38,8 @@ struct Axes {
     double zscale;                // n_z0 / (z0_max - z0_min): z0 bins per cm
     float zs_hi, zs_lo;           // zscale as an unevaluated sum of two floats
     float zmin_hi, zmin_lo;       // z0_min likewise
+    float pi_hi, pi_lo;           // pi as two floats
+    float u_hi, u_lo;             // n_phi / (2 pi) as two floats: bins per radian
 };
 
 // Staged hit, the record the vote and membership kernels stream (16 bytes, one vector load).
@@ -193,7 +195,8 @@ cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, 
 cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
 cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream);
 cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream);
-cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream);
+cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream,
+                          cudaEvent_t between = nullptr);
 cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t total, cudaStream_t stream);
 cudaError_t run_smem_or_bench(int device, int pattern, double ms, double *atomics_per_s, uint64_t *launches);
 
@@ -226,12 +229,29 @@ void note_launches(uint64_t n);
 // Kernels launched by each enqueue function (for hough_kernel_launches).
 constexpr int kStageLaunches = 5;
 constexpr int kVoteLaunches = 2;
-constexpr int kPeakLaunches = 3;
+// peak search, compaction, and for batches of several events the candidate-base scan
+inline int peak_launches(int n_events) { return n_events == 1 ? 2 : 3; }
 constexpr int kStage2Launches = 2;
 
 // Exact FP64 helpers used by the staging, table and refinement code.  They evaluate the
 // definitions in the order of the method's formulas with explicitly rounded operations,
 // so no multiply-add is fused.
+// Error-free transformations of FP32 arithmetic (Knuth's two-sum, and the product with its
+// rounding error from one fused multiply-add): a + b = s + e and a b = p + e exactly.
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return make_float2(p, fmaf(a, b, -p));
+}
+
 __device__ __forceinline__ double qpt_centre(const Axes &ax, int i)
 {
     return __dadd_rn(ax.qpt_min, __dmul_rn((double)i + 0.5, ax.dk));

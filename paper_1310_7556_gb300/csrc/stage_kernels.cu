@@ -13,6 +13,9 @@
 // and one FP32 comparison.  The staging also records, per (layer, phi bucket), the largest
 // and smallest fraction f of the hits in it: with the table they decide every cell of the
 // accumulator directly (see vote_kernel.cu).
+#include <algorithm>
+#include <cstdint>
+
 #include "hough_internal.cuh"
 
 namespace hough {
@@ -21,6 +24,37 @@ namespace {
 
 constexpr int kStageThreads = 256;
 constexpr int kScanThreads = 1024;
+constexpr int kTableThreads = 256;
+constexpr int kClearThreads = 256;
+
+// The per-call state the staging starts from, cleared by one kernel instead of one memset each:
+// up to kClearSegs ranges of 32-bit words, each set to a value (16-byte stores where aligned).
+constexpr int kClearSegs = 6;
+struct ClearList {
+    uint32_t *p[kClearSegs];
+    long long words[kClearSegs];
+    uint32_t value[kClearSegs];
+    int n;
+};
+
+__global__ void __launch_bounds__(kClearThreads) clear_kernel(ClearList cl)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int q = 0; q < cl.n; ++q) {
+        uint32_t *p = cl.p[q];
+        const long long n = cl.words[q];
+        const uint32_t v = cl.value[q];
+        const bool vec = ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) && (n % 4 == 0);
+        if (vec) {
+            uint4 *p4 = reinterpret_cast<uint4 *>(p);
+            const uint4 v4 = make_uint4(v, v, v, v);
+            for (long long k = t0; k < n / 4; k += stride) p4[k] = v4;
+        } else {
+            for (long long k = t0; k < n; k += stride) p[k] = v;
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Workspace w)
 {
@@ -51,17 +85,26 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
             w.key[h] = -1;
             continue;
         }
-        // bin coordinate of the hit's own azimuth: u_h = Nphi (phi + pi) / (2 pi) = J + f
-        const double uh = __dmul_rn(__dmul_rn((double)ax.n_phi, __dadd_rn((double)ph, kPi)), kInvTwoPi);
-        const double fl = floor(uh);
-        long long J = (long long)fl % ax.n_phi;
-        if (J < 0) J += ax.n_phi;
-        float f = (float)(uh - fl);
-        if (f >= 1.0f) {   // the fraction rounded up to 1: carry into J
-            f = 0.0f;
-            J = (J + 1 == ax.n_phi) ? 0 : J + 1;
+        // bin coordinate of the hit's own azimuth: u_h = Nphi (phi + pi) / (2 pi) = J + f, in
+        // two-float arithmetic (about 2^-44 relative: 1e-10 bins at Nphi = 2048), since the
+        // fraction must resolve far below the 1e-4-bin window in which votes may differ
+        float2 sp = two_sum(ph, ax.pi_hi);
+        sp.y = __fadd_rn(sp.y, ax.pi_lo);
+        float2 u = two_prod(sp.x, ax.u_hi);
+        u.y = u.y + (sp.x * ax.u_lo + sp.y * ax.u_hi);
+        float fl = floorf(u.x);
+        float f = __fadd_rn(__fsub_rn(u.x, fl), u.y);   // u.x - fl is exact
+        if (f < 0.f) {
+            f = __fadd_rn(f, 1.f);
+            fl -= 1.f;
         }
-        const int k = l * ax.n_phi + (int)J;
+        if (f >= 1.f) {   // also the fraction that rounded up to 1: carry into J
+            f = __fsub_rn(f, 1.f);
+            fl += 1.f;
+        }
+        int J = (int)fl % ax.n_phi;
+        if (J < 0) J += ax.n_phi;
+        const int k = l * ax.n_phi + J;
         w.key[h] = k;
         w.rank[h] = atomicAdd(&w.counts[(int64_t)e * nkeys + k], 1);
         // bucket extrema of f as ordered bit patterns (f >= 0): .x of bucket J keeps the maximum
@@ -69,7 +112,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
         // maximum of the complement, i.e. the minimum of bucket J
         if (w.prof) {
             uint2 *prof = w.prof + (int64_t)e * prof_event_entries(ax) + (int64_t)l * prof_stride(ax);
-            const int Jm = J == 0 ? ax.n_phi - 1 : (int)J - 1;
+            const int Jm = J == 0 ? ax.n_phi - 1 : J - 1;
             atomicMax(&prof[J].x, __float_as_uint(f) + 1u);
             atomicMax(&prof[Jm].y, ~__float_as_uint(f));
             if (J < kProfPad) atomicMax(&prof[J + ax.n_phi].x, __float_as_uint(f) + 1u);   // the repeated copy
@@ -81,8 +124,10 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
         hh.jl = (uint32_t)J | ((uint32_t)l << 16);
         hh.rows = 0;
         w.hot_tmp[h] = hh;
-        atomicMin(&s_rmin[l], __float_as_uint(rr));
-        atomicMax(&s_rmax[l], __float_as_uint(rr));
+        // radii are mostly equal within a layer: only a hit outside the range seen so far updates it
+        const unsigned rb = __float_as_uint(rr);
+        if (rb < *(volatile unsigned *)&s_rmin[l]) atomicMin(&s_rmin[l], rb);
+        if (rb > *(volatile unsigned *)&s_rmax[l]) atomicMax(&s_rmax[l], rb);
     }
     __syncthreads();
     if (threadIdx.x < HOUGH_MAX_LAYERS && s_rmax[threadIdx.x] != 0u) {
@@ -91,144 +136,141 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
     }
 }
 
-// One warp: per layer, whether all its hits share one radius, that radius's voting rows,
-// and whether the memoised table rows must be recomputed.
-__global__ void layer_info_kernel(Axes ax, Workspace w)
+// One CTA per layer: whether all the layer's hits share one radius, that radius's voting rows and
+// whether the memoised table rows must be recomputed; then, for a uniform layer whose radius
+// changed, per row: T = Nphi asin(x) / (2 pi) split into I + g, the arc length
+// s = r asin(|x|) / |x| for stage 2, and the stage-2 terms derived from it.
+__global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Workspace w)
 {
-    const int l = threadIdx.x;
-    if (l >= HOUGH_MAX_LAYERS) return;
-    LayerInfo li;
-    const unsigned rmin = w.radii->rmin[l], rmax = w.radii->rmax[l];
-    li.present = (l < ax.n_layers) && rmax != 0u;
-    li.uniform = !li.present || rmin == rmax;   // a layer without hits is trivially uniform
-    li.lo = 1;
-    li.hi = 0;
-    li.r_bits = rmin;
-    li.pad[0] = li.pad[1] = li.pad[2] = 0;
-    const int dirty = li.present && li.uniform && !(w.memo->valid[l] && w.memo->r_bits[l] == rmin);
-    if (li.present && li.uniform) {
-        if (dirty) {
-            row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
-            w.memo->r_bits[l] = rmin;
-            w.memo->lo[l] = li.lo;
-            w.memo->hi[l] = li.hi;
-            w.memo->valid[l] = 1;
-        } else {
-            li.lo = w.memo->lo[l];   // the same radius as before: its rows are memoised
-            li.hi = w.memo->hi[l];
+    __shared__ LayerInfo s_li;
+    __shared__ int s_dirty;
+    const int l = blockIdx.x;
+    if (threadIdx.x == 0) {
+        LayerInfo li;
+        const unsigned rmin = w.radii->rmin[l], rmax = w.radii->rmax[l];
+        li.present = (l < ax.n_layers) && rmax != 0u;
+        li.uniform = !li.present || rmin == rmax;   // a layer without hits is trivially uniform
+        li.lo = 1;
+        li.hi = 0;
+        li.r_bits = rmin;
+        li.pad[0] = li.pad[1] = li.pad[2] = 0;
+        const int dirty = li.present && li.uniform && !(w.memo->valid[l] && w.memo->r_bits[l] == rmin);
+        if (li.present && li.uniform) {
+            if (dirty) {
+                row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
+                w.memo->r_bits[l] = rmin;
+                w.memo->lo[l] = li.lo;
+                w.memo->hi[l] = li.hi;
+                w.memo->valid[l] = 1;
+            } else {
+                li.lo = w.memo->lo[l];   // the same radius as before: its rows are memoised
+                li.hi = w.memo->hi[l];
+            }
+        }
+        w.info[l] = li;
+        w.memo->dirty[l] = dirty;
+        s_li = li;
+        s_dirty = dirty;
+    }
+    __syncthreads();
+    if (!s_dirty) return;
+    const LayerInfo li = s_li;
+    const double r = (double)__uint_as_float(li.r_bits);
+    const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
+    for (int i = threadIdx.x; i < ax.n_qpt; i += blockDim.x) {
+        const int q = l * ax.n_qpt + i;
+        TabEntry te;
+        te.I = 0;
+        te.g = 0.f;
+        double s = 0.0;
+        if (i >= li.lo && i <= li.hi) {
+            const double x = __dmul_rn(sagitta_coef(ax, r), qpt_centre(ax, i));
+            const double T = __dmul_rn(__dmul_rn((double)ax.n_phi, asin(x)), kInvTwoPi);
+            const double fI = floor(T);
+            te.I = (int32_t)fI;
+            te.g = (float)(T - fI);
+            if (te.g >= 1.0f) {
+                te.I += 1;
+                te.g = 0.f;
+            }
+            const double axv = fabs(x);
+            s = axv > 0.0 ? __ddiv_rn(__dmul_rn(r, asin(axv)), axv) : r;
+        }
+        w.tab[q] = te;
+        w.arc[q] = s;
+        if (w.zco) {
+            // stage-2 terms of the layer's members on this row: the z0 coordinate of cot row m is
+            // zscale (z - z0_min) - S - m B with S = zscale s t_0 and B = zscale s dt
+            const double S = __dmul_rn(ax.zscale, __dmul_rn(s, t0));
+            const double B = __dmul_rn(ax.zscale, __dmul_rn(s, ax.dt));
+            const float sh = (float)S, bh = (float)B;
+            w.zco[q] = make_float4(sh, (float)(S - (double)sh), bh, (float)(B - (double)bh));
         }
     }
-    w.info[l] = li;
-    w.memo->dirty[l] = dirty;
 }
 
-// Per (layer, row) of a uniform layer whose radius changed: T = Nphi asin(x) / (2 pi) split into
-// I + g, and the arc length s = r asin(|x|) / |x| for stage 2.
-__global__ void table_kernel(Axes ax, Workspace w)
-{
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= ax.n_layers * ax.n_qpt) return;
-    const int l = q / ax.n_qpt, i = q % ax.n_qpt;
-    if (!w.memo->dirty[l]) return;
-    const LayerInfo li = w.info[l];
-    TabEntry te;
-    te.I = 0;
-    te.g = 0.f;
-    double s = 0.0;
-    if (i >= li.lo && i <= li.hi) {
-        const double r = (double)__uint_as_float(li.r_bits);
-        const double x = __dmul_rn(sagitta_coef(ax, r), qpt_centre(ax, i));
-        const double T = __dmul_rn(__dmul_rn((double)ax.n_phi, asin(x)), kInvTwoPi);
-        const double fI = floor(T);
-        te.I = (int32_t)fI;
-        te.g = (float)(T - fI);
-        if (te.g >= 1.0f) {
-            te.I += 1;
-            te.g = 0.f;
-        }
-        const double axv = fabs(x);
-        s = axv > 0.0 ? __ddiv_rn(__dmul_rn(r, asin(axv)), axv) : r;
-    }
-    w.tab[q] = te;
-    w.arc[q] = s;
-    if (w.zco) {
-        // stage-2 terms of the layer's members on this row: the z0 coordinate of cot row m is
-        // zscale (z - z0_min) - S - m B with S = zscale s t_0 and B = zscale s dt
-        const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
-        const double S = __dmul_rn(ax.zscale, __dmul_rn(s, t0));
-        const double B = __dmul_rn(ax.zscale, __dmul_rn(s, ax.dt));
-        const float sh = (float)S, bh = (float)B;
-        w.zco[q] = make_float4(sh, (float)(S - (double)sh), bh, (float)(B - (double)bh));
-    }
-}
-
-// One CTA per event: exclusive scan of the bucket sizes, in tiles of kScanTile counts staged
-// through shared memory with coalesced loads and stores; each warp scans 32 consecutive counts
-// per round with shuffles (no bank conflicts).  Then the vote count of uniform layers.
-constexpr int kScanRounds = 8;
-constexpr int kScanTile = kScanThreads * kScanRounds;
+// One CTA per event: exclusive scan of the bucket sizes.  Each thread owns kScanPerThread
+// consecutive counts of a round (four 16-byte loads), scans them in registers, and the CTA scans
+// the threads' totals (one shuffle scan per warp, one over the warps); a round covers
+// kScanThreads * kScanPerThread buckets, so an event of 10 layers x 2048 buckets takes two.
+// Then the vote count of uniform layers.
+constexpr int kScanPerThread = 16;
+constexpr int kScanRound = kScanThreads * kScanPerThread;
 
 __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Workspace w)
 {
-    __shared__ int s_tile[kScanTile];
     __shared__ int s_warp[kScanThreads / 32];
-    __shared__ int s_total;
     const int e = blockIdx.x;
     const int nkeys = n_keys(ax);
-    const int32_t *counts = w.counts + (int64_t)e * nkeys;
+    const int32_t *counts = w.counts + (int64_t)e * nkeys;   // 16-byte aligned: nkeys % 64 == 0
     int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int carry = 0;
-    for (int base = 0; base < nkeys; base += kScanTile) {
-        const int n = min(kScanTile, nkeys - base);
+    for (int base = 0; base < nkeys; base += kScanRound) {
+        const int k0 = base + threadIdx.x * kScanPerThread;
+        int v[kScanPerThread];
 #pragma unroll
-        for (int r = 0; r < kScanRounds; ++r) {
-            const int k = r * kScanThreads + threadIdx.x;
-            s_tile[k] = k < n ? counts[base + k] : 0;
+        for (int q = 0; q < kScanPerThread; q += 4) {
+            int4 x = make_int4(0, 0, 0, 0);
+            if (k0 + q < nkeys) x = *reinterpret_cast<const int4 *>(counts + k0 + q);   // nkeys % 4 == 0
+            v[q] = x.x; v[q + 1] = x.y; v[q + 2] = x.z; v[q + 3] = x.w;
         }
-        __syncthreads();
-        // warp w owns entries [w * 32 * kScanRounds, (w + 1) * 32 * kScanRounds)
-        int run = 0;
+        int sum = 0;
 #pragma unroll
-        for (int r = 0; r < kScanRounds; ++r) {
-            const int k = warp * 32 * kScanRounds + r * 32 + lane;
-            const int v = s_tile[k];
-            int incl = v;
+        for (int q = 0; q < kScanPerThread; ++q) sum += v[q];
+        int incl = sum;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-                if (lane >= d) incl += t;
-            }
-            s_tile[k] = run + incl - v;
-            run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += t;
         }
-        if (lane == 0) s_warp[warp] = run;
+        if (lane == 31) s_warp[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            const int v = s_warp[lane];
-            int incl = v;
+            const int x = s_warp[lane];
+            int wi = x;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-                if (lane >= d) incl += t;
+                const int t = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+                if (lane >= d) wi += t;
             }
-            s_warp[lane] = incl - v;   // exclusive over warps
-            if (lane == 31) s_total = incl;
+            s_warp[lane] = wi;   // inclusive over warps
         }
         __syncthreads();
+        int run = carry + (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
 #pragma unroll
-        for (int r = 0; r < kScanRounds; ++r) {
-            const int k = r * kScanThreads + threadIdx.x;
-            if (k < n) offs[base + k] = carry + s_warp[k / (32 * kScanRounds)] + s_tile[k];
+        for (int q = 0; q < kScanPerThread; ++q) {
+            if (k0 + q < nkeys) offs[k0 + q] = run;
+            run += v[q];
         }
-        carry += s_total;
+        carry += s_warp[kScanThreads / 32 - 1];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         offs[nkeys] = carry;
         w.stats[e].n_hits = (unsigned long long)carry;
     }
-    __syncthreads();
+    __syncthreads();   // the offsets written by other threads are visible after the barrier
     if (threadIdx.x < ax.n_layers) {
         const int l = threadIdx.x;
         const LayerInfo li = w.info[l];
@@ -287,19 +329,26 @@ int grid_for(int64_t n, int threads)
 cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream)
 {
     const int nkeys = n_keys(ax);
-    cudaError_t err;
-    if ((err = cudaMemsetAsync(w.counts, 0, sizeof(int32_t) * (size_t)w.n_events * nkeys, stream))) return err;
-    if (w.prof && (err = cudaMemsetAsync(w.prof, 0, sizeof(uint2) * (size_t)w.n_events * prof_event_entries(ax), stream)))
-        return err;
-    if ((err = cudaMemsetAsync(w.stats, 0, sizeof(DevStats) * (size_t)w.n_events, stream))) return err;
-    if (w.counters && (err = cudaMemsetAsync(w.counters, 0, sizeof(BatchCounters), stream))) return err;
-    if ((err = cudaMemsetAsync(w.radii->rmin, 0xFF, sizeof(w.radii->rmin), stream))) return err;
-    if ((err = cudaMemsetAsync(w.radii->rmax, 0, sizeof(w.radii->rmax), stream))) return err;
+    ClearList cl{};
+    auto add = [&](void *p, size_t bytes, uint32_t value) {
+        cl.p[cl.n] = static_cast<uint32_t *>(p);
+        cl.words[cl.n] = (long long)(bytes / 4);
+        cl.value[cl.n] = value;
+        ++cl.n;
+    };
+    add(w.counts, sizeof(int32_t) * (size_t)w.n_events * nkeys, 0u);
+    if (w.prof) add(w.prof, sizeof(uint2) * (size_t)w.n_events * prof_event_entries(ax), 0u);
+    add(w.stats, sizeof(DevStats) * (size_t)w.n_events, 0u);
+    if (w.counters) add(w.counters, sizeof(BatchCounters), 0u);
+    add(w.radii->rmin, sizeof(w.radii->rmin), 0xFFFFFFFFu);
+    add(w.radii->rmax, sizeof(w.radii->rmax), 0u);
+    long long vec_words = 0;
+    for (int q = 0; q < cl.n; ++q) vec_words += cl.words[q] / 4 + 1;
+    const int clear_grid = (int)std::min<long long>(2048, (vec_words + kClearThreads - 1) / kClearThreads);
+    clear_kernel<<<std::max(1, clear_grid), kClearThreads, 0, stream>>>(cl);
     const int g = grid_for(w.n_hits_total >= 0 ? w.n_hits_total : w.hit_capacity, kStageThreads);
     stage_count_kernel<<<g, kStageThreads, 0, stream>>>(ax, w);
-    layer_info_kernel<<<1, 32, 0, stream>>>(ax, w);
-    const int nt = ax.n_layers * ax.n_qpt;
-    table_kernel<<<(nt + 127) / 128, 128, 0, stream>>>(ax, w);
+    layer_table_kernel<<<HOUGH_MAX_LAYERS, kTableThreads, 0, stream>>>(ax, w);
     scan_keys_kernel<<<w.n_events, kScanThreads, 0, stream>>>(ax, w);
     scatter_kernel<<<g, kStageThreads, 0, stream>>>(ax, w);
     return cudaGetLastError();

@@ -104,22 +104,7 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
     if (scratch_address(device, &base) != cudaSuccess)
         return fail(HOUGH_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed");
 
-    Axes ax;
-    ax.n_layers = g->n_layers;
-    ax.n_qpt = b->n_qpt;
-    ax.n_phi = b->n_phi;
-    ax.threshold = b->threshold;
-    ax.n_cot = b->n_cot;
-    ax.n_z0 = b->n_z0;
-    ax.b = g->b_tesla;
-    ax.qpt_min = b->qpt_min;
-    ax.qpt_max = b->qpt_max;
-    ax.dk = (b->qpt_max - b->qpt_min) / b->n_qpt;
-    ax.cot_min = b->cot_min;
-    ax.cot_max = b->cot_max;
-    ax.dt = (b->cot_max - b->cot_min) / b->n_cot;
-    ax.z0_min = b->z0_min_cm;
-    ax.z0_max = b->z0_max_cm;
+    const Axes ax = make_axes(g, b);   // host arithmetic only: nothing is allocated
 
     Workspace w{};
     w.n_events = 1;

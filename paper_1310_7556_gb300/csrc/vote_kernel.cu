@@ -413,12 +413,19 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
 }
 
 // One CTA per event: exclusive scan of the band counts, then the band lists concatenated into
-// the raster-ordered candidate list (the first max_cand of them).
-__global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w)
+// the raster-ordered candidate list (the first max_cand of them).  With the band offsets in shared
+// memory every thread copies candidates by their index (the band found by binary search), so the
+// copy costs one round trip however the candidates fall into bands.  `single`: the batch is one
+// event, whose flattened candidate base this kernel then writes itself.
+constexpr int kCompactSmemBands = 4096;
+
+__global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w, int single)
 {
     __shared__ int s_warp[kCompactThreads / 32];
+    __shared__ int s_offs[kCompactSmemBands + 1];
     const int e = blockIdx.x;
     const int nb = n_bands(ax, w.band_rows);
+    const bool staged = nb <= kCompactSmemBands;
     const int32_t *counts = w.band_counts + (int64_t)e * nb;
     int32_t *offs = w.band_offs + (int64_t)e * nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -447,29 +454,50 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
     int run = (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
     for (int k = k0; k < k1; ++k) {
         offs[k] = run;
+        if (staged) s_offs[k] = run;
         run += counts[k];
     }
     const int total = s_warp[kCompactThreads / 32 - 1];
+    const int kept = min(total, w.max_cand);
     if (threadIdx.x == 0) {
         w.stats[e].n_candidates = (unsigned)total;
         if (total > w.max_cand) atomicOr(&w.stats[e].device_error, HOUGH_DEVERR_CAND);
+        if (single) {
+            w.cand_base[0] = 0;
+            w.cand_base[1] = kept;
+            w.counters->total_cands = (unsigned)kept;
+        }
     }
     __syncthreads();
     hough_candidate *cands = w.cands + (int64_t)e * w.max_cand;
     const uint2 *lists = w.band_cands + (int64_t)e * nb * w.band_cap;
+    auto emit = [&](int c, uint2 v) {
+        hough_candidate cd;
+        cd.iq = v.x / (unsigned)ax.n_phi;
+        cd.jphi = v.x % (unsigned)ax.n_phi;
+        cd.mask = v.y;
+        cd.n_members = 0u;
+        cd.icot = cd.jz0 = cd.mask2 = cd.flags = 0u;
+        cands[c] = cd;
+    };
+    if (staged) {
+        for (int c = threadIdx.x; c < kept; c += kCompactThreads) {
+            // the band holding candidate c: the last b with offs[b] <= c (empty bands share offsets)
+            int lo = 0, hi = nb - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_offs[mid] <= c) lo = mid; else hi = mid - 1;
+            }
+            emit(c, lists[(int64_t)lo * w.band_cap + (c - s_offs[lo])]);
+        }
+        return;
+    }
     for (int b = warp; b < nb; b += kCompactThreads / 32) {
         const int n = counts[b], o = offs[b];
         for (int k = lane; k < n; k += 32) {
             const int c = o + k;
             if (c >= w.max_cand) break;
-            const uint2 v = lists[(int64_t)b * w.band_cap + k];
-            hough_candidate cd;
-            cd.iq = v.x / (unsigned)ax.n_phi;
-            cd.jphi = v.x % (unsigned)ax.n_phi;
-            cd.mask = v.y;
-            cd.n_members = 0u;
-            cd.icot = cd.jz0 = cd.mask2 = cd.flags = 0u;
-            cands[c] = cd;
+            emit(c, lists[(int64_t)b * w.band_cap + k]);
         }
     }
 }
@@ -644,8 +672,9 @@ cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &
 
 cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream)
 {
-    compact_kernel<<<w.n_events, kCompactThreads, 0, stream>>>(ax, w);
-    cand_scan_kernel<<<1, kCompactThreads, 0, stream>>>(w);
+    const int single = w.n_events == 1;
+    compact_kernel<<<w.n_events, kCompactThreads, 0, stream>>>(ax, w, single);
+    if (!single) cand_scan_kernel<<<1, kCompactThreads, 0, stream>>>(w);
     return cudaGetLastError();
 }
 
