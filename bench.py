@@ -1,18 +1,24 @@
 #!/usr/bin/env python3
-"""Throughput of the GB300 Hough-transform track finder on a seeded synthetic workload.
+"""Throughput of the GB300 Hough-transform track finder on seeded synthetic workloads.
 
 One step = one event through the whole hot path on the GPU: hit staging, stage-1 vote, peak
 search, membership and the stage-2 vote.  Default workload: the single high-pileup event
 (5,000 helices + 50,000 noise hits, 512 q/pT x 2048 phi0 layer masks, >= 7 layers, 64 x 64
 stage 2).  Inputs are resident in HBM before the timed region; L2 is flushed (a 256 MiB write)
 before every timed step and each step is bracketed by CUDA events on the launching stream.
+A second pass of the same steps with an event after every kernel attributes the step time;
+`roofline` is the kernel with the largest share, `kernels` has all of them.
 
-`e2e` repeats the measurement through the public one-call entry point (hough_process) from
-pinned host buffers: host->device copy of the hits, the path, and the device->host read of the
-candidate list, timed on the host around each call.
+Also reported: `batched` (the batch workload, 256 events of 100-10,000 helices, as one CUDA-graph
+replay per step), `served` (Poisson arrivals at 5k/20k/50k events/s through the continuous-
+batching server against one launch per event), `e2e` (the public one-call entry point
+hough_process from pinned host buffers: host->device copy of the hits, the path, and the
+device->host read of the candidate list, timed on the host around each call), `scatter_mode`
+(the paper's shared-atomic vote design in place of the gather vote), and `cpu_baseline` (the
+FP64 oracle on this machine's host cores, on a bounded sample).
 
 `--impl reference` times the FP64 CPU oracle (the plain restatement of the method the CUDA path is
-checked against) on this machine's host cores, on the same workload and metric.
+checked against) on the host cores, on the same workload and metric.
 
 Launch: `python bench.py [--gpus 1] [--steps K] [--warmup W]`; for N > 1 under
 `python -m torch.distributed.run --nproc-per-node N ... bench.py --gpus N`: every rank processes
@@ -130,21 +136,41 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def cpu_baseline(workload, n_events: int = 4):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload."""
+def _oracle_event(job):
+    """One event of a workload through the oracle (a process-pool task): (votes, seconds)."""
     import oracle
-    w = eg.WORKLOADS[workload]
-    events = [w.event(i) for i in range(n_events)]
+    name, index = job
+    w = eg.WORKLOADS[name]
+    ev = w.event(index)
+    t0 = time.perf_counter()
+    res = oracle.run(w.geometry, w.binning, ev)
+    return int(res["votes_by_layer"].sum()), time.perf_counter() - t0
+
+
+def cpu_baseline(workload, n_single: int = 4):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the workload: one
+    thread on n_single events, then one event per core in spawned processes (the oracle is
+    single-threaded; an event is its unit of parallel work)."""
+    import multiprocessing as mp
+
+    import oracle
     oracle.build()
     t0 = time.perf_counter()
-    votes = 0
-    for ev in events:
-        res = oracle.run(w.geometry, w.binning, ev)
-        votes += int(res["votes_by_layer"].sum())
-    dt = time.perf_counter() - t0
-    return {"value": n_events / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_events} full {workload} events (seeds 0..{n_events - 1}), whole path, FP64, 1 thread",
-            "votes_per_s": votes / dt, "seconds": dt}
+    votes = sum(_oracle_event((workload, i))[0] for i in range(n_single))
+    dt1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_event, [(workload, 0)] * cores)   # start-up and first-touch outside the timing
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_event, [(workload, 100 + i) for i in range(cores)])
+        dtn = time.perf_counter() - t0
+    return {"value": cores / dtn, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} full {workload} events (seeds 100..{99 + cores}), one per core in spawned "
+                      f"processes, whole path (vote, peaks, membership, stage 2), FP64",
+            "votes_per_s": sum(v for v, _ in res) / dtn, "seconds": dtn,
+            "single_thread": {"value": n_single / dt1, "unit": "events/s", "cores": 1,
+                              "sample": f"{n_single} full {workload} events (seeds 0..{n_single - 1})",
+                              "votes_per_s": votes / dt1, "seconds": dt1}}
 
 
 def run_reference(args):
@@ -214,7 +240,10 @@ class Env:
 
 
 def measure_plain(env, args, ctx, tens, n):
-    """One event per step through hough_vote, hough_peaks, hough_stage2 on device-resident hits."""
+    """One event per step through hough_vote, hough_peaks, hough_stage2 on device-resident hits.
+
+    The headline steps run with the library's per-kernel events off; a second pass of the same
+    steps with them on attributes the step time to kernels."""
     torch, binding, stream = env.torch, env.binding, env.stream
 
     def step():
@@ -222,7 +251,7 @@ def measure_plain(env, args, ctx, tens, n):
         ctx.peaks(stream=stream)
         ctx.stage2(stream=stream)
 
-    def timed_steps(steps):
+    def timed_steps(steps, attribute):
         """K steps, each after an L2 flush, bracketed by CUDA events on the launching stream."""
         e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -232,36 +261,140 @@ def measure_plain(env, args, ctx, tens, n):
             e0[k].record(stream)
             step()
             e1[k].record(stream)
-            lib_t.append(ctx.timing())
+            if attribute:
+                lib_t.append(ctx.timing())
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in zip(e0, e1)], lib_t
 
+    ctx.enable_timing(False)
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     st = ctx.stats()
     env.barrier()
     launches0 = binding.kernel_launches()
-    with ClockSampler(env.local) as clocks:
-        step_ms, lib_t = timed_steps(args.steps)
+    step_ms, _ = timed_steps(args.steps, False)
     launches = binding.kernel_launches() - launches0
     total_ms = env.max_over_ranks(sum(step_ms))
     env.barrier()
+    # attribution pass: the same steps with an event after every kernel
+    ctx.enable_timing(True)
+    step()
+    attr_ms, lib_t = timed_steps(min(args.steps, 50), True)
+    kernel_ms = {k: statistics.mean(t[k] for t in lib_t) for k in lib_t[0]}
     out = {"events_per_s": env.world * args.steps / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
-           "stage_ms": {k: statistics.mean(t[k] for t in lib_t) for k in lib_t[0]},
-           "votes": int(st.votes), "candidates": int(st.n_candidates), "members": int(st.n_members),
-           "launches": int(launches), "clocks": clocks.summary()}
+           "stage_ms": kernel_ms, "attributed_ms_per_step": statistics.mean(attr_ms),
+           "votes": int(st.votes), "general_votes": int(st.general_votes), "candidates": int(st.n_candidates),
+           "members": int(st.n_members), "stage2_votes": int(st.stage2_votes), "launches": int(launches)}
     # the same steps with the shared-atomic scatter vote (the paper's GPU design) for comparison
     tiling0 = ctx.get_tiling()
     ctx.set_tiling(vote_mode=binding.VOTE_SCATTER)
     for _ in range(3):
         step()
-    sc_ms, sc_t = timed_steps(min(args.steps, 20))
+    sc_ms, sc_t = timed_steps(min(args.steps, 20), True)
     ctx.set_tiling(**tiling0)
+    ctx.enable_timing(False)
     out["scatter"] = {"events_per_s": len(sc_ms) / (sum(sc_ms) * 1e-3), "ms_per_step": statistics.mean(sc_ms),
                       "vote_ms": statistics.mean(t["vote_ms"] for t in sc_t),
                       "peaks_ms": statistics.mean(t["peaks_ms"] for t in sc_t)}
     return out
+
+
+# Kernels of one plain step: (name, timing key, source file that defines it).  The per-kernel
+# algorithmic work (bytes or lane operations per launch) is kernel_work's model below.
+PLAIN_KERNELS = [
+    ("clear_kernel", "clear_ms", "stage_kernels.cu"),
+    ("stage_count_kernel", "count_ms", "stage_kernels.cu"),
+    ("layer_table_kernel", "table_ms", "stage_kernels.cu"),
+    ("scan_keys_kernel", "scan_ms", "stage_kernels.cu"),
+    ("scatter_kernel (hit sort)", "sort_ms", "stage_kernels.cu"),
+    ("gather_kernel", "gather_ms", "vote_kernel.cu"),
+    ("scatter_kernel (vote of per-vote layers)", "scatter_ms", "vote_kernel.cu"),
+    ("peaks_kernel", "band_peaks_ms", "vote_kernel.cu"),
+    ("compact_kernel", "compact_ms", "vote_kernel.cu"),
+    ("member_kernel + stage2_large_kernel", "stage2_ms", "confirm_kernels.cu"),
+]
+ALU_LANES_PER_SM = 128   # FP32/INT32 lanes of a Blackwell SM
+
+
+def kernel_work(name, w, n_hits, plain):
+    """(bound, algorithmic amount per launch, unit) of one kernel of the plain step:
+    bytes for the memory-bound steps (the reads and writes the step needs, each once),
+    lane operations for the confirmation (24 per member: its two-float stage-2 coefficients and
+    row run; 8 per stage-2 vote: FMA, floor, range tests, the OR, popcount, arg-max compare)."""
+    b = w.binning
+    cells = b.n_qpt * b.n_phi
+    nkeys = w.geometry.n_layers * b.n_phi
+    cands = plain["candidates"]
+    general = plain["general_votes"] / max(1, plain["votes"])
+    model = {
+        "clear_kernel": ("hbm", 4 * nkeys + 8 * 16 * (b.n_phi + 16) + 304),
+        "stage_count_kernel": ("hbm", 37 * n_hits),          # r, phi, z, layer in; key, rank, 16-B record out
+        "layer_table_kernel": ("hbm", 32 * 16),              # layer records (rows only when a radius changes)
+        "scan_keys_kernel": ("hbm", 8 * nkeys),              # bucket counts in, offsets out
+        "scatter_kernel (hit sort)": ("hbm", 68 * n_hits),   # key, rank, record, r, phi, z, offset in; 2 x 16 B out
+        "gather_kernel": ("hbm", 13 * n_hits + 2 * cells),   # the vote: hits in, one 16-bit mask per cell out
+        "scatter_kernel (vote of per-vote layers)": ("hbm", 13 * n_hits * general),
+        "peaks_kernel": ("hbm", 2 * cells + 8 * cands),      # masks in, candidates out
+        "compact_kernel": ("hbm", 40 * cands),               # band lists in, candidate records out
+        "member_kernel + stage2_large_kernel": ("alu", 24 * plain["members"] + 8 * plain["stage2_votes"]),
+    }
+    bound, amount = model[name]
+    return bound, float(amount), "bytes" if bound == "hbm" else "lane operations"
+
+
+def _sources_digest(src):
+    import hashlib
+    h = hashlib.sha256()
+    for f in (src, "hough_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1310_7556_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload, src):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or None when
+    there is none or the kernel's sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.txt")
+    try:
+        with open(path) as f:
+            lines = [ln.rstrip("\n").split("\t") for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    digest = _sources_digest(src)
+    for parts in lines:
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == digest:
+            return float(parts[2])
+    return None
+
+
+def kernel_table(env, w, n_hits, plain, smem_peak, hbm_peak, peaks_kind, clocks):
+    """Per-kernel roofline of the plain step from its attributed device times."""
+    props = env.torch.cuda.get_device_properties(env.dev)
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_mhz * 1e6   # lane ops/s
+    total = sum(plain["stage_ms"][k] for _, k, _ in PLAIN_KERNELS)
+    table = {}
+    for name, key, src in PLAIN_KERNELS:
+        ms = plain["stage_ms"][key]
+        bound, amount, unit = kernel_work(name, w, n_hits, plain)
+        rate = amount / (ms * 1e-3) if ms > 0 else 0.0
+        if bound == "hbm":
+            ach, peak, u = rate / 1e9, hbm_peak, "GB/s"
+            pk = f"{peaks_kind}: MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)"
+        else:
+            ach, peak, u = rate / 1e12, alu_peak / 1e12, "Tops/s"
+            pk = (f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} FP32/INT32 lanes x {sm_mhz:.0f} MHz "
+                  "(median SM clock sampled during the run)")
+        table[name] = {"ms": ms, "share": ms / total if total else None, "bound": bound, "algorithmic": amount,
+                       "algorithmic_unit": unit, "achieved": ach, "peak": peak, "unit": u,
+                       "frac": ach / peak if peak else None, "peak_kind": pk, "source": src}
+    g = table["gather_kernel"]
+    g["smem_atomic_equivalent"] = {
+        "votes_per_s": plain["votes"] / (plain["stage_ms"]["gather_ms"] * 1e-3),
+        "peak": smem_peak, "frac": plain["votes"] / (plain["stage_ms"]["gather_ms"] * 1e-3) / smem_peak,
+        "note": "votes decided per second against the measured shared-atomicOr ceiling of the paper's scatter design"}
+    return table
 
 
 def measure_batched(env, args):
@@ -312,79 +445,43 @@ def _percentiles(lat_ms):
     return {"p50_ms": q(0.50), "p99_ms": q(0.99), "p999_ms": q(0.999), "max_ms": float(a[-1])}
 
 
-def drive_server(env, srv, pool, rate, seconds, seed):
-    """Offer a Poisson stream of `rate` events/s for `seconds` to a server: a submitter thread
-    submits each event at its scheduled arrival (latency counts from that time, so a late
-    submission is charged to the server), a consumer thread polls every admitted ticket."""
-    import collections
+def drive_server(env, srv, pool, rate, seconds, seed, threads=4):
+    """Offer a Poisson stream of `rate` events/s for `seconds` to a server through the library's
+    trigger emulator (native submitter threads, each submitting at the scheduled arrival; latency
+    counts from that time, so a late submission is charged to the server; one native thread polls
+    every admitted event)."""
     binding = env.binding
     n = max(1, int(rate * seconds))
     arrivals = eg.poisson_arrivals(rate, n, seed)
-    admitted = collections.deque()
-    lat_ms, batch_sizes, statuses = [], [], collections.Counter()
-    done_ns = []
-    state = {"finished": False, "dropped": 0, "late_ns": []}
-    start = time.monotonic_ns() + 50_000_000
+    start = binding.serve_clock_ns() + 50_000_000
     at = (start + arrivals * 1e9).astype(np.int64)
-
-    def submitter():
-        for i in range(n):
-            a = int(at[i])
-            now = time.monotonic_ns()
-            if a - now > 300_000:
-                time.sleep((a - now - 200_000) * 1e-9)
-            while time.monotonic_ns() < a:
-                pass
-            ev = pool[i % len(pool)]
-            state["late_ns"].append(time.monotonic_ns() - a)
-            t = srv.submit(ev[0], ev[1], ev[2], ev[3], ev[0].shape[0], arrival_ns=a)
-            if t is None:
-                state["dropped"] += 1
-            else:
-                admitted.append(t)
-        state["finished"] = True
-
-    def consumer():
-        while True:
-            if admitted:
-                t = admitted.popleft()
-                _, res = srv.poll(t, timeout_us=60_000_000, candidates=False,
-                                  allow=(binding.EDEVICE, binding.ENOMEM, binding.ETIMEDOUT))
-                statuses[int(res.status)] += 1
-                lat_ms.append((res.done_ns - res.arrival_ns) * 1e-6)
-                batch_sizes.append(res.batch_events)
-                done_ns.append(res.done_ns)
-            elif state["finished"]:
-                break
-            else:
-                time.sleep(50e-6)
-
     st0 = srv.stats()
-    threads = [threading.Thread(target=submitter), threading.Thread(target=consumer)]
-    for t in threads:
-        t.start()
-    for t in threads:
-        t.join()
+    res = srv.replay(pool, at, threads)
     st1 = srv.stats()
-    span_s = (max(done_ns) - start) * 1e-9 if done_ns else float("nan")
-    out = {"offered_ev_s": rate, "seconds": seconds, "offered": n, "admitted": len(lat_ms),
-           "dropped": state["dropped"], "dropped_frac": state["dropped"] / n,
-           "completed_ev_s": len(lat_ms) / span_s if done_ns else 0.0,
-           **_percentiles(lat_ms),
-           "mean_batch_events": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
-           "max_in_flight": int(st1.max_in_flight), "launches": int(st1.launches - st0.launches),
-           "submit_late_p99_us": float(np.percentile(state["late_ns"], 99)) * 1e-3,
-           "statuses": {str(k): v for k, v in statuses.items()}}
-    return out
+    admitted = res["ticket"] != 0
+    done = res["done_ns"][admitted]
+    lat_ms = ((done - res["arrival_ns"][admitted]) * 1e-6).tolist()
+    late_us = (res["submit_ns"][admitted] - res["arrival_ns"][admitted]) * 1e-3
+    statuses = {}
+    for v in res["status"][admitted].tolist():
+        statuses[str(v)] = statuses.get(str(v), 0) + 1
+    span_s = (int(done.max()) - start) * 1e-9 if done.size else float("nan")
+    n_adm = int(admitted.sum())
+    return {"offered_ev_s": rate, "seconds": seconds, "offered": n, "admitted": n_adm,
+            "dropped": n - n_adm, "dropped_frac": (n - n_adm) / n,
+            "completed_ev_s": n_adm / span_s if done.size else 0.0,
+            **_percentiles(lat_ms),
+            "mean_batch_events": float(res["batch_events"][admitted].mean()) if n_adm else 0.0,
+            "max_in_flight": int(st1.max_in_flight), "launches": int(st1.launches - st0.launches),
+            "submit_late_p99_us": float(np.percentile(late_us, 99)) if n_adm else None,
+            "submitter_threads": threads, "statuses": statuses}
 
 
 def measure_served(env, args):
     """Trigger-style serving of batch-workload events arriving as Poisson streams: continuous
     batching (events admitted while others run join the next launch; up to two launches overlap on
     the device) against one launch per event through the same admission and lanes."""
-    import sys as _sys
     binding = env.binding
-    _sys.setswitchinterval(1e-4)
     wb = eg.WORKLOADS["batch_256"]
     pool_events = [wb.event(1000 + env.rank * 64 + i) for i in range(64)]
     pool = [tuple(np.ascontiguousarray(getattr(e, k)) for k in ("r", "phi", "z", "layer")) for e in pool_events]
@@ -460,28 +557,29 @@ def main():
     tens = [env.torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
     ctx = binding.HoughContext(w.geometry, w.binning, max_hits=n, max_candidates=1 << 18,
                                max_members=1 << 23, device=env.local)
-    ctx.enable_timing(True)
     # measured shared-atomic ceiling (conflict-free 32-lane atomicOr), before anything is timed
     smem_peak = binding.smem_or_throughput(env.local, 0, 30.0)
     smem_peak_rand = binding.smem_or_throughput(env.local, 1, 30.0)
-    plain = measure_plain(env, args, ctx, tens, n)
-    if args.only == "plain":
-        if env.rank == 0:
-            print(json.dumps({"metric": METRIC, "part": "plain", **plain}), flush=True)
-        return
-    batched = measure_batched(env, args)
-    e2e = measure_e2e(env, args, ctx, ev)
-    served = measure_served(env, args)
-
+    with ClockSampler(env.local) as clock_sampler:
+        plain = measure_plain(env, args, ctx, tens, n)
+        if args.only == "plain":
+            batched = e2e = served = None
+        else:
+            batched = measure_batched(env, args)
+            e2e = measure_e2e(env, args, ctx, ev)
+            served = measure_served(env, args)
+    clocks = clock_sampler.summary()
     peaks, peaks_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    kernels = kernel_table(env, w, n, plain, smem_peak, hbm_peak, peaks_kind, clocks)
+    dominant = max(kernels, key=lambda k: kernels[k]["ms"])
+    dk = kernels[dominant]
+    src = dict((name, s) for name, _, s in PLAIN_KERNELS)[dominant]
+    traffic = measured_traffic(dominant, args.workload, src)
     votes = plain["votes"]
-    vote_ms = plain["stage_ms"]["vote_ms"]
     scatter = plain.pop("scatter")
-    scatter["smem_atomic_frac"] = votes / (scatter["vote_ms"] * 1e-3) / smem_peak
     scatter["votes_per_s_in_vote_kernel"] = votes / (scatter["vote_ms"] * 1e-3)
-    # algorithmic bytes of the vote launch: 13 B per hit read (r, phi, z, layer) + 2 B per cell written
-    vote_bytes = 13 * n + 2 * w.binning.n_qpt * w.binning.n_phi
+    scatter["smem_atomic_frac"] = scatter["votes_per_s_in_vote_kernel"] / smem_peak
     line = {
         "metric": METRIC,
         "value": plain["events_per_s"],
@@ -497,26 +595,26 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": n, "votes_per_event": votes,
                    "candidates_per_event": plain["candidates"], "members_per_event": plain["members"],
-                   "mode": "plain: one event per step, one launch sequence",
+                   "stage2_votes_per_event": plain["stage2_votes"],
+                   "mode": "plain: one event per step, hough_vote + hough_peaks + hough_stage2 (11 kernel launches)",
                    "l2": "flushed before every timed step (256 MiB write)", "tiling": ctx.get_tiling()},
         "votes_per_s": votes * plain["events_per_s"],
-        "stage_ms": plain["stage_ms"],
+        "roofline": {"kernel": dominant, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
+                     "unit": dk["unit"], "frac": dk["frac"], "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "algorithmic": dk["algorithmic"], "algorithmic_unit": dk["algorithmic_unit"],
+                     "ms": dk["ms"], "share_of_step": dk["share"], "peak_kind": dk["peak_kind"]},
+        "kernels": kernels,
+        "smem_atomic_peak": {"conflict_free": smem_peak, "random_words": smem_peak_rand,
+                             "unit": "lane atomicOr/s", "how": "hough_microbench_smem_or, 152-multiple persistent grid"},
         "scatter_mode": scatter,
         "batched": batched,
         "served": served,
-        "roofline": {"bound": "smem_atomic", "kernel": "vote_kernel", "achieved": votes / (vote_ms * 1e-3) / 1e9,
-                     "peak": smem_peak / 1e9, "unit": "Gatomic/s", "frac": votes / (vote_ms * 1e-3) / smem_peak,
-                     "peak_kind": "measured by hough_microbench_smem_or (conflict-free 32-lane atomicOr)",
-                     "peak_random_pattern": smem_peak_rand / 1e9,
-                     "traffic": None,
-                     "hbm": {"achieved": vote_bytes / (vote_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": vote_bytes / (vote_ms * 1e-3) / 1e9 / hbm_peak,
-                             "peak_kind": f"{peaks_kind} (MEASURED_PEAKS.json hbm_gbs)"}},
         "e2e": e2e,
         "gpu_launches": plain["launches"],
-        "clocks": plain["clocks"],
+        "clocks": clocks,
     }
-    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline and args.only == "all":
         line["cpu_baseline"] = cpu_baseline(args.workload)
     ctx.close()
     if env.rank == 0:

@@ -242,6 +242,7 @@ typedef struct hough_timing {
     float stage_ms, vote_ms, peaks_ms, stage2_ms;
     float gather_ms, scatter_ms, band_peaks_ms, compact_ms;
     float member_ms, large_ms;   /* stage2_ms = member_ms (membership, small candidates' stage 2) + large_ms */
+    float clear_ms, count_ms, table_ms, scan_ms, sort_ms;   /* the staging kernels: stage_ms is their sum */
 } hough_timing;
 
 int hough_enable_timing(hough_ctx *ctx, int on);
@@ -415,6 +416,25 @@ int hough_serve_poll(hough_server *server, uint64_t ticket, hough_candidate *out
 int hough_serve_drain(hough_server *server, int64_t timeout_us);
 
 int hough_serve_get_stats(hough_server *server, hough_serve_stats *out);
+
+/* One event's hits in host memory, for hough_serve_replay. */
+typedef struct hough_event_view {
+    const float *r, *phi, *z;
+    const uint8_t *layer;
+    int64_t n_hits;
+} hough_event_view;
+
+/*
+ * Trigger emulation: offer n events to the server at the given arrival times (hough_serve_clock_ns
+ * time, non-decreasing).  Arrival i is event pool[i % n_pool]; `threads` submitter threads (1..64)
+ * take arrivals i = t mod threads, each waiting for its arrival time before hough_serve_submit,
+ * while one more thread polls every admitted event in arrival order and drops its candidates.
+ * results[i] (n entries) receives arrival i's result; a refused arrival has ticket 0 and the
+ * refusal (HOUGH_EBUSY) as its status.  Returns when every arrival has been offered and every
+ * admitted event polled; HOUGH_ETIMEDOUT when some admitted event had no result within 60 s.
+ */
+int hough_serve_replay(hough_server *server, const hough_event_view *pool, int32_t n_pool,
+                       const int64_t *arrival_ns, int64_t n, int32_t threads, hough_serve_result *results);
 
 /* Switch a host-side fault (HOUGH_SERVE_FAULT_*) on (on != 0) or off. */
 int hough_serve_inject(hough_server *server, int fault, int on);

@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
 
 class Timing(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in ("stage_ms", "vote_ms", "peaks_ms", "stage2_ms", "gather_ms",
-                                              "scatter_ms", "band_peaks_ms", "compact_ms", "member_ms", "large_ms")]
+                                              "scatter_ms", "band_peaks_ms", "compact_ms", "member_ms", "large_ms",
+                                              "clear_ms", "count_ms", "table_ms", "scan_ms", "sort_ms")]
 
 
 class Tiling(ctypes.Structure):
@@ -91,6 +92,11 @@ class ServeStats(ctypes.Structure):
         "submitted", "admitted", "rejected_busy", "rejected_invalid", "completed", "failed", "launches",
         "launched_events", "max_in_flight", "timeouts", "alloc_failures", "retired_lanes", "lanes", "in_flight",
         "pending_tickets", "device_bytes")]
+
+
+class EventView(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("layer", ctypes.c_void_p), ("n_hits", ctypes.c_int64)]
 
 
 SERVE_FAULT_HOLD, SERVE_FAULT_STALL, SERVE_FAULT_ALLOC = 1, 2, 3
@@ -144,6 +150,8 @@ _SIGNATURES = {
     "hough_serve_drain": ([_P, _I64], ctypes.c_int),
     "hough_serve_get_stats": ([_P, ctypes.POINTER(ServeStats)], ctypes.c_int),
     "hough_serve_inject": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "hough_serve_replay": ([_P, ctypes.POINTER(EventView), _I32, _P, _I64, _I32, ctypes.POINTER(ServeResult)],
+                           ctypes.c_int),
 }
 
 
@@ -485,6 +493,18 @@ class HoughServer:
         st = ServeStats()
         _check(self._lib.hough_serve_get_stats(self._h, ctypes.byref(st)))
         return st
+
+    def replay(self, pool, arrival_ns, threads: int = 4):
+        """hough_serve_replay: offer arrival i = pool[i % len(pool)] (tuples of contiguous r, phi, z
+        float32 and layer uint8 arrays) at arrival_ns[i]; returns the ServeResult array."""
+        views = (EventView * len(pool))()
+        for q, (r, phi, z, layer) in enumerate(pool):
+            views[q] = EventView(_ptr(r), _ptr(phi), _ptr(z), _ptr(layer), int(r.shape[0]))
+        arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        res = (ServeResult * max(1, arr.shape[0]))()
+        self._keep_pool = pool
+        _check(self._lib.hough_serve_replay(self._h, views, len(pool), _ptr(arr), arr.shape[0], threads, res))
+        return np.ctypeslib.as_array(res)[: arr.shape[0]].copy()
 
     def inject(self, fault: int, on: bool = True):
         _check(self._lib.hough_serve_inject(self._h, int(fault), int(bool(on))))

@@ -436,6 +436,7 @@ __device__ void warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
 __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes ax, Workspace w, float s32, float refine_eps,
                                                                         int grid_words)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_m[];
     __shared__ int s_pos[kConfirmWarpsMax][kMemberCap];
     __shared__ WarpScratch s_scratch[kConfirmWarpsMax];
@@ -449,7 +450,8 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
     __syncwarp();
     const int nkeys = ax.n_layers * ax.n_phi;
     const int total = (int)w.counters->total_cands;
-    for (int f = blockIdx.x * nwarps + warp; f < total; f += gridDim.x * nwarps) {
+    // candidate f goes to CTA f mod gridDim, so that a few candidates spread over all SMs
+    for (int f = warp * gridDim.x + blockIdx.x; f < total; f += gridDim.x * nwarps) {
         const int e = upper_index(w.cand_base, w.n_events, f);
         const int c = f - w.cand_base[e];
         const int64_t hstart = w.hit_start[e];
@@ -540,6 +542,7 @@ __device__ __forceinline__ Stage2Ctx stage2_ctx(const Axes &ax, const Workspace 
 __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(Axes ax, Workspace w, float s32,
                                                                                  float refine_eps)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem2[];
     __shared__ int s_pos[kLargeChunk];
     __shared__ float s_a[kLargeChunk], s_b[kLargeChunk];
@@ -639,6 +642,7 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(
 
 __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total)
 {
+    pdl_enter();
     const ColdHit *cold = w.cold + w.hit_start[0];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
         idx_out[q] = cold[w.mem_pool[q]].idx;
@@ -684,22 +688,25 @@ cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float ref
     if (err) return err;
     const int threads = kConfirmWarpsMax * 32;
     const int member_ctas = resident_ctas(member_kernel, threads, member_smem, g_member_ctas);
-    member_kernel<<<member_ctas * sms, threads, member_smem, stream>>>(ax, w, s32, refine_eps, confirm_grid_words(ax));
+    if ((err = launch_chained(member_kernel, dim3(member_ctas * sms), dim3(threads), member_smem, stream, ax, w, s32,
+                              refine_eps, confirm_grid_words(ax))))
+        return err;
     if (between && (err = cudaEventRecord(between, stream))) return err;
     err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem);
     if (!err) err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
     if (err) return err;
     const int large_ctas = resident_ctas(stage2_large_kernel, threads, large_smem, g_large_ctas);
-    stage2_large_kernel<<<large_ctas * sms, threads, large_smem, stream>>>(ax, w, s32, refine_eps);
-    return cudaGetLastError();
+    return launch_chained(stage2_large_kernel, dim3(large_ctas * sms), dim3(threads), large_smem, stream, ax, w, s32,
+                          refine_eps);
 }
 
 cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t total, cudaStream_t stream)
 {
     if (total <= 0) return cudaSuccess;
     const int g = (int)min((total + 255) / 256, (int64_t)4096);
-    member_index_kernel<<<g, 256, 0, stream>>>(w, idx_out, total);
+    cudaError_t err = launch_chained(member_index_kernel, dim3(g), dim3(256), 0, stream, w, idx_out, total);
+    if (err) return err;
     return cudaGetLastError();
 }
 

@@ -69,7 +69,7 @@ struct hough_ctx {
     bool timing = false;
     // 0 before staging, 1 after staging, 2 after the gather, 3 after the vote, 4 after the band
     // peaks, 5 after the candidate scan, 6 after stage 2
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[12] = {};   // 0..7 step boundaries, 8..11 inside the staging
     int timed = 0;                       // bit k: ev[k] recorded for the current event
 
     ~hough_ctx()
@@ -229,8 +229,8 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     c->timed = 0;
     c->w.band_rows = c->tiling.band_rows;
     c->w.band_cap = band_capacity(c->ax, c->tiling.band_rows);
-    if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1; }
-    CU(launch_stage(c->ax, c->w, s), "stage kernels");
+    if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1 | (0xF << 8); }
+    CU(launch_stage(c->ax, c->w, s, c->timing ? c->ev + 8 : nullptr), "stage kernels");
     if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
     if (c->tiling.vote_mode == HOUGH_VOTE_GATHER) CU(launch_gather(c->ax, c->w, s), "gather kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
@@ -534,7 +534,9 @@ int hough_get_timing(hough_ctx *c, hough_timing *out)
     if ((rc = span(0, 1, &out->stage_ms)) || (rc = span(1, 3, &out->vote_ms)) || (rc = span(1, 2, &out->gather_ms)) ||
         (rc = span(2, 3, &out->scatter_ms)) || (rc = span(3, 5, &out->peaks_ms)) ||
         (rc = span(3, 4, &out->band_peaks_ms)) || (rc = span(4, 5, &out->compact_ms)) ||
-        (rc = span(5, 6, &out->stage2_ms)) || (rc = span(5, 7, &out->member_ms)) || (rc = span(7, 6, &out->large_ms)))
+        (rc = span(5, 6, &out->stage2_ms)) || (rc = span(5, 7, &out->member_ms)) || (rc = span(7, 6, &out->large_ms)) ||
+        (rc = span(0, 8, &out->clear_ms)) || (rc = span(8, 9, &out->count_ms)) || (rc = span(9, 10, &out->table_ms)) ||
+        (rc = span(10, 11, &out->scan_ms)) || (rc = span(11, 1, &out->sort_ms)))
         return rc;
     return HOUGH_OK;
 }

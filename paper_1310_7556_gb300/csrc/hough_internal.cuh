@@ -184,7 +184,9 @@ __host__ __device__ inline int band_capacity(const Axes &ax, int band_rows)
 inline float refine_eps_for(const Axes &ax) { return (float)(ax.n_phi * 5e-7 + 1e-4); }
 
 // Kernel launchers (each enqueues on `stream` and returns the launch status).
-cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream);
+// `after`, when given, receives an event after each of the first four staging kernels (clear, count,
+// layer table, scan); the caller times the last one.
+cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream, cudaEvent_t *after = nullptr);
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
                         cudaStream_t stream);
 cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
@@ -236,6 +238,34 @@ constexpr int kStage2Launches = 2;
 // Exact FP64 helpers used by the staging, table and refinement code.  They evaluate the
 // definitions in the order of the method's formulas with explicitly rounded operations,
 // so no multiply-add is fused.
+// Programmatic dependent launch: every kernel of the path is launched with programmatic stream
+// serialisation (launch_chained), so the next kernel's grid is set up while this one runs; each
+// kernel first waits for its predecessor's completion and memory (griddepcontrol.wait) and only
+// then lets its own dependent launch.  A kernel launched without the attribute passes the wait at
+// once.  Every kernel launched through launch_chained must begin with pdl_enter().
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                                  Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Error-free transformations of FP32 arithmetic (Knuth's two-sum, and the product with its
 // rounding error from one fused multiply-add): a + b = s + e and a b = p + e exactly.
 __device__ __forceinline__ float2 two_sum(float a, float b)

@@ -574,6 +574,66 @@ int hough_serve_get_stats(hough_server *s, hough_serve_stats *out)
     return HOUGH_OK;
 }
 
+int hough_serve_replay(hough_server *s, const hough_event_view *pool, int32_t n_pool, const int64_t *arrival_ns,
+                       int64_t n, int32_t threads, hough_serve_result *results)
+{
+    if (!s || !pool || n_pool < 1 || !arrival_ns || n < 0 || threads < 1 || threads > 64 || !results)
+        return set_last_error(HOUGH_EINVAL, "bad arguments");
+    for (int32_t q = 0; q < n_pool; ++q)
+        if (pool[q].n_hits < 0 || (pool[q].n_hits > 0 && (!pool[q].r || !pool[q].phi || !pool[q].z || !pool[q].layer)))
+            return set_last_error(HOUGH_EINVAL, "bad pool event");
+    // ticket of arrival i once submitted: kPending until then, 0 when refused
+    constexpr uint64_t kPending = ~0ull;
+    std::vector<std::atomic<uint64_t>> ticket(n);
+    for (int64_t i = 0; i < n; ++i) ticket[i].store(kPending, std::memory_order_relaxed);
+    std::vector<int32_t> refused(n, 0);
+    auto submitter = [&](int t) {
+        for (int64_t i = t; i < n; i += threads) {
+            const int64_t a = arrival_ns[i];
+            for (int64_t now = clock_ns(); now < a; now = clock_ns())
+                if (a - now > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(a - now - 100000));
+            const hough_event_view &ev = pool[i % n_pool];
+            uint64_t id = 0;
+            const int rc = hough_serve_submit(s, ev.r, ev.phi, ev.z, ev.layer, ev.n_hits, a, &id);
+            refused[i] = rc;
+            ticket[i].store(rc == HOUGH_OK ? id : 0ull, std::memory_order_release);
+        }
+    };
+    int consumer_rc = HOUGH_OK;
+    auto consumer = [&] {
+        for (int64_t i = 0; i < n; ++i) {
+            uint64_t id;
+            while ((id = ticket[i].load(std::memory_order_acquire)) == kPending) std::this_thread::yield();
+            hough_serve_result &r = results[i];
+            std::memset(&r, 0, sizeof(r));
+            if (id == 0) {
+                r.arrival_ns = arrival_ns[i];
+                r.status = refused[i];
+                continue;
+            }
+            int rc = HOUGH_ETIMEDOUT;
+            // a result arrives within a few launches; the bound keeps a stalled server from blocking
+            for (int k = 0; k < 600 && rc == HOUGH_ETIMEDOUT; ++k) {
+                rc = hough_serve_poll(s, id, nullptr, 0, &r, 100000);
+                if (rc == HOUGH_ETIMEDOUT && r.ticket == id) break;   // finished with status ETIMEDOUT
+            }
+            if (rc == HOUGH_ETIMEDOUT && r.ticket != id) {
+                r.ticket = id;
+                r.arrival_ns = arrival_ns[i];
+                r.status = HOUGH_ETIMEDOUT;
+                consumer_rc = HOUGH_ETIMEDOUT;
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < threads; ++t) th.emplace_back(submitter, t);
+    std::thread cons(consumer);
+    for (auto &x : th) x.join();
+    cons.join();
+    if (consumer_rc) return set_last_error(consumer_rc, "some events had no result within 60 s");
+    return HOUGH_OK;
+}
+
 int hough_serve_inject(hough_server *s, int fault, int on)
 {
     if (!s) return set_last_error(HOUGH_EINVAL, "server is required");

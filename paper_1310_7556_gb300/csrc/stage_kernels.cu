@@ -39,6 +39,7 @@ struct ClearList {
 
 __global__ void __launch_bounds__(kClearThreads) clear_kernel(ClearList cl)
 {
+    pdl_enter();
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (int q = 0; q < cl.n; ++q) {
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(kClearThreads) clear_kernel(ClearList cl)
 
 __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Workspace w)
 {
+    pdl_enter();
     __shared__ unsigned int s_rmin[HOUGH_MAX_LAYERS], s_rmax[HOUGH_MAX_LAYERS];
     if (threadIdx.x < HOUGH_MAX_LAYERS) {
         s_rmin[threadIdx.x] = 0xFFFFFFFFu;
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
 // s = r asin(|x|) / |x| for stage 2, and the stage-2 terms derived from it.
 __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Workspace w)
 {
+    pdl_enter();
     __shared__ LayerInfo s_li;
     __shared__ int s_dirty;
     const int l = blockIdx.x;
@@ -209,35 +212,44 @@ __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Wor
     }
 }
 
-// One CTA per event: exclusive scan of the bucket sizes.  Each thread owns kScanPerThread
-// consecutive counts of a round (four 16-byte loads), scans them in registers, and the CTA scans
-// the threads' totals (one shuffle scan per warp, one over the warps); a round covers
-// kScanThreads * kScanPerThread buckets, so an event of 10 layers x 2048 buckets takes two.
-// Then the vote count of uniform layers.
-constexpr int kScanPerThread = 16;
+// One CTA per event: exclusive scan of the bucket sizes, kScanRound counts per round.  The counts
+// are loaded and the offsets stored coalesced through a shared tile; in between each thread scans
+// kScanPerThread consecutive entries in registers and the CTA scans the threads' totals (one
+// shuffle scan per warp, one over the warps).  The tile has one padding word per 32, which keeps
+// the per-thread reads of consecutive words free of bank conflicts.  Then the vote count of
+// uniform layers.
+constexpr int kScanPerThread = 8;
 constexpr int kScanRound = kScanThreads * kScanPerThread;
+
+__device__ __forceinline__ int scan_pad(int k) { return k + (k >> 5); }
 
 __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Workspace w)
 {
+    pdl_enter();
+    __shared__ int s_tile[kScanRound + kScanRound / 32];
     __shared__ int s_warp[kScanThreads / 32];
     const int e = blockIdx.x;
     const int nkeys = n_keys(ax);
-    const int32_t *counts = w.counts + (int64_t)e * nkeys;   // 16-byte aligned: nkeys % 64 == 0
+    const int32_t *counts = w.counts + (int64_t)e * nkeys;
     int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int carry = 0;
     for (int base = 0; base < nkeys; base += kScanRound) {
-        const int k0 = base + threadIdx.x * kScanPerThread;
-        int v[kScanPerThread];
+        const int n = min(kScanRound, nkeys - base);
 #pragma unroll
-        for (int q = 0; q < kScanPerThread; q += 4) {
-            int4 x = make_int4(0, 0, 0, 0);
-            if (k0 + q < nkeys) x = *reinterpret_cast<const int4 *>(counts + k0 + q);   // nkeys % 4 == 0
-            v[q] = x.x; v[q + 1] = x.y; v[q + 2] = x.z; v[q + 3] = x.w;
+        for (int r = 0; r < kScanPerThread; ++r) {
+            const int k = r * kScanThreads + threadIdx.x;
+            s_tile[scan_pad(k)] = k < n ? counts[base + k] : 0;
         }
+        __syncthreads();
+        const int k0 = threadIdx.x * kScanPerThread;
+        int v[kScanPerThread];
         int sum = 0;
 #pragma unroll
-        for (int q = 0; q < kScanPerThread; ++q) sum += v[q];
+        for (int q = 0; q < kScanPerThread; ++q) {
+            v[q] = s_tile[scan_pad(k0 + q)];
+            sum += v[q];
+        }
         int incl = sum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -260,10 +272,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Worksp
         int run = carry + (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
 #pragma unroll
         for (int q = 0; q < kScanPerThread; ++q) {
-            if (k0 + q < nkeys) offs[k0 + q] = run;
+            s_tile[scan_pad(k0 + q)] = run;
             run += v[q];
         }
         carry += s_warp[kScanThreads / 32 - 1];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kScanPerThread; ++r) {
+            const int k = r * kScanThreads + threadIdx.x;
+            if (k < n) offs[base + k] = s_tile[scan_pad(k)];
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -284,6 +302,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Worksp
 // Scatter every valid hit to its sorted position, completing its hot record with its voting rows.
 __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspace w)
 {
+    pdl_enter();
     const int nkeys = n_keys(ax);
     const int64_t total = hit_total(w);
     const HitInputs in = hit_inputs(w);
@@ -326,7 +345,7 @@ int grid_for(int64_t n, int threads)
 
 }  // namespace
 
-cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream)
+cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream, cudaEvent_t *after)
 {
     const int nkeys = n_keys(ax);
     ClearList cl{};
@@ -345,13 +364,20 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
     long long vec_words = 0;
     for (int q = 0; q < cl.n; ++q) vec_words += cl.words[q] / 4 + 1;
     const int clear_grid = (int)std::min<long long>(2048, (vec_words + kClearThreads - 1) / kClearThreads);
-    clear_kernel<<<std::max(1, clear_grid), kClearThreads, 0, stream>>>(cl);
+    cudaError_t err;
+    auto mark = [&](int k) { return after ? cudaEventRecord(after[k], stream) : cudaSuccess; };
+    if ((err = launch_chained(clear_kernel, dim3(std::max(1, clear_grid)), dim3(kClearThreads), 0, stream, cl)))
+        return err;
+    if ((err = mark(0))) return err;
     const int g = grid_for(w.n_hits_total >= 0 ? w.n_hits_total : w.hit_capacity, kStageThreads);
-    stage_count_kernel<<<g, kStageThreads, 0, stream>>>(ax, w);
-    layer_table_kernel<<<HOUGH_MAX_LAYERS, kTableThreads, 0, stream>>>(ax, w);
-    scan_keys_kernel<<<w.n_events, kScanThreads, 0, stream>>>(ax, w);
-    scatter_kernel<<<g, kStageThreads, 0, stream>>>(ax, w);
-    return cudaGetLastError();
+    if ((err = launch_chained(stage_count_kernel, dim3(g), dim3(kStageThreads), 0, stream, ax, w))) return err;
+    if ((err = mark(1))) return err;
+    if ((err = launch_chained(layer_table_kernel, dim3(HOUGH_MAX_LAYERS), dim3(kTableThreads), 0, stream, ax, w)))
+        return err;
+    if ((err = mark(2))) return err;
+    if ((err = launch_chained(scan_keys_kernel, dim3(w.n_events), dim3(kScanThreads), 0, stream, ax, w))) return err;
+    if ((err = mark(3))) return err;
+    return launch_chained(scatter_kernel, dim3(g), dim3(kStageThreads), 0, stream, ax, w);
 }
 
 }  // namespace hough

@@ -62,6 +62,7 @@ __device__ __forceinline__ void layer_masks(const Workspace &w, int L, unsigned 
 template <int TPB, bool GENERAL_ONLY>
 __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_start[kMaxRanges];
     __shared__ int s_pre[kMaxRanges + 1];
@@ -316,6 +317,7 @@ struct GatherParams {
 template <int NL>
 __global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherParams p)
 {
+    pdl_enter();
     __shared__ int rowI[kGatherRows * 16];
     __shared__ unsigned rowG[kGatherRows * 16];
     __shared__ unsigned rowMask[kGatherRows];
@@ -383,6 +385,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherParams p)
 // Peak search of one band of band_rows rows from the accumulator (plus a halo row on each side).
 __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char pc[];
     const int R = w.band_rows;
     const int nb = n_bands(ax, R);
@@ -421,6 +424,7 @@ constexpr int kCompactSmemBands = 4096;
 
 __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w, int single)
 {
+    pdl_enter();
     __shared__ int s_warp[kCompactThreads / 32];
     __shared__ int s_offs[kCompactSmemBands + 1];
     const int e = blockIdx.x;
@@ -506,6 +510,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
 // later kernels can spread all events' candidates over the whole device.
 __global__ void __launch_bounds__(kCompactThreads) cand_scan_kernel(Workspace w)
 {
+    pdl_enter();
     __shared__ int s_warp[kCompactThreads / 32];
     __shared__ int s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -548,6 +553,7 @@ __global__ void __launch_bounds__(kCompactThreads) cand_scan_kernel(Workspace w)
 // All events' candidate lists, concatenated in event order into `out` (positions from cand_base).
 __global__ void pack_candidates_kernel(Workspace w, hough_candidate *out)
 {
+    pdl_enter();
     const int total = w.cand_base[w.n_events];
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < total; f += gridDim.x * blockDim.x) {
         const int e = upper_index(w.cand_base, w.n_events, f);
@@ -561,8 +567,7 @@ cudaError_t launch_scatter(const VoteParams &p, size_t smem, int grid, cudaStrea
     cudaError_t err = cudaFuncSetAttribute(scatter_kernel<TPB, GENERAL_ONLY>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err) return err;
-    scatter_kernel<TPB, GENERAL_ONLY><<<grid, TPB, smem, stream>>>(p);
-    return cudaGetLastError();
+    return launch_chained(scatter_kernel<TPB, GENERAL_ONLY>, dim3(grid), dim3(TPB), smem, stream, p);
 }
 
 template <bool GENERAL_ONLY>
@@ -603,8 +608,7 @@ static VoteParams vote_params(const Axes &ax, const Workspace &w, const Tiling &
 template <int NL>
 cudaError_t launch_gather_nl(const GatherParams &p, int blocks, cudaStream_t stream)
 {
-    gather_kernel<NL><<<blocks, kGatherThreads, 0, stream>>>(p);
-    return cudaGetLastError();
+    return launch_chained(gather_kernel<NL>, dim3(blocks), dim3(kGatherThreads), 0, stream, p);
 }
 
 cudaError_t launch_gather(const Axes &ax, const Workspace &w, cudaStream_t stream)
@@ -666,23 +670,22 @@ cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &
     const size_t smem = (size_t)(w.band_rows + 2) * ax.n_phi;
     cudaError_t err;
     if ((err = cudaFuncSetAttribute(peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return err;
-    peaks_kernel<<<w.n_events * nb, kPeakThreads, smem, stream>>>(ax, w);
+    if ((err = launch_chained(peaks_kernel, dim3(w.n_events * nb), dim3(kPeakThreads), smem, stream, ax, w))) return err;
     return cudaGetLastError();
 }
 
 cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream)
 {
     const int single = w.n_events == 1;
-    compact_kernel<<<w.n_events, kCompactThreads, 0, stream>>>(ax, w, single);
-    if (!single) cand_scan_kernel<<<1, kCompactThreads, 0, stream>>>(w);
-    return cudaGetLastError();
+    cudaError_t err = launch_chained(compact_kernel, dim3(w.n_events), dim3(kCompactThreads), 0, stream, ax, w, single);
+    if (!err && !single) err = launch_chained(cand_scan_kernel, dim3(1), dim3(kCompactThreads), 0, stream, w);
+    return err;
 }
 
 cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream)
 {
     (void)ax;
-    pack_candidates_kernel<<<1216, 256, 0, stream>>>(w, out);
-    return cudaGetLastError();
+    return launch_chained(pack_candidates_kernel, dim3(1216), dim3(256), 0, stream, w, out);
 }
 
 cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)

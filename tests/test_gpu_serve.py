@@ -181,3 +181,25 @@ def test_memory_budget_and_config_checks(binding):
         with _server(binding, lanes=0, max_batch_events=2, max_batch_hits=20_000,
                      memory_budget=int(st.device_bytes // st.lanes * 2.5)) as two:
             assert two.stats().lanes == 2
+
+
+def test_replay_offers_every_arrival_and_polls_every_admitted_event(binding):
+    events = _events(4)
+    pool = [tuple(np.ascontiguousarray(getattr(e, k)) for k in ("r", "phi", "z", "layer")) for e in events]
+    with _server(binding) as srv:
+        start = binding.serve_clock_ns() + 20_000_000
+        arrival = start + np.arange(40, dtype=np.int64) * 500_000   # 2,000 events/s
+        res = srv.replay(pool, arrival, threads=3)
+        assert res.shape == (40,)
+        admitted = res["ticket"] != 0
+        assert admitted.sum() >= 1
+        assert np.all(res["status"][admitted] == binding.OK)
+        assert np.all(res["status"][~admitted] == binding.EBUSY)
+        assert np.all(res["arrival_ns"] == arrival)
+        assert np.all(res["done_ns"][admitted] >= res["arrival_ns"][admitted])
+        # each admitted arrival's vote count is its pool event's
+        votes = [_alone(binding, ev)[1] for ev in events]
+        for i in np.flatnonzero(admitted):
+            assert int(res["votes"][i]) == votes[i % len(pool)]
+        st = srv.stats()
+        assert st.admitted == admitted.sum() and st.completed == admitted.sum() and st.pending_tickets == 0
