@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--only", choices=["all", "plain", "batched", "served"], default="all",
                     help="run one part only (for profiling); the default runs everything")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the batch with the default kernel configuration instead of the tuned one")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="offered-load duration per served point")
     ap.add_argument("--serve-loads", default=",".join(str(int(x)) for x in eg.SERVED_OFFERED_LOADS),
                     help="offered loads (events/s), comma-separated")
@@ -411,6 +413,11 @@ def measure_batched(env, args):
     for _ in range(3):
         batch.run(*bdev, bhs, where=binding.DEVICE, stream=stream)
     torch.cuda.synchronize()
+    # the kernel configuration from the autotuner, chosen on these events before anything is timed
+    tune = batch.autotune(*bdev, bhs, where=binding.DEVICE, reps=2) if args.autotune else None
+    for _ in range(3):
+        batch.run(*bdev, bhs, where=binding.DEVICE, stream=stream)
+    torch.cuda.synchronize()
     bstats = [batch.stats(e) for e in range(len(bev))]
     b0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
     b1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.batch_steps)]
@@ -433,6 +440,10 @@ def measure_batched(env, args):
            "stage2_votes_per_batch": sum(int(st.stage2_votes) for st in bstats),
            "steps": args.batch_steps, "gpu_launches": int(launches),
            "mode": "one CUDA-graph replay per batch; kernels span all events"}
+    if tune is not None:
+        out["autotune"] = {"tiling": {f: getattr(tune.tiling, f) for f in binding.TILING_FIELDS},
+                           "ms_per_batch": tune.ms, "default_ms_per_batch": tune.default_ms,
+                           "configurations_timed": tune.tried}
     batch.close()
     return out
 
@@ -557,6 +568,14 @@ def main():
     tens = [env.torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
     ctx = binding.HoughContext(w.geometry, w.binning, max_hits=n, max_candidates=1 << 18,
                                max_members=1 << 23, device=env.local)
+    plain_tune = None
+    if args.autotune:
+        # the kernel configuration from the autotuner, timed on a one-event batch of this event
+        hs1 = np.array([0, n], dtype=np.int64)
+        with binding.HoughBatch(w.geometry, w.binning, max_events=1, max_hits=n, max_candidates=1 << 18,
+                                max_members=1 << 23, device=env.local) as tb:
+            plain_tune = tb.autotune(*tens, hs1, where=binding.DEVICE, reps=10)
+        ctx.set_tiling(**{f: getattr(plain_tune.tiling, f) for f in binding.TILING_FIELDS})
     # measured shared-atomic ceiling (conflict-free 32-lane atomicOr), before anything is timed
     smem_peak = binding.smem_or_throughput(env.local, 0, 30.0)
     smem_peak_rand = binding.smem_or_throughput(env.local, 1, 30.0)
@@ -597,7 +616,8 @@ def main():
                    "candidates_per_event": plain["candidates"], "members_per_event": plain["members"],
                    "stage2_votes_per_event": plain["stage2_votes"],
                    "mode": "plain: one event per step, hough_vote + hough_peaks + hough_stage2 (11 kernel launches)",
-                   "l2": "flushed before every timed step (256 MiB write)", "tiling": ctx.get_tiling()},
+                   "l2": "flushed before every timed step (256 MiB write)", "tiling": ctx.get_tiling(),
+                   "tiling_from": "autotuner (one-event batch, 10 replays per configuration)" if plain_tune else "default"},
         "votes_per_s": votes * plain["events_per_s"],
         "roofline": {"kernel": dominant, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
                      "unit": dk["unit"], "frac": dk["frac"], "traffic": traffic,

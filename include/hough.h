@@ -62,6 +62,7 @@ extern "C" {
 #define HOUGH_DEVERR_RADIUS    2u   /* a hit had r <= 0 or a non-finite coordinate; it cast no vote */
 #define HOUGH_DEVERR_CAND      4u   /* more candidates than max_candidates; the first ones were kept */
 #define HOUGH_DEVERR_MEMBERS   8u   /* more member hits than max_members; the member lists were cut (stage 2 still saw every member) */
+#define HOUGH_DEVERR_TIMEOUT  16u   /* an on-chip bulk copy did not complete within its bound; the accumulator is incomplete */
 
 /* Barrel detector: number of layers and the solenoid field. */
 typedef struct hough_geometry {
@@ -207,23 +208,33 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
  *
  * vote_mode HOUGH_VOTE_GATHER (default): for every layer whose hits share one radius the
  * accumulator is computed cell by cell from the per-bucket extrema of the hits' azimuth fraction
- * (identical result, no atomics), in bands of band_rows rows with the peak search fused; layers
- * whose hits lie at several radii are added by the shared-atomic scatter kernel.
+ * (identical result, no atomics).  Each CTA of the gather kernel (gather_threads threads) owns a
+ * tile of gather_rows rows x gather_cols columns and stages the slices of the bucket profile the
+ * tile reads into shared memory with bulk asynchronous copies.  Layers whose hits lie at several
+ * radii are added by the shared-atomic scatter kernel.
  * vote_mode HOUGH_VOTE_SCATTER: every layer by the shared-atomic scatter kernel (Sec. 6.1), each
  * CTA owning a tile of tile_qpt rows x tile_phi columns in shared memory.
+ * The peak search works on bands of band_rows rows.
  *
  * tile_phi must divide n_phi and be a multiple of 64; tile_qpt in 1..256; threads in
  * {128, 256, 512, 1024}; tile_qpt * tile_phi * 2 bytes must fit in shared memory; band_rows in
- * 1..16 with (band_rows + 2) * n_phi bytes of shared memory.  HOUGH_EINVAL otherwise.
+ * 1..16 with (band_rows + 2) * n_phi bytes of shared memory; gather_rows in 1..32 (0: 4);
+ * gather_cols a multiple of 64 dividing n_phi (0: the largest such up to 1024) with
+ * (n_layers rounded up to 4) * (gather_cols + 64) * 8 bytes of shared memory; gather_threads in
+ * {256, 512, 1024} (0: 512).  HOUGH_EINVAL otherwise.  Every configuration gives the same results.
  */
 #define HOUGH_VOTE_GATHER  0
 #define HOUGH_VOTE_SCATTER 1
 
 typedef struct hough_tiling {
-    int32_t tile_qpt, tile_phi, threads;
+    int32_t tile_qpt;
+    int32_t tile_phi;
+    int32_t threads;
     int32_t vote_mode;
     int32_t band_rows;
-    int32_t reserved[3];   /* must be 0 */
+    int32_t gather_rows;
+    int32_t gather_cols;
+    int32_t gather_threads;
 } hough_tiling;
 
 int hough_set_tiling(hough_ctx *ctx, const hough_tiling *tiling);
@@ -309,6 +320,35 @@ int hough_batch_stats(hough_batch *batch, int32_t event, hough_stats *out, void 
 
 /* The accumulator of one event of the last run.  Synchronises `stream`. */
 int hough_batch_accumulator(hough_batch *batch, int32_t event, uint16_t *out, int where, void *stream);
+
+/*
+ * Autotuning of a batch's kernel configuration (the paper tuned per target by hand with
+ * preprocessor constants, Sec. 6.1).  hough_batch_autotune times whole batches of the given events
+ * (inputs as hough_batch_run; host inputs are copied to the device once, outside the timing) for
+ * a sweep of configurations -- the gather tile (rows x columns x threads), the shared-atomic
+ * scatter tile of the paper's design (64..256 q/pT rows x 256..512 phi0 columns x threads), then
+ * the peak band height -- each as `reps` (1..100) graph replays after one untimed replay, checks
+ * that all give the same candidate total (HOUGH_EDEVICE otherwise), and applies the fastest to the
+ * batch.  With a cache file (may be NULL) an entry for this GPU, SM count, axes and batch size
+ * (rounded up to a power of two) is applied without timing; a new result is appended to the file
+ * (one text line per entry).  Synchronises the device.
+ */
+typedef struct hough_tune_result {
+    hough_tiling tiling;     /* the configuration applied */
+    float ms;                /* its mean time per batch */
+    float default_ms;        /* the default configuration's (0 when read from the cache) */
+    int32_t tried;           /* configurations timed */
+    int32_t from_cache;      /* 1 when the configuration came from the cache file */
+} hough_tune_result;
+
+int hough_batch_autotune(hough_batch *batch, const hough_geometry *geometry, const hough_binning *binning,
+                         const float *r, const float *phi, const float *z, const uint8_t *layer,
+                         const int64_t *hit_start, int32_t n_events, int where, int32_t reps,
+                         const char *cache_path, hough_tune_result *out);
+
+/* The cached configuration for these axes, this device and batch size: HOUGH_ENOTREADY when none. */
+int hough_tune_lookup(const char *cache_path, const hough_geometry *geometry, const hough_binning *binning,
+                      int device, int32_t n_events, hough_tiling *out);
 
 /*
  * Served mode: a trigger-style request loop with continuous batching (the paper runs events one at

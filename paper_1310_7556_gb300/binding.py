@@ -65,9 +65,12 @@ class Timing(ctypes.Structure):
                                               "clear_ms", "count_ms", "table_ms", "scan_ms", "sort_ms")]
 
 
+TILING_FIELDS = ("tile_qpt", "tile_phi", "threads", "vote_mode", "band_rows", "gather_rows", "gather_cols",
+                 "gather_threads")
+
+
 class Tiling(ctypes.Structure):
-    _fields_ = [("tile_qpt", ctypes.c_int32), ("tile_phi", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("vote_mode", ctypes.c_int32), ("band_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+    _fields_ = [(n, ctypes.c_int32) for n in TILING_FIELDS]
 
 
 VOTE_GATHER, VOTE_SCATTER = 0, 1
@@ -100,6 +103,11 @@ class EventView(ctypes.Structure):
 
 
 SERVE_FAULT_HOLD, SERVE_FAULT_STALL, SERVE_FAULT_ALLOC = 1, 2, 3
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tiling", Tiling), ("ms", ctypes.c_float), ("default_ms", ctypes.c_float),
+                ("tried", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
 
 
 CANDIDATE_DTYPE = np.dtype([("iq", np.uint32), ("jphi", np.uint32), ("mask", np.uint32),
@@ -141,6 +149,10 @@ _SIGNATURES = {
     "hough_batch_candidates": ([_P, _P, _I64, _P, ctypes.c_int, _P], ctypes.c_int),
     "hough_batch_stats": ([_P, _I32, ctypes.POINTER(Stats), _P], ctypes.c_int),
     "hough_batch_accumulator": ([_P, _I32, _P, ctypes.c_int, _P], ctypes.c_int),
+    "hough_batch_autotune": ([_P, ctypes.POINTER(Geometry), ctypes.POINTER(Binning), _P, _P, _P, _P, _P, _I32,
+                              ctypes.c_int, _I32, ctypes.c_char_p, ctypes.POINTER(TuneResult)], ctypes.c_int),
+    "hough_tune_lookup": ([ctypes.c_char_p, ctypes.POINTER(Geometry), ctypes.POINTER(Binning), ctypes.c_int, _I32,
+                           ctypes.POINTER(Tiling)], ctypes.c_int),
     "hough_serve_create": ([ctypes.POINTER(Geometry), ctypes.POINTER(Binning), ctypes.POINTER(ServeConfig),
                             ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hough_serve_destroy": ([_P], None),
@@ -330,12 +342,13 @@ class HoughContext:
 
     # -- tiling -------------------------------------------------------------------------------
     def set_tiling(self, tile_qpt: int = None, tile_phi: int = None, threads: int = None,
-                   vote_mode: int = None, band_rows: int = None):
+                   vote_mode: int = None, band_rows: int = None, gather_rows: int = None,
+                   gather_cols: int = None, gather_threads: int = None):
         """Change the kernel configuration; unspecified fields keep their current value."""
-        cur = self.get_tiling()
-        new = dict(cur)
+        new = self.get_tiling()
         for k, v in dict(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, vote_mode=vote_mode,
-                         band_rows=band_rows).items():
+                         band_rows=band_rows, gather_rows=gather_rows, gather_cols=gather_cols,
+                         gather_threads=gather_threads).items():
             if v is not None:
                 new[k] = v
         t = Tiling(**new)
@@ -344,8 +357,7 @@ class HoughContext:
     def get_tiling(self) -> dict:
         t = Tiling()
         _check(self._lib.hough_get_tiling(self._h, ctypes.byref(t)))
-        return dict(tile_qpt=t.tile_qpt, tile_phi=t.tile_phi, threads=t.threads, vote_mode=t.vote_mode,
-                    band_rows=t.band_rows)
+        return {n: getattr(t, n) for n in TILING_FIELDS}
 
 
 class HoughBatch:
@@ -357,6 +369,7 @@ class HoughBatch:
         self._lib = lib
         self.binning = binning
         g, b = make_geometry(geometry), make_binning(binning)
+        self._geometry, self._binning = g, b
         lim = BatchLimits(max_events=max_events, max_candidates=max_candidates, max_hits=max_hits,
                           max_members=max_members, reserved=0)
         h = _P()
@@ -378,8 +391,10 @@ class HoughBatch:
     def __exit__(self, *exc):
         self.close()
 
-    def set_tiling(self, tile_qpt=16, tile_phi=256, threads=256, vote_mode=VOTE_GATHER, band_rows=1):
-        t = Tiling(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, vote_mode=vote_mode, band_rows=band_rows)
+    def set_tiling(self, tile_qpt=16, tile_phi=256, threads=256, vote_mode=VOTE_GATHER, band_rows=1,
+                   gather_rows=0, gather_cols=0, gather_threads=0):
+        t = Tiling(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, vote_mode=vote_mode, band_rows=band_rows,
+                   gather_rows=gather_rows, gather_cols=gather_cols, gather_threads=gather_threads)
         _check(self._lib.hough_batch_set_tiling(self._h, ctypes.byref(t)))
 
     def run(self, r, phi, z, layer, hit_start, where=HOST, stream=None):
@@ -401,6 +416,20 @@ class HoughBatch:
         cat = lambda name, dt: np.concatenate([getattr(e, name) for e in events]).astype(dt)
         self.run(cat("r", np.float32), cat("phi", np.float32), cat("z", np.float32), cat("layer", np.uint8), hs,
                  stream=stream)
+
+    def autotune(self, r, phi, z, layer, hit_start, where=HOST, reps=3, cache_path=None) -> TuneResult:
+        """hough_batch_autotune on these events; applies and returns the fastest configuration."""
+        hit_start = np.ascontiguousarray(hit_start, dtype=np.int64)
+        if where == HOST and isinstance(r, np.ndarray):
+            r, phi, z = (np.ascontiguousarray(a, dtype=np.float32) for a in (r, phi, z))
+            layer = np.ascontiguousarray(layer, dtype=np.uint8)
+        res = TuneResult()
+        path = cache_path.encode() if cache_path else None
+        _check(self._lib.hough_batch_autotune(self._h, ctypes.byref(self._geometry), ctypes.byref(self._binning),
+                                              _ptr(r), _ptr(phi), _ptr(z), _ptr(layer), _ptr(hit_start),
+                                              hit_start.shape[0] - 1, where, reps, path, ctypes.byref(res)))
+        self.n_events = 0
+        return res
 
     def candidates(self, cap=None, stream=None):
         """(candidates of all events concatenated, offsets[n_events + 1])."""
@@ -508,3 +537,12 @@ class HoughServer:
 
     def inject(self, fault: int, on: bool = True):
         _check(self._lib.hough_serve_inject(self._h, int(fault), int(bool(on))))
+
+
+def tune_lookup(cache_path, geometry, binning, n_events, device=0):
+    """The cached tiling (a dict) for these axes, device and batch size, or None."""
+    g, b = make_geometry(geometry), make_binning(binning)
+    t = Tiling()
+    rc = _check(load().hough_tune_lookup(cache_path.encode(), ctypes.byref(g), ctypes.byref(b), device, n_events,
+                                         ctypes.byref(t)), allow=(ENOTREADY,))
+    return None if rc == ENOTREADY else {n: getattr(t, n) for n in TILING_FIELDS}

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhough.so")
 
-SOURCES = ["hough_api.cu", "stage_kernels.cu", "vote_kernel.cu", "confirm_kernels.cu", "microbench.cu", "static_vote.cu", "batch.cu", "serve.cu"]
+SOURCES = ["hough_api.cu", "stage_kernels.cu", "vote_kernel.cu", "confirm_kernels.cu", "microbench.cu", "static_vote.cu", "batch.cu", "serve.cu", "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread", "-I" + INCLUDE]
 

@@ -78,7 +78,7 @@ struct hough_batch {
     {
         cudaError_t e;
         if ((e = launch_stage(ax, w, s))) return e;
-        if (tiling.vote_mode == HOUGH_VOTE_GATHER && (e = launch_gather(ax, w, s))) return e;
+        if (tiling.vote_mode == HOUGH_VOTE_GATHER && (e = launch_gather(ax, w, tiling, s))) return e;
         if ((e = launch_scatter(ax, w, tiling, refine_eps, tiling.vote_mode == HOUGH_VOTE_GATHER, s))) return e;
         if ((e = launch_band_peaks(ax, w, tiling, s))) return e;
         if ((e = launch_compact(ax, w, s))) return e;
@@ -172,7 +172,7 @@ int hough_batch_set_tiling(hough_batch *b, const hough_tiling *t)
     if (!b) return bfail(HOUGH_EINVAL, "batch is required");
     int rc = check_tiling_for(b->ax, b->device, t);
     if (rc) return rc;
-    b->tiling = Tiling{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows};
+    b->tiling = resolve_tiling(b->ax, t);
     b->w.band_rows = t->band_rows;
     b->w.band_cap = band_capacity(b->ax, t->band_rows);
     // captured graphs hold the old configuration

@@ -145,10 +145,28 @@ Axes make_axes_impl(const hough_geometry *g, const hough_binning *b)
     return ax;
 }
 
+int default_gather_cols(const Axes &ax)
+{
+    int cols = std::min(ax.n_phi, 1024);
+    cols -= cols % 64;
+    while (ax.n_phi % cols) cols -= 64;
+    return cols;
+}
+
+// A public tiling with its gather defaults (zero fields) filled in.
+Tiling resolve_tiling_impl(const Axes &ax, const hough_tiling *t)
+{
+    Tiling r{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows,
+             t->gather_rows, t->gather_cols, t->gather_threads};
+    if (!r.gather_rows) r.gather_rows = 4;
+    if (!r.gather_cols) r.gather_cols = default_gather_cols(ax);
+    if (!r.gather_threads) r.gather_threads = 512;
+    return r;
+}
+
 int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
 {
     if (!t) return fail(HOUGH_EINVAL, "tiling is required");
-    if (t->reserved[0] || t->reserved[1] || t->reserved[2]) return fail(HOUGH_EINVAL, "reserved fields must be 0");
     if (t->tile_qpt < 1 || t->tile_qpt > 256) return fail(HOUGH_EINVAL, "tile_qpt must be 1..256");
     if (t->tile_phi < 64 || t->tile_phi % 64 || ax.n_phi % t->tile_phi)
         return fail(HOUGH_EINVAL, "tile_phi must be a multiple of 64 dividing n_phi");
@@ -157,7 +175,12 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
     if (t->vote_mode != HOUGH_VOTE_GATHER && t->vote_mode != HOUGH_VOTE_SCATTER)
         return fail(HOUGH_EINVAL, "vote_mode must be HOUGH_VOTE_GATHER or HOUGH_VOTE_SCATTER");
     if (t->band_rows < 1 || t->band_rows > 16) return fail(HOUGH_EINVAL, "band_rows must be 1..16");
-    Tiling tt{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows};
+    if (t->gather_rows < 0 || t->gather_rows > 32) return fail(HOUGH_EINVAL, "gather_rows must be 0..32");
+    if (t->gather_cols && (t->gather_cols < 64 || t->gather_cols % 64 || ax.n_phi % t->gather_cols))
+        return fail(HOUGH_EINVAL, "gather_cols must be 0 or a multiple of 64 dividing n_phi");
+    if (t->gather_threads && t->gather_threads != 256 && t->gather_threads != 512 && t->gather_threads != 1024)
+        return fail(HOUGH_EINVAL, "gather_threads must be 0, 256, 512 or 1024");
+    const Tiling tt = resolve_tiling_impl(ax, t);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (vote_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
@@ -166,6 +189,9 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
     if ((size_t)(t->band_rows + 2) * ax.n_phi + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "band of %d rows needs %zu bytes of shared memory, the device allows %d",
                     t->band_rows, (size_t)(t->band_rows + 2) * ax.n_phi, max_smem);
+    if (gather_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
+        return fail(HOUGH_EINVAL, "gather tile needs %zu bytes of shared memory, the device allows %d",
+                    gather_smem_bytes(ax, tt), max_smem);
     return HOUGH_OK;
 }
 
@@ -178,6 +204,9 @@ Tiling default_tiling_impl(const Axes &ax)
     t.threads = 256;
     t.vote_mode = HOUGH_VOTE_GATHER;
     t.band_rows = 1;
+    t.gather_rows = 4;
+    t.gather_cols = default_gather_cols(ax);
+    t.gather_threads = 512;
     return t;
 }
 
@@ -232,7 +261,7 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1 | (0xF << 8); }
     CU(launch_stage(c->ax, c->w, s, c->timing ? c->ev + 8 : nullptr), "stage kernels");
     if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
-    if (c->tiling.vote_mode == HOUGH_VOTE_GATHER) CU(launch_gather(c->ax, c->w, s), "gather kernel");
+    if (c->tiling.vote_mode == HOUGH_VOTE_GATHER) CU(launch_gather(c->ax, c->w, c->tiling, s), "gather kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
     CU(launch_scatter(c->ax, c->w, c->tiling, c->refine_eps, c->tiling.vote_mode == HOUGH_VOTE_GATHER, s), "vote kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[3], s), "event"); c->timed |= 8; }
@@ -253,6 +282,12 @@ int read_stats(hough_ctx *c, cudaStream_t s)
 Axes hough::make_axes(const hough_geometry *g, const hough_binning *b) { return make_axes_impl(g, b); }
 int hough::check_geometry_binning(const hough_geometry *g, const hough_binning *b) { return check_binning(g, b); }
 int hough::check_tiling_for(const Axes &ax, int device, const hough_tiling *t) { return check_tiling_impl(ax, device, t); }
+Tiling hough::resolve_tiling(const Axes &ax, const hough_tiling *t) { return resolve_tiling_impl(ax, t); }
+void hough::public_tiling(const Tiling &t, hough_tiling *out)
+{
+    *out = hough_tiling{t.tile_qpt, t.tile_phi, t.threads, t.vote_mode, t.band_rows,
+                        t.gather_rows, t.gather_cols, t.gather_threads};
+}
 Tiling hough::default_tiling_for(const Axes &ax) { return default_tiling_impl(ax); }
 size_t hough::band_list_entries(const Axes &ax) { return band_list_entries_impl(ax); }
 int hough::check_host_hits_for(const Axes &ax, const float *r, const float *phi, const float *z, const uint8_t *layer,
@@ -502,7 +537,7 @@ int hough_set_tiling(hough_ctx *c, const hough_tiling *t)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     int rc = check_tiling_impl(c->ax, c->device, t);
     if (rc) return rc;
-    c->tiling = Tiling{t->tile_qpt, t->tile_phi, t->threads, t->vote_mode, t->band_rows};
+    c->tiling = resolve_tiling(c->ax, t);
     return HOUGH_OK;
 }
 
@@ -557,12 +592,7 @@ int hough_microbench_smem_or(int device, int pattern, double ms, double *atomics
 int hough_get_tiling(const hough_ctx *c, hough_tiling *t)
 {
     if (!c || !t) return fail(HOUGH_EINVAL, "bad arguments");
-    t->tile_qpt = c->tiling.tile_qpt;
-    t->tile_phi = c->tiling.tile_phi;
-    t->threads = c->tiling.threads;
-    t->vote_mode = c->tiling.vote_mode;
-    t->band_rows = c->tiling.band_rows;
-    t->reserved[0] = t->reserved[1] = t->reserved[2] = 0;
+    public_tiling(c->tiling, t);
     return HOUGH_OK;
 }
 

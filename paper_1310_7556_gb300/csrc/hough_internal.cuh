@@ -155,7 +155,8 @@ struct Workspace {
 struct Tiling {
     int tile_qpt, tile_phi, threads;
     int vote_mode;                // HOUGH_VOTE_GATHER or HOUGH_VOTE_SCATTER
-    int band_rows;                // rows per band of the peak search (and of the gather kernel)
+    int band_rows;                // rows per band of the peak search
+    int gather_rows, gather_cols, gather_threads;   // tile of the gather kernel (0: its default)
 };
 
 constexpr int kPeakThreads = 256;
@@ -191,7 +192,7 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
                         cudaStream_t stream);
 cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
 // The pieces of launch_vote and launch_peaks, for callers that time them separately.
-cudaError_t launch_gather(const Axes &ax, const Workspace &w, cudaStream_t stream);
+cudaError_t launch_gather(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
 cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps, bool general_only,
                            cudaStream_t stream);
 cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
@@ -210,6 +211,9 @@ Axes make_axes(const hough_geometry *g, const hough_binning *b);
 int check_geometry_binning(const hough_geometry *g, const hough_binning *b);
 int check_tiling_for(const Axes &ax, int device, const hough_tiling *t);
 Tiling default_tiling_for(const Axes &ax);
+Tiling resolve_tiling(const Axes &ax, const hough_tiling *t);   // gather defaults filled in
+void public_tiling(const Tiling &t, hough_tiling *out);
+size_t gather_smem_bytes(const Axes &ax, const Tiling &t);
 size_t band_list_entries(const Axes &ax);
 int check_host_hits_for(const Axes &ax, const float *r, const float *phi, const float *z, const uint8_t *layer,
                         int64_t n);
@@ -264,6 +268,52 @@ inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 bloc
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Bulk asynchronous copies (TMA, untiled form) from global to shared memory, completing on an
+// mbarrier.  Both addresses must be 16-byte aligned and the size a multiple of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `phase` of the mbarrier for at most `max_cycles` SM cycles; false when the bound
+// ran out (the caller reports it and must not use the copied data).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, long long max_cycles)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, phase))
+        if (clock64() - t0 > max_cycles) return false;
+    return true;
 }
 
 // Error-free transformations of FP32 arithmetic (Knuth's two-sum, and the product with its

@@ -137,6 +137,9 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
     t.threads = 256;
     t.vote_mode = HOUGH_VOTE_SCATTER;   // the shared-atomic vote kernel alone: no bucket profile needed
     t.band_rows = 4;
+    t.gather_rows = 4;
+    t.gather_cols = t.tile_phi;
+    t.gather_threads = 512;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The array keeps the previous call's contents: reset what the kernels expect to start at zero.

@@ -26,6 +26,7 @@
 // Peaks: candidates of each band of band_rows rows (one row by default) go to a band list in
 // raster order; a per-event scan then concatenates the band lists into the raster-ordered list.
 #include <algorithm>
+#include <climits>
 
 #include "hough_internal.cuh"
 
@@ -42,8 +43,6 @@ struct VoteParams {
 };
 
 constexpr int kMaxRanges = 2 * HOUGH_MAX_LAYERS;
-constexpr int kGatherThreads = 512;
-constexpr int kGatherRows = 4;
 constexpr int kCompactThreads = 1024;
 
 // Layers of the batch: bit l of *uniform_out is set when layer l takes the table path; bit l of
@@ -271,68 +270,49 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     if (threadIdx.x == 0 && s_refined) atomicAdd(&p.w.stats[e].refined_votes, s_refined);
 }
 
-// Layer bits of the 8 cells j0..j0+7 of one row for one layer: cell j0 + c takes bucket entry
-// J1 + c (J1 = (j0 + I) mod Nphi) and is set when .x > gb or .y > ~gb.  The 8 entries are read
-// as 16-byte vectors from the even-aligned window [J1 & ~1, (J1 & ~1) + 10), which the repeated
-// buckets at the end of each layer keep from wrapping.
-__device__ __forceinline__ unsigned gather8(const uint2 *prof_l, int J1, unsigned gb)
-{
-    const uint4 *v = reinterpret_cast<const uint4 *>(prof_l + (J1 & ~1));
-    uint4 q[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] = __ldg(&v[k]);
-    // entries e[0..9]: e[2k] = (q[k].x, q[k].y), e[2k+1] = (q[k].z, q[k].w)
-    const unsigned ngb = ~gb;
-    unsigned bits = 0u;
-    if (J1 & 1) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int t = c + 1;
-            const unsigned x = (t & 1) ? q[t >> 1].z : q[t >> 1].x;
-            const unsigned y = (t & 1) ? q[t >> 1].w : q[t >> 1].y;
-            bits |= (unsigned)((x > gb) | (y > ngb)) << c;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const unsigned x = (c & 1) ? q[c >> 1].z : q[c >> 1].x;
-            const unsigned y = (c & 1) ? q[c >> 1].w : q[c >> 1].y;
-            bits |= (unsigned)((x > gb) | (y > ngb)) << c;
-        }
-    }
-    return bits;
-}
-
-// Gather: one tile of kGatherRows rows x `cols` columns of the accumulator from the per-bucket f
-// extrema and the table.  Each thread owns 8 consecutive cells of one row (one 16-byte store); the
-// layer loop is unrolled over the NL layers with every layer's loads issued unconditionally (a
-// layer that does not vote on the row reads its zero-shift window and is masked off), so all of a
-// thread's loads can be in flight at once.
+// Gather: one tile of `rows` rows x `cols` columns of the accumulator from the per-bucket f
+// extrema and the table.  On row i a layer's cells read the bucket entries shifted by I_i, which
+// grows with i, so the tile reads one contiguous window of each layer's entries:
+// [c0 + min_i I_i, c0 + cols + 2 + max_i I_i).  Thread 0 copies every layer's window into shared
+// memory with bulk asynchronous copies (one or two pieces, the second when the window wraps
+// around phi) completing on one mbarrier, while the other threads wait; a layer whose window does
+// not fit its slot reads global memory instead.  A warp then takes a strip of up to 256 cells of a
+// row, 8 per lane at a stride of 32; the staging put bucket J+1's smallest fraction beside bucket
+// J's largest, so a layer's bit of cell j reads the one 8-byte entry j + I: conflict-free shared
+// loads, one per (cell, voting layer), the layer's shift and threshold read once per 8 cells.
 struct GatherParams {
     Axes ax;
     Workspace w;
-    int cols, col_tiles, tiles_per_event;
+    int rows, cols, col_tiles, tiles_per_event;
+    int cap;   // entries of a layer's staging slot (even)
 };
 
-template <int NL>
-__global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherParams p)
+constexpr int kGatherRowsMax = 32;
+constexpr long long kCopyWaitCycles = 2000000000LL;   // about a second: bulk copies take microseconds
+
+template <int NL, int TPB>
+__global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
 {
     pdl_enter();
-    __shared__ int rowI[kGatherRows * 16];
-    __shared__ unsigned rowG[kGatherRows * 16];
-    __shared__ unsigned rowMask[kGatherRows];
+    extern __shared__ __align__(16) unsigned char gather_smem[];
+    __shared__ int rowI[kGatherRowsMax * 16];
+    __shared__ unsigned rowG[kGatherRowsMax * 16];
+    __shared__ unsigned rowMask[kGatherRowsMax];
+    __shared__ int s_wbase[16], s_wlen[16];
+    __shared__ unsigned s_staged;
+    __shared__ __align__(8) uint64_t s_bar;
     const Axes &ax = p.ax;
     const Workspace &w = p.w;
     const int e = blockIdx.x / p.tiles_per_event;
     const int t = blockIdx.x - e * p.tiles_per_event;
     const int rt = t / p.col_tiles, ct = t - rt * p.col_tiles;
-    const int i0 = rt * kGatherRows, c0 = ct * p.cols;
-    const int nrows = min(kGatherRows, ax.n_qpt - i0);
+    const int i0 = rt * p.rows, c0 = ct * p.cols;
+    const int nrows = min(p.rows, ax.n_qpt - i0);
     const int L = ax.n_layers, nphi = ax.n_phi;
 
-    // per (row, layer): the table entry and whether the layer votes on that row by the gather;
-    // whole warps take part in the ballot
-    for (int q = threadIdx.x; q < kGatherRows * 16; q += kGatherThreads) {
+    // per (row, layer): the table entry and whether the layer votes on that row by the gather
+    // (whole warps, so that the ballot sees full warps; TPB is a multiple of 32)
+    for (int q = threadIdx.x; q < ((p.rows * 16 + 31) & ~31); q += TPB) {
         const int rr = q >> 4, l = q & 15, i = i0 + rr;
         int I = 0;
         unsigned gb = 0u, valid = 0u;
@@ -351,36 +331,111 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(GatherParams p)
         if ((threadIdx.x & 15) == 0) rowMask[rr] = m & 0xFFFFu;
     }
     __syncthreads();
+    // each layer's window of bucket entries (unwrapped indices, start even)
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        bool staged = false;
+        if (l < L) {
+            int lo = INT_MAX, hi = INT_MIN;
+            for (int rr = 0; rr < nrows; ++rr)
+                if ((rowMask[rr] >> l) & 1u) {
+                    lo = min(lo, rowI[rr * 16 + l]);
+                    hi = max(hi, rowI[rr * 16 + l]);
+                }
+            if (lo <= hi) {
+                const int ws = (c0 + lo) - ((c0 + lo) & 1);
+                int len = c0 + p.cols + 2 + hi - ws;
+                len += len & 1;
+                staged = len <= p.cap && len <= nphi;
+                s_wbase[l] = ws;
+                s_wlen[l] = len;
+            }
+        }
+        const unsigned sm = __ballot_sync(0xFFFFFFFFu, staged);
+        if (l == 0) {
+            s_staged = sm;
+            if (sm) mbar_init(&s_bar, 1);
+        }
+    }
+    __syncthreads();
+    const unsigned staged = s_staged;
     const uint2 *prof = w.prof + (int64_t)e * prof_event_entries(ax);
     const int pstride = prof_stride(ax);
+    uint2 *win = reinterpret_cast<uint2 *>(gather_smem);
+    if (staged) {
+        if (threadIdx.x == 0) {
+            unsigned bytes = 0;
+            for (int l = 0; l < L; ++l)
+                if ((staged >> l) & 1u) bytes += 8u * (unsigned)s_wlen[l];
+            mbar_arrive_expect(&s_bar, bytes);
+            for (int l = 0; l < L; ++l) {
+                if (!((staged >> l) & 1u)) continue;
+                const int len = s_wlen[l];
+                const int a = ((s_wbase[l] % nphi) + nphi) % nphi;   // even, as nphi is
+                const uint2 *src = prof + (int64_t)l * pstride;
+                uint2 *dst = win + (int64_t)l * p.cap;
+                const int first = min(len, nphi - a);
+                bulk_copy_g2s(dst, src + a, 8u * (unsigned)first, &s_bar);
+                if (first < len) bulk_copy_g2s(dst + first, src, 8u * (unsigned)(len - first), &s_bar);
+            }
+        }
+        const bool ok = mbar_wait_bounded(&s_bar, 0, kCopyWaitCycles);
+        if (!__syncthreads_and(ok)) {
+            // the copies did not land in time: report it, give them one more bound, write nothing
+            if (threadIdx.x == 0) atomicOr(&w.stats[e].device_error, HOUGH_DEVERR_TIMEOUT);
+            mbar_wait_bounded(&s_bar, 0, kCopyWaitCycles);
+            return;
+        }
+    }
+    // one warp per strip of up to 256 cells of a row, lane t taking cells t, t + 32, ...: a layer's
+    // bit of cell j is the comparison of bucket entry j + I alone, so each of the lane's loads is
+    // one 8-byte entry and a warp's loads cover consecutive entries
+    constexpr int kCells = 8;
     uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
-    const int per_row = p.cols >> 3;
-    const int nq = nrows * per_row;
-    for (int q = threadIdx.x; q < nq; q += kGatherThreads) {
-        const int rr = q / per_row;
-        const int j0 = c0 + (q - rr * per_row) * 8;
+    const int kc = min(kCells, p.cols >> 5);   // cells per lane (cols is a multiple of 64)
+    const int strip = kc * 32;
+    const int per_row = p.cols / strip;
+    const int nstrips = nrows * per_row;
+    const int lane = threadIdx.x & 31;
+    for (int sidx = threadIdx.x >> 5; sidx < nstrips; sidx += TPB / 32) {
+        const int rr = sidx / per_row;
+        const int jb = c0 + (sidx - rr * per_row) * strip + lane;
         const unsigned vm = rowMask[rr];
         const int *rI = rowI + rr * 16;
         const unsigned *rG = rowG + rr * 16;
-        unsigned bits[NL];
+        unsigned mask[kCells];
+#pragma unroll
+        for (int c = 0; c < kCells; ++c) mask[c] = 0u;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-            const int J1 = wrap_col(j0 + rI[l], nphi);
-            bits[l] = gather8(prof + (int64_t)l * pstride, J1, rG[l]) & (0u - ((vm >> l) & 1u));
-        }
-        unsigned lo[4] = {0u, 0u, 0u, 0u}, hi[4] = {0u, 0u, 0u, 0u};
+            if (!((vm >> l) & 1u)) continue;   // the same for the whole warp: the row's layers
+            const int I = rI[l];
+            const unsigned gb = rG[l], ngb = ~gb;
+            if ((staged >> l) & 1u) {
+                const uint2 *src = win + (int64_t)l * p.cap + (jb + I - s_wbase[l]);   // inside the window
 #pragma unroll
-        for (int l = 0; l < NL; ++l) {
+                for (int c = 0; c < kCells; ++c)
+                    if (c < kc) {
+                        const uint2 v = src[32 * c];
+                        mask[c] |= (unsigned)((v.x > gb) | (v.y > ngb)) << l;
+                    }
+            } else {
+                const uint2 *src = prof + (int64_t)l * pstride;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                lo[k] |= ((bits[l] >> (2 * k)) & 1u) << l;
-                hi[k] |= ((bits[l] >> (2 * k + 1)) & 1u) << l;
+                for (int c = 0; c < kCells; ++c)
+                    if (c < kc) {
+                        const uint2 v = __ldg(&src[wrap_col(jb + 32 * c + I, nphi)]);
+                        mask[c] |= (unsigned)((v.x > gb) | (v.y > ngb)) << l;
+                    }
             }
         }
-        *reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + j0) =
-            make_uint4(lo[0] | (hi[0] << 16), lo[1] | (hi[1] << 16), lo[2] | (hi[2] << 16), lo[3] | (hi[3] << 16));
+        uint16_t *row = M + (int64_t)(i0 + rr) * nphi + jb;
+#pragma unroll
+        for (int c = 0; c < kCells; ++c)
+            if (c < kc) row[32 * c] = (uint16_t)mask[c];
     }
 }
+
 
 // Peak search of one band of band_rows rows from the accumulator (plus a halo row on each side).
 __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w)
@@ -606,42 +661,52 @@ static VoteParams vote_params(const Axes &ax, const Workspace &w, const Tiling &
 }
 
 template <int NL>
-cudaError_t launch_gather_nl(const GatherParams &p, int blocks, cudaStream_t stream)
+cudaError_t launch_gather_nl(const GatherParams &p, int threads, size_t smem, int blocks, cudaStream_t stream)
 {
-    return launch_chained(gather_kernel<NL>, dim3(blocks), dim3(kGatherThreads), 0, stream, p);
+    cudaError_t err;
+    switch (threads) {
+    case 256:
+        if ((err = cudaFuncSetAttribute(gather_kernel<NL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+            return err;
+        return launch_chained(gather_kernel<NL, 256>, dim3(blocks), dim3(256), smem, stream, p);
+    case 1024:
+        if ((err = cudaFuncSetAttribute(gather_kernel<NL, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+            return err;
+        return launch_chained(gather_kernel<NL, 1024>, dim3(blocks), dim3(1024), smem, stream, p);
+    default:
+        if ((err = cudaFuncSetAttribute(gather_kernel<NL, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+            return err;
+        return launch_chained(gather_kernel<NL, 512>, dim3(blocks), dim3(512), smem, stream, p);
+    }
 }
 
-cudaError_t launch_gather(const Axes &ax, const Workspace &w, cudaStream_t stream)
+size_t gather_smem_bytes(const Axes &ax, const Tiling &t)
+{
+    return (size_t)ax.n_layers * (size_t)(t.gather_cols + 64) * sizeof(uint2);
+}
+
+static cudaError_t launch_gather_tiled(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
 {
     GatherParams p;
     p.ax = ax;
     p.w = w;
-    // the widest tile of at most 8 * kGatherThreads / kGatherRows cells per row that divides Nphi
-    int cols = std::min(ax.n_phi, 8 * kGatherThreads / kGatherRows);
-    cols -= cols % 64;
-    while (ax.n_phi % cols) cols -= 64;
-    p.cols = cols;
-    p.col_tiles = ax.n_phi / cols;
-    p.tiles_per_event = ((ax.n_qpt + kGatherRows - 1) / kGatherRows) * p.col_tiles;
+    p.rows = t.gather_rows;
+    p.cols = t.gather_cols;
+    p.cap = t.gather_cols + 64;
+    p.col_tiles = ax.n_phi / p.cols;
+    p.tiles_per_event = ((ax.n_qpt + p.rows - 1) / p.rows) * p.col_tiles;
     const int blocks = w.n_events * p.tiles_per_event;
-    switch (ax.n_layers) {
-    case 1: return launch_gather_nl<1>(p, blocks, stream);
-    case 2: return launch_gather_nl<2>(p, blocks, stream);
-    case 3: return launch_gather_nl<3>(p, blocks, stream);
-    case 4: return launch_gather_nl<4>(p, blocks, stream);
-    case 5: return launch_gather_nl<5>(p, blocks, stream);
-    case 6: return launch_gather_nl<6>(p, blocks, stream);
-    case 7: return launch_gather_nl<7>(p, blocks, stream);
-    case 8: return launch_gather_nl<8>(p, blocks, stream);
-    case 9: return launch_gather_nl<9>(p, blocks, stream);
-    case 10: return launch_gather_nl<10>(p, blocks, stream);
-    case 11: return launch_gather_nl<11>(p, blocks, stream);
-    case 12: return launch_gather_nl<12>(p, blocks, stream);
-    case 13: return launch_gather_nl<13>(p, blocks, stream);
-    case 14: return launch_gather_nl<14>(p, blocks, stream);
-    case 15: return launch_gather_nl<15>(p, blocks, stream);
-    default: return launch_gather_nl<16>(p, blocks, stream);
-    }
+    const size_t smem = gather_smem_bytes(ax, t);
+    // layer loops unrolled to the next multiple of four
+    if (ax.n_layers <= 4) return launch_gather_nl<4>(p, t.gather_threads, smem, blocks, stream);
+    if (ax.n_layers <= 8) return launch_gather_nl<8>(p, t.gather_threads, smem, blocks, stream);
+    if (ax.n_layers <= 12) return launch_gather_nl<12>(p, t.gather_threads, smem, blocks, stream);
+    return launch_gather_nl<16>(p, t.gather_threads, smem, blocks, stream);
+}
+
+cudaError_t launch_gather(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
+{
+    return launch_gather_tiled(ax, w, t, stream);
 }
 
 cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps, bool general_only,
@@ -659,7 +724,7 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
 {
     if (t.vote_mode == HOUGH_VOTE_SCATTER) return launch_scatter(ax, w, t, refine_eps, false, stream);
     // gather every table layer, then let the scatter kernel add the layers whose radii differ
-    cudaError_t err = launch_gather(ax, w, stream);
+    cudaError_t err = launch_gather(ax, w, t, stream);
     if (err) return err;
     return launch_scatter(ax, w, t, refine_eps, true, stream);
 }

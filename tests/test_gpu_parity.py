@@ -93,10 +93,15 @@ def test_device_pointers_match_host_path(binding):
 @pytest.mark.parametrize("tiling", [(1, 64, 128, 1), (7, 128, 256, 1), (16, 256, 256, 1), (32, 512, 512, 1),
                                     (64, 1024, 1024, 1), (3, 2048, 128, 1), (16, 256, 256, 0, 1),
                                     (16, 256, 256, 0, 3), (16, 256, 256, 0, 8), (16, 256, 256, 0, 16),
-                                    (16, 256, 256, 1, 5)])
+                                    (16, 256, 256, 1, 5), (16, 256, 256, 0, 1, 1, 64, 256),
+                                    (16, 256, 256, 0, 1, 3, 128, 512), (16, 256, 256, 0, 1, 5, 512, 1024),
+                                    (16, 256, 256, 0, 2, 7, 256, 256), (16, 256, 256, 0, 1, 8, 2048, 512),
+                                    (16, 256, 256, 0, 1, 16, 256, 512), (16, 256, 256, 0, 4, 32, 128, 256)])
 def test_tilings_agree_bit_for_bit(binding, tiling):
-    """Every tile shape of the scatter kernel (ragged last slabs: 512 rows by 7 or 3), and every band
-    height of the gather kernel and of the peak search, gives the same result."""
+    """Every tile shape of the scatter kernel (ragged last slabs: 512 rows by 7 or 3), every band
+    height of the peak search, and every gather tile (rows x columns x threads; ragged last row
+    bands; a full-row tile whose profile windows exceed their shared-memory slot and are read from
+    global memory) gives the same result."""
     w = eg.WORKLOADS["pileup_100k"]
     ev = w.event(2).subset(np.arange(40000))
     base = run_gpu(binding, w.geometry, w.binning, ev)
