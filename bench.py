@@ -43,6 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1310_7556_gb300 import eventgen as eg  # noqa: E402
+from paper_1310_7556_gb300 import replicas  # noqa: E402
 
 METRIC = "Hough votes/s and events/s on 1 GB300 (batched vs plain); p50/p99 event latency"
 WORKLOAD_TEXT = {
@@ -221,7 +222,7 @@ class Env:
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         if self.world > 1:
-            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            dist.init_process_group(replicas.backend_for(True), device_id=torch.device("cuda", self.local))
         torch.cuda.set_device(self.local)
         self.dev = torch.device("cuda", self.local)
         binding.load()
@@ -229,11 +230,7 @@ class Env:
         self.flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=self.dev)
 
     def max_over_ranks(self, x: float) -> float:
-        if self.world == 1:
-            return x
-        t = self.torch.tensor([x], device=self.dev)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(self.dist if self.world > 1 else None, x, device=self.dev)
 
     def barrier(self):
         if self.world > 1:
@@ -284,7 +281,7 @@ def measure_plain(env, args, ctx, tens, n):
     step()
     attr_ms, lib_t = timed_steps(min(args.steps, 50), True)
     kernel_ms = {k: statistics.mean(t[k] for t in lib_t) for k in lib_t[0]}
-    out = {"events_per_s": env.world * args.steps / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
+    out = {"events_per_s": replicas.job_rate(args.steps, env.world, total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
            "stage_ms": kernel_ms, "attributed_ms_per_step": statistics.mean(attr_ms),
            "votes": int(st.votes), "general_votes": int(st.general_votes), "candidates": int(st.n_candidates),
            "members": int(st.n_members), "stage2_votes": int(st.stage2_votes), "launches": int(launches)}
@@ -404,7 +401,7 @@ def measure_batched(env, args):
     step over all events of the batch."""
     torch, binding, stream = env.torch, env.binding, env.stream
     wb = eg.WORKLOADS["batch_256"]
-    bev = [wb.event(env.rank * args.batch_events + i) for i in range(args.batch_events)]
+    bev = [wb.event(i) for i in replicas.event_indices(env.rank, env.world, args.batch_events)]
     bhs = np.zeros(len(bev) + 1, dtype=np.int64)
     bhs[1:] = np.cumsum([e.n_hits for e in bev])
     bdev = [torch.from_numpy(np.concatenate([getattr(e, k) for e in bev])).to(env.dev) for k in ("r", "phi", "z", "layer")]
@@ -432,8 +429,8 @@ def measure_batched(env, args):
     launches = binding.kernel_launches() - launch0
     total = env.max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(b0, b1)))
     votes = sum(int(st.votes) for st in bstats)
-    out = {"events_per_s": env.world * len(bev) * args.batch_steps / (total * 1e-3),
-           "votes_per_s": env.world * votes * args.batch_steps / (total * 1e-3),
+    out = {"events_per_s": replicas.job_rate(len(bev) * args.batch_steps, env.world, total * 1e-3),
+           "votes_per_s": replicas.job_rate(votes * args.batch_steps, env.world, total * 1e-3),
            "ms_per_batch": total / args.batch_steps, "events_per_batch": len(bev), "hits_per_batch": int(bhs[-1]),
            "votes_per_batch": votes, "candidates_per_batch": sum(int(st.n_candidates) for st in bstats),
            "members_per_batch": sum(int(st.n_members) for st in bstats),
@@ -494,7 +491,7 @@ def measure_served(env, args):
     the device) against one launch per event through the same admission and lanes."""
     binding = env.binding
     wb = eg.WORKLOADS["batch_256"]
-    pool_events = [wb.event(1000 + env.rank * 64 + i) for i in range(64)]
+    pool_events = [wb.event(i) for i in replicas.event_indices(env.rank, env.world, 64, base=1000)]
     pool = [tuple(np.ascontiguousarray(getattr(e, k)) for k in ("r", "phi", "z", "layer")) for e in pool_events]
     max_event_hits = max(e.n_hits for e in pool_events)
     loads = [float(x) for x in args.serve_loads.split(",") if x]
@@ -545,7 +542,8 @@ def measure_e2e(env, args, ctx, ev):
         got = ctx.process(*pinned, n_hits=n, out=out, stream=stream)
         e2e_s.append(time.perf_counter() - t0)
     total = env.max_over_ranks(sum(e2e_s))
-    return {"value": env.world * args.steps / total, "unit": "events/s", "h2d_bytes_per_step": n * (4 + 4 + 4 + 1),
+    return {"value": replicas.job_rate(args.steps, env.world, total), "unit": "events/s",
+            "h2d_bytes_per_step": n * (4 + 4 + 4 + 1),
             "d2h_bytes_per_step": len(got) * 32 + 160}
 
 
@@ -563,7 +561,7 @@ def main():
         return
 
     w = eg.WORKLOADS[args.workload]
-    ev = w.event(env.rank)     # each rank its own event
+    ev = w.event(replicas.event_indices(env.rank, env.world, 1)[0])     # each rank its own event
     n = ev.n_hits
     tens = [env.torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
     ctx = binding.HoughContext(w.geometry, w.binning, max_hits=n, max_candidates=1 << 18,

@@ -219,9 +219,9 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
  * tile_phi must divide n_phi and be a multiple of 64; tile_qpt in 1..256; threads in
  * {128, 256, 512, 1024}; tile_qpt * tile_phi * 2 bytes must fit in shared memory; band_rows in
  * 1..16 with (band_rows + 2) * n_phi bytes of shared memory; gather_rows in 1..32 (0: 4);
- * gather_cols a multiple of 64 dividing n_phi (0: the largest such up to 1024) with
- * (n_layers rounded up to 4) * (gather_cols + 64) * 8 bytes of shared memory; gather_threads in
- * {256, 512, 1024} (0: 512).  HOUGH_EINVAL otherwise.  Every configuration gives the same results.
+ * gather_cols a multiple of 64 dividing n_phi (0: the largest such up to 512) with
+ * n_layers * (gather_cols + 64) * 8 bytes of shared memory; gather_threads in {256, 512, 1024}
+ * (0: 256).  HOUGH_EINVAL otherwise.  Every configuration gives the same results.
  */
 #define HOUGH_VOTE_GATHER  0
 #define HOUGH_VOTE_SCATTER 1

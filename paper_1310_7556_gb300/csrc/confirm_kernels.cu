@@ -63,7 +63,7 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
         sc.nr = 2;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            const int J = ((j + te.I + side) % nphi + nphi) % nphi;
+            const int J = wrap_col(j + te.I + side, nphi);   // |I| <= nphi / 4 + 1: within one wrap
             sc.st[side] = offs[l * nphi + J];
             sc.en[side] = offs[l * nphi + J + 1];
         }
@@ -81,7 +81,7 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
     if (jb - ja + 1 >= nphi) {
         sc.nr = 1; sc.st[0] = lstart; sc.en[0] = lend;
     } else {
-        const int a = ((ja % nphi) + nphi) % nphi, b = ((jb % nphi) + nphi) % nphi;
+        const int a = wrap_col(ja, nphi), b = wrap_col(jb, nphi);   // within nphi / 4 + 3 of [0, nphi)
         if (a <= b) {
             sc.nr = 1; sc.st[0] = offs[l * nphi + a]; sc.en[0] = offs[l * nphi + b + 1];
         } else {
@@ -276,8 +276,9 @@ __device__ __forceinline__ void member_rows(const Axes &ax, float a, float b, in
         *hi = in ? ax.n_cot - 1 : 0;
         return;
     }
-    const float flo = floorf((float)mref + (a - (float)ax.n_z0) / b);
-    const float fhi = floorf((float)mref + a / b) + 1.f;
+    // approximate quotients: the run is widened by a row each side and every pair is tested exactly
+    const float flo = floorf((float)mref + __fdividef(a - (float)ax.n_z0, b));
+    const float fhi = floorf((float)mref + __fdividef(a, b)) + 1.f;
     *lo = (int)fminf(fmaxf(flo, 0.f), top + 1.f);
     *hi = (int)fminf(fmaxf(fhi, -1.f), top);
 }

@@ -147,7 +147,7 @@ Axes make_axes_impl(const hough_geometry *g, const hough_binning *b)
 
 int default_gather_cols(const Axes &ax)
 {
-    int cols = std::min(ax.n_phi, 1024);
+    int cols = std::min(ax.n_phi, 512);
     cols -= cols % 64;
     while (ax.n_phi % cols) cols -= 64;
     return cols;
@@ -160,7 +160,7 @@ Tiling resolve_tiling_impl(const Axes &ax, const hough_tiling *t)
              t->gather_rows, t->gather_cols, t->gather_threads};
     if (!r.gather_rows) r.gather_rows = 4;
     if (!r.gather_cols) r.gather_cols = default_gather_cols(ax);
-    if (!r.gather_threads) r.gather_threads = 512;
+    if (!r.gather_threads) r.gather_threads = 256;
     return r;
 }
 
@@ -206,7 +206,7 @@ Tiling default_tiling_impl(const Axes &ax)
     t.band_rows = 1;
     t.gather_rows = 4;
     t.gather_cols = default_gather_cols(ax);
-    t.gather_threads = 512;
+    t.gather_threads = 256;
     return t;
 }
 
