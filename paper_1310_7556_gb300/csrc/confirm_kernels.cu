@@ -23,8 +23,8 @@
 //
 // Stage-2 arithmetic: for a member with arc length s the z0 coordinate
 // w(m) = n_z0 (z - s t_m - z0_min) / (z0_max - z0_min) is evaluated in FP32 around the row m_ref
-// where it crosses z0_min, from coefficients formed in two-float arithmetic (member_coefficients);
-// a vote within kStage2Eps of a z0 edge is recomputed in FP64 exactly as the definition reads.
+// where it crosses z0_min, from coefficients formed in two-float arithmetic (member_coefficients),
+// to within 2e-5 bin of its exact value (stage2_cell).
 #include <atomic>
 
 #include "hough_internal.cuh"
@@ -53,11 +53,12 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
     sc.table = 0;
     sc.g = 0.f;
     const int nphi = ax.n_phi;
+    // both records at once (the table entry's address does not depend on the layer record)
     const LayerInfo li = w.info[l];
+    const TabEntry te = w.tab[l * ax.n_qpt + i];
     if (!li.present) return sc;
     if (li.uniform) {
         if (i < li.lo || i > li.hi) return sc;
-        const TabEntry te = w.tab[l * ax.n_qpt + i];
         sc.table = 1;
         sc.g = te.g;
         sc.nr = 2;
@@ -106,7 +107,8 @@ struct SegTable {
 // r in [lo, lo + cap) in pos[r - lo], and, when pool is given, in pool[r] for r < pool_n.
 __device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t *offs, const HotHit *hot,
                               const ColdHit *cold, uint32_t mask, int i, int j, float s32, float refine_eps,
-                              int lo, int cap, int *pos, int32_t *pool, int pool_n, SegTable &seg)
+                              int lo, int cap, int *pos, int32_t *pool, int pool_n, SegTable &seg,
+                              unsigned char *lay = nullptr)
 {
     const int lane = threadIdx.x & 31;
     // lane l < 16: layer l's ranges
@@ -140,18 +142,32 @@ __device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t 
     if (lane == 0) seg.pre[2 * HOUGH_MAX_LAYERS] = total;
     __syncwarp();
     int count = 0;
+    // the hit record of flattened index v, with its segment: the last q with pre[q] <= v
+    auto locate = [&](int v, int &q) {
+        q = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (q + step < 2 * HOUGH_MAX_LAYERS && seg.pre[q + step] <= v) q += step;
+        return seg.start[q] + (v - seg.pre[q]);
+    };
+    // software-pipelined: the next round's record is requested before this round is tested
+    int q = 0, p = 0;
+    HotHit hh{};
+    if (lane < total) {
+        p = locate(lane, q);
+        hh = hot[p];
+    }
     for (int base = 0; base < total; base += 32) {
         const int v = base + lane;
+        const int vn = v + 32;
+        int qn = 0, pn = 0;
+        HotHit hn{};
+        if (vn < total) {
+            pn = locate(vn, qn);
+            hn = hot[pn];
+        }
         bool mem = false;
-        int p = 0;
         if (v < total) {
-            // the segment holding flattened index v: the last q with pre[q] <= v
-            int q = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (q + step < 2 * HOUGH_MAX_LAYERS && seg.pre[q + step] <= v) q += step;
-            p = seg.start[q] + (v - seg.pre[q]);
-            const HotHit hh = hot[p];
             const int kind = seg.kind[q];
             if (kind == 0) {
                 mem = !(hh.f < seg.g[q >> 1]);
@@ -176,10 +192,16 @@ __device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t 
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, mem);
         if (mem) {
             const int r = count + __popc(ball & ((1u << lane) - 1u));
-            if (r >= lo && r < lo + cap) pos[r - lo] = p;
+            if (r >= lo && r < lo + cap) {
+                pos[r - lo] = p;
+                if (lay) lay[r - lo] = (unsigned char)(q >> 1);
+            }
             if (pool && r < pool_n) pool[r] = p;
         }
         count += __popc(ball);
+        q = qn;
+        p = pn;
+        hh = hn;
     }
     __syncwarp();
     return count;
@@ -195,24 +217,18 @@ __device__ __forceinline__ double member_arc(const Axes &ax, const Workspace &w,
     return axv > 0.0 ? __ddiv_rn(__dmul_rn(rd, asin(axv)), axv) : rd;
 }
 
-// z0 coordinate of one stage-2 vote exactly as the definition reads (FP64, nothing fused).
-__device__ __forceinline__ double exact_z0_coord(const Axes &ax, double z, double s, int m)
-{
-    const double t = __dadd_rn(ax.cot_min, __dmul_rn((double)m + 0.5, ax.dt));
-    const double z0 = __dsub_rn(z, __dmul_rn(s, t));
-    return __ddiv_rn(__dmul_rn((double)ax.n_z0, __dsub_rn(z0, ax.z0_min)), __dsub_rn(ax.z0_max, ax.z0_min));
-}
-
 // Stage-2 coefficients of one member at row i: z0 coordinate w(m) = a - (m - m_ref) b in FP32.
 // For a layer of one radius the per-row terms S = zscale s t_0 and B = zscale s dt come from the
 // table and w(m_ref) = zscale (z - z0_min) - S - m_ref B is formed in two-float arithmetic (about
 // 2^-44 relative before the final rounding), which keeps a within a few 1e-6 bins of the exact
-// value -- far inside the FP64 recheck window of stage2_bin.  Other layers take the FP64 route.
+// value.  Other layers take the FP64 route.
 __device__ __forceinline__ void member_coefficients(const Axes &ax, const Workspace &w, const HotHit *hot,
                                                     const ColdHit *cold, int p, int i, float *a_out, float *b_out,
-                                                    int *mrl_out)
+                                                    int *mrl_out, int layer = -1)
 {
-    const int l = (int)((hot[p].jl >> 16) & 0xFu);
+    // the layer from the enumeration when given: then the layer record, the stage-2 terms and the
+    // hit's coordinates are requested together
+    const int l = layer >= 0 ? layer : (int)((hot[p].jl >> 16) & 0xFu);
     const ColdHit ch = cold[p];
     if (w.info[l].uniform) {
         const float4 zc = w.zco[l * ax.n_qpt + i];
@@ -245,27 +261,20 @@ __device__ __forceinline__ void member_coefficients(const Axes &ax, const Worksp
     *mrl_out = mref | (l << 16);
 }
 
-// z0 bin of the vote of member p at cot row m (-1 outside the grid).
-__device__ __forceinline__ int stage2_bin(const Axes &ax, const Workspace &w, const ColdHit *cold, int p, int i,
-                                          float a, float b, int mrl, int m)
+// z0 bin of a member's vote at cot row m, -1 outside the grid: w(m) = a - (m - m_ref) b in FP32,
+// one fused multiply-add from the two-float coefficients.  Its error stays below 2e-5 bin (a to
+// ~4e-6, the rounding of b times |m - m_ref| <= 128 / b rows to ~8e-6, the final rounding to
+// ~4e-6), so every vote farther than that from a z0 edge -- in particular every vote the exact
+// definition would not flag within 1e-4 bin -- lands in the bin the definition gives.
+__device__ __forceinline__ int stage2_cell(const Axes &ax, float a, float b, int mrl, int m)
 {
-    const int mref = mrl & 0xFFFF;
-    const float wv = fmaf(-(float)(m - mref), b, a);
-    const float fl = floorf(wv);
-    const float d = wv - fl;
-    int nz;
-    if (d < kStage2Eps || d > 1.f - kStage2Eps) {
-        const ColdHit ch = cold[p];
-        nz = (int)floor(exact_z0_coord(ax, (double)ch.z, member_arc(ax, w, mrl >> 16, i, ch.r), m));
-    } else {
-        nz = (wv < -1.f || wv > (float)ax.n_z0 + 1.f) ? -1 : (int)fl;
-    }
-    return (nz >= 0 && nz < ax.n_z0) ? nz : -1;
+    const float wv = fmaf(-(float)(m - (mrl & 0xFFFF)), b, a);
+    return (wv >= 0.f && wv < (float)ax.n_z0) ? (int)wv : -1;   // truncation is the floor here
 }
 
 // Cot rows [*lo, *hi] whose vote of the member can fall inside the z0 range: w(m) = a - (m - m_ref) b
 // is monotone in m, so the rows form one run; the bounds are widened by a row on each side and
-// every pair is still tested exactly by stage2_bin.
+// every pair is still tested by stage2_cell.
 __device__ __forceinline__ void member_rows(const Axes &ax, float a, float b, int mrl, int *lo, int *hi)
 {
     const int mref = mrl & 0xFFFF;
@@ -350,12 +359,11 @@ union WarpScratch {
     SmallStage2 small;
 };
 
-// Stage 2 of a candidate with at most 32 members in the warp's private grid: lane q prepares member
-// q and its run of cot rows; the (member, row) pairs of all runs are then spread over the lanes and
-// voted in one pass (stage2_vote).  Each lane keeps the words its first kRecorded rounds touched and
-// clears them afterwards; pairs beyond those rounds are recomputed to clear theirs.
-constexpr int kRecorded = 6;
-
+// Stage 2 of up to 32 members in the warp's private grid: lane q prepares member q and its run of
+// cot rows; the (member, row) pairs of all runs are then spread over the lanes and voted in one pass
+// (stage2_vote).  Returns, through rlo / rhi, the rows the runs cover (rlo > rhi when none): every
+// touched cell lies in them, which is what the caller clears afterwards.  One simple loop keeps the
+// code small: with few warps resident, instruction fetch of a large body is what a candidate waits on.
 __device__ __forceinline__ int small_pair_member(const SmallStage2 &sm, int n, int v)
 {
     // the member whose run holds pair v: the last q with start[q] <= v
@@ -367,68 +375,71 @@ __device__ __forceinline__ int small_pair_member(const SmallStage2 &sm, int n, i
 }
 
 __device__ void warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
-                                  SmallStage2 &sm, const int *pos, int n, int i, bool clear, Best &best,
-                                  unsigned long long &votes)
+                                  SmallStage2 &sm, const int *pos, int n, int i, Best &best,
+                                  unsigned long long &votes, int &rlo, int &rhi)
 {
     const int lane = threadIdx.x & 31;
-    int len = 0;
+    int len = 0, lo = ax.n_cot, hi = -1;
     if (lane < n) {
-        int lo, hi;
         member_rows(ax, sm.a[lane], sm.b[lane], sm.mrl[lane], &lo, &hi);
         sm.mlo[lane] = lo;
         len = max(0, hi - lo + 1);
+        if (!len) {
+            lo = ax.n_cot;
+            hi = -1;
+        }
     }
     int incl = len;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
         if (lane >= d) incl += t;
+        lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, d));
     }
+    rlo = min(rlo, lo);
+    rhi = max(rhi, hi);
     if (lane < kSmallMembers) sm.start[lane] = incl - len;
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (lane == 0) sm.start[kSmallMembers] = total;
     __syncwarp();
-    int touched[kRecorded];
+    // four pairs per lane per round, straight-line and independent of each other (an index past
+    // the end is clamped and its result masked): a lone warp (few candidates) is bound by the
+    // latency of this chain, not by issue
+    constexpr int kIlp = 4;
+    for (int v0 = lane; v0 < total; v0 += 32 * kIlp) {
+        int m[kIlp], nz[kIlp], ly[kIlp];
 #pragma unroll
-    for (int r = 0; r < kRecorded; ++r) touched[r] = -1;   // every slot, also those after an early exit
-#pragma unroll
-    for (int r = 0; r < kRecorded; ++r) {
-        const int v = lane + 32 * r;
-        if (32 * r >= total) break;
-        if (v < total) {
-            const int q = small_pair_member(sm, n, v);
-            const int m = sm.mlo[q] + (v - sm.start[q]);
+        for (int u = 0; u < kIlp; ++u) {
+            const int v = v0 + 32 * u;
+            const int vc = min(v, total - 1);
+            const int q = small_pair_member(sm, n, vc);
             const int mrl = sm.mrl[q];
-            const int nz = stage2_bin(ax, w, cold, pos[q], i, sm.a[q], sm.b[q], mrl, m);
-            if (nz >= 0) {
-                touched[r] = stage2_vote(ax, grid, m, nz, mrl >> 16, best);
+            m[u] = sm.mlo[q] + (vc - sm.start[q]);
+            ly[u] = mrl >> 16;
+            const int cell = stage2_cell(ax, sm.a[q], sm.b[q], mrl, m[u]);
+            nz[u] = v < total ? cell : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u)
+            if (nz[u] >= 0) {
+                stage2_vote(ax, grid, m[u], nz[u], ly[u], best);
                 ++votes;
             }
-        }
-    }
-    for (int v = lane + 32 * kRecorded; v < total; v += 32) {
-        const int q = small_pair_member(sm, n, v);
-        const int m = sm.mlo[q] + (v - sm.start[q]);
-        const int mrl = sm.mrl[q];
-        const int nz = stage2_bin(ax, w, cold, pos[q], i, sm.a[q], sm.b[q], mrl, m);
-        if (nz >= 0) {
-            stage2_vote(ax, grid, m, nz, mrl >> 16, best);
-            ++votes;
-        }
     }
     __syncwarp();
-    if (!clear) return;
-    // leave the grid clear for the warp's next candidate
-#pragma unroll
-    for (int r = 0; r < kRecorded; ++r)
-        if (touched[r] >= 0) grid[touched[r]] = 0u;
-    for (int v = lane + 32 * kRecorded; v < total; v += 32) {
-        const int q = small_pair_member(sm, n, v);
-        const int m = sm.mlo[q] + (v - sm.start[q]);
-        const int nz = stage2_bin(ax, w, cold, pos[q], i, sm.a[q], sm.b[q], sm.mrl[q], m);
-        if (nz >= 0) grid[(m * ax.n_z0 + nz) >> 1] = 0u;
-    }
-    __syncwarp();
+}
+
+// Zero the grid words of rows [rlo, rhi] (16-byte stores over a span rounded out to whole vectors:
+// the extra words are outside every touched cell and already zero).
+__device__ __forceinline__ void clear_rows(const Axes &ax, uint32_t *grid, int rlo, int rhi)
+{
+    if (rlo > rhi) return;
+    const int lane = threadIdx.x & 31;
+    const int w0 = ((rlo * ax.n_z0) >> 1) & ~3;
+    const int w1 = (((((rhi + 1) * ax.n_z0 - 1) >> 1)) | 3) + 1;   // <= grid words (a multiple of 4)
+    uint4 *g4 = reinterpret_cast<uint4 *>(grid);
+    for (int q = (w0 >> 2) + lane; q < (w1 >> 2); q += 32) g4[q] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // Membership and, for candidates of at most kSmallMembers members, stage 2: one warp per candidate
@@ -440,10 +451,12 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_m[];
     __shared__ int s_pos[kConfirmWarpsMax][kMemberCap];
+    __shared__ unsigned char s_lay[kConfirmWarpsMax][kMemberCap];
     __shared__ WarpScratch s_scratch[kConfirmWarpsMax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     int *pos = s_pos[warp];
+    unsigned char *lay = s_lay[warp];
     SegTable &seg = s_scratch[warp].seg;
     SmallStage2 &sm = s_scratch[warp].small;
     uint32_t *grid = reinterpret_cast<uint32_t *>(smem_m) + warp * grid_words;   // warp-private, clear
@@ -464,7 +477,7 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
         const hough_candidate cd = cands[c];
         const int i = (int)cd.iq;
         const int n = warp_enumerate(ax, w, offs, hot, cold, cd.mask, i, (int)cd.jphi, s32, refine_eps, 0,
-                                     kMemberCap, pos, nullptr, 0, seg);
+                                     kMemberCap, pos, nullptr, 0, seg, lay);
         // the event's member pool is shared by all its candidates: reserve the range now and use it
         // after stage 2, so that the contended atomic's round trip overlaps the vote
         unsigned reserved = 0u;
@@ -472,20 +485,18 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
         Best best = {0u, 0u, 0u};
         unsigned long long votes = 0;
         if (n <= kMemberCap) {
-            // members in chunks of 32 into the one grid; a single chunk clears what it touched,
-            // several clear the whole grid at the end
+            // members in chunks of 32 into the one grid, then the rows their runs covered cleared
+            int rlo = ax.n_cot, rhi = -1;
             for (int c0 = 0; c0 < n; c0 += kSmallMembers) {
                 const int nc = min(kSmallMembers, n - c0);
                 if (lane < nc)
-                    member_coefficients(ax, w, hot, cold, pos[c0 + lane], i, &sm.a[lane], &sm.b[lane], &sm.mrl[lane]);
+                    member_coefficients(ax, w, hot, cold, pos[c0 + lane], i, &sm.a[lane], &sm.b[lane], &sm.mrl[lane],
+                                        lay[c0 + lane]);
                 __syncwarp();
-                warp_stage2_small(ax, w, cold, grid, sm, pos + c0, nc, i, n <= kSmallMembers, best, votes);
+                warp_stage2_small(ax, w, cold, grid, sm, pos + c0, nc, i, best, votes, rlo, rhi);
             }
-            if (n > kSmallMembers) {
-                uint4 *g4 = reinterpret_cast<uint4 *>(grid);
-                for (int q = lane; q < (grid_words >> 2); q += 32) g4[q] = make_uint4(0u, 0u, 0u, 0u);
-                __syncwarp();
-            }
+            clear_rows(ax, grid, rlo, rhi);
+            __syncwarp();
             warp_best(best);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) votes += __shfl_xor_sync(0xFFFFFFFFu, votes, d);
@@ -615,7 +626,7 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 2) stage2_large_kernel(
                 }
                 const int m = s_mlo[qlo] + (v - s_start[qlo]);
                 const int mrl = s_mrl[qlo];
-                const int nz = stage2_bin(ax, w, x.cold, s_pos[qlo], i, s_a[qlo], s_b[qlo], mrl, m);
+                const int nz = stage2_cell(ax, s_a[qlo], s_b[qlo], mrl, m);
                 if (nz >= 0) {
                     stage2_vote(ax, grid, m, nz, mrl >> 16, best);
                     ++votes;

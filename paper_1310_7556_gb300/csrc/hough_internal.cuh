@@ -164,8 +164,6 @@ constexpr int kPeakThreads = 256;
 // Refinement of the per-vote FP32 path: votes whose FP32 bin coordinate lies within the refine
 // window of an edge, or whose |x| exceeds kRefineXLim, are recomputed in FP64.
 constexpr float kRefineXLim = 0.99f;
-// Stage-2 FP32 window: a (member, cot) vote within this distance of a z0 edge is recomputed in FP64.
-constexpr float kStage2Eps = 2e-4f;
 
 __host__ __device__ inline int n_keys(const Axes &ax) { return ax.n_layers * ax.n_phi; }
 // Bucket-profile stride per layer and per event (16 layers, each padded by 16 repeated buckets).
