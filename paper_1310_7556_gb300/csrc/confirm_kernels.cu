@@ -466,8 +466,9 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
     const int total = (int)w.counters->total_cands;
     // candidate f goes to CTA f mod gridDim, so that a few candidates spread over all SMs
     for (int f = warp * gridDim.x + blockIdx.x; f < total; f += gridDim.x * nwarps) {
-        const int e = upper_index(w.cand_base, w.n_events, f);
-        const int c = f - w.cand_base[e];
+        // a one-event batch has its candidates at their flattened indices (no dependent lookup)
+        const int e = w.n_events == 1 ? 0 : upper_index(w.cand_base, w.n_events, f);
+        const int c = w.n_events == 1 ? f : f - w.cand_base[e];
         const int64_t hstart = w.hit_start[e];
         const HotHit *hot = w.hot + hstart;
         const ColdHit *cold = w.cold + hstart;
