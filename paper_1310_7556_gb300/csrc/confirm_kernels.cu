@@ -26,6 +26,7 @@
 // where it crosses z0_min, from coefficients formed in two-float arithmetic (member_coefficients),
 // to within 2e-5 bin of its exact value (stage2_cell).
 #include <atomic>
+#include <climits>
 
 #include "hough_internal.cuh"
 
@@ -465,10 +466,21 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
     const int nkeys = ax.n_layers * ax.n_phi;
     const int total = (int)w.counters->total_cands;
     // candidate f goes to CTA f mod gridDim, so that a few candidates spread over all SMs
+    int e = 0, e_base = 0, e_next = w.n_events == 1 ? INT_MAX : -1;   // the event of the last candidate
     for (int f = warp * gridDim.x + blockIdx.x; f < total; f += gridDim.x * nwarps) {
-        // a one-event batch has its candidates at their flattened indices (no dependent lookup)
-        const int e = w.n_events == 1 ? 0 : upper_index(w.cand_base, w.n_events, f);
-        const int c = w.n_events == 1 ? f : f - w.cand_base[e];
+        // a warp's candidates come in increasing flattened order, so its event only moves forward:
+        // a short forward step instead of a binary search (none at all for a one-event batch)
+        if (e_next < 0) {
+            e = upper_index(w.cand_base, w.n_events, f);
+            e_base = w.cand_base[e];
+            e_next = w.cand_base[e + 1];
+        }
+        while (f >= e_next) {
+            ++e;
+            e_base = e_next;
+            e_next = w.cand_base[e + 1];
+        }
+        const int c = f - e_base;
         const int64_t hstart = w.hit_start[e];
         const HotHit *hot = w.hot + hstart;
         const ColdHit *cold = w.cold + hstart;

@@ -477,12 +477,14 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
 // event, whose flattened candidate base this kernel then writes itself.
 constexpr int kCompactSmemBands = 4096;
 
-__global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w, int single)
+__global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w, int single, int parts)
 {
     pdl_enter();
     __shared__ int s_warp[kCompactThreads / 32];
     __shared__ int s_offs[kCompactSmemBands + 1];
-    const int e = blockIdx.x;
+    // `parts` CTAs per event: each scans the band counts and copies its slice of the candidates;
+    // the first also records the event's totals (and handles band counts too many to stage)
+    const int e = blockIdx.x / parts, part = blockIdx.x - e * parts;
     const int nb = n_bands(ax, w.band_rows);
     const bool staged = nb <= kCompactSmemBands;
     const int32_t *counts = w.band_counts + (int64_t)e * nb;
@@ -512,13 +514,13 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
     __syncthreads();
     int run = (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
     for (int k = k0; k < k1; ++k) {
-        offs[k] = run;
         if (staged) s_offs[k] = run;
+        else if (part == 0) offs[k] = run;
         run += counts[k];
     }
     const int total = s_warp[kCompactThreads / 32 - 1];
     const int kept = min(total, w.max_cand);
-    if (threadIdx.x == 0) {
+    if (part == 0 && threadIdx.x == 0) {
         w.stats[e].n_candidates = (unsigned)total;
         if (total > w.max_cand) atomicOr(&w.stats[e].device_error, HOUGH_DEVERR_CAND);
         if (single) {
@@ -540,7 +542,9 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
         cands[c] = cd;
     };
     if (staged) {
-        for (int c = threadIdx.x; c < kept; c += kCompactThreads) {
+        const int per = (kept + parts - 1) / parts;
+        const int c_end = min(kept, (part + 1) * per);
+        for (int c = part * per + threadIdx.x; c < c_end; c += kCompactThreads) {
             // the band holding candidate c: the last b with offs[b] <= c (empty bands share offsets)
             int lo = 0, hi = nb - 1;
             while (lo < hi) {
@@ -551,6 +555,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
         }
         return;
     }
+    if (part != 0) return;
     for (int b = warp; b < nb; b += kCompactThreads / 32) {
         const int n = counts[b], o = offs[b];
         for (int k = lane; k < n; k += 32) {
@@ -742,7 +747,14 @@ cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &
 cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream)
 {
     const int single = w.n_events == 1;
-    cudaError_t err = launch_chained(compact_kernel, dim3(w.n_events), dim3(kCompactThreads), 0, stream, ax, w, single);
+    // about two CTAs per SM over all events (the copy of a dense event's tens of thousands of
+    // candidates is latency-bound in one CTA)
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int parts = std::max(1, std::min(16, (2 * sms + w.n_events - 1) / w.n_events));
+    cudaError_t err = launch_chained(compact_kernel, dim3(w.n_events * parts), dim3(kCompactThreads), 0, stream, ax, w,
+                                     single, parts);
     if (!err && !single) err = launch_chained(cand_scan_kernel, dim3(1), dim3(kCompactThreads), 0, stream, w);
     return err;
 }
