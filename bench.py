@@ -470,6 +470,8 @@ def drive_server(env, srv, pool, rate, seconds, seed, threads=4):
     done = res["done_ns"][admitted]
     lat_ms = ((done - res["arrival_ns"][admitted]) * 1e-6).tolist()
     late_us = (res["submit_ns"][admitted] - res["arrival_ns"][admitted]) * 1e-3
+    queue_ms = (res["launch_ns"][admitted] - res["arrival_ns"][admitted]) * 1e-6
+    service_ms = (done - res["launch_ns"][admitted]) * 1e-6
     statuses = {}
     for v in res["status"][admitted].tolist():
         statuses[str(v)] = statuses.get(str(v), 0) + 1
@@ -482,6 +484,8 @@ def drive_server(env, srv, pool, rate, seconds, seed, threads=4):
             "mean_batch_events": float(res["batch_events"][admitted].mean()) if n_adm else 0.0,
             "max_in_flight": int(st1.max_in_flight), "launches": int(st1.launches - st0.launches),
             "submit_late_p99_us": float(np.percentile(late_us, 99)) if n_adm else None,
+            "queue_ms_p50_p99": [float(np.percentile(queue_ms, 50)), float(np.percentile(queue_ms, 99))] if n_adm else None,
+            "service_ms_p50_p99": [float(np.percentile(service_ms, 50)), float(np.percentile(service_ms, 99))] if n_adm else None,
             "submitter_threads": threads, "statuses": statuses}
 
 

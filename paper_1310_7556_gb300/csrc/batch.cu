@@ -41,6 +41,7 @@ struct hough_batch {
     int64_t *hit_start = nullptr;        // device, max_events + 1
     HitInputs *inputs_dev = nullptr;     // device copy of the current hit pointers
     HitInputs inputs_host{};
+    HitInputs inputs_on_device{};        // what inputs_dev holds (copied only when it changes)
     float *in_r = nullptr, *in_phi = nullptr, *in_z = nullptr;
     uint8_t *in_layer = nullptr;
     hough_candidate *packed = nullptr;   // all events' candidates, concatenated
@@ -153,6 +154,7 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i + 0.5) * ax.dk);
     A(cudaMemcpy(w.kq32, kq.data(), sizeof(float) * ax.n_qpt, cudaMemcpyHostToDevice));
     A(cudaMemset(w.memo, 0, sizeof(TableMemo)));
+    A(cudaMemset(b->inputs_dev, 0, sizeof(HitInputs)));   // as inputs_on_device says
     A(cudaMemset(w.stats, 0, sizeof(DevStats) * E));
     A(cudaMemset(w.cand_base, 0, sizeof(int32_t) * (E + 1)));
     A(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
@@ -214,9 +216,13 @@ int hough::batch_run(hough_batch *b, const float *r, const float *phi, const flo
     } else {
         b->inputs_host = HitInputs{r, phi, z, layer};
     }
-    // the next replay reads these through device memory (copies from pageable host memory are
-    // staged before the call returns, so the host values may change right after)
-    BCU(cudaMemcpyAsync(b->inputs_dev, &b->inputs_host, sizeof(HitInputs), cudaMemcpyHostToDevice, s), "copy inputs failed");
+    // the next replay reads these through device memory; the record changes only when the caller
+    // switches buffers (copies from pageable host memory are staged before the call returns)
+    if (std::memcmp(&b->inputs_host, &b->inputs_on_device, sizeof(HitInputs)) != 0) {
+        BCU(cudaMemcpyAsync(b->inputs_dev, &b->inputs_host, sizeof(HitInputs), cudaMemcpyHostToDevice, s),
+            "copy inputs failed");
+        b->inputs_on_device = b->inputs_host;
+    }
     BCU(cudaMemcpyAsync(b->hit_start, hit_start, sizeof(int64_t) * (n_events + 1), cudaMemcpyHostToDevice, s),
         "copy hit_start failed");
     b->w.n_events = n_events;
@@ -260,6 +266,16 @@ int hough::batch_enqueue_offsets(hough_batch *b, int32_t *offsets_host, cudaStre
     return HOUGH_OK;
 }
 
+int hough::batch_enqueue_offsets_mapped(hough_batch *b, int32_t *offsets_host, hough_candidate *mapped, int64_t cap,
+                                        cudaStream_t s)
+{
+    BCU(launch_pack_candidates(b->ax, b->w, mapped, s, cap, b->packed), "pack kernel failed");   // the rest stays on the device
+    note_launches(1);
+    BCU(cudaMemcpyAsync(offsets_host, b->w.cand_base, sizeof(int32_t) * (b->n_events + 1), cudaMemcpyDeviceToHost, s),
+        "copy offsets failed");
+    return HOUGH_OK;
+}
+
 // Enqueue the copy of the first n events' counters to `stats_host`; no synchronisation.
 int hough::batch_enqueue_stats(hough_batch *b, DevStats *stats_host, int n, cudaStream_t s)
 {
@@ -269,11 +285,13 @@ int hough::batch_enqueue_stats(hough_batch *b, DevStats *stats_host, int n, cuda
 
 size_t hough::batch_device_bytes(const hough_batch *b) { return b->device_bytes; }
 
-// Enqueue the copy of the first n packed candidates to `out_host`; no synchronisation.
-int hough::batch_enqueue_candidates(hough_batch *b, hough_candidate *out_host, int64_t n, cudaStream_t s)
+// Enqueue the copy of packed candidates [first, n) to dst_host[0, n - first); no synchronisation.
+int hough::batch_enqueue_candidates(hough_batch *b, hough_candidate *dst_host, int64_t n, cudaStream_t s,
+                                    int64_t first)
 {
-    if (n > 0)
-        BCU(cudaMemcpyAsync(out_host, b->packed, sizeof(hough_candidate) * n, cudaMemcpyDeviceToHost, s),
+    if (n > first)
+        BCU(cudaMemcpyAsync(dst_host, b->packed + first, sizeof(hough_candidate) * (n - first),
+                            cudaMemcpyDeviceToHost, s),
             "copy candidates failed");
     return HOUGH_OK;
 }

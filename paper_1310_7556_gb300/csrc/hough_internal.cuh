@@ -195,7 +195,10 @@ cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, 
                            cudaStream_t stream);
 cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
 cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream);
-cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream);
+// All events' candidates concatenated: the first `limit` into `out` (device-accessible), the rest
+// into `rest` at the same indices when it is given, else dropped.
+cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream,
+                                   long long limit = 1LL << 62, hough_candidate *rest = nullptr);
 cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream,
                           cudaEvent_t between = nullptr);
 cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t total, cudaStream_t stream);
@@ -222,7 +225,11 @@ void fill_stats(const DevStats &d, const LayerInfo *info, int n_layers, hough_st
 int batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
               const int64_t *hit_start, int32_t n_events, int where, cudaStream_t stream, bool check_hits);
 int batch_enqueue_offsets(hough_batch *b, int32_t *offsets_host, cudaStream_t s);
-int batch_enqueue_candidates(hough_batch *b, hough_candidate *out_host, int64_t n, cudaStream_t s);
+// The same, with the candidates packed straight into `mapped` (a device pointer of mapped pinned
+// host memory), at most `cap` of them; the rest stay in the batch's device buffer.
+int batch_enqueue_offsets_mapped(hough_batch *b, int32_t *offsets_host, hough_candidate *mapped, int64_t cap,
+                                 cudaStream_t s);
+int batch_enqueue_candidates(hough_batch *b, hough_candidate *dst_host, int64_t n, cudaStream_t s, int64_t first = 0);
 int batch_enqueue_stats(hough_batch *b, DevStats *stats_host, int n, cudaStream_t s);
 size_t batch_device_bytes(const hough_batch *b);
 

@@ -10,9 +10,10 @@
 // filling batch is full and no lane is free to take the next one, an event is refused with
 // HOUGH_EBUSY -- a trigger's dead time.
 //
-// Results come back in two steps, neither of which blocks the dispatcher: after the batch's graph
-// the lane copies its per-event candidate offsets and counters, and once those are on the host it
-// copies exactly the candidates they announce.  Stream completions reach the dispatcher through
+// Results come back without blocking the dispatcher: after the batch's graph the lane packs the
+// candidates straight into mapped pinned host memory (up to its capacity) and copies the per-event
+// offsets and counters; a batch with more candidates than that copies the rest once the offsets
+// announce them.  Stream completions reach the dispatcher through
 // host functions enqueued on the lane's stream; the dispatcher itself only polls flags, so a lane
 // that never completes is caught by its watchdog (lane_timeout_us) instead of blocking the loop.
 #include <algorithm>
@@ -73,7 +74,10 @@ struct Lane {
     int64_t *hit_start = nullptr;
     int32_t *offsets = nullptr;
     DevStats *stats = nullptr;
-    hough_candidate *cands = nullptr;
+    hough_candidate *mcands = nullptr;      // mapped pinned: the pack kernel writes the first mcap here
+    hough_candidate *mcands_dev = nullptr;  // its device address
+    int64_t mcap = 0;
+    hough_candidate *cands = nullptr;       // pinned overflow: candidates mcap.. of a larger batch
     int64_t cand_cap = 0;
     // the batch being filled or processed
     std::vector<Ticket *> tickets;
@@ -164,6 +168,7 @@ hough_server::~hough_server()
         cudaFreeHost(l->hit_start);
         cudaFreeHost(l->offsets);
         cudaFreeHost(l->stats);
+        cudaFreeHost(l->mcands);
         cudaFreeHost(l->cands);
     }
 }
@@ -182,20 +187,22 @@ int hough_server::enqueue_batch(Lane *l)
     l->phase_wanted = 1;
     int rc = batch_run(l->b, l->r, l->phi, l->z, l->layer, l->hit_start, n, HOUGH_HOST, l->stream, false);
     if (!rc) rc = batch_enqueue_stats(l->b, l->stats, n, l->stream);
-    if (!rc) rc = batch_enqueue_offsets(l->b, l->offsets, l->stream);
+    if (!rc) rc = batch_enqueue_offsets_mapped(l->b, l->offsets, l->mcands_dev, l->mcap, l->stream);
     if (!rc && cudaLaunchHostFunc(l->stream, lane_phase_done, l) != cudaSuccess)
         rc = set_last_error(HOUGH_ECUDA, "cudaLaunchHostFunc failed");
     return rc;
 }
 
-// Offsets and counters are on the host: enqueue the copy of exactly the announced candidates,
-// growing the pinned result buffer first if needed.  Unlocked; returns a status.
+// Offsets and counters are on the host, and the first mcap candidates in the mapped buffer: enqueue
+// the copy of the rest, growing the pinned overflow buffer first if needed.  Unlocked; returns a
+// status.
 int hough_server::enqueue_candidates(Lane *l, bool injected_alloc_failure)
 {
     const int64_t total = l->offsets[l->n_events];
-    if (total > l->cand_cap || injected_alloc_failure) {
+    const int64_t rest = total - l->mcap;
+    if (rest > l->cand_cap || injected_alloc_failure) {
         int64_t cap = std::max<int64_t>(l->cand_cap, 1);
-        while (cap < total) cap *= 2;
+        while (cap < rest) cap *= 2;
         hough_candidate *grown = nullptr;
         if (injected_alloc_failure)
             return set_last_error(HOUGH_ENOMEM, "injected result-buffer allocation failure");
@@ -206,7 +213,7 @@ int hough_server::enqueue_candidates(Lane *l, bool injected_alloc_failure)
         l->cand_cap = cap;
     }
     l->phase_wanted = 2;
-    int rc = batch_enqueue_candidates(l->b, l->cands, total, l->stream);
+    int rc = batch_enqueue_candidates(l->b, l->cands, total, l->stream, l->mcap);
     if (!rc && cudaLaunchHostFunc(l->stream, lane_phase_done, l) != cudaSuccess)
         rc = set_last_error(HOUGH_ECUDA, "cudaLaunchHostFunc failed");
     return rc;
@@ -219,7 +226,11 @@ void hough_server::fill_results(Lane *l)
     for (int e = 0; e < l->n_events; ++e) {
         Ticket *k = l->tickets[e];
         const int64_t a = l->offsets[e], b = l->offsets[e + 1];
-        k->cands.assign(l->cands + a, l->cands + b);
+        const int64_t split = std::min(std::max(a, l->mcap), b);   // [a, split) mapped, [split, b) overflow
+        k->cands.resize((size_t)(b - a));
+        if (split > a) std::memcpy(k->cands.data(), l->mcands + a, sizeof(hough_candidate) * (split - a));
+        if (b > split) std::memcpy(k->cands.data() + (split - a), l->cands + (split - l->mcap),
+                                   sizeof(hough_candidate) * (b - split));
         k->n_candidates = b - a;
         const DevStats &d = l->stats[e];
         uint64_t v = 0;
@@ -281,15 +292,20 @@ void hough_server::run()
                 if (l->state == LaneState::Running) {
                     const bool inject = fail_alloc;
                     fail_alloc = false;
+                    const bool fits = l->offsets[l->n_events] <= l->mcap;
                     g.unlock();
-                    const int rc = enqueue_candidates(l, inject);
+                    int rc = HOUGH_OK;
+                    if (inject || !fits) rc = enqueue_candidates(l, inject);
+                    else fill_results(l);   // every candidate is already in the mapped buffer
                     std::string why = rc ? hough_last_error() : "";
                     g.lock();
                     if (rc) {
                         if (rc == HOUGH_ENOMEM) st.alloc_failures += 1;
                         fail_lane(l, rc, rc != HOUGH_ENOMEM, why.c_str());
-                    } else {
+                    } else if (inject || !fits) {
                         l->state = LaneState::Copying;
+                    } else {
+                        complete_lane(l);
                     }
                 } else {
                     g.unlock();
@@ -388,7 +404,8 @@ int hough_serve_create(const hough_geometry *geometry, const hough_binning *binn
         }
         s->device_bytes += bytes;
         bool ok = cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) == cudaSuccess;
-        l->cand_cap = std::max<int64_t>(1 << 16, (int64_t)E * 1024);
+        l->cand_cap = std::max<int64_t>(1 << 14, (int64_t)E * 256);
+        l->mcap = std::max<int64_t>(1 << 16, (int64_t)E * 4096);
         ok = ok && cudaHostAlloc(&l->r, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->phi, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->z, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;
@@ -397,6 +414,8 @@ int hough_serve_create(const hough_geometry *geometry, const hough_binning *binn
         ok = ok && cudaHostAlloc(&l->offsets, sizeof(int32_t) * (E + 1), cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->stats, sizeof(DevStats) * E, cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->cands, sizeof(hough_candidate) * l->cand_cap, cudaHostAllocDefault) == cudaSuccess;
+        ok = ok && cudaHostAlloc(&l->mcands, sizeof(hough_candidate) * l->mcap, cudaHostAllocMapped) == cudaSuccess;
+        ok = ok && cudaHostGetDevicePointer(reinterpret_cast<void **>(&l->mcands_dev), l->mcands, 0) == cudaSuccess;
         s->lanes.push_back(std::move(l));
         if (!ok) return set_last_error(HOUGH_ENOMEM, "lane allocation failed");
     }

@@ -611,13 +611,17 @@ __global__ void __launch_bounds__(kCompactThreads) cand_scan_kernel(Workspace w)
 }
 
 // All events' candidate lists, concatenated in event order into `out` (positions from cand_base).
-__global__ void pack_candidates_kernel(Workspace w, hough_candidate *out)
+// (the first `limit` to `out`, the rest -- when `rest` is given -- to rest at the same index)
+__global__ void pack_candidates_kernel(Workspace w, hough_candidate *out, long long limit, hough_candidate *rest)
 {
     pdl_enter();
     const int total = w.cand_base[w.n_events];
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < total; f += gridDim.x * blockDim.x) {
+    const int n = rest ? total : (int)min((long long)total, limit);
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n; f += gridDim.x * blockDim.x) {
         const int e = upper_index(w.cand_base, w.n_events, f);
-        out[f] = w.cands[(int64_t)e * w.max_cand + (f - w.cand_base[e])];
+        const hough_candidate cd = w.cands[(int64_t)e * w.max_cand + (f - w.cand_base[e])];
+        if (f < limit) out[f] = cd;
+        else rest[f] = cd;
     }
 }
 
@@ -759,10 +763,11 @@ cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stre
     return err;
 }
 
-cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream)
+cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream,
+                                   long long limit, hough_candidate *rest)
 {
     (void)ax;
-    return launch_chained(pack_candidates_kernel, dim3(1216), dim3(256), 0, stream, w, out);
+    return launch_chained(pack_candidates_kernel, dim3(1216), dim3(256), 0, stream, w, out, limit, rest);
 }
 
 cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
