@@ -52,6 +52,8 @@ WORKLOAD_TEXT = {
                    "512 q/pT x 2048 phi0 uint16 layer masks, threshold >=7, 64 cot x 64 z0 stage 2",
     "single_50trk": "single event: 50 helices pT 1-50 GeV, no noise; 128 q/pT x 256 phi0, threshold >=8",
     "fine_4m": "fine binning: 20000 helices + 200000 noise hits; 1024 q/pT x 4096 phi0, threshold >=7",
+    "paper_2048": "the paper's detector (10 layers evenly spaced to 110 cm, 0.4 mm, transverse plane), "
+                  "5000 helices pT 1-100 GeV, no noise; 2048 q/pT x 2048 phi0, threshold >=8",
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -66,7 +68,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--only", choices=["all", "plain", "batched", "served"], default="all",
+    ap.add_argument("--only", choices=["all", "plain", "batched", "served", "paper_sweep"], default="all",
                     help="run one part only (for profiling); the default runs everything")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the batch with the default kernel configuration instead of the tuned one")
@@ -528,6 +530,49 @@ def measure_served(env, args):
     return out
 
 
+def measure_paper_sweep(env, args):
+    """The paper's timing experiment (Fig. 2: time per event against the number of tracks on its
+    detector and 2048 x 2048 grid) on this GPU: the plain path, one event per step, device-resident
+    hits, L2 flushed before every step; and the FP64 oracle single-threaded on the host, at the
+    sizes it finishes within a few seconds."""
+    import oracle
+    torch, binding, stream = env.torch, env.binding, env.stream
+    points = []
+    oracle.build()
+    for nt in eg.PAPER_TRACK_COUNTS:
+        w = eg.paper_workload(nt)
+        ev = w.event(0)
+        tens = [torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
+        with binding.HoughContext(w.geometry, w.binning, max_hits=max(ev.n_hits, 1), max_candidates=1 << 18,
+                                  max_members=1 << 22, device=env.local) as ctx:
+            def step():
+                ctx.vote(*tens, n_hits=ev.n_hits, where=binding.DEVICE, stream=stream)
+                ctx.peaks(stream=stream)
+                ctx.stage2(stream=stream)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            k = 50
+            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+            for q in range(k):
+                env.flush.zero_()
+                e0[q].record(stream)
+                step()
+                e1[q].record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(b) for a, b in zip(e0, e1))
+        p = {"tracks": nt, "hits": int(ev.n_hits), "votes": int(st.votes), "candidates": int(st.n_candidates),
+             "gpu_ms_per_event": ms, "gpu_events_per_s": 1e3 / ms}
+        if nt <= 2000 or nt == eg.PAPER_TRACK_COUNTS[-1]:
+            t0 = time.perf_counter()
+            oracle.run(w.geometry, w.binning, ev)
+            p["oracle_ms_per_event_1_thread"] = (time.perf_counter() - t0) * 1e3
+        points.append(p)
+    return {"workload": WORKLOAD_TEXT["paper_2048"].replace("5000 helices", "N helices"), "points": points}
+
+
 def measure_e2e(env, args, ctx, ev):
     """hough_process from pinned host buffers: hits to the device, the path, candidates back."""
     torch, stream = env.torch, env.stream
@@ -558,8 +603,8 @@ def main():
         return
     env = Env()
     binding = env.binding
-    if args.only in ("batched", "served"):
-        out = measure_batched(env, args) if args.only == "batched" else measure_served(env, args)
+    if args.only in ("batched", "served", "paper_sweep"):
+        out = {"batched": measure_batched, "served": measure_served, "paper_sweep": measure_paper_sweep}[args.only](env, args)
         if env.rank == 0:
             print(json.dumps({"metric": METRIC, "part": args.only, **out}), flush=True)
         return
@@ -584,11 +629,12 @@ def main():
     with ClockSampler(env.local) as clock_sampler:
         plain = measure_plain(env, args, ctx, tens, n)
         if args.only == "plain":
-            batched = e2e = served = None
+            batched = e2e = served = paper = None
         else:
             batched = measure_batched(env, args)
             e2e = measure_e2e(env, args, ctx, ev)
             served = measure_served(env, args)
+            paper = measure_paper_sweep(env, args) if env.rank == 0 else None
     clocks = clock_sampler.summary()
     peaks, peaks_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -632,6 +678,7 @@ def main():
         "scatter_mode": scatter,
         "batched": batched,
         "served": served,
+        "paper_sweep": paper,
         "e2e": e2e,
         "gpu_launches": plain["launches"],
         "clocks": clocks,

@@ -75,6 +75,15 @@ def test_pileup_event_full_size(binding):
     assert r["got"]["stats"].refined_votes == 0
 
 
+@pytest.mark.parametrize("n_tracks", [100, 5000])
+def test_paper_geometry_2048_grid(binding, n_tracks):
+    """The paper's detector (ten layers evenly spaced to 110 cm, 0.4 mm resolution, transverse
+    plane) on its 2048 x 2048 grid, at a small and at the largest event of its timing sweep."""
+    w = eg.paper_workload(n_tracks)
+    r = check_event(binding, w.geometry, w.binning, w.event(0))
+    assert r["got"]["stats"].uniform_layers == (1 << 10) - 1
+
+
 def test_fine_binning_event_full_size(binding):
     """The 400k-hit, 1024 x 4096 event, every cell compared."""
     w = eg.WORKLOADS["fine_4m"]
