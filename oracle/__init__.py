@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ETRUNC = 0, -1, -2
+ACC_LAYERS, ACC_COUNTS = 0, 1   # accumulator kinds: layer bit masks, saturating vote counts
 
 
 def build(force: bool = False) -> str:
@@ -40,6 +41,7 @@ def build(force: bool = False) -> str:
 class Binning(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int32), ("n_qpt", ctypes.c_int32), ("n_phi", ctypes.c_int32),
                 ("threshold", ctypes.c_int32), ("n_cot", ctypes.c_int32), ("n_z0", ctypes.c_int32),
+                ("accumulator", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("b_tesla", ctypes.c_double), ("qpt_min", ctypes.c_double), ("qpt_max", ctypes.c_double),
                 ("cot_min", ctypes.c_double), ("cot_max", ctypes.c_double),
                 ("z0_min", ctypes.c_double), ("z0_max", ctypes.c_double)]
@@ -78,6 +80,7 @@ def make_binning(geometry, binning) -> Binning:
     """The oracle's view of a (Geometry, Binning) pair from the event generator."""
     return Binning(n_layers=geometry.n_layers, n_qpt=binning.n_qpt, n_phi=binning.n_phi,
                    threshold=binning.threshold, n_cot=binning.n_cot, n_z0=binning.n_z0,
+                   accumulator=int(getattr(binning, "accumulator", ACC_LAYERS)), pad=0,
                    b_tesla=geometry.b_tesla, qpt_min=binning.qpt_min, qpt_max=binning.qpt_max,
                    cot_min=binning.cot_min, cot_max=binning.cot_max,
                    z0_min=binning.z0_min, z0_max=binning.z0_max)
@@ -96,7 +99,9 @@ def _hits(event):
 
 
 def vote(b: Binning, event):
-    """Stage-1 vote.  Returns (M uint16 [n_qpt, n_phi], votes_by_layer uint64[16], flags)."""
+    """Stage-1 vote.  Returns (M uint16 [n_qpt, n_phi], votes_by_layer uint64[16], flags).
+
+    M holds layer masks or saturating vote counts, as ``b.accumulator`` says."""
     lib = _load()
     r, phi, _, layer = _hits(event)
     M = np.zeros((b.n_qpt, b.n_phi), dtype=np.uint16)

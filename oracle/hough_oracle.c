@@ -13,10 +13,13 @@
  *   1. vote   - every hit marks every cell of a discrete (curvature, azimuth)
  *               parameter grid that is consistent with it (Sec. 4; the
  *               A[B[i]] += 1 scatter of Sec. 8).  Curvature is q/pT, azimuth is
- *               the track direction at the beam line phi0, and a cell records
- *               which detector layers voted for it as a bit mask;
+ *               the track direction at the beam line phi0.  A cell records
+ *               either which detector layers voted for it, as a bit mask (the
+ *               layer accumulator), or how many votes it received, A[B[i]] += 1
+ *               literally, saturating at 65535 (the count accumulator);
  *   2. peaks  - cells with many votes that are local maxima of the grid are
- *               track candidates (Sec. 4, second step; Sec. 8);
+ *               track candidates (Sec. 4, second step; Sec. 8).  "Many votes"
+ *               is the number of layers of a mask, or the count itself;
  *   3. confirm - "more expensive computations" on each candidate (Sec. 4): the
  *               candidate's member hits vote in a second (cot theta, z0) grid.
  *
@@ -45,6 +48,9 @@
 #define ORACLE_EDGE_WINDOW 1e-4
 #define ORACLE_DOMAIN_WINDOW 1e-6
 
+#define ORACLE_ACC_LAYERS 0   /* a cell holds the bit mask of the layers that voted */
+#define ORACLE_ACC_COUNTS 1   /* a cell holds its number of votes, saturating at 65535 */
+
 #define ORACLE_OK 0
 #define ORACLE_EINVAL (-1)
 #define ORACLE_ETRUNC (-2)
@@ -56,6 +62,8 @@ typedef struct {
     int32_t threshold;
     int32_t n_cot;
     int32_t n_z0;
+    int32_t accumulator;   /* ORACLE_ACC_LAYERS or ORACLE_ACC_COUNTS */
+    int32_t pad;
     double b_tesla;
     double qpt_min, qpt_max;
     double cot_min, cot_max;
@@ -90,6 +98,12 @@ static int popcount16(uint32_t m)
     int c = 0;
     while (m) { c += (int)(m & 1u); m >>= 1; }
     return c;
+}
+
+/* The vote weight of a cell: its number of layers, or its count. */
+static int cell_value(const oracle_binning *b, uint16_t m)
+{
+    return b->accumulator == ORACLE_ACC_COUNTS ? (int)m : popcount16(m);
 }
 
 static int64_t floor_mod(int64_t a, int64_t n)
@@ -161,6 +175,8 @@ static int check_hits(const oracle_binning *b, const uint8_t *layer, int64_t n)
 {
     if (b->n_layers < 1 || b->n_layers > 16 || b->n_qpt < 1 || b->n_phi < 3)
         return ORACLE_EINVAL;
+    if (b->accumulator != ORACLE_ACC_LAYERS && b->accumulator != ORACLE_ACC_COUNTS)
+        return ORACLE_EINVAL;
     for (int64_t h = 0; h < n; ++h)
         if (layer[h] >= b->n_layers) return ORACLE_EINVAL;
     return ORACLE_OK;
@@ -169,6 +185,8 @@ static int check_hits(const oracle_binning *b, const uint8_t *layer, int64_t n)
 /*
  * Stage-1 vote (Sec. 4, first step).  M is n_qpt x n_phi, row-major, and is
  * overwritten.  votes_by_layer[l] counts the votes cast by hits of layer l.
+ * A vote ORs the hit's layer bit into its cell, or adds one to the cell's count
+ * (held at 65535 once it gets there).
  */
 int oracle_vote(const oracle_binning *b, const float *r, const float *phi, const uint8_t *layer,
                 int64_t n, uint16_t *M, uint64_t *votes_by_layer,
@@ -184,7 +202,12 @@ int oracle_vote(const oracle_binning *b, const float *r, const float *phi, const
             int32_t j, alt, kind;
             int cast = vote_one(b, (double)r[h], (double)phi[h], i, &j, &alt, &kind);
             if (cast) {
-                M[(size_t)i * b->n_phi + j] |= (uint16_t)(1u << l);
+                uint16_t *cell = &M[(size_t)i * b->n_phi + j];
+                if (b->accumulator == ORACLE_ACC_COUNTS) {
+                    if (*cell < 65535u) *cell = (uint16_t)(*cell + 1u);
+                } else {
+                    *cell |= (uint16_t)(1u << l);
+                }
                 votes_by_layer[l]++;
             }
             if (kind)
@@ -195,8 +218,9 @@ int oracle_vote(const oracle_binning *b, const float *r, const float *phi, const
 }
 
 /*
- * Peak search (Sec. 4, second step): a cell is a candidate when its layer count
- * p reaches the threshold, no neighbour of the 3 x 3 block exceeds it, and the
+ * Peak search (Sec. 4, second step): a cell is a candidate when its value p
+ * (layer accumulator: the number of layers in its mask; count accumulator: its
+ * count) reaches the threshold, no neighbour of the 3 x 3 block exceeds it, and the
  * four neighbours that precede it in raster order -- offsets (-1,-1), (-1,0),
  * (-1,+1), (0,-1) -- are strictly lower.  phi0 wraps; rows outside the grid
  * count as empty.  Candidates are listed in raster order.
@@ -207,7 +231,7 @@ int oracle_peaks(const oracle_binning *b, const uint16_t *M, oracle_candidate *o
     int64_t n = 0;
     for (int i = 0; i < b->n_qpt; ++i) {
         for (int j = 0; j < b->n_phi; ++j) {
-            int p = popcount16(M[(size_t)i * b->n_phi + j]);
+            int p = cell_value(b, M[(size_t)i * b->n_phi + j]);
             if (p < b->threshold) continue;
             int is_peak = 1;
             for (int di = -1; di <= 1 && is_peak; ++di) {
@@ -217,7 +241,7 @@ int oracle_peaks(const oracle_binning *b, const uint16_t *M, oracle_candidate *o
                     int q = 0;
                     if (ii >= 0 && ii < b->n_qpt) {
                         int jj = (int)floor_mod(j + dj, b->n_phi);
-                        q = popcount16(M[(size_t)ii * b->n_phi + jj]);
+                        q = cell_value(b, M[(size_t)ii * b->n_phi + jj]);
                     }
                     int precedes = (di < 0) || (di == 0 && dj < 0);
                     if (precedes ? (q >= p) : (q > p)) { is_peak = 0; break; }
@@ -310,7 +334,8 @@ int oracle_members(const oracle_binning *b, const float *r, const float *phi, co
  * votes in an n_cot x n_z0 grid of (cot theta, z0) with z0 = z - s * cot theta,
  * s the transverse arc length at the candidate's curvature.  z0 is not cyclic:
  * votes outside [z0_min, z0_max) are not cast.  The result is the cell of most
- * layers, the lowest row-major index on ties.
+ * layers, the lowest row-major index on ties.  With either stage-1 accumulator
+ * the second grid holds layer masks.
  */
 int oracle_stage2(const oracle_binning *b, const float *r, const float *z, const uint8_t *layer,
                   int64_t n, const oracle_candidate *c, int64_t n_cand,

@@ -330,6 +330,128 @@ def test_peaks_invariants_on_random_accumulators():
 
 
 # --------------------------------------------------------------------------------------------
+# The count accumulator (Sec. 8: A[B[i]] += 1): a cell holds its number of votes
+# --------------------------------------------------------------------------------------------
+
+def _counts_binning(geometry, binning, **kw):
+    return oracle.make_binning(geometry, eg.Binning(**{**binning.__dict__, "accumulator": eg.ACC_COUNTS, **kw}))
+
+
+def test_golden_count_peak_cases():
+    """Hand-derived cases (tests/golden/count_peak_cases.json), each read both ways: as counts and
+    as layer masks, which disagree on every case but one."""
+    with open(os.path.join(GOLDEN, "count_peak_cases.json")) as f:
+        spec = json.load(f)
+    for case in spec["cases"]:
+        nq, nphi = case["shape"]
+        M = np.zeros((nq, nphi), np.uint16)
+        for i, j, v in case["cells"]:
+            M[i, j] = v
+        for acc, key in ((eg.ACC_COUNTS, "expected"), (eg.ACC_LAYERS, "expected_layers")):
+            bn = eg.Binning(n_qpt=nq, qpt_min=-1, qpt_max=1, n_phi=nphi, threshold=case["threshold"],
+                            accumulator=acc)
+            got = [(int(c["iq"]), int(c["jphi"]), int(c["mask"])) for c in oracle.peaks(oracle.make_binning(GEOM, bn), M)]
+            assert [(i, j) for i, j, _ in got] == [tuple(x) for x in case[key]], (case["name"], key)
+            assert all(v == int(M[i, j]) for i, j, v in got)   # the candidate carries the cell's value
+
+
+def test_count_peaks_are_the_strict_maxima_of_distinct_counts():
+    """With every count distinct there are no ties, so the candidates are exactly the cells at or
+    above threshold that equal the maximum of their 3 x 3 block -- computed here with
+    scipy.ndimage.maximum_filter (phi0 wrapped, rows outside the grid empty)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(11)
+    for nq, nphi, thr in ((9, 16, 1), (17, 64, 900), (33, 128, 3000)):
+        M = (rng.permutation(nq * nphi) + 1).astype(np.uint16).reshape(nq, nphi)
+        padded = np.zeros((nq + 2, nphi + 2), np.int64)
+        padded[1:-1, 1:-1] = M
+        padded[1:-1, 0] = M[:, -1]
+        padded[1:-1, -1] = M[:, 0]
+        local_max = ndimage.maximum_filter(padded, size=3, mode="constant", cval=0)[1:-1, 1:-1]
+        expect = [(int(i), int(j)) for i, j in np.argwhere((M == local_max) & (M >= thr))]
+        bn = eg.Binning(n_qpt=nq, qpt_min=-1, qpt_max=1, n_phi=nphi, threshold=thr, accumulator=eg.ACC_COUNTS)
+        got = [(int(c["iq"]), int(c["jphi"])) for c in oracle.peaks(oracle.make_binning(GEOM, bn), M)]
+        assert got == expect and len(got) > 0
+
+
+def test_counts_are_sums_of_single_hit_votes():
+    """A cell's count is the number of hits whose vote fell in it: summing, over the hits one at a
+    time, the cells each single hit marks in the (pinned) layer accumulator gives the count
+    accumulator of the whole event, cell for cell."""
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(4).subset(np.arange(60))
+    bl = oracle.make_binning(w.geometry, w.binning)
+    bc = _counts_binning(w.geometry, w.binning)
+    expect = np.zeros((bl.n_qpt, bl.n_phi), np.int64)
+    for h in range(ev.n_hits):
+        Mh, _, _ = oracle.vote(bl, ev.subset(np.array([h])))
+        expect += Mh != 0
+    Mc, votes, _ = oracle.vote(bc, ev)
+    assert np.array_equal(Mc.astype(np.int64), expect)
+    assert int(Mc.sum()) == int(votes.sum())
+
+
+@pytest.mark.parametrize("name", ["single_50trk", "pileup_100k", "paper_500"])
+def test_counts_conserve_votes_and_bound_the_layer_masks(name):
+    """Unsaturated counts sum to the votes cast; a cell is non-empty in one accumulator exactly
+    when it is in the other, and its count is at least its number of layers."""
+    w = eg.paper_workload(500) if name == "paper_500" else eg.WORKLOADS[name]
+    ev = w.event(1)
+    if ev.n_hits > 20000:
+        ev = ev.subset(np.arange(20000))
+    Ml, vl, fl = oracle.vote(oracle.make_binning(w.geometry, w.binning), ev)
+    Mc, vc, fc = oracle.vote(_counts_binning(w.geometry, w.binning), ev)
+    assert np.array_equal(vl, vc) and np.array_equal(fl, fc)
+    assert int(Mc.max()) < 65535 and int(Mc.sum()) == int(vc.sum())
+    assert np.array_equal(Mc > 0, Ml != 0)
+    assert np.all(Mc >= _popcount(Ml))
+
+
+def test_counts_equal_layer_counts_for_one_hit_per_layer():
+    """A single track leaves at most one hit per layer, so no two votes in a cell share a layer:
+    every count equals the number of layers in the same cell's mask."""
+    rng = np.random.default_rng(21)
+    for geom, bn in ((GEOM, eg.BINNING_SMALL), (GEOM, eg.BINNING_PILEUP), (eg.PAPER_GEOMETRY, eg.BINNING_PAPER)):
+        i, j = int(rng.integers(2, bn.n_qpt - 2)), int(rng.integers(0, bn.n_phi))
+        k, phi0, _, _ = _centres(bn, i, j)
+        r, phi, z, layer, _ = eg.helix_hits(geom, [k], [phi0], [0.0], [0.0])
+        ev = _event(r, phi, z, layer)
+        Ml, _, _ = oracle.vote(oracle.make_binning(geom, bn), ev)
+        Mc, _, _ = oracle.vote(_counts_binning(geom, bn), ev)
+        assert np.array_equal(Mc.astype(np.int64), _popcount(Ml))
+        assert int(Mc[i, j]) == len(layer)
+
+
+def test_duplicated_hits_multiply_counts():
+    """Every hit taken d times: each count is d times the original, the layer masks do not change."""
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(6)
+    d = 3
+    dup = ev.subset(np.repeat(np.arange(ev.n_hits), d))
+    bl, bc = oracle.make_binning(w.geometry, w.binning), _counts_binning(w.geometry, w.binning)
+    Mc1, _, _ = oracle.vote(bc, ev)
+    Mcd, _, _ = oracle.vote(bc, dup)
+    assert np.array_equal(Mcd.astype(np.int64), d * Mc1.astype(np.int64))
+    assert np.array_equal(oracle.vote(bl, dup)[0], oracle.vote(bl, ev)[0])
+
+
+def test_counts_saturate_at_65535():
+    """70,000 copies of one hit: every cell it votes in holds 65535, the votes are all counted."""
+    bn = eg.Binning(n_qpt=2, qpt_min=-0.5, qpt_max=0.5, n_phi=64, threshold=1, accumulator=eg.ACC_COUNTS)
+    n = 70000
+    ev = _event(np.full(n, 30.0), np.full(n, 0.3), np.zeros(n), np.zeros(n, np.uint8))
+    M, votes, _ = oracle.vote(oracle.make_binning(GEOM, bn), ev)
+    assert int(votes.sum()) == 2 * n
+    assert sorted(M[M > 0].tolist()) == [65535, 65535] and np.count_nonzero(M[0]) == 1
+
+
+def test_unknown_accumulator_kind_is_rejected():
+    bn = eg.Binning(n_qpt=4, qpt_min=-1, qpt_max=1, n_phi=64, threshold=1, accumulator=2)
+    with pytest.raises(ValueError):
+        oracle.vote(oracle.make_binning(GEOM, bn), _event([30.0], [0.1], [0.0], [0]))
+
+
+# --------------------------------------------------------------------------------------------
 # Membership and the second-stage vote
 # --------------------------------------------------------------------------------------------
 
