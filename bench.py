@@ -14,8 +14,10 @@ replay per step), `served` (Poisson arrivals at 5k/20k/50k events/s through the 
 batching server against one launch per event), `e2e` (the public one-call entry point
 hough_process from pinned host buffers: host->device copy of the hits, the path, and the
 device->host read of the candidate list, timed on the host around each call), `scatter_mode`
-(the paper's shared-atomic vote design in place of the gather vote), and `cpu_baseline` (the
-FP64 oracle on this machine's host cores, on a bounded sample).
+(the paper's shared-atomic vote design in place of the gather vote), `count_accumulator` (cells
+holding vote counts, the paper's literal A[B[i]] += 1, on the pileup event and the paper's grid),
+`paper_sweep` (the paper's Fig. 2 experiment) and `cpu_baseline` (the FP64 oracle on this
+machine's host cores, on a bounded sample).
 
 `--impl reference` times the FP64 CPU oracle (the plain restatement of the method the CUDA path is
 checked against) on the host cores, on the same workload and metric.
@@ -68,7 +70,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--only", choices=["all", "plain", "batched", "served", "paper_sweep"], default="all",
+    ap.add_argument("--only", choices=["all", "plain", "batched", "served", "paper_sweep", "counts"], default="all",
                     help="run one part only (for profiling); the default runs everything")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the batch with the default kernel configuration instead of the tuned one")
@@ -573,6 +575,80 @@ def measure_paper_sweep(env, args):
     return {"workload": WORKLOAD_TEXT["paper_2048"].replace("5000 helices", "N helices"), "points": points}
 
 
+def count_workloads():
+    """The count accumulator's workloads: (name, workload, what it is)."""
+    acc = eg.ACC_COUNTS
+    return [
+        ("pileup_100k", eg.with_binning(eg.WORKLOADS["pileup_100k"], accumulator=acc, threshold=70),
+         WORKLOAD_TEXT["pileup_100k"].replace("uint16 layer masks, threshold >=7",
+                                              "uint16 vote counts, threshold >=70 votes (about 48 per cell)")),
+        ("paper_2048_500", eg.with_binning(eg.paper_workload(500), accumulator=acc, threshold=8),
+         WORKLOAD_TEXT["paper_2048"].replace("5000 helices", "500 helices").replace(
+             "threshold >=8", "uint16 vote counts, threshold >=8 votes")),
+    ]
+
+
+def measure_counts(env, args, smem_peak=None, hbm_peak=None):
+    """The count accumulator (A[B[i]] += 1 of Sec. 8: a cell holds its number of votes, saturating
+    at 65535; the shared-memory scatter kernel votes, the peak search reads counts): the plain path,
+    one event per step, device-resident hits, L2 flushed before every step, then an attribution
+    pass with an event after every kernel."""
+    torch, binding, stream = env.torch, env.binding, env.stream
+    out = {}
+    for name, w, text in count_workloads():
+        ev = w.event(replicas.event_indices(env.rank, env.world, 1)[0])
+        tens = [torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
+        with binding.HoughContext(w.geometry, w.binning, max_hits=max(ev.n_hits, 1), max_candidates=1 << 18,
+                                  max_members=1 << 23, device=env.local) as ctx:
+            def step():
+                ctx.vote(*tens, n_hits=ev.n_hits, where=binding.DEVICE, stream=stream)
+                ctx.peaks(stream=stream)
+                ctx.stage2(stream=stream)
+
+            def timed(k, attribute):
+                e0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+                e1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+                lib_t = []
+                for q in range(k):
+                    env.flush.zero_()
+                    e0[q].record(stream)
+                    step()
+                    e1[q].record(stream)
+                    if attribute:
+                        lib_t.append(ctx.timing())
+                torch.cuda.synchronize()
+                return [a.elapsed_time(b) for a, b in zip(e0, e1)], lib_t
+
+            ctx.enable_timing(False)
+            for _ in range(max(3, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            env.barrier()
+            step_ms, _ = timed(args.steps, False)
+            total = env.max_over_ranks(sum(step_ms))
+            ctx.enable_timing(True)
+            step()
+            _, lib_t = timed(min(args.steps, 30), True)
+            ctx.enable_timing(False)
+            t = {k: statistics.mean(x[k] for x in lib_t) for k in lib_t[0]}
+        cells = w.binning.n_qpt * w.binning.n_phi
+        vote_ms = t["scatter_ms"]
+        p = {"workload": text, "hits": int(ev.n_hits), "votes": int(st.votes), "candidates": int(st.n_candidates),
+             "members": int(st.n_members), "events_per_s": replicas.job_rate(args.steps, env.world, total * 1e-3),
+             "ms_per_event": total / args.steps, "stage_ms": t["stage_ms"], "vote_ms": vote_ms,
+             "peaks_ms": t["peaks_ms"], "stage2_ms": t["stage2_ms"],
+             "votes_per_s_in_vote_kernel": st.votes / (vote_ms * 1e-3) if vote_ms > 0 else None}
+        if smem_peak and vote_ms > 0:
+            p["vote_kernel_vs_smem_atomic_peak"] = p["votes_per_s_in_vote_kernel"] / smem_peak
+        if hbm_peak and vote_ms > 0:
+            gbs = (13 * ev.n_hits + 2 * cells) / (vote_ms * 1e-3) / 1e9
+            p["vote_kernel_hbm"] = {"achieved_gbs": gbs, "frac": gbs / hbm_peak,
+                                    "algorithmic": "13 B per hit in, 2 B per cell out"}
+        out[name] = p
+    return out
+
+
 def measure_e2e(env, args, ctx, ev):
     """hough_process from pinned host buffers: hits to the device, the path, candidates back."""
     torch, stream = env.torch, env.stream
@@ -603,8 +679,9 @@ def main():
         return
     env = Env()
     binding = env.binding
-    if args.only in ("batched", "served", "paper_sweep"):
-        out = {"batched": measure_batched, "served": measure_served, "paper_sweep": measure_paper_sweep}[args.only](env, args)
+    if args.only in ("batched", "served", "paper_sweep", "counts"):
+        out = {"batched": measure_batched, "served": measure_served, "paper_sweep": measure_paper_sweep,
+               "counts": measure_counts}[args.only](env, args)
         if env.rank == 0:
             print(json.dumps({"metric": METRIC, "part": args.only, **out}), flush=True)
         return
@@ -628,16 +705,17 @@ def main():
     smem_peak_rand = binding.smem_or_throughput(env.local, 1, 30.0)
     with ClockSampler(env.local) as clock_sampler:
         plain = measure_plain(env, args, ctx, tens, n)
+        peaks, peaks_kind = measured_peaks()
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
         if args.only == "plain":
-            batched = e2e = served = paper = None
+            batched = e2e = served = paper = counts = None
         else:
             batched = measure_batched(env, args)
             e2e = measure_e2e(env, args, ctx, ev)
             served = measure_served(env, args)
             paper = measure_paper_sweep(env, args) if env.rank == 0 else None
+            counts = measure_counts(env, args, smem_peak, hbm_peak)
     clocks = clock_sampler.summary()
-    peaks, peaks_kind = measured_peaks()
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     kernels = kernel_table(env, w, n, plain, smem_peak, hbm_peak, peaks_kind, clocks)
     dominant = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dominant]
@@ -679,6 +757,7 @@ def main():
         "batched": batched,
         "served": served,
         "paper_sweep": paper,
+        "count_accumulator": counts,
         "e2e": e2e,
         "gpu_launches": plain["launches"],
         "clocks": clocks,

@@ -71,19 +71,29 @@ typedef struct hough_geometry {
     double  b_tesla;    /* field in tesla, > 0 */
 } hough_geometry;
 
+/* What a stage-1 cell holds (hough_binning.accumulator). */
+#define HOUGH_ACC_LAYERS 0   /* bit l set when a hit of layer l voted for the cell */
+#define HOUGH_ACC_COUNTS 1   /* the number of votes the cell received (Sec. 8: A[B[i]] += 1), saturating at 65535 */
+
 /*
  * Accumulator axes (Sec. 4: "a discrete grid in the parameter space").
  * Stage 1: n_qpt rows of q/pT over [qpt_min, qpt_max] (c/GeV) by n_phi columns
- * of phi0 over [-pi, pi), cyclic.  A cell is a candidate when popcount(mask) >=
- * threshold and it is a local maximum (see hough_peaks).  Stage 2: n_cot rows
- * of cot(theta) over [cot_min, cot_max] by n_z0 columns of z0 over
- * [z0_min_cm, z0_max_cm), not cyclic.
+ * of phi0 over [-pi, pi), cyclic.  A cell's value is popcount(mask) with the
+ * layer accumulator, its count with the count accumulator; a cell is a
+ * candidate when its value >= threshold and it is a local maximum (see
+ * hough_peaks).  Stage 2: n_cot rows of cot(theta) over [cot_min, cot_max] by
+ * n_z0 columns of z0 over [z0_min_cm, z0_max_cm), not cyclic; its cells hold
+ * layer masks with either accumulator.
  * Limits: 1 <= n_qpt <= 65535; 64 <= n_phi <= 32768 and n_phi % 64 == 0;
- * 1 <= threshold <= 16; 1 <= n_cot, n_z0 <= 256 and n_cot * n_z0 <= 16384;
+ * 1 <= threshold <= 16 (layer accumulator) or <= 65535 (count accumulator);
+ * 1 <= n_cot, n_z0 <= 256 and n_cot * n_z0 <= 16384;
  * qpt_min < qpt_max, cot_min < cot_max, z0_min_cm < z0_max_cm.
+ * The count accumulator votes with the shared-memory scatter kernel
+ * (HOUGH_VOTE_SCATTER): the gather decides whether a layer voted, not how often.
  */
 typedef struct hough_binning {
-    int32_t n_qpt, n_phi, threshold, n_cot, n_z0, reserved;
+    int32_t n_qpt, n_phi, threshold, n_cot, n_z0;
+    int32_t accumulator;   /* HOUGH_ACC_LAYERS or HOUGH_ACC_COUNTS */
     double  qpt_min, qpt_max;
     double  cot_min, cot_max;
     double  z0_min_cm, z0_max_cm;
@@ -97,12 +107,14 @@ typedef struct hough_limits {
 } hough_limits;
 
 /*
- * One track candidate.  (iq, jphi) is the stage-1 cell, mask its layer mask;
- * n_members the hits whose stage-1 vote fell in the cell; (icot, jz0) the
- * stage-2 maximum (most layers, lowest row-major index on ties) and mask2 its
- * layer mask.  flags: bit 0 set when popcount(mask2) >= threshold (confirmed),
- * bit 1 when the member list was cut by max_members.  The stage-2 fields are 0
- * until hough_stage2 has run.
+ * One track candidate.  (iq, jphi) is the stage-1 cell, mask its value as
+ * stored (the layer mask, or with the count accumulator the count); n_members
+ * the hits whose stage-1 vote fell in the cell (with the count accumulator
+ * equal to the count below saturation); (icot, jz0) the stage-2 maximum (most
+ * layers, lowest row-major index on ties) and mask2 its layer mask.  flags:
+ * bit 0 set when popcount(mask2) >= min(threshold, n_layers) (confirmed), bit 1
+ * when the member list was cut by max_members.  The stage-2 fields are 0 until
+ * hough_stage2 has run.
  */
 typedef struct hough_candidate {
     uint32_t iq, jphi, mask, n_members;
@@ -155,9 +167,10 @@ int hough_vote(hough_ctx *ctx, const float *r, const float *phi, const float *z,
 
 /*
  * Peak search (Sec. 4, second step) on the accumulator of the last vote: cell
- * (i, j) with layer count p = popcount(mask) is a candidate when p >= threshold,
- * no 3 x 3 neighbour has a larger count and the neighbours at offsets (-1,-1),
- * (-1,0), (-1,+1), (0,-1) have strictly smaller counts.  phi0 wraps; rows
+ * (i, j) with value p (popcount(mask), or the count with HOUGH_ACC_COUNTS) is a
+ * candidate when p >= threshold, no 3 x 3 neighbour has a larger value and the
+ * neighbours at offsets (-1,-1), (-1,0), (-1,+1), (0,-1) have strictly smaller
+ * values.  phi0 wraps; rows
  * outside the grid count as empty.  Candidates are kept in raster order.
  * Asynchronous on `stream`.
  */
@@ -216,9 +229,13 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
  * CTA owning a tile of tile_qpt rows x tile_phi columns in shared memory.
  * The peak search works on bands of band_rows rows.
  *
+ * With the count accumulator the vote takes the scatter kernel, whose tile holds 32-bit counters
+ * that are saturated to 16 bits when the tile is written out; HOUGH_VOTE_GATHER is refused.
+ *
  * tile_phi must divide n_phi and be a multiple of 64; tile_qpt in 1..256; threads in
- * {128, 256, 512, 1024}; tile_qpt * tile_phi * 2 bytes must fit in shared memory; band_rows in
- * 1..16 with (band_rows + 2) * n_phi bytes of shared memory; gather_rows in 1..32 (0: 4);
+ * {128, 256, 512, 1024}; tile_qpt * tile_phi * 2 bytes (4 with the count accumulator) must fit
+ * in shared memory; band_rows in 1..16 with (band_rows + 2) * n_phi bytes (twice that with the
+ * count accumulator) of shared memory; gather_rows in 1..32 (0: 4);
  * gather_cols a multiple of 64 dividing n_phi (0: the largest such up to 512) with
  * n_layers * (gather_cols + 64) * 8 bytes of shared memory; gather_threads in {256, 512, 1024}
  * (0: 256).  HOUGH_EINVAL otherwise.  Every configuration gives the same results.
@@ -488,7 +505,8 @@ int hough_serve_inject(hough_server *server, int fault, int on);
  *
  * Runs the staging and vote kernels of hough_vote on the hits r, phi, z, layer (device pointers,
  * n_hits entries, same meaning and checks as hough_vote with HOUGH_DEVICE) and writes the
- * n_qpt x n_phi row-major layer masks to `accumulator` (device, caller-owned).  If `device_error`
+ * n_qpt x n_phi row-major cells -- layer masks, or counts with HOUGH_ACC_COUNTS -- to
+ * `accumulator` (device, caller-owned).  If `device_error`
  * is not NULL it receives (device memory, asynchronously) the HOUGH_DEVERR_* bits of dropped hits.
  * The geometry and binning are read at each call; the stage-2 fields of the binning are ignored.
  *

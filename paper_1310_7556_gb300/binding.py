@@ -35,7 +35,7 @@ class Geometry(ctypes.Structure):
 
 class Binning(ctypes.Structure):
     _fields_ = [("n_qpt", ctypes.c_int32), ("n_phi", ctypes.c_int32), ("threshold", ctypes.c_int32),
-                ("n_cot", ctypes.c_int32), ("n_z0", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_cot", ctypes.c_int32), ("n_z0", ctypes.c_int32), ("accumulator", ctypes.c_int32),
                 ("qpt_min", ctypes.c_double), ("qpt_max", ctypes.c_double),
                 ("cot_min", ctypes.c_double), ("cot_max", ctypes.c_double),
                 ("z0_min_cm", ctypes.c_double), ("z0_max_cm", ctypes.c_double)]
@@ -74,6 +74,7 @@ class Tiling(ctypes.Structure):
 
 
 VOTE_GATHER, VOTE_SCATTER = 0, 1
+ACC_LAYERS, ACC_COUNTS = 0, 1   # hough_binning.accumulator: layer masks, saturating vote counts
 
 
 class ServeConfig(ctypes.Structure):
@@ -238,7 +239,8 @@ def make_geometry(geometry) -> Geometry:
 
 def make_binning(binning) -> Binning:
     return Binning(n_qpt=binning.n_qpt, n_phi=binning.n_phi, threshold=binning.threshold,
-                   n_cot=binning.n_cot, n_z0=binning.n_z0, reserved=0,
+                   n_cot=binning.n_cot, n_z0=binning.n_z0,
+                   accumulator=int(getattr(binning, "accumulator", ACC_LAYERS)),
                    qpt_min=binning.qpt_min, qpt_max=binning.qpt_max,
                    cot_min=binning.cot_min, cot_max=binning.cot_max,
                    z0_min_cm=binning.z0_min, z0_max_cm=binning.z0_max)

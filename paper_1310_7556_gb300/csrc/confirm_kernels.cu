@@ -15,7 +15,8 @@
 // a CTA each, which re-reads them from the pool (or re-enumerates them, when the pool overflowed)
 // in chunks of kLargeChunk.
 //
-// Membership: only layers present in the candidate's mask can hold members.  For a table layer
+// Membership: only layers present in the candidate's mask can hold members (with the count
+// accumulator the cell holds a count, and every layer is scanned).  For a table layer
 // the vote inverts exactly -- a hit of bucket J votes into column j on row i when
 // J = j + I_i + (f < g_i) -- so two buckets of the sorted hits hold all of that layer's members;
 // other layers scan the buckets their radius range allows and redo the vote per hit (FP32 with
@@ -112,6 +113,8 @@ __device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t 
                               unsigned char *lay = nullptr)
 {
     const int lane = threadIdx.x & 31;
+    // a count says nothing of which layers voted: every layer may hold members
+    if (ax.counts) mask = 0xFFFFu;
     // lane l < 16: layer l's ranges
     int st0 = 0, len0 = 0, st1 = 0, len1 = 0;
     unsigned char k0 = 0, k1 = 0;
@@ -340,7 +343,7 @@ __device__ __forceinline__ hough_candidate finished(const Axes &ax, hough_candid
     cd.icot = b.cell / (unsigned)ax.n_z0;
     cd.jz0 = b.cell % (unsigned)ax.n_z0;
     cd.mask2 = b.mask;
-    cd.flags = ((int)b.cnt >= ax.threshold ? 1u : 0u) | (written < n ? 2u : 0u);
+    cd.flags = ((int)b.cnt >= min(ax.threshold, ax.n_layers) ? 1u : 0u) | (written < n ? 2u : 0u);
     return cd;
 }
 

@@ -99,11 +99,16 @@ int check_binning(const hough_geometry *g, const hough_binning *b)
 {
     if (!g || !b) return fail(HOUGH_EINVAL, "geometry and binning are required");
     if (g->n_layers < 1 || g->n_layers > HOUGH_MAX_LAYERS) return fail(HOUGH_EINVAL, "n_layers must be 1..16");
-    if (g->reserved != 0 || b->reserved != 0) return fail(HOUGH_EINVAL, "reserved fields must be 0");
+    if (g->reserved != 0) return fail(HOUGH_EINVAL, "reserved fields must be 0");
+    if (b->accumulator != HOUGH_ACC_LAYERS && b->accumulator != HOUGH_ACC_COUNTS)
+        return fail(HOUGH_EINVAL, "accumulator must be HOUGH_ACC_LAYERS or HOUGH_ACC_COUNTS");
     if (!(g->b_tesla > 0.0) || !std::isfinite(g->b_tesla)) return fail(HOUGH_EINVAL, "b_tesla must be > 0");
     if (b->n_qpt < 1 || b->n_qpt > 65535) return fail(HOUGH_EINVAL, "n_qpt must be 1..65535");
     if (b->n_phi < 64 || b->n_phi > 32768 || b->n_phi % 64) return fail(HOUGH_EINVAL, "n_phi must be a multiple of 64 in 64..32768");
-    if (b->threshold < 1 || b->threshold > 16) return fail(HOUGH_EINVAL, "threshold must be 1..16");
+    if (b->accumulator == HOUGH_ACC_LAYERS && (b->threshold < 1 || b->threshold > 16))
+        return fail(HOUGH_EINVAL, "threshold must be 1..16 layers");
+    if (b->accumulator == HOUGH_ACC_COUNTS && (b->threshold < 1 || b->threshold > 65535))
+        return fail(HOUGH_EINVAL, "threshold must be 1..65535 votes");
     if (b->n_cot < 1 || b->n_cot > 256 || b->n_z0 < 1 || b->n_z0 > 256 || b->n_cot * b->n_z0 > 16384)
         return fail(HOUGH_EINVAL, "n_cot and n_z0 must be 1..256 with n_cot * n_z0 <= 16384");
     if (!(b->qpt_min < b->qpt_max) || !(b->cot_min < b->cot_max) || !(b->z0_min_cm < b->z0_max_cm))
@@ -121,6 +126,7 @@ Axes make_axes_impl(const hough_geometry *g, const hough_binning *b)
     ax.n_qpt = b->n_qpt;
     ax.n_phi = b->n_phi;
     ax.threshold = b->threshold;
+    ax.counts = b->accumulator == HOUGH_ACC_COUNTS ? 1 : 0;
     ax.n_cot = b->n_cot;
     ax.n_z0 = b->n_z0;
     ax.b = g->b_tesla;
@@ -180,15 +186,17 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
         return fail(HOUGH_EINVAL, "gather_cols must be 0 or a multiple of 64 dividing n_phi");
     if (t->gather_threads && t->gather_threads != 256 && t->gather_threads != 512 && t->gather_threads != 1024)
         return fail(HOUGH_EINVAL, "gather_threads must be 0, 256, 512 or 1024");
+    if (ax.counts && t->vote_mode != HOUGH_VOTE_SCATTER)
+        return fail(HOUGH_EINVAL, "the count accumulator needs vote_mode HOUGH_VOTE_SCATTER");
     const Tiling tt = resolve_tiling_impl(ax, t);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (vote_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "tile needs %zu bytes of shared memory, the device allows %d",
                     vote_smem_bytes(ax, tt), max_smem);
-    if ((size_t)(t->band_rows + 2) * ax.n_phi + 1024 > (size_t)max_smem)
+    if (band_smem_bytes(ax, t->band_rows) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "band of %d rows needs %zu bytes of shared memory, the device allows %d",
-                    t->band_rows, (size_t)(t->band_rows + 2) * ax.n_phi, max_smem);
+                    t->band_rows, band_smem_bytes(ax, t->band_rows), max_smem);
     if (gather_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "gather tile needs %zu bytes of shared memory, the device allows %d",
                     gather_smem_bytes(ax, tt), max_smem);
@@ -202,7 +210,7 @@ Tiling default_tiling_impl(const Axes &ax)
     while (ax.n_phi % t.tile_phi) t.tile_phi -= 64;
     t.tile_qpt = std::min(ax.n_qpt, 16);
     t.threads = 256;
-    t.vote_mode = HOUGH_VOTE_GATHER;
+    t.vote_mode = ax.counts ? HOUGH_VOTE_SCATTER : HOUGH_VOTE_GATHER;
     t.band_rows = 1;
     t.gather_rows = 4;
     t.gather_cols = default_gather_cols(ax);

@@ -33,6 +33,7 @@ constexpr double kInvTwoPi = 0.15915494309189535;  // 1 / (2 pi) rounded to doub
 // Axes of the two grids, by value into every kernel.
 struct Axes {
     int n_layers, n_qpt, n_phi, threshold, n_cot, n_z0;
+    int counts;                   // 1: cells hold saturating vote counts; 0: layer masks
     double b, qpt_min, qpt_max, dk;
     double cot_min, cot_max, dt, z0_min, z0_max;
     double zscale;                // n_z0 / (z0_max - z0_min): z0 bins per cm
@@ -205,6 +206,8 @@ cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t to
 cudaError_t run_smem_or_bench(int device, int pattern, double ms, double *atomics_per_s, uint64_t *launches);
 
 size_t vote_smem_bytes(const Axes &ax, const Tiling &t);
+// Shared memory of the peak search over bands of band_rows rows.
+size_t band_smem_bytes(const Axes &ax, int band_rows);
 size_t stage2_smem_bytes(const Axes &ax);
 
 // Host helpers shared by the single-event and the batch entry points (hough_api.cu).
@@ -424,15 +427,16 @@ __device__ __forceinline__ int wrap_col(int j, int n)
     return j >= n ? j - n : j;
 }
 
-// Peak test of the cells of rows 1..nrows of a band held as layer counts in shared memory
-// (`pc`, (nrows + 2) rows of Nphi bytes, row 0 and row nrows + 1 the halo), in raster order.
-// A cell with count p is a candidate when p >= threshold, the neighbours at (-1,-1), (-1,0),
+// Peak test of the cells of rows 1..nrows of a band held as cell values in shared memory
+// (`pc`, (nrows + 2) rows of Nphi values of type V -- layer counts as bytes, or 16-bit vote
+// counts -- row 0 and row nrows + 1 the halo), in raster order.
+// A cell with value p is a candidate when p >= threshold, the neighbours at (-1,-1), (-1,0),
 // (-1,+1), (0,-1) are below p and the other four are not above it; phi0 wraps.  Each thread tests
 // 8 consecutive cells per pass, so thread order is raster order and one block-wide scan of the
 // per-thread counts places every candidate.  Candidates go to `out` (cell index i * Nphi + j,
 // mask read from M) in raster order; returns their number.  Called by all TPB threads.
-template <int TPB>
-__device__ __forceinline__ int band_peak_search(const unsigned char *pc, int nrows, int i0, int nphi, int threshold,
+template <int TPB, typename V>
+__device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, int nphi, int threshold,
                                                 const uint16_t *M, uint2 *out, int cap)
 {
     __shared__ int s_warp[TPB / 32];
@@ -448,8 +452,8 @@ __device__ __forceinline__ int band_peak_search(const unsigned char *pc, int nro
         if (it < items) {
             rr = it / eighth;
             j0 = (it - rr * eighth) * 8;
-            const unsigned char *row = pc + (rr + 1) * nphi;
-            const unsigned char *up = row - nphi, *dn = row + nphi;
+            const V *row = pc + (rr + 1) * nphi;
+            const V *up = row - nphi, *dn = row + nphi;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int j = j0 + c;

@@ -91,6 +91,8 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
         return fail(HOUGH_EINVAL, "n_layers must be 1..16 and b_tesla > 0");
     if (b->n_qpt < 1 || b->n_phi < 64 || b->n_phi % 64 || b->threshold < 1 || !(b->qpt_min < b->qpt_max))
         return fail(HOUGH_EINVAL, "invalid binning");
+    if (b->accumulator != HOUGH_ACC_LAYERS && b->accumulator != HOUGH_ACC_COUNTS)
+        return fail(HOUGH_EINVAL, "accumulator must be HOUGH_ACC_LAYERS or HOUGH_ACC_COUNTS");
     if (b->n_qpt > kStaticMaxQpt || b->n_phi > kStaticMaxPhi)
         return fail(HOUGH_ECAPACITY, "hough_vote_static: n_qpt must be <= 1024 and n_phi <= 4096");
     if (n_hits < 0) return fail(HOUGH_EINVAL, "n_hits must be >= 0");

@@ -17,7 +17,10 @@
 //    hits that can vote into its tile -- per layer one or two contiguous ranges of the
 //    (layer, phi bin)-sorted hits -- lane by lane, and loops over the tile's rows in lockstep, so a
 //    warp's 32 same-layer, azimuth-sorted hits update neighbouring words of one row; a lane whose
-//    (word, bit) equals its left neighbour's skips its atomicOr.  Table layers vote at
+//    (word, bit) equals its left neighbour's skips its atomicOr.  With the count accumulator the
+//    tile holds a 32-bit counter per cell instead: each run of lanes voting into the same cell
+//    adds its length with one atomicAdd from its first lane, and the flush saturates every counter
+//    to 16 bits -- the literal A[B[i]] += 1 of Sec. 8.  Table layers vote at
 //    J - I - (f < g); other layers take FP32 asinf per vote, and a vote within `refine_eps` of an
 //    edge (or with |x| > kRefineXLim) is recomputed in FP64 in the definition's order.  In the
 //    default (gather) mode this kernel handles only the layers whose radii differ and ORs its tile
@@ -58,9 +61,10 @@ __device__ __forceinline__ void layer_masks(const Workspace &w, int L, unsigned 
     *general_out = __ballot_sync(0xFFFFFFFFu, l < L && li.present && !li.uniform);
 }
 
-template <int TPB, bool GENERAL_ONLY>
+template <int TPB, bool GENERAL_ONLY, bool COUNTS>
 __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 {
+    static_assert(!(GENERAL_ONLY && COUNTS), "the count accumulator votes every layer here");
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_start[kMaxRanges];
@@ -70,8 +74,9 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 
     const Axes &ax = p.ax;
     const int R = p.R, W = p.W, Wh = W >> 1, L = ax.n_layers, nphi = ax.n_phi;
-    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
-    TabEntry *tab = reinterpret_cast<TabEntry *>(tile + R * Wh);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);   // 2 masks a word, or 1 counter a word
+    const int tile_words = COUNTS ? R * W : R * Wh;
+    TabEntry *tab = reinterpret_cast<TabEntry *>(tile + tile_words);
     float *kq = reinterpret_cast<float *>(tab + L * R);
 
     const int e = blockIdx.x / p.tiles_per_event;
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 
     // clear the tile; stage this slab's table rows and FP32 q/pT centres
     uint4 *tile4 = reinterpret_cast<uint4 *>(tile);
-    for (int q = threadIdx.x; q < (R * Wh) >> 2; q += TPB) tile4[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = threadIdx.x; q < tile_words >> 2; q += TPB) tile4[q] = make_uint4(0u, 0u, 0u, 0u);
     for (int q = threadIdx.x; q < L * R; q += TPB) {
         const int l = q / R, rr = q - l * R;
         TabEntry te;
@@ -242,6 +247,19 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
             j -= j >= nphi ? nphi : 0;
             const int jt = j - J0;
             const bool in = act && (unsigned)jt < (unsigned)W;
+            if (COUNTS) {
+                // runs of lanes with the same cell: the first lane of a run adds the run's length
+                const uint32_t cell = in ? (uint32_t)(rr * W + jt) : 0xFFFFFFFFu;
+                const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cell, 1);
+                const bool head = lane == 0 || prev != cell;
+                const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+                if (in && head) {
+                    const unsigned later = lane == 31 ? 0u : heads & (0xFFFFFFFFu << (lane + 1));
+                    const int end = later ? __ffs(later) - 1 : 32;
+                    atomicAdd(&tile[cell], (uint32_t)(end - lane));
+                }
+                continue;
+            }
             const int word = rr * Wh + (jt >> 1);
             const uint32_t tag = in ? (((uint32_t)word << 5) | ((uint32_t)l << 1) | (uint32_t)(jt & 1)) : 0xFFFFFFFFu;
             const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, tag, 1);
@@ -257,6 +275,13 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     for (int q = threadIdx.x; q < nrows * v8; q += TPB) {
         const int rr = q / v8, c8 = q - rr * v8;
         uint4 *dst = reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + J0 + c8 * 8);
+        if (COUNTS) {
+            // 8 counters, saturated to 16 bits and packed two a word
+            const uint4 a = tile4[2 * (rr * v8 + c8)], b = tile4[2 * (rr * v8 + c8) + 1];
+            auto pack = [](uint32_t lo, uint32_t hi) { return min(lo, 65535u) | (min(hi, 65535u) << 16); };
+            *dst = make_uint4(pack(a.x, a.y), pack(a.z, a.w), pack(b.x, b.y), pack(b.z, b.w));
+            continue;
+        }
         uint4 v = tile4[rr * v8 + c8];
         if (GENERAL_ONLY) {
             const uint4 old = *dst;
@@ -438,6 +463,9 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
 
 
 // Peak search of one band of band_rows rows from the accumulator (plus a halo row on each side).
+// COUNTS: the cells are vote counts, staged as they are (2 bytes each); otherwise layer masks,
+// staged as their layer counts (1 byte each).
+template <bool COUNTS>
 __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w)
 {
     pdl_enter();
@@ -450,6 +478,21 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
     const int nrows = min(R, ax.n_qpt - i0);
     const uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
     const int v8 = nphi >> 3;
+    uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
+    if (COUNTS) {
+        uint16_t *pv = reinterpret_cast<uint16_t *>(pc);
+        for (int q = threadIdx.x; q < (nrows + 2) * v8; q += kPeakThreads) {
+            const int rr = q / v8, c8 = q - rr * v8;
+            const int i = i0 - 1 + rr;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (i >= 0 && i < ax.n_qpt) v = *reinterpret_cast<const uint4 *>(M + (int64_t)i * nphi + c8 * 8);
+            *reinterpret_cast<uint4 *>(pv + rr * nphi + c8 * 8) = v;
+        }
+        __syncthreads();
+        const int cnt = band_peak_search<kPeakThreads>(pv, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
+        if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+        return;
+    }
     for (int q = threadIdx.x; q < (nrows + 2) * v8; q += kPeakThreads) {
         const int rr = q / v8, c8 = q - rr * v8;
         const int i = i0 - 1 + rr;
@@ -465,7 +508,6 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
         *reinterpret_cast<uint2 *>(pc + rr * nphi + c8 * 8) = make_uint2(packed[0], packed[1]);
     }
     __syncthreads();
-    uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
     const int cnt = band_peak_search<kPeakThreads>(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
     if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
 }
@@ -625,23 +667,23 @@ __global__ void pack_candidates_kernel(Workspace w, hough_candidate *out, long l
     }
 }
 
-template <int TPB, bool GENERAL_ONLY>
+template <int TPB, bool GENERAL_ONLY, bool COUNTS>
 cudaError_t launch_scatter(const VoteParams &p, size_t smem, int grid, cudaStream_t stream)
 {
-    cudaError_t err = cudaFuncSetAttribute(scatter_kernel<TPB, GENERAL_ONLY>,
+    cudaError_t err = cudaFuncSetAttribute(scatter_kernel<TPB, GENERAL_ONLY, COUNTS>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err) return err;
-    return launch_chained(scatter_kernel<TPB, GENERAL_ONLY>, dim3(grid), dim3(TPB), smem, stream, p);
+    return launch_chained(scatter_kernel<TPB, GENERAL_ONLY, COUNTS>, dim3(grid), dim3(TPB), smem, stream, p);
 }
 
-template <bool GENERAL_ONLY>
+template <bool GENERAL_ONLY, bool COUNTS>
 cudaError_t launch_scatter_tpb(const VoteParams &p, int threads, size_t smem, int grid, cudaStream_t stream)
 {
     switch (threads) {
-    case 128: return launch_scatter<128, GENERAL_ONLY>(p, smem, grid, stream);
-    case 256: return launch_scatter<256, GENERAL_ONLY>(p, smem, grid, stream);
-    case 512: return launch_scatter<512, GENERAL_ONLY>(p, smem, grid, stream);
-    case 1024: return launch_scatter<1024, GENERAL_ONLY>(p, smem, grid, stream);
+    case 128: return launch_scatter<128, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
+    case 256: return launch_scatter<256, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
+    case 512: return launch_scatter<512, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
+    case 1024: return launch_scatter<1024, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -650,8 +692,8 @@ cudaError_t launch_scatter_tpb(const VoteParams &p, int threads, size_t smem, in
 
 size_t vote_smem_bytes(const Axes &ax, const Tiling &t)
 {
-    return (size_t)t.tile_qpt * t.tile_phi * 2 + (size_t)ax.n_layers * t.tile_qpt * sizeof(TabEntry) +
-           (size_t)t.tile_qpt * sizeof(float);
+    return (size_t)t.tile_qpt * t.tile_phi * (ax.counts ? 4 : 2) +
+           (size_t)ax.n_layers * t.tile_qpt * sizeof(TabEntry) + (size_t)t.tile_qpt * sizeof(float);
 }
 
 
@@ -724,27 +766,37 @@ cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, 
     const VoteParams p = vote_params(ax, w, t, refine_eps);
     const size_t smem = vote_smem_bytes(ax, t);
     const int grid = w.n_events * p.tiles_per_event;
-    return general_only ? launch_scatter_tpb<true>(p, t.threads, smem, grid, stream)
-                        : launch_scatter_tpb<false>(p, t.threads, smem, grid, stream);
+    if (ax.counts) {   // every layer, counted (the gather cannot count)
+        if (general_only) return cudaErrorInvalidValue;
+        return launch_scatter_tpb<false, true>(p, t.threads, smem, grid, stream);
+    }
+    return general_only ? launch_scatter_tpb<true, false>(p, t.threads, smem, grid, stream)
+                        : launch_scatter_tpb<false, false>(p, t.threads, smem, grid, stream);
 }
 
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
                         cudaStream_t stream)
 {
-    if (t.vote_mode == HOUGH_VOTE_SCATTER) return launch_scatter(ax, w, t, refine_eps, false, stream);
+    if (t.vote_mode == HOUGH_VOTE_SCATTER || ax.counts) return launch_scatter(ax, w, t, refine_eps, false, stream);
     // gather every table layer, then let the scatter kernel add the layers whose radii differ
     cudaError_t err = launch_gather(ax, w, t, stream);
     if (err) return err;
     return launch_scatter(ax, w, t, refine_eps, true, stream);
 }
 
+size_t band_smem_bytes(const Axes &ax, int band_rows)
+{
+    return (size_t)(band_rows + 2) * ax.n_phi * (ax.counts ? 2 : 1);
+}
+
 cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
 {
     const int nb = n_bands(ax, w.band_rows);
-    const size_t smem = (size_t)(w.band_rows + 2) * ax.n_phi;
+    const size_t smem = band_smem_bytes(ax, w.band_rows);
+    auto kernel = ax.counts ? peaks_kernel<true> : peaks_kernel<false>;
     cudaError_t err;
-    if ((err = cudaFuncSetAttribute(peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return err;
-    if ((err = launch_chained(peaks_kernel, dim3(w.n_events * nb), dim3(kPeakThreads), smem, stream, ax, w))) return err;
+    if ((err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return err;
+    if ((err = launch_chained(kernel, dim3(w.n_events * nb), dim3(kPeakThreads), smem, stream, ax, w))) return err;
     return cudaGetLastError();
 }
 

@@ -3,7 +3,8 @@
 Rule: the integer layer masks and the candidate list are bit-exact, except where a vote the
 oracle flags (its bin coordinate within 1e-4 bin of an edge, or |x| within 1e-6 of 1) may
 legitimately land on the other side in FP32; the number of mismatched (cell, layer) pairs must
-not exceed the number of flagged votes, and each must be explained by one.
+not exceed the number of flagged votes, and each must be explained by one.  Counts likewise:
+each cell equal up to the flagged votes that may have left it or landed in it.
 """
 from __future__ import annotations
 
@@ -41,7 +42,40 @@ def accumulator_mismatches(M_gpu: np.ndarray, M_ref: np.ndarray, flags) -> tuple
     return mism, unexplained
 
 
-def assert_accumulator_parity(M_gpu, M_ref, flags):
+def count_slack(flags, shape):
+    """Per cell, how far a count may fall below (lo <= 0) or rise above (hi >= 0) the oracle's:
+    a flagged vote may leave its oracle bin and land in its alternative bin; a domain-edge flag
+    with no oracle bin may add one vote anywhere on its row (row_extra)."""
+    n_q, n_phi = shape
+    lo = np.zeros(shape, np.int64)
+    hi = np.zeros(shape, np.int64)
+    row_extra = np.zeros(n_q, np.int64)
+    for f in flags:
+        row, b, a = int(f["row"]), int(f["bin"]), int(f["alt"])
+        if b >= 0:
+            lo[row, b % n_phi] -= 1
+        if a >= 0:
+            hi[row, a % n_phi] += 1
+        if int(f["kind"]) == 2 and b < 0:
+            row_extra[row] += 1
+    return lo, hi, row_extra
+
+
+def assert_count_parity(M_gpu, M_ref, flags):
+    """Count accumulator: every cell equal, except for the flagged votes' moves; returns the number
+    of cells that differ."""
+    lo, hi, row_extra = count_slack(flags, M_ref.shape)
+    diff = M_gpu.astype(np.int64) - M_ref.astype(np.int64)
+    bad = np.argwhere((diff < lo) | (diff > hi + row_extra[:, None]))
+    assert len(bad) == 0, f"{len(bad)} counts differ beyond the flagged votes: " + \
+        str([(int(i), int(j), int(M_gpu[i, j]), int(M_ref[i, j])) for i, j in bad[:8]])
+    assert int(np.abs(diff).sum()) <= 2 * len(flags)
+    return int(np.count_nonzero(diff))
+
+
+def assert_accumulator_parity(M_gpu, M_ref, flags, counts=False):
+    if counts:
+        return assert_count_parity(M_gpu, M_ref, flags)
     mism, unexplained = accumulator_mismatches(M_gpu, M_ref, flags)
     assert not unexplained, f"{len(unexplained)} accumulator bits differ at unflagged votes: {unexplained[:8]}"
     assert len(mism) <= len(flags), f"{len(mism)} mismatched bits > {len(flags)} flagged votes"
@@ -84,11 +118,18 @@ def assert_candidate_parity(c_gpu, c_ref, flags, n_phi):
     return len(set(g) ^ set(r))
 
 
-def assert_members_and_stage2_parity(c_gpu, off_gpu, mem_gpu, ref, threshold):
+def assert_members_and_stage2_parity(c_gpu, off_gpu, mem_gpu, ref, threshold, n_layers=16, counts=False):
     """Member lists and stage-2 results of candidates present on both sides.
 
     A member list may differ only by hits whose vote on that row the oracle flags; a stage-2
-    result may differ only for such candidates or where the oracle flags a z0 vote."""
+    result may differ only for such candidates or where the oracle flags a z0 vote.  A candidate is
+    confirmed when its stage-2 cell holds min(threshold, n_layers) layers.  With the count
+    accumulator every candidate's member count equals its count (below saturation)."""
+    confirm = min(threshold, n_layers)
+    if counts:
+        for c in c_gpu:
+            if int(c["mask"]) < 65535 and not int(c["flags"]) & 2:
+                assert int(c["n_members"]) == int(c["mask"]), f"({int(c['iq'])}, {int(c['jphi'])}): members vs count"
     c_ref = ref["candidates"]
     index_ref = {(int(c["iq"]), int(c["jphi"])): q for q, c in enumerate(c_ref)}
     mflag_hits = {}
@@ -112,6 +153,6 @@ def assert_members_and_stage2_parity(c_gpu, off_gpu, mem_gpu, ref, threshold):
         s = ref["stage2"][p]
         assert (int(c["icot"]), int(c["jz0"]), int(c["mask2"])) == (int(s["icot"]), int(s["jz0"]), int(s["mask2"])), \
             f"candidate {key}: stage 2 {(int(c['icot']), int(c['jz0']), int(c['mask2']))} vs oracle {tuple(int(v) for v in s)[:3]}"
-        assert (int(c["flags"]) & 1) == (1 if bin(int(s["mask2"])).count("1") >= threshold else 0)
+        assert (int(c["flags"]) & 1) == (1 if bin(int(s["mask2"])).count("1") >= confirm else 0)
         checked += 1
     return checked
