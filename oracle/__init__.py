@@ -41,15 +41,21 @@ def build(force: bool = False) -> str:
 class Binning(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int32), ("n_qpt", ctypes.c_int32), ("n_phi", ctypes.c_int32),
                 ("threshold", ctypes.c_int32), ("n_cot", ctypes.c_int32), ("n_z0", ctypes.c_int32),
-                ("accumulator", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("accumulator", ctypes.c_int32), ("n_d0", ctypes.c_int32),
                 ("b_tesla", ctypes.c_double), ("qpt_min", ctypes.c_double), ("qpt_max", ctypes.c_double),
                 ("cot_min", ctypes.c_double), ("cot_max", ctypes.c_double),
-                ("z0_min", ctypes.c_double), ("z0_max", ctypes.c_double)]
+                ("z0_min", ctypes.c_double), ("z0_max", ctypes.c_double),
+                ("d0_min", ctypes.c_double), ("d0_max", ctypes.c_double)]
+
+    @property
+    def n_rows(self) -> int:
+        """Rows of the stacked grid: d0 slices x q/pT rows."""
+        return max(self.n_d0, 1) * self.n_qpt
 
 
 FLAG_DTYPE = np.dtype([("hit", np.int64), ("row", np.int32), ("bin", np.int32), ("alt", np.int32),
                        ("layer", np.int32), ("kind", np.int32), ("cand", np.int32)], align=True)
-CAND_DTYPE = np.dtype([("iq", np.int32), ("jphi", np.int32), ("mask", np.uint32), ("pad", np.int32)],
+CAND_DTYPE = np.dtype([("iq", np.int32), ("jphi", np.int32), ("mask", np.uint32), ("id0", np.int32)],
                       align=True)
 STAGE2_DTYPE = np.dtype([("icot", np.int32), ("jz0", np.int32), ("mask2", np.uint32),
                          ("n_votes", np.int32)], align=True)
@@ -80,10 +86,12 @@ def make_binning(geometry, binning) -> Binning:
     """The oracle's view of a (Geometry, Binning) pair from the event generator."""
     return Binning(n_layers=geometry.n_layers, n_qpt=binning.n_qpt, n_phi=binning.n_phi,
                    threshold=binning.threshold, n_cot=binning.n_cot, n_z0=binning.n_z0,
-                   accumulator=int(getattr(binning, "accumulator", ACC_LAYERS)), pad=0,
+                   accumulator=int(getattr(binning, "accumulator", ACC_LAYERS)),
+                   n_d0=int(getattr(binning, "n_d0", 0)),
                    b_tesla=geometry.b_tesla, qpt_min=binning.qpt_min, qpt_max=binning.qpt_max,
                    cot_min=binning.cot_min, cot_max=binning.cot_max,
-                   z0_min=binning.z0_min, z0_max=binning.z0_max)
+                   z0_min=binning.z0_min, z0_max=binning.z0_max,
+                   d0_min=float(getattr(binning, "d0_min", -1.0)), d0_max=float(getattr(binning, "d0_max", 1.0)))
 
 
 def _ptr(a: np.ndarray):
@@ -99,12 +107,13 @@ def _hits(event):
 
 
 def vote(b: Binning, event):
-    """Stage-1 vote.  Returns (M uint16 [n_qpt, n_phi], votes_by_layer uint64[16], flags).
+    """Stage-1 vote.  Returns (M uint16 [n_rows, n_phi], votes_by_layer uint64[16], flags).
 
-    M holds layer masks or saturating vote counts, as ``b.accumulator`` says."""
+    M holds layer masks or saturating vote counts, as ``b.accumulator`` says; its rows are the
+    stacked rows m * n_qpt + i of the d0 slices (one slice without a d0 axis), as are the flags'."""
     lib = _load()
     r, phi, _, layer = _hits(event)
-    M = np.zeros((b.n_qpt, b.n_phi), dtype=np.uint16)
+    M = np.zeros((b.n_rows, b.n_phi), dtype=np.uint16)
     votes = np.zeros(16, dtype=np.uint64)
     cap = 1 << 16
     while True:
@@ -120,7 +129,7 @@ def vote(b: Binning, event):
 
 
 def peaks(b: Binning, M: np.ndarray):
-    """Local-maximum candidates in raster order (structured array iq, jphi, mask)."""
+    """Local-maximum candidates in raster order (structured array iq, jphi, mask, id0)."""
     lib = _load()
     M = np.ascontiguousarray(M, dtype=np.uint16)
     cap = max(1024, M.size // 4 + 1)

@@ -33,6 +33,23 @@
  *   s     = r * asin(|x|) / |x|               transverse arc length (s = r at x = 0)
  *   z0    = z - s * cot(theta)
  *
+ * Non-prompt tracks (the paper's aim of reconstructing prompt and non-prompt
+ * tracks, Sec. 2 and Sec. 4) add a third axis, the signed transverse impact
+ * parameter d0: the track's closest approach to the beam line is the point
+ * d0 * (-sin phi0, cos phi0), where it runs along phi0.  Its circle, of
+ * curvature rho = 2 x / r (1/cm), has its centre at (d0 + 1/rho)(-sin phi0,
+ * cos phi0), and a hit at (r, phi) on it satisfies
+ *
+ *   sin(phi - phi0) = (rho r^2 + 2 d0 + rho d0^2) / (2 r (1 + rho d0))   (= x at d0 = 0)
+ *   chord           = sqrt(r^2 + d0^2 - 2 r d0 sin(phi - phi0))          closest approach to hit
+ *   s               = 2 asin(|rho| chord / 2) / |rho|                    (= chord at rho = 0)
+ *
+ * (1 + rho d0 > 0 for the point to be the closest one; the hit is the first
+ * crossing of radius r, the principal arcsine.)  With d0 bins the grid has
+ * n_d0 slices of n_qpt x n_phi cells, stored one after the other ("stacked
+ * rows": row m * n_qpt + i holds d0 bin m, q/pT bin i); without them
+ * (n_d0 = 0) d0 is 0 and the grid is one slice.
+ *
  * Each value is evaluated in IEEE double in exactly the order written here,
  * inputs promoted exactly from FP32.  A vote whose bin coordinate lies within
  * 1e-4 bin widths of a bin edge (or whose |x| lies within 1e-6 of 1) is
@@ -63,17 +80,18 @@ typedef struct {
     int32_t n_cot;
     int32_t n_z0;
     int32_t accumulator;   /* ORACLE_ACC_LAYERS or ORACLE_ACC_COUNTS */
-    int32_t pad;
+    int32_t n_d0;          /* d0 bins over [d0_min, d0_max] cm; 0: prompt tracks, d0 = 0 */
     double b_tesla;
     double qpt_min, qpt_max;
     double cot_min, cot_max;
     double z0_min, z0_max;
+    double d0_min, d0_max;
 } oracle_binning;
 
 /* A vote whose outcome is within the flag window of a decision edge. */
 typedef struct {
     int64_t hit;     /* hit index in the event */
-    int32_t row;     /* iq (stage 1) or icot (stage 2) */
+    int32_t row;     /* stacked row m * n_qpt + iq (stage 1) or icot (stage 2) */
     int32_t bin;     /* the oracle's bin on that row, -1 when the oracle cast no vote */
     int32_t alt;     /* the bin on the other side of the edge, -1 when that side casts no vote */
     int32_t layer;
@@ -84,7 +102,7 @@ typedef struct {
 typedef struct {
     int32_t iq, jphi;
     uint32_t mask;
-    int32_t pad;
+    int32_t id0;     /* d0 bin (0 without a d0 axis) */
 } oracle_candidate;
 
 typedef struct {
@@ -125,10 +143,50 @@ static double sagitta_arg(const oracle_binning *b, double r_cm, double k)
     return 0.15 * b->b_tesla * (r_cm / 100.0) * k;
 }
 
-/* phi0 bin coordinate of the vote of a hit at azimuth phi with sagitta argument x. */
-static double phi0_coord(const oracle_binning *b, double phi, double x)
+/* Number of d0 slices of the grid, and the d0 bin centre of slice m (cm). */
+static int n_slices(const oracle_binning *b)
 {
-    double phi0 = phi - asin(x);
+    return b->n_d0 > 0 ? b->n_d0 : 1;
+}
+
+static double d0_centre(const oracle_binning *b, int m)
+{
+    if (b->n_d0 <= 0) return 0.0;
+    double dd = (b->d0_max - b->d0_min) / b->n_d0;
+    return b->d0_min + (m + 0.5) * dd;
+}
+
+/*
+ * sin(phi - phi0) of a hit at radius r on the track of sagitta argument x and
+ * impact parameter d0.  Returns 0 when 1 + rho d0 <= 0 (no such track).
+ */
+static int track_sin(double r, double x, double d0, double *y)
+{
+    if (d0 == 0.0) {
+        *y = x;
+        return 1;
+    }
+    double rho = 2.0 * x / r;
+    double den = 2.0 * r * (1.0 + rho * d0);
+    if (!(den > 0.0)) return 0;
+    *y = (rho * r * r + 2.0 * d0 + rho * d0 * d0) / den;
+    return 1;
+}
+
+/* Transverse arc length from the closest approach to the hit (r, with sin(phi - phi0) = y). */
+static double track_arc(double r, double x, double d0, double y)
+{
+    double ax = fabs(x);
+    if (d0 == 0.0) return ax > 0.0 ? r * asin(ax) / ax : r;
+    double chord = sqrt(r * r + d0 * d0 - 2.0 * r * d0 * y);
+    double arho = 2.0 * ax / r;
+    return arho > 0.0 ? 2.0 * asin(arho * chord / 2.0) / arho : chord;
+}
+
+/* phi0 bin coordinate of the vote of a hit at azimuth phi with sin(phi - phi0) = y. */
+static double phi0_coord(const oracle_binning *b, double phi, double y)
+{
+    double phi0 = phi - asin(y);
     return b->n_phi * (phi0 + ORACLE_PI) / (2.0 * ORACLE_PI);
 }
 
@@ -144,22 +202,25 @@ static void push_flag(oracle_flag *flags, int64_t cap, int64_t *n, int64_t hit, 
 }
 
 /*
- * The vote of one hit on one q/pT row.  Returns 1 and sets *j when a vote is cast.
- * Sets *flag_kind (0, 1 or 2) and *alt, the bin on the other side of the edge.
+ * The vote of one hit on q/pT row i of d0 slice m.  Returns 1 and sets *j when a
+ * vote is cast.  Sets *flag_kind (0, 1 or 2) and *alt, the bin on the other side
+ * of the edge.
  */
-static int vote_one(const oracle_binning *b, double r, double phi, int i,
+static int vote_one(const oracle_binning *b, double r, double phi, int m, int i,
                     int32_t *j, int32_t *alt, int32_t *flag_kind)
 {
     double x = sagitta_arg(b, r, qpt_centre(b, i));
-    int domain = fabs(fabs(x) - 1.0) < ORACLE_DOMAIN_WINDOW;
+    double y = 2.0;
+    int exists = track_sin(r, x, d0_centre(b, m), &y);
+    int domain = exists && fabs(fabs(y) - 1.0) < ORACLE_DOMAIN_WINDOW;
     *flag_kind = 0;
     *alt = -1;
     *j = -1;
-    if (!(fabs(x) <= 1.0)) {
+    if (!exists || !(fabs(y) <= 1.0)) {
         if (domain) *flag_kind = 2;   /* FP32 may cast this vote */
         return 0;
     }
-    double u = phi0_coord(b, phi, x);
+    double u = phi0_coord(b, phi, y);
     *j = (int32_t)floor_mod((int64_t)floor(u), b->n_phi);
     double e = nearbyint(u);
     if (fabs(u - e) < ORACLE_EDGE_WINDOW) {
@@ -177,14 +238,16 @@ static int check_hits(const oracle_binning *b, const uint8_t *layer, int64_t n)
         return ORACLE_EINVAL;
     if (b->accumulator != ORACLE_ACC_LAYERS && b->accumulator != ORACLE_ACC_COUNTS)
         return ORACLE_EINVAL;
+    if (b->n_d0 < 0 || (b->n_d0 > 0 && !(b->d0_min < b->d0_max)))
+        return ORACLE_EINVAL;
     for (int64_t h = 0; h < n; ++h)
         if (layer[h] >= b->n_layers) return ORACLE_EINVAL;
     return ORACLE_OK;
 }
 
 /*
- * Stage-1 vote (Sec. 4, first step).  M is n_qpt x n_phi, row-major, and is
- * overwritten.  votes_by_layer[l] counts the votes cast by hits of layer l.
+ * Stage-1 vote (Sec. 4, first step).  M is n_slices x n_qpt x n_phi, row-major
+ * (stacked rows), and is overwritten.  votes_by_layer[l] counts the votes cast by hits of layer l.
  * A vote ORs the hit's layer bit into its cell, or adds one to the cell's count
  * (held at 65535 once it gets there).
  */
@@ -193,16 +256,18 @@ int oracle_vote(const oracle_binning *b, const float *r, const float *phi, const
                 oracle_flag *flags, int64_t flag_cap, int64_t *n_flags)
 {
     if (check_hits(b, layer, n) != ORACLE_OK) return ORACLE_EINVAL;
-    memset(M, 0, sizeof(uint16_t) * (size_t)b->n_qpt * (size_t)b->n_phi);
+    const int64_t rows = (int64_t)n_slices(b) * b->n_qpt;
+    memset(M, 0, sizeof(uint16_t) * (size_t)rows * (size_t)b->n_phi);
     for (int l = 0; l < 16; ++l) votes_by_layer[l] = 0;
     *n_flags = 0;
     for (int64_t h = 0; h < n; ++h) {
         int l = layer[h];
-        for (int i = 0; i < b->n_qpt; ++i) {
+        for (int64_t row = 0; row < rows; ++row) {
+            int m = (int)(row / b->n_qpt), i = (int)(row % b->n_qpt);
             int32_t j, alt, kind;
-            int cast = vote_one(b, (double)r[h], (double)phi[h], i, &j, &alt, &kind);
+            int cast = vote_one(b, (double)r[h], (double)phi[h], m, i, &j, &alt, &kind);
             if (cast) {
-                uint16_t *cell = &M[(size_t)i * b->n_phi + j];
+                uint16_t *cell = &M[(size_t)row * b->n_phi + j];
                 if (b->accumulator == ORACLE_ACC_COUNTS) {
                     if (*cell < 65535u) *cell = (uint16_t)(*cell + 1u);
                 } else {
@@ -211,7 +276,7 @@ int oracle_vote(const oracle_binning *b, const float *r, const float *phi, const
                 votes_by_layer[l]++;
             }
             if (kind)
-                push_flag(flags, flag_cap, n_flags, h, i, j, alt, l, kind, -1);
+                push_flag(flags, flag_cap, n_flags, h, (int32_t)row, j, alt, l, kind, -1);
         }
     }
     return ORACLE_OK;
@@ -220,39 +285,47 @@ int oracle_vote(const oracle_binning *b, const float *r, const float *phi, const
 /*
  * Peak search (Sec. 4, second step): a cell is a candidate when its value p
  * (layer accumulator: the number of layers in its mask; count accumulator: its
- * count) reaches the threshold, no neighbour of the 3 x 3 block exceeds it, and the
- * four neighbours that precede it in raster order -- offsets (-1,-1), (-1,0),
- * (-1,+1), (0,-1) -- are strictly lower.  phi0 wraps; rows outside the grid
- * count as empty.  Candidates are listed in raster order.
+ * count) reaches the threshold, no neighbour of its 3 x 3 block -- 3 x 3 x 3
+ * with a d0 axis -- exceeds it, and the neighbours that precede it in raster
+ * order (d0 bin, then q/pT row, then phi0 column) are strictly lower: in one
+ * slice the offsets (-1,-1), (-1,0), (-1,+1), (0,-1), and with a d0 axis also
+ * the whole block of the slice before.  phi0 wraps; rows and slices outside the
+ * grid count as empty.  Candidates are listed in raster order.
  */
 int oracle_peaks(const oracle_binning *b, const uint16_t *M, oracle_candidate *out,
                  int64_t cap, int64_t *n_out)
 {
     int64_t n = 0;
-    for (int i = 0; i < b->n_qpt; ++i) {
-        for (int j = 0; j < b->n_phi; ++j) {
-            int p = cell_value(b, M[(size_t)i * b->n_phi + j]);
-            if (p < b->threshold) continue;
-            int is_peak = 1;
-            for (int di = -1; di <= 1 && is_peak; ++di) {
-                for (int dj = -1; dj <= 1; ++dj) {
-                    if (di == 0 && dj == 0) continue;
-                    int ii = i + di;
-                    int q = 0;
-                    if (ii >= 0 && ii < b->n_qpt) {
-                        int jj = (int)floor_mod(j + dj, b->n_phi);
-                        q = cell_value(b, M[(size_t)ii * b->n_phi + jj]);
+    const int D = n_slices(b);
+    const size_t slice = (size_t)b->n_qpt * (size_t)b->n_phi;
+    for (int m = 0; m < D; ++m) {
+        for (int i = 0; i < b->n_qpt; ++i) {
+            for (int j = 0; j < b->n_phi; ++j) {
+                int p = cell_value(b, M[m * slice + (size_t)i * b->n_phi + j]);
+                if (p < b->threshold) continue;
+                int is_peak = 1;
+                for (int dm = -1; dm <= 1 && is_peak; ++dm) {
+                    for (int di = -1; di <= 1 && is_peak; ++di) {
+                        for (int dj = -1; dj <= 1; ++dj) {
+                            if (dm == 0 && di == 0 && dj == 0) continue;
+                            int mm = m + dm, ii = i + di;
+                            int q = 0;
+                            if (mm >= 0 && mm < D && ii >= 0 && ii < b->n_qpt) {
+                                int jj = (int)floor_mod(j + dj, b->n_phi);
+                                q = cell_value(b, M[mm * slice + (size_t)ii * b->n_phi + jj]);
+                            }
+                            int precedes = (dm < 0) || (dm == 0 && di < 0) || (dm == 0 && di == 0 && dj < 0);
+                            if (precedes ? (q >= p) : (q > p)) { is_peak = 0; break; }
+                        }
                     }
-                    int precedes = (di < 0) || (di == 0 && dj < 0);
-                    if (precedes ? (q >= p) : (q > p)) { is_peak = 0; break; }
                 }
+                if (!is_peak) continue;
+                if (n < cap) {
+                    out[n].iq = i; out[n].jphi = j;
+                    out[n].mask = M[m * slice + (size_t)i * b->n_phi + j]; out[n].id0 = m;
+                }
+                n++;
             }
-            if (!is_peak) continue;
-            if (n < cap) {
-                out[n].iq = i; out[n].jphi = j;
-                out[n].mask = M[(size_t)i * b->n_phi + j]; out[n].pad = 0;
-            }
-            n++;
         }
     }
     *n_out = n;
@@ -270,8 +343,8 @@ static int64_t find_candidate(const oracle_candidate *c, int64_t lo, int64_t hi,
 }
 
 /*
- * Membership: hit h belongs to candidate (i, j) when its stage-1 vote on row i
- * fell in bin j.  offsets has n_cand + 1 entries; members lists hit indices in
+ * Membership: hit h belongs to candidate (m, i, j) when its stage-1 vote on
+ * q/pT row i of d0 slice m fell in bin j.  offsets has n_cand + 1 entries; members lists hit indices in
  * increasing order per candidate.  A flagged vote whose bin or alternative bin
  * is a candidate is reported with that candidate's index.
  */
@@ -281,12 +354,13 @@ int oracle_members(const oracle_binning *b, const float *r, const float *phi, co
                    oracle_flag *flags, int64_t flag_cap, int64_t *n_flags)
 {
     if (check_hits(b, layer, n) != ORACLE_OK) return ORACLE_EINVAL;
-    /* row_start[i] .. row_start[i+1]: the candidates on row i */
-    int64_t *row_start = (int64_t *)calloc((size_t)b->n_qpt + 1, sizeof(int64_t));
+    /* row_start[row] .. row_start[row+1]: the candidates on stacked row m * n_qpt + i */
+    const int64_t rows = (int64_t)n_slices(b) * b->n_qpt;
+    int64_t *row_start = (int64_t *)calloc((size_t)rows + 1, sizeof(int64_t));
     int64_t *fill = (int64_t *)calloc((size_t)n_cand + 1, sizeof(int64_t));
     if (!row_start || !fill) { free(row_start); free(fill); return ORACLE_EINVAL; }
-    for (int64_t q = 0; q < n_cand; ++q) row_start[c[q].iq + 1]++;
-    for (int i = 0; i < b->n_qpt; ++i) row_start[i + 1] += row_start[i];
+    for (int64_t q = 0; q < n_cand; ++q) row_start[(int64_t)c[q].id0 * b->n_qpt + c[q].iq + 1]++;
+    for (int64_t row = 0; row < rows; ++row) row_start[row + 1] += row_start[row];
     *n_flags = 0;
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1) {
@@ -295,10 +369,11 @@ int oracle_members(const oracle_binning *b, const float *r, const float *phi, co
             memset(fill, 0, sizeof(int64_t) * (size_t)(n_cand + 1));
         }
         for (int64_t h = 0; h < n; ++h) {
-            for (int i = 0; i < b->n_qpt; ++i) {
+            for (int64_t i = 0; i < rows; ++i) {   /* i: stacked row */
                 if (row_start[i] == row_start[i + 1]) continue;
                 int32_t j, alt, kind;
-                int cast = vote_one(b, (double)r[h], (double)phi[h], i, &j, &alt, &kind);
+                int cast = vote_one(b, (double)r[h], (double)phi[h], (int)(i / b->n_qpt), (int)(i % b->n_qpt),
+                                    &j, &alt, &kind);
                 if (cast) {
                     int64_t q = find_candidate(c, row_start[i], row_start[i + 1], j);
                     if (q < row_start[i + 1] && c[q].jphi == j) {
@@ -315,11 +390,11 @@ int oracle_members(const oracle_binning *b, const float *r, const float *phi, co
                         if (probe[e] < 0) continue;
                         int64_t q = find_candidate(c, row_start[i], row_start[i + 1], probe[e]);
                         if (q < row_start[i + 1] && c[q].jphi == probe[e])
-                            push_flag(flags, flag_cap, n_flags, h, i, j, alt, layer[h], kind, (int32_t)q);
+                            push_flag(flags, flag_cap, n_flags, h, (int32_t)i, j, alt, layer[h], kind, (int32_t)q);
                     }
                     if (kind == 2 && j < 0)   /* a vote the oracle did not cast: any candidate on the row */
                         for (int64_t q = row_start[i]; q < row_start[i + 1]; ++q)
-                            push_flag(flags, flag_cap, n_flags, h, i, j, alt, layer[h], kind, (int32_t)q);
+                            push_flag(flags, flag_cap, n_flags, h, (int32_t)i, j, alt, layer[h], kind, (int32_t)q);
                 }
             }
         }
@@ -332,7 +407,8 @@ int oracle_members(const oracle_binning *b, const float *r, const float *phi, co
 /*
  * Second-stage vote (the confirmation step): every member hit of a candidate
  * votes in an n_cot x n_z0 grid of (cot theta, z0) with z0 = z - s * cot theta,
- * s the transverse arc length at the candidate's curvature.  z0 is not cyclic:
+ * s the transverse arc length at the candidate's curvature (and d0), from the
+ * closest approach to the hit.  z0 is not cyclic:
  * votes outside [z0_min, z0_max) are not cast.  The result is the cell of most
  * layers, the lowest row-major index on ties.  With either stage-1 accumulator
  * the second grid holds layer masks.
@@ -351,12 +427,15 @@ int oracle_stage2(const oracle_binning *b, const float *r, const float *z, const
     for (int64_t q = 0; q < n_cand; ++q) {
         memset(M2, 0, sizeof(uint16_t) * cells);
         double k = qpt_centre(b, c[q].iq);
+        double d0 = d0_centre(b, c[q].id0);
         int32_t votes = 0;
         for (int64_t e = offsets[q]; e < offsets[q + 1]; ++e) {
             int64_t h = members[e];
             double rr = (double)r[h];
-            double ax = fabs(sagitta_arg(b, rr, k));
-            double s = ax > 0.0 ? rr * asin(ax) / ax : rr;
+            double x = sagitta_arg(b, rr, k);
+            double y = x;
+            track_sin(rr, x, d0, &y);   /* a member's track exists: its vote was cast */
+            double s = track_arc(rr, x, d0, y);
             for (int m = 0; m < b->n_cot; ++m) {
                 double t = b->cot_min + (m + 0.5) * dt;
                 double z0 = (double)z[h] - s * t;

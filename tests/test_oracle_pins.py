@@ -452,6 +452,196 @@ def test_unknown_accumulator_kind_is_rejected():
 
 
 # --------------------------------------------------------------------------------------------
+# Non-prompt tracks: the impact-parameter axis d0
+# --------------------------------------------------------------------------------------------
+
+BINNING_D0 = eg.Binning(n_qpt=128, qpt_min=-1.0, qpt_max=1.0, n_phi=256, threshold=8,
+                        n_d0=9, d0_min=-0.9, d0_max=0.9)
+
+
+def _d0_centre(bn, m):
+    return bn.d0_min + (m + 0.5) * (bn.d0_max - bn.d0_min) / bn.n_d0
+
+
+def test_displaced_hits_lie_on_the_track_circle():
+    """Plane geometry of the displaced forward model: every hit is on the circle of radius
+    R = 100 / (0.3 B |k|) about the centre (d0 + R_signed)(-sin phi0, cos phi0), the circle's
+    closest approach to the beam line is |d0| away, z advances with the arc length from it (from the
+    chord, 2 R asin(chord / 2R), not the swept angle the model uses), and with d0 = 0 the model
+    reproduces the prompt helices."""
+    rng = np.random.default_rng(31)
+    k = rng.uniform(-1.2, 1.2, 40)
+    phi0 = rng.uniform(-math.pi, math.pi, 40)
+    d0 = rng.uniform(-2.0, 2.0, 40)
+    cot = rng.uniform(-2.0, 2.0, 40)
+    z0 = rng.uniform(-5.0, 5.0, 40)
+    r, phi, z, layer, tk = eg.displaced_hits(GEOM, k, phi0, d0, cot, z0)
+    assert len(r) > 200
+    rs = 100.0 / (0.3 * GEOM.b_tesla * k)
+    n = np.stack([-np.sin(phi0), np.cos(phi0)], 1)
+    centre = (d0 + rs)[:, None] * n
+    assert np.allclose(np.abs(np.linalg.norm(centre, axis=1) - np.abs(rs)), np.abs(d0), atol=1e-9)
+    pts = np.stack([r * np.cos(phi), r * np.sin(phi)], 1)
+    assert np.allclose(np.linalg.norm(pts - centre[tk], axis=1), np.abs(rs[tk]), rtol=1e-10, atol=1e-8)
+    chord = np.linalg.norm(pts - (d0[:, None] * n)[tk], axis=1)
+    arc = 2.0 * np.abs(rs[tk]) * np.arcsin(np.clip(chord / (2.0 * np.abs(rs[tk])), -1.0, 1.0))
+    assert np.allclose(z, z0[tk] + cot[tk] * arc, rtol=1e-9, atol=1e-7)
+    prompt = eg.helix_hits(GEOM, k, phi0, cot, z0)
+    zero = eg.displaced_hits(GEOM, k, phi0, np.zeros(40), cot, z0)
+    for a, b in zip(prompt, zero):
+        assert np.allclose(np.asarray(a, float), np.asarray(b, float), rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_displaced_helix_generating_cell_holds_all_layers(seed):
+    """A noiseless displaced helix with q/pT, phi0 and d0 on bin centres puts every reached layer
+    in its generating (d0, q/pT, phi0) cell, no vote of that row is flagged, and the raster-first
+    cell holding every reached layer is a candidate."""
+    rng = np.random.default_rng(200 + seed)
+    bn = BINNING_D0
+    b = oracle.make_binning(GEOM, bn)
+    for _ in range(4):
+        i, j, m = int(rng.integers(2, bn.n_qpt - 2)), int(rng.integers(0, bn.n_phi)), int(rng.integers(0, bn.n_d0))
+        k, phi0, _, _ = _centres(bn, i, j)
+        r, phi, z, layer, _ = eg.displaced_hits(GEOM, [k], [phi0], [_d0_centre(bn, m)], [0.0], [0.0])
+        M, votes, flags = oracle.vote(b, _event(r, phi, z, layer))
+        assert M.shape == (bn.n_d0 * bn.n_qpt, bn.n_phi)
+        reached = sum(1 << int(l) for l in layer)
+        row = m * bn.n_qpt + i
+        assert int(M[row, j]) == reached
+        assert not np.any(flags["row"] == row)
+        cands = oracle.peaks(b, M)
+        first = np.argwhere(M == reached)[0]
+        got = {(int(c["id0"]) * bn.n_qpt + int(c["iq"]), int(c["jphi"])) for c in cands}
+        assert (int(first[0]), int(first[1])) in got
+        assert all(int(c["mask"]) != 0 for c in cands)
+
+
+def test_d0_vote_matches_plane_geometry():
+    """The d0 vote of each (hit, q/pT row, d0 slice) against plane geometry: the forward model puts
+    a track of phi0 = 0 through the hit's layer at azimuth D(k, d0, r), so by rotation the track
+    through the hit has phi0 = phi - D; its bin must be the oracle's (votes the oracle flags
+    excepted), and where the forward model finds no crossing the oracle casts no vote."""
+    rng = np.random.default_rng(41)
+    # q/pT up to 3 and |d0| up to 6 cm: many (row, layer) pairs have no crossing (|x| > 1, |d0| > r)
+    bn = eg.Binning(n_qpt=32, qpt_min=-3.0, qpt_max=3.0, n_phi=512, threshold=8, n_d0=7, d0_min=-7.0, d0_max=7.0)
+    b = oracle.make_binning(GEOM, bn)
+    checked = missing = 0
+    for _ in range(60):
+        l = int(rng.integers(0, GEOM.n_layers))
+        phi = float(rng.uniform(-math.pi, math.pi))
+        ev = _event([GEOM.radii_cm[l]], [phi], [0.0], [l])
+        M, _, flags = oracle.vote(b, ev)
+        flagged = {int(f["row"]) for f in flags}
+        one = eg.Geometry(radii_cm=(GEOM.radii_cm[l],), b_tesla=GEOM.b_tesla)
+        for row in range(b.n_rows):
+            if row in flagged:
+                continue
+            m, i = divmod(row, bn.n_qpt)
+            k, _, _, _ = _centres(bn, i, 0)
+            rr, ph, _, _, _ = eg.displaced_hits(one, [k], [0.0], [_d0_centre(bn, m)], [0.0], [0.0])
+            voted = np.nonzero(M[row])[0]
+            if len(rr) == 0:
+                assert len(voted) == 0, (row, voted)
+                missing += 1
+                continue
+            phi0 = np.float64(np.float32(phi)) - ph[0]
+            j = int(math.floor(bn.n_phi * (phi0 + math.pi) / (2 * math.pi))) % bn.n_phi
+            assert voted.tolist() == [j], (row, voted, j)
+            checked += 1
+    assert checked > 5000 and missing > 100
+
+
+def test_centred_d0_slice_equals_the_prompt_grid():
+    """With an odd number of d0 bins centred on 0 the middle slice has d0 = 0 exactly and must be
+    the prompt accumulator, cell for cell, with the same flags."""
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(3)
+    prompt = oracle.make_binning(w.geometry, w.binning)
+    b3 = oracle.make_binning(w.geometry, eg.Binning(**{**w.binning.__dict__, "n_d0": 3, "d0_min": -1.5, "d0_max": 1.5}))
+    Mp, vp, fp = oracle.vote(prompt, ev)
+    M3, v3, f3 = oracle.vote(b3, ev)
+    q = w.binning.n_qpt
+    assert np.array_equal(M3[q:2 * q], Mp)
+    mid = f3[(f3["row"] >= q) & (f3["row"] < 2 * q)].copy()
+    mid["row"] -= q
+    assert np.array_equal(mid, fp)
+    assert int(v3.sum()) >= int(vp.sum())
+
+
+def test_golden_peak3_cases():
+    with open(os.path.join(GOLDEN, "peak3_cases.json")) as f:
+        spec = json.load(f)
+    for case in spec["cases"]:
+        nd, nq, nphi = case["shape"]
+        M = np.zeros((nd * nq, nphi), np.uint16)
+        for m, i, j, mask in case["cells"]:
+            M[m * nq + i, j] = mask
+        bn = eg.Binning(n_qpt=nq, qpt_min=-1, qpt_max=1, n_phi=nphi, threshold=case["threshold"],
+                        n_d0=nd, d0_min=-1.0, d0_max=1.0)
+        got = [(int(c["id0"]), int(c["iq"]), int(c["jphi"])) for c in oracle.peaks(oracle.make_binning(GEOM, bn), M)]
+        assert got == [tuple(x) for x in case["expected"]], case["name"]
+
+
+def test_peaks3_are_the_strict_maxima_of_distinct_values():
+    """Distinct counts in a d0 grid: the candidates are exactly the cells at or above threshold equal
+    to the maximum of their 3 x 3 x 3 block (scipy.ndimage.maximum_filter; phi0 wrapped, rows and
+    slices outside the grid empty)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(13)
+    nd, nq, nphi = 5, 9, 64
+    vals = (rng.permutation(nd * nq * nphi) + 1).astype(np.uint16).reshape(nd, nq, nphi)
+    padded = np.zeros((nd + 2, nq + 2, nphi + 2), np.int64)
+    padded[1:-1, 1:-1, 1:-1] = vals
+    padded[1:-1, 1:-1, 0] = vals[:, :, -1]
+    padded[1:-1, 1:-1, -1] = vals[:, :, 0]
+    local_max = ndimage.maximum_filter(padded, size=3, mode="constant", cval=0)[1:-1, 1:-1, 1:-1]
+    expect = [tuple(int(v) for v in x) for x in np.argwhere((vals == local_max) & (vals >= 500))]
+    bn = eg.Binning(n_qpt=nq, qpt_min=-1, qpt_max=1, n_phi=nphi, threshold=500, accumulator=eg.ACC_COUNTS,
+                    n_d0=nd, d0_min=-1.0, d0_max=1.0)
+    got = [(int(c["id0"]), int(c["iq"]), int(c["jphi"]))
+           for c in oracle.peaks(oracle.make_binning(GEOM, bn), vals.reshape(nd * nq, nphi))]
+    assert got == expect and len(got) > 20
+
+
+def test_stage2_displaced_helix_closed_form():
+    """Member hits of a noiseless displaced helix with cot(theta) and z0 on stage-2 bin centres all
+    vote for the generating (cot, z0) cell: the arc length from the closest approach is the one
+    the forward model advanced z by."""
+    bn = eg.Binning(**{**eg.BINNING_PILEUP.__dict__, "n_d0": 8, "d0_min": -2.0, "d0_max": 2.0})
+    b = oracle.make_binning(GEOM, bn)
+    rng = np.random.default_rng(19)
+    for _ in range(8):
+        i, j = int(rng.integers(0, bn.n_qpt)), int(rng.integers(0, bn.n_phi))
+        m, n, md = int(rng.integers(0, bn.n_cot)), int(rng.integers(0, bn.n_z0)), int(rng.integers(0, bn.n_d0))
+        k, phi0, cot, z0 = _centres(bn, i, j, m, n)
+        r, phi, z, layer, _ = eg.displaced_hits(GEOM, [k], [phi0], [_d0_centre(bn, md)], [cot], [z0])
+        ev = _event(r, phi, z, layer)
+        cand = np.zeros(1, oracle.CAND_DTYPE)
+        cand["iq"], cand["jphi"], cand["id0"] = i, j, md
+        res, _ = oracle.stage2(b, ev, cand, np.array([0, len(r)], np.int64), np.arange(len(r), dtype=np.int64))
+        assert (int(res[0]["icot"]), int(res[0]["jz0"])) == (m, n)
+        assert int(res[0]["mask2"]) == sum(1 << int(l) for l in layer)
+
+
+def test_d0_members_reproduce_candidate_masks():
+    """In a d0 grid, the members of each candidate (hits whose vote on its q/pT row of its d0 slice
+    fell in its column) OR to its mask."""
+    w = eg.displaced_workload()
+    b = oracle.make_binning(w.geometry, w.binning)
+    ev = w.event(0)
+    M, _, _ = oracle.vote(b, ev)
+    cands = oracle.peaks(b, M)
+    offsets, mem, _ = oracle.members(b, ev, cands)
+    assert len(cands) > 20 and len(np.unique(cands["id0"])) > 3
+    for q, c in enumerate(cands):
+        acc = 0
+        for h in mem[offsets[q]:offsets[q + 1]]:
+            acc |= 1 << int(ev.layer[h])
+        assert acc == int(c["mask"])
+
+
+# --------------------------------------------------------------------------------------------
 # Membership and the second-stage vote
 # --------------------------------------------------------------------------------------------
 
