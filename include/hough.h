@@ -90,6 +90,22 @@ typedef struct hough_geometry {
  * qpt_min < qpt_max, cot_min < cot_max, z0_min_cm < z0_max_cm.
  * The count accumulator votes with the shared-memory scatter kernel
  * (HOUGH_VOTE_SCATTER): the gather decides whether a layer voted, not how often.
+ *
+ * Non-prompt tracks (n_d0 > 0): a third axis of n_d0 bins of the signed
+ * transverse impact parameter d0 over [d0_min_cm, d0_max_cm).  A track whose
+ * closest approach to the beam line is the point d0 (-sin phi0, cos phi0),
+ * where it runs along phi0, with curvature rho = 0.003 B q/pT (1/cm), puts
+ * its hit at radius r where sin(phi - phi0) = (rho r^2 + 2 d0 + rho d0^2) /
+ * (2 r (1 + rho d0)) (the prompt relation phi0 = phi - asin(x) at d0 = 0);
+ * a vote needs 1 + rho d0 > 0 and |sin(phi - phi0)| <= 1.  The arc length of
+ * stage 2 runs from the closest approach.  The grid is then n_d0 slices of
+ * n_qpt x n_phi cells stored one after the other: stacked row m * n_qpt + i
+ * holds d0 bin m and q/pT bin i; accumulators, candidate rows (iq) and
+ * hough_get_accumulator all use stacked rows.  A cell is a candidate when it
+ * is a local maximum of its 3 x 3 x 3 block (the 13 neighbours before it in
+ * raster order -- slice, row, column -- strictly lower); band_rows must be 1.
+ * n_d0 = 0: prompt tracks (d0 = 0), one slice, the d0 fields ignored.
+ * Limits: 0 <= n_d0 and n_d0 * n_qpt <= 65535; d0_min_cm < d0_max_cm, finite.
  */
 typedef struct hough_binning {
     int32_t n_qpt, n_phi, threshold, n_cot, n_z0;
@@ -97,6 +113,9 @@ typedef struct hough_binning {
     double  qpt_min, qpt_max;
     double  cot_min, cot_max;
     double  z0_min_cm, z0_max_cm;
+    int32_t n_d0;          /* d0 bins; 0: prompt tracks only */
+    int32_t reserved;      /* must be 0 */
+    double  d0_min_cm, d0_max_cm;
 } hough_binning;
 
 /* Capacities fixed at creation; every device buffer is sized from them. */
@@ -107,7 +126,8 @@ typedef struct hough_limits {
 } hough_limits;
 
 /*
- * One track candidate.  (iq, jphi) is the stage-1 cell, mask its value as
+ * One track candidate.  (iq, jphi) is the stage-1 cell (iq the stacked row
+ * m * n_qpt + i with a d0 axis), mask its value as
  * stored (the layer mask, or with the count accumulator the count); n_members
  * the hits whose stage-1 vote fell in the cell (with the count accumulator
  * equal to the count below saturation); (icot, jz0) the stage-2 maximum (most
@@ -170,7 +190,7 @@ int hough_vote(hough_ctx *ctx, const float *r, const float *phi, const float *z,
  * (i, j) with value p (popcount(mask), or the count with HOUGH_ACC_COUNTS) is a
  * candidate when p >= threshold, no 3 x 3 neighbour has a larger value and the
  * neighbours at offsets (-1,-1), (-1,0), (-1,+1), (0,-1) have strictly smaller
- * values.  phi0 wraps; rows
+ * values (with a d0 axis: the 3 x 3 x 3 block, see hough_binning).  phi0 wraps; rows
  * outside the grid count as empty.  Candidates are kept in raster order.
  * Asynchronous on `stream`.
  */
@@ -192,7 +212,7 @@ int hough_stage2(hough_ctx *ctx, void *stream);
 int hough_get_candidates(hough_ctx *ctx, hough_candidate *out, int32_t cap, int32_t *n_out,
                          int where, void *stream);
 
-/* Copy the n_qpt x n_phi row-major accumulator of the last vote.  Synchronises `stream`. */
+/* Copy the (stacked) rows x n_phi row-major accumulator of the last vote.  Synchronises `stream`. */
 int hough_get_accumulator(hough_ctx *ctx, uint16_t *out, int where, void *stream);
 
 /*
@@ -505,14 +525,14 @@ int hough_serve_inject(hough_server *server, int fault, int on);
  *
  * Runs the staging and vote kernels of hough_vote on the hits r, phi, z, layer (device pointers,
  * n_hits entries, same meaning and checks as hough_vote with HOUGH_DEVICE) and writes the
- * n_qpt x n_phi row-major cells -- layer masks, or counts with HOUGH_ACC_COUNTS -- to
+ * (stacked) rows x n_phi row-major cells -- layer masks, or counts with HOUGH_ACC_COUNTS -- to
  * `accumulator` (device, caller-owned).  If `device_error`
  * is not NULL it receives (device memory, asynchronously) the HOUGH_DEVERR_* bits of dropped hits.
  * The geometry and binning are read at each call; the stage-2 fields of the binning are ignored.
  *
  * Scratch: one fixed 8 MiB array in device memory, reserved by the CUDA runtime on every GPU that
- * loads this library and held until the process exits.  Limits: n_hits <= 131072, n_qpt <= 1024,
- * n_phi <= 4096; larger inputs return HOUGH_ECAPACITY before any work.  The first call on a device
+ * loads this library and held until the process exits.  Limits: n_hits <= 131072, rows (n_qpt,
+ * times n_d0 with a d0 axis) <= 1024, n_phi <= 4096; larger inputs return HOUGH_ECAPACITY before any work.  The first call on a device
  * (with that device current) looks up the array's device address; make that first call before
  * any stream capture.  Every call reuses the same array and clears what must start empty, so calls
  * whose work may overlap on the GPU race: issue them on one stream or synchronise between them.

@@ -38,7 +38,9 @@ class Binning(ctypes.Structure):
                 ("n_cot", ctypes.c_int32), ("n_z0", ctypes.c_int32), ("accumulator", ctypes.c_int32),
                 ("qpt_min", ctypes.c_double), ("qpt_max", ctypes.c_double),
                 ("cot_min", ctypes.c_double), ("cot_max", ctypes.c_double),
-                ("z0_min_cm", ctypes.c_double), ("z0_max_cm", ctypes.c_double)]
+                ("z0_min_cm", ctypes.c_double), ("z0_max_cm", ctypes.c_double),
+                ("n_d0", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("d0_min_cm", ctypes.c_double), ("d0_max_cm", ctypes.c_double)]
 
 
 class Limits(ctypes.Structure):
@@ -243,7 +245,14 @@ def make_binning(binning) -> Binning:
                    accumulator=int(getattr(binning, "accumulator", ACC_LAYERS)),
                    qpt_min=binning.qpt_min, qpt_max=binning.qpt_max,
                    cot_min=binning.cot_min, cot_max=binning.cot_max,
-                   z0_min_cm=binning.z0_min, z0_max_cm=binning.z0_max)
+                   z0_min_cm=binning.z0_min, z0_max_cm=binning.z0_max,
+                   n_d0=int(getattr(binning, "n_d0", 0)), reserved=0,
+                   d0_min_cm=float(getattr(binning, "d0_min", -1.0)), d0_max_cm=float(getattr(binning, "d0_max", 1.0)))
+
+
+def grid_rows(binning) -> int:
+    """Rows of the accumulator: n_qpt, times n_d0 with a d0 axis (stacked rows m * n_qpt + i)."""
+    return binning.n_qpt * max(int(getattr(binning, "n_d0", 0)), 1)
 
 
 class HoughContext:
@@ -303,7 +312,7 @@ class HoughContext:
         return out[: n.value].copy()
 
     def accumulator(self, stream=None) -> np.ndarray:
-        out = np.zeros((self.binning.n_qpt, self.binning.n_phi), dtype=np.uint16)
+        out = np.zeros((grid_rows(self.binning), self.binning.n_phi), dtype=np.uint16)
         _check(self._lib.hough_get_accumulator(self._h, _ptr(out), HOST, _stream(stream)))
         return out
 
@@ -448,7 +457,7 @@ class HoughBatch:
         return st
 
     def accumulator(self, event, stream=None) -> np.ndarray:
-        out = np.zeros((self.binning.n_qpt, self.binning.n_phi), dtype=np.uint16)
+        out = np.zeros((grid_rows(self.binning), self.binning.n_phi), dtype=np.uint16)
         _check(self._lib.hough_batch_accumulator(self._h, event, _ptr(out), HOST, _stream(stream)))
         return out
 

@@ -36,10 +36,10 @@ std::string tune_key(const hough_geometry *g, const hough_binning *bn, int devic
     while (bucket < n_events) bucket <<= 1;
     char buf[512];
     std::snprintf(buf, sizeof(buf),
-                  "gpu=%s;sms=%d;layers=%d;b=%.9g;acc=%d;qpt=%d[%.9g,%.9g];phi=%d;thr=%d;cot=%d[%.9g,%.9g];z0=%d[%.9g,%.9g];events<=%d",
+                  "gpu=%s;sms=%d;layers=%d;b=%.9g;acc=%d;qpt=%d[%.9g,%.9g];phi=%d;thr=%d;cot=%d[%.9g,%.9g];z0=%d[%.9g,%.9g];d0=%d[%.9g,%.9g];events<=%d",
                   prop.name, prop.multiProcessorCount, g->n_layers, g->b_tesla, bn->accumulator, bn->n_qpt, bn->qpt_min, bn->qpt_max,
                   bn->n_phi, bn->threshold, bn->n_cot, bn->cot_min, bn->cot_max, bn->n_z0, bn->z0_min_cm,
-                  bn->z0_max_cm, bucket);
+                  bn->z0_max_cm, bn->n_d0, bn->n_d0 > 0 ? bn->d0_min_cm : 0.0, bn->n_d0 > 0 ? bn->d0_max_cm : 0.0, bucket);
     for (char *p = buf; *p; ++p)
         if (*p == '\t' || *p == '\n') *p = ' ';
     return buf;

@@ -151,7 +151,7 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     w.band_rows = b->tiling.band_rows;
     w.band_cap = band_capacity(ax, b->tiling.band_rows);
     std::vector<float> kq(ax.n_qpt);
-    for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i + 0.5) * ax.dk);
+    for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
     A(cudaMemcpy(w.kq32, kq.data(), sizeof(float) * ax.n_qpt, cudaMemcpyHostToDevice));
     A(cudaMemset(w.memo, 0, sizeof(TableMemo)));
     A(cudaMemset(b->inputs_dev, 0, sizeof(HitInputs)));   // as inputs_on_device says

@@ -60,7 +60,7 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
     const TabEntry te = w.tab[l * ax.n_qpt + i];
     if (!li.present) return sc;
     if (li.uniform) {
-        if (i < li.lo || i > li.hi) return sc;
+        if (i < li.lo || i > li.hi || te.I == kNoVote) return sc;
         sc.table = 1;
         sc.g = te.g;
         sc.nr = 2;
@@ -72,6 +72,11 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
         }
         return sc;
     }
+    const int lstart = offs[l * nphi], lend = offs[(l + 1) * nphi];
+    if (ax.n_d0) {   // per-vote layer on a grid with a d0 axis: every hit of the layer
+        sc.nr = 1; sc.st[0] = lstart; sc.en[0] = lend;
+        return sc;
+    }
     // per-vote layer: the buckets allowed by the layer's radius range on row i
     const float k = w.kq32[i];
     const float c_lo = 0.15f * (float)ax.b / 100.f * __uint_as_float(w.radii->rmin[l]) * 0.999f;
@@ -80,7 +85,6 @@ __device__ LayerScan layer_scan(const Axes &ax, const Workspace &w, const int32_
     const float a2 = asinf(fminf(fmaxf(c_hi * k, -1.f), 1.f));
     const int ja = (int)floorf(j + s32 * fminf(a1, a2)) - 2;
     const int jb = (int)floorf(j + 1 + s32 * fmaxf(a1, a2)) + 2;
-    const int lstart = offs[l * nphi], lend = offs[(l + 1) * nphi];
     if (jb - ja + 1 >= nphi) {
         sc.nr = 1; sc.st[0] = lstart; sc.en[0] = lend;
     } else {
@@ -179,7 +183,11 @@ __device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t 
                 mem = hh.f < seg.g[q >> 1];
             } else {
                 const int rlo = (int)(hh.rows & 0xFFFFu), rhi = (int)(hh.rows >> 16);
-                if (i >= rlo && i <= rhi) {
+                if (ax.n_d0) {   // every vote in FP64 on a grid with a d0 axis
+                    const ColdHit ch = cold[p];
+                    int jj = 0;
+                    mem = exact_vote(ax, (double)ch.r, (double)ch.phi, i, &jj) && jj == j;
+                } else if (i >= rlo && i <= rhi) {
                     const float x = fminf(fmaxf(hh.c * w.kq32[i], -1.f), 1.f);
                     const float vq = fmaf(-asinf(x), s32, hh.f);
                     const float fl = floorf(vq);
@@ -211,14 +219,18 @@ __device__ int warp_enumerate(const Axes &ax, const Workspace &w, const int32_t 
     return count;
 }
 
-// Arc length of a member at row i: from the table for a uniform layer, else r asin(|x|) / |x| in FP64.
+// Arc length of a member at row i: from the table for a uniform layer, else from the closest
+// approach in FP64 (r asin(|x|) / |x| for prompt tracks).
 __device__ __forceinline__ double member_arc(const Axes &ax, const Workspace &w, int l, int i, float r)
 {
     const LayerInfo li = w.info[l];
     if (li.uniform) return w.arc[l * ax.n_qpt + i];
     const double rd = (double)r;
-    const double axv = fabs(__dmul_rn(sagitta_coef(ax, rd), qpt_centre(ax, i)));
-    return axv > 0.0 ? __ddiv_rn(__dmul_rn(rd, asin(axv)), axv) : rd;
+    const double x = __dmul_rn(sagitta_coef(ax, rd), qpt_centre(ax, i));
+    const double d0 = d0_centre(ax, i);
+    double y = x;
+    track_sin(rd, x, d0, &y);   // a member's track passes its radius: its vote was cast
+    return track_arc(rd, x, d0, y);
 }
 
 // Stage-2 coefficients of one member at row i: z0 coordinate w(m) = a - (m - m_ref) b in FP32.

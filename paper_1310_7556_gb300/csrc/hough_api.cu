@@ -116,6 +116,11 @@ int check_binning(const hough_geometry *g, const hough_binning *b)
     if (!std::isfinite(b->qpt_min) || !std::isfinite(b->qpt_max) || !std::isfinite(b->cot_min) ||
         !std::isfinite(b->cot_max) || !std::isfinite(b->z0_min_cm) || !std::isfinite(b->z0_max_cm))
         return fail(HOUGH_EINVAL, "axis bounds must be finite");
+    if (b->reserved != 0) return fail(HOUGH_EINVAL, "reserved fields must be 0");
+    if (b->n_d0 < 0 || (int64_t)b->n_d0 * b->n_qpt > 65535)
+        return fail(HOUGH_EINVAL, "n_d0 must be >= 0 with n_d0 * n_qpt <= 65535");
+    if (b->n_d0 > 0 && (!(b->d0_min_cm < b->d0_max_cm) || !std::isfinite(b->d0_min_cm) || !std::isfinite(b->d0_max_cm)))
+        return fail(HOUGH_EINVAL, "the d0 axis needs finite d0_min_cm < d0_max_cm");
     return HOUGH_OK;
 }
 
@@ -123,7 +128,11 @@ Axes make_axes_impl(const hough_geometry *g, const hough_binning *b)
 {
     Axes ax;
     ax.n_layers = g->n_layers;
-    ax.n_qpt = b->n_qpt;
+    ax.q_rows = b->n_qpt;
+    ax.n_d0 = b->n_d0 > 0 ? b->n_d0 : 0;
+    ax.n_qpt = b->n_qpt * (ax.n_d0 ? ax.n_d0 : 1);   // rows of the stacked grid
+    ax.d0_min = ax.n_d0 ? b->d0_min_cm : 0.0;
+    ax.dd = ax.n_d0 ? (b->d0_max_cm - b->d0_min_cm) / b->n_d0 : 0.0;
     ax.n_phi = b->n_phi;
     ax.threshold = b->threshold;
     ax.counts = b->accumulator == HOUGH_ACC_COUNTS ? 1 : 0;
@@ -188,6 +197,7 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
         return fail(HOUGH_EINVAL, "gather_threads must be 0, 256, 512 or 1024");
     if (ax.counts && t->vote_mode != HOUGH_VOTE_SCATTER)
         return fail(HOUGH_EINVAL, "the count accumulator needs vote_mode HOUGH_VOTE_SCATTER");
+    if (ax.n_d0 && t->band_rows != 1) return fail(HOUGH_EINVAL, "a d0 axis needs band_rows 1");
     const Tiling tt = resolve_tiling_impl(ax, t);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -390,7 +400,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     w.band_cap = band_capacity(ax, c->tiling.band_rows);
     // FP32 q/pT bin centres: the FP64 centre rounded once
     std::vector<float> kq(ax.n_qpt);
-    for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i + 0.5) * ax.dk);
+    for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
     A(cudaMemcpy(w.kq32, kq.data(), sizeof(float) * ax.n_qpt, cudaMemcpyHostToDevice));
     A(cudaMemset(c->hit_start, 0, 2 * sizeof(int64_t)));
     A(cudaMemset(w.memo, 0, sizeof(TableMemo)));

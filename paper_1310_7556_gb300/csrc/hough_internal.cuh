@@ -32,8 +32,11 @@ constexpr double kInvTwoPi = 0.15915494309189535;  // 1 / (2 pi) rounded to doub
 
 // Axes of the two grids, by value into every kernel.
 struct Axes {
-    int n_layers, n_qpt, n_phi, threshold, n_cot, n_z0;
+    int n_layers, n_qpt, n_phi, threshold, n_cot, n_z0;   // n_qpt: rows of the grid, every d0 slice's
     int counts;                   // 1: cells hold saturating vote counts; 0: layer masks
+    int q_rows;                   // q/pT bins: row r holds q/pT bin r % q_rows of d0 slice r / q_rows
+    int n_d0;                     // d0 bins (0: prompt tracks, one slice at d0 = 0)
+    double d0_min, dd;            // d0 axis: first edge and bin width (cm)
     double b, qpt_min, qpt_max, dk;
     double cot_min, cot_max, dt, z0_min, z0_max;
     double zscale;                // n_z0 / (z0_max - z0_min): z0 bins per cm
@@ -86,10 +89,15 @@ struct LayerRadii {
 struct LayerInfo {
     int32_t present;    // the layer has hits
     int32_t uniform;    // all its hits share one radius (or it has none): the table path applies
-    int32_t lo, hi;     // voting rows of that radius (lo > hi: none)
+    int32_t lo, hi;     // rows of that radius that may vote (lo > hi: none); a row votes when its
+                        // table entry is not kNoVote
     uint32_t r_bits;    // the radius (float bits)
-    int32_t pad[3];
+    int32_t nvote;      // rows that vote
+    int32_t pad[2];
 };
+
+// Table entry of a (layer, row) on which the layer's radius casts no vote.
+constexpr int32_t kNoVote = -(1 << 30);
 
 // Memo of the per-(layer, row) table: the radius each layer's rows were computed for.
 struct TableMemo {
@@ -97,6 +105,7 @@ struct TableMemo {
     int32_t valid[HOUGH_MAX_LAYERS];
     int32_t dirty[HOUGH_MAX_LAYERS];
     int32_t lo[HOUGH_MAX_LAYERS], hi[HOUGH_MAX_LAYERS];   // voting rows of r_bits
+    int32_t nvote[HOUGH_MAX_LAYERS];
 };
 
 // Device-resident hit pointers, for launch sequences captured once and replayed on new inputs.
@@ -340,9 +349,48 @@ __device__ __forceinline__ float2 two_prod(float a, float b)
     return make_float2(p, fmaf(a, b, -p));
 }
 
-__device__ __forceinline__ double qpt_centre(const Axes &ax, int i)
+// q/pT bin centre of row r (its q/pT bin r % q_rows with a d0 axis).
+__device__ __forceinline__ double qpt_centre(const Axes &ax, int r)
 {
+    const int i = ax.n_d0 ? r % ax.q_rows : r;
     return __dadd_rn(ax.qpt_min, __dmul_rn((double)i + 0.5, ax.dk));
+}
+
+// d0 bin centre of row r (0 without a d0 axis).
+__device__ __forceinline__ double d0_centre(const Axes &ax, int r)
+{
+    if (!ax.n_d0) return 0.0;
+    return __dadd_rn(ax.d0_min, __dmul_rn((double)(r / ax.q_rows) + 0.5, ax.dd));
+}
+
+// sin(phi - phi0) of a hit at radius r on the track of sagitta argument x and impact parameter d0:
+// (rho r^2 + 2 d0 + rho d0^2) / (2 r (1 + rho d0)) with rho = 2 x / r, in FP64 in that order; x
+// itself at d0 = 0.  Returns false when 1 + rho d0 <= 0 (no such track).
+__device__ __forceinline__ bool track_sin(double r, double x, double d0, double *y)
+{
+    if (d0 == 0.0) {
+        *y = x;
+        return true;
+    }
+    const double rho = __ddiv_rn(__dmul_rn(2.0, x), r);
+    const double den = __dmul_rn(__dmul_rn(2.0, r), __dadd_rn(1.0, __dmul_rn(rho, d0)));
+    if (!(den > 0.0)) return false;
+    const double num = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(rho, r), r), __dmul_rn(2.0, d0)),
+                                 __dmul_rn(__dmul_rn(rho, d0), d0));
+    *y = __ddiv_rn(num, den);
+    return true;
+}
+
+// Transverse arc length from the closest approach to that hit: r asin(|x|) / |x| at d0 = 0, else
+// 2 asin(|rho| chord / 2) / |rho| with chord^2 = r^2 + d0^2 - 2 r d0 y.
+__device__ __forceinline__ double track_arc(double r, double x, double d0, double y)
+{
+    const double ax = fabs(x);
+    if (d0 == 0.0) return ax > 0.0 ? __ddiv_rn(__dmul_rn(r, asin(ax)), ax) : r;
+    const double c2 = __dsub_rn(__dadd_rn(__dmul_rn(r, r), __dmul_rn(d0, d0)), __dmul_rn(__dmul_rn(__dmul_rn(2.0, r), d0), y));
+    const double chord = __dsqrt_rn(c2);
+    const double arho = __ddiv_rn(__dmul_rn(2.0, ax), r);
+    return arho > 0.0 ? __ddiv_rn(__dmul_rn(2.0, asin(__ddiv_rn(__dmul_rn(arho, chord), 2.0))), arho) : chord;
 }
 
 __device__ __forceinline__ double sagitta_coef(const Axes &ax, double r_cm)
@@ -421,6 +469,17 @@ __device__ __forceinline__ int exact_bin(const Axes &ax, double phi, double x)
     return (int)(j < 0 ? j + ax.n_phi : j);
 }
 
+// The vote of a hit (r, phi) on row `row` by the definition, in FP64: false when the row's track
+// cannot pass the hit's radius (1 + rho d0 <= 0 or |sin(phi - phi0)| > 1), else its phi0 bin in *j.
+__device__ __forceinline__ bool exact_vote(const Axes &ax, double r, double phi, int row, int *j)
+{
+    const double x = __dmul_rn(sagitta_coef(ax, r), qpt_centre(ax, row));
+    double y = 2.0;
+    if (!track_sin(r, x, d0_centre(ax, row), &y) || !(fabs(y) <= 1.0)) return false;
+    *j = exact_bin(ax, phi, y);
+    return true;
+}
+
 __device__ __forceinline__ int wrap_col(int j, int n)
 {
     j += j < 0 ? n : 0;
@@ -435,7 +494,10 @@ __device__ __forceinline__ int wrap_col(int j, int n)
 // 8 consecutive cells per pass, so thread order is raster order and one block-wide scan of the
 // per-thread counts places every candidate.  Candidates go to `out` (cell index i * Nphi + j,
 // mask read from M) in raster order; returns their number.  Called by all TPB threads.
-template <int TPB, typename V>
+// D3 (a grid with a d0 axis): one row (nrows = 1) whose 3 x 3 x 3 blocks are held as nine rows,
+// (slice m + dm, row i + di) at index 3 (dm + 1) + di + 1; the nine of slice m - 1 precede the
+// cell in raster order (strictly lower), the nine of slice m + 1 follow it (not higher).
+template <int TPB, typename V, bool D3 = false>
 __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, int nphi, int threshold,
                                                 const uint16_t *M, uint2 *out, int cap)
 {
@@ -452,7 +514,7 @@ __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, 
         if (it < items) {
             rr = it / eighth;
             j0 = (it - rr * eighth) * 8;
-            const V *row = pc + (rr + 1) * nphi;
+            const V *row = pc + (D3 ? 4 : rr + 1) * nphi;
             const V *up = row - nphi, *dn = row + nphi;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -460,8 +522,16 @@ __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, 
                 const int p = row[j];
                 if (p >= threshold) {
                     const int jm = wrap_col(j - 1, nphi), jp = wrap_col(j + 1, nphi);
-                    const bool peak = up[jm] < p && up[j] < p && up[jp] < p && row[jm] < p &&
-                                      row[jp] <= p && dn[jm] <= p && dn[j] <= p && dn[jp] <= p;
+                    bool peak = up[jm] < p && up[j] < p && up[jp] < p && row[jm] < p &&
+                                row[jp] <= p && dn[jm] <= p && dn[j] <= p && dn[jp] <= p;
+                    if (D3) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const V *a = pc + q * nphi, *b = pc + (6 + q) * nphi;
+                            peak = peak && a[jm] < p && a[j] < p && a[jp] < p && b[jm] <= p && b[j] <= p &&
+                                   b[jp] <= p;
+                        }
+                    }
                     pk |= (unsigned)peak << c;
                 }
             }

@@ -140,8 +140,10 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
 
 // One CTA per layer: whether all the layer's hits share one radius, that radius's voting rows and
 // whether the memoised table rows must be recomputed; then, for a uniform layer whose radius
-// changed, per row: T = Nphi asin(x) / (2 pi) split into I + g, the arc length
-// s = r asin(|x|) / |x| for stage 2, and the stage-2 terms derived from it.
+// changed, per row: T = Nphi asin(y) / (2 pi) split into I + g, y = sin(phi - phi0) of the row's
+// track (y = x for prompt tracks, the d0 relation on a grid with a d0 axis), the arc length from
+// the closest approach for stage 2, and the stage-2 terms derived from it.  Rows on which the
+// radius casts no vote get the entry kNoVote.
 __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Workspace w)
 {
     pdl_enter();
@@ -156,11 +158,17 @@ __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Wor
         li.lo = 1;
         li.hi = 0;
         li.r_bits = rmin;
-        li.pad[0] = li.pad[1] = li.pad[2] = 0;
+        li.nvote = 0;
+        li.pad[0] = li.pad[1] = 0;
         const int dirty = li.present && li.uniform && !(w.memo->valid[l] && w.memo->r_bits[l] == rmin);
         if (li.present && li.uniform) {
             if (dirty) {
-                row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
+                if (ax.n_d0) {   // every slice has its own rows; the table marks those that vote
+                    li.lo = 0;
+                    li.hi = ax.n_qpt - 1;
+                } else {
+                    row_range(ax, sagitta_coef(ax, (double)__uint_as_float(rmin)), &li.lo, &li.hi);
+                }
                 w.memo->r_bits[l] = rmin;
                 w.memo->lo[l] = li.lo;
                 w.memo->hi[l] = li.hi;
@@ -168,6 +176,7 @@ __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Wor
             } else {
                 li.lo = w.memo->lo[l];   // the same radius as before: its rows are memoised
                 li.hi = w.memo->hi[l];
+                li.nvote = w.memo->nvote[l];
             }
         }
         w.info[l] = li;
@@ -177,27 +186,35 @@ __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Wor
     }
     __syncthreads();
     if (!s_dirty) return;
+    __shared__ int s_nvote;
+    if (threadIdx.x == 0) s_nvote = 0;
+    __syncthreads();
     const LayerInfo li = s_li;
     const double r = (double)__uint_as_float(li.r_bits);
     const double t0 = __dadd_rn(ax.cot_min, __dmul_rn(0.5, ax.dt));
+    int nvote = 0;
     for (int i = threadIdx.x; i < ax.n_qpt; i += blockDim.x) {
         const int q = l * ax.n_qpt + i;
         TabEntry te;
-        te.I = 0;
+        te.I = kNoVote;
         te.g = 0.f;
         double s = 0.0;
         if (i >= li.lo && i <= li.hi) {
             const double x = __dmul_rn(sagitta_coef(ax, r), qpt_centre(ax, i));
-            const double T = __dmul_rn(__dmul_rn((double)ax.n_phi, asin(x)), kInvTwoPi);
-            const double fI = floor(T);
-            te.I = (int32_t)fI;
-            te.g = (float)(T - fI);
-            if (te.g >= 1.0f) {
-                te.I += 1;
-                te.g = 0.f;
+            const double d0 = d0_centre(ax, i);
+            double y = 2.0;
+            if (track_sin(r, x, d0, &y) && fabs(y) <= 1.0) {
+                const double T = __dmul_rn(__dmul_rn((double)ax.n_phi, asin(y)), kInvTwoPi);
+                const double fI = floor(T);
+                te.I = (int32_t)fI;
+                te.g = (float)(T - fI);
+                if (te.g >= 1.0f) {
+                    te.I += 1;
+                    te.g = 0.f;
+                }
+                s = track_arc(r, x, d0, y);
+                ++nvote;
             }
-            const double axv = fabs(x);
-            s = axv > 0.0 ? __ddiv_rn(__dmul_rn(r, asin(axv)), axv) : r;
         }
         w.tab[q] = te;
         w.arc[q] = s;
@@ -209,6 +226,12 @@ __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Wor
             const float sh = (float)S, bh = (float)B;
             w.zco[q] = make_float4(sh, (float)(S - (double)sh), bh, (float)(B - (double)bh));
         }
+    }
+    if (nvote) atomicAdd(&s_nvote, nvote);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        w.info[l].nvote = s_nvote;
+        w.memo->nvote[l] = s_nvote;
     }
 }
 
@@ -292,9 +315,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Worksp
     if (threadIdx.x < ax.n_layers) {
         const int l = threadIdx.x;
         const LayerInfo li = w.info[l];
-        if (li.present && li.uniform && li.hi >= li.lo) {
+        if (li.present && li.uniform && li.nvote > 0) {
             const long long n_l = offs[(l + 1) * ax.n_phi] - offs[l * ax.n_phi];
-            w.stats[e].votes_by_layer[l] += (unsigned long long)(n_l * (li.hi - li.lo + 1));
+            w.stats[e].votes_by_layer[l] += (unsigned long long)(n_l * li.nvote);
         }
     }
 }
@@ -318,7 +341,19 @@ __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspa
         const LayerInfo li = w.info[l];
         int lo = li.lo, hi = li.hi;
         const float rr = in.r[h];
-        if (!li.uniform) {
+        if (!li.uniform && ax.n_d0) {
+            // every row may hold a vote; the vote kernels decide each in FP64
+            lo = 0;
+            hi = ax.n_qpt - 1;
+            const double c = sagitta_coef(ax, (double)rr);
+            unsigned long long nv = 0;
+            for (int row = 0; row < ax.n_qpt; ++row) {
+                double y = 2.0;
+                if (track_sin((double)rr, __dmul_rn(c, qpt_centre(ax, row)), d0_centre(ax, row), &y) && fabs(y) <= 1.0)
+                    ++nv;
+            }
+            if (nv) atomicAdd(&w.stats[e].votes_by_layer[l], nv);
+        } else if (!li.uniform) {
             row_range(ax, sagitta_coef(ax, (double)rr), &lo, &hi);
             if (hi >= lo)
                 atomicAdd(&w.stats[e].votes_by_layer[l], (unsigned long long)(hi - lo + 1));

@@ -72,7 +72,7 @@ cudaError_t scratch_address(int device, unsigned char **out)
 __global__ void static_kq_kernel(Axes ax, float *kq32)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ax.n_qpt) kq32[i] = (float)(ax.qpt_min + (i + 0.5) * ax.dk);
+    if (i < ax.n_qpt) kq32[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
 }
 
 }  // namespace
@@ -93,8 +93,10 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
         return fail(HOUGH_EINVAL, "invalid binning");
     if (b->accumulator != HOUGH_ACC_LAYERS && b->accumulator != HOUGH_ACC_COUNTS)
         return fail(HOUGH_EINVAL, "accumulator must be HOUGH_ACC_LAYERS or HOUGH_ACC_COUNTS");
-    if (b->n_qpt > kStaticMaxQpt || b->n_phi > kStaticMaxPhi)
-        return fail(HOUGH_ECAPACITY, "hough_vote_static: n_qpt must be <= 1024 and n_phi <= 4096");
+    if (b->n_d0 < 0 || b->reserved != 0 || (b->n_d0 > 0 && !(b->d0_min_cm < b->d0_max_cm)))
+        return fail(HOUGH_EINVAL, "invalid d0 axis");
+    if ((int64_t)b->n_qpt * (b->n_d0 > 0 ? b->n_d0 : 1) > kStaticMaxQpt || b->n_phi > kStaticMaxPhi)
+        return fail(HOUGH_ECAPACITY, "hough_vote_static: rows must be <= 1024 and n_phi <= 4096");
     if (n_hits < 0) return fail(HOUGH_EINVAL, "n_hits must be >= 0");
     if (n_hits > kStaticMaxHits) return fail(HOUGH_ECAPACITY, "hough_vote_static: at most 131072 hits");
     if (n_hits > 0 && (!r || !phi || !z || !layer)) return fail(HOUGH_EINVAL, "hit arrays are required");

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
         tab[q] = te;
     }
     for (int q = threadIdx.x; q < R; q += TPB) kq[q] = q < nrows ? p.w.kq32[i0 + q] : 0.f;
+    __syncthreads();
 
     // per layer, the hits that can vote into this tile: a cyclic range of phi bins J
     if (threadIdx.x < HOUGH_MAX_LAYERS) {
@@ -130,17 +131,26 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                 if (GENERAL_ONLY) {
                     none = true;   // the gather kernel votes for this layer
                 } else {
-                    const LayerInfo li = p.w.info[l];
-                    const int a = max(i0, li.lo), b = min(i0 + nrows - 1, li.hi);
-                    if (a > b) {
+                    // vote bin J - I - (f < g) lies in [J0, J0 + W) only for J in
+                    // [J0 + min I, J0 + W + max I] over the slab's voting rows
+                    int imin = INT_MAX, imax = INT_MIN;
+                    for (int rr = 0; rr < nrows; ++rr) {
+                        const int I = tab[l * R + rr].I;
+                        if (I != kNoVote) {
+                            imin = min(imin, I);
+                            imax = max(imax, I);
+                        }
+                    }
+                    if (imin > imax) {
                         none = true;
                     } else {
-                        // vote bin J - I - (f < g) lies in [J0, J0 + W) only for J in [J0 + I_a, J0 + W + I_b]
-                        const TabEntry ta = p.w.tab[l * ax.n_qpt + a], tb = p.w.tab[l * ax.n_qpt + b];
-                        ja = J0 + ta.I;
-                        jb = J0 + W + tb.I;
+                        ja = J0 + imin;
+                        jb = J0 + W + imax;
                     }
                 }
+            } else if (!none && ax.n_d0) {
+                ja = 0;   // per-vote layer on a grid with a d0 axis: every hit of the layer
+                jb = nphi;
             } else if (!none) {
                 // per-vote layer: bound asin(c k) over the layer's radius range and the slab's rows
                 const float c_lo = 0.15f * (float)ax.b / 100.f * __uint_as_float(p.w.radii->rmin[l]);
@@ -225,11 +235,19 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
         const uint32_t lbit = 1u << l;
         for (int rr = 0; rr < nrows; ++rr) {
             const int i = i0 + rr;
-            const bool act = has && i >= rlo && i <= rhi;
+            bool act = has && i >= rlo && i <= rhi;
             int j;
             if (uni) {
                 const TabEntry te = tab[l * R + rr];
+                act = act && te.I != kNoVote;
                 j = J - te.I - (hh.f < te.g ? 1 : 0);
+            } else if (ax.n_d0) {
+                // a grid with a d0 axis: every vote of a per-vote layer in FP64, in the definition's order
+                j = 0;
+                if (act) {
+                    const ColdHit ch = cold[pos];
+                    act = exact_vote(ax, (double)ch.r, (double)ch.phi, i, &j);
+                }
             } else {
                 const float x = fminf(fmaxf(hh.c * kq[rr], -1.f), 1.f);
                 const float vq = fmaf(-asinf(x), p.s32, hh.f);
@@ -345,9 +363,11 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
             const LayerInfo li = w.info[l];
             if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
                 const TabEntry te = w.tab[l * ax.n_qpt + i];
-                I = te.I;
-                gb = __float_as_uint(te.g);
-                valid = 1u;
+                if (te.I != kNoVote) {
+                    I = te.I;
+                    gb = __float_as_uint(te.g);
+                    valid = 1u;
+                }
             }
         }
         const unsigned m = __ballot_sync(0xFFFFFFFFu, valid) >> (threadIdx.x & 16);
@@ -510,6 +530,51 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
     __syncthreads();
     const int cnt = band_peak_search<kPeakThreads>(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
     if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+}
+
+// Peak search of one stacked row (slice m, q/pT row i) of a grid with a d0 axis: the nine rows
+// (m + dm, i + di) of its cells' 3 x 3 x 3 blocks are staged as cell values -- layer counts as
+// bytes, or 16-bit counts -- rows outside the slice and slices outside the grid as empty.  The
+// row's candidates go to its band list (band height 1), so the lists concatenate in raster order.
+template <bool COUNTS>
+__global__ void __launch_bounds__(kPeakThreads) peaks3_kernel(Axes ax, Workspace w)
+{
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char pc[];
+    const int nb = ax.n_qpt;
+    const int e = blockIdx.x / nb, row = blockIdx.x - e * nb;
+    const int nphi = ax.n_phi, Q = ax.q_rows;
+    const int m = row / Q, i = row - m * Q;
+    const uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
+    const int v8 = nphi >> 3;
+    for (int q = threadIdx.x; q < 9 * v8; q += kPeakThreads) {
+        const int sidx = q / v8, c8 = q - sidx * v8;
+        const int mm = m + sidx / 3 - 1, ii = i + sidx % 3 - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (mm >= 0 && mm < ax.n_d0 && ii >= 0 && ii < Q)
+            v = *reinterpret_cast<const uint4 *>(M + (int64_t)(mm * Q + ii) * nphi + c8 * 8);
+        if (COUNTS) {
+            *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(pc) + sidx * nphi + c8 * 8) = v;
+        } else {
+            const uint32_t words[4] = {v.x, v.y, v.z, v.w};
+            uint32_t packed[2] = {0u, 0u};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t lo = (uint32_t)__popc(words[u] & 0xFFFFu), hi = (uint32_t)__popc(words[u] >> 16);
+                packed[u >> 1] |= (lo | (hi << 8)) << ((u & 1) * 16);
+            }
+            *reinterpret_cast<uint2 *>(pc + sidx * nphi + c8 * 8) = make_uint2(packed[0], packed[1]);
+        }
+    }
+    __syncthreads();
+    uint2 *out = w.band_cands + ((int64_t)e * nb + row) * w.band_cap;
+    int cnt;
+    if (COUNTS)
+        cnt = band_peak_search<kPeakThreads, uint16_t, true>(reinterpret_cast<const uint16_t *>(pc), 1, row, nphi,
+                                                             ax.threshold, M, out, w.band_cap);
+    else
+        cnt = band_peak_search<kPeakThreads, unsigned char, true>(pc, 1, row, nphi, ax.threshold, M, out, w.band_cap);
+    if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + row] = cnt;
 }
 
 // One CTA per event: exclusive scan of the band counts, then the band lists concatenated into
@@ -786,14 +851,16 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
 
 size_t band_smem_bytes(const Axes &ax, int band_rows)
 {
-    return (size_t)(band_rows + 2) * ax.n_phi * (ax.counts ? 2 : 1);
+    const size_t rows = ax.n_d0 ? 9 : (size_t)(band_rows + 2);   // with a d0 axis: one row's 3 x 3 x 3 blocks
+    return rows * ax.n_phi * (ax.counts ? 2 : 1);
 }
 
 cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
 {
     const int nb = n_bands(ax, w.band_rows);
     const size_t smem = band_smem_bytes(ax, w.band_rows);
-    auto kernel = ax.counts ? peaks_kernel<true> : peaks_kernel<false>;
+    auto kernel = ax.n_d0 ? (ax.counts ? peaks3_kernel<true> : peaks3_kernel<false>)
+                          : (ax.counts ? peaks_kernel<true> : peaks_kernel<false>);
     cudaError_t err;
     if ((err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return err;
     if ((err = launch_chained(kernel, dim3(w.n_events * nb), dim3(kPeakThreads), smem, stream, ax, w))) return err;

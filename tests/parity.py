@@ -93,17 +93,31 @@ def _touched(flags, n_phi):
     return cells
 
 
-def assert_candidate_parity(c_gpu, c_ref, flags, n_phi):
-    """Candidate lists equal, except candidates whose 3 x 3 block holds a cell a flagged vote touched."""
+def stacked(cands, n_qpt):
+    """Oracle candidates with iq as the stacked row id0 * n_qpt + iq, as the GPU reports them."""
+    out = cands.copy()
+    out["iq"] = cands["id0"] * n_qpt + cands["iq"]
+    return out
+
+
+def assert_candidate_parity(c_gpu, c_ref, flags, n_phi, q_rows=None):
+    """Candidate lists equal, except candidates whose 3 x 3 block (3 x 3 x 3 with a d0 axis of
+    q_rows rows per slice; rows stacked) holds a cell a flagged vote touched."""
     touched = _touched(flags, n_phi)
     rows_any = {i for (i, j) in touched if j == -1}
 
+    def neighbour_rows(i):
+        if q_rows is None:
+            return [i - 1, i, i + 1]
+        m, q = divmod(i, q_rows)
+        return [(m + dm) * q_rows + q + di for dm in (-1, 0, 1) for di in (-1, 0, 1) if 0 <= q + di < q_rows]
+
     def near(i, j):
-        for di in (-1, 0, 1):
-            if i + di in rows_any:
+        for ii in neighbour_rows(i):
+            if ii in rows_any:
                 return True
             for dj in (-1, 0, 1):
-                if (i + di, (j + dj) % n_phi) in touched:
+                if (ii, (j + dj) % n_phi) in touched:
                     return True
         return False
 
@@ -131,7 +145,8 @@ def assert_members_and_stage2_parity(c_gpu, off_gpu, mem_gpu, ref, threshold, n_
             if int(c["mask"]) < 65535 and not int(c["flags"]) & 2:
                 assert int(c["n_members"]) == int(c["mask"]), f"({int(c['iq'])}, {int(c['jphi'])}): members vs count"
     c_ref = ref["candidates"]
-    index_ref = {(int(c["iq"]), int(c["jphi"])): q for q, c in enumerate(c_ref)}
+    n_qpt = ref.get("n_qpt", 0)
+    index_ref = {(int(c["id0"]) * n_qpt + int(c["iq"]), int(c["jphi"])): q for q, c in enumerate(c_ref)}
     mflag_hits = {}
     for f in ref["member_flags"]:
         mflag_hits.setdefault(int(f["cand"]), set()).add(int(f["hit"]))

@@ -43,7 +43,7 @@ def test_binding_covers_every_declared_symbol(lib):
 def test_struct_layouts_match_header(lib):
     from paper_1310_7556_gb300 import binding
     assert ctypes.sizeof(binding.Geometry) == 16
-    assert ctypes.sizeof(binding.Binning) == 6 * 4 + 6 * 8
+    assert ctypes.sizeof(binding.Binning) == 6 * 4 + 6 * 8 + 2 * 4 + 2 * 8
     assert ctypes.sizeof(binding.Limits) == 16
     assert binding.CANDIDATE_DTYPE.itemsize == 32
     assert ctypes.sizeof(binding.Tiling) == 32

@@ -12,7 +12,7 @@ import oracle
 from paper_1310_7556_gb300 import eventgen as eg
 
 from parity import (assert_accumulator_parity, assert_candidate_parity,
-                    assert_members_and_stage2_parity)
+                    assert_members_and_stage2_parity, stacked)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,13 +49,16 @@ def run_gpu(binding, geometry, binning, ev, tiling=None, where="host", max_candi
 
 def check_event(binding, geometry, binning, ev, **kw):
     ref = oracle.run(geometry, binning, ev)
+    ref["n_qpt"] = binning.n_qpt
+    d0 = binning.n_d0 > 0
     got = run_gpu(binding, geometry, binning, ev, **kw)
     counts = binning.accumulator == eg.ACC_COUNTS
     n_bits = assert_accumulator_parity(got["M"], ref["M"], ref["vote_flags"], counts=counts)
     assert int(got["stats"].votes) == int(ref["votes_by_layer"].sum())
     for l in range(geometry.n_layers):
         assert int(got["stats"].votes_by_layer[l]) == int(ref["votes_by_layer"][l])
-    n_c = assert_candidate_parity(got["candidates"], ref["candidates"], ref["vote_flags"], binning.n_phi)
+    n_c = assert_candidate_parity(got["candidates"], stacked(ref["candidates"], binning.n_qpt), ref["vote_flags"],
+                                  binning.n_phi, q_rows=binning.n_qpt if d0 else None)
     checked = assert_members_and_stage2_parity(got["candidates"], got["member_offsets"], got["members"], ref,
                                                binning.threshold, geometry.n_layers, counts)
     return dict(ref=ref, got=got, mismatched_bits=n_bits, mismatched_cands=n_c, stage2_checked=checked)
