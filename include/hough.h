@@ -230,7 +230,11 @@ int hough_get_stats(hough_ctx *ctx, hough_stats *out, void *stream);
 /*
  * Whole path on one event: hough_vote, hough_peaks, hough_stage2 and
  * hough_get_candidates in one call (hits and candidates both in `where` memory).
- * Synchronises `stream`.
+ * Synchronises `stream`.  With HOUGH_HOST the hits are checked on the device
+ * (the predicates of hough_vote's host check); a bad hit makes the call return
+ * HOUGH_EINVAL after it has synchronised, with no candidates copied.  The first
+ * HOUGH_HOST call allocates the context's pinned result staging
+ * (max_candidates records), kept until hough_destroy.
  */
 int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float *z,
                   const uint8_t *layer, int64_t n_hits, hough_candidate *out, int32_t cap,

@@ -2,6 +2,7 @@
 // device buffers, and the order in which the kernels of the path are enqueued.
 #include <algorithm>
 #include <atomic>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -64,6 +65,8 @@ struct hough_ctx {
     uint8_t *in_layer = nullptr;
     int32_t *mem_idx = nullptr;
     DevStats *stats_host = nullptr;      // pinned
+    hough_candidate *cands_mapped = nullptr;       // pinned, mapped: hough_process's result staging
+    hough_candidate *cands_mapped_dev = nullptr;   // its device address
     int64_t n_hits = 0;
     int stage = 0;                       // 0 nothing, 1 voted, 2 peaks, 3 stage 2
     bool timing = false;
@@ -78,6 +81,7 @@ struct hough_ctx {
         cudaDeviceSynchronize();
         for (void *p : allocations) cudaFree(p);
         if (stats_host) cudaFreeHost(stats_host);
+        if (cands_mapped) cudaFreeHost(cands_mapped);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -237,10 +241,26 @@ size_t band_list_entries_impl(const Axes &ax)
     return best;
 }
 
+// Hits are checked a block at a time without branches (the compiler vectorises the pass); only a
+// block with a bad hit is scanned again hit by hit, to name the first one.
 int check_host_hits_impl(const Axes &ax, const float *r, const float *phi, const float *z,
                          const uint8_t *layer, int64_t n)
 {
-    for (int64_t h = 0; h < n; ++h) {
+    constexpr int64_t kBlock = 4096;
+    const unsigned L = (unsigned)ax.n_layers;
+    int64_t first_bad_block = -1;
+    for (int64_t b0 = 0; b0 < n && first_bad_block < 0; b0 += kBlock) {
+        const int64_t b1 = std::min(n, b0 + kBlock);
+        unsigned bad = 0;
+        for (int64_t h = b0; h < b1; ++h) {
+            const float rr = r[h], pp = phi[h], zz = z[h];
+            bad |= (unsigned)(layer[h] >= L) | (unsigned)!(rr > 0.f) | (unsigned)!(rr <= FLT_MAX) |
+                   (unsigned)!(std::fabs(pp) <= 1000.f) | (unsigned)!(std::fabs(zz) <= FLT_MAX);
+        }
+        if (bad) first_bad_block = b0;
+    }
+    if (first_bad_block < 0) return HOUGH_OK;
+    for (int64_t h = first_bad_block; h < n; ++h) {
         if (layer[h] >= ax.n_layers) return fail(HOUGH_EINVAL, "hit %lld: layer %d >= n_layers", (long long)h, layer[h]);
         if (!(r[h] > 0.f) || !std::isfinite(r[h])) return fail(HOUGH_EINVAL, "hit %lld: r must be finite and > 0", (long long)h);
         if (!(std::fabs(phi[h]) <= 1000.f)) return fail(HOUGH_EINVAL, "hit %lld: phi must be finite, |phi| <= 1000", (long long)h);
@@ -249,21 +269,27 @@ int check_host_hits_impl(const Axes &ax, const float *r, const float *phi, const
     return HOUGH_OK;
 }
 
+// host_check: check host hits on the host before anything runs (else the staging kernel applies
+// the same predicates on the device and drops a bad hit, reporting it in device_error).
 int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z, const uint8_t *layer,
-                 int64_t n, int where, cudaStream_t s)
+                 int64_t n, int where, cudaStream_t s, bool host_check = true)
 {
     if (n < 0) return fail(HOUGH_EINVAL, "n_hits must be >= 0");
     if (n > c->limits.max_hits) return fail(HOUGH_ECAPACITY, "n_hits %lld exceeds max_hits %lld", (long long)n, (long long)c->limits.max_hits);
     if (where != HOUGH_HOST && where != HOUGH_DEVICE) return fail(HOUGH_EINVAL, "where must be HOUGH_HOST or HOUGH_DEVICE");
     if (n > 0 && (!r || !phi || !z || !layer)) return fail(HOUGH_EINVAL, "hit arrays are required");
     if (where == HOUGH_HOST) {
-        int rc = check_host_hits_impl(c->ax, r, phi, z, layer, n);
-        if (rc) return rc;
+        // the copies into the context's own input buffers run while the host checks the hits; a
+        // bad hit returns before anything reads them
         if (n > 0) {
             CU(cudaMemcpyAsync(c->in_r, r, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy r");
             CU(cudaMemcpyAsync(c->in_phi, phi, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy phi");
             CU(cudaMemcpyAsync(c->in_z, z, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy z");
             CU(cudaMemcpyAsync(c->in_layer, layer, n, cudaMemcpyHostToDevice, s), "copy layer");
+        }
+        if (host_check) {
+            int rc = check_host_hits_impl(c->ax, r, phi, z, layer, n);
+            if (rc) return rc;
         }
         c->w.r = c->in_r; c->w.phi = c->in_phi; c->w.z = c->in_z; c->w.layer = c->in_layer;
     } else {
@@ -540,14 +566,52 @@ int hough_get_stats(hough_ctx *c, hough_stats *out, void *stream)
     return HOUGH_OK;
 }
 
+// With host memory the path has one round trip: the hits' per-hit checks run in the staging kernel
+// (the predicates of the host check; a rejected hit makes the call fail with HOUGH_EINVAL once it
+// has synchronised), and the candidates are packed into mapped pinned memory beside the counters'
+// copy, so one synchronisation delivers both.
 int hough_process(hough_ctx *c, const float *r, const float *phi, const float *z, const uint8_t *layer,
                   int64_t n_hits, hough_candidate *out, int32_t cap, int32_t *n_out, int where, void *stream)
 {
-    int rc = hough_vote(c, r, phi, z, layer, n_hits, where, stream);
+    if (where != HOUGH_HOST) {
+        int rc = hough_vote(c, r, phi, z, layer, n_hits, where, stream);
+        if (rc) return rc;
+        if ((rc = hough_peaks(c, stream))) return rc;
+        if ((rc = hough_stage2(c, stream))) return rc;
+        return hough_get_candidates(c, out, cap, n_out, where, stream);
+    }
+    if (!c || !n_out || cap < 0 || (cap > 0 && !out)) return fail(HOUGH_EINVAL, "bad arguments");
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->cands_mapped) {   // the first call allocates the staging, once
+        void *h = nullptr;
+        CU(cudaHostAlloc(&h, sizeof(hough_candidate) * std::max(c->w.max_cand, 1), cudaHostAllocMapped),
+           "cudaHostAlloc of the result staging");
+        c->cands_mapped = static_cast<hough_candidate *>(h);
+        void *d = nullptr;
+        CU(cudaHostGetDevicePointer(&d, h, 0), "cudaHostGetDevicePointer");
+        c->cands_mapped_dev = static_cast<hough_candidate *>(d);
+    }
+    int rc = enqueue_vote(c, r, phi, z, layer, n_hits, HOUGH_HOST, s, false);
     if (rc) return rc;
     if ((rc = hough_peaks(c, stream))) return rc;
     if ((rc = hough_stage2(c, stream))) return rc;
-    return hough_get_candidates(c, out, cap, n_out, where, stream);
+    CU(cudaMemcpyAsync(c->stats_host, c->w.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "copy stats");
+    CU(launch_pack_candidates(c->ax, c->w, c->cands_mapped_dev, s, std::min<long long>(cap, c->w.max_cand)),
+       "pack kernel");
+    g_launches += 1;
+    CU(cudaStreamSynchronize(s), "synchronise");
+    const DevStats &d = *c->stats_host;
+    if (d.device_error & (HOUGH_DEVERR_LAYER | HOUGH_DEVERR_RADIUS))
+        return fail(HOUGH_EINVAL, "a hit had layer >= n_layers, r <= 0, |phi| > 1000 or a non-finite coordinate");
+    const int64_t found = d.n_candidates;
+    const int64_t kept = std::min<int64_t>(found, c->w.max_cand);
+    const int64_t ncopy = std::min<int64_t>(kept, cap);
+    *n_out = (int32_t)std::min<int64_t>(found, INT32_MAX);
+    if (ncopy > 0) std::memcpy(out, c->cands_mapped, sizeof(hough_candidate) * ncopy);
+    if (found > cap) return fail(HOUGH_ETRUNC, "%lld candidates, capacity %d", (long long)found, cap);
+    if (found > kept) return fail(HOUGH_ETRUNC, "%lld candidates, max_candidates %d", (long long)found, c->w.max_cand);
+    return HOUGH_OK;
 }
 
 int hough_set_tiling(hough_ctx *c, const hough_tiling *t)

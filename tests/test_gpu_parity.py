@@ -245,3 +245,27 @@ def test_capacity_error(binding):
         with pytest.raises(binding.HoughError) as e:
             ctx.vote_event(ev)
         assert e.value.code == binding.ECAPACITY
+
+
+def test_process_from_host_memory(binding):
+    """hough_process on host hits (checked on the device, candidates through mapped memory): the
+    same candidates as the step-by-step calls, repeatable, a truncated copy on a small capacity,
+    and HOUGH_EINVAL for an event with a bad hit."""
+    w = eg.WORKLOADS["pileup_100k"]
+    ev = w.event(4)
+    ref = run_gpu(binding, w.geometry, w.binning, ev)["candidates"]
+    with binding.HoughContext(w.geometry, w.binning, max_hits=ev.n_hits, max_candidates=1 << 16) as ctx:
+        for _ in range(2):
+            got = ctx.process(ev.r, ev.phi, ev.z, ev.layer)
+            assert np.array_equal(got, ref)
+        out = np.zeros(len(ref), dtype=binding.CANDIDATE_DTYPE)
+        with pytest.raises(binding.HoughError) as e:
+            ctx.process(ev.r, ev.phi, ev.z, ev.layer, cap=10, out=out)
+        assert e.value.code == binding.ETRUNC
+        assert np.array_equal(out[:10], ref[:10])
+        bad = ev.subset(np.arange(ev.n_hits))
+        bad.z[777] = np.float32(np.inf)
+        with pytest.raises(binding.HoughError) as e:
+            ctx.process(bad.r, bad.phi, bad.z, bad.layer)
+        assert e.value.code == binding.EINVAL
+        assert np.array_equal(ctx.process(ev.r, ev.phi, ev.z, ev.layer), ref)
