@@ -16,6 +16,7 @@ hough_process from pinned host buffers: host->device copy of the hits, the path,
 device->host read of the candidate list, timed on the host around each call), `scatter_mode`
 (the paper's shared-atomic vote design in place of the gather vote), `count_accumulator` (cells
 holding vote counts, the paper's literal A[B[i]] += 1, on the pileup event and the paper's grid),
+`d0_axis` (non-prompt tracks on a (d0, q/pT, phi0) grid),
 `paper_sweep` (the paper's Fig. 2 experiment) and `cpu_baseline` (the FP64 oracle on this
 machine's host cores, on a bounded sample).
 
@@ -70,7 +71,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--only", choices=["all", "plain", "batched", "served", "paper_sweep", "counts"], default="all",
+    ap.add_argument("--only", choices=["all", "plain", "batched", "served", "paper_sweep", "counts", "d0"],
+                    default="all",
                     help="run one part only (for profiling); the default runs everything")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the batch with the default kernel configuration instead of the tuned one")
@@ -588,65 +590,80 @@ def count_workloads():
     ]
 
 
+def _plain_variant(env, args, w, text, smem_peak=None, hbm_peak=None):
+    """One configuration of the plain path, one event per step, device-resident hits, L2 flushed
+    before every step; then an attribution pass with an event after every kernel."""
+    torch, binding, stream = env.torch, env.binding, env.stream
+    ev = w.event(replicas.event_indices(env.rank, env.world, 1)[0])
+    tens = [torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
+    with binding.HoughContext(w.geometry, w.binning, max_hits=max(ev.n_hits, 1), max_candidates=1 << 18,
+                              max_members=1 << 23, device=env.local) as ctx:
+        def step():
+            ctx.vote(*tens, n_hits=ev.n_hits, where=binding.DEVICE, stream=stream)
+            ctx.peaks(stream=stream)
+            ctx.stage2(stream=stream)
+
+        def timed(k, attribute):
+            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+            lib_t = []
+            for q in range(k):
+                env.flush.zero_()
+                e0[q].record(stream)
+                step()
+                e1[q].record(stream)
+                if attribute:
+                    lib_t.append(ctx.timing())
+            torch.cuda.synchronize()
+            return [a.elapsed_time(b) for a, b in zip(e0, e1)], lib_t
+
+        ctx.enable_timing(False)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        st = ctx.stats()
+        env.barrier()
+        step_ms, _ = timed(args.steps, False)
+        total = env.max_over_ranks(sum(step_ms))
+        ctx.enable_timing(True)
+        step()
+        _, lib_t = timed(min(args.steps, 30), True)
+        ctx.enable_timing(False)
+        t = {k: statistics.mean(x[k] for x in lib_t) for k in lib_t[0]}
+        tiling = ctx.get_tiling()
+    cells = binding.grid_rows(w.binning) * w.binning.n_phi
+    vote_ms = t["vote_ms"]
+    p = {"workload": text, "hits": int(ev.n_hits), "cells": cells, "votes": int(st.votes),
+         "candidates": int(st.n_candidates), "members": int(st.n_members),
+         "events_per_s": replicas.job_rate(args.steps, env.world, total * 1e-3), "ms_per_event": total / args.steps,
+         "stage_ms": t["stage_ms"], "vote_ms": vote_ms, "gather_ms": t["gather_ms"], "scatter_ms": t["scatter_ms"],
+         "peaks_ms": t["peaks_ms"], "stage2_ms": t["stage2_ms"],
+         "votes_per_s_in_vote": st.votes / (vote_ms * 1e-3) if vote_ms > 0 else None,
+         "vote_mode": "gather" if tiling["vote_mode"] == binding.VOTE_GATHER else "scatter"}
+    if smem_peak and vote_ms > 0:
+        p["vote_vs_smem_atomic_peak"] = p["votes_per_s_in_vote"] / smem_peak
+    if hbm_peak and vote_ms > 0:
+        gbs = (13 * ev.n_hits + 2 * cells) / (vote_ms * 1e-3) / 1e9
+        p["vote_hbm"] = {"achieved_gbs": gbs, "frac": gbs / hbm_peak, "algorithmic": "13 B per hit in, 2 B per cell out"}
+    return p
+
+
 def measure_counts(env, args, smem_peak=None, hbm_peak=None):
     """The count accumulator (A[B[i]] += 1 of Sec. 8: a cell holds its number of votes, saturating
-    at 65535; the shared-memory scatter kernel votes, the peak search reads counts): the plain path,
-    one event per step, device-resident hits, L2 flushed before every step, then an attribution
-    pass with an event after every kernel."""
-    torch, binding, stream = env.torch, env.binding, env.stream
-    out = {}
-    for name, w, text in count_workloads():
-        ev = w.event(replicas.event_indices(env.rank, env.world, 1)[0])
-        tens = [torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
-        with binding.HoughContext(w.geometry, w.binning, max_hits=max(ev.n_hits, 1), max_candidates=1 << 18,
-                                  max_members=1 << 23, device=env.local) as ctx:
-            def step():
-                ctx.vote(*tens, n_hits=ev.n_hits, where=binding.DEVICE, stream=stream)
-                ctx.peaks(stream=stream)
-                ctx.stage2(stream=stream)
+    at 65535; the shared-memory scatter kernel votes, the peak search reads counts)."""
+    return {name: _plain_variant(env, args, w, text, smem_peak, hbm_peak) for name, w, text in count_workloads()}
 
-            def timed(k, attribute):
-                e0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
-                e1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
-                lib_t = []
-                for q in range(k):
-                    env.flush.zero_()
-                    e0[q].record(stream)
-                    step()
-                    e1[q].record(stream)
-                    if attribute:
-                        lib_t.append(ctx.timing())
-                torch.cuda.synchronize()
-                return [a.elapsed_time(b) for a, b in zip(e0, e1)], lib_t
 
-            ctx.enable_timing(False)
-            for _ in range(max(3, args.warmup)):
-                step()
-            torch.cuda.synchronize()
-            st = ctx.stats()
-            env.barrier()
-            step_ms, _ = timed(args.steps, False)
-            total = env.max_over_ranks(sum(step_ms))
-            ctx.enable_timing(True)
-            step()
-            _, lib_t = timed(min(args.steps, 30), True)
-            ctx.enable_timing(False)
-            t = {k: statistics.mean(x[k] for x in lib_t) for k in lib_t[0]}
-        cells = w.binning.n_qpt * w.binning.n_phi
-        vote_ms = t["scatter_ms"]
-        p = {"workload": text, "hits": int(ev.n_hits), "votes": int(st.votes), "candidates": int(st.n_candidates),
-             "members": int(st.n_members), "events_per_s": replicas.job_rate(args.steps, env.world, total * 1e-3),
-             "ms_per_event": total / args.steps, "stage_ms": t["stage_ms"], "vote_ms": vote_ms,
-             "peaks_ms": t["peaks_ms"], "stage2_ms": t["stage2_ms"],
-             "votes_per_s_in_vote_kernel": st.votes / (vote_ms * 1e-3) if vote_ms > 0 else None}
-        if smem_peak and vote_ms > 0:
-            p["vote_kernel_vs_smem_atomic_peak"] = p["votes_per_s_in_vote_kernel"] / smem_peak
-        if hbm_peak and vote_ms > 0:
-            gbs = (13 * ev.n_hits + 2 * cells) / (vote_ms * 1e-3) / 1e9
-            p["vote_kernel_hbm"] = {"achieved_gbs": gbs, "frac": gbs / hbm_peak,
-                                    "algorithmic": "13 B per hit in, 2 B per cell out"}
-        out[name] = p
-    return out
+def measure_d0(env, args, smem_peak=None, hbm_peak=None):
+    """Non-prompt tracks: the (d0, q/pT, phi0) grid of the displaced workload, with layer masks and
+    with counts."""
+    w = eg.WORKLOADS["displaced_d0"]
+    text = ("displaced tracks: 200 helices pT 2-100 GeV with d0 ~ U(-2, 2) cm (eta +-2.5, z0~N(0,5cm)) + 1000 "
+            "noise hits on 10 barrel layers r=4..110 cm, B=3.8 T; 16 d0 (+-2 cm) x 256 q/pT (+-1) x 2048 phi0 "
+            "uint16 {}, threshold >=8, 3x3x3 peaks, 64 cot x 64 z0 stage 2")
+    wc = eg.with_binning(w, accumulator=eg.ACC_COUNTS)
+    return {"layers": _plain_variant(env, args, w, text.format("layer masks"), smem_peak, hbm_peak),
+            "counts": _plain_variant(env, args, wc, text.format("vote counts"), smem_peak, hbm_peak)}
 
 
 def measure_e2e(env, args, ctx, ev):
@@ -679,9 +696,9 @@ def main():
         return
     env = Env()
     binding = env.binding
-    if args.only in ("batched", "served", "paper_sweep", "counts"):
+    if args.only in ("batched", "served", "paper_sweep", "counts", "d0"):
         out = {"batched": measure_batched, "served": measure_served, "paper_sweep": measure_paper_sweep,
-               "counts": measure_counts}[args.only](env, args)
+               "counts": measure_counts, "d0": measure_d0}[args.only](env, args)
         if env.rank == 0:
             print(json.dumps({"metric": METRIC, "part": args.only, **out}), flush=True)
         return
@@ -708,13 +725,14 @@ def main():
         peaks, peaks_kind = measured_peaks()
         hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
         if args.only == "plain":
-            batched = e2e = served = paper = counts = None
+            batched = e2e = served = paper = counts = d0 = None
         else:
             batched = measure_batched(env, args)
             e2e = measure_e2e(env, args, ctx, ev)
             served = measure_served(env, args)
             paper = measure_paper_sweep(env, args) if env.rank == 0 else None
             counts = measure_counts(env, args, smem_peak, hbm_peak)
+            d0 = measure_d0(env, args, smem_peak, hbm_peak)
     clocks = clock_sampler.summary()
     kernels = kernel_table(env, w, n, plain, smem_peak, hbm_peak, peaks_kind, clocks)
     dominant = max(kernels, key=lambda k: kernels[k]["ms"])
@@ -758,6 +776,7 @@ def main():
         "served": served,
         "paper_sweep": paper,
         "count_accumulator": counts,
+        "d0_axis": d0,
         "e2e": e2e,
         "gpu_launches": plain["launches"],
         "clocks": clocks,
