@@ -286,7 +286,8 @@ class HoughContext:
 
     # -- the path -----------------------------------------------------------------------------
     def vote(self, r, phi, z, layer, n_hits=None, where=HOST, stream=None):
-        if where == HOST:
+        """hough_vote.  Host hits as numpy arrays, or pinned buffers (with data_ptr()) and n_hits."""
+        if where == HOST and isinstance(r, np.ndarray):
             r, phi, z = (np.ascontiguousarray(a, dtype=np.float32) for a in (r, phi, z))
             layer = np.ascontiguousarray(layer, dtype=np.uint8)
             n_hits = r.shape[0]

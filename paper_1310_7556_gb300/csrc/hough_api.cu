@@ -67,6 +67,8 @@ struct hough_ctx {
     DevStats *stats_host = nullptr;      // pinned
     hough_candidate *cands_mapped = nullptr;       // pinned, mapped: hough_process's result staging
     hough_candidate *cands_mapped_dev = nullptr;   // its device address
+    DevStats *stats_mapped = nullptr;              // pinned, mapped: hough_process's counters
+    DevStats *stats_mapped_dev = nullptr;
     int64_t n_hits = 0;
     int stage = 0;                       // 0 nothing, 1 voted, 2 peaks, 3 stage 2
     bool timing = false;
@@ -82,6 +84,7 @@ struct hough_ctx {
         for (void *p : allocations) cudaFree(p);
         if (stats_host) cudaFreeHost(stats_host);
         if (cands_mapped) cudaFreeHost(cands_mapped);
+        if (stats_mapped) cudaFreeHost(stats_mapped);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -269,6 +272,20 @@ int check_host_hits_impl(const Axes &ax, const float *r, const float *phi, const
     return HOUGH_OK;
 }
 
+// The device address of pinned host memory (cudaHostAlloc, cudaHostRegister) under unified
+// addressing; false for other memory.
+bool device_view(const void *p, const void **dp)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // not a pointer the runtime knows: plain host memory
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dp = a.devicePointer;
+    return true;
+}
+
 // host_check: check host hits on the host before anything runs (else the staging kernel applies
 // the same predicates on the device and drops a bad hit, reporting it in device_error).
 int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z, const uint8_t *layer,
@@ -279,9 +296,13 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     if (where != HOUGH_HOST && where != HOUGH_DEVICE) return fail(HOUGH_EINVAL, "where must be HOUGH_HOST or HOUGH_DEVICE");
     if (n > 0 && (!r || !phi || !z || !layer)) return fail(HOUGH_EINVAL, "hit arrays are required");
     if (where == HOUGH_HOST) {
-        // the copies into the context's own input buffers run while the host checks the hits; a
-        // bad hit returns before anything reads them
-        if (n > 0) {
+        // pinned hits are read in place by the staging kernels, over the host link; other host
+        // memory is copied into the context's own input buffers, the copies running while the
+        // host checks the hits (a bad hit returns before anything reads them)
+        const void *dv[4] = {nullptr, nullptr, nullptr, nullptr};
+        const bool in_place = n > 0 && device_view(r, &dv[0]) && device_view(phi, &dv[1]) &&
+                              device_view(z, &dv[2]) && device_view(layer, &dv[3]);
+        if (n > 0 && !in_place) {
             CU(cudaMemcpyAsync(c->in_r, r, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy r");
             CU(cudaMemcpyAsync(c->in_phi, phi, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy phi");
             CU(cudaMemcpyAsync(c->in_z, z, sizeof(float) * n, cudaMemcpyHostToDevice, s), "copy z");
@@ -291,7 +312,14 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
             int rc = check_host_hits_impl(c->ax, r, phi, z, layer, n);
             if (rc) return rc;
         }
-        c->w.r = c->in_r; c->w.phi = c->in_phi; c->w.z = c->in_z; c->w.layer = c->in_layer;
+        if (in_place) {
+            c->w.r = static_cast<const float *>(dv[0]);
+            c->w.phi = static_cast<const float *>(dv[1]);
+            c->w.z = static_cast<const float *>(dv[2]);
+            c->w.layer = static_cast<const uint8_t *>(dv[3]);
+        } else {
+            c->w.r = c->in_r; c->w.phi = c->in_phi; c->w.z = c->in_z; c->w.layer = c->in_layer;
+        }
     } else {
         c->w.r = r; c->w.phi = phi; c->w.z = z; c->w.layer = layer;
     }
@@ -584,23 +612,28 @@ int hough_process(hough_ctx *c, const float *r, const float *phi, const float *z
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->cands_mapped) {   // the first call allocates the staging, once
-        void *h = nullptr;
+        void *h = nullptr, *d = nullptr;
         CU(cudaHostAlloc(&h, sizeof(hough_candidate) * std::max(c->w.max_cand, 1), cudaHostAllocMapped),
            "cudaHostAlloc of the result staging");
         c->cands_mapped = static_cast<hough_candidate *>(h);
-        void *d = nullptr;
         CU(cudaHostGetDevicePointer(&d, h, 0), "cudaHostGetDevicePointer");
         c->cands_mapped_dev = static_cast<hough_candidate *>(d);
+        CU(cudaHostAlloc(&h, sizeof(DevStats), cudaHostAllocMapped), "cudaHostAlloc of the counters");
+        c->stats_mapped = static_cast<DevStats *>(h);
+        CU(cudaHostGetDevicePointer(&d, h, 0), "cudaHostGetDevicePointer");
+        c->stats_mapped_dev = static_cast<DevStats *>(d);
     }
     int rc = enqueue_vote(c, r, phi, z, layer, n_hits, HOUGH_HOST, s, false);
     if (rc) return rc;
     if ((rc = hough_peaks(c, stream))) return rc;
     if ((rc = hough_stage2(c, stream))) return rc;
-    CU(cudaMemcpyAsync(c->stats_host, c->w.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "copy stats");
-    CU(launch_pack_candidates(c->ax, c->w, c->cands_mapped_dev, s, std::min<long long>(cap, c->w.max_cand)),
+    // one kernel writes both the candidates and the counters into mapped memory
+    CU(launch_pack_candidates(c->ax, c->w, c->cands_mapped_dev, s, std::min<long long>(cap, c->w.max_cand), nullptr,
+                              c->stats_mapped_dev, 152),
        "pack kernel");
     g_launches += 1;
     CU(cudaStreamSynchronize(s), "synchronise");
+    *c->stats_host = *c->stats_mapped;   // hough_get_stats and friends read the last event's copy
     const DevStats &d = *c->stats_host;
     if (d.device_error & (HOUGH_DEVERR_LAYER | HOUGH_DEVERR_RADIUS))
         return fail(HOUGH_EINVAL, "a hit had layer >= n_layers, r <= 0, |phi| > 1000 or a non-finite coordinate");

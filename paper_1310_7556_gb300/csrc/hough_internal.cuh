@@ -206,9 +206,11 @@ cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, 
 cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
 cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stream);
 // All events' candidates concatenated: the first `limit` into `out` (device-accessible), the rest
-// into `rest` at the same indices when it is given, else dropped.
+// into `rest` at the same indices when it is given, else dropped; the first event's counters to
+// `stats_out` (device-accessible) when it is given.
 cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream,
-                                   long long limit = 1LL << 62, hough_candidate *rest = nullptr);
+                                   long long limit = 1LL << 62, hough_candidate *rest = nullptr,
+                                   DevStats *stats_out = nullptr, int blocks = 1216);
 cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream,
                           cudaEvent_t between = nullptr);
 cudaError_t launch_member_index(const Workspace &w, int32_t *idx_out, int64_t total, cudaStream_t stream);

@@ -719,9 +719,17 @@ __global__ void __launch_bounds__(kCompactThreads) cand_scan_kernel(Workspace w)
 
 // All events' candidate lists, concatenated in event order into `out` (positions from cand_base).
 // (the first `limit` to `out`, the rest -- when `rest` is given -- to rest at the same index)
-__global__ void pack_candidates_kernel(Workspace w, hough_candidate *out, long long limit, hough_candidate *rest)
+// When `stats_out` is given, block 0 also copies the first event's counters there.
+__global__ void pack_candidates_kernel(Workspace w, hough_candidate *out, long long limit, hough_candidate *rest,
+                                       DevStats *stats_out)
 {
     pdl_enter();
+    static_assert(sizeof(DevStats) % 4 == 0, "the counters are copied as 32-bit words");
+    if (stats_out && blockIdx.x == 0) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(w.stats);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(stats_out);
+        for (int q = threadIdx.x; q < (int)(sizeof(DevStats) / 4); q += blockDim.x) dst[q] = src[q];
+    }
     const int total = w.cand_base[w.n_events];
     const int n = rest ? total : (int)min((long long)total, limit);
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n; f += gridDim.x * blockDim.x) {
@@ -883,10 +891,10 @@ cudaError_t launch_compact(const Axes &ax, const Workspace &w, cudaStream_t stre
 }
 
 cudaError_t launch_pack_candidates(const Axes &ax, const Workspace &w, hough_candidate *out, cudaStream_t stream,
-                                   long long limit, hough_candidate *rest)
+                                   long long limit, hough_candidate *rest, DevStats *stats_out, int blocks)
 {
     (void)ax;
-    return launch_chained(pack_candidates_kernel, dim3(1216), dim3(256), 0, stream, w, out, limit, rest);
+    return launch_chained(pack_candidates_kernel, dim3(blocks), dim3(256), 0, stream, w, out, limit, rest, stats_out);
 }
 
 cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)

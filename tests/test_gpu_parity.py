@@ -269,3 +269,30 @@ def test_process_from_host_memory(binding):
             ctx.process(bad.r, bad.phi, bad.z, bad.layer)
         assert e.value.code == binding.EINVAL
         assert np.array_equal(ctx.process(ev.r, ev.phi, ev.z, ev.layer), ref)
+
+
+def test_process_reads_pinned_hits_in_place(binding):
+    """Pinned host hits are read by the staging kernels in place (no copy); the result equals the
+    pageable-memory path (copied), also through hough_vote with its host check, and a bad pinned
+    hit is still rejected."""
+    torch = pytest.importorskip("torch")
+    w = eg.WORKLOADS["pileup_100k"]
+    ev = w.event(6)
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (ev.r, ev.phi, ev.z, ev.layer)]
+    with binding.HoughContext(w.geometry, w.binning, max_hits=ev.n_hits, max_candidates=1 << 16) as ctx:
+        ref = ctx.process(ev.r, ev.phi, ev.z, ev.layer).copy()
+        got = ctx.process(*pinned, n_hits=ev.n_hits)
+        assert np.array_equal(got, ref)
+        M_ref = ctx.accumulator()
+        ctx.vote(*pinned, n_hits=ev.n_hits, where=binding.HOST)
+        ctx.peaks()
+        ctx.stage2()
+        assert np.array_equal(ctx.accumulator(), M_ref)
+        assert np.array_equal(ctx.candidates(), ref)
+        pinned[0][123] = -1.0
+        with pytest.raises(binding.HoughError) as e:
+            ctx.process(*pinned, n_hits=ev.n_hits)
+        assert e.value.code == binding.EINVAL
+        with pytest.raises(binding.HoughError) as e:
+            ctx.vote(*pinned, n_hits=ev.n_hits, where=binding.HOST)
+        assert e.value.code == binding.EINVAL
