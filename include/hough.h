@@ -103,7 +103,10 @@ typedef struct hough_geometry {
  * holds d0 bin m and q/pT bin i; accumulators, candidate rows (iq) and
  * hough_get_accumulator all use stacked rows.  A cell is a candidate when it
  * is a local maximum of its 3 x 3 x 3 block (the 13 neighbours before it in
- * raster order -- slice, row, column -- strictly lower); band_rows must be 1.
+ * raster order -- slice, row, column -- strictly lower); its peak search works
+ * on bands of band_rows rows of one slice, which need 3 (band_rows + 2) n_phi
+ * bytes of shared memory (twice that with counts); 9 n_phi (18 n_phi) bytes
+ * must fit, else HOUGH_EINVAL.
  * n_d0 = 0: prompt tracks (d0 = 0), one slice, the d0 fields ignored.
  * Limits: 0 <= n_d0 and n_d0 * n_qpt <= 65535; d0_min_cm < d0_max_cm, finite.
  */
@@ -259,7 +262,7 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
  * tile_phi must divide n_phi and be a multiple of 64; tile_qpt in 1..256; threads in
  * {128, 256, 512, 1024}; tile_qpt * tile_phi * 2 bytes (4 with the count accumulator) must fit
  * in shared memory; band_rows in 1..16 with (band_rows + 2) * n_phi bytes (twice that with the
- * count accumulator) of shared memory; gather_rows in 1..32 (0: 4);
+ * count accumulator, three times with a d0 axis) of shared memory; gather_rows in 1..32 (0: 4);
  * gather_cols a multiple of 64 dividing n_phi (0: the largest such up to 512) with
  * n_layers * (gather_cols + 64) * 8 bytes of shared memory; gather_threads in {256, 512, 1024}
  * (0: 256).  HOUGH_EINVAL otherwise.  Every configuration gives the same results.

@@ -128,6 +128,9 @@ int check_binning(const hough_geometry *g, const hough_binning *b)
         return fail(HOUGH_EINVAL, "n_d0 must be >= 0 with n_d0 * n_qpt <= 65535");
     if (b->n_d0 > 0 && (!(b->d0_min_cm < b->d0_max_cm) || !std::isfinite(b->d0_min_cm) || !std::isfinite(b->d0_max_cm)))
         return fail(HOUGH_EINVAL, "the d0 axis needs finite d0_min_cm < d0_max_cm");
+    // the 3 x 3 x 3 peak search stages at least nine rows in shared memory (227 KB on this GPU family)
+    if (b->n_d0 > 0 && (size_t)9 * b->n_phi * (b->accumulator == HOUGH_ACC_COUNTS ? 2 : 1) + 1024 > 232448)
+        return fail(HOUGH_EINVAL, "n_phi too large for a d0 axis: nine rows of it must fit in shared memory");
     return HOUGH_OK;
 }
 
@@ -204,7 +207,6 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
         return fail(HOUGH_EINVAL, "gather_threads must be 0, 256, 512 or 1024");
     if (ax.counts && t->vote_mode != HOUGH_VOTE_SCATTER)
         return fail(HOUGH_EINVAL, "the count accumulator needs vote_mode HOUGH_VOTE_SCATTER");
-    if (ax.n_d0 && t->band_rows != 1) return fail(HOUGH_EINVAL, "a d0 axis needs band_rows 1");
     const Tiling tt = resolve_tiling_impl(ax, t);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -229,6 +231,13 @@ Tiling default_tiling_impl(const Axes &ax)
     t.threads = 256;
     t.vote_mode = ax.counts ? HOUGH_VOTE_SCATTER : HOUGH_VOTE_GATHER;
     t.band_rows = 1;
+    // with a d0 axis a band stages its rows in three slices: taller bands stage each row fewer times
+    if (ax.n_d0)
+        for (int r : {4, 2})
+            if (band_smem_bytes(ax, r) + 1024 <= 232448) {
+                t.band_rows = r;
+                break;
+            }
     t.gather_rows = 4;
     t.gather_cols = default_gather_cols(ax);
     t.gather_threads = 256;

@@ -180,7 +180,12 @@ __host__ __device__ inline int n_keys(const Axes &ax) { return ax.n_layers * ax.
 constexpr int kProfPad = 16;
 __host__ __device__ inline int prof_stride(const Axes &ax) { return ax.n_phi + kProfPad; }
 __host__ __device__ inline int64_t prof_event_entries(const Axes &ax) { return (int64_t)HOUGH_MAX_LAYERS * prof_stride(ax); }
-__host__ __device__ inline int n_bands(const Axes &ax, int band_rows) { return (ax.n_qpt + band_rows - 1) / band_rows; }
+// Bands of band_rows rows; with a d0 axis a band never crosses a slice (each slice is cut alone).
+__host__ __device__ inline int n_bands(const Axes &ax, int band_rows)
+{
+    if (ax.n_d0) return ax.n_d0 * ((ax.q_rows + band_rows - 1) / band_rows);
+    return (ax.n_qpt + band_rows - 1) / band_rows;
+}
 // Candidates are never 8-neighbours, so a band holds at most one per 2 x 2 block.
 __host__ __device__ inline int band_capacity(const Axes &ax, int band_rows)
 {
@@ -496,9 +501,10 @@ __device__ __forceinline__ int wrap_col(int j, int n)
 // 8 consecutive cells per pass, so thread order is raster order and one block-wide scan of the
 // per-thread counts places every candidate.  Candidates go to `out` (cell index i * Nphi + j,
 // mask read from M) in raster order; returns their number.  Called by all TPB threads.
-// D3 (a grid with a d0 axis): one row (nrows = 1) whose 3 x 3 x 3 blocks are held as nine rows,
-// (slice m + dm, row i + di) at index 3 (dm + 1) + di + 1; the nine of slice m - 1 precede the
-// cell in raster order (strictly lower), the nine of slice m + 1 follow it (not higher).
+// D3 (a grid with a d0 axis): the band's 3 x 3 x 3 blocks are held as three slices of nrows + 2
+// rows each -- slice m - 1, the band's own, slice m + 1 -- the band's rows in the middle one; the
+// nine neighbours of slice m - 1 precede a cell in raster order (strictly lower), the nine of
+// slice m + 1 follow it (not higher).
 template <int TPB, typename V, bool D3 = false>
 __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, int nphi, int threshold,
                                                 const uint16_t *M, uint2 *out, int cap)
@@ -516,7 +522,8 @@ __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, 
         if (it < items) {
             rr = it / eighth;
             j0 = (it - rr * eighth) * 8;
-            const V *row = pc + (D3 ? 4 : rr + 1) * nphi;
+            const int S = nrows + 2;   // rows of one staged slice (D3)
+            const V *row = pc + (D3 ? S + rr + 1 : rr + 1) * nphi;
             const V *up = row - nphi, *dn = row + nphi;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -529,7 +536,7 @@ __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, 
                     if (D3) {
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            const V *a = pc + q * nphi, *b = pc + (6 + q) * nphi;
+                            const V *a = pc + (rr + q) * nphi, *b = pc + (2 * S + rr + q) * nphi;
                             peak = peak && a[jm] < p && a[j] < p && a[jp] < p && b[jm] <= p && b[j] <= p &&
                                    b[jp] <= p;
                         }

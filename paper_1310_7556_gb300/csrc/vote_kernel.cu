@@ -532,24 +532,30 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
     if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
 }
 
-// Peak search of one stacked row (slice m, q/pT row i) of a grid with a d0 axis: the nine rows
-// (m + dm, i + di) of its cells' 3 x 3 x 3 blocks are staged as cell values -- layer counts as
-// bytes, or 16-bit counts -- rows outside the slice and slices outside the grid as empty.  The
-// row's candidates go to its band list (band height 1), so the lists concatenate in raster order.
+// Peak search of one band of band_rows q/pT rows of one d0 slice m of a grid with a d0 axis: the
+// rows of its cells' 3 x 3 x 3 blocks -- rows i0 - 1 .. i0 + nrows of slices m - 1, m, m + 1 --
+// are staged as cell values (layer counts as bytes, or 16-bit counts), rows outside the slice and
+// slices outside the grid as empty.  Bands never cross a slice, so the band lists concatenate in
+// raster order.
 template <bool COUNTS>
 __global__ void __launch_bounds__(kPeakThreads) peaks3_kernel(Axes ax, Workspace w)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char pc[];
-    const int nb = ax.n_qpt;
-    const int e = blockIdx.x / nb, row = blockIdx.x - e * nb;
-    const int nphi = ax.n_phi, Q = ax.q_rows;
-    const int m = row / Q, i = row - m * Q;
+    const int R = w.band_rows, Q = ax.q_rows;
+    const int bps = (Q + R - 1) / R;   // bands per slice
+    const int nb = n_bands(ax, R);
+    const int e = blockIdx.x / nb, band = blockIdx.x - e * nb;
+    const int m = band / bps, i0 = (band - m * bps) * R;
+    const int nrows = min(R, Q - i0);
+    const int S = nrows + 2;
+    const int nphi = ax.n_phi;
     const uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
     const int v8 = nphi >> 3;
-    for (int q = threadIdx.x; q < 9 * v8; q += kPeakThreads) {
+    for (int q = threadIdx.x; q < 3 * S * v8; q += kPeakThreads) {
         const int sidx = q / v8, c8 = q - sidx * v8;
-        const int mm = m + sidx / 3 - 1, ii = i + sidx % 3 - 1;
+        const int slice = sidx / S;
+        const int mm = m + slice - 1, ii = i0 - 1 + (sidx - slice * S);
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (mm >= 0 && mm < ax.n_d0 && ii >= 0 && ii < Q)
             v = *reinterpret_cast<const uint4 *>(M + (int64_t)(mm * Q + ii) * nphi + c8 * 8);
@@ -567,14 +573,16 @@ __global__ void __launch_bounds__(kPeakThreads) peaks3_kernel(Axes ax, Workspace
         }
     }
     __syncthreads();
-    uint2 *out = w.band_cands + ((int64_t)e * nb + row) * w.band_cap;
+    uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
+    const int row0 = m * Q + i0;   // stacked row of the band's first row
     int cnt;
     if (COUNTS)
-        cnt = band_peak_search<kPeakThreads, uint16_t, true>(reinterpret_cast<const uint16_t *>(pc), 1, row, nphi,
+        cnt = band_peak_search<kPeakThreads, uint16_t, true>(reinterpret_cast<const uint16_t *>(pc), nrows, row0, nphi,
                                                              ax.threshold, M, out, w.band_cap);
     else
-        cnt = band_peak_search<kPeakThreads, unsigned char, true>(pc, 1, row, nphi, ax.threshold, M, out, w.band_cap);
-    if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + row] = cnt;
+        cnt = band_peak_search<kPeakThreads, unsigned char, true>(pc, nrows, row0, nphi, ax.threshold, M, out,
+                                                                  w.band_cap);
+    if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
 }
 
 // One CTA per event: exclusive scan of the band counts, then the band lists concatenated into
@@ -859,7 +867,8 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
 
 size_t band_smem_bytes(const Axes &ax, int band_rows)
 {
-    const size_t rows = ax.n_d0 ? 9 : (size_t)(band_rows + 2);   // with a d0 axis: one row's 3 x 3 x 3 blocks
+    // with a d0 axis the band's rows and their halo in three slices
+    const size_t rows = (size_t)(band_rows + 2) * (ax.n_d0 ? 3 : 1);
     return rows * ax.n_phi * (ax.counts ? 2 : 1);
 }
 

@@ -82,9 +82,11 @@ def test_centred_slice_equals_the_prompt_grid(binding):
 @pytest.mark.parametrize("tiling", [dict(vote_mode=1), dict(vote_mode=1, tile_qpt=7, tile_phi=128, threads=512),
                                     dict(vote_mode=1, tile_qpt=32, tile_phi=2048, threads=1024),
                                     dict(gather_rows=16, gather_cols=256, gather_threads=512),
-                                    dict(gather_rows=3, gather_cols=1024, gather_threads=1024)])
+                                    dict(gather_rows=3, gather_cols=1024, gather_threads=1024),
+                                    dict(band_rows=1), dict(band_rows=3), dict(band_rows=7), dict(band_rows=16)])
 def test_d0_configurations_agree_bit_for_bit(binding, tiling):
-    """Gather and scatter votes, tiles straddling d0 slices (ragged by 7 and 3 rows), one result."""
+    """Gather and scatter votes, tiles straddling d0 slices (ragged by 7 and 3 rows), and peak bands
+    of 1 to 16 rows (ragged at each slice's end by 3 and 7), one result."""
     w = eg.WORKLOADS["displaced_d0"]
     ev = w.event(1)
     base = run_gpu(binding, w.geometry, w.binning, ev)
@@ -93,12 +95,12 @@ def test_d0_configurations_agree_bit_for_bit(binding, tiling):
     assert np.array_equal(base["candidates"], other["candidates"])
 
 
-def test_d0_needs_band_height_one(binding):
-    w = _small_d0()
-    with binding.HoughContext(w.geometry, w.binning, max_hits=16) as ctx:
-        with pytest.raises(binding.HoughError) as e:
-            ctx.set_tiling(band_rows=2)
-        assert e.value.code == binding.EINVAL
+def test_d0_grid_too_wide_is_refused(binding):
+    """Nine rows of 32768 counts do not fit in shared memory: the axes are refused at creation."""
+    w = eg.with_binning(_small_d0(), n_phi=32768, accumulator=eg.ACC_COUNTS)
+    with pytest.raises(binding.HoughError) as e:
+        binding.HoughContext(w.geometry, w.binning, max_hits=16)
+    assert e.value.code == binding.EINVAL
 
 
 def test_d0_batch_equals_events_alone(binding):
