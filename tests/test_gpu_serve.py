@@ -203,3 +203,38 @@ def test_replay_offers_every_arrival_and_polls_every_admitted_event(binding):
             assert int(res["votes"][i]) == votes[i % len(pool)]
         st = srv.stats()
         assert st.admitted == admitted.sum() and st.completed == admitted.sum() and st.pending_tickets == 0
+
+
+@pytest.mark.parametrize("variant", ["counts", "d0"])
+def test_served_variants_equal_alone(binding, variant):
+    """The count accumulator and the d0 axis through the server: each event as alone."""
+    if variant == "counts":
+        w = eg.with_binning(W, accumulator=eg.ACC_COUNTS, threshold=12)
+        events = _events(10)
+    else:
+        w = eg.WORKLOADS["displaced_d0"]
+        events = [w.event(i) for i in range(8)]
+    expect = []
+    for ev in events:
+        with binding.HoughContext(w.geometry, w.binning, max_hits=max(ev.n_hits, 1), max_candidates=1 << 17,
+                                  max_members=1 << 21) as ctx:
+            expect.append(ctx.process(ev.r, ev.phi, ev.z, ev.layer, ev.n_hits).copy())
+    with binding.HoughServer(w.geometry, w.binning, max_batch_events=4, max_batch_hits=4 * 12_000, lanes=2,
+                             max_candidates=1 << 17, max_members=1 << 21) as srv:
+        srv.inject(binding.SERVE_FAULT_HOLD, True)
+        tickets = [srv.submit_event(ev) for ev in events[:4]]
+        srv.inject(binding.SERVE_FAULT_HOLD, False)
+        for ev in events[4:]:
+            t = None
+            while t is None:
+                t = srv.submit_event(ev)
+                if t is None:
+                    time.sleep(0.0005)
+            tickets.append(t)
+        sizes = []
+        for i, t in enumerate(tickets):
+            cands, res = srv.poll(t, timeout_us=30_000_000)
+            assert res.status == binding.OK
+            assert np.array_equal(cands, expect[i]), f"event {i}"
+            sizes.append(res.batch_events)
+        assert max(sizes) > 1
