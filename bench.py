@@ -310,8 +310,7 @@ def measure_plain(env, args, ctx, tens, n):
 PLAIN_KERNELS = [
     ("clear_kernel", "clear_ms", "stage_kernels.cu"),
     ("stage_count_kernel", "count_ms", "stage_kernels.cu"),
-    ("layer_table_kernel", "table_ms", "stage_kernels.cu"),
-    ("scan_keys_kernel", "scan_ms", "stage_kernels.cu"),
+    ("table_scan_kernel", "table_ms", "stage_kernels.cu"),
     ("scatter_kernel (hit sort)", "sort_ms", "stage_kernels.cu"),
     ("gather_kernel", "gather_ms", "vote_kernel.cu"),
     ("scatter_kernel (vote of per-vote layers)", "scatter_ms", "vote_kernel.cu"),
@@ -335,8 +334,7 @@ def kernel_work(name, w, n_hits, plain):
     model = {
         "clear_kernel": ("hbm", 4 * nkeys + 8 * 16 * (b.n_phi + 16) + 304),
         "stage_count_kernel": ("hbm", 37 * n_hits),          # r, phi, z, layer in; key, rank, 16-B record out
-        "layer_table_kernel": ("hbm", 32 * 16),              # layer records (rows only when a radius changes)
-        "scan_keys_kernel": ("hbm", 8 * nkeys),              # bucket counts in, offsets out
+        "table_scan_kernel": ("hbm", 8 * nkeys + 32 * 16),   # bucket counts in, offsets out; layer records
         "scatter_kernel (hit sort)": ("hbm", 68 * n_hits),   # key, rank, record, r, phi, z, offset in; 2 x 16 B out
         "gather_kernel": ("hbm", 13 * n_hits + 2 * cells),   # the vote: hits in, one 16-bit mask per cell out
         "scatter_kernel (vote of per-vote layers)": ("hbm", 13 * n_hits * general),
@@ -759,7 +757,7 @@ def main():
         "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": n, "votes_per_event": votes,
                    "candidates_per_event": plain["candidates"], "members_per_event": plain["members"],
                    "stage2_votes_per_event": plain["stage2_votes"],
-                   "mode": "plain: one event per step, hough_vote + hough_peaks + hough_stage2 (11 kernel launches)",
+                   "mode": "plain: one event per step, hough_vote + hough_peaks + hough_stage2 (10 kernel launches)",
                    "l2": "flushed before every timed step (256 MiB write)", "tiling": ctx.get_tiling(),
                    "tiling_from": "autotuner (one-event batch, 10 replays per configuration)" if plain_tune else "default"},
         "votes_per_s": votes * plain["events_per_s"],

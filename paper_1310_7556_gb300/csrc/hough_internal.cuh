@@ -257,7 +257,7 @@ int set_last_error(int code, const char *msg);
 void note_launches(uint64_t n);
 
 // Kernels launched by each enqueue function (for hough_kernel_launches).
-constexpr int kStageLaunches = 5;
+constexpr int kStageLaunches = 4;
 constexpr int kVoteLaunches = 2;
 // peak search, compaction, and for batches of several events the candidate-base scan
 inline int peak_launches(int n_events) { return n_events == 1 ? 2 : 3; }

@@ -24,7 +24,6 @@ namespace {
 
 constexpr int kStageThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr int kTableThreads = 256;
 constexpr int kClearThreads = 256;
 
 // The per-call state the staging starts from, cleared by one kernel instead of one memset each:
@@ -144,12 +143,10 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
 // track (y = x for prompt tracks, the d0 relation on a grid with a d0 axis), the arc length from
 // the closest approach for stage 2, and the stage-2 terms derived from it.  Rows on which the
 // radius casts no vote get the entry kNoVote.
-__global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Workspace w)
+__device__ __forceinline__ void layer_table(const Axes &ax, const Workspace &w, const int l)
 {
-    pdl_enter();
     __shared__ LayerInfo s_li;
     __shared__ int s_dirty;
-    const int l = blockIdx.x;
     if (threadIdx.x == 0) {
         LayerInfo li;
         const unsigned rmin = w.radii->rmin[l], rmax = w.radii->rmax[l];
@@ -239,19 +236,16 @@ __global__ void __launch_bounds__(kTableThreads) layer_table_kernel(Axes ax, Wor
 // are loaded and the offsets stored coalesced through a shared tile; in between each thread scans
 // kScanPerThread consecutive entries in registers and the CTA scans the threads' totals (one
 // shuffle scan per warp, one over the warps).  The tile has one padding word per 32, which keeps
-// the per-thread reads of consecutive words free of bank conflicts.  Then the vote count of
-// uniform layers.
+// the per-thread reads of consecutive words free of bank conflicts.
 constexpr int kScanPerThread = 8;
 constexpr int kScanRound = kScanThreads * kScanPerThread;
 
 __device__ __forceinline__ int scan_pad(int k) { return k + (k >> 5); }
 
-__global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Workspace w)
+__device__ __forceinline__ void scan_keys(const Axes &ax, const Workspace &w, const int e)
 {
-    pdl_enter();
     __shared__ int s_tile[kScanRound + kScanRound / 32];
     __shared__ int s_warp[kScanThreads / 32];
-    const int e = blockIdx.x;
     const int nkeys = n_keys(ax);
     const int32_t *counts = w.counts + (int64_t)e * nkeys;
     int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
@@ -311,15 +305,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_keys_kernel(Axes ax, Worksp
         offs[nkeys] = carry;
         w.stats[e].n_hits = (unsigned long long)carry;
     }
-    __syncthreads();   // the offsets written by other threads are visible after the barrier
-    if (threadIdx.x < ax.n_layers) {
-        const int l = threadIdx.x;
-        const LayerInfo li = w.info[l];
-        if (li.present && li.uniform && li.nvote > 0) {
-            const long long n_l = offs[(l + 1) * ax.n_phi] - offs[l * ax.n_phi];
-            w.stats[e].votes_by_layer[l] += (unsigned long long)(n_l * li.nvote);
-        }
-    }
+}
+
+// The layer tables and the bucket scans in one launch, as they do not depend on each other:
+// blocks [0, n_events) scan one event's bucket counts each, the next HOUGH_MAX_LAYERS blocks
+// compute one layer's table each.
+__global__ void __launch_bounds__(kScanThreads) table_scan_kernel(Axes ax, Workspace w)
+{
+    pdl_enter();
+    if ((int)blockIdx.x < w.n_events) scan_keys(ax, w, blockIdx.x);
+    else layer_table(ax, w, blockIdx.x - w.n_events);
 }
 
 // Scatter every valid hit to its sorted position, completing its hot record with its voting rows.
@@ -327,6 +322,17 @@ __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspa
 {
     pdl_enter();
     const int nkeys = n_keys(ax);
+    // the votes of layers of one radius: the layer's hits times its voting rows, per event
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)w.n_events * ax.n_layers;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(t / ax.n_layers), l = (int)(t - (int64_t)e * ax.n_layers);
+        const LayerInfo li = w.info[l];
+        if (li.present && li.uniform && li.nvote > 0) {
+            const int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
+            const long long n_l = offs[(l + 1) * ax.n_phi] - offs[l * ax.n_phi];
+            if (n_l) atomicAdd(&w.stats[e].votes_by_layer[l], (unsigned long long)(n_l * li.nvote));
+        }
+    }
     const int64_t total = hit_total(w);
     const HitInputs in = hit_inputs(w);
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total;
@@ -407,10 +413,10 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
     const int g = grid_for(w.n_hits_total >= 0 ? w.n_hits_total : w.hit_capacity, kStageThreads);
     if ((err = launch_chained(stage_count_kernel, dim3(g), dim3(kStageThreads), 0, stream, ax, w))) return err;
     if ((err = mark(1))) return err;
-    if ((err = launch_chained(layer_table_kernel, dim3(HOUGH_MAX_LAYERS), dim3(kTableThreads), 0, stream, ax, w)))
+    if ((err = launch_chained(table_scan_kernel, dim3(w.n_events + HOUGH_MAX_LAYERS), dim3(kScanThreads), 0, stream, ax,
+                              w)))
         return err;
-    if ((err = mark(2))) return err;
-    if ((err = launch_chained(scan_keys_kernel, dim3(w.n_events), dim3(kScanThreads), 0, stream, ax, w))) return err;
+    if ((err = mark(2))) return err;   // table_ms covers both; scan_ms stays empty
     if ((err = mark(3))) return err;
     return launch_chained(scatter_kernel, dim3(g), dim3(kStageThreads), 0, stream, ax, w);
 }
