@@ -600,8 +600,17 @@ def _plain_variant(env, args, w, text, smem_peak=None, hbm_peak=None):
     torch, binding, stream = env.torch, env.binding, env.stream
     ev = w.event(replicas.event_indices(env.rank, env.world, 1)[0])
     tens = [torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
+    tune = None
+    if args.autotune:
+        # the kernel configuration from the autotuner, timed on a one-event batch of this event
+        with binding.HoughBatch(w.geometry, w.binning, max_events=1, max_hits=max(ev.n_hits, 1),
+                                max_candidates=1 << 18, max_members=1 << 23, device=env.local) as tb:
+            tune = tb.autotune(*tens, np.array([0, ev.n_hits], dtype=np.int64), where=binding.DEVICE, reps=5)
     with binding.HoughContext(w.geometry, w.binning, max_hits=max(ev.n_hits, 1), max_candidates=1 << 18,
                               max_members=1 << 23, device=env.local) as ctx:
+        if tune is not None:
+            ctx.set_tiling(**{f: getattr(tune.tiling, f) for f in binding.TILING_FIELDS})
+
         def step():
             ctx.vote(*tens, n_hits=ev.n_hits, where=binding.DEVICE, stream=stream)
             ctx.peaks(stream=stream)
@@ -643,7 +652,8 @@ def _plain_variant(env, args, w, text, smem_peak=None, hbm_peak=None):
          "stage_ms": t["stage_ms"], "vote_ms": vote_ms, "gather_ms": t["gather_ms"], "scatter_ms": t["scatter_ms"],
          "peaks_ms": t["peaks_ms"], "stage2_ms": t["stage2_ms"],
          "votes_per_s_in_vote": st.votes / (vote_ms * 1e-3) if vote_ms > 0 else None,
-         "vote_mode": "gather" if tiling["vote_mode"] == binding.VOTE_GATHER else "scatter"}
+         "vote_mode": "gather" if tiling["vote_mode"] == binding.VOTE_GATHER else "scatter",
+         "tiling": tiling, "tiling_from": "autotuner (one-event batch)" if tune is not None else "default"}
     if smem_peak and vote_ms > 0:
         p["vote_vs_smem_atomic_peak"] = p["votes_per_s_in_vote"] / smem_peak
     if hbm_peak and vote_ms > 0:

@@ -4,8 +4,8 @@
 // The sweep times whole batches -- every kernel of the path, as the captured graph runs them --
 // for each configuration of the stage-1 vote and the peak search:
 //   gather vote: rows x columns of the accumulator tile per CTA, threads per CTA;
-//   scatter vote (the paper's shared-atomic design): q/pT rows x phi0 columns of the shared tile,
-//   threads per CTA (each thread handles one hit at a time);
+//   scatter vote (the paper's shared-atomic design, and the count accumulator's): q/pT rows x phi0
+//   columns of the shared tile, threads per CTA (each thread handles one hit at a time);
 //   peak search: rows per band.
 // It proceeds coordinate-wise (the vote configuration with the default band height, then the band
 // height with the best vote configuration), times `reps` replays of each after one untimed replay
@@ -188,8 +188,8 @@ int hough_batch_autotune(hough_batch *b, const hough_geometry *geometry, const h
                 if (rows * cols / 8 < threads / 2) continue;   // under half the threads would have cells
                 votes.push_back(t);
             }
-    for (int tq : {64, 128, 256})
-        for (int tp : {256, 512})
+    for (int tq : {8, 16, 32, 64, 128, 256})
+        for (int tp : {128, 256, 512})
             for (int threads : {256, 512, 1024}) {
                 hough_tiling t = best;
                 t.vote_mode = HOUGH_VOTE_SCATTER;
