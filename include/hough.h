@@ -88,8 +88,9 @@ typedef struct hough_geometry {
  * 1 <= threshold <= 16 (layer accumulator) or <= 65535 (count accumulator);
  * 1 <= n_cot, n_z0 <= 256 and n_cot * n_z0 <= 16384;
  * qpt_min < qpt_max, cot_min < cot_max, z0_min_cm < z0_max_cm.
- * The count accumulator votes with the shared-memory scatter kernel
- * (HOUGH_VOTE_SCATTER): the gather decides whether a layer voted, not how often.
+ * With the count accumulator HOUGH_VOTE_GATHER counts per cell the hits of the
+ * two buckets its votes come from, and HOUGH_VOTE_SCATTER is the shared-memory
+ * atomic scatter; both give the same counts.
  *
  * Non-prompt tracks (n_d0 > 0): a third axis of n_d0 bins of the signed
  * transverse impact parameter d0 over [d0_min_cm, d0_max_cm).  A track whose
@@ -256,8 +257,10 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
  * CTA owning a tile of tile_qpt rows x tile_phi columns in shared memory.
  * The peak search works on bands of band_rows rows.
  *
- * With the count accumulator the vote takes the scatter kernel, whose tile holds 32-bit counters
- * that are saturated to 16 bits when the tile is written out; HOUGH_VOTE_GATHER is refused.
+ * With the count accumulator the gather counts its tile of gather_rows x gather_cols cells in
+ * 32-bit shared counters (gather_rows * gather_cols * 4 bytes plus a staging slot of at least
+ * 16 KB must fit in shared memory) and the scatter's tile holds 32-bit counters; both saturate
+ * to 16 bits when the tile is written out.
  *
  * tile_phi must divide n_phi and be a multiple of 64; tile_qpt in 1..256; threads in
  * {128, 256, 512, 1024}; tile_qpt * tile_phi * 2 bytes (4 with the count accumulator) must fit

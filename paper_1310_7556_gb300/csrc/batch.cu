@@ -125,7 +125,7 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     A(b->alloc(&b->inputs_dev, 1));
     A(b->alloc(&b->in_r, H)); A(b->alloc(&b->in_phi, H)); A(b->alloc(&b->in_z, H)); A(b->alloc(&b->in_layer, H));
     A(b->alloc(&w.key, H)); A(b->alloc(&w.rank, H)); A(b->alloc(&w.hot_tmp, H));
-    A(b->alloc(&w.hot, H)); A(b->alloc(&w.cold, H));
+    A(b->alloc(&w.hot, H)); A(b->alloc(&w.cold, H)); A(b->alloc(&w.fsort, H));
     A(b->alloc(&w.counts, E * nkeys)); A(b->alloc(&w.offs, E * (nkeys + 1)));
     A(b->alloc(&w.prof, (size_t)(E * prof_event_entries(ax))));
     A(b->alloc(&w.radii, 1)); A(b->alloc(&w.info, HOUGH_MAX_LAYERS)); A(b->alloc(&w.memo, 1));

@@ -205,8 +205,6 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
         return fail(HOUGH_EINVAL, "gather_cols must be 0 or a multiple of 64 dividing n_phi");
     if (t->gather_threads && t->gather_threads != 256 && t->gather_threads != 512 && t->gather_threads != 1024)
         return fail(HOUGH_EINVAL, "gather_threads must be 0, 256, 512 or 1024");
-    if (ax.counts && t->vote_mode != HOUGH_VOTE_SCATTER)
-        return fail(HOUGH_EINVAL, "the count accumulator needs vote_mode HOUGH_VOTE_SCATTER");
     const Tiling tt = resolve_tiling_impl(ax, t);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -216,6 +214,11 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
     if (band_smem_bytes(ax, t->band_rows) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "band of %d rows needs %zu bytes of shared memory, the device allows %d",
                     t->band_rows, band_smem_bytes(ax, t->band_rows), max_smem);
+    if (ax.counts && t->vote_mode == HOUGH_VOTE_GATHER) {
+        if (gather_count_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
+            return fail(HOUGH_EINVAL, "count gather tile needs %zu bytes of shared memory, the device allows %d",
+                        gather_count_smem_bytes(ax, tt), max_smem);
+    }
     if (gather_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "gather tile needs %zu bytes of shared memory, the device allows %d",
                     gather_smem_bytes(ax, tt), max_smem);
@@ -229,7 +232,7 @@ Tiling default_tiling_impl(const Axes &ax)
     while (ax.n_phi % t.tile_phi) t.tile_phi -= 64;
     t.tile_qpt = std::min(ax.n_qpt, 16);
     t.threads = 256;
-    t.vote_mode = ax.counts ? HOUGH_VOTE_SCATTER : HOUGH_VOTE_GATHER;
+    t.vote_mode = HOUGH_VOTE_GATHER;
     t.band_rows = 1;
     // with a d0 axis a band stages its rows in three slices: taller bands stage each row fewer times
     if (ax.n_d0)
@@ -437,7 +440,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&c->in_r, n)); A(c->alloc(&c->in_phi, n)); A(c->alloc(&c->in_z, n)); A(c->alloc(&c->in_layer, n));
     A(c->alloc(&w.key, n)); A(c->alloc(&w.rank, n)); A(c->alloc(&w.hot_tmp, n));
     A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1)); A(c->alloc(&w.prof, (size_t)prof_event_entries(ax)));
-    A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n));
+    A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n)); A(c->alloc(&w.fsort, n));
     A(c->alloc(&w.radii, 1)); A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
     A(c->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(c->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
     A(c->alloc(&w.zco, (size_t)ax.n_layers * ax.n_qpt));

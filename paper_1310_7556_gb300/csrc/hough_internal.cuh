@@ -137,6 +137,7 @@ struct Workspace {
     int32_t *offs;                // n_events * (nkeys + 1)
     uint2 *prof;                  // n_events * prof_event_entries
     HotHit *hot;                  // per hit, sorted within each event's range
+    float *fsort;                 // per hit, sorted: the hot record's f alone (count gather; may be null)
     ColdHit *cold;
     LayerRadii *radii;            // batch-wide
     LayerInfo *info;              // HOUGH_MAX_LAYERS
@@ -234,6 +235,8 @@ Tiling default_tiling_for(const Axes &ax);
 Tiling resolve_tiling(const Axes &ax, const hough_tiling *t);   // gather defaults filled in
 void public_tiling(const Tiling &t, hough_tiling *out);
 size_t gather_smem_bytes(const Axes &ax, const Tiling &t);
+// Shared memory of the count accumulator's gather kernel.
+size_t gather_count_smem_bytes(const Axes &ax, const Tiling &t);
 size_t band_list_entries(const Axes &ax);
 int check_host_hits_for(const Axes &ax, const float *r, const float *phi, const float *z, const uint8_t *layer,
                         int64_t n);

@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspa
         const int64_t start = w.hit_start[e];
         const int64_t pos = start + w.offs[(int64_t)e * (nkeys + 1) + k] + w.rank[h];
         HotHit hh = w.hot_tmp[h];
+        if (w.fsort) w.fsort[pos] = hh.f;
         const int l = (hh.jl >> 16) & 0xF;
         const LayerInfo li = w.info[l];
         int lo = li.lo, hi = li.hi;

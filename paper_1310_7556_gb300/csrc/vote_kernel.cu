@@ -64,7 +64,6 @@ __device__ __forceinline__ void layer_masks(const Workspace &w, int L, unsigned 
 template <int TPB, bool GENERAL_ONLY, bool COUNTS>
 __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 {
-    static_assert(!(GENERAL_ONLY && COUNTS), "the count accumulator votes every layer here");
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_start[kMaxRanges];
@@ -294,8 +293,14 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
         const int rr = q / v8, c8 = q - rr * v8;
         uint4 *dst = reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + J0 + c8 * 8);
         if (COUNTS) {
-            // 8 counters, saturated to 16 bits and packed two a word
-            const uint4 a = tile4[2 * (rr * v8 + c8)], b = tile4[2 * (rr * v8 + c8) + 1];
+            // 8 counters, saturated to 16 bits and packed two a word (added to the gathered
+            // layers' counts when only the layers of several radii were voted here)
+            uint4 a = tile4[2 * (rr * v8 + c8)], b = tile4[2 * (rr * v8 + c8) + 1];
+            if (GENERAL_ONLY) {
+                const uint4 old = *dst;
+                a.x += old.x & 0xFFFFu; a.y += old.x >> 16; a.z += old.y & 0xFFFFu; a.w += old.y >> 16;
+                b.x += old.z & 0xFFFFu; b.y += old.z >> 16; b.z += old.w & 0xFFFFu; b.w += old.w >> 16;
+            }
             auto pack = [](uint32_t lo, uint32_t hi) { return min(lo, 65535u) | (min(hi, 65535u) << 16); };
             *dst = make_uint4(pack(a.x, a.y), pack(a.z, a.w), pack(b.x, b.y), pack(b.z, b.w));
             continue;
@@ -481,6 +486,175 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
     }
 }
 
+
+// Count accumulator by gather.  On row i a layer of one radius adds to cell j the hits of bucket
+// J' = (j + I_i) mod Nphi with f >= g_i and the hits of bucket J' + 1 with f < g_i: exactly the
+// hits whose vote J - I_i - (f < g_i) is j, by the same FP32 comparison, so the same counts as the
+// scatter -- with no atomics.  A CTA owns `rows` x `cols` cells, counted in shared memory.  Layer
+// by layer it stages the f values of the layer's window of buckets (the sorted hits of consecutive
+// buckets are contiguous, so the window is one or, when it wraps around phi, two ranges) with
+// their bucket offsets; warps then take 32 cells of a row at a time, a lane per cell, scanning the
+// two buckets its cell reads.  A window too wide or too full for its slot is read from global
+// memory.  Layers whose hits lie at several radii are added by the scatter kernel afterwards.
+constexpr int kCountWinPad = 128;    // window buckets beyond cols + 2 held in the staging slot
+constexpr int kCountSmemBudget = 96 * 1024;
+
+__host__ __device__ inline int count_win_cap(int cols) { return cols + 2 + kCountWinPad; }
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB) gather_count_kernel(GatherParams p, int fcap)
+{
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char count_smem[];
+    __shared__ int rowI[kGatherRowsMax * 16];
+    __shared__ float rowG[kGatherRowsMax * 16];
+    __shared__ unsigned rowMask[kGatherRowsMax];
+    __shared__ int s_lo, s_hi, s_total, s_a;
+    __shared__ int s_warp[TPB / 32];
+    const Axes &ax = p.ax;
+    const Workspace &w = p.w;
+    const int e = blockIdx.x / p.tiles_per_event;
+    const int t = blockIdx.x - e * p.tiles_per_event;
+    const int rt = t / p.col_tiles, ct = t - rt * p.col_tiles;
+    const int i0 = rt * p.rows, c0 = ct * p.cols;
+    const int nrows = min(p.rows, ax.n_qpt - i0);
+    const int C = p.cols, L = ax.n_layers, nphi = ax.n_phi;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wcap = count_win_cap(C);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(count_smem);   // rows x cols
+    int *bpre = reinterpret_cast<int *>(cnt + p.rows * C);      // wcap + 1 bucket offsets
+    float *fs = reinterpret_cast<float *>(bpre + wcap + 1);      // fcap f values
+    const int64_t hstart = w.hit_start[e];
+    const float *fsort = w.fsort + hstart;
+    const int32_t *offs = w.offs + (int64_t)e * (n_keys(ax) + 1);
+
+    for (int q = threadIdx.x; q < p.rows * C; q += TPB) cnt[q] = 0u;
+    for (int q = threadIdx.x; q < ((p.rows * 16 + 31) & ~31); q += TPB) {
+        const int rr = q >> 4, l = q & 15, i = i0 + rr;
+        int I = 0;
+        float g = 0.f;
+        unsigned valid = 0u;
+        if (l < L && rr < nrows) {
+            const LayerInfo li = w.info[l];
+            if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
+                const TabEntry te = w.tab[l * ax.n_qpt + i];
+                if (te.I != kNoVote) {
+                    I = te.I;
+                    g = te.g;
+                    valid = 1u;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, valid) >> (threadIdx.x & 16);
+        rowI[q] = I;
+        rowG[q] = g;
+        if ((threadIdx.x & 15) == 0) rowMask[rr] = m & 0xFFFFu;
+    }
+    __syncthreads();
+    for (int l = 0; l < L; ++l) {
+        // the layer's window: buckets [c0 + min I, c0 + C + max I] over the rows it votes on
+        __syncthreads();   // every thread has read the previous layer's window bounds
+        if (threadIdx.x == 0) {
+            int lo = INT_MAX, hi = INT_MIN;
+            for (int rr = 0; rr < nrows; ++rr)
+                if ((rowMask[rr] >> l) & 1u) {
+                    lo = min(lo, rowI[rr * 16 + l]);
+                    hi = max(hi, rowI[rr * 16 + l]);
+                }
+            s_lo = lo;
+            s_hi = hi;
+        }
+        __syncthreads();
+        const int lo = s_lo, hi = s_hi;
+        if (lo > hi) continue;   // uniform for the CTA: no row of this tile takes the layer here
+        const int wlen = C + 1 + (hi - lo) + 1;   // buckets J' and J' + 1 of every cell
+        const int jlo = c0 + lo;                  // unwrapped first bucket
+        const int32_t *lofs = offs + l * nphi;
+        const bool fits_win = wlen <= wcap && wlen <= nphi;   // one pass over the ring at most
+        if (fits_win) {
+            // bucket sizes of the window, scanned into offsets within the staged array
+            int carry = 0;
+            for (int b0 = 0; b0 < wlen; b0 += TPB) {
+                const int q = b0 + threadIdx.x;
+                int n = 0;
+                if (q < wlen) {
+                    const int J = wrap_col(jlo + q, nphi);
+                    n = lofs[J + 1] - lofs[J];
+                }
+                int incl = n;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                    if (lane >= d) incl += v;
+                }
+                if (lane == 31) s_warp[warp] = incl;
+                __syncthreads();
+                if (warp == 0) {
+                    const int v = lane < TPB / 32 ? s_warp[lane] : 0;
+                    int wi = v;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int u = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+                        if (lane >= d) wi += u;
+                    }
+                    if (lane < TPB / 32) s_warp[lane] = wi - v;
+                    if (lane == 31) s_total = wi;
+                }
+                __syncthreads();
+                if (q < wlen) bpre[q] = carry + s_warp[warp] + incl - n;
+                carry += s_total;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                bpre[wlen] = carry;
+                s_a = wrap_col(jlo, nphi);
+            }
+            __syncthreads();
+        }
+        const bool staged = fits_win && bpre[wlen] <= fcap;
+        if (staged) {
+            // the window's hits: from bucket a on, wrapping to the layer's first bucket
+            const int total = bpre[wlen];
+            const int a = s_a;
+            const int first = min(total, lofs[nphi] - lofs[a]);
+            for (int q = threadIdx.x; q < total; q += TPB)
+                fs[q] = q < first ? fsort[lofs[a] + q] : fsort[lofs[0] + (q - first)];
+        }
+        __syncthreads();
+        // a task is 32 cells of one row; each cell is one task's alone in this pass
+        const int per_row = C >> 5;
+        for (int task = warp; task < nrows * per_row; task += TPB / 32) {
+            const int rr = task / per_row;
+            if (!((rowMask[rr] >> l) & 1u)) continue;
+            const int c = (task - rr * per_row) * 32 + lane;
+            const int I = rowI[rr * 16 + l];
+            const float g = rowG[rr * 16 + l];
+            uint32_t add = 0;
+            if (staged) {
+                const int b = c + I - lo;   // bucket J' in the window
+                const int s0 = bpre[b], s1 = bpre[b + 1], s2 = bpre[b + 2];
+                for (int q = s0; q < s1; ++q) add += fs[q] < g ? 0u : 1u;
+                for (int q = s1; q < s2; ++q) add += fs[q] < g ? 1u : 0u;
+            } else {
+                const int J0 = wrap_col(c0 + c + I, nphi), J1 = wrap_col(c0 + c + I + 1, nphi);
+                for (int q = lofs[J0]; q < lofs[J0 + 1]; ++q) add += fsort[q] < g ? 0u : 1u;
+                for (int q = lofs[J1]; q < lofs[J1 + 1]; ++q) add += fsort[q] < g ? 1u : 0u;
+            }
+            cnt[rr * C + c] += add;
+        }
+        __syncthreads();
+    }
+    // counts saturated to 16 bits, 8 cells per 16-byte store
+    uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
+    const int v8 = C >> 3;
+    for (int q = threadIdx.x; q < nrows * v8; q += TPB) {
+        const int rr = q / v8, c8 = q - rr * v8;
+        const uint32_t *src = cnt + rr * C + c8 * 8;
+        auto pack = [](uint32_t lo, uint32_t hi) { return min(lo, 65535u) | (min(hi, 65535u) << 16); };
+        *reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + c0 + c8 * 8) =
+            make_uint4(pack(src[0], src[1]), pack(src[2], src[3]), pack(src[4], src[5]), pack(src[6], src[7]));
+    }
+}
 
 // Peak search of one band of band_rows rows from the accumulator (plus a halo row on each side).
 // COUNTS: the cells are vote counts, staged as they are (2 bytes each); otherwise layer masks,
@@ -771,6 +945,14 @@ cudaError_t launch_scatter_tpb(const VoteParams &p, int threads, size_t smem, in
 
 }  // namespace
 
+size_t gather_count_smem_bytes(const Axes &ax, const Tiling &t)
+{
+    (void)ax;
+    const size_t base = (size_t)t.gather_rows * t.gather_cols * 4 + (size_t)(count_win_cap(t.gather_cols) + 1) * 4;
+    const size_t fbytes = base + 16384 > (size_t)kCountSmemBudget ? 16384 : (size_t)kCountSmemBudget - base;
+    return base + fbytes;
+}
+
 size_t vote_smem_bytes(const Axes &ax, const Tiling &t)
 {
     return (size_t)t.tile_qpt * t.tile_phi * (ax.counts ? 4 : 2) +
@@ -836,9 +1018,36 @@ static cudaError_t launch_gather_tiled(const Axes &ax, const Workspace &w, const
     return launch_gather_nl<16>(p, t.gather_threads, smem, blocks, stream);
 }
 
+template <int TPB>
+cudaError_t launch_gather_count_tpb(const GatherParams &p, size_t smem, int fcap, int blocks, cudaStream_t stream)
+{
+    cudaError_t err = cudaFuncSetAttribute(gather_count_kernel<TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err) return err;
+    return launch_chained(gather_count_kernel<TPB>, dim3(blocks), dim3(TPB), smem, stream, p, fcap);
+}
+
 cudaError_t launch_gather(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
 {
-    return launch_gather_tiled(ax, w, t, stream);
+    if (!ax.counts) return launch_gather_tiled(ax, w, t, stream);
+    if (!w.fsort) return cudaErrorInvalidValue;   // the count gather reads the sorted f values
+    GatherParams p;
+    p.ax = ax;
+    p.w = w;
+    p.rows = t.gather_rows;
+    p.cols = t.gather_cols;
+    p.cap = 0;
+    p.col_tiles = ax.n_phi / p.cols;
+    p.tiles_per_event = ((ax.n_qpt + p.rows - 1) / p.rows) * p.col_tiles;
+    const int blocks = w.n_events * p.tiles_per_event;
+    const size_t smem = gather_count_smem_bytes(ax, t);
+    const size_t base = (size_t)t.gather_rows * t.gather_cols * 4 + (size_t)(count_win_cap(t.gather_cols) + 1) * 4;
+    const int fcap = (int)((smem - base) / 4);
+    switch (t.gather_threads) {
+    case 256: return launch_gather_count_tpb<256>(p, smem, fcap, blocks, stream);
+    case 1024: return launch_gather_count_tpb<1024>(p, smem, fcap, blocks, stream);
+    default: return launch_gather_count_tpb<512>(p, smem, fcap, blocks, stream);
+    }
 }
 
 cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps, bool general_only,
@@ -847,10 +1056,9 @@ cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, 
     const VoteParams p = vote_params(ax, w, t, refine_eps);
     const size_t smem = vote_smem_bytes(ax, t);
     const int grid = w.n_events * p.tiles_per_event;
-    if (ax.counts) {   // every layer, counted (the gather cannot count)
-        if (general_only) return cudaErrorInvalidValue;
-        return launch_scatter_tpb<false, true>(p, t.threads, smem, grid, stream);
-    }
+    if (ax.counts)
+        return general_only ? launch_scatter_tpb<true, true>(p, t.threads, smem, grid, stream)
+                            : launch_scatter_tpb<false, true>(p, t.threads, smem, grid, stream);
     return general_only ? launch_scatter_tpb<true, false>(p, t.threads, smem, grid, stream)
                         : launch_scatter_tpb<false, false>(p, t.threads, smem, grid, stream);
 }
@@ -858,7 +1066,7 @@ cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, 
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
                         cudaStream_t stream)
 {
-    if (t.vote_mode == HOUGH_VOTE_SCATTER || ax.counts) return launch_scatter(ax, w, t, refine_eps, false, stream);
+    if (t.vote_mode == HOUGH_VOTE_SCATTER || (ax.counts && !w.fsort)) return launch_scatter(ax, w, t, refine_eps, false, stream);
     // gather every table layer, then let the scatter kernel add the layers whose radii differ
     cudaError_t err = launch_gather(ax, w, t, stream);
     if (err) return err;

@@ -1,5 +1,7 @@
 """The count accumulator on the GPU (needs a GPU): a cell holds its number of votes, the literal
-A[B[i]] += 1 of Sec. 8, saturating at 65535, and the peak search reads the count.
+A[B[i]] += 1 of Sec. 8, saturating at 65535, and the peak search reads the count.  It is voted by
+a gather (per cell, the hits of two buckets compared with the row's table fraction; the default)
+or by the paper's shared-memory atomic scatter, bit for bit alike.
 
 Every count is compared with the FP64 oracle cell by cell (equal up to the votes the oracle flags
 as within its edge window), then the candidates, member lists and stage-2 results as for the
@@ -96,29 +98,44 @@ def test_counts_saturate_at_65535(binding):
     assert int(got["stats"].votes) == 2 * n
 
 
-@pytest.mark.parametrize("tiling", [dict(tile_qpt=1, tile_phi=64, threads=128), dict(tile_qpt=7, tile_phi=128),
-                                    dict(tile_qpt=16, tile_phi=256, threads=512),
-                                    dict(tile_qpt=32, tile_phi=512, threads=1024),
-                                    dict(tile_qpt=3, tile_phi=2048, threads=256),
+@pytest.mark.parametrize("tiling", [dict(vote_mode=1, tile_qpt=1, tile_phi=64, threads=128),
+                                    dict(vote_mode=1, tile_qpt=7, tile_phi=128),
+                                    dict(vote_mode=1, tile_qpt=16, tile_phi=256, threads=512),
+                                    dict(vote_mode=1, tile_qpt=32, tile_phi=512, threads=1024),
+                                    dict(vote_mode=1, tile_qpt=3, tile_phi=2048, threads=256),
+                                    dict(gather_rows=1, gather_cols=64, gather_threads=256),
+                                    dict(gather_rows=7, gather_cols=256, gather_threads=512),
+                                    dict(gather_rows=32, gather_cols=1024, gather_threads=1024),
+                                    dict(gather_rows=3, gather_cols=2048, gather_threads=256),
                                     dict(band_rows=5), dict(band_rows=16)])
 def test_count_tilings_agree_bit_for_bit(binding, tiling):
-    """Every scatter tile (ragged last slabs of 512 rows by 7 and 3 rows) and band height gives the
-    same counts and candidates."""
+    """Every scatter tile (ragged last slabs of 512 rows by 7 and 3 rows), every count-gather tile
+    (ragged row bands; windows staged, too full for their slot, and wider than the ring, both read
+    from global memory) and band height gives the same counts and candidates."""
     w = _counts(eg.WORKLOADS["pileup_100k"], 40)
     ev = w.event(2).subset(np.arange(40000))
     base = run_gpu(binding, w.geometry, w.binning, ev)
-    other = run_gpu(binding, w.geometry, w.binning, ev, tiling=dict(vote_mode=binding.VOTE_SCATTER, **tiling))
+    other = run_gpu(binding, w.geometry, w.binning, ev, tiling=tiling)
     assert np.array_equal(base["M"], other["M"])
     assert np.array_equal(base["candidates"], other["candidates"])
 
 
-def test_gather_vote_is_refused_for_counts(binding):
+def test_count_gather_is_the_default(binding):
     w = _counts(eg.WORKLOADS["single_50trk"], 8)
     with binding.HoughContext(w.geometry, w.binning, max_hits=16) as ctx:
-        assert ctx.get_tiling()["vote_mode"] == binding.VOTE_SCATTER
-        with pytest.raises(binding.HoughError) as e:
-            ctx.set_tiling(vote_mode=binding.VOTE_GATHER)
-        assert e.value.code == binding.EINVAL
+        assert ctx.get_tiling()["vote_mode"] == binding.VOTE_GATHER
+
+
+@pytest.mark.parametrize("vote_mode", [0, 1])
+def test_counts_mixed_uniform_and_non_uniform_layers(binding, vote_mode):
+    """Layers of one radius counted by the gather (or the scatter), the others added by the scatter."""
+    w = _counts(eg.WORKLOADS["pileup_100k"], 40)
+    ev = w.event(7).subset(np.arange(25000))
+    jitter = ev.layer % 2 == 1
+    ev.r = np.where(jitter, ev.r * np.float32(1.003), ev.r).astype(np.float32)
+    ev.r[np.nonzero(jitter)[0][::2]] *= np.float32(0.999)
+    r = check_event(binding, w.geometry, w.binning, ev, tiling=dict(vote_mode=vote_mode))
+    assert r["got"]["stats"].uniform_layers == 0b0101010101
 
 
 def test_count_threshold_range(binding):
