@@ -24,10 +24,16 @@
 //    J - I - (f < g); other layers take FP32 asinf per vote, and a vote within `refine_eps` of an
 //    edge (or with |x| > kRefineXLim) is recomputed in FP64 in the definition's order.  In the
 //    default (gather) mode this kernel handles only the layers whose radii differ and ORs its tile
-//    into the accumulator; in scatter mode it handles every layer and stores its tile.
+//    into the accumulator (adds it, with counts); in scatter mode it handles every layer and stores
+//    its tile.
+//
+// 3. Count gather (the count accumulator's gather mode): per cell and layer of one radius, the hits
+//    of bucket J' with f >= g_i and of bucket J' + 1 with f < g_i, counted from the sorted f values
+//    of the tile's window of buckets (gather_count_kernel).
 //
 // Peaks: candidates of each band of band_rows rows (one row by default) go to a band list in
 // raster order; a per-event scan then concatenates the band lists into the raster-ordered list.
+// With a d0 axis a band lies in one slice and its cells take the 3 x 3 x 3 rule (peaks3_kernel).
 #include <algorithm>
 #include <climits>
 
