@@ -1,7 +1,7 @@
 // Stage-1 vote (Sec. 4, first step; the A[B[i]] += 1 scatter of Sec. 8), accumulator flush and
 // the peak search over row bands (Sec. 4, second step).
 //
-// Two ways to fill the accumulator, selected per layer on the device:
+// Three ways to fill the accumulator, selected per layer on the device:
 //
 // 1. Gather (layers whose hits share one radius; every configured workload).  On row i every
 //    hit of such a layer votes at J - I_i - (f < g_i): its own bin coordinate J + f shifted by the
@@ -496,13 +496,15 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
 // Count accumulator by gather.  On row i a layer of one radius adds to cell j the hits of bucket
 // J' = (j + I_i) mod Nphi with f >= g_i and the hits of bucket J' + 1 with f < g_i: exactly the
 // hits whose vote J - I_i - (f < g_i) is j, by the same FP32 comparison, so the same counts as the
-// scatter -- with no atomics.  A CTA owns `rows` x `cols` cells, counted in shared memory.  Layer
-// by layer it stages the f values of the layer's window of buckets (the sorted hits of consecutive
-// buckets are contiguous, so the window is one or, when it wraps around phi, two ranges) with
-// their bucket offsets; warps then take 32 cells of a row at a time, a lane per cell, scanning the
-// two buckets its cell reads.  A window too wide or too full for its slot is read from global
-// memory.  Layers whose hits lie at several radii are added by the scatter kernel afterwards.
-constexpr int kCountWinPad = 128;    // window buckets beyond cols + 2 held in the staging slot
+// scatter -- with no atomics.  A CTA owns `rows` x `cols` cells.  It first stages, for every layer
+// at once, the window of buckets its tile reads: the buckets' offsets (the bucket offsets are a
+// prefix sum already, so a window's are a difference of two, or three when it wraps around phi)
+// and the f values of their hits (the sorted hits of consecutive buckets are contiguous: one
+// range, or two when the window wraps).  Then a lane per cell sums, over the layers, the hits of
+// the two buckets its cell reads, and writes the saturated count.  A window too wide or too full
+// for its slot is read from global memory.  Layers whose hits lie at several radii are added by
+// the scatter kernel afterwards.
+constexpr int kCountWinPad = 128;    // window buckets beyond cols + 2 held in a layer's slot
 constexpr int kCountSmemBudget = 96 * 1024;
 
 __host__ __device__ inline int count_win_cap(int cols) { return cols + 2 + kCountWinPad; }
@@ -515,8 +517,9 @@ __global__ void __launch_bounds__(TPB) gather_count_kernel(GatherParams p, int f
     __shared__ int rowI[kGatherRowsMax * 16];
     __shared__ float rowG[kGatherRowsMax * 16];
     __shared__ unsigned rowMask[kGatherRowsMax];
-    __shared__ int s_lo, s_hi, s_total, s_a;
-    __shared__ int s_warp[TPB / 32];
+    __shared__ int s_lo[HOUGH_MAX_LAYERS], s_len[HOUGH_MAX_LAYERS], s_a[HOUGH_MAX_LAYERS];
+    __shared__ int s_total[HOUGH_MAX_LAYERS], s_first[HOUGH_MAX_LAYERS], s_fbase[HOUGH_MAX_LAYERS];
+    __shared__ unsigned s_staged;
     const Axes &ax = p.ax;
     const Workspace &w = p.w;
     const int e = blockIdx.x / p.tiles_per_event;
@@ -527,14 +530,12 @@ __global__ void __launch_bounds__(TPB) gather_count_kernel(GatherParams p, int f
     const int C = p.cols, L = ax.n_layers, nphi = ax.n_phi;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wcap = count_win_cap(C);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(count_smem);   // rows x cols
-    int *bpre = reinterpret_cast<int *>(cnt + p.rows * C);      // wcap + 1 bucket offsets
-    float *fs = reinterpret_cast<float *>(bpre + wcap + 1);      // fcap f values
+    int *bpre = reinterpret_cast<int *>(count_smem);          // L slots of wcap + 1 bucket offsets
+    float *fs = reinterpret_cast<float *>(bpre + L * (wcap + 1));   // fcap f values, layer after layer
     const int64_t hstart = w.hit_start[e];
     const float *fsort = w.fsort + hstart;
     const int32_t *offs = w.offs + (int64_t)e * (n_keys(ax) + 1);
 
-    for (int q = threadIdx.x; q < p.rows * C; q += TPB) cnt[q] = 0u;
     for (int q = threadIdx.x; q < ((p.rows * 16 + 31) & ~31); q += TPB) {
         const int rr = q >> 4, l = q & 15, i = i0 + rr;
         int I = 0;
@@ -557,108 +558,93 @@ __global__ void __launch_bounds__(TPB) gather_count_kernel(GatherParams p, int f
         if ((threadIdx.x & 15) == 0) rowMask[rr] = m & 0xFFFFu;
     }
     __syncthreads();
-    for (int l = 0; l < L; ++l) {
-        // the layer's window: buckets [c0 + min I, c0 + C + max I] over the rows it votes on
-        __syncthreads();   // every thread has read the previous layer's window bounds
-        if (threadIdx.x == 0) {
-            int lo = INT_MAX, hi = INT_MIN;
+    // each layer's window: buckets [c0 + min I, c0 + C + max I] over the rows it votes on
+    if (threadIdx.x < HOUGH_MAX_LAYERS) {
+        const int l = threadIdx.x;
+        int lo = INT_MAX, hi = INT_MIN, len = 0, a = 0, total = 0, first = 0;
+        if (l < L) {
             for (int rr = 0; rr < nrows; ++rr)
                 if ((rowMask[rr] >> l) & 1u) {
                     lo = min(lo, rowI[rr * 16 + l]);
                     hi = max(hi, rowI[rr * 16 + l]);
                 }
-            s_lo = lo;
-            s_hi = hi;
+            if (lo <= hi) {
+                len = C + 2 + (hi - lo);   // buckets J' and J' + 1 of every cell
+                a = wrap_col(c0 + lo, nphi);
+                if (len <= wcap && len <= nphi) {   // one pass over the ring at most
+                    const int32_t *lofs = offs + l * nphi;
+                    const int end = a + len;          // unwrapped end bucket
+                    first = end <= nphi ? lofs[end] - lofs[a] : lofs[nphi] - lofs[a];
+                    total = first + (end <= nphi ? 0 : lofs[end - nphi] - lofs[0]);
+                } else {
+                    len = -len;   // not staged
+                }
+            }
         }
-        __syncthreads();
-        const int lo = s_lo, hi = s_hi;
-        if (lo > hi) continue;   // uniform for the CTA: no row of this tile takes the layer here
-        const int wlen = C + 1 + (hi - lo) + 1;   // buckets J' and J' + 1 of every cell
-        const int jlo = c0 + lo;                  // unwrapped first bucket
+        s_lo[l] = lo;
+        s_len[l] = len;
+        s_a[l] = a;
+        s_total[l] = total;
+        s_first[l] = first;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned staged = 0u;
+        int fbase = 0;
+        for (int l = 0; l < L; ++l) {
+            s_fbase[l] = fbase;
+            if (s_len[l] > 0 && fbase + s_total[l] <= fcap) {
+                staged |= 1u << l;
+                fbase += s_total[l];
+            }
+        }
+        s_staged = staged;
+    }
+    __syncthreads();
+    const unsigned staged = s_staged;
+    // staging: every staged layer's bucket offsets (relative to its f values) and f values
+    for (int l = 0; l < L; ++l) {
+        if (!((staged >> l) & 1u)) continue;
         const int32_t *lofs = offs + l * nphi;
-        const bool fits_win = wlen <= wcap && wlen <= nphi;   // one pass over the ring at most
-        if (fits_win) {
-            // bucket sizes of the window, scanned into offsets within the staged array
-            int carry = 0;
-            for (int b0 = 0; b0 < wlen; b0 += TPB) {
-                const int q = b0 + threadIdx.x;
-                int n = 0;
-                if (q < wlen) {
-                    const int J = wrap_col(jlo + q, nphi);
-                    n = lofs[J + 1] - lofs[J];
-                }
-                int incl = n;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-                    if (lane >= d) incl += v;
-                }
-                if (lane == 31) s_warp[warp] = incl;
-                __syncthreads();
-                if (warp == 0) {
-                    const int v = lane < TPB / 32 ? s_warp[lane] : 0;
-                    int wi = v;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const int u = __shfl_up_sync(0xFFFFFFFFu, wi, d);
-                        if (lane >= d) wi += u;
-                    }
-                    if (lane < TPB / 32) s_warp[lane] = wi - v;
-                    if (lane == 31) s_total = wi;
-                }
-                __syncthreads();
-                if (q < wlen) bpre[q] = carry + s_warp[warp] + incl - n;
-                carry += s_total;
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) {
-                bpre[wlen] = carry;
-                s_a = wrap_col(jlo, nphi);
-            }
-            __syncthreads();
+        const int a = s_a[l], len = s_len[l], first = s_first[l], total = s_total[l], fb = s_fbase[l];
+        int *bp = bpre + l * (wcap + 1);
+        for (int q = threadIdx.x; q <= len; q += TPB) {
+            const int J = a + q;   // unwrapped
+            bp[q] = fb + (J <= nphi ? lofs[J] - lofs[a] : first + lofs[J - nphi] - lofs[0]);
         }
-        const bool staged = fits_win && bpre[wlen] <= fcap;
-        if (staged) {
-            // the window's hits: from bucket a on, wrapping to the layer's first bucket
-            const int total = bpre[wlen];
-            const int a = s_a;
-            const int first = min(total, lofs[nphi] - lofs[a]);
-            for (int q = threadIdx.x; q < total; q += TPB)
-                fs[q] = q < first ? fsort[lofs[a] + q] : fsort[lofs[0] + (q - first)];
-        }
-        __syncthreads();
-        // a task is 32 cells of one row; each cell is one task's alone in this pass
-        const int per_row = C >> 5;
-        for (int task = warp; task < nrows * per_row; task += TPB / 32) {
-            const int rr = task / per_row;
-            if (!((rowMask[rr] >> l) & 1u)) continue;
-            const int c = (task - rr * per_row) * 32 + lane;
+        for (int q = threadIdx.x; q < total; q += TPB)
+            fs[fb + q] = q < first ? fsort[lofs[a] + q] : fsort[lofs[0] + (q - first)];
+    }
+    __syncthreads();
+    // a lane per cell, 32 cells of one row per warp pass, every layer summed in a register
+    uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
+    const int per_row = C >> 5;
+    for (int task = warp; task < nrows * per_row; task += TPB / 32) {
+        const int rr = task / per_row;
+        const int c = (task - rr * per_row) * 32 + lane;
+        const unsigned vm = rowMask[rr];
+        uint32_t count = 0;
+        for (int l = 0; l < L; ++l) {
+            if (!((vm >> l) & 1u)) continue;   // the same for the whole warp: the row's layers
             const int I = rowI[rr * 16 + l];
             const float g = rowG[rr * 16 + l];
-            uint32_t add = 0;
-            if (staged) {
-                const int b = c + I - lo;   // bucket J' in the window
-                const int s0 = bpre[b], s1 = bpre[b + 1], s2 = bpre[b + 2];
-                for (int q = s0; q < s1; ++q) add += fs[q] < g ? 0u : 1u;
-                for (int q = s1; q < s2; ++q) add += fs[q] < g ? 1u : 0u;
+            if ((staged >> l) & 1u) {
+                const int *bp = bpre + l * (wcap + 1) + (c + I - s_lo[l]);   // bucket J' of the window
+                const int s0 = bp[0], s1 = bp[1], s2 = bp[2];
+                for (int q = s0; q < s1; ++q) count += fs[q] < g ? 0u : 1u;
+                for (int q = s1; q < s2; ++q) count += fs[q] < g ? 1u : 0u;
             } else {
+                const int32_t *lofs = offs + l * nphi;
                 const int J0 = wrap_col(c0 + c + I, nphi), J1 = wrap_col(c0 + c + I + 1, nphi);
-                for (int q = lofs[J0]; q < lofs[J0 + 1]; ++q) add += fsort[q] < g ? 0u : 1u;
-                for (int q = lofs[J1]; q < lofs[J1 + 1]; ++q) add += fsort[q] < g ? 1u : 0u;
+                for (int q = lofs[J0]; q < lofs[J0 + 1]; ++q) count += fsort[q] < g ? 0u : 1u;
+                for (int q = lofs[J1]; q < lofs[J1 + 1]; ++q) count += fsort[q] < g ? 1u : 0u;
             }
-            cnt[rr * C + c] += add;
         }
-        __syncthreads();
-    }
-    // counts saturated to 16 bits, 8 cells per 16-byte store
-    uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
-    const int v8 = C >> 3;
-    for (int q = threadIdx.x; q < nrows * v8; q += TPB) {
-        const int rr = q / v8, c8 = q - rr * v8;
-        const uint32_t *src = cnt + rr * C + c8 * 8;
-        auto pack = [](uint32_t lo, uint32_t hi) { return min(lo, 65535u) | (min(hi, 65535u) << 16); };
-        *reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + c0 + c8 * 8) =
-            make_uint4(pack(src[0], src[1]), pack(src[2], src[3]), pack(src[4], src[5]), pack(src[6], src[7]));
+        // saturated to 16 bits; even lanes store their cell and the next one as one word
+        const uint32_t v = min(count, 65535u);
+        const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, v, 1);
+        if (!(lane & 1))
+            *reinterpret_cast<uint32_t *>(M + (int64_t)(i0 + rr) * nphi + c0 + c) = v | (next << 16);
     }
 }
 
@@ -951,10 +937,15 @@ cudaError_t launch_scatter_tpb(const VoteParams &p, int threads, size_t smem, in
 
 }  // namespace
 
+// Bucket-offset slots of every layer, then the f values (at least 16 KB, the rest of the budget).
+static size_t gather_count_base_bytes(const Axes &ax, const Tiling &t)
+{
+    return (size_t)ax.n_layers * (count_win_cap(t.gather_cols) + 1) * 4;
+}
+
 size_t gather_count_smem_bytes(const Axes &ax, const Tiling &t)
 {
-    (void)ax;
-    const size_t base = (size_t)t.gather_rows * t.gather_cols * 4 + (size_t)(count_win_cap(t.gather_cols) + 1) * 4;
+    const size_t base = gather_count_base_bytes(ax, t);
     const size_t fbytes = base + 16384 > (size_t)kCountSmemBudget ? 16384 : (size_t)kCountSmemBudget - base;
     return base + fbytes;
 }
@@ -1047,8 +1038,7 @@ cudaError_t launch_gather(const Axes &ax, const Workspace &w, const Tiling &t, c
     p.tiles_per_event = ((ax.n_qpt + p.rows - 1) / p.rows) * p.col_tiles;
     const int blocks = w.n_events * p.tiles_per_event;
     const size_t smem = gather_count_smem_bytes(ax, t);
-    const size_t base = (size_t)t.gather_rows * t.gather_cols * 4 + (size_t)(count_win_cap(t.gather_cols) + 1) * 4;
-    const int fcap = (int)((smem - base) / 4);
+    const int fcap = (int)((smem - gather_count_base_bytes(ax, t)) / 4);
     switch (t.gather_threads) {
     case 256: return launch_gather_count_tpb<256>(p, smem, fcap, blocks, stream);
     case 1024: return launch_gather_count_tpb<1024>(p, smem, fcap, blocks, stream);
