@@ -76,7 +76,7 @@ def parse_args():
                     help="run one part only (for profiling); the default runs everything")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the batch with the default kernel configuration instead of the tuned one")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="offered-load duration per served point")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="offered-load duration per served point")
     ap.add_argument("--serve-loads", default=",".join(str(int(x)) for x in eg.SERVED_OFFERED_LOADS),
                     help="offered loads (events/s), comma-separated")
     return ap.parse_args()
