@@ -183,3 +183,35 @@ def test_static_vote_counts(binding):
     torch.cuda.synchronize()
     got = acc.cpu().numpy().view(np.uint16)
     assert np.array_equal(got, run_gpu(binding, w.geometry, w.binning, ev)["M"])
+
+
+def _ev(r, phi, z, layer):
+    return eg.Event(np.asarray(r, np.float32), np.asarray(phi, np.float32), np.asarray(z, np.float32),
+                    np.asarray(layer, np.uint8), np.zeros(len(r), np.int32))
+
+
+def test_count_edge_cases(binding):
+    """Empty event, single hits at the extreme azimuths, 20,000 hits at one azimuth (one bucket
+    holds more hits than the gather's staging slot: read from global memory), a one-row grid and a
+    3-layer, 77 x 192 grid with odd stage-2 axes -- counts by gather and by scatter."""
+    w = _counts(eg.WORKLOADS["pileup_100k"], 3)
+    got = run_gpu(binding, w.geometry, w.binning, _ev([], [], [], []))
+    assert not got["M"].any() and len(got["candidates"]) == 0
+    pi32 = np.float32(np.pi)
+    for phi in (0.0, pi32, -pi32, np.nextafter(pi32, np.float32(0)), 999.0, -999.0):
+        check_event(binding, w.geometry, w.binning, _ev([110.0], [phi], [0.0], [9]))
+    n = 20000
+    layer = np.arange(n) % 10
+    r = np.asarray(w.geometry.radii_cm, np.float32)[layer]
+    hot = _ev(r, np.full(n, 0.7), np.zeros(n), layer)
+    for mode in (0, 1):
+        check_event(binding, w.geometry, w.binning, hot, tiling=dict(vote_mode=mode))
+    g = eg.Geometry()
+    bn = eg.Binning(n_qpt=1, qpt_min=-0.3, qpt_max=0.1, n_phi=64, threshold=2, accumulator=eg.ACC_COUNTS)
+    check_event(binding, g, bn, eg.WORKLOADS["single_50trk"].event(3))
+    g3 = eg.Geometry(radii_cm=(5.0, 30.0, 90.0), b_tesla=2.0)
+    bn3 = eg.Binning(n_qpt=77, qpt_min=-1.3, qpt_max=0.9, n_phi=192, threshold=2, n_cot=17, n_z0=23,
+                     cot_min=-3.0, cot_max=2.0, z0_min=-20.0, z0_max=10.0, accumulator=eg.ACC_COUNTS)
+    ev3 = eg.simulate_event(g3, 40, (0.7, 20.0), 30, seed=99)
+    for t in (dict(gather_rows=5, gather_cols=64), dict(vote_mode=1, tile_qpt=5, tile_phi=64)):
+        check_event(binding, g3, bn3, ev3, tiling=t)

@@ -133,3 +133,26 @@ def test_d0_static_vote(binding):
     torch.cuda.synchronize()
     got = acc.cpu().numpy().view(np.uint16)
     assert np.array_equal(got, run_gpu(binding, w.geometry, w.binning, ev)["M"])
+
+
+def test_single_d0_slice_at_zero_is_the_prompt_path(binding):
+    """One d0 bin centred on 0 (d0 = 0 exactly): the accumulator, the 3x3x3 peak rule with no
+    neighbouring slices and stage 2 reduce to the prompt path's, result for result."""
+    w = eg.WORKLOADS["pileup_100k"]
+    ev = w.event(2).subset(np.arange(30000))
+    prompt = run_gpu(binding, w.geometry, w.binning, ev)
+    w1 = eg.with_binning(w, n_d0=1, d0_min=-0.5, d0_max=0.5)
+    one = run_gpu(binding, w1.geometry, w1.binning, ev)
+    assert np.array_equal(one["M"], prompt["M"])
+    assert np.array_equal(one["candidates"], prompt["candidates"])
+
+
+def test_d0_odd_sizes_and_few_layers(binding):
+    """3 layers at 5, 30 and 90 cm, 3 d0 bins over +-4 cm, 77 x 192 cells per slice, odd stage-2
+    axes; displaced tracks (d0 within +-3 cm), with the default, a gather and a scatter tiling."""
+    g = eg.Geometry(radii_cm=(5.0, 30.0, 90.0), b_tesla=2.0)
+    bn = eg.Binning(n_qpt=77, qpt_min=-1.3, qpt_max=0.9, n_phi=192, threshold=2, n_cot=17, n_z0=23,
+                    cot_min=-3.0, cot_max=2.0, z0_min=-20.0, z0_max=10.0, n_d0=3, d0_min=-4.0, d0_max=4.0)
+    ev = eg.simulate_event(g, 40, (0.7, 20.0), 30, seed=98, d0_range=(-3.0, 3.0))
+    for t in (None, dict(gather_rows=5, gather_cols=64, band_rows=3), dict(vote_mode=1, tile_qpt=5, tile_phi=64)):
+        check_event(binding, g, bn, ev, tiling=t)

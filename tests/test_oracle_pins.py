@@ -569,6 +569,17 @@ def test_centred_d0_slice_equals_the_prompt_grid():
     assert int(v3.sum()) >= int(vp.sum())
 
 
+def test_single_d0_slice_at_zero_is_the_prompt_oracle():
+    """One d0 bin centred on 0: the d0 grid is the prompt grid, and the 3x3x3 rule with no
+    neighbouring slices is the 3x3 rule -- same accumulator, flags, candidates and stage 2."""
+    w = eg.WORKLOADS["single_50trk"]
+    ev = w.event(1)
+    prompt = oracle.run(w.geometry, w.binning, ev)
+    one = oracle.run(w.geometry, eg.Binning(**{**w.binning.__dict__, "n_d0": 1, "d0_min": -0.5, "d0_max": 0.5}), ev)
+    for k in ("M", "vote_flags", "candidates", "member_offsets", "members", "stage2"):
+        assert np.array_equal(one[k], prompt[k]), k
+
+
 def test_golden_peak3_cases():
     with open(os.path.join(GOLDEN, "peak3_cases.json")) as f:
         spec = json.load(f)
