@@ -527,6 +527,8 @@ def measure_served(env, args):
             while t is None:
                 t = srv.submit(e[0], e[1], e[2], e[3], e[0].shape[0])
             srv.poll(t, timeout_us=60_000_000, candidates=False)
+        # and a short saturating burst, so that the result buffers have grown to full batches
+        drive_server(env, srv, pool, 50_000.0, 0.5, seed=5)
         res = []
         for k, rate in enumerate(loads):
             res.append(drive_server(env, srv, pool, rate, args.serve_seconds, seed=77 + k))

@@ -52,6 +52,89 @@ struct hough_server;
 
 namespace {
 
+// The host buffers of one batch's candidates: a mapped pinned part the pack kernel writes the first
+// `cap` candidates to, and a pinned overflow the rest of a larger batch is copied to.  A finished
+// batch hands its block to its events' tickets (shared ownership) and the lane takes a spare block
+// for its next launch, so the dispatcher copies no candidate: a poll copies its event's range
+// straight to the caller, and the last ticket released returns the block to the pool.
+struct ResultBlock {
+    hough_candidate *host = nullptr;
+    hough_candidate *dev = nullptr;    // its device address
+    int64_t cap = 0;
+    hough_candidate *over = nullptr;   // candidates cap.. of the batch
+    int64_t over_cap = 0;
+};
+
+// Copy candidates [a, a + n) of a block's batch to `out`.
+void copy_candidates(const ResultBlock &b, int64_t a, int64_t n, hough_candidate *out)
+{
+    const int64_t split = std::min(std::max(a, b.cap), a + n);   // [a, split) mapped, [split, a + n) overflow
+    if (split > a) std::memcpy(out, b.host + a, sizeof(hough_candidate) * (split - a));
+    if (a + n > split) std::memcpy(out + (split - a), b.over + (split - b.cap), sizeof(hough_candidate) * (a + n - split));
+}
+
+struct BlockPool {
+    std::mutex mu;
+    std::vector<ResultBlock *> free;
+    int total = 0;       // blocks allocated
+    int limit = 0;       // at most this many; beyond it results are copied out of the lane's block
+    int64_t cap = 0;     // candidates in a block's mapped part
+    int64_t over0 = 0;   // and in a new block's overflow (grown on demand)
+    // overflows replaced by larger ones: freed only with the pool, since freeing pinned memory
+    // synchronises the device and would stall the lanes in flight
+    std::vector<hough_candidate *> retired;
+    ~BlockPool()
+    {
+        for (ResultBlock *b : free) {
+            cudaFreeHost(b->host);
+            cudaFreeHost(b->over);
+            delete b;
+        }
+        for (hough_candidate *p : retired) cudaFreeHost(p);
+    }
+};
+
+// A free block of the pool, or a new one while the pool is below its limit; null otherwise (or when
+// the allocation fails).  Never blocks on the device.
+std::shared_ptr<ResultBlock> take_block(const std::shared_ptr<BlockPool> &pool)
+{
+    ResultBlock *b = nullptr;
+    {
+        std::lock_guard<std::mutex> g(pool->mu);
+        if (!pool->free.empty()) {
+            b = pool->free.back();
+            pool->free.pop_back();
+        } else if (pool->total < pool->limit) {
+            ++pool->total;
+        } else {
+            return nullptr;
+        }
+    }
+    if (!b) {
+        b = new (std::nothrow) ResultBlock();
+        bool ok = b && cudaHostAlloc(&b->host, sizeof(hough_candidate) * pool->cap, cudaHostAllocMapped) == cudaSuccess;
+        ok = ok && cudaHostGetDevicePointer(reinterpret_cast<void **>(&b->dev), b->host, 0) == cudaSuccess;
+        ok = ok && cudaHostAlloc(&b->over, sizeof(hough_candidate) * pool->over0, cudaHostAllocDefault) == cudaSuccess;
+        if (ok) {
+            b->cap = pool->cap;
+            b->over_cap = pool->over0;
+        } else {
+            if (b) {
+                if (b->host) cudaFreeHost(b->host);
+                if (b->over) cudaFreeHost(b->over);
+                delete b;
+            }
+            std::lock_guard<std::mutex> g(pool->mu);
+            --pool->total;
+            return nullptr;
+        }
+    }
+    return std::shared_ptr<ResultBlock>(b, [pool](ResultBlock *x) {
+        std::lock_guard<std::mutex> g(pool->mu);
+        pool->free.push_back(x);
+    });
+}
+
 struct Ticket {
     int64_t arrival_ns = 0, submit_ns = 0, launch_ns = 0, done_ns = 0;
     int32_t status = HOUGH_ENOTREADY;
@@ -59,7 +142,9 @@ struct Ticket {
     uint64_t votes = 0;
     uint32_t device_error = 0;
     int64_t n_candidates = 0;
-    std::vector<hough_candidate> cands;
+    std::shared_ptr<ResultBlock> block;   // the candidates are [block_off, + n_candidates) of the block ...
+    int64_t block_off = 0;
+    std::vector<hough_candidate> cands;   // ... or, without a block, here
     bool done = false;
 };
 
@@ -74,11 +159,8 @@ struct Lane {
     int64_t *hit_start = nullptr;
     int32_t *offsets = nullptr;
     DevStats *stats = nullptr;
-    hough_candidate *mcands = nullptr;      // mapped pinned: the pack kernel writes the first mcap here
-    hough_candidate *mcands_dev = nullptr;  // its device address
+    std::shared_ptr<ResultBlock> blk;       // the pack kernel writes the first mcap candidates here
     int64_t mcap = 0;
-    hough_candidate *cands = nullptr;       // pinned overflow: candidates mcap.. of a larger batch
-    int64_t cand_cap = 0;
     // the batch being filled or processed
     std::vector<Ticket *> tickets;
     int n_events = 0;          // events reserved (copies may still be in progress)
@@ -100,6 +182,7 @@ struct hough_server {
     hough_serve_config cfg{};
     Axes ax{};
     std::vector<std::unique_ptr<Lane>> lanes;
+    std::shared_ptr<BlockPool> pool = std::make_shared<BlockPool>();
     size_t device_bytes = 0;
     std::mutex mu;
     std::condition_variable cv_dispatch;   // wakes the dispatcher
@@ -168,8 +251,6 @@ hough_server::~hough_server()
         cudaFreeHost(l->hit_start);
         cudaFreeHost(l->offsets);
         cudaFreeHost(l->stats);
-        cudaFreeHost(l->mcands);
-        cudaFreeHost(l->cands);
     }
 }
 
@@ -187,7 +268,7 @@ int hough_server::enqueue_batch(Lane *l)
     l->phase_wanted = 1;
     int rc = batch_run(l->b, l->r, l->phi, l->z, l->layer, l->hit_start, n, HOUGH_HOST, l->stream, false);
     if (!rc) rc = batch_enqueue_stats(l->b, l->stats, n, l->stream);
-    if (!rc) rc = batch_enqueue_offsets_mapped(l->b, l->offsets, l->mcands_dev, l->mcap, l->stream);
+    if (!rc) rc = batch_enqueue_offsets_mapped(l->b, l->offsets, l->blk->dev, l->mcap, l->stream);
     if (!rc && cudaLaunchHostFunc(l->stream, lane_phase_done, l) != cudaSuccess)
         rc = set_last_error(HOUGH_ECUDA, "cudaLaunchHostFunc failed");
     return rc;
@@ -200,37 +281,46 @@ int hough_server::enqueue_candidates(Lane *l, bool injected_alloc_failure)
 {
     const int64_t total = l->offsets[l->n_events];
     const int64_t rest = total - l->mcap;
-    if (rest > l->cand_cap || injected_alloc_failure) {
-        int64_t cap = std::max<int64_t>(l->cand_cap, 1);
+    ResultBlock &blk = *l->blk;
+    if (rest > blk.over_cap || injected_alloc_failure) {
+        int64_t cap = std::max<int64_t>(blk.over_cap, 1);
         while (cap < rest) cap *= 2;
         hough_candidate *grown = nullptr;
         if (injected_alloc_failure)
             return set_last_error(HOUGH_ENOMEM, "injected result-buffer allocation failure");
         if (cudaHostAlloc(&grown, sizeof(hough_candidate) * cap, cudaHostAllocDefault) != cudaSuccess)
             return set_last_error(HOUGH_ENOMEM, "pinned result buffer allocation failed");
-        cudaFreeHost(l->cands);
-        l->cands = grown;
-        l->cand_cap = cap;
+        {
+            std::lock_guard<std::mutex> g(pool->mu);
+            pool->retired.push_back(blk.over);
+        }
+        blk.over = grown;
+        blk.over_cap = cap;
     }
     l->phase_wanted = 2;
-    int rc = batch_enqueue_candidates(l->b, l->cands, total, l->stream, l->mcap);
+    int rc = batch_enqueue_candidates(l->b, blk.over, total, l->stream, l->mcap);
     if (!rc && cudaLaunchHostFunc(l->stream, lane_phase_done, l) != cudaSuccess)
         rc = set_last_error(HOUGH_ECUDA, "cudaLaunchHostFunc failed");
     return rc;
 }
 
 // Everything of the lane's batch is on the host: fill each event's result (unlocked; pollers
-// look at a ticket only once `done` is published under the mutex).
+// look at a ticket only once `done` is published under the mutex).  With a spare block the
+// events share the lane's block and the lane moves on to the spare; without one (the pollers lag
+// and the pool is at its limit) each event's candidates are copied out and the lane keeps it.
 void hough_server::fill_results(Lane *l)
 {
+    std::shared_ptr<ResultBlock> spare = take_block(pool);
     for (int e = 0; e < l->n_events; ++e) {
         Ticket *k = l->tickets[e];
         const int64_t a = l->offsets[e], b = l->offsets[e + 1];
-        const int64_t split = std::min(std::max(a, l->mcap), b);   // [a, split) mapped, [split, b) overflow
-        k->cands.resize((size_t)(b - a));
-        if (split > a) std::memcpy(k->cands.data(), l->mcands + a, sizeof(hough_candidate) * (split - a));
-        if (b > split) std::memcpy(k->cands.data() + (split - a), l->cands + (split - l->mcap),
-                                   sizeof(hough_candidate) * (b - split));
+        if (spare) {
+            k->block = l->blk;
+            k->block_off = a;
+        } else {
+            k->cands.resize((size_t)(b - a));
+            copy_candidates(*l->blk, a, b - a, k->cands.data());
+        }
         k->n_candidates = b - a;
         const DevStats &d = l->stats[e];
         uint64_t v = 0;
@@ -239,6 +329,7 @@ void hough_server::fill_results(Lane *l)
         k->device_error = d.device_error;
         k->status = d.device_error ? HOUGH_EDEVICE : HOUGH_OK;
     }
+    if (spare) l->blk = std::move(spare);
 }
 
 // Publish the lane's results and free it (mutex held).
@@ -404,7 +495,6 @@ int hough_serve_create(const hough_geometry *geometry, const hough_binning *binn
         }
         s->device_bytes += bytes;
         bool ok = cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) == cudaSuccess;
-        l->cand_cap = std::max<int64_t>(1 << 14, (int64_t)E * 256);
         l->mcap = std::max<int64_t>(1 << 16, (int64_t)E * 4096);
         ok = ok && cudaHostAlloc(&l->r, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->phi, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;
@@ -413,13 +503,24 @@ int hough_serve_create(const hough_geometry *geometry, const hough_binning *binn
         ok = ok && cudaHostAlloc(&l->hit_start, sizeof(int64_t) * (E + 1), cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->offsets, sizeof(int32_t) * (E + 1), cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->stats, sizeof(DevStats) * E, cudaHostAllocDefault) == cudaSuccess;
-        ok = ok && cudaHostAlloc(&l->cands, sizeof(hough_candidate) * l->cand_cap, cudaHostAllocDefault) == cudaSuccess;
-        ok = ok && cudaHostAlloc(&l->mcands, sizeof(hough_candidate) * l->mcap, cudaHostAllocMapped) == cudaSuccess;
-        ok = ok && cudaHostGetDevicePointer(reinterpret_cast<void **>(&l->mcands_dev), l->mcands, 0) == cudaSuccess;
+        if (i == 0) {
+            // every lane's block, as many spares, and room for as many again while pollers lag
+            s->pool->cap = l->mcap;
+            s->pool->over0 = std::max<int64_t>(1 << 14, (int64_t)E * 256);
+            s->pool->limit = 3 * want;
+        }
+        l->blk = ok ? take_block(s->pool) : nullptr;
+        ok = ok && l->blk;
         s->lanes.push_back(std::move(l));
         if (!ok) return set_last_error(HOUGH_ENOMEM, "lane allocation failed");
     }
     if (s->lanes.size() < 2) return set_last_error(HOUGH_ENOMEM, "fewer than two lanes fit");
+    {
+        // a spare result block per lane now, so that no completion in service waits on an allocation
+        std::vector<std::shared_ptr<ResultBlock>> spares;
+        for (size_t i = 0; i < s->lanes.size(); ++i)
+            if (auto b = take_block(s->pool)) spares.push_back(std::move(b));
+    }
     c.lanes = (int)s->lanes.size();
     if (c.max_in_flight == 0) c.max_in_flight = c.lanes - 1;
     s->cfg = c;
@@ -560,8 +661,11 @@ int hough_serve_poll(hough_server *s, uint64_t ticket, hough_candidate *out, int
         result->device_error = t->device_error;
         result->reserved = 0;
     }
-    if (cap > 0 && t->n_candidates > 0)
-        std::memcpy(out, t->cands.data(), sizeof(hough_candidate) * std::min<int64_t>(cap, t->n_candidates));
+    if (cap > 0 && t->n_candidates > 0) {
+        const int64_t n = std::min<int64_t>(cap, t->n_candidates);
+        if (t->block) copy_candidates(*t->block, t->block_off, n, out);
+        else std::memcpy(out, t->cands.data(), sizeof(hough_candidate) * n);
+    }
     if (t->status != HOUGH_OK)
         return set_last_error(t->status, why.empty() ? "the event failed" : why.c_str());
     if (t->n_candidates > cap && cap >= 0 && out != nullptr)
