@@ -103,6 +103,33 @@ def test_served_results_equal_alone(binding):
         assert max(sizes) > 1, "no launch held more than one event"
 
 
+def test_unpolled_results_fill_the_pool_then_are_copied(binding):
+    """Full-size events, four per launch: a batch's candidates overflow the mapped part of its
+    result block (65,536 candidates), so polls read across both parts; six batches left unpolled
+    hold every block the pool may allocate (three per lane), so the last completions copy their
+    events' candidates out instead.  Every event still equals its result alone."""
+    base = [W.event(i) for i in range(8)]
+    expect = [_alone(binding, ev)[0] for ev in base]
+    per = 4
+    with _server(binding, lanes=2, max_batch_events=per,
+                 max_batch_hits=per * max(ev.n_hits for ev in base)) as srv:
+        tickets = []
+        for b in range(6):
+            srv.inject(binding.SERVE_FAULT_HOLD, True)
+            tickets += [srv.submit_event(base[(b * per + k) % len(base)]) for k in range(per)]
+            srv.inject(binding.SERVE_FAULT_HOLD, False)
+            srv.drain(timeout_us=30_000_000)
+        assert all(t is not None for t in tickets)
+        assert srv.stats().pending_tickets == len(tickets)
+        n_first = 0
+        for i, t in enumerate(tickets):
+            cands, res = srv.poll(t, timeout_us=30_000_000)
+            assert res.status == binding.OK and res.batch_events == per
+            assert np.array_equal(cands, expect[i % len(base)]), f"event {i}"
+            n_first += res.n_candidates if i < per else 0
+        assert n_first > 65_536, "the first batch did not reach into its block's overflow"
+
+
 def test_admission_is_bounded_and_hold_times_out(binding):
     events = _events(6)
     with _server(binding, max_batch_events=2, lanes=2) as srv:
