@@ -390,6 +390,33 @@ __device__ __forceinline__ int small_pair_member(const SmallStage2 &sm, int n, i
     return q;
 }
 
+// K pairs per lane, v0 + 32 u for u < K, straight-line and independent of each other (an index
+// past the end is clamped and its result masked): a lone warp (few candidates) is bound by the
+// latency of this chain, not by issue.
+template <int K>
+__device__ __forceinline__ void vote_pairs(const Axes &ax, uint32_t *grid, const SmallStage2 &sm, int n, int total,
+                                           int v0, Best &best, unsigned long long &votes)
+{
+    int m[K], nz[K], ly[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        const int v = v0 + 32 * u;
+        const int vc = min(v, total - 1);
+        const int q = small_pair_member(sm, n, vc);
+        const int mrl = sm.mrl[q];
+        m[u] = sm.mlo[q] + (vc - sm.start[q]);
+        ly[u] = mrl >> 16;
+        const int cell = stage2_cell(ax, sm.a[q], sm.b[q], mrl, m[u]);
+        nz[u] = v < total ? cell : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+        if (nz[u] >= 0) {
+            stage2_vote(ax, grid, m[u], nz[u], ly[u], best);
+            ++votes;
+        }
+}
+
 __device__ void warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
                                   SmallStage2 &sm, const int *pos, int n, int i, Best &best,
                                   unsigned long long &votes, int &rlo, int &rhi)
@@ -419,30 +446,12 @@ __device__ void warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (lane == 0) sm.start[kSmallMembers] = total;
     __syncwarp();
-    // four pairs per lane per round, straight-line and independent of each other (an index past
-    // the end is clamped and its result masked): a lone warp (few candidates) is bound by the
-    // latency of this chain, not by issue
+    // rounds of four pairs per lane while more than two lanes' worth remain, then one pair per lane:
+    // a masked four-pair round costs a full round's instructions however few pairs it holds
     constexpr int kIlp = 4;
-    for (int v0 = lane; v0 < total; v0 += 32 * kIlp) {
-        int m[kIlp], nz[kIlp], ly[kIlp];
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
-            const int v = v0 + 32 * u;
-            const int vc = min(v, total - 1);
-            const int q = small_pair_member(sm, n, vc);
-            const int mrl = sm.mrl[q];
-            m[u] = sm.mlo[q] + (vc - sm.start[q]);
-            ly[u] = mrl >> 16;
-            const int cell = stage2_cell(ax, sm.a[q], sm.b[q], mrl, m[u]);
-            nz[u] = v < total ? cell : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u)
-            if (nz[u] >= 0) {
-                stage2_vote(ax, grid, m[u], nz[u], ly[u], best);
-                ++votes;
-            }
-    }
+    int base = 0;
+    for (; total - base > 64; base += 32 * kIlp) vote_pairs<kIlp>(ax, grid, sm, n, total, base + lane, best, votes);
+    for (; base < total; base += 32) vote_pairs<1>(ax, grid, sm, n, total, base + lane, best, votes);
     __syncwarp();
 }
 
