@@ -3,7 +3,8 @@
 // (membership) and their vote in a (cot theta, z0) grid of layer masks (stage 2).
 //
 // Work scales with a candidate's votes, not with the size of the stage-2 grid.  Each confirming
-// warp owns a clear n_cot x n_z0 grid in shared memory.  A member's z0 coordinate is linear in the
+// warp owns a clear n_cot x n_z0 grid in shared memory (16-bit masks; in batches of a detector of
+// at most 10 layers, 10-bit masks three to a word, which lets more warps share an SM).  A member's z0 coordinate is linear in the
 // cot row, so only a run of rows can vote inside the z0 range; the (member, row) pairs of all
 // runs are spread over the lanes and voted with a shared atomicOr, whose returned word also
 // judges the cell (stage2_vote): the arg-max falls out of the one pass.
@@ -318,20 +319,23 @@ struct Best {
 // seen over all votes is the grid's maximum, the cells seen with it are exactly the cells that
 // reach it, and the lowest of them -- with the mask seen there, which is its final mask -- is the
 // row-major-first arg-max.  No second pass over the votes is needed.  Returns the word index.
+// P10: the grid packs three 10-bit masks a word (detectors of at most 10 layers), else two 16-bit.
+template <bool P10 = false>
 __device__ __forceinline__ int stage2_vote(const Axes &ax, uint32_t *grid, int m, int nz, int layer, Best &best)
 {
     const unsigned cell = (unsigned)(m * ax.n_z0 + nz);
-    const unsigned shift = (cell & 1u) << 4;
+    const unsigned word = P10 ? cell / 3u : cell >> 1;
+    const unsigned shift = P10 ? (cell - word * 3u) * 10u : (cell & 1u) << 4;
     const uint32_t bit = 1u << layer;
-    const uint32_t old = atomicOr(&grid[cell >> 1], bit << shift);
-    const uint32_t m16 = ((old >> shift) & 0xFFFFu) | bit;
+    const uint32_t old = atomicOr(&grid[word], bit << shift);
+    const uint32_t m16 = ((old >> shift) & (P10 ? 0x3FFu : 0xFFFFu)) | bit;
     const unsigned cnt = (unsigned)__popc(m16);
     if (cnt > best.cnt || (cnt == best.cnt && cell < best.cell)) {
         best.cnt = cnt;
         best.cell = cell;
         best.mask = m16;
     }
-    return (int)(cell >> 1);
+    return (int)word;
 }
 
 __device__ __forceinline__ void warp_best(Best &best)
@@ -393,7 +397,7 @@ __device__ __forceinline__ int small_pair_member(const SmallStage2 &sm, int n, i
 // K pairs per lane, v0 + 32 u for u < K, straight-line and independent of each other (an index
 // past the end is clamped and its result masked): a lone warp (few candidates) is bound by the
 // latency of this chain, not by issue.
-template <int K>
+template <int K, bool P10>
 __device__ __forceinline__ void vote_pairs(const Axes &ax, uint32_t *grid, const SmallStage2 &sm, int n, int total,
                                            int v0, Best &best, unsigned long long &votes)
 {
@@ -412,11 +416,12 @@ __device__ __forceinline__ void vote_pairs(const Axes &ax, uint32_t *grid, const
 #pragma unroll
     for (int u = 0; u < K; ++u)
         if (nz[u] >= 0) {
-            stage2_vote(ax, grid, m[u], nz[u], ly[u], best);
+            stage2_vote<P10>(ax, grid, m[u], nz[u], ly[u], best);
             ++votes;
         }
 }
 
+template <bool P10>
 __device__ void warp_stage2_small(const Axes &ax, const Workspace &w, const ColdHit *cold, uint32_t *grid,
                                   SmallStage2 &sm, const int *pos, int n, int i, Best &best,
                                   unsigned long long &votes, int &rlo, int &rhi)
@@ -450,19 +455,22 @@ __device__ void warp_stage2_small(const Axes &ax, const Workspace &w, const Cold
     // a masked four-pair round costs a full round's instructions however few pairs it holds
     constexpr int kIlp = 4;
     int base = 0;
-    for (; total - base > 64; base += 32 * kIlp) vote_pairs<kIlp>(ax, grid, sm, n, total, base + lane, best, votes);
-    for (; base < total; base += 32) vote_pairs<1>(ax, grid, sm, n, total, base + lane, best, votes);
+    for (; total - base > 64; base += 32 * kIlp)
+        vote_pairs<kIlp, P10>(ax, grid, sm, n, total, base + lane, best, votes);
+    for (; base < total; base += 32) vote_pairs<1, P10>(ax, grid, sm, n, total, base + lane, best, votes);
     __syncwarp();
 }
 
 // Zero the grid words of rows [rlo, rhi] (16-byte stores over a span rounded out to whole vectors:
-// the extra words are outside every touched cell and already zero).
+// the extra words hold only cells outside the touched rows, already zero).
+template <bool P10>
 __device__ __forceinline__ void clear_rows(const Axes &ax, uint32_t *grid, int rlo, int rhi)
 {
     if (rlo > rhi) return;
     const int lane = threadIdx.x & 31;
-    const int w0 = ((rlo * ax.n_z0) >> 1) & ~3;
-    const int w1 = (((((rhi + 1) * ax.n_z0 - 1) >> 1)) | 3) + 1;   // <= grid words (a multiple of 4)
+    const int c0 = rlo * ax.n_z0, c1 = (rhi + 1) * ax.n_z0 - 1;   // first and last cell
+    const int w0 = (P10 ? c0 / 3 : c0 >> 1) & ~3;
+    const int w1 = ((P10 ? c1 / 3 : c1 >> 1) | 3) + 1;   // <= grid words (a multiple of 4)
     uint4 *g4 = reinterpret_cast<uint4 *>(grid);
     for (int q = (w0 >> 2) + lane; q < (w1 >> 2); q += 32) g4[q] = make_uint4(0u, 0u, 0u, 0u);
 }
@@ -470,8 +478,11 @@ __device__ __forceinline__ void clear_rows(const Axes &ax, uint32_t *grid, int r
 // Membership and, for candidates of at most kSmallMembers members, stage 2: one warp per candidate
 // over all events' candidates.  Members go once, in the fixed order, to the member pool; a larger
 // candidate is filed for the CTA stage-2 kernel.
-__global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes ax, Workspace w, float s32, float refine_eps,
-                                                                        int grid_words)
+// P10: 10-bit masks, three to a word (at most 10 layers): a 64 x 64 grid takes 5.3 KB instead of
+// 8 KB, which with 64 registers a thread lets four CTAs share an SM instead of three.
+template <bool P10>
+__global__ void __launch_bounds__(kConfirmWarpsMax * 32, P10 ? 4 : 3)
+    member_kernel(Axes ax, Workspace w, float s32, float refine_eps, int grid_words)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_m[];
@@ -530,9 +541,9 @@ __global__ void __launch_bounds__(kConfirmWarpsMax * 32, 3) member_kernel(Axes a
                     member_coefficients(ax, w, hot, cold, pos[c0 + lane], i, &sm.a[lane], &sm.b[lane], &sm.mrl[lane],
                                         lay[c0 + lane]);
                 __syncwarp();
-                warp_stage2_small(ax, w, cold, grid, sm, pos + c0, nc, i, best, votes, rlo, rhi);
+                warp_stage2_small<P10>(ax, w, cold, grid, sm, pos + c0, nc, i, best, votes, rlo, rhi);
             }
-            clear_rows(ax, grid, rlo, rhi);
+            clear_rows<P10>(ax, grid, rlo, rhi);
             __syncwarp();
             warp_best(best);
 #pragma unroll
@@ -699,6 +710,9 @@ __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total
 
 int confirm_grid_words(const Axes &ax) { return (((ax.n_cot * ax.n_z0 + 1) >> 1) + 3) & ~3; }
 
+// Words of a warp's grid of 10-bit masks, three to a word, rounded up to whole 16-byte vectors.
+int packed_grid_words(const Axes &ax) { return (((ax.n_cot * ax.n_z0 + 2) / 3) + 3) & ~3; }
+
 
 }  // namespace
 
@@ -706,20 +720,41 @@ size_t stage2_smem_bytes(const Axes &ax) { return (size_t)confirm_grid_words(ax)
 
 namespace {
 
-// Resident CTAs per SM of a kernel at a dynamic shared-memory size, asked once per size (the
-// answer depends on the kernel and the device only; the library drives one device model).
+// Resident CTAs per SM of a kernel at a block size and dynamic shared-memory size, asked once per
+// pair (the answer depends on the kernel and the device only; the library drives one device model).
 template <typename K>
 int resident_ctas(K kernel, int threads, size_t smem, std::atomic<unsigned long long> &memo)
 {
+    const unsigned long long key = (unsigned long long)smem | ((unsigned long long)threads << 20);
     const unsigned long long m = memo.load(std::memory_order_relaxed);
-    if (m && (m >> 32) == (unsigned long long)smem) return (int)(m & 0xFFFFFFFFull);
+    if (m && (m >> 32) == key) return (int)(m & 0xFFFFFFFFull);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
-    memo.store(((unsigned long long)smem << 32) | (unsigned)n, std::memory_order_relaxed);
+    memo.store((key << 32) | (unsigned)n, std::memory_order_relaxed);
     return n;
 }
 
-std::atomic<unsigned long long> g_member_ctas{0}, g_large_ctas{0};
+std::atomic<unsigned long long> g_member_ctas{0}, g_member_p10_ctas{0}, g_large_ctas{0};
+std::atomic<int> g_member_static{-1}, g_smem_optin{-1};
+
+// Warps per member CTA: kConfirmWarpsMax, or as many as shared memory holds when each warp's grid
+// is large (n_cot * n_z0 up to 16384 cells, 32 KB a warp).
+int member_warps(size_t grid_bytes)
+{
+    if (g_member_static.load(std::memory_order_relaxed) < 0) {
+        cudaFuncAttributes fa{};
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        if (cudaFuncGetAttributes(&fa, member_kernel<false>) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return kConfirmWarpsMax;   // the launch itself then reports what is wrong
+        g_smem_optin.store(optin, std::memory_order_relaxed);
+        g_member_static.store((int)fa.sharedSizeBytes, std::memory_order_relaxed);
+    }
+    const long long room = (long long)g_smem_optin.load(std::memory_order_relaxed) -
+                           (long long)g_member_static.load(std::memory_order_relaxed);
+    return (int)std::max(1LL, std::min((long long)kConfirmWarpsMax, room / (long long)std::max<size_t>(grid_bytes, 1)));
+}
 
 }  // namespace
 
@@ -730,21 +765,30 @@ cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float ref
     // the number of candidates is known on the device only: persistent grids of exactly the
     // resident CTAs, each warp or CTA striding over the flattened (event, candidate) work
     const size_t large_smem = (size_t)confirm_grid_words(ax) * 4;
-    const size_t member_smem = kConfirmWarpsMax * large_smem;
-    cudaError_t err = cudaFuncSetAttribute(member_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)member_smem);
-    if (!err) err = cudaFuncSetAttribute(member_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+    // a warp's grid: 10-bit masks three to a word when the layers fit and a batch of events keeps
+    // every warp busy (the fourth CTA an SM then holds is worth more than the 64-register cap
+    // costs); otherwise, and for one event, whose candidates are spread one to a CTA and whose
+    // time is one warp's chain, 16-bit masks and 80 registers
+    const bool p10 = ax.n_layers <= 10 && w.n_events > 1;
+    const int words = p10 ? packed_grid_words(ax) : confirm_grid_words(ax);
+    const int warps = member_warps((size_t)words * 4);
+    const size_t member_smem = (size_t)warps * words * 4;
+    auto member = p10 ? member_kernel<true> : member_kernel<false>;
+    cudaError_t err = cudaFuncSetAttribute(member, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)member_smem);
+    if (!err) err = cudaFuncSetAttribute(member, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
     if (err) return err;
-    const int threads = kConfirmWarpsMax * 32;
-    const int member_ctas = resident_ctas(member_kernel, threads, member_smem, g_member_ctas);
-    if ((err = launch_chained(member_kernel, dim3(member_ctas * sms), dim3(threads), member_smem, stream, ax, w, s32,
-                              refine_eps, confirm_grid_words(ax))))
+    const int member_threads = warps * 32;
+    const int member_ctas = resident_ctas(member, member_threads, member_smem, p10 ? g_member_p10_ctas : g_member_ctas);
+    if ((err = launch_chained(member, dim3(member_ctas * sms), dim3(member_threads), member_smem, stream, ax, w, s32,
+                              refine_eps, words)))
         return err;
     if (between && (err = cudaEventRecord(between, stream))) return err;
     err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large_smem);
     if (!err) err = cudaFuncSetAttribute(stage2_large_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
     if (err) return err;
+    const int threads = kConfirmWarpsMax * 32;
     const int large_ctas = resident_ctas(stage2_large_kernel, threads, large_smem, g_large_ctas);
     return launch_chained(stage2_large_kernel, dim3(large_ctas * sms), dim3(threads), large_smem, stream, ax, w, s32,
                           refine_eps);

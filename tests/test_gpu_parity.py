@@ -193,6 +193,26 @@ def test_odd_sizes_and_few_layers(binding):
     check_event(binding, g, bn, ev)
 
 
+@pytest.mark.parametrize("n_cot,n_z0,dense", [(128, 128, True), (256, 64, False), (64, 256, False)])
+def test_largest_stage2_grids(binding, n_cot, n_z0, dense):
+    """Stage-2 grids of the largest size accepted (16,384 cells: 32 KB of masks for each
+    confirming warp, so fewer warps share a CTA), on the pileup event cut to 30,000 hits (many
+    candidates per CTA) and on a 50-track event."""
+    w = eg.WORKLOADS["pileup_100k" if dense else "single_50trk"]
+    ev = w.event(1).subset(np.arange(30000)) if dense else w.event(1)
+    bn = eg.with_binning(w, n_cot=n_cot, n_z0=n_z0).binning
+    r = check_event(binding, w.geometry, bn, ev)
+    assert r["stage2_checked"] > (200 if dense else 20)
+    # the same event in a batch (where a detector of ten layers takes the packed 10-bit grids)
+    other = w.event(2).subset(np.arange(min(w.event(2).n_hits, 20000)))
+    events = [other, ev]
+    with binding.HoughBatch(w.geometry, bn, max_events=2, max_hits=other.n_hits + ev.n_hits) as b:
+        b.run_events(events)
+        cands, offs = b.candidates()
+    assert np.array_equal(cands[offs[1]:offs[2]], r["got"]["candidates"])
+    assert np.array_equal(cands[offs[0]:offs[1]], run_gpu(binding, w.geometry, bn, other)["candidates"])
+
+
 def test_candidate_capacity_truncates_in_raster_order(binding):
     w = eg.WORKLOADS["single_50trk"]
     ev = w.event(0)
