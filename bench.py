@@ -16,7 +16,8 @@ hough_process from pinned host buffers: host->device copy of the hits, the path,
 device->host read of the candidate list, timed on the host around each call), `scatter_mode`
 (the paper's shared-atomic vote design in place of the gather vote), `count_accumulator` (cells
 holding vote counts, the paper's literal A[B[i]] += 1, on the pileup event and the paper's grid),
-`d0_axis` (non-prompt tracks on a (d0, q/pT, phi0) grid),
+`d0_axis` (non-prompt tracks on a (d0, q/pT, phi0) grid), `fused_vote_peak` (the vote and the
+peak search in one kernel, the accumulator kept in shared memory, against the separate kernels),
 `paper_sweep` (the paper's Fig. 2 experiment) and `cpu_baseline` (the FP64 oracle on this
 machine's host cores, on a bounded sample).
 
@@ -71,7 +72,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-events", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--only", choices=["all", "plain", "batched", "served", "paper_sweep", "counts", "d0"],
+    ap.add_argument("--only", choices=["all", "plain", "batched", "served", "paper_sweep", "counts", "d0", "fused"],
                     default="all",
                     help="run one part only (for profiling); the default runs everything")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -682,6 +683,73 @@ def measure_d0(env, args, smem_peak=None, hbm_peak=None):
             "counts": _plain_variant(env, args, wc, text.format("vote counts"), smem_peak, hbm_peak)}
 
 
+def measure_fused(env, args):
+    """The fused vote and peak search (vote_mode HOUGH_VOTE_FUSED: the accumulator stays in shared
+    memory) against the default separate kernels: the plain step on the pileup event for a sweep
+    of band heights and block sizes, and a 64-event batch of the batch workload; L2 flushed before
+    every timed step.  The fused candidates are checked equal to the default ones."""
+    torch, binding, stream = env.torch, env.binding, env.stream
+    w = eg.WORKLOADS["pileup_100k"]
+    ev = w.event(replicas.event_indices(env.rank, env.world, 1)[0])
+    tens = [torch.from_numpy(np.ascontiguousarray(a)).to(env.dev) for a in (ev.r, ev.phi, ev.z, ev.layer)]
+
+    def timed(step, k):
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for q in range(k):
+            env.flush.zero_()
+            e0[q].record(stream)
+            step()
+            e1[q].record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in zip(e0, e1))
+
+    plain = {}
+    with binding.HoughContext(w.geometry, w.binning, max_hits=ev.n_hits, max_candidates=1 << 18,
+                              max_members=1 << 23, device=env.local) as ctx:
+        def step():
+            ctx.vote(*tens, n_hits=ev.n_hits, where=binding.DEVICE, stream=stream)
+            ctx.peaks(stream=stream)
+            ctx.stage2(stream=stream)
+        base = ctx.get_tiling()
+        k = max(10, min(args.steps, 50))
+        plain["default"] = timed(step, k)
+        ref = ctx.candidates(stream=stream).copy()
+        same = True
+        for r in (2, 4, 8):
+            for th in (512, 1024):
+                ctx.set_tiling(**{**base, "vote_mode": binding.VOTE_FUSED, "band_rows": r, "gather_threads": th})
+                plain[f"fused band_rows={r} threads={th}"] = timed(step, k)
+                same = same and np.array_equal(ctx.candidates(stream=stream), ref)
+    best = min((v, name) for name, v in plain.items() if name != "default")
+    wb = eg.WORKLOADS["batch_256"]
+    events = [wb.event(i) for i in replicas.event_indices(env.rank, env.world, 64)]
+    hs = np.zeros(len(events) + 1, dtype=np.int64)
+    hs[1:] = np.cumsum([e.n_hits for e in events])
+    cat = lambda name, dt: torch.from_numpy(np.concatenate([getattr(e, name) for e in events]).astype(dt)).to(env.dev)
+    bt = [cat("r", np.float32), cat("phi", np.float32), cat("z", np.float32), cat("layer", np.uint8)]
+    batch = {}
+    with binding.HoughBatch(wb.geometry, wb.binning, max_events=len(events), max_hits=int(hs[-1]),
+                            device=env.local) as b:
+        def bstep():
+            b.run(*bt, hs, where=binding.DEVICE, stream=stream)
+        for name, kw in (("default", {}), ("fused band_rows=8 threads=512", dict(vote_mode=binding.VOTE_FUSED, band_rows=8,
+                                                                                 gather_threads=512)),
+                         ("fused band_rows=16 threads=512", dict(vote_mode=binding.VOTE_FUSED, band_rows=16,
+                                                                 gather_threads=512))):
+            b.set_tiling(**kw)
+            batch[name] = timed(bstep, 5)
+    return {"workload": WORKLOAD_TEXT["pileup_100k"] + "; and 64 events of the batch workload",
+            "plain_ms_per_event": plain, "best_fused": best[1], "best_fused_vs_default": best[0] / plain["default"],
+            "fused_candidates_equal_default": bool(same),
+            "batch64_ms_per_batch": batch,
+            "note": "vote_mode HOUGH_VOTE_FUSED computes each band of full rows with its two halo rows in shared "
+                    "memory and searches it there; the accumulator is not written"}
+
+
 def measure_e2e(env, args, ctx, ev):
     """hough_process from pinned host buffers: hits to the device, the path, candidates back."""
     torch, stream = env.torch, env.stream
@@ -712,9 +780,9 @@ def main():
         return
     env = Env()
     binding = env.binding
-    if args.only in ("batched", "served", "paper_sweep", "counts", "d0"):
+    if args.only in ("batched", "served", "paper_sweep", "counts", "d0", "fused"):
         out = {"batched": measure_batched, "served": measure_served, "paper_sweep": measure_paper_sweep,
-               "counts": measure_counts, "d0": measure_d0}[args.only](env, args)
+               "counts": measure_counts, "d0": measure_d0, "fused": measure_fused}[args.only](env, args)
         if env.rank == 0:
             print(json.dumps({"metric": METRIC, "part": args.only, **out}), flush=True)
         return
@@ -741,7 +809,7 @@ def main():
         peaks, peaks_kind = measured_peaks()
         hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
         if args.only == "plain":
-            batched = e2e = served = paper = counts = d0 = None
+            batched = e2e = served = paper = counts = d0 = fused = None
         else:
             batched = measure_batched(env, args)
             e2e = measure_e2e(env, args, ctx, ev)
@@ -749,6 +817,7 @@ def main():
             paper = measure_paper_sweep(env, args) if env.rank == 0 else None
             counts = measure_counts(env, args, smem_peak, hbm_peak)
             d0 = measure_d0(env, args, smem_peak, hbm_peak)
+            fused = measure_fused(env, args)
     clocks = clock_sampler.summary()
     kernels = kernel_table(env, w, n, plain, smem_peak, hbm_peak, peaks_kind, clocks)
     dominant = max(kernels, key=lambda k: kernels[k]["ms"])
@@ -793,6 +862,7 @@ def main():
         "paper_sweep": paper,
         "count_accumulator": counts,
         "d0_axis": d0,
+        "fused_vote_peak": fused,
         "e2e": e2e,
         "gpu_launches": plain["launches"],
         "clocks": clocks,

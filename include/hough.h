@@ -216,7 +216,8 @@ int hough_stage2(hough_ctx *ctx, void *stream);
 int hough_get_candidates(hough_ctx *ctx, hough_candidate *out, int32_t cap, int32_t *n_out,
                          int where, void *stream);
 
-/* Copy the (stacked) rows x n_phi row-major accumulator of the last vote.  Synchronises `stream`. */
+/* Copy the (stacked) rows x n_phi row-major accumulator of the last vote.  Synchronises `stream`.
+ * HOUGH_ENOTREADY under vote_mode HOUGH_VOTE_FUSED, which does not keep it. */
 int hough_get_accumulator(hough_ctx *ctx, uint16_t *out, int where, void *stream);
 
 /*
@@ -255,6 +256,14 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
  * radii are added by the shared-atomic scatter kernel.
  * vote_mode HOUGH_VOTE_SCATTER: every layer by the shared-atomic scatter kernel (Sec. 6.1), each
  * CTA owning a tile of tile_qpt rows x tile_phi columns in shared memory.
+ * vote_mode HOUGH_VOTE_FUSED (layer masks without a d0 axis): the gather and the peak search in
+ * one kernel, a CTA (gather_threads threads) per band of band_rows full rows, which computes the
+ * band's cells and those of the row above and below it into shared memory and searches the band
+ * for peaks there: the accumulator is neither written to nor read back from device memory, and
+ * hough_get_accumulator / hough_batch_accumulator return HOUGH_ENOTREADY.  When a layer's hits
+ * lie at several radii the scatter kernel must add its votes first; the fused kernel then writes
+ * the band's rows and the peak kernel runs as in the other modes.  Needs (band_rows + 2) *
+ * n_phi * 2 bytes of shared memory.
  * The peak search works on bands of band_rows rows.
  *
  * With the count accumulator the gather counts its tile of gather_rows x gather_cols cells in
@@ -272,6 +281,7 @@ int hough_process(hough_ctx *ctx, const float *r, const float *phi, const float 
  */
 #define HOUGH_VOTE_GATHER  0
 #define HOUGH_VOTE_SCATTER 1
+#define HOUGH_VOTE_FUSED   2
 
 typedef struct hough_tiling {
     int32_t tile_qpt;
@@ -292,8 +302,8 @@ int hough_get_tiling(const hough_ctx *ctx, hough_tiling *tiling);
  * call was given (enabled by hough_enable_timing; off by default).  stage_ms: hit staging;
  * vote_ms: the vote (= gather_ms + scatter_ms); peaks_ms: peak search (= band_peaks_ms +
  * compact_ms); stage2_ms: membership and the stage-2 vote.  gather_ms covers the gather kernel
- * (with the fused peak search); scatter_ms the shared-atomic kernel; band_peaks_ms the standalone
- * peak kernel; compact_ms the candidate scan.  hough_get_timing synchronises; HOUGH_ENOTREADY
+ * (with HOUGH_VOTE_FUSED, the fused vote and peak search); scatter_ms the shared-atomic kernel;
+ * band_peaks_ms the standalone peak kernel; compact_ms the candidate scan.  hough_get_timing synchronises; HOUGH_ENOTREADY
  * before a timed event.
  */
 typedef struct hough_timing {
@@ -365,7 +375,8 @@ int hough_batch_candidates(hough_batch *batch, hough_candidate *out, int64_t cap
 /* Counters of one event of the last run.  Synchronises `stream`. */
 int hough_batch_stats(hough_batch *batch, int32_t event, hough_stats *out, void *stream);
 
-/* The accumulator of one event of the last run.  Synchronises `stream`. */
+/* The accumulator of one event of the last run.  Synchronises `stream`.  HOUGH_ENOTREADY under
+ * vote_mode HOUGH_VOTE_FUSED. */
 int hough_batch_accumulator(hough_batch *batch, int32_t event, uint16_t *out, int where, void *stream);
 
 /*

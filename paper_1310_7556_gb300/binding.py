@@ -75,7 +75,7 @@ class Tiling(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in TILING_FIELDS]
 
 
-VOTE_GATHER, VOTE_SCATTER = 0, 1
+VOTE_GATHER, VOTE_SCATTER, VOTE_FUSED = 0, 1, 2
 ACC_LAYERS, ACC_COUNTS = 0, 1   # hough_binning.accumulator: layer masks, saturating vote counts
 
 

@@ -79,8 +79,8 @@ struct hough_batch {
     {
         cudaError_t e;
         if ((e = launch_stage(ax, w, s))) return e;
-        if (tiling.vote_mode == HOUGH_VOTE_GATHER && (e = launch_gather(ax, w, tiling, s))) return e;
-        if ((e = launch_scatter(ax, w, tiling, refine_eps, tiling.vote_mode == HOUGH_VOTE_GATHER, s))) return e;
+        if (tiling.vote_mode != HOUGH_VOTE_SCATTER && (e = launch_gather(ax, w, tiling, s))) return e;
+        if ((e = launch_scatter(ax, w, tiling, refine_eps, tiling.vote_mode != HOUGH_VOTE_SCATTER, s))) return e;
         if ((e = launch_band_peaks(ax, w, tiling, s))) return e;
         if ((e = launch_compact(ax, w, s))) return e;
         return launch_stage2(ax, w, sms, refine_eps, s);
@@ -150,6 +150,7 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     w.inputs = b->inputs_dev;
     w.band_rows = b->tiling.band_rows;
     w.band_cap = band_capacity(ax, b->tiling.band_rows);
+    w.fused = b->tiling.vote_mode == HOUGH_VOTE_FUSED;
     std::vector<float> kq(ax.n_qpt);
     for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
     A(cudaMemcpy(w.kq32, kq.data(), sizeof(float) * ax.n_qpt, cudaMemcpyHostToDevice));
@@ -177,6 +178,7 @@ int hough_batch_set_tiling(hough_batch *b, const hough_tiling *t)
     b->tiling = resolve_tiling(b->ax, t);
     b->w.band_rows = t->band_rows;
     b->w.band_cap = band_capacity(b->ax, t->band_rows);
+    b->w.fused = b->tiling.vote_mode == HOUGH_VOTE_FUSED;
     // captured graphs hold the old configuration
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
@@ -358,6 +360,7 @@ int hough_batch_accumulator(hough_batch *b, int32_t event, uint16_t *out, int wh
     if (!b->ran) return bfail(HOUGH_ENOTREADY, "hough_batch_run has not run");
     if (event < 0 || event >= b->n_events) return bfail(HOUGH_EINVAL, "event out of range");
     if (where != HOUGH_HOST && where != HOUGH_DEVICE) return bfail(HOUGH_EINVAL, "bad where");
+    if (b->w.fused) return bfail(HOUGH_ENOTREADY, "the fused vote and peak search does not keep the accumulator");
     BCU(cudaSetDevice(b->device), "cudaSetDevice failed");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t cells = (size_t)b->ax.n_qpt * b->ax.n_phi;

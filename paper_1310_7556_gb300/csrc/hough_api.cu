@@ -197,8 +197,10 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
         return fail(HOUGH_EINVAL, "tile_phi must be a multiple of 64 dividing n_phi");
     if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
         return fail(HOUGH_EINVAL, "threads must be 128, 256, 512 or 1024");
-    if (t->vote_mode != HOUGH_VOTE_GATHER && t->vote_mode != HOUGH_VOTE_SCATTER)
-        return fail(HOUGH_EINVAL, "vote_mode must be HOUGH_VOTE_GATHER or HOUGH_VOTE_SCATTER");
+    if (t->vote_mode != HOUGH_VOTE_GATHER && t->vote_mode != HOUGH_VOTE_SCATTER && t->vote_mode != HOUGH_VOTE_FUSED)
+        return fail(HOUGH_EINVAL, "vote_mode must be HOUGH_VOTE_GATHER, HOUGH_VOTE_SCATTER or HOUGH_VOTE_FUSED");
+    if (t->vote_mode == HOUGH_VOTE_FUSED && (ax.counts || ax.n_d0))
+        return fail(HOUGH_EINVAL, "HOUGH_VOTE_FUSED needs the layer accumulator and no d0 axis");
     if (t->band_rows < 1 || t->band_rows > 16) return fail(HOUGH_EINVAL, "band_rows must be 1..16");
     if (t->gather_rows < 0 || t->gather_rows > 32) return fail(HOUGH_EINVAL, "gather_rows must be 0..32");
     if (t->gather_cols && (t->gather_cols < 64 || t->gather_cols % 64 || ax.n_phi % t->gather_cols))
@@ -222,6 +224,10 @@ int check_tiling_impl(const Axes &ax, int device, const hough_tiling *t)
     if (gather_smem_bytes(ax, tt) + 1024 > (size_t)max_smem)
         return fail(HOUGH_EINVAL, "gather tile needs %zu bytes of shared memory, the device allows %d",
                     gather_smem_bytes(ax, tt), max_smem);
+    // the fused kernel's band of masks, plus its row tables (5 KB) in static shared memory
+    if (t->vote_mode == HOUGH_VOTE_FUSED && fused_smem_bytes(ax, t->band_rows) + 6144 + 1024 > (size_t)max_smem)
+        return fail(HOUGH_EINVAL, "fused band of %d rows needs %zu bytes of shared memory, the device allows %d",
+                    t->band_rows, fused_smem_bytes(ax, t->band_rows), max_smem);
     return HOUGH_OK;
 }
 
@@ -342,12 +348,13 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     c->timed = 0;
     c->w.band_rows = c->tiling.band_rows;
     c->w.band_cap = band_capacity(c->ax, c->tiling.band_rows);
+    c->w.fused = c->tiling.vote_mode == HOUGH_VOTE_FUSED;
     if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1 | (0xF << 8); }
     CU(launch_stage(c->ax, c->w, s, c->timing ? c->ev + 8 : nullptr), "stage kernels");
     if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
-    if (c->tiling.vote_mode == HOUGH_VOTE_GATHER) CU(launch_gather(c->ax, c->w, c->tiling, s), "gather kernel");
+    if (c->tiling.vote_mode != HOUGH_VOTE_SCATTER) CU(launch_gather(c->ax, c->w, c->tiling, s), "gather kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
-    CU(launch_scatter(c->ax, c->w, c->tiling, c->refine_eps, c->tiling.vote_mode == HOUGH_VOTE_GATHER, s), "vote kernel");
+    CU(launch_scatter(c->ax, c->w, c->tiling, c->refine_eps, c->tiling.vote_mode != HOUGH_VOTE_SCATTER, s), "vote kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[3], s), "event"); c->timed |= 8; }
     g_launches += kStageLaunches + (c->tiling.vote_mode == HOUGH_VOTE_SCATTER ? 1 : kVoteLaunches);
     c->stage = 1;
@@ -464,6 +471,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     w.inputs = nullptr;
     w.band_rows = c->tiling.band_rows;
     w.band_cap = band_capacity(ax, c->tiling.band_rows);
+    w.fused = 0;
     // FP32 q/pT bin centres: the FP64 centre rounded once
     std::vector<float> kq(ax.n_qpt);
     for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
@@ -546,6 +554,7 @@ int hough_get_accumulator(hough_ctx *c, uint16_t *out, int where, void *stream)
     if (!c || !out) return fail(HOUGH_EINVAL, "bad arguments");
     if (where != HOUGH_HOST && where != HOUGH_DEVICE) return fail(HOUGH_EINVAL, "bad where");
     if (c->stage < 1) return fail(HOUGH_ENOTREADY, "hough_vote has not run");
+    if (c->w.fused) return fail(HOUGH_ENOTREADY, "the fused vote and peak search does not keep the accumulator");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(out, c->w.M, sizeof(uint16_t) * (size_t)c->ax.n_qpt * c->ax.n_phi,

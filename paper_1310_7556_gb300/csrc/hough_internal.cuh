@@ -160,12 +160,13 @@ struct Workspace {
     DevStats *stats;              // n_events
     int max_cand, max_members;
     int band_rows, band_cap;
+    int fused;                    // vote_mode HOUGH_VOTE_FUSED: the vote kernel searched the bands
 };
 
 // Vote-kernel configuration.
 struct Tiling {
     int tile_qpt, tile_phi, threads;
-    int vote_mode;                // HOUGH_VOTE_GATHER or HOUGH_VOTE_SCATTER
+    int vote_mode;                // HOUGH_VOTE_GATHER, HOUGH_VOTE_SCATTER or HOUGH_VOTE_FUSED
     int band_rows;                // rows per band of the peak search
     int gather_rows, gather_cols, gather_threads;   // tile of the gather kernel (0: its default)
 };
@@ -235,6 +236,8 @@ Tiling default_tiling_for(const Axes &ax);
 Tiling resolve_tiling(const Axes &ax, const hough_tiling *t);   // gather defaults filled in
 void public_tiling(const Tiling &t, hough_tiling *out);
 size_t gather_smem_bytes(const Axes &ax, const Tiling &t);
+// Dynamic shared memory of the fused vote and peak kernel: the band's masks and its two halo rows.
+size_t fused_smem_bytes(const Axes &ax, int band_rows);
 // Shared memory of the count accumulator's gather kernel.
 size_t gather_count_smem_bytes(const Axes &ax, const Tiling &t);
 size_t band_list_entries(const Axes &ax);
@@ -508,10 +511,13 @@ __device__ __forceinline__ int wrap_col(int j, int n)
 // rows each -- slice m - 1, the band's own, slice m + 1 -- the band's rows in the middle one; the
 // nine neighbours of slice m - 1 precede a cell in raster order (strictly lower), the nine of
 // slice m + 1 follow it (not higher).
-template <int TPB, typename V, bool D3 = false>
+// MASKS: the staged values are the cells' layer masks themselves (compared by their layer counts,
+// and written out from shared memory, M unused).
+template <int TPB, typename V, bool D3 = false, bool MASKS = false>
 __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, int nphi, int threshold,
                                                 const uint16_t *M, uint2 *out, int cap)
 {
+    auto val = [](V x) -> int { return MASKS ? __popc((unsigned)x) : (int)x; };
     __shared__ int s_warp[TPB / 32];
     __shared__ int s_total;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -531,11 +537,11 @@ __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, 
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int j = j0 + c;
-                const int p = row[j];
+                const int p = val(row[j]);
                 if (p >= threshold) {
                     const int jm = wrap_col(j - 1, nphi), jp = wrap_col(j + 1, nphi);
-                    bool peak = up[jm] < p && up[j] < p && up[jp] < p && row[jm] < p &&
-                                row[jp] <= p && dn[jm] <= p && dn[j] <= p && dn[jp] <= p;
+                    bool peak = val(up[jm]) < p && val(up[j]) < p && val(up[jp]) < p && val(row[jm]) < p &&
+                                val(row[jp]) <= p && val(dn[jm]) <= p && val(dn[j]) <= p && val(dn[jp]) <= p;
                     if (D3) {
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
@@ -576,7 +582,8 @@ __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, 
             const int c = __ffs(pk) - 1;
             pk &= pk - 1u;
             const unsigned cellg = (unsigned)(i0 + rr) * (unsigned)nphi + (unsigned)(j0 + c);
-            if (idx < cap) out[idx] = make_uint2(cellg, (unsigned)M[cellg]);
+            if (idx < cap)
+                out[idx] = make_uint2(cellg, MASKS ? (unsigned)pc[(rr + 1) * nphi + j0 + c] : (unsigned)M[cellg]);
             ++idx;
         }
         running += s_total;

@@ -35,6 +35,7 @@
 // raster order; a per-event scan then concatenates the band lists into the raster-ordered list.
 // With a d0 axis a band lies in one slice and its cells take the 3 x 3 x 3 rule (peaks3_kernel).
 #include <algorithm>
+#include <atomic>
 #include <climits>
 
 #include "hough_internal.cuh"
@@ -493,6 +494,152 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
 }
 
 
+// Fused vote and peak search (vote_mode HOUGH_VOTE_FUSED): a CTA per band of band_rows full rows.
+// A cell of a layer of one radius is a function of its row's table entry and two bucket-profile
+// entries alone, so the CTA computes the band's masks and those of the row above and below it
+// (the 3 x 3 neighbourhoods; phi wraps within the full rows) into shared memory, searches the
+// band for peaks there and writes the band's candidate list and count as the peak kernel does --
+// the accumulator never goes to device memory.  Full rows read every bucket of a layer, so when
+// they fit (STAGE) the voting layers' whole profiles are first copied into shared memory with bulk
+// asynchronous copies; otherwise they are read through the cache.  When a present layer's hits lie at several radii
+// the scatter kernel adds that layer's votes afterwards: the CTA then writes the band's rows to
+// the accumulator instead, and the peak kernel searches it.
+
+__device__ __forceinline__ bool all_layers_uniform(const Axes &ax, const Workspace &w)
+{
+    for (int l = 0; l < ax.n_layers; ++l) {
+        const LayerInfo li = w.info[l];
+        if (li.present && !li.uniform) return false;
+    }
+    return true;
+}
+
+template <int NL, int TPB, bool STAGE>
+__global__ void __launch_bounds__(TPB) fused_kernel(GatherParams p)
+{
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char fused_smem[];
+    __shared__ int rowI[kGatherRowsMax * 16];
+    __shared__ unsigned rowG[kGatherRowsMax * 16];
+    __shared__ unsigned rowMask[kGatherRowsMax];
+    __shared__ __align__(8) uint64_t s_bar;
+    const Axes &ax = p.ax;
+    const Workspace &w = p.w;
+    const int nb = p.tiles_per_event;
+    const int e = blockIdx.x / nb, band = blockIdx.x - e * nb;
+    const int R = p.rows, i0 = band * R;
+    const int nrows = min(R, ax.n_qpt - i0);
+    const int L = ax.n_layers, nphi = ax.n_phi;
+    const bool search = all_layers_uniform(ax, w);
+    // computed rows: i0 - 1 .. i0 + nrows (halo included) when searching, else the band's own
+    const int first = search ? i0 - 1 : i0;
+    const int S = search ? nrows + 2 : nrows;
+    for (int q = threadIdx.x; q < ((S * 16 + 31) & ~31); q += TPB) {
+        const int s = q >> 4, l = q & 15, i = first + s;
+        int I = 0;
+        unsigned gb = 0u, valid = 0u;
+        if (l < L && s < S && i >= 0 && i < ax.n_qpt) {   // rows outside the grid hold no votes
+            const LayerInfo li = w.info[l];
+            if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
+                const TabEntry te = w.tab[l * ax.n_qpt + i];
+                if (te.I != kNoVote) {
+                    I = te.I;
+                    gb = __float_as_uint(te.g);
+                    valid = 1u;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, valid) >> (threadIdx.x & 16);
+        rowI[q] = I;
+        rowG[q] = gb;
+        if ((threadIdx.x & 15) == 0) rowMask[s] = m & 0xFFFFu;
+    }
+    __syncthreads();
+    constexpr bool stage = STAGE;
+    const uint2 *prof = w.prof + (int64_t)e * prof_event_entries(ax);
+    const int pstride = prof_stride(ax);
+    uint2 *win = reinterpret_cast<uint2 *>(fused_smem);   // staged: layer l's profile at l * n_phi
+    uint16_t *tm = reinterpret_cast<uint16_t *>(fused_smem + (stage ? (size_t)L * nphi * sizeof(uint2) : 0));
+    unsigned used = 0u;   // layers voting on any computed row
+    for (int q = 0; q < S; ++q) used |= rowMask[q];
+    if (stage && used) {
+        if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect(&s_bar, (unsigned)__popc(used) * (unsigned)nphi * 8u);
+            for (int l = 0; l < L; ++l)
+                if ((used >> l) & 1u)
+                    bulk_copy_g2s(win + (int64_t)l * nphi, prof + (int64_t)l * pstride, 8u * (unsigned)nphi, &s_bar);
+        }
+        const bool ok = mbar_wait_bounded(&s_bar, 0, kCopyWaitCycles);
+        if (!__syncthreads_and(ok)) {
+            // the copies did not land in time: report it, give them one more bound, find nothing
+            if (threadIdx.x == 0) {
+                atomicOr(&w.stats[e].device_error, HOUGH_DEVERR_TIMEOUT);
+                if (search) w.band_counts[(int64_t)e * nb + band] = 0;
+            }
+            mbar_wait_bounded(&s_bar, 0, kCopyWaitCycles);
+            return;
+        }
+    }
+    // a warp per strip of 256 cells of a row (the last strip of a row may be shorter: n_phi is a
+    // multiple of 64), lane t taking cells t, t + 32, ...; a layer's bit of cell j compares the
+    // profile entry j + I of that layer
+    constexpr int kCells = 8;
+    const int per_row = (nphi + 32 * kCells - 1) / (32 * kCells);
+    const int lane = threadIdx.x & 31;
+    for (int sidx = threadIdx.x >> 5; sidx < S * per_row; sidx += TPB / 32) {
+        const int s = sidx / per_row;
+        const int jb = (sidx - s * per_row) * 32 * kCells + lane;
+        const unsigned vm = rowMask[s];
+        unsigned mask[kCells];
+#pragma unroll
+        for (int c = 0; c < kCells; ++c) mask[c] = 0u;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            if (!((vm >> l) & 1u)) continue;   // the same for the whole warp: the row's layers
+            const int I = rowI[s * 16 + l];
+            const unsigned gb = rowG[s * 16 + l], ngb = ~gb;
+            if (stage) {
+                const uint2 *src = win + (int64_t)l * nphi;
+#pragma unroll
+                for (int c = 0; c < kCells; ++c)
+                    if (jb + 32 * c < nphi) {
+                        const uint2 v = src[wrap_col(jb + 32 * c + I, nphi)];
+                        mask[c] |= (unsigned)((v.x > gb) | (v.y > ngb)) << l;
+                    }
+            } else {
+                const uint2 *src = prof + (int64_t)l * pstride;
+#pragma unroll
+                for (int c = 0; c < kCells; ++c)
+                    if (jb + 32 * c < nphi) {
+                        const uint2 v = __ldg(&src[wrap_col(jb + 32 * c + I, nphi)]);
+                        mask[c] |= (unsigned)((v.x > gb) | (v.y > ngb)) << l;
+                    }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kCells; ++c)
+            if (jb + 32 * c < nphi) tm[s * nphi + jb + 32 * c] = (uint16_t)mask[c];
+    }
+    __syncthreads();
+    if (!search) {
+        // the scatter adds the other layers' votes: hand the band's rows to the peak kernel
+        uint16_t *M = w.M + (int64_t)e * ax.n_qpt * nphi;
+        const int v8 = nphi >> 3;
+        for (int q = threadIdx.x; q < nrows * v8; q += TPB) {
+            const int rr = q / v8, c8 = q - rr * v8;
+            *reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + c8 * 8) =
+                *reinterpret_cast<const uint4 *>(tm + rr * nphi + c8 * 8);
+        }
+        return;
+    }
+    uint2 *out = w.band_cands + ((int64_t)e * nb + band) * w.band_cap;
+    const int cnt = band_peak_search<TPB, uint16_t, false, true>(tm, nrows, i0, nphi, ax.threshold, nullptr, out,
+                                                                 w.band_cap);
+    if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+}
+
 // Count accumulator by gather.  On row i a layer of one radius adds to cell j the hits of bucket
 // J' = (j + I_i) mod Nphi with f >= g_i and the hits of bucket J' + 1 with f < g_i: exactly the
 // hits whose vote J - I_i - (f < g_i) is j, by the same FP32 comparison, so the same counts as the
@@ -655,6 +802,7 @@ template <bool COUNTS>
 __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w)
 {
     pdl_enter();
+    if (!COUNTS && w.fused && all_layers_uniform(ax, w)) return;   // the fused vote searched the bands
     extern __shared__ __align__(16) unsigned char pc[];
     const int R = w.band_rows;
     const int nb = n_bands(ax, R);
@@ -991,6 +1139,26 @@ cudaError_t launch_gather_nl(const GatherParams &p, int threads, size_t smem, in
     }
 }
 
+size_t fused_smem_bytes(const Axes &ax, int band_rows)
+{
+    return (size_t)(band_rows + 2) * ax.n_phi * sizeof(uint16_t);
+}
+
+// Whether the fused kernel's CTA also holds every layer's whole bucket profile (8 bytes a bucket)
+// beside its masks and row tables.
+bool fused_stages_profiles(const Axes &ax, int band_rows)
+{
+    static std::atomic<int> optin{0};
+    int m = optin.load(std::memory_order_relaxed);
+    if (!m) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&m, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+        optin.store(m, std::memory_order_relaxed);
+    }
+    return fused_smem_bytes(ax, band_rows) + (size_t)ax.n_layers * ax.n_phi * sizeof(uint2) + 6144 + 1024 <= (size_t)m;
+}
+
 size_t gather_smem_bytes(const Axes &ax, const Tiling &t)
 {
     return (size_t)ax.n_layers * (size_t)(t.gather_cols + 64) * sizeof(uint2);
@@ -1015,6 +1183,44 @@ static cudaError_t launch_gather_tiled(const Axes &ax, const Workspace &w, const
     return launch_gather_nl<16>(p, t.gather_threads, smem, blocks, stream);
 }
 
+template <int NL, int TPB>
+cudaError_t launch_fused_tpb(const GatherParams &p, size_t smem, int blocks, cudaStream_t stream)
+{
+    auto kernel = p.cap ? fused_kernel<NL, TPB, true> : fused_kernel<NL, TPB, false>;
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err) return err;
+    return launch_chained(kernel, dim3(blocks), dim3(TPB), smem, stream, p);
+}
+
+template <int NL>
+cudaError_t launch_fused_nl(const GatherParams &p, int threads, size_t smem, int blocks, cudaStream_t stream)
+{
+    switch (threads) {
+    case 256: return launch_fused_tpb<NL, 256>(p, smem, blocks, stream);
+    case 1024: return launch_fused_tpb<NL, 1024>(p, smem, blocks, stream);
+    default: return launch_fused_tpb<NL, 512>(p, smem, blocks, stream);
+    }
+}
+
+// One CTA per band of the peak search (w.band_rows full rows).
+static cudaError_t launch_fused(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
+{
+    GatherParams p;
+    p.ax = ax;
+    p.w = w;
+    p.rows = w.band_rows;
+    p.cols = ax.n_phi;
+    p.cap = fused_stages_profiles(ax, w.band_rows) ? 1 : 0;
+    p.col_tiles = 1;
+    p.tiles_per_event = n_bands(ax, w.band_rows);
+    const int blocks = w.n_events * p.tiles_per_event;
+    const size_t smem = fused_smem_bytes(ax, w.band_rows) + (p.cap ? (size_t)ax.n_layers * ax.n_phi * sizeof(uint2) : 0);
+    if (ax.n_layers <= 4) return launch_fused_nl<4>(p, t.gather_threads, smem, blocks, stream);
+    if (ax.n_layers <= 8) return launch_fused_nl<8>(p, t.gather_threads, smem, blocks, stream);
+    if (ax.n_layers <= 12) return launch_fused_nl<12>(p, t.gather_threads, smem, blocks, stream);
+    return launch_fused_nl<16>(p, t.gather_threads, smem, blocks, stream);
+}
+
 template <int TPB>
 cudaError_t launch_gather_count_tpb(const GatherParams &p, size_t smem, int fcap, int blocks, cudaStream_t stream)
 {
@@ -1026,6 +1232,7 @@ cudaError_t launch_gather_count_tpb(const GatherParams &p, size_t smem, int fcap
 
 cudaError_t launch_gather(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
 {
+    if (t.vote_mode == HOUGH_VOTE_FUSED) return launch_fused(ax, w, t, stream);
     if (!ax.counts) return launch_gather_tiled(ax, w, t, stream);
     if (!w.fsort) return cudaErrorInvalidValue;   // the count gather reads the sorted f values
     GatherParams p;
@@ -1063,7 +1270,8 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
                         cudaStream_t stream)
 {
     if (t.vote_mode == HOUGH_VOTE_SCATTER || (ax.counts && !w.fsort)) return launch_scatter(ax, w, t, refine_eps, false, stream);
-    // gather every table layer, then let the scatter kernel add the layers whose radii differ
+    // gather every table layer (fused with the peak search under HOUGH_VOTE_FUSED), then let the
+    // scatter kernel add the layers whose radii differ
     cudaError_t err = launch_gather(ax, w, t, stream);
     if (err) return err;
     return launch_scatter(ax, w, t, refine_eps, true, stream);

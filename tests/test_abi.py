@@ -49,6 +49,20 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(binding.Tiling) == 32
 
 
+def test_binding_constants_match_header():
+    """Every integer #define of the header that the binding names (prefix HOUGH_ dropped) has the
+    header's value; the vote modes, accumulators and status codes must all be named."""
+    from paper_1310_7556_gb300 import binding
+    text = open(HEADER).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+HOUGH_(\w+)\s+\(?(-?\d+)\)?", text)}
+    for name in ("VOTE_GATHER", "VOTE_SCATTER", "VOTE_FUSED", "ACC_LAYERS", "ACC_COUNTS", "OK", "EINVAL",
+                 "ENOTREADY", "EBUSY", "HOST", "DEVICE"):
+        assert name in defines and hasattr(binding, name), name
+    for name, value in defines.items():
+        if hasattr(binding, name):
+            assert getattr(binding, name) == value, name
+
+
 def test_version_and_error_strings_without_gpu(lib):
     from paper_1310_7556_gb300 import binding
     L = binding.load()
