@@ -242,17 +242,15 @@ constexpr int kScanRound = kScanThreads * kScanPerThread;
 
 __device__ __forceinline__ int scan_pad(int k) { return k + (k >> 5); }
 
-__device__ __forceinline__ void scan_keys(const Axes &ax, const Workspace &w, const int e)
+// Exclusive scan of counts[k0, k1) into offs[k0, k1), starting from `carry`; returns the running
+// total after k1.  Every thread of the CTA takes part.
+__device__ __forceinline__ int scan_range(const int32_t *counts, int32_t *offs, const int k0, const int k1, int carry)
 {
     __shared__ int s_tile[kScanRound + kScanRound / 32];
     __shared__ int s_warp[kScanThreads / 32];
-    const int nkeys = n_keys(ax);
-    const int32_t *counts = w.counts + (int64_t)e * nkeys;
-    int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int carry = 0;
-    for (int base = 0; base < nkeys; base += kScanRound) {
-        const int n = min(kScanRound, nkeys - base);
+    for (int base = k0; base < k1; base += kScanRound) {
+        const int n = min(kScanRound, k1 - base);
 #pragma unroll
         for (int r = 0; r < kScanPerThread; ++r) {
             const int k = r * kScanThreads + threadIdx.x;
@@ -301,20 +299,57 @@ __device__ __forceinline__ void scan_keys(const Axes &ax, const Workspace &w, co
         }
         __syncthreads();
     }
+    return carry;
+}
+
+// One CTA per event: the scan of all its keys.
+__device__ __forceinline__ void scan_keys(const Axes &ax, const Workspace &w, const int e)
+{
+    const int nkeys = n_keys(ax);
+    const int total = scan_range(w.counts + (int64_t)e * nkeys, w.offs + (int64_t)e * (nkeys + 1), 0, nkeys, 0);
     if (threadIdx.x == 0) {
-        offs[nkeys] = carry;
-        w.stats[e].n_hits = (unsigned long long)carry;
+        w.offs[(int64_t)e * (nkeys + 1) + nkeys] = total;
+        w.stats[e].n_hits = (unsigned long long)total;
     }
 }
 
-// The layer tables and the bucket scans in one launch, as they do not depend on each other:
-// blocks [0, n_events) scan one event's bucket counts each, the next HOUGH_MAX_LAYERS blocks
-// compute one layer's table each.
-__global__ void __launch_bounds__(kScanThreads) table_scan_kernel(Axes ax, Workspace w)
+// One CTA per (event, layer) for events with few CTAs to spread over: the CTA first sums the
+// event's counts of the layers before its own (its offset), then scans its layer's buckets, so the
+// layers of an event are scanned side by side instead of one after another.  Integer sums: the
+// same offsets as scan_keys.
+__device__ __forceinline__ void scan_layer(const Axes &ax, const Workspace &w, const int e, const int l)
+{
+    __shared__ int s_part[kScanThreads / 32];
+    const int nkeys = n_keys(ax), nphi = ax.n_phi;
+    const int32_t *counts = w.counts + (int64_t)e * nkeys;
+    int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
+    int part = 0;
+    for (int k = threadIdx.x; k < l * nphi; k += kScanThreads) part += counts[k];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, d);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+    __syncthreads();
+    int base = 0;
+#pragma unroll
+    for (int q = 0; q < kScanThreads / 32; ++q) base += s_part[q];
+    const int total = scan_range(counts, offs, l * nphi, (l + 1) * nphi, base);
+    if (threadIdx.x == 0 && l == ax.n_layers - 1) {
+        offs[nkeys] = total;
+        w.stats[e].n_hits = (unsigned long long)total;
+    }
+}
+
+// The layer tables and the bucket scans in one launch, as they do not depend on each other: the
+// first `scans` blocks scan the events' bucket counts (one block per event, or with `by_layer` one
+// per (event, layer)), the next HOUGH_MAX_LAYERS blocks compute one layer's table each.
+__global__ void __launch_bounds__(kScanThreads) table_scan_kernel(Axes ax, Workspace w, int by_layer)
 {
     pdl_enter();
-    if ((int)blockIdx.x < w.n_events) scan_keys(ax, w, blockIdx.x);
-    else layer_table(ax, w, blockIdx.x - w.n_events);
+    const int scans = by_layer ? w.n_events * ax.n_layers : w.n_events;
+    const int b = blockIdx.x;
+    if (b >= scans) layer_table(ax, w, b - scans);
+    else if (by_layer) scan_layer(ax, w, b / ax.n_layers, b % ax.n_layers);
+    else scan_keys(ax, w, b);
 }
 
 // Scatter every valid hit to its sorted position, completing its hot record with its voting rows.
@@ -414,8 +449,11 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
     const int g = grid_for(w.n_hits_total >= 0 ? w.n_hits_total : w.hit_capacity, kStageThreads);
     if ((err = launch_chained(stage_count_kernel, dim3(g), dim3(kStageThreads), 0, stream, ax, w))) return err;
     if ((err = mark(1))) return err;
-    if ((err = launch_chained(table_scan_kernel, dim3(w.n_events + HOUGH_MAX_LAYERS), dim3(kScanThreads), 0, stream, ax,
-                              w)))
+    // a few events leave most SMs idle under one scan block each: then a block per (event, layer)
+    const int by_layer = w.n_events <= 16 ? 1 : 0;
+    const int scans = by_layer ? w.n_events * ax.n_layers : w.n_events;
+    if ((err = launch_chained(table_scan_kernel, dim3(scans + HOUGH_MAX_LAYERS), dim3(kScanThreads), 0, stream, ax, w,
+                              by_layer)))
         return err;
     if ((err = mark(2))) return err;   // table_ms covers both; scan_ms stays empty
     if ((err = mark(3))) return err;
