@@ -500,10 +500,10 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
 // (the 3 x 3 neighbourhoods; phi wraps within the full rows) into shared memory, searches the
 // band for peaks there and writes the band's candidate list and count as the peak kernel does --
 // the accumulator never goes to device memory.  Full rows read every bucket of a layer, so when
-// they fit (STAGE) the voting layers' whole profiles are first copied into shared memory with bulk
-// asynchronous copies; otherwise they are read through the cache.  When a present layer's hits lie at several radii
-// the scatter kernel adds that layer's votes afterwards: the CTA then writes the band's rows to
-// the accumulator instead, and the peak kernel searches it.
+// they fit (STAGE) the voting layers' whole profiles are first copied into shared memory with
+// bulk asynchronous copies; otherwise they are read through the cache.  When a present layer's
+// hits lie at several radii the scatter kernel adds that layer's votes afterwards: the CTA then
+// writes the band's rows to the accumulator instead, and the peak kernel searches it.
 
 __device__ __forceinline__ bool all_layers_uniform(const Axes &ax, const Workspace &w)
 {
