@@ -481,7 +481,7 @@ typedef struct hough_server hough_server;
 /*
  * Create a server on `device`: allocates the lanes (HOUGH_ENOMEM when fewer than two, or fewer than
  * `lanes`, fit the budget), captures every batch size's graph, and starts the dispatcher thread.
- * Results live in pinned host blocks: a mapped part of max(65536, 4096 * max_batch_events)
+ * Results live in pinned host blocks: a mapped part of max(16384, 1024 * max_batch_events)
  * candidates the pack kernel writes to, and an overflow grown to the largest batch.  A finished
  * batch's block is shared by its events until the last of them is polled (poll copies from it);
  * the pool holds at most 3 * lanes blocks, beyond which (unpolled results piling up) each event's

@@ -495,7 +495,7 @@ int hough_serve_create(const hough_geometry *geometry, const hough_binning *binn
         }
         s->device_bytes += bytes;
         bool ok = cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) == cudaSuccess;
-        l->mcap = std::max<int64_t>(1 << 16, (int64_t)E * 4096);
+        l->mcap = std::max<int64_t>(1 << 14, (int64_t)E * 1024);
         ok = ok && cudaHostAlloc(&l->r, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->phi, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaHostAlloc(&l->z, sizeof(float) * H, cudaHostAllocDefault) == cudaSuccess;

@@ -105,7 +105,7 @@ def test_served_results_equal_alone(binding):
 
 def test_unpolled_results_fill_the_pool_then_are_copied(binding):
     """Full-size events, four per launch: a batch's candidates overflow the mapped part of its
-    result block (65,536 candidates), so polls read across both parts; six batches left unpolled
+    result block (16,384 candidates), so polls read across both parts; six batches left unpolled
     hold every block the pool may allocate (three per lane), so the last completions copy their
     events' candidates out instead.  Every event still equals its result alone."""
     base = [W.event(i) for i in range(8)]
@@ -127,7 +127,7 @@ def test_unpolled_results_fill_the_pool_then_are_copied(binding):
             assert res.status == binding.OK and res.batch_events == per
             assert np.array_equal(cands, expect[i % len(base)]), f"event {i}"
             n_first += res.n_candidates if i < per else 0
-        assert n_first > 65_536, "the first batch did not reach into its block's overflow"
+        assert n_first > 16_384, "the first batch did not reach into its block's overflow"
 
 
 def test_admission_is_bounded_and_hold_times_out(binding):
