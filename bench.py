@@ -306,8 +306,8 @@ def measure_plain(env, args, ctx, tens, n):
     return out
 
 
-# Kernels of one plain step: (name, timing key, source file that defines it).  The per-kernel
-# algorithmic work (bytes or lane operations per launch) is kernel_work's model below.
+# Kernels of one plain step: (name, timing key, source file that defines it).  Their algorithmic
+# work per launch is kernel_work's model below.
 PLAIN_KERNELS = [
     ("clear_kernel", "clear_ms", "stage_kernels.cu"),
     ("stage_count_kernel", "count_ms", "stage_kernels.cu"),
@@ -317,34 +317,53 @@ PLAIN_KERNELS = [
     ("scatter_kernel (vote of per-vote layers)", "scatter_ms", "vote_kernel.cu"),
     ("peaks_kernel", "band_peaks_ms", "vote_kernel.cu"),
     ("compact_kernel", "compact_ms", "vote_kernel.cu"),
-    ("member_kernel + stage2_large_kernel", "stage2_ms", "confirm_kernels.cu"),
+    ("confirm_kernel", "stage2_ms", "confirm_kernels.cu"),
 ]
-ALU_LANES_PER_SM = 128   # FP32/INT32 lanes of a Blackwell SM
+SMEM_PEAK_HOW = ("hough_microbench_smem_or: 32-bit shared-memory atomicOr, the 32 lanes of a warp on 32 different "
+                 "banks, persistent grid of 152-multiple CTAs, measured in this run (not in MEASURED_PEAKS.json)")
 
 
-def kernel_work(name, w, n_hits, plain):
-    """(bound, algorithmic amount per launch, unit) of one kernel of the plain step:
-    bytes for the memory-bound steps (the reads and writes the step needs, each once),
-    lane operations for the confirmation (24 per member: its two-float stage-2 coefficients and
-    row run; 8 per stage-2 vote: FMA, floor, range tests, the OR, popcount, arg-max compare)."""
+def kernel_work(name, w, n_hits, st):
+    """Algorithmic work of one launch on one event (or a batch): (bytes, votes or None).
+
+    bytes: what the step must read and write, each once -- hits 13 B (r, phi, z, layer), 2 B per
+    accumulator cell written by the vote and read by the peak search, 8 B per band candidate and
+    40 B per listed candidate, and for the confirmation 64 B per candidate record (read and
+    written), 28 B per (candidate, layer) of table entries, stage-2 terms and bucket offsets, and
+    8 B per member (its azimuth fraction and z).  votes: stage-1 votes for the vote kernels, stage-2
+    votes for the confirmation: the unit of the shared-atomic ceiling."""
     b = w.binning
-    cells = b.n_qpt * b.n_phi
-    nkeys = w.geometry.n_layers * b.n_phi
-    cands = plain["candidates"]
-    general = plain["general_votes"] / max(1, plain["votes"])
+    L = w.geometry.n_layers
+    cells = st["cells"]
+    nkeys = L * b.n_phi * st["events"]
+    cands = st["candidates"]
+    general = st["general_votes"] / max(1, st["votes"])
     model = {
-        "clear_kernel": ("hbm", 4 * nkeys + 8 * 16 * (b.n_phi + 16) + 304),
-        "stage_count_kernel": ("hbm", 37 * n_hits),          # r, phi, z, layer in; key, rank, 16-B record out
-        "table_scan_kernel": ("hbm", 8 * nkeys + 32 * 16),   # bucket counts in, offsets out; layer records
-        "scatter_kernel (hit sort)": ("hbm", 68 * n_hits),   # key, rank, record, r, phi, z, offset in; 2 x 16 B out
-        "gather_kernel": ("hbm", 13 * n_hits + 2 * cells),   # the vote: hits in, one 16-bit mask per cell out
-        "scatter_kernel (vote of per-vote layers)": ("hbm", 13 * n_hits * general),
-        "peaks_kernel": ("hbm", 2 * cells + 8 * cands),      # masks in, candidates out
-        "compact_kernel": ("hbm", 40 * cands),               # band lists in, candidate records out
-        "member_kernel + stage2_large_kernel": ("alu", 24 * plain["members"] + 8 * plain["stage2_votes"]),
+        "clear_kernel": (4 * nkeys + 8 * 16 * (b.n_phi + 16) * st["events"] + 304, None),
+        "stage_count_kernel": (37 * n_hits, None),            # r, phi, z, layer in; key, rank, 16-B record out
+        "table_scan_kernel": (8 * nkeys + 32 * 16, None),     # bucket counts in, offsets out; layer records
+        "scatter_kernel (hit sort)": (72 * n_hits, None),     # key, rank, record, r, phi, z, offset in; 2 x 16 B + f + z out
+        "gather_kernel": (13 * n_hits + 2 * cells, st["votes"] - st["general_votes"]),
+        "scatter_kernel (vote of per-vote layers)": (13 * n_hits * general, st["general_votes"]),
+        "peaks_kernel": (2 * cells + 8 * cands, None),
+        "compact_kernel": (40 * cands, None),
+        "confirm_kernel": (64 * cands + 28 * L * cands + 8 * st["members"], st["stage2_votes"]),
     }
-    bound, amount = model[name]
-    return bound, float(amount), "bytes" if bound == "hbm" else "lane operations"
+    staging = ("clear_kernel", "stage_count_kernel", "table_scan_kernel", "scatter_kernel (hit sort)")
+    model["staging (clear, count, table and scan, hit sort)"] = (sum(model[k][0] for k in staging), None)
+    model["compact_kernel + cand_scan_kernel"] = (model["compact_kernel"][0] + 8 * st["events"], None)
+    return model[name]
+
+
+# Steps of a batch as hough_batch_profile times them.
+BATCH_STEPS = [
+    ("staging (clear, count, table and scan, hit sort)", "stage_ms", "stage_kernels.cu"),
+    ("gather_kernel", "gather_ms", "vote_kernel.cu"),
+    ("scatter_kernel (vote of per-vote layers)", "scatter_ms", "vote_kernel.cu"),
+    ("peaks_kernel", "band_peaks_ms", "vote_kernel.cu"),
+    ("compact_kernel + cand_scan_kernel", "compact_ms", "vote_kernel.cu"),
+    ("confirm_kernel", "stage2_ms", "confirm_kernels.cu"),
+]
 
 
 def _sources_digest(src):
@@ -372,33 +391,50 @@ def measured_traffic(kernel, workload, src):
     return None
 
 
-def kernel_table(env, w, n_hits, plain, smem_peak, hbm_peak, peaks_kind, clocks):
-    """Per-kernel roofline of the plain step from its attributed device times."""
-    props = env.torch.cuda.get_device_properties(env.dev)
-    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
-    alu_peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_mhz * 1e6   # lane ops/s
-    total = sum(plain["stage_ms"][k] for _, k, _ in PLAIN_KERNELS)
+def roofline_entry(ms, nbytes, votes, smem_peak, hbm_peak, peaks_kind):
+    """One kernel's rooflines: algorithmic bytes against the measured HBM copy rate and, for the
+    vote kernels, votes against the measured shared-atomic ceiling (the blueprint's two ceilings)."""
+    sec = ms * 1e-3
+    e = {"ms": ms, "hbm": {"algorithmic_bytes": nbytes, "achieved_gbs": nbytes / sec / 1e9 if sec > 0 else None,
+                           "peak_gbs": hbm_peak, "frac": nbytes / sec / 1e9 / hbm_peak if sec > 0 else None,
+                           "peak_kind": f"{peaks_kind}: MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)"}}
+    if votes is not None:
+        e["smem_atomic"] = {"votes": votes, "achieved_votes_per_s": votes / sec if sec > 0 else None,
+                            "peak_votes_per_s": smem_peak, "frac": votes / sec / smem_peak if sec > 0 else None,
+                            "peak_kind": SMEM_PEAK_HOW}
+    e["bound"] = "smem_atomic" if votes is not None else "hbm"
+    return e
+
+
+def kernel_table(w, n_hits, st, smem_peak, hbm_peak, peaks_kind, steps=PLAIN_KERNELS):
+    """Per-kernel rooflines of one step from its attributed device times (st: counts and stage_ms)."""
+    total = sum(st["stage_ms"][k] for _, k, _ in steps)
     table = {}
-    for name, key, src in PLAIN_KERNELS:
-        ms = plain["stage_ms"][key]
-        bound, amount, unit = kernel_work(name, w, n_hits, plain)
-        rate = amount / (ms * 1e-3) if ms > 0 else 0.0
-        if bound == "hbm":
-            ach, peak, u = rate / 1e9, hbm_peak, "GB/s"
-            pk = f"{peaks_kind}: MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)"
-        else:
-            ach, peak, u = rate / 1e12, alu_peak / 1e12, "Tops/s"
-            pk = (f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} FP32/INT32 lanes x {sm_mhz:.0f} MHz "
-                  "(median SM clock sampled during the run)")
-        table[name] = {"ms": ms, "share": ms / total if total else None, "bound": bound, "algorithmic": amount,
-                       "algorithmic_unit": unit, "achieved": ach, "peak": peak, "unit": u,
-                       "frac": ach / peak if peak else None, "peak_kind": pk, "source": src}
-    g = table["gather_kernel"]
-    g["smem_atomic_equivalent"] = {
-        "votes_per_s": plain["votes"] / (plain["stage_ms"]["gather_ms"] * 1e-3),
-        "peak": smem_peak, "frac": plain["votes"] / (plain["stage_ms"]["gather_ms"] * 1e-3) / smem_peak,
-        "note": "votes decided per second against the measured shared-atomicOr ceiling of the paper's scatter design"}
+    for name, key, src in steps:
+        ms = st["stage_ms"][key]
+        nbytes, votes = kernel_work(name, w, n_hits, st)
+        e = roofline_entry(ms, float(nbytes), None if votes is None else float(votes), smem_peak, hbm_peak, peaks_kind)
+        e["share"] = ms / total if total else None
+        e["source"] = src
+        table[name] = e
     return table
+
+
+def headline_roofline(table, dominant, traffic):
+    """The bench line's roofline object for the dominant kernel: its votes against the shared-atomic
+    ceiling when it votes, else its algorithmic bytes against HBM, with the other beside it."""
+    d = table[dominant]
+    if d["bound"] == "smem_atomic":
+        sa = d["smem_atomic"]
+        r = {"kernel": dominant, "bound": "smem_atomic", "achieved": sa["achieved_votes_per_s"],
+             "peak": sa["peak_votes_per_s"], "unit": "votes/s", "frac": sa["frac"], "peak_kind": sa["peak_kind"]}
+    else:
+        h = d["hbm"]
+        r = {"kernel": dominant, "bound": "hbm", "achieved": h["achieved_gbs"], "peak": h["peak_gbs"],
+             "unit": "GB/s", "frac": h["frac"], "peak_kind": h["peak_kind"]}
+    r.update({"traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+              "hbm": d["hbm"], "ms": d["ms"], "share_of_step": d.get("share")})
+    return r
 
 
 def measure_batched(env, args):
@@ -434,6 +470,17 @@ def measure_batched(env, args):
     launches = binding.kernel_launches() - launch0
     total = env.max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(b0, b1)))
     votes = sum(int(st.votes) for st in bstats)
+    # attribution: the same run kernel by kernel (hough_batch_profile), an event after each step
+    prof = []
+    for _ in range(3):
+        env.flush.zero_()
+        prof.append(batch.profile(*bdev, bhs, where=binding.DEVICE, stream=stream))
+    bst = {"events": len(bev), "cells": len(bev) * binding.grid_rows(wb.binning) * wb.binning.n_phi, "votes": votes,
+           "general_votes": sum(int(st.general_votes) for st in bstats),
+           "candidates": sum(int(st.n_candidates) for st in bstats),
+           "members": sum(int(st.n_members) for st in bstats),
+           "stage2_votes": sum(int(st.stage2_votes) for st in bstats),
+           "stage_ms": {k: statistics.mean(p[k] for p in prof) for k in prof[0]}}
     out = {"events_per_s": replicas.job_rate(len(bev) * args.batch_steps, env.world, total * 1e-3),
            "votes_per_s": replicas.job_rate(votes * args.batch_steps, env.world, total * 1e-3),
            "ms_per_batch": total / args.batch_steps, "events_per_batch": len(bev), "hits_per_batch": int(bhs[-1]),
@@ -441,7 +488,13 @@ def measure_batched(env, args):
            "members_per_batch": sum(int(st.n_members) for st in bstats),
            "stage2_votes_per_batch": sum(int(st.stage2_votes) for st in bstats),
            "steps": args.batch_steps, "gpu_launches": int(launches),
-           "mode": "one CUDA-graph replay per batch; kernels span all events"}
+           "mode": "one CUDA-graph replay per batch; kernels span all events",
+           "stage_ms_profiled": bst["stage_ms"]}
+    if getattr(args, "smem_peak", None):
+        table = kernel_table(wb, int(bhs[-1]), bst, args.smem_peak, args.hbm_peak, args.peaks_kind, BATCH_STEPS)
+        dominant = max(table, key=lambda k: table[k]["ms"])
+        out["kernels"] = table
+        out["roofline"] = headline_roofline(table, dominant, None)
     if tune is not None:
         out["autotune"] = {"tiling": {f: getattr(tune.tiling, f) for f in binding.TILING_FIELDS},
                            "ms_per_batch": tune.ms, "default_ms_per_batch": tune.default_ms,
@@ -650,6 +703,7 @@ def _plain_variant(env, args, w, text, smem_peak=None, hbm_peak=None):
     cells = binding.grid_rows(w.binning) * w.binning.n_phi
     vote_ms = t["vote_ms"]
     p = {"workload": text, "hits": int(ev.n_hits), "cells": cells, "votes": int(st.votes),
+         "general_votes": int(st.general_votes), "refined_votes": int(st.refined_votes),
          "candidates": int(st.n_candidates), "members": int(st.n_members),
          "events_per_s": replicas.job_rate(args.steps, env.world, total * 1e-3), "ms_per_event": total / args.steps,
          "stage_ms": t["stage_ms"], "vote_ms": vote_ms, "gather_ms": t["gather_ms"], "scatter_ms": t["scatter_ms"],
@@ -773,6 +827,31 @@ def measure_e2e(env, args, ctx, ev):
             "d2h_bytes_per_step": len(got) * 32 + 160}
 
 
+def served_headline(served):
+    """Completed events/s and latency percentiles of each served setting at each offered load."""
+    if not served:
+        return None
+    out = {}
+    for mode in ("continuous_batching", "continuous_batching_large"):
+        if mode in served:
+            out[mode] = {str(int(p["offered_ev_s"])): {"completed_ev_s": p["completed_ev_s"], "p50_ms": p["p50_ms"],
+                                                        "p99_ms": p["p99_ms"], "dropped_frac": p["dropped_frac"]}
+                         for p in served[mode]["loads"]}
+    return out
+
+
+def measure_per_vote_path(env, args, smem_peak, hbm_peak):
+    """The pileup event on a detector whose modules sit within +-0.5 cm of their layer's radius: no
+    layer's hits share one radius, so every stage-1 vote is evaluated per hit in the shared-atomic
+    scatter kernel (FP32 arcsine, FP64 near a bin edge) -- the path the gather cannot take."""
+    w = eg.WORKLOADS["pileup_100k_jittered"]
+    text = WORKLOAD_TEXT["pileup_100k"].replace("+ 50000 uniform noise hits",
+                                                "+ 50000 uniform noise hits, every hit at its layer radius + U(-0.5, 0.5) cm")
+    p = _plain_variant(env, args, w, text, smem_peak, hbm_peak)
+    p["note"] = "all votes cast by scatter_kernel (vote of per-vote layers); vote_vs_smem_atomic_peak is its rate"
+    return p
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -780,6 +859,10 @@ def main():
         return
     env = Env()
     binding = env.binding
+    if args.only == "batched":
+        peaks, args.peaks_kind = measured_peaks()
+        args.hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        args.smem_peak = binding.smem_or_throughput(env.local, 0, 30.0)
     if args.only in ("batched", "served", "paper_sweep", "counts", "d0", "fused"):
         out = {"batched": measure_batched, "served": measure_served, "paper_sweep": measure_paper_sweep,
                "counts": measure_counts, "d0": measure_d0, "fused": measure_fused}[args.only](env, args)
@@ -804,10 +887,12 @@ def main():
     # measured shared-atomic ceiling (conflict-free 32-lane atomicOr), before anything is timed
     smem_peak = binding.smem_or_throughput(env.local, 0, 30.0)
     smem_peak_rand = binding.smem_or_throughput(env.local, 1, 30.0)
+    peaks, peaks_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    args.smem_peak, args.hbm_peak, args.peaks_kind = smem_peak, hbm_peak, peaks_kind
     with ClockSampler(env.local) as clock_sampler:
         plain = measure_plain(env, args, ctx, tens, n)
-        peaks, peaks_kind = measured_peaks()
-        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        per_vote = measure_per_vote_path(env, args, smem_peak, hbm_peak)
         if args.only == "plain":
             batched = e2e = served = paper = counts = d0 = fused = None
         else:
@@ -819,9 +904,9 @@ def main():
             d0 = measure_d0(env, args, smem_peak, hbm_peak)
             fused = measure_fused(env, args)
     clocks = clock_sampler.summary()
-    kernels = kernel_table(env, w, n, plain, smem_peak, hbm_peak, peaks_kind, clocks)
+    st = dict(plain, events=1, cells=binding.grid_rows(w.binning) * w.binning.n_phi)
+    kernels = kernel_table(w, n, st, smem_peak, hbm_peak, peaks_kind)
     dominant = max(kernels, key=lambda k: kernels[k]["ms"])
-    dk = kernels[dominant]
     src = dict((name, s) for name, _, s in PLAIN_KERNELS)[dominant]
     traffic = measured_traffic(dominant, args.workload, src)
     votes = plain["votes"]
@@ -841,6 +926,11 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
+        # the other headline figures first, so that a truncated copy of this line keeps them
+        "batched_events_per_s": batched["events_per_s"] if batched else None,
+        "batched_votes_per_s": batched["votes_per_s"] if batched else None,
+        "batched_ms_per_256_events": batched["ms_per_batch"] if batched else None,
+        "served": served_headline(served),
         "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": n, "votes_per_event": votes,
                    "candidates_per_event": plain["candidates"], "members_per_event": plain["members"],
                    "stage2_votes_per_event": plain["stage2_votes"],
@@ -848,17 +938,15 @@ def main():
                    "l2": "flushed before every timed step (256 MiB write)", "tiling": ctx.get_tiling(),
                    "tiling_from": "autotuner (one-event batch, 10 replays per configuration)" if plain_tune else "default"},
         "votes_per_s": votes * plain["events_per_s"],
-        "roofline": {"kernel": dominant, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
-                     "unit": dk["unit"], "frac": dk["frac"], "traffic": traffic,
-                     "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "algorithmic": dk["algorithmic"], "algorithmic_unit": dk["algorithmic_unit"],
-                     "ms": dk["ms"], "share_of_step": dk["share"], "peak_kind": dk["peak_kind"]},
+        "roofline": headline_roofline(kernels, dominant, traffic),
+        "batched_roofline": batched.get("roofline") if batched else None,
         "kernels": kernels,
         "smem_atomic_peak": {"conflict_free": smem_peak, "random_words": smem_peak_rand,
-                             "unit": "lane atomicOr/s", "how": "hough_microbench_smem_or, 152-multiple persistent grid"},
+                             "unit": "lane atomicOr/s", "how": SMEM_PEAK_HOW},
         "scatter_mode": scatter,
+        "per_vote_path": per_vote,
         "batched": batched,
-        "served": served,
+        "served_detail": served,
         "paper_sweep": paper,
         "count_accumulator": counts,
         "d0_axis": d0,

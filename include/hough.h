@@ -316,6 +316,16 @@ typedef struct hough_timing {
 int hough_enable_timing(hough_ctx *ctx, int on);
 int hough_get_timing(hough_ctx *ctx, hough_timing *out);
 
+/*
+ * Test of the device-side bounded wait (no GPU fault is made).  The gather vote's CTAs wait for
+ * their bulk copies into shared memory with a bound of about a second; when it expires they set
+ * HOUGH_DEVERR_TIMEOUT, wait once more with the full bound for the copies to land, and write
+ * nothing (the accumulator is then incomplete).  first_bound < 0 makes the first bound of every
+ * such wait of this context expire at once, so that a test can run that error path; 0 restores
+ * the normal bound.  HOUGH_EINVAL without a context.
+ */
+int hough_set_copy_wait(hough_ctx *ctx, int first_bound);
+
 /* Kernels this library has launched in the process so far (all contexts). */
 uint64_t hough_kernel_launches(void);
 
@@ -371,6 +381,17 @@ int hough_batch_run(hough_batch *batch, const float *r, const float *phi, const 
  */
 int hough_batch_candidates(hough_batch *batch, hough_candidate *out, int64_t cap, int64_t *offsets,
                            int where, void *stream);
+
+/*
+ * hough_batch_run with each step timed: the same kernels, enqueued one by one instead of as the
+ * captured graph, with a CUDA event after each step; synchronises `stream` and fills in `out`
+ * (hough_timing, below) the device time of the staging (stage_ms), the gather and scatter votes,
+ * the peak search and candidate scan, and the confirmation (stage2_ms = member_ms).  The results
+ * are those of hough_batch_run.
+ */
+int hough_batch_profile(hough_batch *batch, const float *r, const float *phi, const float *z,
+                        const uint8_t *layer, const int64_t *hit_start, int32_t n_events, int where,
+                        void *stream, hough_timing *out);
 
 /* Counters of one event of the last run.  Synchronises `stream`. */
 int hough_batch_stats(hough_batch *batch, int32_t event, hough_stats *out, void *stream);
@@ -552,15 +573,19 @@ int hough_serve_inject(hough_server *server, int fault, int on);
  * Runs the staging and vote kernels of hough_vote on the hits r, phi, z, layer (device pointers,
  * n_hits entries, same meaning and checks as hough_vote with HOUGH_DEVICE) and writes the
  * (stacked) rows x n_phi row-major cells -- layer masks, or counts with HOUGH_ACC_COUNTS -- to
- * `accumulator` (device, caller-owned).  If `device_error`
+ * `accumulator` (device, caller-owned, 16-byte aligned: the kernel writes it in 16-byte vectors;
+ * another alignment returns HOUGH_EINVAL before any work).  If `device_error`
  * is not NULL it receives (device memory, asynchronously) the HOUGH_DEVERR_* bits of dropped hits.
  * The geometry and binning are read at each call; the stage-2 fields of the binning are ignored.
  *
- * Scratch: one fixed 8 MiB array in device memory, reserved by the CUDA runtime on every GPU that
- * loads this library and held until the process exits.  Limits: n_hits <= 131072, rows (n_qpt,
- * times n_d0 with a d0 axis) <= 1024, n_phi <= 4096; larger inputs return HOUGH_ECAPACITY before any work.  The first call on a device
- * (with that device current) looks up the array's device address; make that first call before
- * any stream capture.  Every call reuses the same array and clears what must start empty, so calls
+ * Scratch: one fixed 8 MiB array in device memory, reserved on a GPU when the library's device
+ * code is loaded there and held until the process exits.  With the CUDA runtime's lazy module
+ * loading (its default) that happens at the first call on each device, which therefore does
+ * reserve memory: make it at start-up, outside the real-time loop and before any stream capture;
+ * later calls allocate nothing.  Limits: n_hits <= 131072, rows (n_qpt, times n_d0 with a d0 axis)
+ * <= 1024, n_phi <= 4096; larger inputs return HOUGH_ECAPACITY before any work.  Each call looks up
+ * the array's device address on the current device (no allocation), so a device reset is
+ * harmless.  Every call reuses the same array and clears what must start empty, so calls
  * whose work may overlap on the GPU race: issue them on one stream or synchronise between them.
  * Asynchronous on `stream` (a cudaStream_t of the current device, NULL for the legacy stream).
  */

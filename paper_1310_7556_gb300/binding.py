@@ -148,7 +148,9 @@ _SIGNATURES = {
                             ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "hough_batch_destroy": ([_P], None),
     "hough_batch_set_tiling": ([_P, ctypes.POINTER(Tiling)], ctypes.c_int),
+    "hough_set_copy_wait": ([_P, ctypes.c_int], ctypes.c_int),
     "hough_batch_run": ([_P, _P, _P, _P, _P, _P, _I32, ctypes.c_int, _P], ctypes.c_int),
+    "hough_batch_profile": ([_P, _P, _P, _P, _P, _P, _I32, ctypes.c_int, _P, ctypes.POINTER(Timing)], ctypes.c_int),
     "hough_batch_candidates": ([_P, _P, _I64, _P, ctypes.c_int, _P], ctypes.c_int),
     "hough_batch_stats": ([_P, _I32, ctypes.POINTER(Stats), _P], ctypes.c_int),
     "hough_batch_accumulator": ([_P, _I32, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -347,6 +349,10 @@ class HoughContext:
     def enable_timing(self, on=True):
         _check(self._lib.hough_enable_timing(self._h, 1 if on else 0))
 
+    def set_copy_wait(self, first_bound: int):
+        """hough_set_copy_wait: < 0 makes the first bound of the vote's bulk-copy waits expire at once."""
+        _check(self._lib.hough_set_copy_wait(self._h, int(first_bound)))
+
     def timing(self) -> dict:
         t = Timing()
         _check(self._lib.hough_get_timing(self._h, ctypes.byref(t)))
@@ -403,7 +409,7 @@ class HoughBatch:
     def __exit__(self, *exc):
         self.close()
 
-    def set_tiling(self, tile_qpt=16, tile_phi=256, threads=256, vote_mode=VOTE_GATHER, band_rows=1,
+    def set_tiling(self, tile_qpt=32, tile_phi=256, threads=256, vote_mode=VOTE_GATHER, band_rows=1,
                    gather_rows=0, gather_cols=0, gather_threads=0):
         t = Tiling(tile_qpt=tile_qpt, tile_phi=tile_phi, threads=threads, vote_mode=vote_mode, band_rows=band_rows,
                    gather_rows=gather_rows, gather_cols=gather_cols, gather_threads=gather_threads)
@@ -420,6 +426,17 @@ class HoughBatch:
         _check(self._lib.hough_batch_run(self._h, _ptr(r), _ptr(phi), _ptr(z), _ptr(layer), _ptr(hit_start),
                                          n_events, where, _stream(stream)))
         self.n_events = n_events
+
+    def profile(self, r, phi, z, layer, hit_start, where=HOST, stream=None) -> dict:
+        """hough_batch_profile: the run with every step timed on the stream (synchronises)."""
+        hit_start = np.ascontiguousarray(hit_start, dtype=np.int64)
+        self._keep = (r, phi, z, layer, hit_start)
+        n_events = hit_start.shape[0] - 1
+        t = Timing()
+        _check(self._lib.hough_batch_profile(self._h, _ptr(r), _ptr(phi), _ptr(z), _ptr(layer), _ptr(hit_start),
+                                             n_events, where, _stream(stream), ctypes.byref(t)))
+        self.n_events = n_events
+        return {n: getattr(t, n) for n, _ in Timing._fields_}
 
     def run_events(self, events, stream=None):
         """Concatenate Event objects (host) and run them."""

@@ -17,7 +17,9 @@ LIB = os.path.join(PKG, "libhough.so")
 
 SOURCES = ["hough_api.cu", "stage_kernels.cu", "vote_kernel.cu", "confirm_kernels.cu", "microbench.cu", "static_vote.cu", "batch.cu", "serve.cu", "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread", "-I" + INCLUDE]
+# host code: no contraction of a*b+c into fused multiply-adds, so host arithmetic rounds alike on x86
+# and Arm (GCC contracts by default on Arm)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread,-ffp-contract=off", "-I" + INCLUDE]
 
 
 def nvcc() -> str:

@@ -188,7 +188,7 @@ int hough_batch_autotune(hough_batch *b, const hough_geometry *geometry, const h
                 if (rows * cols / 8 < threads / 2) continue;   // under half the threads would have cells
                 votes.push_back(t);
             }
-    for (int tq : {8, 16, 32, 64, 128, 256})
+    for (int tq : {32, 64, 128})   // the scatter kernel's lanes take 32 rows each
         for (int tp : {128, 256, 512})
             for (int threads : {256, 512, 1024}) {
                 hough_tiling t = best;

@@ -125,7 +125,7 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     A(b->alloc(&b->inputs_dev, 1));
     A(b->alloc(&b->in_r, H)); A(b->alloc(&b->in_phi, H)); A(b->alloc(&b->in_z, H)); A(b->alloc(&b->in_layer, H));
     A(b->alloc(&w.key, H)); A(b->alloc(&w.rank, H)); A(b->alloc(&w.hot_tmp, H));
-    A(b->alloc(&w.hot, H)); A(b->alloc(&w.cold, H)); A(b->alloc(&w.fsort, H));
+    A(b->alloc(&w.hot, H)); A(b->alloc(&w.cold, H)); A(b->alloc(&w.fsort, H)); A(b->alloc(&w.zsort, H));
     A(b->alloc(&w.counts, E * nkeys)); A(b->alloc(&w.offs, E * (nkeys + 1)));
     A(b->alloc(&w.prof, (size_t)(E * prof_event_entries(ax))));
     A(b->alloc(&w.radii, 1)); A(b->alloc(&w.info, HOUGH_MAX_LAYERS)); A(b->alloc(&w.memo, 1));
@@ -136,9 +136,6 @@ int hough_batch_create(const hough_geometry *geometry, const hough_binning *binn
     A(b->alloc(&w.band_cands, (size_t)E * band_list_entries(ax)));
     A(b->alloc(&w.band_counts, (size_t)E * n_bands(ax, 1))); A(b->alloc(&w.band_offs, (size_t)E * n_bands(ax, 1)));
     A(b->alloc(&w.cands, E * C));
-    A(b->alloc(&w.mem_pool, E * Mm));
-    A(b->alloc(&w.mem_start, E * C)); A(b->alloc(&w.mem_count, E * C));
-    A(b->alloc(&w.large_list, E * C));
     A(b->alloc(&w.cand_base, E + 1)); A(b->alloc(&w.counters, 1));
     A(b->alloc(&w.stats, E));
     A(b->alloc(&b->packed, E * C));
@@ -189,8 +186,9 @@ int hough_batch_set_tiling(hough_batch *b, const hough_tiling *t)
 
 }  // extern "C"
 
-int hough::batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
-                     const int64_t *hit_start, int32_t n_events, int where, cudaStream_t stream, bool check_hits)
+// Checks of a run's arguments, the copies of its inputs and hit offsets (enqueued on `stream`).
+static int batch_prepare(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                         const int64_t *hit_start, int32_t n_events, int where, cudaStream_t stream, bool check_hits)
 {
     if (!b || !hit_start) return bfail(HOUGH_EINVAL, "batch and hit_start are required");
     if (n_events < 1 || n_events > b->limits.max_events) return bfail(HOUGH_ECAPACITY, "n_events outside 1..max_events");
@@ -228,6 +226,15 @@ int hough::batch_run(hough_batch *b, const float *r, const float *phi, const flo
     BCU(cudaMemcpyAsync(b->hit_start, hit_start, sizeof(int64_t) * (n_events + 1), cudaMemcpyHostToDevice, s),
         "copy hit_start failed");
     b->w.n_events = n_events;
+    return HOUGH_OK;
+}
+
+int hough::batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                     const int64_t *hit_start, int32_t n_events, int where, cudaStream_t stream, bool check_hits)
+{
+    int rc = batch_prepare(b, r, phi, z, layer, hit_start, n_events, where, stream, check_hits);
+    if (rc) return rc;
+    cudaStream_t s = stream;
     auto it = b->graphs.find(n_events);
     if (it == b->graphs.end()) {
         // capture on the library's own stream, ordered after the copies above
@@ -299,6 +306,57 @@ int hough::batch_enqueue_candidates(hough_batch *b, hough_candidate *dst_host, i
 }
 
 extern "C" {
+
+// The launch sequence of hough_batch_run enqueued kernel by kernel (not the captured graph), with a
+// CUDA event on `stream` after each step, so that each step's device time can be read.
+int hough_batch_profile(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
+                        const int64_t *hit_start, int32_t n_events, int where, void *stream, hough_timing *out)
+{
+    if (!out) return bfail(HOUGH_EINVAL, "out is required");
+    int rc = batch_prepare(b, r, phi, z, layer, hit_start, n_events, where, static_cast<cudaStream_t>(stream), true);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev[7] = {};
+    for (auto &e : ev) BCU(cudaEventCreate(&e), "event failed");
+    auto done = [&](int code) {
+        for (auto &e : ev) cudaEventDestroy(e);
+        return code;
+    };
+    const Axes &ax = b->ax;
+    const Workspace &w = b->w;
+    const Tiling &t = b->tiling;
+    cudaError_t e = cudaEventRecord(ev[0], s);
+    if (!e) e = launch_stage(ax, w, s);
+    if (!e) e = cudaEventRecord(ev[1], s);
+    if (!e && t.vote_mode != HOUGH_VOTE_SCATTER) e = launch_gather(ax, w, t, s);
+    if (!e) e = cudaEventRecord(ev[2], s);
+    if (!e) e = launch_scatter(ax, w, t, b->refine_eps, t.vote_mode != HOUGH_VOTE_SCATTER, s);
+    if (!e) e = cudaEventRecord(ev[3], s);
+    if (!e) e = launch_band_peaks(ax, w, t, s);
+    if (!e) e = cudaEventRecord(ev[4], s);
+    if (!e) e = launch_compact(ax, w, s);
+    if (!e) e = cudaEventRecord(ev[5], s);
+    if (!e) e = launch_stage2(ax, w, b->sms, b->refine_eps, s);
+    if (!e) e = cudaEventRecord(ev[6], s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return done(bfail(HOUGH_ECUDA, "profiled batch run failed"));
+    note_launches(kStageLaunches + kVoteLaunches + peak_launches(n_events) + kStage2Launches);
+    b->n_events = n_events;
+    b->ran = true;
+    float ms[6];
+    for (int k = 0; k < 6; ++k)
+        if (cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]) != cudaSuccess) return done(bfail(HOUGH_ECUDA, "event time failed"));
+    std::memset(out, 0, sizeof(*out));
+    out->stage_ms = ms[0];
+    out->gather_ms = ms[1];
+    out->scatter_ms = ms[2];
+    out->vote_ms = ms[1] + ms[2];
+    out->band_peaks_ms = ms[3];
+    out->compact_ms = ms[4];
+    out->peaks_ms = ms[3] + ms[4];
+    out->stage2_ms = out->member_ms = ms[5];
+    return done(HOUGH_OK);
+}
 
 int hough_batch_run(hough_batch *b, const float *r, const float *phi, const float *z, const uint8_t *layer,
                     const int64_t *hit_start, int32_t n_events, int where, void *stream)

@@ -236,8 +236,8 @@ Tiling default_tiling_impl(const Axes &ax)
     Tiling t;
     t.tile_phi = std::min(ax.n_phi, 256);
     while (ax.n_phi % t.tile_phi) t.tile_phi -= 64;
-    t.tile_qpt = std::min(ax.n_qpt, 16);
-    t.threads = 256;
+    t.tile_qpt = std::min(ax.n_qpt, 32);   // the scatter kernel's lanes take 32 rows
+    t.threads = 1024;                      // a tile's hits shared by 32 warps
     t.vote_mode = HOUGH_VOTE_GATHER;
     t.band_rows = 1;
     // with a d0 axis a band stages its rows in three slices: taller bands stage each row fewer times
@@ -447,7 +447,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&c->in_r, n)); A(c->alloc(&c->in_phi, n)); A(c->alloc(&c->in_z, n)); A(c->alloc(&c->in_layer, n));
     A(c->alloc(&w.key, n)); A(c->alloc(&w.rank, n)); A(c->alloc(&w.hot_tmp, n));
     A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1)); A(c->alloc(&w.prof, (size_t)prof_event_entries(ax)));
-    A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n)); A(c->alloc(&w.fsort, n));
+    A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n)); A(c->alloc(&w.fsort, n)); A(c->alloc(&w.zsort, n));
     A(c->alloc(&w.radii, 1)); A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
     A(c->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(c->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
     A(c->alloc(&w.zco, (size_t)ax.n_layers * ax.n_qpt));
@@ -457,7 +457,6 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&w.band_cands, band_list_entries_impl(ax)));
     A(c->alloc(&w.band_counts, n_bands(ax, 1))); A(c->alloc(&w.band_offs, n_bands(ax, 1)));
     A(c->alloc(&w.mem_start, w.max_cand)); A(c->alloc(&w.mem_count, w.max_cand));
-    A(c->alloc(&w.large_list, w.max_cand));
     A(c->alloc(&w.cand_base, 2)); A(c->alloc(&w.counters, 1));
     A(c->alloc(&w.mem_pool, w.max_members)); A(c->alloc(&c->mem_idx, w.max_members));
     A(c->alloc(&w.stats, 1));
@@ -472,6 +471,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     w.band_rows = c->tiling.band_rows;
     w.band_cap = band_capacity(ax, c->tiling.band_rows);
     w.fused = 0;
+    w.keep_members = 1;   // hough_get_members reads the member lists
     // FP32 q/pT bin centres: the FP64 centre rounded once
     std::vector<float> kq(ax.n_qpt);
     for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
@@ -674,6 +674,13 @@ int hough_set_tiling(hough_ctx *c, const hough_tiling *t)
     int rc = check_tiling_impl(c->ax, c->device, t);
     if (rc) return rc;
     c->tiling = resolve_tiling(c->ax, t);
+    return HOUGH_OK;
+}
+
+int hough_set_copy_wait(hough_ctx *c, int first_bound)
+{
+    if (!c) return fail(HOUGH_EINVAL, "ctx is required");
+    c->w.copy_wait = first_bound < 0 ? -1 : 0;
     return HOUGH_OK;
 }
 

@@ -17,6 +17,7 @@
 //   band_cands[n_bands*band_cap] (8 B)  peak candidates of each row band: cell index, mask
 //   cands[max_cand] (32 B)    hough_candidate records in raster order
 //   mem_pool[max_members]     member hits (staged positions); mem_start/mem_count per candidate
+//                             (contexts only: a batch keeps no member lists)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -117,7 +118,7 @@ struct HitInputs {
 // Counters of a whole batch.
 struct BatchCounters {
     unsigned int total_cands;      // candidates kept over all events
-    unsigned int n_large;          // entries of the CTA stage-2 work list
+    unsigned int pad1;
     unsigned int pad0;
     unsigned int pad;
 };
@@ -137,7 +138,8 @@ struct Workspace {
     int32_t *offs;                // n_events * (nkeys + 1)
     uint2 *prof;                  // n_events * prof_event_entries
     HotHit *hot;                  // per hit, sorted within each event's range
-    float *fsort;                 // per hit, sorted: the hot record's f alone (count gather; may be null)
+    float *fsort;                 // per hit, sorted: the hot record's f alone (count gather, membership)
+    float *zsort;                 // per hit, sorted: z alone (membership; may be null when no stage 2 runs)
     ColdHit *cold;
     LayerRadii *radii;            // batch-wide
     LayerInfo *info;              // HOUGH_MAX_LAYERS
@@ -151,16 +153,17 @@ struct Workspace {
     int32_t *band_counts;         // n_events * n_bands
     int32_t *band_offs;           // n_events * n_bands
     hough_candidate *cands;       // n_events * max_cand
-    int32_t *mem_pool;            // n_events * max_members: event-local staged positions
-    int32_t *mem_start;           // n_events * max_cand
-    int32_t *mem_count;           // n_events * max_cand: entries written to the pool
-    int2 *large_list;             // n_events * max_cand (event, candidate): for the CTA stage-2 kernel
+    int32_t *mem_pool;            // max_members: event-local staged positions (contexts only)
+    int32_t *mem_start;           // max_cand (contexts only)
+    int32_t *mem_count;           // max_cand: entries written to the pool (contexts only)
     int32_t *cand_base;           // n_events + 1: first flattened candidate index of each event
     BatchCounters *counters;
     DevStats *stats;              // n_events
     int max_cand, max_members;
     int band_rows, band_cap;
     int fused;                    // vote_mode HOUGH_VOTE_FUSED: the vote kernel searched the bands
+    int keep_members;             // 1: confirmation writes member lists to mem_pool (contexts); 0: none (batches)
+    int copy_wait;                // < 0: the first bound on a bulk-copy wait expires at once (a test of the error path)
 };
 
 // Vote-kernel configuration.
@@ -267,7 +270,7 @@ constexpr int kStageLaunches = 4;
 constexpr int kVoteLaunches = 2;
 // peak search, compaction, and for batches of several events the candidate-base scan
 inline int peak_launches(int n_events) { return n_events == 1 ? 2 : 3; }
-constexpr int kStage2Launches = 2;
+constexpr int kStage2Launches = 1;
 
 // Exact FP64 helpers used by the staging, table and refinement code.  They evaluate the
 // definitions in the order of the method's formulas with explicitly rounded operations,

@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspa
         ch.z = in.z[h];
         ch.idx = (int32_t)(h - start);
         w.cold[pos] = ch;
+        if (w.zsort) w.zsort[pos] = ch.z;
     }
 }
 

@@ -6,8 +6,10 @@
 // afterwards.  Frameworks that hand all device memory to their own pool are in the same position.
 // Such callers cannot create a hough_ctx (hough_create allocates every buffer it needs).  This entry
 // point runs the same staging and vote kernels as hough_vote, but keeps their scratch in one
-// fixed, file-scope device array that the CUDA runtime reserves when it loads the library; the
-// caller passes only its inputs and the output accumulator.
+// fixed, file-scope device array; the caller passes only its inputs and the output accumulator.
+// The array is reserved on a device when the library's device code is loaded there: with the CUDA
+// runtime's lazy loading (its default) that is the first call on that device, which therefore
+// belongs to the caller's start-up, outside its real-time loop and before any stream capture.
 //
 // Limits of the fixed array (8 MiB per GPU that loads the library, held until the process exits):
 // at most kStaticMaxHits hits, n_qpt <= kStaticMaxQpt, n_phi <= kStaticMaxPhi, 16 layers.
@@ -23,7 +25,6 @@ constexpr int64_t kStaticMaxHits = 1 << 17;   // 131,072 hits
 constexpr int kStaticMaxQpt = 1024;
 constexpr int kStaticMaxPhi = 4096;
 constexpr int kStaticMaxKeys = HOUGH_MAX_LAYERS * kStaticMaxPhi;
-constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -51,19 +52,18 @@ static_assert(kStaticBytes <= (size_t)8 << 20, "the fixed scratch must stay with
 static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 
 std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device, looked up once per device.
-cudaError_t scratch_address(int device, unsigned char **out)
+// Device address of g_scratch on the current device.  It is looked up on every call (a table
+// lookup in the runtime, no allocation) rather than cached: after cudaDeviceReset, or once the
+// primary context has been released and created again, the module is loaded anew and the array
+// may sit elsewhere.
+cudaError_t scratch_address(unsigned char **out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[device] = p;
-    }
-    *out = static_cast<unsigned char *>(g_scratch_addr[device]);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 
@@ -71,8 +71,9 @@ cudaError_t scratch_address(int device, unsigned char **out)
 // copy would need a staging buffer.
 __global__ void static_kq_kernel(Axes ax, float *kq32)
 {
+    // rounded like the host's centres of a context: the product, then the sum, each rounded once
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ax.n_qpt) kq32[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
+    if (i < ax.n_qpt) kq32[i] = (float)__dadd_rn(ax.qpt_min, __dmul_rn((double)(i % ax.q_rows) + 0.5, ax.dk));
 }
 
 }  // namespace
@@ -87,6 +88,9 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
 {
     auto fail = [](int code, const char *msg) { return set_last_error(code, msg); };
     if (!g || !b || !accumulator) return fail(HOUGH_EINVAL, "geometry, binning and accumulator are required");
+    // the vote kernel writes the accumulator in 16-byte vectors
+    if (reinterpret_cast<uintptr_t>(accumulator) & 15u)
+        return fail(HOUGH_EINVAL, "hough_vote_static: the accumulator must be 16-byte aligned");
     if (g->n_layers < 1 || g->n_layers > HOUGH_MAX_LAYERS || !(g->b_tesla > 0.0))
         return fail(HOUGH_EINVAL, "n_layers must be 1..16 and b_tesla > 0");
     if (b->n_qpt < 1 || b->n_phi < 64 || b->n_phi % 64 || b->threshold < 1 || !(b->qpt_min < b->qpt_max))
@@ -102,10 +106,10 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
     if (n_hits > 0 && (!r || !phi || !z || !layer)) return fail(HOUGH_EINVAL, "hit arrays are required");
 
     int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices)
+    if (cudaGetDevice(&device) != cudaSuccess || device < 0)
         return fail(HOUGH_ECUDA, "no usable current device");
     unsigned char *base = nullptr;
-    if (scratch_address(device, &base) != cudaSuccess)
+    if (scratch_address(&base) != cudaSuccess)
         return fail(HOUGH_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed");
 
     const Axes ax = make_axes(g, b);   // host arithmetic only: nothing is allocated
@@ -137,7 +141,7 @@ extern "C" int hough_vote_static(const hough_geometry *g, const hough_binning *b
     Tiling t;
     t.tile_phi = b->n_phi < 256 ? b->n_phi : 256;
     while (b->n_phi % t.tile_phi) t.tile_phi -= 64;
-    t.tile_qpt = b->n_qpt < 16 ? b->n_qpt : 16;
+    t.tile_qpt = b->n_qpt < 32 ? b->n_qpt : 32;
     t.threads = 256;
     t.vote_mode = HOUGH_VOTE_SCATTER;   // the shared-atomic vote kernel alone: no bucket profile needed
     t.band_rows = 4;

@@ -53,6 +53,7 @@ struct VoteParams {
 };
 
 constexpr int kMaxRanges = 2 * HOUGH_MAX_LAYERS;
+constexpr int kRefineQueue = 64;   // a warp's queue of votes decided in FP64 (see scatter_kernel)
 constexpr int kCompactThreads = 1024;
 
 // Layers of the batch: bit l of *uniform_out is set when layer l takes the table path; bit l of
@@ -68,22 +69,55 @@ __device__ __forceinline__ void layer_masks(const Workspace &w, int L, unsigned 
     *general_out = __ballot_sync(0xFFFFFFFFu, l < L && li.present && !li.uniform);
 }
 
-template <int TPB, bool GENERAL_ONLY, bool COUNTS>
+// Shared tile of the scatter kernel, column-major: cell (row rr, column jt) of a tile of R rows
+// lives in word jt * pitch + rr (CELL 1: a layer mask a word; CELL 2: a 32-bit counter a word) or,
+// when that tile does not fit in shared memory, word (jt >> 1) * pitch + rr (CELL 0: two 16-bit layer
+// masks a word).  The lanes of a warp vote for 32 consecutive rows, so their 32 atomics fall in 32
+// different banks whatever columns the votes land in.
+__host__ __device__ inline int tile_row_pitch(int R) { return R <= 32 ? R : (R + 31) & ~31; }
+__host__ __device__ inline int scatter_tile_words(int R, int W, bool wide)
+{
+    return (wide ? W : W >> 1) * tile_row_pitch(R);
+}
+// Byte offset of the per-warp hit buffers in the scatter kernel's dynamic shared memory.
+__host__ __device__ inline size_t scatter_hit_offset(int R, int W, int L, bool wide)
+{
+    return ((size_t)scatter_tile_words(R, W, wide) * 4 + (size_t)L * R * sizeof(TabEntry) + (size_t)R * 4 + 15) &
+           ~(size_t)15;
+}
+
+// One shared atomic update of cell (rr, jt) of the tile: the layer bit (masks) or one vote (counts).
+template <int CELL>
+__device__ __forceinline__ void tile_vote(uint32_t *tile, int pitch, int rr, int jt, uint32_t lbit)
+{
+    if (CELL == 2) atomicAdd(&tile[jt * pitch + rr], 1u);
+    else if (CELL == 1) atomicOr(&tile[jt * pitch + rr], lbit);
+    else atomicOr(&tile[(jt >> 1) * pitch + rr], lbit << ((jt & 1) << 4));
+}
+
+template <int TPB, bool GENERAL_ONLY, int CELL>
 __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 {
+    constexpr bool COUNTS = CELL == 2;
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_start[kMaxRanges];
+    __shared__ int s_start[kMaxRanges], s_off[kMaxRanges];
     __shared__ int s_pre[kMaxRanges + 1];
     __shared__ unsigned long long s_refined;
     __shared__ unsigned s_umask, s_gmask;
 
     const Axes &ax = p.ax;
-    const int R = p.R, W = p.W, Wh = W >> 1, L = ax.n_layers, nphi = ax.n_phi;
-    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);   // 2 masks a word, or 1 counter a word
-    const int tile_words = COUNTS ? R * W : R * Wh;
+    const int R = p.R, W = p.W, L = ax.n_layers, nphi = ax.n_phi;
+    const int pitch = tile_row_pitch(R);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
+    const int tile_words = scatter_tile_words(R, W, CELL != 0);
     TabEntry *tab = reinterpret_cast<TabEntry *>(tile + tile_words);
     float *kq = reinterpret_cast<float *>(tab + L * R);
+    // the warp's 32 staged hits: f (bits), J (shifted into the window for a table layer), c (bits), rows
+    uint4 *hitbuf = reinterpret_cast<uint4 *>(smem_raw + scatter_hit_offset(R, W, L, CELL != 0)) + 32 * (threadIdx.x >> 5);
+    // the warp's queue of votes to be decided in FP64: (staged position, row | layer << 16)
+    uint2 *rq = reinterpret_cast<uint2 *>(smem_raw + scatter_hit_offset(R, W, L, CELL != 0) + (size_t)TPB * sizeof(uint4)) +
+                kRefineQueue * (threadIdx.x >> 5);
 
     const int e = blockIdx.x / p.tiles_per_event;
     const int t = blockIdx.x - e * p.tiles_per_event;
@@ -117,7 +151,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     for (int q = threadIdx.x; q < L * R; q += TPB) {
         const int l = q / R, rr = q - l * R;
         TabEntry te;
-        te.I = 0;
+        te.I = kNoVote;
         te.g = 0.f;
         if (!GENERAL_ONLY && rr < nrows && ((umask >> l) & 1u)) te = p.w.tab[l * ax.n_qpt + i0 + rr];
         tab[q] = te;
@@ -125,10 +159,12 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     for (int q = threadIdx.x; q < R; q += TPB) kq[q] = q < nrows ? p.w.kq32[i0 + q] : 0.f;
     __syncthreads();
 
-    // per layer, the hits that can vote into this tile: a cyclic range of phi bins J
+    // Per layer, the hits that can vote into this tile: a cyclic window [ja, jb] of phi bins J,
+    // as one or two ranges of the sorted hits.  s_off[q] is the shift that takes the J of range q's
+    // hits into the window's unwrapped coordinates (J + s_off in [ja, jb]).
     if (threadIdx.x < HOUGH_MAX_LAYERS) {
         const int l = threadIdx.x;
-        int nr = 0, st[2] = {0, 0}, ln[2] = {0, 0};
+        int nr = 0, st[2] = {0, 0}, ln[2] = {0, 0}, of[2] = {0, 0};
         if (l < L) {
             const int lstart = offs[l * nphi], lend = offs[(l + 1) * nphi];
             int ja = 0, jb = -1;   // inclusive J window, possibly beyond [0, nphi)
@@ -184,6 +220,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                 } else {
                     const int a = ((ja % nphi) + nphi) % nphi;
                     const int b = ((jb % nphi) + nphi) % nphi;
+                    of[0] = ja - a;
                     if (a <= b) {
                         nr = 1;
                         st[0] = offs[l * nphi + a];
@@ -194,12 +231,15 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                         ln[0] = lend - st[0];
                         st[1] = lstart;
                         ln[1] = offs[l * nphi + b + 1] - lstart;
+                        of[1] = ja - a + nphi;
                     }
                 }
             }
         }
         s_start[2 * l] = st[0];
         s_start[2 * l + 1] = st[1];
+        s_off[2 * l] = of[0];
+        s_off[2 * l + 1] = of[1];
         s_pre[2 * l] = nr >= 1 ? ln[0] : 0;       // lengths for now
         s_pre[2 * l + 1] = nr >= 2 ? ln[1] : 0;
     }
@@ -215,104 +255,191 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     }
     __syncthreads();
 
+    // A warp votes for 32 consecutive rows of the tile, a lane per row, taking the tile's hits 32
+    // at a time: the 32 are staged in the warp's buffer and broadcast one by one to all lanes.  For
+    // a table layer the lane's vote is j = J - I_row - (f < g_row): with the table entry in
+    // registers, a compare, an add and the atomic.  When the tile is at most a quarter of the row,
+    // the window of a layer's J is shorter than a row less the tile, so the vote lands in the tile
+    // exactly when (J + s_off) - (I + J0) - (f < g) lies in [0, W), with no reduction modulo Nphi.
     const int total = s_pre[kMaxRanges];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = TPB / 32;
+    const int NG = (R + 31) >> 5;           // groups of 32 rows
+    const int HS = max(1, NW / NG);         // warps sharing a row group's hits
+    const bool wrap = W > (nphi >> 2);
     unsigned long long refined = 0;
-    for (int base = warp * 32; base < total; base += TPB) {
-        const int v = base + lane;
-        const bool has = v < total;
-        HotHit hh;
-        hh.f = 0.f;
-        hh.c = 0.f;
-        hh.jl = 0u;
-        hh.rows = 1u;   // rows [1, 0]: none
-        int pos = 0;
-        if (has) {
-            int q = 0;
-            while (q + 1 < kMaxRanges && s_pre[q + 1] <= v) ++q;
-            pos = s_start[q] + (v - s_pre[q]);
-            hh = hot[pos];
+    // Votes of the per-vote path within the refine window are not decided in the loop below: a
+    // warp would run the FP64 arcsine for one lane.  They wait in the warp's queue, and every 32 of
+    // them are decided together, a lane each (and cast: the atomics commute).
+    int qn = 0;   // queued votes (the same in every lane)
+    auto flush_refines = [&]() {
+        __syncwarp();
+        for (int t = lane; t < qn; t += 32) {
+            const uint2 q = rq[t];
+            const int row = (int)(q.y & 0xFFFFu);
+            const ColdHit ch = cold[q.x];
+            const double x64 = __dmul_rn(sagitta_coef(ax, (double)ch.r), qpt_centre(ax, i0 + row));
+            const int jt = exact_bin(ax, (double)ch.phi, x64) - J0;
+            if ((unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, row, jt, 1u << (q.y >> 16));
         }
-        const int J = (int)(hh.jl & 0xFFFFu);
-        const int l = (int)((hh.jl >> 16) & 0xFu);
-        const int rlo = (int)(hh.rows & 0xFFFFu), rhi = (int)(hh.rows >> 16);
-        const bool uni = !GENERAL_ONLY && ((umask >> l) & 1u);
-        const uint32_t lbit = 1u << l;
-        for (int rr = 0; rr < nrows; ++rr) {
-            const int i = i0 + rr;
-            bool act = has && i >= rlo && i <= rhi;
-            int j;
-            if (uni) {
-                const TabEntry te = tab[l * R + rr];
-                act = act && te.I != kNoVote;
-                j = J - te.I - (hh.f < te.g ? 1 : 0);
-            } else if (ax.n_d0) {
-                // a grid with a d0 axis: every vote of a per-vote layer in FP64, in the definition's order
-                j = 0;
-                if (act) {
-                    const ColdHit ch = cold[pos];
-                    act = exact_vote(ax, (double)ch.r, (double)ch.phi, i, &j);
+        __syncwarp();
+        qn = 0;
+    };
+    for (int task = warp; task < NG * HS; task += NW) {
+        const int rr = (task % NG) * 32 + lane;
+        const int hs = task / NG;
+        const bool rowok = rr < nrows;
+        const int i = i0 + rr;
+        const float kqr = rowok ? kq[rr] : 0.f;
+        for (int cb = hs * 32; cb < total; cb += HS * 32) {
+            const int v = cb + lane;
+            const int nvalid = min(32, total - cb);
+            HotHit hh;
+            hh.f = 0.f;
+            hh.c = 0.f;
+            hh.jl = 0u;
+            hh.rows = 1u;   // rows [1, 0]: none
+            int pos = 0, off = 0, l = 16;
+            if (v < total) {
+                int q = 0;   // the range holding v: the last q with s_pre[q] <= v
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (s_pre[q + step] <= v) q += step;
+                pos = s_start[q] + (v - s_pre[q]);
+                off = s_off[q];
+                hh = hot[pos];
+                l = (int)((hh.jl >> 16) & 0xFu);
+            }
+            const int J = (int)(hh.jl & 0xFFFFu);
+            const bool table_hit = !GENERAL_ONLY && l < 16 && ((umask >> l) & 1u);
+            hitbuf[lane] = make_uint4(__float_as_uint(hh.f), (uint32_t)(wrap || !table_hit ? J : J + off),
+                                      __float_as_uint(hh.c), hh.rows);
+            __syncwarp();
+            // runs of hits of one layer (the ranges are in layer order)
+            const int lprev = __shfl_up_sync(0xFFFFFFFFu, l, 1);
+            unsigned heads = __ballot_sync(0xFFFFFFFFu, lane < nvalid && (lane == 0 || l != lprev));
+            while (heads) {
+                const int k0 = __ffs(heads) - 1;
+                heads &= heads - 1u;
+                const int k1 = heads ? __ffs(heads) - 1 : nvalid;
+                const int lr = __shfl_sync(0xFFFFFFFFu, l, k0);
+                const uint32_t lbit = 1u << lr;
+                if (!GENERAL_ONLY && ((umask >> lr) & 1u)) {
+                    const TabEntry te = tab[lr * R + (rowok ? rr : 0)];
+                    const bool valid = rowok && te.I != kNoVote;
+                    const float g = te.g;
+                    if (!wrap) {
+                        const int K = valid ? te.I + J0 : -(1 << 30);   // an invalid row's votes all miss
+                        // four hits at a time: their loads issue together, then their atomics
+                        int k = k0;
+                        const uint2 *hb2 = reinterpret_cast<const uint2 *>(hitbuf);   // (f, J) of hit k at 2 k
+                        for (; k + 4 <= k1; k += 4) {
+                            uint2 h[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) h[u] = hb2[2 * (k + u)];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int jt = (int)h[u].y - K - (__uint_as_float(h[u].x) < g ? 1 : 0);
+                                if ((unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                            }
+                        }
+                        for (; k < k1; ++k) {
+                            const uint2 h = hb2[2 * k];
+                            const int jt = (int)h.y - K - (__uint_as_float(h.x) < g ? 1 : 0);
+                            if ((unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                        }
+                    } else {
+                        for (int k = k0; k < k1; ++k) {
+                            const uint4 h = hitbuf[k];
+                            int j = (int)h.y - te.I - (__uint_as_float(h.x) < g ? 1 : 0);
+                            j += j < 0 ? nphi : 0;
+                            j -= j >= nphi ? nphi : 0;
+                            const int jt = j - J0;
+                            if (valid && (unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                        }
+                    }
+                    continue;
                 }
-            } else {
-                const float x = fminf(fmaxf(hh.c * kq[rr], -1.f), 1.f);
-                const float vq = fmaf(-asinf(x), p.s32, hh.f);
-                const float fl = floorf(vq);
-                const float d = vq - fl;
-                j = J + (int)fl;
-                if (act && (d < p.refine_eps || d > 1.f - p.refine_eps || fabsf(x) > kRefineXLim)) {
-                    const ColdHit ch = cold[pos];
-                    const double x64 = __dmul_rn(sagitta_coef(ax, (double)ch.r), qpt_centre(ax, i));
-                    j = exact_bin(ax, (double)ch.phi, x64);
-                    ++refined;
+                // a layer whose hits lie at several radii: every vote evaluated per hit
+                for (int k = k0; k < k1; ++k) {
+                    const uint4 h = hitbuf[k];
+                    const float c = __uint_as_float(h.z), fk = __uint_as_float(h.x);
+                    const uint32_t rows = h.w;
+                    const int Jk = (int)h.y;
+                    bool act = rowok && i >= (int)(rows & 0xFFFFu) && i <= (int)(rows >> 16);
+                    int j = 0;
+                    if (ax.n_d0) {
+                        // a grid with a d0 axis: every vote of a per-vote layer in FP64, in the definition's order
+                        const int pk = __shfl_sync(0xFFFFFFFFu, pos, k);
+                        if (act) {
+                            const ColdHit ch = cold[pk];
+                            act = exact_vote(ax, (double)ch.r, (double)ch.phi, i, &j);
+                        }
+                    } else {
+                        const float x = fminf(fmaxf(c * kqr, -1.f), 1.f);
+                        const float vq = fmaf(-asinf(x), p.s32, fk);
+                        const float fl = floorf(vq);
+                        const float d = vq - fl;
+                        j = Jk + (int)fl;
+                        const bool need = act && (d < p.refine_eps || d > 1.f - p.refine_eps || fabsf(x) > kRefineXLim);
+                        if (__any_sync(0xFFFFFFFFu, need)) {   // rare: queue them
+                            const int pk = __shfl_sync(0xFFFFFFFFu, pos, k);
+                            const unsigned rb = __ballot_sync(0xFFFFFFFFu, need);
+                            if (need) rq[qn + __popc(rb & ((1u << lane) - 1u))] = make_uint2((uint32_t)pk, (uint32_t)rr | ((uint32_t)lr << 16));
+                            qn += __popc(rb);
+                            if (lane == 0) refined += __popc(rb);
+                            act = act && !need;
+                        }
+                    }
+                    j += j < 0 ? nphi : 0;
+                    j -= j >= nphi ? nphi : 0;
+                    const int jt = j - J0;
+                    if (act && (unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                    if (qn >= 32) flush_refines();   // at most 63 queued
                 }
             }
-            j += j < 0 ? nphi : 0;
-            j -= j >= nphi ? nphi : 0;
-            const int jt = j - J0;
-            const bool in = act && (unsigned)jt < (unsigned)W;
-            if (COUNTS) {
-                // runs of lanes with the same cell: the first lane of a run adds the run's length
-                const uint32_t cell = in ? (uint32_t)(rr * W + jt) : 0xFFFFFFFFu;
-                const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cell, 1);
-                const bool head = lane == 0 || prev != cell;
-                const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
-                if (in && head) {
-                    const unsigned later = lane == 31 ? 0u : heads & (0xFFFFFFFFu << (lane + 1));
-                    const int end = later ? __ffs(later) - 1 : 32;
-                    atomicAdd(&tile[cell], (uint32_t)(end - lane));
-                }
-                continue;
-            }
-            const int word = rr * Wh + (jt >> 1);
-            const uint32_t tag = in ? (((uint32_t)word << 5) | ((uint32_t)l << 1) | (uint32_t)(jt & 1)) : 0xFFFFFFFFu;
-            const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, tag, 1);
-            if (in && !(lane > 0 && prev == tag)) atomicOr(&tile[word], lbit << ((jt & 1) << 4));
+            __syncwarp();   // the buffer is read before the next chunk overwrites it
         }
     }
+    if (qn) flush_refines();
     if (refined) atomicAdd(&s_refined, refined);
     __syncthreads();
 
-    // flush the tile: each row is W/8 16-byte vectors (ORed into the gathered layers' bits)
+    // flush the tile: 8 cells of a row per thread, consecutive threads on consecutive rows (one
+    // bank each in the column-major tile), one 16-byte store (ORed into the gathered layers' bits,
+    // or added to their counts, when only the layers of several radii were voted here)
     uint16_t *M = p.w.M + (int64_t)e * ax.n_qpt * nphi;
     const int v8 = W >> 3;
     for (int q = threadIdx.x; q < nrows * v8; q += TPB) {
-        const int rr = q / v8, c8 = q - rr * v8;
+        const int c8 = q / nrows, rr = q - c8 * nrows;
         uint4 *dst = reinterpret_cast<uint4 *>(M + (int64_t)(i0 + rr) * nphi + J0 + c8 * 8);
         if (COUNTS) {
-            // 8 counters, saturated to 16 bits and packed two a word (added to the gathered
-            // layers' counts when only the layers of several radii were voted here)
-            uint4 a = tile4[2 * (rr * v8 + c8)], b = tile4[2 * (rr * v8 + c8) + 1];
+            uint32_t cnt[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cnt[k] = tile[(c8 * 8 + k) * pitch + rr];
             if (GENERAL_ONLY) {
                 const uint4 old = *dst;
-                a.x += old.x & 0xFFFFu; a.y += old.x >> 16; a.z += old.y & 0xFFFFu; a.w += old.y >> 16;
-                b.x += old.z & 0xFFFFu; b.y += old.z >> 16; b.z += old.w & 0xFFFFu; b.w += old.w >> 16;
+                const uint32_t ow[4] = {old.x, old.y, old.z, old.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    cnt[2 * k] += ow[k] & 0xFFFFu;
+                    cnt[2 * k + 1] += ow[k] >> 16;
+                }
             }
             auto pack = [](uint32_t lo, uint32_t hi) { return min(lo, 65535u) | (min(hi, 65535u) << 16); };
-            *dst = make_uint4(pack(a.x, a.y), pack(a.z, a.w), pack(b.x, b.y), pack(b.z, b.w));
+            *dst = make_uint4(pack(cnt[0], cnt[1]), pack(cnt[2], cnt[3]), pack(cnt[4], cnt[5]), pack(cnt[6], cnt[7]));
             continue;
         }
-        uint4 v = tile4[rr * v8 + c8];
+        uint4 v;
+        if (CELL == 1) {   // a mask a word: pairs of cells into one word
+            uint32_t m[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m[k] = tile[(c8 * 8 + k) * pitch + rr];
+            v = make_uint4(m[0] | (m[1] << 16), m[2] | (m[3] << 16), m[4] | (m[5] << 16), m[6] | (m[7] << 16));
+        } else {
+            v = make_uint4(tile[(c8 * 4) * pitch + rr], tile[(c8 * 4 + 1) * pitch + rr], tile[(c8 * 4 + 2) * pitch + rr],
+                           tile[(c8 * 4 + 3) * pitch + rr]);
+        }
         if (GENERAL_ONLY) {
             const uint4 old = *dst;
             v.x |= old.x;
@@ -344,6 +471,16 @@ struct GatherParams {
 
 constexpr int kGatherRowsMax = 32;
 constexpr long long kCopyWaitCycles = 2000000000LL;   // about a second: bulk copies take microseconds
+
+// The first bound on the wait for a CTA's bulk copies: about a second, or none at all when a test of
+// the error path asked for it (Workspace::copy_wait < 0).  On expiry the CTA reports
+// HOUGH_DEVERR_TIMEOUT and waits once more, with the full bound, for its copies to land, so that it
+// leaves no copy writing into shared memory after it has exited (unless that wait expires too).
+__device__ __forceinline__ bool first_copy_wait(const Workspace &w, uint64_t *bar)
+{
+    if (w.copy_wait < 0) return false;
+    return mbar_wait_bounded(bar, 0, kCopyWaitCycles);
+}
 
 template <int NL, int TPB>
 __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
@@ -436,7 +573,7 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
                 if (first < len) bulk_copy_g2s(dst + first, src, 8u * (unsigned)(len - first), &s_bar);
             }
         }
-        const bool ok = mbar_wait_bounded(&s_bar, 0, kCopyWaitCycles);
+        const bool ok = first_copy_wait(w, &s_bar);
         if (!__syncthreads_and(ok)) {
             // the copies did not land in time: report it, give them one more bound, write nothing
             if (threadIdx.x == 0) atomicOr(&w.stats[e].device_error, HOUGH_DEVERR_TIMEOUT);
@@ -571,7 +708,7 @@ __global__ void __launch_bounds__(TPB) fused_kernel(GatherParams p)
                 if ((used >> l) & 1u)
                     bulk_copy_g2s(win + (int64_t)l * nphi, prof + (int64_t)l * pstride, 8u * (unsigned)nphi, &s_bar);
         }
-        const bool ok = mbar_wait_bounded(&s_bar, 0, kCopyWaitCycles);
+        const bool ok = first_copy_wait(w, &s_bar);
         if (!__syncthreads_and(ok)) {
             // the copies did not land in time: report it, give them one more bound, find nothing
             if (threadIdx.x == 0) {
@@ -1062,23 +1199,23 @@ __global__ void pack_candidates_kernel(Workspace w, hough_candidate *out, long l
     }
 }
 
-template <int TPB, bool GENERAL_ONLY, bool COUNTS>
+template <int TPB, bool GENERAL_ONLY, int CELL>
 cudaError_t launch_scatter(const VoteParams &p, size_t smem, int grid, cudaStream_t stream)
 {
-    cudaError_t err = cudaFuncSetAttribute(scatter_kernel<TPB, GENERAL_ONLY, COUNTS>,
+    cudaError_t err = cudaFuncSetAttribute(scatter_kernel<TPB, GENERAL_ONLY, CELL>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err) return err;
-    return launch_chained(scatter_kernel<TPB, GENERAL_ONLY, COUNTS>, dim3(grid), dim3(TPB), smem, stream, p);
+    return launch_chained(scatter_kernel<TPB, GENERAL_ONLY, CELL>, dim3(grid), dim3(TPB), smem, stream, p);
 }
 
-template <bool GENERAL_ONLY, bool COUNTS>
+template <bool GENERAL_ONLY, int CELL>
 cudaError_t launch_scatter_tpb(const VoteParams &p, int threads, size_t smem, int grid, cudaStream_t stream)
 {
     switch (threads) {
-    case 128: return launch_scatter<128, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
-    case 256: return launch_scatter<256, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
-    case 512: return launch_scatter<512, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
-    case 1024: return launch_scatter<1024, GENERAL_ONLY, COUNTS>(p, smem, grid, stream);
+    case 128: return launch_scatter<128, GENERAL_ONLY, CELL>(p, smem, grid, stream);
+    case 256: return launch_scatter<256, GENERAL_ONLY, CELL>(p, smem, grid, stream);
+    case 512: return launch_scatter<512, GENERAL_ONLY, CELL>(p, smem, grid, stream);
+    case 1024: return launch_scatter<1024, GENERAL_ONLY, CELL>(p, smem, grid, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1098,11 +1235,16 @@ size_t gather_count_smem_bytes(const Axes &ax, const Tiling &t)
     return base + fbytes;
 }
 
-size_t vote_smem_bytes(const Axes &ax, const Tiling &t)
+// Shared memory of the scatter kernel: the column-major tile, the slab's table rows and q/pT centres,
+// then a 32-hit buffer and a queue of FP64 votes per warp.  wide: a 32-bit word a cell.
+static size_t scatter_smem_bytes(const Axes &ax, const Tiling &t, bool wide)
 {
-    return (size_t)t.tile_qpt * t.tile_phi * (ax.counts ? 4 : 2) +
-           (size_t)ax.n_layers * t.tile_qpt * sizeof(TabEntry) + (size_t)t.tile_qpt * sizeof(float);
+    return scatter_hit_offset(t.tile_qpt, t.tile_phi, ax.n_layers, wide) + (size_t)t.threads * sizeof(uint4) +
+           (size_t)(t.threads / 32) * kRefineQueue * sizeof(uint2);
 }
+
+// The smallest form the tile can take: two 16-bit masks a word, or 32-bit counters.
+size_t vote_smem_bytes(const Axes &ax, const Tiling &t) { return scatter_smem_bytes(ax, t, ax.counts != 0); }
 
 
 static VoteParams vote_params(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps)
@@ -1257,13 +1399,28 @@ cudaError_t launch_scatter(const Axes &ax, const Workspace &w, const Tiling &t, 
                            cudaStream_t stream)
 {
     const VoteParams p = vote_params(ax, w, t, refine_eps);
-    const size_t smem = vote_smem_bytes(ax, t);
     const int grid = w.n_events * p.tiles_per_event;
-    if (ax.counts)
-        return general_only ? launch_scatter_tpb<true, true>(p, t.threads, smem, grid, stream)
-                            : launch_scatter_tpb<false, true>(p, t.threads, smem, grid, stream);
-    return general_only ? launch_scatter_tpb<true, false>(p, t.threads, smem, grid, stream)
-                        : launch_scatter_tpb<false, false>(p, t.threads, smem, grid, stream);
+    if (ax.counts) {
+        const size_t smem = scatter_smem_bytes(ax, t, true);
+        return general_only ? launch_scatter_tpb<true, 2>(p, t.threads, smem, grid, stream)
+                            : launch_scatter_tpb<false, 2>(p, t.threads, smem, grid, stream);
+    }
+    // a mask a word when that tile fits (no shift to place the bit), else two a word
+    static std::atomic<int> optin{0};
+    int m = optin.load(std::memory_order_relaxed);
+    if (!m) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&m, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) m = 48 * 1024;
+        optin.store(m, std::memory_order_relaxed);
+    }
+    const size_t wide = scatter_smem_bytes(ax, t, true);
+    if (wide + 1024 <= (size_t)m)
+        return general_only ? launch_scatter_tpb<true, 1>(p, t.threads, wide, grid, stream)
+                            : launch_scatter_tpb<false, 1>(p, t.threads, wide, grid, stream);
+    const size_t smem = scatter_smem_bytes(ax, t, false);
+    return general_only ? launch_scatter_tpb<true, 0>(p, t.threads, smem, grid, stream)
+                        : launch_scatter_tpb<false, 0>(p, t.threads, smem, grid, stream);
 }
 
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
