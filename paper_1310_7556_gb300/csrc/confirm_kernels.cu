@@ -405,7 +405,7 @@ struct PassOut {
 // (par, and the bit of each one's first pair in starts, counted from the chunk's first pair);
 // rlo / rhi widen to the rows their runs cover.  Otherwise (member lists): member r's staged
 // position goes to pool[r] for r < pool_n.
-template <int WPC, int CAP, int MAXP, bool RUNS>
+template <int WPC, int CAP, int MAXP, bool RUNS, bool GEN>
 __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, MAXP> &S, const HotHit *hot,
                                const float *fsort, const float *zsort, const ColdHit *cold, int i, int j, float s32,
                                float refine_eps, int lo, int &rlo, int &rhi, int32_t *pool = nullptr, int pool_n = 0)
@@ -462,7 +462,7 @@ __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, 
         bool mem = false;
         if (v < T) {
             if (!(kd & 32u)) mem = (f < gg) == ((kd & 16u) != 0u);   // side 1: f < g; side 0: f >= g
-            else mem = general_member(ax, w, hot, cold, p, i, j, s32, refine_eps);
+            else if (GEN) mem = general_member(ax, w, hot, cold, p, i, j, s32, refine_eps);
         }
         if (RUNS) {
             float a = 0.f, bb = 0.f;
@@ -473,9 +473,11 @@ __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, 
                 if (!(kd & 32u)) {
                     rb = S.rb[l];
                     table_coefficients(ax, S.zco[l], rb, z, l, &a, &bb, &mrl);
-                } else {
+                } else if (GEN) {
                     exact_coefficients(ax, l, i, cold[p], &a, &bb, &mrl);
                     rb = bb > 0.f ? __frcp_rn(bb) : 0.f;
+                } else {
+                    rb = 0.f;
                 }
                 member_run(ax, a, bb, rb, mrl, &mlo, &len);
             }
@@ -534,9 +536,13 @@ __device__ void vote_pairs(const Axes &ax, const Scratch<CAP, MAXP> &S, uint32_t
     for (int bw = 32 * wg; bw < npairs; bw += 32 * WPC) {
         const unsigned bits = S.starts[bw >> 5];
         const int owner = before + __popc(bits & ((2u << lane) - 1u)) - 1;
+        if (WPC == 1) {
+            before += __popc(bits);
+        } else {
 #pragma unroll
-        for (int k = 0; k < WPC; ++k)
-            if ((bw >> 5) + k < MAXP / 32) before += __popc(S.starts[(bw >> 5) + k]);
+            for (int k = 0; k < WPC; ++k)
+                if ((bw >> 5) + k < MAXP / 32) before += __popc(S.starts[(bw >> 5) + k]);
+        }
         const int v = bw + lane;
         if (v < npairs) {
             const int4 pr = S.par[owner];
@@ -550,22 +556,15 @@ __device__ void vote_pairs(const Axes &ax, const Scratch<CAP, MAXP> &S, uint32_t
     }
 }
 
-// Membership and stage 2 of every candidate of every event, a group of WPC warps per candidate.
-template <int WPC, int CAP, int MAXP, bool P10>
-__global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC == 1 ? 7 : 1)
-    confirm_kernel(Axes ax, Workspace w, float s32, float refine_eps, int grid_words, int scratch_bytes)
+// Membership and stage 2 of every candidate a group takes.  GEN: some layer's hits lie at several
+// radii (their votes are redone per hit, partly in FP64); without it that code is left out, which
+// spares the common path its registers.
+template <int WPC, int CAP, int MAXP, bool P10, bool GEN>
+__device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, float s32, float refine_eps,
+                                            Scratch<CAP, MAXP> &S, uint32_t *grid, const LayerInfo *s_info,
+                                            int ngroups, int gidx)
 {
-    pdl_enter();
-    extern __shared__ __align__(16) unsigned char smem_c[];
-    __shared__ LayerInfo s_info[HOUGH_MAX_LAYERS];
-    const int ngroups = WPC == 1 ? (int)(blockDim.x >> 5) : 1;
-    const int gidx = WPC == 1 ? (int)(threadIdx.x >> 5) : 0;
-    Scratch<CAP, MAXP> &S = *reinterpret_cast<Scratch<CAP, MAXP> *>(smem_c + (size_t)gidx * scratch_bytes);
-    uint32_t *grid = reinterpret_cast<uint32_t *>(smem_c + (size_t)ngroups * scratch_bytes) + (size_t)gidx * grid_words;
     const int tid = group_tid<WPC>(), lane = threadIdx.x & 31, wg = group_warp<WPC>();
-    if (threadIdx.x < HOUGH_MAX_LAYERS) s_info[threadIdx.x] = w.info[threadIdx.x];
-    for (int q = tid; q < grid_words; q += 32 * WPC) grid[q] = 0u;
-    __syncthreads();
     const int L = ax.n_layers, nphi = ax.n_phi, nkeys = L * nphi;
     const bool keep = w.keep_members != 0;
     const int total = (int)w.counters->total_cands;
@@ -622,7 +621,7 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
                             }
                         }
                     }
-                } else if (li.present) {
+                } else if (GEN && li.present) {
                     int sts[2] = {0, 0}, ens[2] = {0, 0};
                     const int nr = general_ranges(ax, w, offs, l, i, j, s32, sts, ens);
                     if (side < nr) {
@@ -656,13 +655,13 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
         unsigned best = 0u, votes = 0u;
         int rlo = INT_MAX, rhi = -1;
         const PassOut first =
-            member_pass<WPC, CAP, MAXP, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, 0, rlo, rhi);
+            member_pass<WPC, CAP, MAXP, true, GEN>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, 0, rlo, rhi);
         const int n = first.n;
         for (int lo = 0, kept = 0; lo < first.nrun; lo += kept) {
             PassOut po = first;
             if (lo > 0) {
                 group_sync<WPC>();   // the previous chunk's votes have read its members
-                po = member_pass<WPC, CAP, MAXP, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, lo, rlo,
+                po = member_pass<WPC, CAP, MAXP, true, GEN>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, lo, rlo,
                                                  rhi);
             }
             kept = po.nkept;
@@ -687,7 +686,7 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
                 w.mem_count[(int64_t)e * w.max_cand + c] = written;
             }
             if (written > 0)
-                member_pass<WPC, CAP, MAXP, false>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, 0, rlo, rhi,
+                member_pass<WPC, CAP, MAXP, false, GEN>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, 0, rlo, rhi,
                                              w.mem_pool + (int64_t)e * w.max_members + base, written);
         }
         // step 5: the group's best key and votes, the final mask of its cell, the touched rows cleared
@@ -726,6 +725,32 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
         if (acc_members) atomicAdd(&w.stats[acc_e].n_members, acc_members);
         if (acc_votes) atomicAdd(&w.stats[acc_e].stage2_votes, acc_votes);
     }
+}
+
+// Membership and stage 2 of every candidate of every event, a group of WPC warps per candidate.
+template <int WPC, int CAP, int MAXP, bool P10>
+__global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC == 1 ? 7 : 1)
+    confirm_kernel(Axes ax, Workspace w, float s32, float refine_eps, int grid_words, int scratch_bytes)
+{
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char smem_c[];
+    __shared__ LayerInfo s_info[HOUGH_MAX_LAYERS];
+    __shared__ int s_general;
+    const int ngroups = WPC == 1 ? (int)(blockDim.x >> 5) : 1;
+    const int gidx = WPC == 1 ? (int)(threadIdx.x >> 5) : 0;
+    Scratch<CAP, MAXP> &S = *reinterpret_cast<Scratch<CAP, MAXP> *>(smem_c + (size_t)gidx * scratch_bytes);
+    uint32_t *grid = reinterpret_cast<uint32_t *>(smem_c + (size_t)ngroups * scratch_bytes) + (size_t)gidx * grid_words;
+    if (threadIdx.x < HOUGH_MAX_LAYERS) s_info[threadIdx.x] = w.info[threadIdx.x];
+    for (int q = group_tid<WPC>(); q < grid_words; q += 32 * WPC) grid[q] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int g = 0;
+        for (int l = 0; l < ax.n_layers; ++l) g |= s_info[l].present && !s_info[l].uniform;
+        s_general = g;
+    }
+    __syncthreads();
+    if (s_general) confirm_all<WPC, CAP, MAXP, P10, true>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx);
+    else confirm_all<WPC, CAP, MAXP, P10, false>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx);
 }
 
 __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total)
