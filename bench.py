@@ -292,17 +292,26 @@ def measure_plain(env, args, ctx, tens, n):
            "stage_ms": kernel_ms, "attributed_ms_per_step": statistics.mean(attr_ms),
            "votes": int(st.votes), "general_votes": int(st.general_votes), "candidates": int(st.n_candidates),
            "members": int(st.n_members), "stage2_votes": int(st.stage2_votes), "launches": int(launches)}
-    # the same steps with the shared-atomic scatter vote (the paper's GPU design) for comparison
+    # the same steps with the shared-atomic scatter vote (the paper's GPU design) for comparison, in
+    # a few tile shapes (q/pT rows x phi0 columns x threads), the fastest reported
     tiling0 = ctx.get_tiling()
-    ctx.set_tiling(vote_mode=binding.VOTE_SCATTER)
-    for _ in range(3):
-        step()
-    sc_ms, sc_t = timed_steps(min(args.steps, 20), True)
+    best = None
+    for rows, cols, threads in ((32, 256, 1024), (27, 256, 1024), (32, 128, 1024), (32, 256, 512)):
+        if binding.grid_rows(ctx.binning) < rows or ctx.binning.n_phi % cols:
+            continue
+        ctx.set_tiling(vote_mode=binding.VOTE_SCATTER, tile_qpt=rows, tile_phi=cols, threads=threads)
+        for _ in range(3):
+            step()
+        sc_ms, sc_t = timed_steps(min(args.steps, 20), True)
+        r = {"events_per_s": len(sc_ms) / (sum(sc_ms) * 1e-3), "ms_per_step": statistics.mean(sc_ms),
+             "vote_ms": statistics.mean(t["vote_ms"] for t in sc_t),
+             "peaks_ms": statistics.mean(t["peaks_ms"] for t in sc_t),
+             "tile": {"tile_qpt": rows, "tile_phi": cols, "threads": threads}}
+        if best is None or r["vote_ms"] < best["vote_ms"]:
+            best = r
     ctx.set_tiling(**tiling0)
     ctx.enable_timing(False)
-    out["scatter"] = {"events_per_s": len(sc_ms) / (sum(sc_ms) * 1e-3), "ms_per_step": statistics.mean(sc_ms),
-                      "vote_ms": statistics.mean(t["vote_ms"] for t in sc_t),
-                      "peaks_ms": statistics.mean(t["peaks_ms"] for t in sc_t)}
+    out["scatter"] = best
     return out
 
 

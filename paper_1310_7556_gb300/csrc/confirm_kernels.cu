@@ -71,7 +71,7 @@ struct __align__(16) Scratch {
     int seg_pre[32], seg_start[32];
     unsigned seg_kind[32];
     float seg_g[32];
-    int wtmp[kMaxGroupWarps];
+    int wtmp[4 * kMaxGroupWarps];
     int n_seg, total, pool_base, pool_written;
 };
 
@@ -161,6 +161,38 @@ __device__ __forceinline__ unsigned group_reduce(unsigned v, int *wtmp)
     for (int k = 1; k < WPC; ++k) r = MAX ? max(r, (unsigned)wtmp[k]) : min(r, (unsigned)wtmp[k]);
     __syncthreads();
     return r;
+}
+
+// Warp totals v of N quantities made group-wide: the sums over the warps before this one (pre)
+// and over all (tot), in one exchange through shared memory (wx: WPC * N words).
+template <int WPC, int N>
+__device__ __forceinline__ void group_exchange(const int (&v)[N], int (&pre)[N], int (&tot)[N], int *wx)
+{
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        pre[n] = 0;
+        tot[n] = v[n];
+    }
+    if (WPC == 1) return;
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) wx[w * N + n] = v[n];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        int p = 0, t = 0;
+#pragma unroll
+        for (int k = 0; k < WPC; ++k) {
+            const int x = wx[k * N + n];
+            p += k < w ? x : 0;
+            t += x;
+        }
+        pre[n] = p;
+        tot[n] = t;
+    }
+    __syncthreads();
 }
 
 // Sum of v over the group, returned to every thread.
@@ -482,16 +514,29 @@ __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, 
                 member_run(ax, a, bb, rb, mrl, &mlo, &len);
             }
             const bool run = len > 0;
-            int nr, np;
-            const int r2 = out.nrun + group_excl_count<WPC>(run, &nr, S.wtmp);
-            const int s2 = pairs + group_excl_scan<WPC>(len, &np, S.wtmp);
+            // ranks and prefixes within the warp, then over the group in one exchange
+            const unsigned bmem = __ballot_sync(0xFFFFFFFFu, mem), brun = __ballot_sync(0xFFFFFFFFu, run);
+            int linc = len;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, linc, d);
+                if (lane >= d) linc += t;
+            }
+            int pre1[3], tot1[3];
+            group_exchange<WPC, 3>({__popc(brun), __shfl_sync(0xFFFFFFFFu, linc, 31), __popc(bmem)}, pre1, tot1, S.wtmp);
+            const int r2 = out.nrun + pre1[0] + __popc(brun & lanes_below());
+            const int s2 = pairs + pre1[1] + linc - len;
             if (lo > 0) before += (int)group_reduce_add<WPC>(run && r2 < lo ? (unsigned)len : 0u, S.wtmp);
             const int st = s2 - before;   // every member ranked below lo precedes this one
             // the kept ranks are contiguous: st + len and r2 grow together
             const bool keep = run && r2 >= lo && r2 - lo < CAP && st + len <= MAXP;
-            int nk;
-            const int slot = out.nkept + group_excl_count<WPC>(keep, &nk, S.wtmp);
-            out.npairs += (int)group_reduce_add<WPC>(keep ? (unsigned)len : 0u, S.wtmp);
+            const unsigned bkeep = __ballot_sync(0xFFFFFFFFu, keep);
+            int pre2[2], tot2[2];
+            group_exchange<WPC, 2>({__popc(bkeep), (int)__reduce_add_sync(0xFFFFFFFFu, keep ? (unsigned)len : 0u)},
+                                   pre2, tot2, S.wtmp);
+            const int slot = out.nkept + pre2[0] + __popc(bkeep & lanes_below());
+            const int nk = tot2[0], nr = tot1[0], np = tot1[1];
+            out.npairs += tot2[1];
             if (keep) {
                 const int c0 = mlo - st;
                 S.par[slot] = make_int4(__float_as_int(a), __float_as_int(bb),
@@ -503,7 +548,7 @@ __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, 
             out.nkept += nk;
             out.nrun += nr;
             pairs += np;
-            out.n += (int)group_reduce_add<WPC>(mem ? 1u : 0u, S.wtmp);
+            out.n += tot1[2];
         } else {
             int nm;
             const int r = out.n + group_excl_count<WPC>(mem, &nm, S.wtmp);
@@ -690,10 +735,27 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
                                              w.mem_pool + (int64_t)e * w.max_members + base, written);
         }
         // step 5: the group's best key and votes, the final mask of its cell, the touched rows cleared
-        best = group_reduce<WPC, true>(best, S.wtmp);
-        votes = group_reduce_add<WPC>(votes, S.wtmp);
-        rlo = (int)group_reduce<WPC, false>((unsigned)rlo, S.wtmp);
-        rhi = (int)group_reduce<WPC, true>((unsigned)(rhi + 1), S.wtmp) - 1;
+        best = __reduce_max_sync(0xFFFFFFFFu, best);
+        votes = __reduce_add_sync(0xFFFFFFFFu, votes);
+        rlo = (int)__reduce_min_sync(0xFFFFFFFFu, (unsigned)rlo);
+        rhi = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)(rhi + 1)) - 1;
+        if (WPC > 1) {   // the warps' results combined in one exchange
+            if (lane == 0) {
+                S.wtmp[4 * wg] = (int)best;
+                S.wtmp[4 * wg + 1] = (int)votes;
+                S.wtmp[4 * wg + 2] = rlo;
+                S.wtmp[4 * wg + 3] = rhi;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < WPC; ++k) {
+                best = max(best, (unsigned)S.wtmp[4 * k]);
+                votes += k == wg ? 0u : (unsigned)S.wtmp[4 * k + 1];
+                rlo = min(rlo, S.wtmp[4 * k + 2]);
+                rhi = max(rhi, S.wtmp[4 * k + 3]);
+            }
+            __syncthreads();
+        }
         group_sync<WPC>();   // every vote has landed
         const unsigned cell = best ? 0xFFFFu - (best & 0xFFFFu) : 0u;
         const uint32_t mask2 = best ? grid_mask<P10>(grid, cell) : 0u;

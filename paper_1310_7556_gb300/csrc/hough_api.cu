@@ -1,6 +1,7 @@
 // C ABI of the hough library (declared in include/hough.h): argument checks, the context and its
 // device buffers, and the order in which the kernels of the path are enqueued.
 #include <algorithm>
+#include <cstddef>
 #include <atomic>
 #include <cfloat>
 #include <cmath>
@@ -71,6 +72,12 @@ struct hough_ctx {
     DevStats *stats_mapped_dev = nullptr;
     int64_t n_hits = 0;
     int stage = 0;                       // 0 nothing, 1 voted, 2 peaks, 3 stage 2
+    // counters and radius ranges alternate between two buffers (Workspace::recycle); `clean`: the
+    // last event's kernels left the rest of the state as the next event starts from
+    DevStats *stats_buf[2] = {nullptr, nullptr};
+    LayerRadii *radii_buf[2] = {nullptr, nullptr};
+    int parity = 0;
+    bool clean = true;
     bool timing = false;
     // 0 before staging, 1 after staging, 2 after the gather, 3 after the vote, 4 after the band
     // peaks, 5 after the candidate scan, 6 after stage 2
@@ -350,13 +357,21 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     c->w.band_cap = band_capacity(c->ax, c->tiling.band_rows);
     c->w.fused = c->tiling.vote_mode == HOUGH_VOTE_FUSED;
     if (c->timing) { CU(cudaEventRecord(c->ev[0], s), "event"); c->timed |= 1 | (0xF << 8); }
-    CU(launch_stage(c->ax, c->w, s, c->timing ? c->ev + 8 : nullptr), "stage kernels");
+    // this event's counters and radius ranges; the other buffer of each is zeroed for the next one
+    c->w.stats = c->stats_buf[c->parity];
+    c->w.radii = c->radii_buf[c->parity];
+    c->w.stats_next = c->stats_buf[c->parity ^ 1];
+    c->w.radii_next = c->radii_buf[c->parity ^ 1];
+    const bool clear = !c->clean;   // the last event did not run its peak search: clear the state
+    CU(launch_stage(c->ax, c->w, s, c->timing ? c->ev + 8 : nullptr, clear), "stage kernels");
+    c->parity ^= 1;
+    c->clean = false;
     if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
     if (c->tiling.vote_mode != HOUGH_VOTE_SCATTER) CU(launch_gather(c->ax, c->w, c->tiling, s), "gather kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
     CU(launch_scatter(c->ax, c->w, c->tiling, c->refine_eps, c->tiling.vote_mode != HOUGH_VOTE_SCATTER, s), "vote kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[3], s), "event"); c->timed |= 8; }
-    g_launches += kStageLaunches + (c->tiling.vote_mode == HOUGH_VOTE_SCATTER ? 1 : kVoteLaunches);
+    g_launches += kStageLaunches - (clear ? 0 : 1) + (c->tiling.vote_mode == HOUGH_VOTE_SCATTER ? 1 : kVoteLaunches);
     c->stage = 1;
     return HOUGH_OK;
 }
@@ -448,7 +463,8 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&w.key, n)); A(c->alloc(&w.rank, n)); A(c->alloc(&w.hot_tmp, n));
     A(c->alloc(&w.counts, nkeys)); A(c->alloc(&w.offs, nkeys + 1)); A(c->alloc(&w.prof, (size_t)prof_event_entries(ax)));
     A(c->alloc(&w.hot, n)); A(c->alloc(&w.cold, n)); A(c->alloc(&w.fsort, n)); A(c->alloc(&w.zsort, n));
-    A(c->alloc(&w.radii, 1)); A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
+    A(c->alloc(&c->radii_buf[0], 1)); A(c->alloc(&c->radii_buf[1], 1));
+    A(c->alloc(&w.info, HOUGH_MAX_LAYERS)); A(c->alloc(&w.memo, 1));
     A(c->alloc(&w.tab, (size_t)ax.n_layers * ax.n_qpt)); A(c->alloc(&w.arc, (size_t)ax.n_layers * ax.n_qpt));
     A(c->alloc(&w.zco, (size_t)ax.n_layers * ax.n_qpt));
     A(c->alloc(&w.kq32, ax.n_qpt));
@@ -459,7 +475,7 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     A(c->alloc(&w.mem_start, w.max_cand)); A(c->alloc(&w.mem_count, w.max_cand));
     A(c->alloc(&w.cand_base, 2)); A(c->alloc(&w.counters, 1));
     A(c->alloc(&w.mem_pool, w.max_members)); A(c->alloc(&c->mem_idx, w.max_members));
-    A(c->alloc(&w.stats, 1));
+    A(c->alloc(&c->stats_buf[0], 1)); A(c->alloc(&c->stats_buf[1], 1));
     A(cudaMallocHost(&c->stats_host, sizeof(DevStats)));
     if (e != cudaSuccess) {
         delete c;
@@ -472,13 +488,26 @@ int hough_create(const hough_geometry *geometry, const hough_binning *binning, c
     w.band_cap = band_capacity(ax, c->tiling.band_rows);
     w.fused = 0;
     w.keep_members = 1;   // hough_get_members reads the member lists
+    w.recycle = 1;
+    w.compact_in_peaks = 1;
+    w.stats = c->stats_buf[0];
+    w.radii = c->radii_buf[0];
     // FP32 q/pT bin centres: the FP64 centre rounded once
     std::vector<float> kq(ax.n_qpt);
     for (int i = 0; i < ax.n_qpt; ++i) kq[i] = (float)(ax.qpt_min + (i % ax.q_rows + 0.5) * ax.dk);
     A(cudaMemcpy(w.kq32, kq.data(), sizeof(float) * ax.n_qpt, cudaMemcpyHostToDevice));
     A(cudaMemset(c->hit_start, 0, 2 * sizeof(int64_t)));
     A(cudaMemset(w.memo, 0, sizeof(TableMemo)));
-    A(cudaMemset(w.stats, 0, sizeof(DevStats)));
+    // the state every event starts from (Workspace::recycle keeps it so from then on)
+    for (int q = 0; q < 2; ++q) {
+        A(cudaMemset(c->stats_buf[q], 0, sizeof(DevStats)));
+        char *rb = reinterpret_cast<char *>(c->radii_buf[q]);
+        A(cudaMemset(rb + offsetof(LayerRadii, rmin), 0xFF, sizeof(LayerRadii::rmin)));
+        A(cudaMemset(rb + offsetof(LayerRadii, rmax), 0, sizeof(LayerRadii::rmax)));
+    }
+    A(cudaMemset(w.counts, 0, sizeof(int32_t) * nkeys));
+    A(cudaMemset(w.prof, 0, sizeof(uint2) * (size_t)prof_event_entries(ax)));
+    A(cudaMemset(w.counters, 0, sizeof(BatchCounters)));
     A(cudaDeviceSynchronize());
     if (e != cudaSuccess) {
         delete c;
@@ -503,11 +532,16 @@ int hough_peaks(hough_ctx *c, void *stream)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     if (c->stage < 1) return fail(HOUGH_ENOTREADY, "hough_vote has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
+    // the peak kernel's last CTA compacts the candidates, except after the fused vote (whose peak
+    // kernel may not run); either way the peak kernel zeroes the bucket profile for the next event
+    const bool fused = c->tiling.vote_mode == HOUGH_VOTE_FUSED;
+    c->w.compact_in_peaks = fused ? 0 : 1;
     CU(launch_band_peaks(c->ax, c->w, c->tiling, (cudaStream_t)stream), "peak kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
-    CU(launch_compact(c->ax, c->w, (cudaStream_t)stream), "candidate scan kernel");
+    if (fused) CU(launch_compact(c->ax, c->w, (cudaStream_t)stream), "candidate scan kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[5], (cudaStream_t)stream), "event"); c->timed |= 32; }
-    g_launches += peak_launches(1);
+    g_launches += fused ? peak_launches(1) : 1;
+    c->clean = true;
     c->stage = 2;
     return HOUGH_OK;
 }

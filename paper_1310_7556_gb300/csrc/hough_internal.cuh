@@ -119,7 +119,7 @@ struct HitInputs {
 struct BatchCounters {
     unsigned int total_cands;      // candidates kept over all events
     unsigned int pad1;
-    unsigned int pad0;
+    unsigned int peaks_done;       // CTAs of the peak search finished (compaction in the last one)
     unsigned int pad;
 };
 
@@ -164,6 +164,14 @@ struct Workspace {
     int fused;                    // vote_mode HOUGH_VOTE_FUSED: the vote kernel searched the bands
     int keep_members;             // 1: confirmation writes member lists to mem_pool (contexts); 0: none (batches)
     int copy_wait;                // < 0: the first bound on a bulk-copy wait expires at once (a test of the error path)
+    int compact_in_peaks;         // one event: the peak kernel's last CTA compacts the candidate list
+    // A context's state is left clean for its next event by the kernels that last use it, so that no
+    // clearing kernel opens the next event: the hit sort zeroes the bucket counts, the peak search
+    // the bucket profile, and the counting kernel the counters and radius ranges of the next event,
+    // which alternate between two buffers (the host may read this event's counters meanwhile).
+    int recycle;
+    DevStats *stats_next;         // recycle: the next event's counters, zeroed by the counting kernel
+    LayerRadii *radii_next;       // recycle: the next event's radius ranges, reset likewise
 };
 
 // Vote-kernel configuration.
@@ -205,7 +213,9 @@ inline float refine_eps_for(const Axes &ax) { return (float)(ax.n_phi * 5e-7 + 1
 // Kernel launchers (each enqueues on `stream` and returns the launch status).
 // `after`, when given, receives an event after each of the first four staging kernels (clear, count,
 // layer table, scan); the caller times the last one.
-cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream, cudaEvent_t *after = nullptr);
+// clear: open with the clearing kernel (else the state must have been left clean, Workspace::recycle).
+cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream, cudaEvent_t *after = nullptr,
+                         bool clear = true);
 cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, float refine_eps,
                         cudaStream_t stream);
 cudaError_t launch_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream);
@@ -228,7 +238,12 @@ cudaError_t run_smem_or_bench(int device, int pattern, double ms, double *atomic
 
 size_t vote_smem_bytes(const Axes &ax, const Tiling &t);
 // Shared memory of the peak search over bands of band_rows rows.
-size_t band_smem_bytes(const Axes &ax, int band_rows);
+__host__ __device__ inline size_t band_smem_bytes(const Axes &ax, int band_rows)
+{
+    // with a d0 axis the band's rows and their halo in three slices
+    const size_t rows = (size_t)(band_rows + 2) * (ax.n_d0 ? 3 : 1);
+    return rows * ax.n_phi * (ax.counts ? 2 : 1);
+}
 size_t stage2_smem_bytes(const Axes &ax);
 
 // Host helpers shared by the single-event and the batch entry points (hough_api.cu).

@@ -64,6 +64,15 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
         s_rmin[threadIdx.x] = 0xFFFFFFFFu;
         s_rmax[threadIdx.x] = 0u;
     }
+    if (w.recycle && blockIdx.x == 0) {
+        // the next event's counters and radius ranges (the other buffer of each pair)
+        uint32_t *sn = reinterpret_cast<uint32_t *>(w.stats_next);
+        for (int q = threadIdx.x; q < (int)(sizeof(DevStats) / 4); q += blockDim.x) sn[q] = 0u;
+        if (threadIdx.x < HOUGH_MAX_LAYERS) {
+            w.radii_next->rmin[threadIdx.x] = 0xFFFFFFFFu;
+            w.radii_next->rmax[threadIdx.x] = 0u;
+        }
+    }
     __syncthreads();
     const int nkeys = n_keys(ax);
     // FP32 sagitta coefficient of the per-vote path; its rounding is covered by the refine window
@@ -368,6 +377,16 @@ __global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspa
             if (n_l) atomicAdd(&w.stats[e].votes_by_layer[l], (unsigned long long)(n_l * li.nvote));
         }
     }
+    if (w.recycle) {
+        // the bucket counts are read for the last time by the scan, which this kernel follows
+        uint4 *c4 = reinterpret_cast<uint4 *>(w.counts);
+        const int64_t n4 = (int64_t)w.n_events * nkeys / 4;
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x)
+            c4[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (int64_t q = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)w.n_events * nkeys;
+             q += (int64_t)gridDim.x * blockDim.x)
+            w.counts[q] = 0;
+    }
     const int64_t total = hit_total(w);
     const HitInputs in = hit_inputs(w);
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total;
@@ -423,7 +442,7 @@ int grid_for(int64_t n, int threads)
 
 }  // namespace
 
-cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream, cudaEvent_t *after)
+cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream, cudaEvent_t *after, bool clear)
 {
     const int nkeys = n_keys(ax);
     ClearList cl{};
@@ -444,7 +463,7 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
     const int clear_grid = (int)std::min<long long>(2048, (vec_words + kClearThreads - 1) / kClearThreads);
     cudaError_t err;
     auto mark = [&](int k) { return after ? cudaEventRecord(after[k], stream) : cudaSuccess; };
-    if ((err = launch_chained(clear_kernel, dim3(std::max(1, clear_grid)), dim3(kClearThreads), 0, stream, cl)))
+    if (clear && (err = launch_chained(clear_kernel, dim3(std::max(1, clear_grid)), dim3(kClearThreads), 0, stream, cl)))
         return err;
     if ((err = mark(0))) return err;
     const int g = grid_for(w.n_hits_total >= 0 ? w.n_hits_total : w.hit_capacity, kStageThreads);

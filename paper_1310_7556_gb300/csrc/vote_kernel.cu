@@ -95,6 +95,19 @@ __device__ __forceinline__ void tile_vote(uint32_t *tile, int pitch, int rr, int
     else atomicOr(&tile[(jt >> 1) * pitch + rr], lbit << ((jt & 1) << 4));
 }
 
+// The same for a vote that may miss the tile (in false): every lane issues its atomic, a missing
+// vote adding nothing to a cell of its own row, so that no branch surrounds the atomic.  rowp,
+// stride: the lane's row of the tile and the column stride (pitch), or for a lane without a row of
+// the tile a word of its own with stride 0.
+template <int CELL>
+__device__ __forceinline__ void tile_vote_if(uint32_t *rowp, int stride, int jt, int W, bool in, uint32_t lbit)
+{
+    const int jc = (int)min((unsigned)jt, (unsigned)(W - 1));   // a column of the tile
+    if (CELL == 2) atomicAdd(&rowp[jc * stride], in ? 1u : 0u);
+    else if (CELL == 1) atomicOr(&rowp[jc * stride], in ? lbit : 0u);
+    else atomicOr(&rowp[(jc >> 1) * stride], in ? lbit << ((jc & 1) << 4) : 0u);
+}
+
 template <int TPB, bool GENERAL_ONLY, int CELL>
 __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 {
@@ -118,6 +131,9 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     // the warp's queue of votes to be decided in FP64: (staged position, row | layer << 16)
     uint2 *rq = reinterpret_cast<uint2 *>(smem_raw + scatter_hit_offset(R, W, L, CELL != 0) + (size_t)TPB * sizeof(uint4)) +
                 kRefineQueue * (threadIdx.x >> 5);
+    // 32 words that the atomics of lanes without a row of the tile go to (adding nothing)
+    uint32_t *spare = reinterpret_cast<uint32_t *>(smem_raw + scatter_hit_offset(R, W, L, CELL != 0) +
+                                                   (size_t)TPB * sizeof(uint4) + (size_t)(TPB / 32) * kRefineQueue * sizeof(uint2));
 
     const int e = blockIdx.x / p.tiles_per_event;
     const int t = blockIdx.x - e * p.tiles_per_event;
@@ -291,6 +307,8 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
         const bool rowok = rr < nrows;
         const int i = i0 + rr;
         const float kqr = rowok ? kq[rr] : 0.f;
+        uint32_t *rowp = rowok ? tile + rr : spare + lane;
+        const int stride = rowok ? pitch : 0;
         for (int cb = hs * 32; cb < total; cb += HS * 32) {
             const int v = cb + lane;
             const int nvalid = min(32, total - cb);
@@ -340,13 +358,13 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
                                 const int jt = (int)h[u].y - K - (__uint_as_float(h[u].x) < g ? 1 : 0);
-                                if ((unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                                tile_vote_if<CELL>(rowp, stride, jt, W, (unsigned)jt < (unsigned)W, lbit);
                             }
                         }
                         for (; k < k1; ++k) {
                             const uint2 h = hb2[2 * k];
                             const int jt = (int)h.y - K - (__uint_as_float(h.x) < g ? 1 : 0);
-                            if ((unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                            tile_vote_if<CELL>(rowp, stride, jt, W, (unsigned)jt < (unsigned)W, lbit);
                         }
                     } else {
                         for (int k = k0; k < k1; ++k) {
@@ -355,7 +373,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                             j += j < 0 ? nphi : 0;
                             j -= j >= nphi ? nphi : 0;
                             const int jt = j - J0;
-                            if (valid && (unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                            tile_vote_if<CELL>(rowp, stride, jt, W, valid && (unsigned)jt < (unsigned)W, lbit);
                         }
                     }
                     continue;
@@ -394,7 +412,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                     j += j < 0 ? nphi : 0;
                     j -= j >= nphi ? nphi : 0;
                     const int jt = j - J0;
-                    if (act && (unsigned)jt < (unsigned)W) tile_vote<CELL>(tile, pitch, rr, jt, lbit);
+                    tile_vote_if<CELL>(rowp, stride, jt, W, act && (unsigned)jt < (unsigned)W, lbit);
                     if (qn >= 32) flush_refines();   // at most 63 queued
                 }
             }
@@ -932,6 +950,19 @@ __global__ void __launch_bounds__(TPB) gather_count_kernel(GatherParams p, int f
     }
 }
 
+__device__ void compact_if_last(const Axes &ax, const Workspace &w, void *buf, size_t buf_bytes);
+
+// A context's bucket profile is read for the last time by the vote, which the peak search follows:
+// zero it here for the next event (Workspace::recycle).
+__device__ __forceinline__ void recycle_profile(const Axes &ax, const Workspace &w)
+{
+    if (!w.recycle || !w.prof) return;
+    uint4 *p4 = reinterpret_cast<uint4 *>(w.prof);
+    const int64_t n4 = (int64_t)w.n_events * prof_event_entries(ax) / 2;   // two entries a vector
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x)
+        p4[q] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Peak search of one band of band_rows rows from the accumulator (plus a halo row on each side).
 // COUNTS: the cells are vote counts, staged as they are (2 bytes each); otherwise layer masks,
 // staged as their layer counts (1 byte each).
@@ -939,6 +970,7 @@ template <bool COUNTS>
 __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace w)
 {
     pdl_enter();
+    recycle_profile(ax, w);
     if (!COUNTS && w.fused && all_layers_uniform(ax, w)) return;   // the fused vote searched the bands
     extern __shared__ __align__(16) unsigned char pc[];
     const int R = w.band_rows;
@@ -962,6 +994,8 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
         __syncthreads();
         const int cnt = band_peak_search<kPeakThreads>(pv, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
         if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+        __syncthreads();   // the band buffer is free
+        compact_if_last(ax, w, pc, band_smem_bytes(ax, R));
         return;
     }
     for (int q = threadIdx.x; q < (nrows + 2) * v8; q += kPeakThreads) {
@@ -981,6 +1015,8 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
     __syncthreads();
     const int cnt = band_peak_search<kPeakThreads>(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
     if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+    __syncthreads();   // the band buffer is free
+    compact_if_last(ax, w, pc, band_smem_bytes(ax, R));
 }
 
 // Peak search of one band of band_rows q/pT rows of one d0 slice m of a grid with a d0 axis: the
@@ -992,6 +1028,7 @@ template <bool COUNTS>
 __global__ void __launch_bounds__(kPeakThreads) peaks3_kernel(Axes ax, Workspace w)
 {
     pdl_enter();
+    recycle_profile(ax, w);
     extern __shared__ __align__(16) unsigned char pc[];
     const int R = w.band_rows, Q = ax.q_rows;
     const int bps = (Q + R - 1) / R;   // bands per slice
@@ -1034,30 +1071,33 @@ __global__ void __launch_bounds__(kPeakThreads) peaks3_kernel(Axes ax, Workspace
         cnt = band_peak_search<kPeakThreads, unsigned char, true>(pc, nrows, row0, nphi, ax.threshold, M, out,
                                                                   w.band_cap);
     if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
+    __syncthreads();   // the band buffer is free
+    compact_if_last(ax, w, pc, band_smem_bytes(ax, R));
 }
 
-// One CTA per event: exclusive scan of the band counts, then the band lists concatenated into
-// the raster-ordered candidate list (the first max_cand of them).  With the band offsets in shared
-// memory every thread copies candidates by their index (the band found by binary search), so the
-// copy costs one round trip however the candidates fall into bands.  `single`: the batch is one
-// event, whose flattened candidate base this kernel then writes itself.
+// One event's candidate list: exclusive scan of the band counts, then the band lists concatenated
+// into the raster-ordered candidate list (the first max_cand of them).  With the band offsets in
+// shared memory every thread copies candidates by their index (the band found by binary search
+// over the offsets), so the copy costs one round trip however the candidates fall into bands.
+// `parts` CTAs may share an event, each copying its slice (this one is `part`); part 0 also records
+// the event's totals (and handles band counts too many to stage).  `single`: the batch is one
+// event, whose flattened candidate base this CTA then writes itself.  Called by all TPB threads.
+// The band offsets are staged in shared memory when they fit (`offs_smem`, `offs_cap` entries);
+// otherwise they go through device memory and a warp copies a band at a time.
 constexpr int kCompactSmemBands = 4096;
 
-__global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w, int single, int parts)
+template <int TPB>
+__device__ void compact_event(const Axes &ax, const Workspace &w, int e, int part, int parts, int single,
+                              int *s_offs, int offs_cap)
 {
-    pdl_enter();
-    __shared__ int s_warp[kCompactThreads / 32];
-    __shared__ int s_offs[kCompactSmemBands + 1];
-    // `parts` CTAs per event: each scans the band counts and copies its slice of the candidates;
-    // the first also records the event's totals (and handles band counts too many to stage)
-    const int e = blockIdx.x / parts, part = blockIdx.x - e * parts;
+    __shared__ int s_warp[TPB / 32];
     const int nb = n_bands(ax, w.band_rows);
-    const bool staged = nb <= kCompactSmemBands;
+    const bool staged = nb + 1 <= offs_cap;
     const int32_t *counts = w.band_counts + (int64_t)e * nb;
     int32_t *offs = w.band_offs + (int64_t)e * nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int chunk = (nb + kCompactThreads - 1) / kCompactThreads;
-    const int k0 = min(nb, threadIdx.x * chunk), k1 = min(nb, k0 + chunk);
+    const int chunk = (nb + TPB - 1) / TPB;
+    const int k0 = min(nb, (int)threadIdx.x * chunk), k1 = min(nb, k0 + chunk);
     int sum = 0;
     for (int k = k0; k < k1; ++k) sum += counts[k];
     int incl = sum;
@@ -1069,13 +1109,13 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int wv = s_warp[lane];
+        int wv = lane < TPB / 32 ? s_warp[lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int t = __shfl_up_sync(0xFFFFFFFFu, wv, d);
             if (lane >= d) wv += t;
         }
-        s_warp[lane] = wv;
+        if (lane < TPB / 32) s_warp[lane] = wv;
     }
     __syncthreads();
     int run = (warp > 0 ? s_warp[warp - 1] : 0) + incl - sum;
@@ -1084,7 +1124,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
         else if (part == 0) offs[k] = run;
         run += counts[k];
     }
-    const int total = s_warp[kCompactThreads / 32 - 1];
+    const int total = s_warp[TPB / 32 - 1];
     const int kept = min(total, w.max_cand);
     if (part == 0 && threadIdx.x == 0) {
         w.stats[e].n_candidates = (unsigned)total;
@@ -1110,7 +1150,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
     if (staged) {
         const int per = (kept + parts - 1) / parts;
         const int c_end = min(kept, (part + 1) * per);
-        for (int c = part * per + threadIdx.x; c < c_end; c += kCompactThreads) {
+        for (int c = part * per + threadIdx.x; c < c_end; c += TPB) {
             // the band holding candidate c: the last b with offs[b] <= c (empty bands share offsets)
             int lo = 0, hi = nb - 1;
             while (lo < hi) {
@@ -1122,7 +1162,8 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
         return;
     }
     if (part != 0) return;
-    for (int b = warp; b < nb; b += kCompactThreads / 32) {
+    __syncthreads();   // the offsets in device memory are complete
+    for (int b = warp; b < nb; b += TPB / 32) {
         const int n = counts[b], o = offs[b];
         for (int k = lane; k < n; k += 32) {
             const int c = o + k;
@@ -1130,6 +1171,32 @@ __global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Works
             emit(c, lists[(int64_t)b * w.band_cap + k]);
         }
     }
+}
+
+__global__ void __launch_bounds__(kCompactThreads) compact_kernel(Axes ax, Workspace w, int single, int parts)
+{
+    pdl_enter();
+    __shared__ int s_offs[kCompactSmemBands + 1];
+    compact_event<kCompactThreads>(ax, w, blockIdx.x / parts, blockIdx.x % parts, parts, single, s_offs,
+                                   kCompactSmemBands + 1);
+}
+
+// One event in one context: the CTA of the peak search that finishes last compacts the candidate
+// list itself, saving the launch of the compaction (the band counts and lists of every CTA are
+// visible to it after their fences).  Its band buffer (`buf`, `buf_bytes`), no longer needed,
+// holds the band offsets.
+__device__ void compact_if_last(const Axes &ax, const Workspace &w, void *buf, size_t buf_bytes)
+{
+    __shared__ int s_last;
+    if (!w.compact_in_peaks) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&w.counters->peaks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    compact_event<kPeakThreads>(ax, w, 0, 0, 1, 1, static_cast<int *>(buf), (int)(buf_bytes / sizeof(int)));
+    if (threadIdx.x == 0) w.counters->peaks_done = 0u;   // ready for the next event
 }
 
 // One CTA: the first flattened candidate index of every event (kept candidates only), so that
@@ -1240,7 +1307,7 @@ size_t gather_count_smem_bytes(const Axes &ax, const Tiling &t)
 static size_t scatter_smem_bytes(const Axes &ax, const Tiling &t, bool wide)
 {
     return scatter_hit_offset(t.tile_qpt, t.tile_phi, ax.n_layers, wide) + (size_t)t.threads * sizeof(uint4) +
-           (size_t)(t.threads / 32) * kRefineQueue * sizeof(uint2);
+           (size_t)(t.threads / 32) * kRefineQueue * sizeof(uint2) + 32 * sizeof(uint32_t);
 }
 
 // The smallest form the tile can take: two 16-bit masks a word, or 32-bit counters.
@@ -1434,12 +1501,6 @@ cudaError_t launch_vote(const Axes &ax, const Workspace &w, const Tiling &t, flo
     return launch_scatter(ax, w, t, refine_eps, true, stream);
 }
 
-size_t band_smem_bytes(const Axes &ax, int band_rows)
-{
-    // with a d0 axis the band's rows and their halo in three slices
-    const size_t rows = (size_t)(band_rows + 2) * (ax.n_d0 ? 3 : 1);
-    return rows * ax.n_phi * (ax.counts ? 2 : 1);
-}
 
 cudaError_t launch_band_peaks(const Axes &ax, const Workspace &w, const Tiling &t, cudaStream_t stream)
 {
