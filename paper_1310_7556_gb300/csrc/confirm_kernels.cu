@@ -57,6 +57,7 @@ constexpr int kEventCap = 256;     // members a four-warp group holds at a time 
 constexpr int kEventPairs = 4096;  // pairs it votes at a time
 constexpr int kEventWarps = 4;     // warps per candidate for a single event
 constexpr int kBatchGroups = 4;    // one-warp groups per CTA at most (batches)
+constexpr int kMaxBandsRead = 8192;   // band offsets a single event's CTA may hold to read the band lists
 
 // Per-group scratch.  Kind of a range: bits 0..3 the layer, bit 4 the side (1: f < g), bit 5 a
 // layer whose hits lie at several radii (each hit's vote recomputed).
@@ -601,18 +602,49 @@ __device__ void vote_pairs(const Axes &ax, const Scratch<CAP, MAXP> &S, uint32_t
     }
 }
 
+// Exclusive prefix of counts[0, n) into out[0, n] (out[n]: the sum, also returned), by the whole CTA.
+__device__ int block_excl_scan(const int32_t *counts, int n, int *out)
+{
+    __shared__ int s_w[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int k0 = min(n, (int)threadIdx.x * chunk), k1 = min(n, k0 + chunk);
+    int sum = 0;
+    for (int k = k0; k < k1; ++k) sum += counts[k];
+    int incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int k = 0; k < nw; ++k) {
+        before += k < warp ? s_w[k] : 0;
+        all += s_w[k];
+    }
+    int run = before + incl - sum;
+    for (int k = k0; k < k1; ++k) {
+        out[k] = run;
+        run += counts[k];
+    }
+    if (threadIdx.x == 0) out[n] = all;
+    __syncthreads();
+    return all;
+}
+
 // Membership and stage 2 of every candidate a group takes.  GEN: some layer's hits lie at several
 // radii (their votes are redone per hit, partly in FP64); without it that code is left out, which
 // spares the common path its registers.
 template <int WPC, int CAP, int MAXP, bool P10, bool GEN>
 __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, float s32, float refine_eps,
                                             Scratch<CAP, MAXP> &S, uint32_t *grid, const LayerInfo *s_info,
-                                            int ngroups, int gidx)
+                                            int ngroups, int gidx, int total, const int *band_offs)
 {
     const int tid = group_tid<WPC>(), lane = threadIdx.x & 31, wg = group_warp<WPC>();
     const int L = ax.n_layers, nphi = ax.n_phi, nkeys = L * nphi;
     const bool keep = w.keep_members != 0;
-    const int total = (int)w.counters->total_cands;
     // the event's counters, summed by the group's first thread over the event's candidates it takes
     int acc_e = -1;
     unsigned acc_members = 0u;
@@ -639,7 +671,22 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
         const ColdHit *cold = w.cold + hstart;
         const int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
         hough_candidate *cands = w.cands + (int64_t)e * w.max_cand;
-        const hough_candidate cd = load_candidate(cands + c);
+        hough_candidate cd;
+        if (WPC > 1 && band_offs) {
+            // one event whose candidate list was not compacted: candidate c from its band's list
+            int b = 0, hi = n_bands(ax, w.band_rows) - 1;   // the last band with offset <= c (shared memory)
+            while (b < hi) {
+                const int mid = (b + hi + 1) >> 1;
+                if (band_offs[mid] <= c) b = mid; else hi = mid - 1;
+            }
+            const uint2 v = w.band_cands[(int64_t)b * w.band_cap + (c - band_offs[b])];
+            cd.iq = v.x / (unsigned)nphi;
+            cd.jphi = v.x % (unsigned)nphi;
+            cd.mask = v.y;
+            cd.n_members = cd.icot = cd.jz0 = cd.mask2 = cd.flags = 0u;
+        } else {
+            cd = load_candidate(cands + c);
+        }
         const int i = (int)cd.iq, j = (int)cd.jphi;
         // step 1: the candidate's ranges, lane t of the first warp taking range t = (layer t/2, side t%2)
         if (wg == 0) {
@@ -811,8 +858,31 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
         s_general = g;
     }
     __syncthreads();
-    if (s_general) confirm_all<WPC, CAP, MAXP, P10, true>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx);
-    else confirm_all<WPC, CAP, MAXP, P10, false>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx);
+    // one event of a context whose candidate list was not compacted: every CTA scans the band counts
+    // into shared memory (behind the groups' scratch and grids) and reads its candidates from the
+    // band lists; the first CTA records the totals the compaction would have
+    int total;
+    const int *band_offs = nullptr;
+    if (WPC > 1 && w.cands_from_bands) {   // (batches use one-warp groups and a compacted list)
+        int *bo = reinterpret_cast<int *>(smem_c + (size_t)ngroups * scratch_bytes + (size_t)ngroups * grid_words * 4);
+        const int nb = n_bands(ax, w.band_rows);
+        const int found = block_excl_scan(w.band_counts, nb, bo);
+        total = min(found, w.max_cand);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            w.stats[0].n_candidates = (unsigned)found;
+            if (found > w.max_cand) atomicOr(&w.stats[0].device_error, HOUGH_DEVERR_CAND);
+            w.cand_base[0] = 0;
+            w.cand_base[1] = total;
+            w.counters->total_cands = (unsigned)total;
+        }
+        band_offs = bo;
+    } else {
+        total = (int)w.counters->total_cands;
+    }
+    if (s_general)
+        confirm_all<WPC, CAP, MAXP, P10, true>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
+    else
+        confirm_all<WPC, CAP, MAXP, P10, false>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
 }
 
 __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total)
@@ -871,7 +941,8 @@ cudaError_t launch_confirm(const Axes &ax, const Workspace &w, int sms, float s3
     // one-warp groups: as many per CTA (up to kBatchGroups) as shared memory holds
     const int room = smem_optin() - (int)(sizeof(LayerInfo) * HOUGH_MAX_LAYERS) - 1024;
     const int groups = WPC == 1 ? std::max(1, std::min(kBatchGroups, room / (int)per_group)) : 1;
-    const size_t smem = (size_t)groups * per_group;
+    const size_t smem = (size_t)groups * per_group +
+                        (w.cands_from_bands ? ((size_t)n_bands(ax, w.band_rows) + 1) * sizeof(int) : 0);
     cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (!err) err = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
@@ -887,6 +958,8 @@ cudaError_t launch_confirm(const Axes &ax, const Workspace &w, int sms, float s3
 }  // namespace
 
 size_t stage2_smem_bytes(const Axes &ax) { return (size_t)grid_words_for(ax, false) * 4; }
+
+bool stage2_reads_bands(const Axes &ax, int band_rows) { return n_bands(ax, band_rows) <= kMaxBandsRead; }
 
 cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float refine_eps, cudaStream_t stream,
                           cudaEvent_t between)

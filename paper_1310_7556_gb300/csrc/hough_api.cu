@@ -78,6 +78,9 @@ struct hough_ctx {
     LayerRadii *radii_buf[2] = {nullptr, nullptr};
     int parity = 0;
     bool clean = true;
+    // the peak search left the candidate list uncompacted (stage 2 reads the band lists itself);
+    // a call that reads the list or the counters before stage 2 compacts it first
+    bool list_pending = false;
     bool timing = false;
     // 0 before staging, 1 after staging, 2 after the gather, 3 after the vote, 4 after the band
     // peaks, 5 after the candidate scan, 6 after stage 2
@@ -366,6 +369,7 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     CU(launch_stage(c->ax, c->w, s, c->timing ? c->ev + 8 : nullptr, clear), "stage kernels");
     c->parity ^= 1;
     c->clean = false;
+    c->list_pending = false;
     if (c->timing) { CU(cudaEventRecord(c->ev[1], s), "event"); c->timed |= 2; }
     if (c->tiling.vote_mode != HOUGH_VOTE_SCATTER) CU(launch_gather(c->ax, c->w, c->tiling, s), "gather kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[2], s), "event"); c->timed |= 4; }
@@ -376,8 +380,20 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     return HOUGH_OK;
 }
 
+// The compaction a peak search left to stage 2, run now for a caller that reads the list first.
+int settle_list(hough_ctx *c, cudaStream_t s)
+{
+    if (!c->list_pending) return HOUGH_OK;
+    CU(launch_compact(c->ax, c->w, s), "candidate scan kernel");
+    g_launches += peak_launches(1) - 1;
+    c->list_pending = false;
+    return HOUGH_OK;
+}
+
 int read_stats(hough_ctx *c, cudaStream_t s)
 {
+    int rc = settle_list(c, s);
+    if (rc) return rc;
     CU(cudaMemcpyAsync(c->stats_host, c->w.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "copy stats");
     CU(cudaStreamSynchronize(s), "synchronise");
     return HOUGH_OK;
@@ -532,15 +548,19 @@ int hough_peaks(hough_ctx *c, void *stream)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     if (c->stage < 1) return fail(HOUGH_ENOTREADY, "hough_vote has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    // the peak kernel's last CTA compacts the candidates, except after the fused vote (whose peak
-    // kernel may not run); either way the peak kernel zeroes the bucket profile for the next event
+    // The candidate list: stage 2 reads the band lists itself when their offsets fit its shared
+    // memory (the list is compacted later only for a caller that reads it first); else the peak
+    // kernel's last CTA compacts it, except after the fused vote (whose peak kernel may not run).
+    // Either way the peak kernel zeroes the bucket profile for the next event.
     const bool fused = c->tiling.vote_mode == HOUGH_VOTE_FUSED;
-    c->w.compact_in_peaks = fused ? 0 : 1;
+    const bool deferred = !fused && stage2_reads_bands(c->ax, c->tiling.band_rows);
+    c->w.compact_in_peaks = fused || deferred ? 0 : 1;
     CU(launch_band_peaks(c->ax, c->w, c->tiling, (cudaStream_t)stream), "peak kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
     if (fused) CU(launch_compact(c->ax, c->w, (cudaStream_t)stream), "candidate scan kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[5], (cudaStream_t)stream), "event"); c->timed |= 32; }
     g_launches += fused ? peak_launches(1) : 1;
+    c->list_pending = deferred;
     c->clean = true;
     c->stage = 2;
     return HOUGH_OK;
@@ -551,8 +571,11 @@ int hough_stage2(hough_ctx *c, void *stream)
     if (!c) return fail(HOUGH_EINVAL, "ctx is required");
     if (c->stage < 2) return fail(HOUGH_ENOTREADY, "hough_peaks has not run");
     CU(cudaSetDevice(c->device), "cudaSetDevice");
+    c->w.cands_from_bands = c->list_pending ? 1 : 0;   // the confirmation compacts as it goes
     CU(launch_stage2(c->ax, c->w, c->sms, c->refine_eps, (cudaStream_t)stream, c->timing ? c->ev[7] : nullptr),
        "stage-2 kernels");
+    c->w.cands_from_bands = 0;
+    c->list_pending = false;
     if (c->timing) { CU(cudaEventRecord(c->ev[6], (cudaStream_t)stream), "event"); c->timed |= 64 | 128; }
     g_launches += kStage2Launches;
     c->stage = 3;

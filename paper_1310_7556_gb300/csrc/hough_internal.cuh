@@ -165,6 +165,7 @@ struct Workspace {
     int keep_members;             // 1: confirmation writes member lists to mem_pool (contexts); 0: none (batches)
     int copy_wait;                // < 0: the first bound on a bulk-copy wait expires at once (a test of the error path)
     int compact_in_peaks;         // one event: the peak kernel's last CTA compacts the candidate list
+    int cands_from_bands;         // one event: the confirmation reads its candidates from the band lists
     // A context's state is left clean for its next event by the kernels that last use it, so that no
     // clearing kernel opens the next event: the hit sort zeroes the bucket counts, the peak search
     // the bucket profile, and the counting kernel the counters and radius ranges of the next event,
@@ -245,6 +246,8 @@ __host__ __device__ inline size_t band_smem_bytes(const Axes &ax, int band_rows)
     return rows * ax.n_phi * (ax.counts ? 2 : 1);
 }
 size_t stage2_smem_bytes(const Axes &ax);
+// Whether the confirmation of one event may read its candidates straight from the band lists.
+bool stage2_reads_bands(const Axes &ax, int band_rows);
 
 // Host helpers shared by the single-event and the batch entry points (hough_api.cu).
 Axes make_axes(const hough_geometry *g, const hough_binning *b);
