@@ -19,13 +19,15 @@
 //   2. Membership.  The group tests the flattened union of the ranges, a lane per hit.  A lane's
 //      range is found without a search: the ranges starting inside the warp's window of 32 hits
 //      are OR-reduced into one bit mask (a redux), and a population count below the lane gives its
-//      range.  Members are ranked by ballot in the fixed order (layer, bucket, position).
-//   3. Coefficients.  For each member, the z0 coordinate of its vote on cot row m,
+//      range.  Members are ranked by ballot in the fixed order (layer, bucket, position) and
+//      listed, each with its z, in the group's shared memory.
+//   3. Coefficients.  A lane per listed member (so this arithmetic runs once per 32 members, not
+//      once per 32 hits scanned): the z0 coordinate of its vote on cot row m,
 //      w(m) = n_z0 (z - s t_m - z0_min) / (z0_max - z0_min) = a - (m - m_ref) b, evaluated in FP32
 //      around the row m_ref where it crosses z0_min, from coefficients formed in two-float
 //      arithmetic (to within 2e-5 bin of its exact value), and the exact run of rows whose vote
 //      falls inside the z0 range (w is monotone in m, so they form one run).  Members with a
-//      non-empty run are compacted with the exclusive prefix of the run lengths.
+//      non-empty run are compacted in place with the exclusive prefix of the run lengths.
 //   4. Stage-2 vote.  The (member, row) pairs of all runs are spread over the lanes -- a pair's
 //      member found like a hit's range above -- and voted with a shared atomicOr into the group's
 //      own n_cot x n_z0 grid (16-bit masks, or in batches of a detector of at most 10 layers
@@ -36,11 +38,11 @@
 //      complement of the cell index), and a redux finds the group's.
 //   5. The cell's final mask is read back, the touched rows cleared, the candidate written.
 //
-// A candidate with more members than the group holds (kCap) is done in chunks of kCap members, the
-// membership pass repeated for each chunk, all chunks voting into the one grid.  The member lists
-// are kept for contexts (hough_get_members reads them), in the event's member pool; a batch keeps
-// none.  The event's member and stage-2 vote counters are summed per group and added once per
-// event a group visits.
+// A candidate with more members than the list holds (kBatchCap, kEventCap), or whose runs hold more
+// pairs than a chunk votes at a time, is done in chunks, the membership pass repeated for each,
+// all chunks voting into the one grid.  The member lists are kept for contexts (hough_get_members
+// reads them), in the event's member pool; a batch keeps none.  The event's member and stage-2
+// vote counters are summed per group and added once per event a group visits.
 #include <atomic>
 #include <climits>
 
@@ -302,8 +304,8 @@ __device__ __forceinline__ void table_coefficients(const Axes &ax, const float4 
     // A = Z - S
     float2 A = two_sum(zp.x, -zc.x);
     A.y = A.y + (zlo - zc.y);
-    int mref = 0;
-    if (zc.z > 0.f) mref = (int)fminf(fmaxf(rintf(A.x * rb), 0.f), (float)(ax.n_cot - 1));   // any nearby row will do
+    // any nearby row will do
+    const int mref = zc.z > 0.f ? (int)fminf(fmaxf(rintf(A.x * rb), 0.f), (float)(ax.n_cot - 1)) : 0;
     // a = A - m_ref B; m_ref B.hi is exact as a two-float product
     const float fm = (float)mref;
     const float2 q = two_prod(fm, zc.z);
@@ -355,36 +357,35 @@ __device__ __forceinline__ void member_run(const Axes &ax, float a, float b, flo
 {
     const int mref = mrl & 0xFFFF;
     const float top = (float)(ax.n_cot - 1);
-    int lo, hi;
-    if (!(b > 0.f)) {
+    const float flo = floorf((float)mref + (a - (float)ax.n_z0) * rb);   // rb: about 1 / b
+    const float fhi = floorf((float)mref + a * rb) + 1.f;
+    int lo = (int)fminf(fmaxf(flo, 0.f), top + 1.f);
+    int hi = (int)fminf(fmaxf(fhi, -1.f), top);
+    lo += (lo <= hi && stage2_cell(ax, a, b, mrl, lo) < 0) ? 1 : 0;
+    hi -= (hi >= lo && stage2_cell(ax, a, b, mrl, hi) < 0) ? 1 : 0;
+    if (!(b > 0.f)) {   // w constant in m: every row or none
         const bool in = a >= 0.f && a < (float)ax.n_z0;
         lo = 0;
         hi = in ? ax.n_cot - 1 : -1;
-    } else {
-        const float flo = floorf((float)mref + (a - (float)ax.n_z0) * rb);   // rb: about 1 / b
-        const float fhi = floorf((float)mref + a * rb) + 1.f;
-        lo = (int)fminf(fmaxf(flo, 0.f), top + 1.f);
-        hi = (int)fminf(fmaxf(fhi, -1.f), top);
-        lo += (lo <= hi && stage2_cell(ax, a, b, mrl, lo) < 0) ? 1 : 0;
-        hi -= (hi >= lo && stage2_cell(ax, a, b, mrl, hi) < 0) ? 1 : 0;
     }
     *lo_out = lo;
     *len_out = max(0, hi - lo + 1);
 }
 
-// One stage-2 vote: OR the member's layer bit into `cell` = m n_z0 + nz of `grid`; returns the key of the
-// cell as the OR left it: its popcount above the complement of the cell index, so that the larger
+// One stage-2 vote (when `in`): OR the member's layer bit into `cell` = m n_z0 + nz of `grid`; returns
+// the key of the cell as the OR left it (0 when not `in`): its popcount above the complement of the cell index, so that the larger
 // key is the larger popcount and, on a tie, the lower cell.  P10: the grid packs three 10-bit
 // masks a word (detectors of at most 10 layers), else two 16-bit ones.
 template <bool P10>
-__device__ __forceinline__ unsigned stage2_vote(uint32_t *grid, unsigned cell, int layer)
+__device__ __forceinline__ unsigned stage2_vote(uint32_t *grid, unsigned cell, int layer, bool in)
 {
     const unsigned word = P10 ? cell / 3u : cell >> 1;
     const unsigned shift = P10 ? (cell - word * 3u) * 10u : (cell & 1u) << 4;
     const uint32_t bit = 1u << layer;
-    const uint32_t old = atomicOr(&grid[word], bit << shift);
+    uint32_t old = 0u;
+    if (in) old = atomicOr(&grid[word], bit << shift);
     const uint32_t msk = ((old >> shift) & (P10 ? 0x3FFu : 0xFFFFu)) | bit;
-    return ((unsigned)__popc(msk) << 16) | (0xFFFFu - cell);
+    return in ? ((unsigned)__popc(msk) << 16) | (0xFFFFu - cell) : 0u;
 }
 
 template <bool P10>
@@ -405,43 +406,25 @@ __device__ __forceinline__ void clear_rows(const Axes &ax, uint32_t *grid, int r
     const int w0 = (P10 ? c0 / 3 : c0 >> 1) & ~3;
     const int w1 = ((P10 ? c1 / 3 : c1 >> 1) | 3) + 1;   // <= grid words (a multiple of 4)
     uint4 *g4 = reinterpret_cast<uint4 *>(grid);
+#pragma unroll 4
     for (int q = (w0 >> 2) + group_tid<WPC>(); q < (w1 >> 2); q += 32 * WPC) g4[q] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // A candidate record as two 16-byte vectors (the arrays are 16-byte aligned, 32 bytes an entry).
-__device__ __forceinline__ hough_candidate load_candidate(const hough_candidate *p)
-{
-    const uint4 a = reinterpret_cast<const uint4 *>(p)[0], b = reinterpret_cast<const uint4 *>(p)[1];
-    hough_candidate c;
-    c.iq = a.x; c.jphi = a.y; c.mask = a.z; c.n_members = a.w;
-    c.icot = b.x; c.jz0 = b.y; c.mask2 = b.z; c.flags = b.w;
-    return c;
-}
-
 __device__ __forceinline__ void store_candidate(hough_candidate *p, const hough_candidate &c)
 {
     reinterpret_cast<uint4 *>(p)[0] = make_uint4(c.iq, c.jphi, c.mask, c.n_members);
     reinterpret_cast<uint4 *>(p)[1] = make_uint4(c.icot, c.jz0, c.mask2, c.flags);
 }
 
-// Totals of one membership pass.
-struct PassOut {
-    int n;          // members of the candidate
-    int nrun;       // members whose run of cot rows is not empty
-    int npairs;     // (member, row) pairs of the chunk's members
-    int nkept;      // members in the chunk
-};
-
-// One pass over the candidate's ranges (steps 2 and 3), a lane per hit.  RUNS: every member's
-// stage-2 coefficients and run of cot rows are formed in the round that finds it; the members with
-// a run, ranked, go to the chunk from rank lo on while it holds at most CAP members and MAXP pairs
-// (par, and the bit of each one's first pair in starts, counted from the chunk's first pair);
-// rlo / rhi widen to the rows their runs cover.  Otherwise (member lists): member r's staged
-// position goes to pool[r] for r < pool_n.
-template <int WPC, int CAP, int MAXP, bool RUNS, bool GEN>
-__device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, MAXP> &S, const HotHit *hot,
-                               const float *fsort, const float *zsort, const ColdHit *cold, int i, int j, float s32,
-                               float refine_eps, int lo, int &rlo, int &rhi, int32_t *pool = nullptr, int pool_n = 0)
+// Step 2: one pass over the candidate's ranges, a lane per hit, software-pipelined (the next
+// round's hit is requested before this round is tested).  Members are ranked in the fixed order
+// (layer, bucket, position) and sink(r, p, kd, z) receives member r: its staged position, the kind
+// of its range and (Z) its z.  Returns the number of members.
+template <int WPC, int CAP, int MAXP, bool GEN, bool Z, typename Sink>
+__device__ int scan_members(const Axes &ax, const Workspace &w, Scratch<CAP, MAXP> &S, const HotHit *hot,
+                            const float *fsort, const float *zsort, const ColdHit *cold, int i, int j, float s32,
+                            float refine_eps, Sink &&sink)
 {
     const int lane = threadIdx.x & 31;
     const int T = S.total, nseg = S.n_seg;
@@ -461,14 +444,7 @@ __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, 
     };
     const int G = 32 * WPC;
     const int wb = 32 * group_warp<WPC>();
-    PassOut out{0, 0, 0, 0};
-    int pairs = 0;      // pairs of every member with a run so far
-    int before = 0;     // pairs of the members with a run ranked below lo
-    if (RUNS) {
-        for (int q = group_tid<WPC>(); q < MAXP / 32; q += 32 * WPC) S.starts[q] = 0u;
-        group_sync<WPC>();
-    }
-    // software-pipelined: the next round's hit is requested before this round is tested
+    int n = 0;
     int p = 0;
     unsigned kd = 0u;
     float gg = 0.f, f = 0.f, z = 0.f;
@@ -476,7 +452,7 @@ __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, 
         locate(wb, p, kd, gg);
         if (wb + lane < T && !(kd & 32u)) {
             f = __ldg(&fsort[p]);
-            if (RUNS) z = __ldg(&zsort[p]);
+            if (Z) z = __ldg(&zsort[p]);
         }
     }
     for (int b0 = 0; b0 < T; b0 += G) {
@@ -489,80 +465,90 @@ __device__ PassOut member_pass(const Axes &ax, const Workspace &w, Scratch<CAP, 
             locate(bn, pn, kdn, ggn);
             if (bn + lane < T && !(kdn & 32u)) {
                 fn = __ldg(&fsort[pn]);
-                if (RUNS) zn = __ldg(&zsort[pn]);
+                if (Z) zn = __ldg(&zsort[pn]);
             }
         }
-        bool mem = false;
-        if (v < T) {
-            if (!(kd & 32u)) mem = (f < gg) == ((kd & 16u) != 0u);   // side 1: f < g; side 0: f >= g
-            else if (GEN) mem = general_member(ax, w, hot, cold, p, i, j, s32, refine_eps);
-        }
-        if (RUNS) {
-            float a = 0.f, bb = 0.f;
-            int mrl = 0, mlo = 0, len = 0;
-            if (mem) {
-                const int l = (int)(kd & 15u);
-                float rb;
-                if (!(kd & 32u)) {
-                    rb = S.rb[l];
-                    table_coefficients(ax, S.zco[l], rb, z, l, &a, &bb, &mrl);
-                } else if (GEN) {
-                    exact_coefficients(ax, l, i, cold[p], &a, &bb, &mrl);
-                    rb = bb > 0.f ? __frcp_rn(bb) : 0.f;
-                } else {
-                    rb = 0.f;
-                }
-                member_run(ax, a, bb, rb, mrl, &mlo, &len);
-            }
-            const bool run = len > 0;
-            // ranks and prefixes within the warp, then over the group in one exchange
-            const unsigned bmem = __ballot_sync(0xFFFFFFFFu, mem), brun = __ballot_sync(0xFFFFFFFFu, run);
-            int linc = len;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(0xFFFFFFFFu, linc, d);
-                if (lane >= d) linc += t;
-            }
-            int pre1[3], tot1[3];
-            group_exchange<WPC, 3>({__popc(brun), __shfl_sync(0xFFFFFFFFu, linc, 31), __popc(bmem)}, pre1, tot1, S.wtmp);
-            const int r2 = out.nrun + pre1[0] + __popc(brun & lanes_below());
-            const int s2 = pairs + pre1[1] + linc - len;
-            if (lo > 0) before += (int)group_reduce_add<WPC>(run && r2 < lo ? (unsigned)len : 0u, S.wtmp);
-            const int st = s2 - before;   // every member ranked below lo precedes this one
-            // the kept ranks are contiguous: st + len and r2 grow together
-            const bool keep = run && r2 >= lo && r2 - lo < CAP && st + len <= MAXP;
-            const unsigned bkeep = __ballot_sync(0xFFFFFFFFu, keep);
-            int pre2[2], tot2[2];
-            group_exchange<WPC, 2>({__popc(bkeep), (int)__reduce_add_sync(0xFFFFFFFFu, keep ? (unsigned)len : 0u)},
-                                   pre2, tot2, S.wtmp);
-            const int slot = out.nkept + pre2[0] + __popc(bkeep & lanes_below());
-            const int nk = tot2[0], nr = tot1[0], np = tot1[1];
-            out.npairs += tot2[1];
-            if (keep) {
-                const int c0 = mlo - st;
-                S.par[slot] = make_int4(__float_as_int(a), __float_as_int(bb),
-                                        (c0 - (mrl & 0xFFFF) + kDmBias) | ((mrl >> 16) << 20), c0 * ax.n_z0);
-                atomicOr(&S.starts[st >> 5], 1u << (st & 31));
-                rlo = min(rlo, mlo);
-                rhi = max(rhi, mlo + len - 1);
-            }
-            out.nkept += nk;
-            out.nrun += nr;
-            pairs += np;
-            out.n += tot1[2];
-        } else {
-            int nm;
-            const int r = out.n + group_excl_count<WPC>(mem, &nm, S.wtmp);
-            if (mem && r < pool_n) pool[r] = p;
-            out.n += nm;
-        }
+        bool mem = v < T && (f < gg) == ((kd & 16u) != 0u);   // side 1: f < g; side 0: f >= g
+        if (GEN && v < T && (kd & 32u)) mem = general_member(ax, w, hot, cold, p, i, j, s32, refine_eps);
+        int nm;
+        const int r = n + group_excl_count<WPC>(mem, &nm, S.wtmp);
+        if (mem) sink(r, p, kd, z);
+        n += nm;
         p = pn;
         kd = kdn;
         gg = ggn;
         f = fn;
         z = zn;
     }
-    return out;
+    return n;
+}
+
+// Totals of a chunk's runs.
+struct ChunkOut {
+    int npairs;     // (member, row) pairs of the members kept
+    int consumed;   // members of the list the chunk has dealt with (kept, or without a run)
+};
+
+// Step 3 for the chunk's m members listed in par as {position, kind, z bits}: each one's stage-2
+// coefficients and run of cot rows, a lane per member.  The members with a run are kept, in order,
+// while their pairs fit MAXP: par is rewritten in place from slot 0 (a slot never lies past the
+// entry it comes from, and a round's entries are all read before any is written), and the bit of
+// each kept member's first pair is set in starts.  rlo / rhi widen to the rows the runs cover.
+template <int WPC, int CAP, int MAXP, bool GEN>
+__device__ ChunkOut chunk_runs(const Axes &ax, Scratch<CAP, MAXP> &S, const ColdHit *cold, int i, int m, int &rlo,
+                               int &rhi)
+{
+    const int tid = group_tid<WPC>();
+    const int G = 32 * WPC;
+    for (int q = tid; q < MAXP / 32; q += G) S.starts[q] = 0u;
+    int pairs = 0, kept = 0, consumed = 0;
+    for (int b0 = 0; b0 < m; b0 += G) {
+        const int idx = b0 + tid;
+        const bool valid = idx < m;
+        int4 e = make_int4(0, 0, 0, 0);
+        if (valid) e = S.par[idx];
+        group_sync<WPC>();   // the round's entries are read (and starts cleared) before any write
+        // every lane forms coefficients (a lane past the list from entry 0's zeros) and the run is
+        // dropped where not valid: no divergent branch on the table path
+        float a, bb;
+        int mrl, mlo, len;
+        const unsigned kd = (unsigned)e.y;
+        const int l = (int)(kd & 15u);
+        float rb = S.rb[l];
+        table_coefficients(ax, S.zco[l], rb, __int_as_float(e.z), l, &a, &bb, &mrl);
+        if (GEN && valid && (kd & 32u)) {
+            exact_coefficients(ax, l, i, cold[e.x], &a, &bb, &mrl);
+            rb = bb > 0.f ? __frcp_rn(bb) : 0.f;
+        }
+        member_run(ax, a, bb, rb, mrl, &mlo, &len);
+        if (!valid) len = 0;
+        // pair prefix over the round (members without a run add nothing); a member whose pairs end
+        // past MAXP, and every one after it (their prefixes only grow), waits for the next chunk
+        int tot_len;
+        const int st = pairs + group_excl_scan<WPC>(len, &tot_len, S.wtmp);
+        const bool after = valid && st + len > MAXP;
+        const bool keep = len > 0 && !after;
+        const unsigned bkeep = __ballot_sync(0xFFFFFFFFu, keep);
+        int pre[3], tot[3];
+        group_exchange<WPC, 3>({__popc(bkeep), (int)__reduce_add_sync(0xFFFFFFFFu, keep ? (unsigned)len : 0u),
+                                __popc(__ballot_sync(0xFFFFFFFFu, after))},
+                               pre, tot, S.wtmp);
+        if (WPC == 1) __syncwarp();
+        if (keep) {
+            const int slot = kept + pre[0] + __popc(bkeep & lanes_below());
+            const int c0 = mlo - st;
+            S.par[slot] = make_int4(__float_as_int(a), __float_as_int(bb),
+                                    (c0 - (mrl & 0xFFFF) + kDmBias) | ((mrl >> 16) << 20), c0 * ax.n_z0);
+            atomicOr(&S.starts[st >> 5], 1u << (st & 31));
+            rlo = min(rlo, mlo);
+            rhi = max(rhi, mlo + len - 1);
+        }
+        kept += tot[0];
+        pairs += tot[1];
+        consumed += min(G, m - b0) - tot[2];
+        if (tot[2] > 0) break;
+    }
+    return {pairs, consumed};
 }
 
 // Stage-2 vote of the chunk's pairs (step 4); best keeps the lane's largest key and votes its
@@ -589,16 +575,15 @@ __device__ void vote_pairs(const Axes &ax, const Scratch<CAP, MAXP> &S, uint32_t
             for (int k = 0; k < WPC; ++k)
                 if ((bw >> 5) + k < MAXP / 32) before += __popc(S.starts[(bw >> 5) + k]);
         }
+        // owner is a kept member for every lane, past npairs too (pair 0 starts a run)
         const int v = bw + lane;
-        if (v < npairs) {
-            const int4 pr = S.par[owner];
-            // w(m) = a - (m - m_ref) b at the pair's row m, as stage2_cell evaluates it
-            const float wv = fmaf(-(float)(v + (pr.z & 0xFFFFF) - kDmBias), __int_as_float(pr.y), __int_as_float(pr.x));
-            if (wv >= 0.f && wv < nz0) {
-                best = max(best, stage2_vote<P10>(grid, (unsigned)(v * ax.n_z0 + pr.w + (int)wv), pr.z >> 20));
-                ++votes;
-            }
-        }
+        const int4 pr = S.par[owner];
+        // w(m) = a - (m - m_ref) b at the pair's row m, as stage2_cell evaluates it
+        const float wv = fmaf(-(float)(v + (pr.z & 0xFFFFF) - kDmBias), __int_as_float(pr.y), __int_as_float(pr.x));
+        const bool in = v < npairs && wv >= 0.f && wv < nz0;
+        const unsigned key = stage2_vote<P10>(grid, (unsigned)(v * ax.n_z0 + pr.w + (int)wv), pr.z >> 20, in);
+        best = max(best, key);
+        votes += in ? 1u : 0u;
     }
 }
 
@@ -649,10 +634,12 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
     int acc_e = -1;
     unsigned acc_members = 0u;
     unsigned long long acc_votes = 0ull;
-    // candidate f goes to CTA f mod gridDim, so that a few candidates spread over all SMs
-    int e = 0, e_base = 0, e_next = w.n_events == 1 ? INT_MAX : -1;   // the event of the last candidate
-    for (int f = gidx * gridDim.x + blockIdx.x; f < total; f += gridDim.x * ngroups) {
-        // a group's candidates come in increasing flattened order, so its event only moves forward
+    // candidate f goes to CTA f mod gridDim, so that a few candidates spread over all SMs; a group's
+    // candidates come in increasing flattened order, so its event only moves forward
+    int e = 0, e_base = 0, e_next = w.n_events == 1 ? INT_MAX : -1;   // the event of the last candidate fetched
+    // (i, j, mask) of candidate f, whose event becomes e; the next candidate's is requested while
+    // this one is confirmed, taking its loads off the candidate's chain
+    auto fetch = [&](int f) {
         if (e_next < 0) {
             e = upper_index(w.cand_base, w.n_events, f);
             e_base = w.cand_base[e];
@@ -664,14 +651,6 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
             e_next = w.cand_base[e + 1];
         }
         const int c = f - e_base;
-        const int64_t hstart = w.hit_start[e];
-        const HotHit *hot = w.hot + hstart;
-        const float *fsort = w.fsort + hstart;
-        const float *zsort = w.zsort + hstart;
-        const ColdHit *cold = w.cold + hstart;
-        const int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
-        hough_candidate *cands = w.cands + (int64_t)e * w.max_cand;
-        hough_candidate cd;
         if (WPC > 1 && band_offs) {
             // one event whose candidate list was not compacted: candidate c from its band's list
             int b = 0, hi = n_bands(ax, w.band_rows) - 1;   // the last band with offset <= c (shared memory)
@@ -680,13 +659,29 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
                 if (band_offs[mid] <= c) b = mid; else hi = mid - 1;
             }
             const uint2 v = w.band_cands[(int64_t)b * w.band_cap + (c - band_offs[b])];
-            cd.iq = v.x / (unsigned)nphi;
-            cd.jphi = v.x % (unsigned)nphi;
-            cd.mask = v.y;
-            cd.n_members = cd.icot = cd.jz0 = cd.mask2 = cd.flags = 0u;
-        } else {
-            cd = load_candidate(cands + c);
+            return make_uint3(v.x / (unsigned)nphi, v.x % (unsigned)nphi, v.y);
         }
+        const uint4 v = *reinterpret_cast<const uint4 *>(w.cands + (int64_t)e * w.max_cand + c);
+        return make_uint3(v.x, v.y, v.z);
+    };
+    const int stride = gridDim.x * ngroups;
+    int f = gidx * gridDim.x + blockIdx.x;
+    uint3 rec = f < total ? fetch(f) : make_uint3(0u, 0u, 0u);
+    for (; f < total; f += stride) {
+        const int ev = e, c = f - e_base;
+        hough_candidate cd;
+        cd.iq = rec.x;
+        cd.jphi = rec.y;
+        cd.mask = rec.z;
+        cd.n_members = cd.icot = cd.jz0 = cd.mask2 = cd.flags = 0u;
+        if (f + stride < total) rec = fetch(f + stride);
+        const int64_t hstart = w.hit_start[ev];
+        const HotHit *hot = w.hot + hstart;
+        const float *fsort = w.fsort + hstart;
+        const float *zsort = w.zsort + hstart;
+        const ColdHit *cold = w.cold + hstart;
+        const int32_t *offs = w.offs + (int64_t)ev * (nkeys + 1);
+        hough_candidate *cands = w.cands + (int64_t)ev * w.max_cand;
         const int i = (int)cd.iq, j = (int)cd.jphi;
         // step 1: the candidate's ranges, lane t of the first warp taking range t = (layer t/2, side t%2)
         if (wg == 0) {
@@ -743,28 +738,32 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
             }
         }
         group_sync<WPC>();
-        // steps 2-4, chunk by chunk: the first pass counts the members and fills the first chunk
+        // steps 2-4, chunk by chunk: a membership pass lists the members of ranks [lo, lo + CAP)
+        // (the first also counts them all), their runs are formed, and the kept members vote
         unsigned best = 0u, votes = 0u;
         int rlo = INT_MAX, rhi = -1;
-        const PassOut first =
-            member_pass<WPC, CAP, MAXP, true, GEN>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, 0, rlo, rhi);
-        const int n = first.n;
-        for (int lo = 0, kept = 0; lo < first.nrun; lo += kept) {
-            PassOut po = first;
+        int lo = 0;
+        auto to_chunk = [&](int r, int p, unsigned kd, float z) {
+            if (r >= lo && r < lo + CAP) S.par[r - lo] = make_int4(p, (int)kd, __float_as_int(z), 0);
+        };
+        const int n = scan_members<WPC, CAP, MAXP, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
+                                                             to_chunk);
+        while (lo < n) {
             if (lo > 0) {
                 group_sync<WPC>();   // the previous chunk's votes have read its members
-                po = member_pass<WPC, CAP, MAXP, true, GEN>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, lo, rlo,
-                                                 rhi);
+                scan_members<WPC, CAP, MAXP, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, to_chunk);
             }
-            kept = po.nkept;
-            group_sync<WPC>();
-            vote_pairs<WPC, CAP, MAXP, P10>(ax, S, grid, po.npairs, best, votes);
+            group_sync<WPC>();   // the chunk's list is complete
+            const ChunkOut co = chunk_runs<WPC, CAP, MAXP, GEN>(ax, S, cold, i, min(n - lo, CAP), rlo, rhi);
+            group_sync<WPC>();   // its runs and start bits are complete
+            vote_pairs<WPC, CAP, MAXP, P10>(ax, S, grid, co.npairs, best, votes);
+            lo += co.consumed;
         }
         int written = n;
         if (keep) {
             // the event's member pool is shared by all its candidates: reserve, then list the members
             if (tid == 0) {
-                const unsigned reserved = n ? atomicAdd(&w.stats[e].pool_used, (unsigned)n) : 0u;
+                const unsigned reserved = n ? atomicAdd(&w.stats[ev].pool_used, (unsigned)n) : 0u;
                 const long long room = (long long)w.max_members - (long long)reserved;
                 S.pool_base = (int)min((long long)reserved, (long long)w.max_members);
                 S.pool_written = n ? (int)max(0LL, min((long long)n, room)) : 0;
@@ -774,12 +773,16 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
             written = S.pool_written;
             group_sync<WPC>();
             if (tid == 0) {
-                w.mem_start[(int64_t)e * w.max_cand + c] = base;
-                w.mem_count[(int64_t)e * w.max_cand + c] = written;
+                w.mem_start[(int64_t)ev * w.max_cand + c] = base;
+                w.mem_count[(int64_t)ev * w.max_cand + c] = written;
             }
-            if (written > 0)
-                member_pass<WPC, CAP, MAXP, false, GEN>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, 0, rlo, rhi,
-                                             w.mem_pool + (int64_t)e * w.max_members + base, written);
+            if (written > 0) {
+                int32_t *pool = w.mem_pool + (int64_t)ev * w.max_members + base;
+                scan_members<WPC, CAP, MAXP, GEN, false>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
+                                                         [&](int r, int p, unsigned, float) {
+                                                             if (r < written) pool[r] = p;
+                                                         });
+            }
         }
         // step 5: the group's best key and votes, the final mask of its cell, the touched rows cleared
         best = __reduce_max_sync(0xFFFFFFFFu, best);
@@ -816,12 +819,12 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
             out.mask2 = mask2;
             out.flags = ((int)(best >> 16) >= min(ax.threshold, ax.n_layers) ? 1u : 0u) | (written < n ? 2u : 0u);
             store_candidate(cands + c, out);
-            if (e != acc_e) {
+            if (ev != acc_e) {
                 if (acc_e >= 0) {
                     if (acc_members) atomicAdd(&w.stats[acc_e].n_members, acc_members);
                     if (acc_votes) atomicAdd(&w.stats[acc_e].stage2_votes, acc_votes);
                 }
-                acc_e = e;
+                acc_e = ev;
                 acc_members = 0u;
                 acc_votes = 0ull;
             }
@@ -851,6 +854,9 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
     uint32_t *grid = reinterpret_cast<uint32_t *>(smem_c + (size_t)ngroups * scratch_bytes) + (size_t)gidx * grid_words;
     if (threadIdx.x < HOUGH_MAX_LAYERS) s_info[threadIdx.x] = w.info[threadIdx.x];
     for (int q = group_tid<WPC>(); q < grid_words; q += 32 * WPC) grid[q] = 0u;
+    // the scratch starts zeroed: lanes past a list read its terms without a branch
+    for (int q = group_tid<WPC>(); q < (int)(sizeof(Scratch<CAP, MAXP>) / 4); q += 32 * WPC)
+        reinterpret_cast<uint32_t *>(&S)[q] = 0u;
     __syncthreads();
     if (threadIdx.x == 0) {
         int g = 0;
