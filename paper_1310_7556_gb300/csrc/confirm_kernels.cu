@@ -52,8 +52,7 @@ namespace hough {
 
 namespace {
 
-constexpr int kMaxGroupWarps = 8;
-constexpr int kBatchCap = 64;      // members a warp holds at a time (batches)
+constexpr int kBatchCap = 40;      // members a warp holds at a time (batches)
 constexpr int kBatchPairs = 1024;  // (member, row) pairs a warp votes at a time (batches)
 constexpr int kEventCap = 256;     // members a four-warp group holds at a time (single events)
 constexpr int kEventPairs = 4096;  // pairs it votes at a time
@@ -61,20 +60,20 @@ constexpr int kEventWarps = 4;     // warps per candidate for a single event
 constexpr int kBatchGroups = 4;    // one-warp groups per CTA at most (batches)
 constexpr int kMaxBandsRead = 8192;   // band offsets a single event's CTA may hold to read the band lists
 
-// Per-group scratch.  Kind of a range: bits 0..3 the layer, bit 4 the side (1: f < g), bit 5 a
+// Per-group scratch of a group of WPC warps, for detectors of at most NL layers.  Kind of a range: bits 0..3 the layer, bit 4 the side (1: f < g), bit 5 a
 // layer whose hits lie at several radii (each hit's vote recomputed).
-template <int CAP, int MAXP>
+template <int WPC, int CAP, int MAXP, int NL>
 struct __align__(16) Scratch {
     // chunk member with a run of cot rows: a, b (float bits); (first row - first pair - m_ref) +
     // kDmBias in bits 0..19 and the layer in bits 20..23; (first row - first pair) * n_z0
     int4 par[CAP];
-    float4 zco[HOUGH_MAX_LAYERS];   // stage-2 terms {S hi, S lo, B hi, B lo} of each table layer at this row
-    float rb[HOUGH_MAX_LAYERS];     // 1 / B hi of each table layer at this row (approximate)
+    float4 zco[NL];                 // stage-2 terms {S hi, S lo, B hi, B lo} of each table layer at this row
+    float rb[NL];                   // 1 / B hi of each table layer at this row (approximate)
     unsigned starts[MAXP / 32];     // bit v: a chunk member's run starts at pair v
-    int seg_pre[32], seg_start[32];
-    unsigned seg_kind[32];
-    float seg_g[32];
-    int wtmp[4 * kMaxGroupWarps];
+    int seg_pre[2 * NL], seg_start[2 * NL];   // the ranges, two a layer at most
+    unsigned seg_kind[2 * NL];
+    float seg_g[2 * NL];
+    int wtmp[4 * WPC];
     int n_seg, total, pool_base, pool_written;
 };
 
@@ -421,8 +420,8 @@ __device__ __forceinline__ void store_candidate(hough_candidate *p, const hough_
 // round's hit is requested before this round is tested).  Members are ranked in the fixed order
 // (layer, bucket, position) and sink(r, p, kd, z) receives member r: its staged position, the kind
 // of its range and (Z) its z.  Returns the number of members.
-template <int WPC, int CAP, int MAXP, bool GEN, bool Z, typename Sink>
-__device__ int scan_members(const Axes &ax, const Workspace &w, Scratch<CAP, MAXP> &S, const HotHit *hot,
+template <int WPC, int CAP, int MAXP, int NL, bool GEN, bool Z, typename Sink>
+__device__ int scan_members(const Axes &ax, const Workspace &w, Scratch<WPC, CAP, MAXP, NL> &S, const HotHit *hot,
                             const float *fsort, const float *zsort, const ColdHit *cold, int i, int j, float s32,
                             float refine_eps, Sink &&sink)
 {
@@ -494,8 +493,8 @@ struct ChunkOut {
 // while their pairs fit MAXP: par is rewritten in place from slot 0 (a slot never lies past the
 // entry it comes from, and a round's entries are all read before any is written), and the bit of
 // each kept member's first pair is set in starts.  rlo / rhi widen to the rows the runs cover.
-template <int WPC, int CAP, int MAXP, bool GEN>
-__device__ ChunkOut chunk_runs(const Axes &ax, Scratch<CAP, MAXP> &S, const ColdHit *cold, int i, int m, int &rlo,
+template <int WPC, int CAP, int MAXP, int NL, bool GEN>
+__device__ ChunkOut chunk_runs(const Axes &ax, Scratch<WPC, CAP, MAXP, NL> &S, const ColdHit *cold, int i, int m, int &rlo,
                                int &rhi)
 {
     const int tid = group_tid<WPC>();
@@ -555,35 +554,45 @@ __device__ ChunkOut chunk_runs(const Axes &ax, Scratch<CAP, MAXP> &S, const Cold
 // count of votes cast.  Each warp takes windows of 32 consecutive pairs, one word of the start bits:
 // the member owning pair bw + lane is the number of runs starting at or before it, less one -- the
 // runs starting before the window (counted as the windows go by) plus a population count of the
-// window's bits up to the lane.
-template <int WPC, int CAP, int MAXP, bool P10>
-__device__ void vote_pairs(const Axes &ax, const Scratch<CAP, MAXP> &S, uint32_t *grid, int npairs, unsigned &best,
-                           unsigned &votes)
+// window's bits up to the lane.  A lane's owner is a kept member past npairs too (pair 0 starts a
+// run), so every lane reads a valid entry and only the atomic is predicated.
+template <int WPC, int CAP, int MAXP, int NL, bool P10>
+__device__ void vote_pairs(const Axes &ax, const Scratch<WPC, CAP, MAXP, NL> &S, uint32_t *grid, int npairs,
+                           unsigned &best, unsigned &votes)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned upto = (2u << lane) - 1u;
     const float nz0 = (float)ax.n_z0;
     const int wg = group_warp<WPC>();
-    int before = 0;   // runs starting in the windows before this warp's current one
-    for (int k = 0; k < wg; ++k) before += __popc(S.starts[k]);
-    for (int bw = 32 * wg; bw < npairs; bw += 32 * WPC) {
-        const unsigned bits = S.starts[bw >> 5];
-        const int owner = before + __popc(bits & ((2u << lane) - 1u)) - 1;
-        if (WPC == 1) {
-            before += __popc(bits);
-        } else {
-#pragma unroll
-            for (int k = 0; k < WPC; ++k)
-                if ((bw >> 5) + k < MAXP / 32) before += __popc(S.starts[(bw >> 5) + k]);
-        }
-        // owner is a kept member for every lane, past npairs too (pair 0 starts a run)
-        const int v = bw + lane;
+    auto vote = [&](int v, int owner) {
         const int4 pr = S.par[owner];
         // w(m) = a - (m - m_ref) b at the pair's row m, as stage2_cell evaluates it
         const float wv = fmaf(-(float)(v + (pr.z & 0xFFFFF) - kDmBias), __int_as_float(pr.y), __int_as_float(pr.x));
         const bool in = v < npairs && wv >= 0.f && wv < nz0;
-        const unsigned key = stage2_vote<P10>(grid, (unsigned)(v * ax.n_z0 + pr.w + (int)wv), pr.z >> 20, in);
-        best = max(best, key);
+        best = max(best, stage2_vote<P10>(grid, (unsigned)(v * ax.n_z0 + pr.w + (int)wv), pr.z >> 20, in));
         votes += in ? 1u : 0u;
+    };
+    int before = 0;   // runs starting in the windows before this warp's current one
+    if constexpr (WPC == 1) {
+        // two windows an iteration: two independent chains for the scheduler to interleave
+        for (int bw = 0; bw < npairs; bw += 64) {
+            const int q = bw >> 5;
+            const unsigned b0 = S.starts[q], b1 = q + 1 < MAXP / 32 ? S.starts[q + 1] : 0u;
+            const int n0 = __popc(b0);
+            vote(bw + lane, before + __popc(b0 & upto) - 1);
+            vote(bw + 32 + lane, before + n0 + __popc(b1 & upto) - 1);
+            before += n0 + __popc(b1);
+        }
+    } else {
+        for (int k = 0; k < wg; ++k) before += __popc(S.starts[k]);
+        for (int bw = 32 * wg; bw < npairs; bw += 32 * WPC) {
+            const unsigned bits = S.starts[bw >> 5];
+            const int owner = before + __popc(bits & upto) - 1;
+#pragma unroll
+            for (int k = 0; k < WPC; ++k)
+                if ((bw >> 5) + k < MAXP / 32) before += __popc(S.starts[(bw >> 5) + k]);
+            vote(bw + lane, owner);
+        }
     }
 }
 
@@ -622,9 +631,9 @@ __device__ int block_excl_scan(const int32_t *counts, int n, int *out)
 // Membership and stage 2 of every candidate a group takes.  GEN: some layer's hits lie at several
 // radii (their votes are redone per hit, partly in FP64); without it that code is left out, which
 // spares the common path its registers.
-template <int WPC, int CAP, int MAXP, bool P10, bool GEN>
+template <int WPC, int CAP, int MAXP, int NL, bool P10, bool GEN>
 __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, float s32, float refine_eps,
-                                            Scratch<CAP, MAXP> &S, uint32_t *grid, const LayerInfo *s_info,
+                                            Scratch<WPC, CAP, MAXP, NL> &S, uint32_t *grid, const LayerInfo *s_info,
                                             int ngroups, int gidx, int total, const int *band_offs)
 {
     const int tid = group_tid<WPC>(), lane = threadIdx.x & 31, wg = group_warp<WPC>();
@@ -746,17 +755,17 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
         auto to_chunk = [&](int r, int p, unsigned kd, float z) {
             if (r >= lo && r < lo + CAP) S.par[r - lo] = make_int4(p, (int)kd, __float_as_int(z), 0);
         };
-        const int n = scan_members<WPC, CAP, MAXP, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
+        const int n = scan_members<WPC, CAP, MAXP, NL, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
                                                              to_chunk);
         while (lo < n) {
             if (lo > 0) {
                 group_sync<WPC>();   // the previous chunk's votes have read its members
-                scan_members<WPC, CAP, MAXP, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, to_chunk);
+                scan_members<WPC, CAP, MAXP, NL, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, to_chunk);
             }
             group_sync<WPC>();   // the chunk's list is complete
-            const ChunkOut co = chunk_runs<WPC, CAP, MAXP, GEN>(ax, S, cold, i, min(n - lo, CAP), rlo, rhi);
+            const ChunkOut co = chunk_runs<WPC, CAP, MAXP, NL, GEN>(ax, S, cold, i, min(n - lo, CAP), rlo, rhi);
             group_sync<WPC>();   // its runs and start bits are complete
-            vote_pairs<WPC, CAP, MAXP, P10>(ax, S, grid, co.npairs, best, votes);
+            vote_pairs<WPC, CAP, MAXP, NL, P10>(ax, S, grid, co.npairs, best, votes);
             lo += co.consumed;
         }
         int written = n;
@@ -778,7 +787,7 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
             }
             if (written > 0) {
                 int32_t *pool = w.mem_pool + (int64_t)ev * w.max_members + base;
-                scan_members<WPC, CAP, MAXP, GEN, false>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
+                scan_members<WPC, CAP, MAXP, NL, GEN, false>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
                                                          [&](int r, int p, unsigned, float) {
                                                              if (r < written) pool[r] = p;
                                                          });
@@ -840,8 +849,8 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
 }
 
 // Membership and stage 2 of every candidate of every event, a group of WPC warps per candidate.
-template <int WPC, int CAP, int MAXP, bool P10>
-__global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC == 1 ? 7 : 1)
+template <int WPC, int CAP, int MAXP, int NL, bool P10>
+__global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC == 1 ? (P10 ? 8 : 5) : 1)
     confirm_kernel(Axes ax, Workspace w, float s32, float refine_eps, int grid_words, int scratch_bytes)
 {
     pdl_enter();
@@ -850,12 +859,12 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
     __shared__ int s_general;
     const int ngroups = WPC == 1 ? (int)(blockDim.x >> 5) : 1;
     const int gidx = WPC == 1 ? (int)(threadIdx.x >> 5) : 0;
-    Scratch<CAP, MAXP> &S = *reinterpret_cast<Scratch<CAP, MAXP> *>(smem_c + (size_t)gidx * scratch_bytes);
+    Scratch<WPC, CAP, MAXP, NL> &S = *reinterpret_cast<Scratch<WPC, CAP, MAXP, NL> *>(smem_c + (size_t)gidx * scratch_bytes);
     uint32_t *grid = reinterpret_cast<uint32_t *>(smem_c + (size_t)ngroups * scratch_bytes) + (size_t)gidx * grid_words;
     if (threadIdx.x < HOUGH_MAX_LAYERS) s_info[threadIdx.x] = w.info[threadIdx.x];
     for (int q = group_tid<WPC>(); q < grid_words; q += 32 * WPC) grid[q] = 0u;
     // the scratch starts zeroed: lanes past a list read its terms without a branch
-    for (int q = group_tid<WPC>(); q < (int)(sizeof(Scratch<CAP, MAXP>) / 4); q += 32 * WPC)
+    for (int q = group_tid<WPC>(); q < (int)(sizeof(Scratch<WPC, CAP, MAXP, NL>) / 4); q += 32 * WPC)
         reinterpret_cast<uint32_t *>(&S)[q] = 0u;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -886,9 +895,9 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
         total = (int)w.counters->total_cands;
     }
     if (s_general)
-        confirm_all<WPC, CAP, MAXP, P10, true>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
+        confirm_all<WPC, CAP, MAXP, NL, P10, true>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
     else
-        confirm_all<WPC, CAP, MAXP, P10, false>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
+        confirm_all<WPC, CAP, MAXP, NL, P10, false>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
 }
 
 __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total)
@@ -936,13 +945,13 @@ int smem_optin()
     return m;
 }
 
-template <int WPC, int CAP, int MAXP, bool P10>
+template <int WPC, int CAP, int MAXP, int NL, bool P10>
 cudaError_t launch_confirm(const Axes &ax, const Workspace &w, int sms, float s32, float refine_eps,
                            cudaStream_t stream, std::atomic<unsigned long long> &memo)
 {
-    auto kernel = confirm_kernel<WPC, CAP, MAXP, P10>;
+    auto kernel = confirm_kernel<WPC, CAP, MAXP, NL, P10>;
     const int words = grid_words_for(ax, P10);
-    const size_t scratch = (sizeof(Scratch<CAP, MAXP>) + 15) & ~(size_t)15;
+    const size_t scratch = (sizeof(Scratch<WPC, CAP, MAXP, NL>) + 15) & ~(size_t)15;
     const size_t per_group = scratch + (size_t)words * 4;
     // one-warp groups: as many per CTA (up to kBatchGroups) as shared memory holds
     const int room = smem_optin() - (int)(sizeof(LayerInfo) * HOUGH_MAX_LAYERS) - 1024;
@@ -974,12 +983,12 @@ cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float ref
     cudaError_t err;
     if (w.n_events == 1) {
         // one event: a few hundred candidates, each a chain of dependent steps, so four warps share one
-        err = launch_confirm<kEventWarps, kEventCap, kEventPairs, false>(ax, w, sms, s32, refine_eps, stream, g_ctas[0]);
+        err = launch_confirm<kEventWarps, kEventCap, kEventPairs, HOUGH_MAX_LAYERS, false>(ax, w, sms, s32, refine_eps, stream, g_ctas[0]);
     } else if (ax.n_layers <= 10) {
         // a batch: a warp per candidate, the grid's masks packed three to a word so more warps fit an SM
-        err = launch_confirm<1, kBatchCap, kBatchPairs, true>(ax, w, sms, s32, refine_eps, stream, g_ctas[1]);
+        err = launch_confirm<1, kBatchCap, kBatchPairs, 10, true>(ax, w, sms, s32, refine_eps, stream, g_ctas[1]);
     } else {
-        err = launch_confirm<1, kBatchCap, kBatchPairs, false>(ax, w, sms, s32, refine_eps, stream, g_ctas[2]);
+        err = launch_confirm<1, kBatchCap, kBatchPairs, HOUGH_MAX_LAYERS, false>(ax, w, sms, s32, refine_eps, stream, g_ctas[2]);
     }
     if (err) return err;
     if (between && (err = cudaEventRecord(between, stream))) return err;
