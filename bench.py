@@ -59,6 +59,9 @@ WORKLOAD_TEXT = {
     "paper_2048": "the paper's detector (10 layers evenly spaced to 110 cm, 0.4 mm, transverse plane), "
                   "5000 helices pT 1-100 GeV, no noise; 2048 q/pT x 2048 phi0, threshold >=8",
 }
+# the pileup event on modules within +-0.5 cm of their layer's radius: every vote per hit
+WORKLOAD_TEXT["pileup_100k_jittered"] = WORKLOAD_TEXT["pileup_100k"].replace(
+    "+ 50000 uniform noise hits", "+ 50000 uniform noise hits, every hit at its layer radius + U(-0.5, 0.5) cm")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -321,7 +324,7 @@ PLAIN_KERNELS = [
     ("clear_kernel", "clear_ms", "stage_kernels.cu"),
     ("stage_count_kernel", "count_ms", "stage_kernels.cu"),
     ("table_scan_kernel", "table_ms", "stage_kernels.cu"),
-    ("scatter_kernel (hit sort)", "sort_ms", "stage_kernels.cu"),
+    ("hit_sort_kernel", "sort_ms", "stage_kernels.cu"),
     ("gather_kernel", "gather_ms", "vote_kernel.cu"),
     ("scatter_kernel (vote of per-vote layers)", "scatter_ms", "vote_kernel.cu"),
     ("peaks_kernel", "band_peaks_ms", "vote_kernel.cu"),
@@ -351,14 +354,14 @@ def kernel_work(name, w, n_hits, st):
         "clear_kernel": (4 * nkeys + 8 * 16 * (b.n_phi + 16) * st["events"] + 304, None),
         "stage_count_kernel": (37 * n_hits, None),            # r, phi, z, layer in; key, rank, 16-B record out
         "table_scan_kernel": (8 * nkeys + 32 * 16, None),     # bucket counts in, offsets out; layer records
-        "scatter_kernel (hit sort)": (72 * n_hits, None),     # key, rank, record, r, phi, z, offset in; 2 x 16 B + f + z out
+        "hit_sort_kernel": (72 * n_hits, None),     # key, rank, record, r, phi, z, offset in; 2 x 16 B + f + z out
         "gather_kernel": (13 * n_hits + 2 * cells, st["votes"] - st["general_votes"]),
         "scatter_kernel (vote of per-vote layers)": (13 * n_hits * general, st["general_votes"]),
         "peaks_kernel": (2 * cells + 8 * cands, None),
         "compact_kernel": (40 * cands, None),
         "confirm_kernel": (64 * cands + 28 * L * cands + 8 * st["members"], st["stage2_votes"]),
     }
-    staging = ("clear_kernel", "stage_count_kernel", "table_scan_kernel", "scatter_kernel (hit sort)")
+    staging = ("clear_kernel", "stage_count_kernel", "table_scan_kernel", "hit_sort_kernel")
     model["staging (clear, count, table and scan, hit sort)"] = (sum(model[k][0] for k in staging), None)
     model["compact_kernel + cand_scan_kernel"] = (model["compact_kernel"][0] + 8 * st["events"], None)
     return model[name]
@@ -854,9 +857,7 @@ def measure_per_vote_path(env, args, smem_peak, hbm_peak):
     layer's hits share one radius, so every stage-1 vote is evaluated per hit in the shared-atomic
     scatter kernel (FP32 arcsine, FP64 near a bin edge) -- the path the gather cannot take."""
     w = eg.WORKLOADS["pileup_100k_jittered"]
-    text = WORKLOAD_TEXT["pileup_100k"].replace("+ 50000 uniform noise hits",
-                                                "+ 50000 uniform noise hits, every hit at its layer radius + U(-0.5, 0.5) cm")
-    p = _plain_variant(env, args, w, text, smem_peak, hbm_peak)
+    p = _plain_variant(env, args, w, WORKLOAD_TEXT["pileup_100k_jittered"], smem_peak, hbm_peak)
     p["note"] = "all votes cast by scatter_kernel (vote of per-vote layers); vote_vs_smem_atomic_peak is its rate"
     return p
 

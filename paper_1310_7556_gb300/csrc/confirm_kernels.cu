@@ -684,7 +684,7 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
         cd.mask = rec.z;
         cd.n_members = cd.icot = cd.jz0 = cd.mask2 = cd.flags = 0u;
         if (f + stride < total) rec = fetch(f + stride);
-        const int64_t hstart = w.hit_start[ev];
+        const int64_t hstart = ev == 0 ? 0 : w.hit_start[ev];   // hit_start[0] is 0
         const HotHit *hot = w.hot + hstart;
         const float *fsort = w.fsort + hstart;
         const float *zsort = w.zsort + hstart;
@@ -861,18 +861,10 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
     const int gidx = WPC == 1 ? (int)(threadIdx.x >> 5) : 0;
     Scratch<WPC, CAP, MAXP, NL> &S = *reinterpret_cast<Scratch<WPC, CAP, MAXP, NL> *>(smem_c + (size_t)gidx * scratch_bytes);
     uint32_t *grid = reinterpret_cast<uint32_t *>(smem_c + (size_t)ngroups * scratch_bytes) + (size_t)gidx * grid_words;
-    if (threadIdx.x < HOUGH_MAX_LAYERS) s_info[threadIdx.x] = w.info[threadIdx.x];
-    for (int q = group_tid<WPC>(); q < grid_words; q += 32 * WPC) grid[q] = 0u;
-    // the scratch starts zeroed: lanes past a list read its terms without a branch
-    for (int q = group_tid<WPC>(); q < (int)(sizeof(Scratch<WPC, CAP, MAXP, NL>) / 4); q += 32 * WPC)
-        reinterpret_cast<uint32_t *>(&S)[q] = 0u;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int g = 0;
-        for (int l = 0; l < ax.n_layers; ++l) g |= s_info[l].present && !s_info[l].uniform;
-        s_general = g;
-    }
-    __syncthreads();
+    // the layer records are requested first and stored last, so that their round trip overlaps the
+    // band counts' (or the candidate total's)
+    LayerInfo li{};
+    if (threadIdx.x < HOUGH_MAX_LAYERS) li = w.info[threadIdx.x];
     // one event of a context whose candidate list was not compacted: every CTA scans the band counts
     // into shared memory (behind the groups' scratch and grids) and reads its candidates from the
     // band lists; the first CTA records the totals the compaction would have
@@ -894,6 +886,18 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
     } else {
         total = (int)w.counters->total_cands;
     }
+    for (int q = group_tid<WPC>(); q < grid_words; q += 32 * WPC) grid[q] = 0u;
+    // the scratch starts zeroed: lanes past a list read its terms without a branch
+    for (int q = group_tid<WPC>(); q < (int)(sizeof(Scratch<WPC, CAP, MAXP, NL>) / 4); q += 32 * WPC)
+        reinterpret_cast<uint32_t *>(&S)[q] = 0u;
+    if (threadIdx.x < HOUGH_MAX_LAYERS) s_info[threadIdx.x] = li;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int g = 0;
+        for (int l = 0; l < ax.n_layers; ++l) g |= s_info[l].present && !s_info[l].uniform;
+        s_general = g;
+    }
+    __syncthreads();
     if (s_general)
         confirm_all<WPC, CAP, MAXP, NL, P10, true>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
     else

@@ -243,7 +243,10 @@ __host__ __device__ inline size_t band_smem_bytes(const Axes &ax, int band_rows)
 {
     // with a d0 axis the band's rows and their halo in three slices
     const size_t rows = (size_t)(band_rows + 2) * (ax.n_d0 ? 3 : 1);
-    return rows * ax.n_phi * (ax.counts ? 2 : 1);
+    // layer masks: the layer counts as bytes, then the band's own rows' masks (the candidates' masks,
+    // read from there instead of from device memory)
+    const size_t masks = (!ax.n_d0 && !ax.counts) ? (size_t)band_rows * ax.n_phi * 2 : 0;
+    return rows * ax.n_phi * (ax.counts ? 2 : 1) + masks;
 }
 size_t stage2_smem_bytes(const Axes &ax);
 // Whether the confirmation of one event may read its candidates straight from the band lists.
@@ -533,8 +536,9 @@ __device__ __forceinline__ int wrap_col(int j, int n)
 // nine neighbours of slice m - 1 precede a cell in raster order (strictly lower), the nine of
 // slice m + 1 follow it (not higher).
 // MASKS: the staged values are the cells' layer masks themselves (compared by their layer counts,
-// and written out from shared memory, M unused).
-template <int TPB, typename V, bool D3 = false, bool MASKS = false>
+// and written out from shared memory, M unused).  SMASK: M points to the band's own rows' masks in
+// shared memory (nrows rows of Nphi), not to the accumulator.
+template <int TPB, typename V, bool D3 = false, bool MASKS = false, bool SMASK = false>
 __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, int nphi, int threshold,
                                                 const uint16_t *M, uint2 *out, int cap)
 {
@@ -604,7 +608,9 @@ __device__ __forceinline__ int band_peak_search(const V *pc, int nrows, int i0, 
             pk &= pk - 1u;
             const unsigned cellg = (unsigned)(i0 + rr) * (unsigned)nphi + (unsigned)(j0 + c);
             if (idx < cap)
-                out[idx] = make_uint2(cellg, MASKS ? (unsigned)pc[(rr + 1) * nphi + j0 + c] : (unsigned)M[cellg]);
+                out[idx] = make_uint2(cellg, MASKS   ? (unsigned)pc[(rr + 1) * nphi + j0 + c]
+                                             : SMASK ? (unsigned)M[rr * nphi + j0 + c]
+                                                     : (unsigned)M[cellg]);
             ++idx;
         }
         running += s_total;

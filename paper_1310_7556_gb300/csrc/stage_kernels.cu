@@ -56,10 +56,10 @@ __global__ void __launch_bounds__(kClearThreads) clear_kernel(ClearList cl)
     }
 }
 
-__global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Workspace w)
+// The state a counting CTA starts from: its radius ranges, and (with recycling, block 0) the next
+// event's counters and radius ranges.  The caller synchronises the CTA afterwards.
+__device__ __forceinline__ void count_prologue(const Workspace &w, unsigned *s_rmin, unsigned *s_rmax)
 {
-    pdl_enter();
-    __shared__ unsigned int s_rmin[HOUGH_MAX_LAYERS], s_rmax[HOUGH_MAX_LAYERS];
     if (threadIdx.x < HOUGH_MAX_LAYERS) {
         s_rmin[threadIdx.x] = 0xFFFFFFFFu;
         s_rmax[threadIdx.x] = 0u;
@@ -73,77 +73,95 @@ __global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Wor
             w.radii_next->rmax[threadIdx.x] = 0u;
         }
     }
+}
+
+// Hit h of event e: validation, its key (layer, azimuth bucket) and rank within the bucket, the
+// bucket's extrema of f, its hot record in input order, and the CTA's radius range of its layer.
+__device__ __forceinline__ void count_hit(const Axes &ax, const Workspace &w, const HitInputs &in, float cscale,
+                                          int nkeys, int64_t h, int e, unsigned *s_rmin, unsigned *s_rmax)
+{
+    const float rr = __ldg(&in.r[h]);
+    const float ph = __ldg(&in.phi[h]);
+    const float zz = __ldg(&in.z[h]);
+    const int l = __ldg(&in.layer[h]);
+    unsigned bad = 0;
+    if (l >= ax.n_layers) bad |= HOUGH_DEVERR_LAYER;
+    if (!(rr > 0.f) || !isfinite(rr) || !(fabsf(ph) <= 1000.f) || !isfinite(zz))
+        bad |= HOUGH_DEVERR_RADIUS;
+    if (bad) {
+        atomicOr(&w.stats[e].device_error, bad);
+        w.key[h] = -1;
+        return;
+    }
+    // bin coordinate of the hit's own azimuth: u_h = Nphi (phi + pi) / (2 pi) = J + f, in
+    // two-float arithmetic (about 2^-44 relative: 1e-10 bins at Nphi = 2048), since the
+    // fraction must resolve far below the 1e-4-bin window in which votes may differ
+    float2 sp = two_sum(ph, ax.pi_hi);
+    sp.y = __fadd_rn(sp.y, ax.pi_lo);
+    float2 u = two_prod(sp.x, ax.u_hi);
+    u.y = u.y + (sp.x * ax.u_lo + sp.y * ax.u_hi);
+    float fl = floorf(u.x);
+    float f = __fadd_rn(__fsub_rn(u.x, fl), u.y);   // u.x - fl is exact
+    if (f < 0.f) {
+        f = __fadd_rn(f, 1.f);
+        fl -= 1.f;
+    }
+    if (f >= 1.f) {   // also the fraction that rounded up to 1: carry into J
+        f = __fsub_rn(f, 1.f);
+        fl += 1.f;
+    }
+    int J = (int)fl % ax.n_phi;
+    if (J < 0) J += ax.n_phi;
+    const int k = l * ax.n_phi + J;
+    w.key[h] = k;
+    w.rank[h] = atomicAdd(&w.counts[(int64_t)e * nkeys + k], 1);
+    // bucket extrema of f as ordered bit patterns (f >= 0): .x of bucket J keeps the maximum
+    // (offset by one so an empty bucket, 0, is below every hit), .y of bucket J-1 keeps the
+    // maximum of the complement, i.e. the minimum of bucket J
+    if (w.prof) {
+        uint2 *prof = w.prof + (int64_t)e * prof_event_entries(ax) + (int64_t)l * prof_stride(ax);
+        const int Jm = J == 0 ? ax.n_phi - 1 : J - 1;
+        atomicMax(&prof[J].x, __float_as_uint(f) + 1u);
+        atomicMax(&prof[Jm].y, ~__float_as_uint(f));
+        if (J < kProfPad) atomicMax(&prof[J + ax.n_phi].x, __float_as_uint(f) + 1u);   // the repeated copy
+        if (Jm < kProfPad) atomicMax(&prof[Jm + ax.n_phi].y, ~__float_as_uint(f));
+    }
+    HotHit hh;
+    hh.f = f;
+    hh.c = __fmul_rn(cscale, rr);
+    hh.jl = (uint32_t)J | ((uint32_t)l << 16);
+    hh.rows = 0;
+    w.hot_tmp[h] = hh;
+    // radii are mostly equal within a layer: only a hit outside the range seen so far updates it
+    const unsigned rb = __float_as_uint(rr);
+    if (rb < *(volatile unsigned *)&s_rmin[l]) atomicMin(&s_rmin[l], rb);
+    if (rb > *(volatile unsigned *)&s_rmax[l]) atomicMax(&s_rmax[l], rb);
+}
+
+// The CTA's radius ranges into the event's (after a CTA barrier).
+__device__ __forceinline__ void count_epilogue(const Workspace &w, const unsigned *s_rmin, const unsigned *s_rmax)
+{
+    if (threadIdx.x < HOUGH_MAX_LAYERS && s_rmax[threadIdx.x] != 0u) {
+        atomicMin(&w.radii->rmin[threadIdx.x], s_rmin[threadIdx.x]);
+        atomicMax(&w.radii->rmax[threadIdx.x], s_rmax[threadIdx.x]);
+    }
+}
+
+__global__ void __launch_bounds__(kStageThreads) stage_count_kernel(Axes ax, Workspace w)
+{
+    pdl_enter();
+    __shared__ unsigned int s_rmin[HOUGH_MAX_LAYERS], s_rmax[HOUGH_MAX_LAYERS];
+    count_prologue(w, s_rmin, s_rmax);
     __syncthreads();
     const int nkeys = n_keys(ax);
     // FP32 sagitta coefficient of the per-vote path; its rounding is covered by the refine window
     const float cscale = (float)(0.15 * ax.b / 100.0);
     const int64_t total = hit_total(w);
     const HitInputs in = hit_inputs(w);
-    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total;
-         h += (int64_t)gridDim.x * blockDim.x) {
-        const int e = event_of(w.hit_start, w.n_events, h);
-        const float rr = __ldg(&in.r[h]);
-        const float ph = __ldg(&in.phi[h]);
-        const float zz = __ldg(&in.z[h]);
-        const int l = __ldg(&in.layer[h]);
-        unsigned bad = 0;
-        if (l >= ax.n_layers) bad |= HOUGH_DEVERR_LAYER;
-        if (!(rr > 0.f) || !isfinite(rr) || !(fabsf(ph) <= 1000.f) || !isfinite(zz))
-            bad |= HOUGH_DEVERR_RADIUS;
-        if (bad) {
-            atomicOr(&w.stats[e].device_error, bad);
-            w.key[h] = -1;
-            continue;
-        }
-        // bin coordinate of the hit's own azimuth: u_h = Nphi (phi + pi) / (2 pi) = J + f, in
-        // two-float arithmetic (about 2^-44 relative: 1e-10 bins at Nphi = 2048), since the
-        // fraction must resolve far below the 1e-4-bin window in which votes may differ
-        float2 sp = two_sum(ph, ax.pi_hi);
-        sp.y = __fadd_rn(sp.y, ax.pi_lo);
-        float2 u = two_prod(sp.x, ax.u_hi);
-        u.y = u.y + (sp.x * ax.u_lo + sp.y * ax.u_hi);
-        float fl = floorf(u.x);
-        float f = __fadd_rn(__fsub_rn(u.x, fl), u.y);   // u.x - fl is exact
-        if (f < 0.f) {
-            f = __fadd_rn(f, 1.f);
-            fl -= 1.f;
-        }
-        if (f >= 1.f) {   // also the fraction that rounded up to 1: carry into J
-            f = __fsub_rn(f, 1.f);
-            fl += 1.f;
-        }
-        int J = (int)fl % ax.n_phi;
-        if (J < 0) J += ax.n_phi;
-        const int k = l * ax.n_phi + J;
-        w.key[h] = k;
-        w.rank[h] = atomicAdd(&w.counts[(int64_t)e * nkeys + k], 1);
-        // bucket extrema of f as ordered bit patterns (f >= 0): .x of bucket J keeps the maximum
-        // (offset by one so an empty bucket, 0, is below every hit), .y of bucket J-1 keeps the
-        // maximum of the complement, i.e. the minimum of bucket J
-        if (w.prof) {
-            uint2 *prof = w.prof + (int64_t)e * prof_event_entries(ax) + (int64_t)l * prof_stride(ax);
-            const int Jm = J == 0 ? ax.n_phi - 1 : J - 1;
-            atomicMax(&prof[J].x, __float_as_uint(f) + 1u);
-            atomicMax(&prof[Jm].y, ~__float_as_uint(f));
-            if (J < kProfPad) atomicMax(&prof[J + ax.n_phi].x, __float_as_uint(f) + 1u);   // the repeated copy
-            if (Jm < kProfPad) atomicMax(&prof[Jm + ax.n_phi].y, ~__float_as_uint(f));
-        }
-        HotHit hh;
-        hh.f = f;
-        hh.c = __fmul_rn(cscale, rr);
-        hh.jl = (uint32_t)J | ((uint32_t)l << 16);
-        hh.rows = 0;
-        w.hot_tmp[h] = hh;
-        // radii are mostly equal within a layer: only a hit outside the range seen so far updates it
-        const unsigned rb = __float_as_uint(rr);
-        if (rb < *(volatile unsigned *)&s_rmin[l]) atomicMin(&s_rmin[l], rb);
-        if (rb > *(volatile unsigned *)&s_rmax[l]) atomicMax(&s_rmax[l], rb);
-    }
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total; h += (int64_t)gridDim.x * blockDim.x)
+        count_hit(ax, w, in, cscale, nkeys, h, event_of(w.hit_start, w.n_events, h), s_rmin, s_rmax);
     __syncthreads();
-    if (threadIdx.x < HOUGH_MAX_LAYERS && s_rmax[threadIdx.x] != 0u) {
-        atomicMin(&w.radii->rmin[threadIdx.x], s_rmin[threadIdx.x]);
-        atomicMax(&w.radii->rmax[threadIdx.x], s_rmax[threadIdx.x]);
-    }
+    count_epilogue(w, s_rmin, s_rmax);
 }
 
 // One CTA per layer: whether all the layer's hits share one radius, that radius's voting rows and
@@ -158,7 +176,10 @@ __device__ __forceinline__ void layer_table(const Axes &ax, const Workspace &w, 
     __shared__ int s_dirty;
     if (threadIdx.x == 0) {
         LayerInfo li;
+        // every load of the decision at once (one round trip, not a chain of them)
         const unsigned rmin = w.radii->rmin[l], rmax = w.radii->rmax[l];
+        const int m_valid = w.memo->valid[l], m_lo = w.memo->lo[l], m_hi = w.memo->hi[l], m_nvote = w.memo->nvote[l];
+        const unsigned m_r = w.memo->r_bits[l];
         li.present = (l < ax.n_layers) && rmax != 0u;
         li.uniform = !li.present || rmin == rmax;   // a layer without hits is trivially uniform
         li.lo = 1;
@@ -166,7 +187,7 @@ __device__ __forceinline__ void layer_table(const Axes &ax, const Workspace &w, 
         li.r_bits = rmin;
         li.nvote = 0;
         li.pad[0] = li.pad[1] = 0;
-        const int dirty = li.present && li.uniform && !(w.memo->valid[l] && w.memo->r_bits[l] == rmin);
+        const int dirty = li.present && li.uniform && !(m_valid && m_r == rmin);
         if (li.present && li.uniform) {
             if (dirty) {
                 if (ax.n_d0) {   // every slice has its own rows; the table marks those that vote
@@ -180,9 +201,9 @@ __device__ __forceinline__ void layer_table(const Axes &ax, const Workspace &w, 
                 w.memo->hi[l] = li.hi;
                 w.memo->valid[l] = 1;
             } else {
-                li.lo = w.memo->lo[l];   // the same radius as before: its rows are memoised
-                li.hi = w.memo->hi[l];
-                li.nvote = w.memo->nvote[l];
+                li.lo = m_lo;   // the same radius as before: its rows are memoised
+                li.hi = m_hi;
+                li.nvote = m_nvote;
             }
         }
         w.info[l] = li;
@@ -260,11 +281,14 @@ __device__ __forceinline__ int scan_range(const int32_t *counts, int32_t *offs, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int base = k0; base < k1; base += kScanRound) {
         const int n = min(kScanRound, k1 - base);
+        int cv[kScanPerThread];   // every load in flight before the first store
 #pragma unroll
         for (int r = 0; r < kScanPerThread; ++r) {
             const int k = r * kScanThreads + threadIdx.x;
-            s_tile[scan_pad(k)] = k < n ? counts[base + k] : 0;
+            cv[r] = k < n ? counts[base + k] : 0;
         }
+#pragma unroll
+        for (int r = 0; r < kScanPerThread; ++r) s_tile[scan_pad(r * kScanThreads + threadIdx.x)] = cv[r];
         __syncthreads();
         const int k0 = threadIdx.x * kScanPerThread;
         int v[kScanPerThread];
@@ -332,8 +356,21 @@ __device__ __forceinline__ void scan_layer(const Axes &ax, const Workspace &w, c
     const int nkeys = n_keys(ax), nphi = ax.n_phi;
     const int32_t *counts = w.counts + (int64_t)e * nkeys;
     int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
+    // the counts of the layers before: 16-byte loads, eight in flight per thread (one round trip
+    // for most grids, where a sum of dependent loads would take one per element)
     int part = 0;
-    for (int k = threadIdx.x; k < l * nphi; k += kScanThreads) part += counts[k];
+    const int4 *c4 = reinterpret_cast<const int4 *>(counts);   // n_phi is a multiple of 64
+    const int n4 = l * nphi / 4;
+    for (int base = 0; base < n4; base += 8 * kScanThreads) {
+        int4 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int q = base + r * kScanThreads + threadIdx.x;
+            v[r] = q < n4 ? c4[q] : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) part += (v[r].x + v[r].y) + (v[r].z + v[r].w);
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, d);
     if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
@@ -361,75 +398,105 @@ __global__ void __launch_bounds__(kScanThreads) table_scan_kernel(Axes ax, Works
     else scan_keys(ax, w, b);
 }
 
-// Scatter every valid hit to its sorted position, completing its hot record with its voting rows.
-__global__ void __launch_bounds__(kStageThreads) scatter_kernel(Axes ax, Workspace w)
+// The votes of layers of one radius, per event: the layer's hits times its voting rows (thread t of
+// `nthreads` takes (event, layer) pairs t, t + nthreads, ...).  offs_of(e) is the event's offsets.
+template <typename Offs>
+__device__ __forceinline__ void count_table_votes(const Axes &ax, const Workspace &w, int64_t t0, int64_t nthreads,
+                                                  Offs offs_of)
 {
-    pdl_enter();
-    const int nkeys = n_keys(ax);
-    // the votes of layers of one radius: the layer's hits times its voting rows, per event
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)w.n_events * ax.n_layers;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = t0; t < (int64_t)w.n_events * ax.n_layers; t += nthreads) {
         const int e = (int)(t / ax.n_layers), l = (int)(t - (int64_t)e * ax.n_layers);
         const LayerInfo li = w.info[l];
         if (li.present && li.uniform && li.nvote > 0) {
-            const int32_t *offs = w.offs + (int64_t)e * (nkeys + 1);
-            const long long n_l = offs[(l + 1) * ax.n_phi] - offs[l * ax.n_phi];
+            const long long n_l = offs_of(e, (l + 1) * ax.n_phi) - offs_of(e, l * ax.n_phi);
             if (n_l) atomicAdd(&w.stats[e].votes_by_layer[l], (unsigned long long)(n_l * li.nvote));
         }
     }
-    if (w.recycle) {
-        // the bucket counts are read for the last time by the scan, which this kernel follows
-        uint4 *c4 = reinterpret_cast<uint4 *>(w.counts);
-        const int64_t n4 = (int64_t)w.n_events * nkeys / 4;
-        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x)
-            c4[q] = make_uint4(0u, 0u, 0u, 0u);
-        for (int64_t q = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)w.n_events * nkeys;
-             q += (int64_t)gridDim.x * blockDim.x)
-            w.counts[q] = 0;
+}
+
+// The bucket counts zeroed for the next event (recycling), by thread t0 of nthreads: the scan has
+// read them for the last time.
+__device__ __forceinline__ void recycle_counts(const Axes &ax, const Workspace &w, int64_t t0, int64_t nthreads)
+{
+    const int64_t n = (int64_t)w.n_events * n_keys(ax);
+    uint4 *c4 = reinterpret_cast<uint4 *>(w.counts);
+    for (int64_t q = t0; q < n / 4; q += nthreads) c4[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t q = n / 4 * 4 + t0; q < n; q += nthreads) w.counts[q] = 0;
+}
+
+// Valid hit h (input index; event start `start`) to its sorted position pos: its f, hot record hh
+// completed with its voting rows, cold record (r, phi, z) and z.
+__device__ __forceinline__ void sort_hit(const Axes &ax, const Workspace &w, int64_t h, int e, int64_t start,
+                                         int64_t pos, HotHit hh, float rr, float ph, float zz)
+{
+    if (w.fsort) w.fsort[pos] = hh.f;
+    const int l = (hh.jl >> 16) & 0xF;
+    const LayerInfo li = w.info[l];
+    int lo = li.lo, hi = li.hi;
+    if (!li.uniform && ax.n_d0) {
+        // every row may hold a vote; the vote kernels decide each in FP64
+        lo = 0;
+        hi = ax.n_qpt - 1;
+        const double c = sagitta_coef(ax, (double)rr);
+        unsigned long long nv = 0;
+        for (int row = 0; row < ax.n_qpt; ++row) {
+            double y = 2.0;
+            if (track_sin((double)rr, __dmul_rn(c, qpt_centre(ax, row)), d0_centre(ax, row), &y) && fabs(y) <= 1.0)
+                ++nv;
+        }
+        if (nv) atomicAdd(&w.stats[e].votes_by_layer[l], nv);
+    } else if (!li.uniform) {
+        row_range(ax, sagitta_coef(ax, (double)rr), &lo, &hi);
+        if (hi >= lo)
+            atomicAdd(&w.stats[e].votes_by_layer[l], (unsigned long long)(hi - lo + 1));
     }
+    if (hi < lo) { lo = 1; hi = 0; }
+    hh.rows = (uint32_t)lo | ((uint32_t)hi << 16);
+    w.hot[pos] = hh;
+    ColdHit ch;
+    ch.r = rr;
+    ch.phi = ph;
+    ch.z = zz;
+    ch.idx = (int32_t)(h - start);
+    w.cold[pos] = ch;
+    if (w.zsort) w.zsort[pos] = ch.z;
+}
+
+// Scatter every valid hit to its sorted position, completing its hot record with its voting rows.
+__global__ void __launch_bounds__(kStageThreads) hit_sort_kernel(Axes ax, Workspace w)
+{
+    pdl_enter();
+    const int nkeys = n_keys(ax);
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     const int64_t total = hit_total(w);
     const HitInputs in = hit_inputs(w);
-    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < total;
-         h += (int64_t)gridDim.x * blockDim.x) {
+    // this thread's first (event, layer) pair of the one-radius vote counts: its inputs requested
+    // now, counted after the hits, so the loads overlap the hits' own
+    const int64_t npairs = (int64_t)w.n_events * ax.n_layers;
+    LayerInfo tli{};
+    int tn = 0, te = 0, tl = 0;
+    if (t0 < npairs) {
+        te = (int)(t0 / ax.n_layers);
+        tl = (int)(t0 - (int64_t)te * ax.n_layers);
+        tli = w.info[tl];
+        const int32_t *o = w.offs + (int64_t)te * (nkeys + 1);
+        tn = o[(tl + 1) * ax.n_phi] - o[tl * ax.n_phi];
+    }
+    for (int64_t h = t0; h < total; h += nt) {
+        // every load that does not depend on another first, then the bucket offset and layer
+        // record that do: two round trips a hit
         const int k = w.key[h];
-        if (k < 0) continue;
+        const int rank = w.rank[h];
+        const HotHit hh = w.hot_tmp[h];
+        const float rr = in.r[h], ph = in.phi[h], zz = in.z[h];
         const int e = event_of(w.hit_start, w.n_events, h);
         const int64_t start = w.hit_start[e];
-        const int64_t pos = start + w.offs[(int64_t)e * (nkeys + 1) + k] + w.rank[h];
-        HotHit hh = w.hot_tmp[h];
-        if (w.fsort) w.fsort[pos] = hh.f;
-        const int l = (hh.jl >> 16) & 0xF;
-        const LayerInfo li = w.info[l];
-        int lo = li.lo, hi = li.hi;
-        const float rr = in.r[h];
-        if (!li.uniform && ax.n_d0) {
-            // every row may hold a vote; the vote kernels decide each in FP64
-            lo = 0;
-            hi = ax.n_qpt - 1;
-            const double c = sagitta_coef(ax, (double)rr);
-            unsigned long long nv = 0;
-            for (int row = 0; row < ax.n_qpt; ++row) {
-                double y = 2.0;
-                if (track_sin((double)rr, __dmul_rn(c, qpt_centre(ax, row)), d0_centre(ax, row), &y) && fabs(y) <= 1.0)
-                    ++nv;
-            }
-            if (nv) atomicAdd(&w.stats[e].votes_by_layer[l], nv);
-        } else if (!li.uniform) {
-            row_range(ax, sagitta_coef(ax, (double)rr), &lo, &hi);
-            if (hi >= lo)
-                atomicAdd(&w.stats[e].votes_by_layer[l], (unsigned long long)(hi - lo + 1));
-        }
-        if (hi < lo) { lo = 1; hi = 0; }
-        hh.rows = (uint32_t)lo | ((uint32_t)hi << 16);
-        w.hot[pos] = hh;
-        ColdHit ch;
-        ch.r = rr;
-        ch.phi = in.phi[h];
-        ch.z = in.z[h];
-        ch.idx = (int32_t)(h - start);
-        w.cold[pos] = ch;
-        if (w.zsort) w.zsort[pos] = ch.z;
+        if (k >= 0) sort_hit(ax, w, h, e, start, start + w.offs[(int64_t)e * (nkeys + 1) + k] + rank, hh, rr, ph, zz);
     }
+    if (t0 < npairs && tli.present && tli.uniform && tli.nvote > 0 && tn)
+        atomicAdd(&w.stats[te].votes_by_layer[tl], (unsigned long long)tn * (unsigned long long)tli.nvote);
+    count_table_votes(ax, w, t0 + nt, nt, [&](int e, int k) { return w.offs[(int64_t)e * (nkeys + 1) + k]; });
+    if (w.recycle) recycle_counts(ax, w, t0, nt);
 }
 
 int grid_for(int64_t n, int threads)
@@ -477,7 +544,7 @@ cudaError_t launch_stage(const Axes &ax, const Workspace &w, cudaStream_t stream
         return err;
     if ((err = mark(2))) return err;   // table_ms covers both; scan_ms stays empty
     if ((err = mark(3))) return err;
-    return launch_chained(scatter_kernel, dim3(g), dim3(kStageThreads), 0, stream, ax, w);
+    return launch_chained(hit_sort_kernel, dim3(g), dim3(kStageThreads), 0, stream, ax, w);
 }
 
 }  // namespace hough

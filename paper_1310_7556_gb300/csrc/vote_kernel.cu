@@ -528,8 +528,8 @@ __global__ void __launch_bounds__(TPB, 1) gather_kernel(GatherParams p)
         unsigned gb = 0u, valid = 0u;
         if (l < L && rr < nrows) {
             const LayerInfo li = w.info[l];
+            const TabEntry te = w.tab[l * ax.n_qpt + i];   // requested with the layer record: one round trip
             if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
-                const TabEntry te = w.tab[l * ax.n_qpt + i];
                 if (te.I != kNoVote) {
                     I = te.I;
                     gb = __float_as_uint(te.g);
@@ -695,8 +695,8 @@ __global__ void __launch_bounds__(TPB) fused_kernel(GatherParams p)
         unsigned gb = 0u, valid = 0u;
         if (l < L && s < S && i >= 0 && i < ax.n_qpt) {   // rows outside the grid hold no votes
             const LayerInfo li = w.info[l];
+            const TabEntry te = w.tab[l * ax.n_qpt + i];   // requested with the layer record: one round trip
             if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
-                const TabEntry te = w.tab[l * ax.n_qpt + i];
                 if (te.I != kNoVote) {
                     I = te.I;
                     gb = __float_as_uint(te.g);
@@ -845,8 +845,8 @@ __global__ void __launch_bounds__(TPB) gather_count_kernel(GatherParams p, int f
         unsigned valid = 0u;
         if (l < L && rr < nrows) {
             const LayerInfo li = w.info[l];
+            const TabEntry te = w.tab[l * ax.n_qpt + i];   // requested with the layer record: one round trip
             if (li.present && li.uniform && i >= li.lo && i <= li.hi) {
-                const TabEntry te = w.tab[l * ax.n_qpt + i];
                 if (te.I != kNoVote) {
                     I = te.I;
                     g = te.g;
@@ -998,11 +998,13 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
         compact_if_last(ax, w, pc, band_smem_bytes(ax, R));
         return;
     }
+    uint16_t *pm = reinterpret_cast<uint16_t *>(pc + (size_t)(R + 2) * nphi);   // the band's own rows' masks
     for (int q = threadIdx.x; q < (nrows + 2) * v8; q += kPeakThreads) {
         const int rr = q / v8, c8 = q - rr * v8;
         const int i = i0 - 1 + rr;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (i >= 0 && i < ax.n_qpt) v = *reinterpret_cast<const uint4 *>(M + (int64_t)i * nphi + c8 * 8);
+        if (rr >= 1 && rr <= nrows) *reinterpret_cast<uint4 *>(pm + (rr - 1) * nphi + c8 * 8) = v;
         const uint32_t words[4] = {v.x, v.y, v.z, v.w};
         uint32_t packed[2] = {0u, 0u};
 #pragma unroll
@@ -1013,7 +1015,8 @@ __global__ void __launch_bounds__(kPeakThreads) peaks_kernel(Axes ax, Workspace 
         *reinterpret_cast<uint2 *>(pc + rr * nphi + c8 * 8) = make_uint2(packed[0], packed[1]);
     }
     __syncthreads();
-    const int cnt = band_peak_search<kPeakThreads>(pc, nrows, i0, nphi, ax.threshold, M, out, w.band_cap);
+    const int cnt = band_peak_search<kPeakThreads, unsigned char, false, false, true>(pc, nrows, i0, nphi, ax.threshold,
+                                                                                     pm, out, w.band_cap);
     if (threadIdx.x == 0) w.band_counts[(int64_t)e * nb + band] = cnt;
     __syncthreads();   // the band buffer is free
     compact_if_last(ax, w, pc, band_smem_bytes(ax, R));
