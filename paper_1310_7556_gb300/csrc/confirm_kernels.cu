@@ -59,6 +59,7 @@ constexpr int kEventPairs = 4096;  // pairs it votes at a time
 constexpr int kEventWarps = 4;     // warps per candidate for a single event
 constexpr int kBatchGroups = 4;    // one-warp groups per CTA at most (batches)
 constexpr int kMaxBandsRead = 8192;   // band offsets a single event's CTA may hold to read the band lists
+constexpr int kManyPerCta = 2;        // one event with more candidates than this per CTA: a warp per candidate
 
 // Per-group scratch of a group of WPC warps, for detectors of at most NL layers.  Kind of a range: bits 0..3 the layer, bit 4 the side (1: f < g), bit 5 a
 // layer whose hits lie at several radii (each hit's vote recomputed).
@@ -660,7 +661,7 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
             e_next = w.cand_base[e + 1];
         }
         const int c = f - e_base;
-        if (WPC > 1 && band_offs) {
+        if (band_offs) {
             // one event whose candidate list was not compacted: candidate c from its band's list
             int b = 0, hi = n_bands(ax, w.band_rows) - 1;   // the last band with offset <= c (shared memory)
             while (b < hi) {
@@ -851,7 +852,8 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
 // Membership and stage 2 of every candidate of every event, a group of WPC warps per candidate.
 template <int WPC, int CAP, int MAXP, int NL, bool P10>
 __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC == 1 ? (P10 ? 8 : 5) : 1)
-    confirm_kernel(Axes ax, Workspace w, float s32, float refine_eps, int grid_words, int scratch_bytes)
+    confirm_kernel(Axes ax, Workspace w, float s32, float refine_eps, int grid_words, int scratch_bytes,
+                   int bands_at, int many_groups, int many_scratch_bytes)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_c[];
@@ -871,7 +873,7 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
     int total;
     const int *band_offs = nullptr;
     if (WPC > 1 && w.cands_from_bands) {   // (batches use one-warp groups and a compacted list)
-        int *bo = reinterpret_cast<int *>(smem_c + (size_t)ngroups * scratch_bytes + (size_t)ngroups * grid_words * 4);
+        int *bo = reinterpret_cast<int *>(smem_c + bands_at);
         const int nb = n_bands(ax, w.band_rows);
         const int found = block_excl_scan(w.band_counts, nb, bo);
         total = min(found, w.max_cand);
@@ -885,6 +887,38 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
         band_offs = bo;
     } else {
         total = (int)w.counters->total_cands;
+    }
+    if constexpr (WPC > 1) {
+        if (many_groups && total > kManyPerCta * (int)gridDim.x) {
+            // one event with many candidates (a fine grid, a busy event): each warp confirms its
+            // own candidates with its own scratch and grid, as in batches, instead of four warps
+            // sharing one candidate's chain
+            using S1 = Scratch<1, kBatchCap, kBatchPairs, NL>;
+            const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            S1 &s1 = *reinterpret_cast<S1 *>(smem_c + (size_t)g * many_scratch_bytes);
+            uint32_t *grid1 = reinterpret_cast<uint32_t *>(smem_c + (size_t)many_groups * many_scratch_bytes) +
+                              (size_t)g * grid_words;
+            if (g < many_groups) {
+                for (int q = lane; q < grid_words; q += 32) grid1[q] = 0u;
+                for (int q = lane; q < (int)(sizeof(S1) / 4); q += 32) reinterpret_cast<uint32_t *>(&s1)[q] = 0u;
+            }
+            if (threadIdx.x < HOUGH_MAX_LAYERS) s_info[threadIdx.x] = li;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int gen = 0;
+                for (int l = 0; l < ax.n_layers; ++l) gen |= s_info[l].present && !s_info[l].uniform;
+                s_general = gen;
+            }
+            __syncthreads();
+            if (g >= many_groups) return;
+            if (s_general)
+                confirm_all<1, kBatchCap, kBatchPairs, NL, P10, true>(ax, w, s32, refine_eps, s1, grid1, s_info, many_groups,
+                                                                      g, total, band_offs);
+            else
+                confirm_all<1, kBatchCap, kBatchPairs, NL, P10, false>(ax, w, s32, refine_eps, s1, grid1, s_info,
+                                                                       many_groups, g, total, band_offs);
+            return;
+        }
     }
     for (int q = group_tid<WPC>(); q < grid_words; q += 32 * WPC) grid[q] = 0u;
     // the scratch starts zeroed: lanes past a list read its terms without a branch
@@ -960,8 +994,13 @@ cudaError_t launch_confirm(const Axes &ax, const Workspace &w, int sms, float s3
     // one-warp groups: as many per CTA (up to kBatchGroups) as shared memory holds
     const int room = smem_optin() - (int)(sizeof(LayerInfo) * HOUGH_MAX_LAYERS) - 1024;
     const int groups = WPC == 1 ? std::max(1, std::min(kBatchGroups, room / (int)per_group)) : 1;
-    const size_t smem = (size_t)groups * per_group +
-                        (w.cands_from_bands ? ((size_t)n_bands(ax, w.band_rows) + 1) * sizeof(int) : 0);
+    // a group of several warps may split into one-warp groups when its event has many candidates:
+    // room for WPC one-warp scratches and grids too, when they fit beside the bands
+    const size_t many_scratch = (sizeof(Scratch<1, kBatchCap, kBatchPairs, NL>) + 15) & ~(size_t)15;
+    const size_t many_bytes = (size_t)WPC * (many_scratch + (size_t)words * 4);
+    const int many = WPC > 1 && many_bytes <= 128 * 1024 ? WPC : 0;
+    const size_t layout = std::max((size_t)groups * per_group, many ? many_bytes : (size_t)0);
+    const size_t smem = layout + (w.cands_from_bands ? ((size_t)n_bands(ax, w.band_rows) + 1) * sizeof(int) : 0);
     cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (!err) err = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
@@ -971,7 +1010,7 @@ cudaError_t launch_confirm(const Axes &ax, const Workspace &w, int sms, float s3
     // the number of candidates is known on the device only: a persistent grid of exactly the
     // resident CTAs, each group striding over the flattened (event, candidate) work
     return launch_chained(kernel, dim3(ctas * sms), dim3(threads), smem, stream, ax, w, s32, refine_eps, words,
-                          (int)scratch);
+                          (int)scratch, (int)layout, many, (int)many_scratch);
 }
 
 }  // namespace
