@@ -19,7 +19,8 @@ holding vote counts, the paper's literal A[B[i]] += 1, on the pileup event and t
 `d0_axis` (non-prompt tracks on a (d0, q/pT, phi0) grid), `fused_vote_peak` (the vote and the
 peak search in one kernel, the accumulator kept in shared memory, against the separate kernels),
 `paper_sweep` (the paper's Fig. 2 experiment) and `cpu_baseline` (the FP64 oracle on this
-machine's host cores, on a bounded sample).
+machine's host cores, on a bounded sample; beside it, as context, `fp32_openmp`: the FP32 OpenMP
+CPU implementation in the paper's CPU manner on the three single-event workloads).
 
 `--impl reference` times the FP64 CPU oracle (the plain restatement of the method the CUDA path is
 checked against) on the host cores, on the same workload and metric.
@@ -184,6 +185,28 @@ def cpu_baseline(workload, n_single: int = 4):
             "single_thread": {"value": n_single / dt1, "unit": "events/s", "cores": 1,
                               "sample": f"{n_single} full {workload} events (seeds 0..{n_single - 1})",
                               "votes_per_s": votes / dt1, "seconds": dt1}}
+
+
+def fp32_baseline(workload, seconds: float = 3.0):
+    """The FP32 OpenMP CPU implementation (baseline/hough_cpu.c, the paper's CPU recipe of Sec. 6.2:
+    threads over the hits with thread-private accumulators merged at the end, over the rows of the
+    peak search and over the candidates) on every host core: events of the workload, one after
+    another, for about `seconds` after one untimed event."""
+    import baseline
+    w = eg.WORKLOADS[workload]
+    b = baseline.make_binning(w.geometry, w.binning)
+    cores = os.cpu_count() or 1
+    baseline.run_event(b, w.event(0), threads=cores)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        baseline.run_event(b, w.event(200 + n), threads=cores)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= 200:
+            break
+    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "fp32_openmp",
+            "sample": f"{n} full {workload} events (seeds 200..{199 + n}), one after another, each on all "
+                      f"{cores} threads, whole path (vote, peaks, membership, stage 2), FP32", "seconds": dt}
 
 
 def run_reference(args):
@@ -967,6 +990,8 @@ def main():
     }
     if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline and args.only == "all":
         line["cpu_baseline"] = cpu_baseline(args.workload)
+        # context: the FP32 multi-core CPU implementation on the three single-event workloads
+        line["cpu_baseline"]["fp32_openmp"] = {k: fp32_baseline(k) for k in ("single_50trk", "pileup_100k", "fine_4m")}
     ctx.close()
     if env.rank == 0:
         print(json.dumps(line), flush=True)
