@@ -316,3 +316,30 @@ def test_process_reads_pinned_hits_in_place(binding):
         with pytest.raises(binding.HoughError) as e:
             ctx.vote(*pinned, n_hits=ev.n_hits, where=binding.HOST)
         assert e.value.code == binding.EINVAL
+
+
+def test_back_to_back_events_on_one_context(binding):
+    """Events put through one context with nothing between one event's stage 2 and the next
+    event's vote (the next event's counting then runs beside the last confirmation): the last
+    event's results equal those of a context that saw it alone."""
+    import torch
+    w = eg.WORKLOADS["pileup_100k"]
+    evs = [w.event(7), w.event(8).subset(np.arange(20000)), w.event(9)]
+    dev = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (e.r, e.phi, e.z, e.layer)] for e in evs]
+    torch.cuda.synchronize()
+    n_max = max(e.n_hits for e in evs)
+    with binding.HoughContext(w.geometry, w.binning, max_hits=n_max) as ctx:
+        for k, e in enumerate(evs):
+            ctx.vote(*dev[k], n_hits=e.n_hits, where=binding.DEVICE)
+            ctx.peaks()
+            ctx.stage2()
+        cands = ctx.candidates()
+        st = ctx.stats()
+        off, mem = ctx.members(len(cands))
+        M = ctx.accumulator()
+    alone = run_gpu(binding, w.geometry, w.binning, evs[-1], where="device")
+    assert np.array_equal(M, alone["M"])
+    assert np.array_equal(cands, alone["candidates"])
+    assert np.array_equal(off, alone["member_offsets"]) and np.array_equal(mem, alone["members"])
+    for f in ("votes", "n_candidates", "n_members", "stage2_votes"):
+        assert int(getattr(st, f)) == int(getattr(alone["stats"], f)), f
