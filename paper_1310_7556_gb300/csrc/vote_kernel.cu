@@ -75,9 +75,14 @@ __device__ __forceinline__ void layer_masks(const Workspace &w, int L, unsigned 
 // masks a word).  The lanes of a warp vote for 32 consecutive rows, so their 32 atomics fall in 32
 // different banks whatever columns the votes land in.
 __host__ __device__ inline int tile_row_pitch(int R) { return R <= 32 ? R : (R + 31) & ~31; }
+// Margin columns on each side of the tile: a table layer's vote j - J0 lies within its window's
+// spread of I beyond the tile's columns, so when that spread fits the margin every vote of the
+// layer is cast where it falls -- into the tile or into a margin, which the flush ignores --
+// without a test, a clamp or a select (even, so two-mask words keep their pairing).
+constexpr int kTileMargin = 64;
 __host__ __device__ inline int scatter_tile_words(int R, int W, bool wide)
 {
-    return (wide ? W : W >> 1) * tile_row_pitch(R);
+    return (wide ? W + 2 * kTileMargin : (W + 2 * kTileMargin) >> 1) * tile_row_pitch(R);
 }
 // Byte offset of the per-warp hit buffers in the scatter kernel's dynamic shared memory.
 __host__ __device__ inline size_t scatter_hit_offset(int R, int W, int L, bool wide)
@@ -93,6 +98,17 @@ __device__ __forceinline__ void tile_vote(uint32_t *tile, int pitch, int rr, int
     if (CELL == 2) atomicAdd(&tile[jt * pitch + rr], 1u);
     else if (CELL == 1) atomicOr(&tile[jt * pitch + rr], lbit);
     else atomicOr(&tile[(jt >> 1) * pitch + rr], lbit << ((jt & 1) << 4));
+}
+
+// A vote cast where it falls, at column jt of the lane's row (base: the row's word of column 0 as a
+// shared-memory address, s4: the column stride in bytes, 0 for a lane whose votes all go to a
+// word of its own).  jt may lie in a margin.
+template <int CELL>
+__device__ __forceinline__ void tile_vote_at(unsigned base, int s4, int jt, uint32_t lbit)
+{
+    if (CELL == 2) asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(base + jt * s4) : "memory");
+    else if (CELL == 1) asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(base + jt * s4), "r"(lbit) : "memory");
+    else asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(base + (jt >> 1) * s4), "r"(lbit << ((jt & 1) << 4)) : "memory");
 }
 
 // The same for a vote that may miss the tile (in false): every lane issues its atomic, a missing
@@ -118,13 +134,15 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     __shared__ int s_pre[kMaxRanges + 1];
     __shared__ unsigned long long s_refined;
     __shared__ unsigned s_umask, s_gmask;
+    __shared__ unsigned s_fast;   // table layers whose spread of I fits the tile's margins
 
     const Axes &ax = p.ax;
     const int R = p.R, W = p.W, L = ax.n_layers, nphi = ax.n_phi;
     const int pitch = tile_row_pitch(R);
-    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *tile_all = reinterpret_cast<uint32_t *>(smem_raw);
     const int tile_words = scatter_tile_words(R, W, CELL != 0);
-    TabEntry *tab = reinterpret_cast<TabEntry *>(tile + tile_words);
+    uint32_t *tile = tile_all + (CELL != 0 ? kTileMargin : kTileMargin / 2) * pitch;   // column 0
+    TabEntry *tab = reinterpret_cast<TabEntry *>(tile_all + tile_words);
     float *kq = reinterpret_cast<float *>(tab + L * R);
     // the warp's 32 staged hits: f (bits), J (shifted into the window for a table layer), c (bits), rows
     uint4 *hitbuf = reinterpret_cast<uint4 *>(smem_raw + scatter_hit_offset(R, W, L, CELL != 0)) + 32 * (threadIdx.x >> 5);
@@ -154,6 +172,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
             s_umask = GENERAL_ONLY ? ~g : u;   // layers this kernel treats with the table
             s_gmask = g;
             s_refined = 0ull;
+            s_fast = 0u;
         }
     }
     __syncthreads();
@@ -162,7 +181,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     const unsigned umask = s_umask;
 
     // clear the tile; stage this slab's table rows and FP32 q/pT centres
-    uint4 *tile4 = reinterpret_cast<uint4 *>(tile);
+    uint4 *tile4 = reinterpret_cast<uint4 *>(tile_all);
     for (int q = threadIdx.x; q < tile_words >> 2; q += TPB) tile4[q] = make_uint4(0u, 0u, 0u, 0u);
     for (int q = threadIdx.x; q < L * R; q += TPB) {
         const int l = q / R, rr = q - l * R;
@@ -204,6 +223,8 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                     } else {
                         ja = J0 + imin;
                         jb = J0 + W + imax;
+                        // votes of this window fall in [imin - imax - 1, W + imax - imin] of the tile
+                        if (imax - imin + 1 <= kTileMargin) atomicOr(&s_fast, 1u << l);
                     }
                 }
             } else if (!none && ax.n_d0) {
@@ -346,7 +367,27 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                     const TabEntry te = tab[lr * R + (rowok ? rr : 0)];
                     const bool valid = rowok && te.I != kNoVote;
                     const float g = te.g;
-                    if (!wrap) {
+                    if (!wrap && ((s_fast >> lr) & 1u)) {
+                        // every vote where it falls: a lane of an invalid row (or none) votes into a
+                        // word of its own
+                        const unsigned base = valid ? smem_u32(tile + rr) : smem_u32(spare + lane);
+                        const int s4 = valid ? 4 * pitch : 0;
+                        const int K = te.I + J0;
+                        int k = k0;
+                        const uint2 *hb2 = reinterpret_cast<const uint2 *>(hitbuf);   // (f, J) of hit k at 2 k
+                        for (; k + 8 <= k1; k += 8) {
+                            uint2 h[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) h[u] = hb2[2 * (k + u)];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                tile_vote_at<CELL>(base, s4, (int)h[u].y - K - (__uint_as_float(h[u].x) < g ? 1 : 0), lbit);
+                        }
+                        for (; k < k1; ++k) {
+                            const uint2 h = hb2[2 * k];
+                            tile_vote_at<CELL>(base, s4, (int)h.y - K - (__uint_as_float(h.x) < g ? 1 : 0), lbit);
+                        }
+                    } else if (!wrap) {
                         const int K = valid ? te.I + J0 : -(1 << 30);   // an invalid row's votes all miss
                         // four hits at a time: their loads issue together, then their atomics
                         int k = k0;
