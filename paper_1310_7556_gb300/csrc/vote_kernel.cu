@@ -111,6 +111,39 @@ __device__ __forceinline__ void tile_vote_at(unsigned base, int s4, int jt, uint
     else asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(base + (jt >> 1) * s4), "r"(lbit << ((jt & 1) << 4)) : "memory");
 }
 
+// The votes of hits k0..k1-1 of the warp's buffer (f, byte offset of the column) for one row and
+// one layer of one mask a word: the vote of hit k goes to rowbase + offset_k - (f_k < g) s4b.  PRED:
+// some lane's row casts nothing (valid false), its atomics predicated off.
+template <int CELL, bool PRED>
+__device__ __forceinline__ void vote_run(const uint2 *hb2, int k0, int k1, float g, unsigned rowbase, unsigned s4b,
+                                         uint32_t lbit, bool valid)
+{
+    const unsigned vflag = valid ? 1u : 0u;
+    auto one = [&](uint2 h) {
+        const unsigned a = rowbase + h.y - (__uint_as_float(h.x) < g ? s4b : 0u);
+        if (PRED) {
+            if (CELL == 2)
+                asm volatile("{ .reg .pred p; setp.ne.u32 p, %1, 0; @p red.shared.add.u32 [%0], 1; }" ::"r"(a), "r"(vflag)
+                             : "memory");
+            else
+                asm volatile("{ .reg .pred p; setp.ne.u32 p, %2, 0; @p red.shared.or.b32 [%0], %1; }" ::"r"(a), "r"(lbit),
+                             "r"(vflag) : "memory");
+        } else {
+            if (CELL == 2) asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a) : "memory");
+            else asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(a), "r"(lbit) : "memory");
+        }
+    };
+    int k = k0;
+    for (; k + 8 <= k1; k += 8) {
+        uint2 h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) h[u] = hb2[2 * (k + u)];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) one(h[u]);
+    }
+    for (; k < k1; ++k) one(hb2[2 * k]);
+}
+
 // The same for a vote that may miss the tile (in false): every lane issues its atomic, a missing
 // vote adding nothing to a cell of its own row, so that no branch surrounds the atomic.  rowp,
 // stride: the lane's row of the tile and the column stride (pitch), or for a lane without a row of
@@ -330,15 +363,15 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
         const float kqr = rowok ? kq[rr] : 0.f;
         uint32_t *rowp = rowok ? tile + rr : spare + lane;
         const int stride = rowok ? pitch : 0;
-        for (int cb = hs * 32; cb < total; cb += HS * 32) {
-            const int v = cb + lane;
-            const int nvalid = min(32, total - cb);
-            HotHit hh;
+        // hit v's staged position, window shift and record (empty past the last hit); the next
+        // chunk's record is requested before this chunk votes, so its load overlaps the votes
+        auto fetch_hit = [&](int v, int &pos, int &off, HotHit &hh) {
             hh.f = 0.f;
             hh.c = 0.f;
-            hh.jl = 0u;
-            hh.rows = 1u;   // rows [1, 0]: none
-            int pos = 0, off = 0, l = 16;
+            hh.jl = 16u << 16;   // layer 16: none
+            hh.rows = 1u;        // rows [1, 0]: none
+            pos = 0;
+            off = 0;
             if (v < total) {
                 int q = 0;   // the range holding v: the last q with s_pre[q] <= v
 #pragma unroll
@@ -347,11 +380,25 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                 pos = s_start[q] + (v - s_pre[q]);
                 off = s_off[q];
                 hh = hot[pos];
-                l = (int)((hh.jl >> 16) & 0xFu);
             }
+        };
+        int pos_n, off_n;
+        HotHit hh_n;
+        fetch_hit(hs * 32 + lane, pos_n, off_n, hh_n);
+        for (int cb = hs * 32; cb < total; cb += HS * 32) {
+            const int nvalid = min(32, total - cb);
+            const int pos = pos_n, off = off_n;
+            const HotHit hh = hh_n;
+            if (cb + HS * 32 < total) fetch_hit(cb + HS * 32 + lane, pos_n, off_n, hh_n);
+            const int l = (int)((hh.jl >> 16) & 0x1Fu);
             const int J = (int)(hh.jl & 0xFFFFu);
             const bool table_hit = !GENERAL_ONLY && l < 16 && ((umask >> l) & 1u);
-            hitbuf[lane] = make_uint4(__float_as_uint(hh.f), (uint32_t)(wrap || !table_hit ? J : J + off),
+            // a table layer whose votes fall within the margins, one mask a word: the byte offset
+            // of its column in a row of the tile (the vote then subtracts the row's shift in bytes)
+            const bool fast_hit = CELL != 0 && !wrap && table_hit && ((s_fast >> l) & 1u);
+            hitbuf[lane] = make_uint4(__float_as_uint(hh.f),
+                                      fast_hit ? (uint32_t)((J + off) * 4 * pitch)
+                                               : (uint32_t)(wrap || !table_hit ? J : J + off),
                                       __float_as_uint(hh.c), hh.rows);
             __syncwarp();
             // runs of hits of one layer (the ranges are in layer order)
@@ -367,9 +414,19 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
                     const TabEntry te = tab[lr * R + (rowok ? rr : 0)];
                     const bool valid = rowok && te.I != kNoVote;
                     const float g = te.g;
-                    if (!wrap && ((s_fast >> lr) & 1u)) {
-                        // every vote where it falls: a lane of an invalid row (or none) votes into a
-                        // word of its own
+                    if (CELL != 0 && !wrap && ((s_fast >> lr) & 1u)) {
+                        // every vote where it falls: the word of column (J + off) - K - (f < g) of the
+                        // lane's row, its byte offset from the staged column offset; a lane of an
+                        // invalid row (or none) casts nothing
+                        const unsigned s4b = 4u * (unsigned)pitch;
+                        const unsigned rowbase = smem_u32(tile + rr) - (unsigned)(te.I + J0) * s4b;
+                        const uint2 *hb2 = reinterpret_cast<const uint2 *>(hitbuf);   // (f, column bytes) of hit k at 2 k
+                        if (__all_sync(0xFFFFFFFFu, valid))
+                            vote_run<CELL, false>(hb2, k0, k1, g, rowbase, s4b, lbit, true);
+                        else
+                            vote_run<CELL, true>(hb2, k0, k1, g, rowbase, s4b, lbit, valid);
+                    } else if (!wrap && ((s_fast >> lr) & 1u)) {
+                        // the same with two masks a word: the vote's column from its J
                         const unsigned base = valid ? smem_u32(tile + rr) : smem_u32(spare + lane);
                         const int s4 = valid ? 4 * pitch : 0;
                         const int K = te.I + J0;
