@@ -447,6 +447,8 @@ def kernel_table(w, n_hits, st, smem_peak, hbm_peak, peaks_kind, steps=PLAIN_KER
     table = {}
     for name, key, src in steps:
         ms = st["stage_ms"][key]
+        if ms == 0.0 and name in ("clear_kernel", "compact_kernel"):
+            continue   # not launched for this event (the state was clean; stage 2 read the band lists)
         nbytes, votes = kernel_work(name, w, n_hits, st)
         e = roofline_entry(ms, float(nbytes), None if votes is None else float(votes), smem_peak, hbm_peak, peaks_kind)
         e["share"] = ms / total if total else None

@@ -303,13 +303,15 @@ int hough_get_tiling(const hough_ctx *ctx, hough_tiling *tiling);
  * vote_ms: the vote (= gather_ms + scatter_ms); peaks_ms: peak search (= band_peaks_ms +
  * compact_ms); stage2_ms: membership and the stage-2 vote.  gather_ms covers the gather kernel
  * (with HOUGH_VOTE_FUSED, the fused vote and peak search); scatter_ms the shared-atomic kernel;
- * band_peaks_ms the standalone peak kernel; compact_ms the candidate scan.  hough_get_timing synchronises; HOUGH_ENOTREADY
- * before a timed event.
+ * band_peaks_ms the standalone peak kernel; compact_ms the candidate scan.  A kernel that did not
+ * run for the event (the clearing kernel when the last event left the state clean, the candidate
+ * scan when stage 2 reads the band lists) reports 0.  hough_get_timing synchronises;
+ * HOUGH_ENOTREADY before a timed event.
  */
 typedef struct hough_timing {
     float stage_ms, vote_ms, peaks_ms, stage2_ms;
     float gather_ms, scatter_ms, band_peaks_ms, compact_ms;
-    float member_ms, large_ms;   /* stage2_ms = member_ms (membership, small candidates' stage 2) + large_ms */
+    float member_ms, large_ms;   /* stage2_ms = member_ms (the confirmation kernel) + large_ms (0: no second kernel) */
     float clear_ms, count_ms, table_ms, scan_ms, sort_ms;   /* the staging kernels: stage_ms is their sum */
 } hough_timing;
 

@@ -86,6 +86,7 @@ struct hough_ctx {
     // peaks, 5 after the candidate scan, 6 after stage 2
     cudaEvent_t ev[12] = {};   // 0..7 step boundaries, 8..11 inside the staging
     int timed = 0;                       // bit k: ev[k] recorded for the current event
+    bool cleared = false, compacted = false;   // the clearing / compaction kernel ran for this event
 
     ~hough_ctx()
     {
@@ -367,6 +368,8 @@ int enqueue_vote(hough_ctx *c, const float *r, const float *phi, const float *z,
     c->w.radii_next = c->radii_buf[c->parity ^ 1];
     const bool clear = !c->clean;   // the last event did not run its peak search: clear the state
     CU(launch_stage(c->ax, c->w, s, c->timing ? c->ev + 8 : nullptr, clear), "stage kernels");
+    c->cleared = clear;
+    c->compacted = false;
     c->parity ^= 1;
     c->clean = false;
     c->list_pending = false;
@@ -556,6 +559,7 @@ int hough_peaks(hough_ctx *c, void *stream)
     const bool deferred = !fused && stage2_reads_bands(c->ax, c->tiling.band_rows);
     c->w.compact_in_peaks = fused || deferred ? 0 : 1;
     CU(launch_band_peaks(c->ax, c->w, c->tiling, (cudaStream_t)stream), "peak kernel");
+    c->compacted = fused;   // a separate compaction kernel (the peak kernel's own last CTA is timed with it)
     if (c->timing) { CU(cudaEventRecord(c->ev[4], (cudaStream_t)stream), "event"); c->timed |= 16; }
     if (fused) CU(launch_compact(c->ax, c->w, (cudaStream_t)stream), "candidate scan kernel");
     if (c->timing) { CU(cudaEventRecord(c->ev[5], (cudaStream_t)stream), "event"); c->timed |= 32; }
@@ -773,6 +777,10 @@ int hough_get_timing(hough_ctx *c, hough_timing *out)
         (rc = span(0, 8, &out->clear_ms)) || (rc = span(8, 9, &out->count_ms)) || (rc = span(9, 10, &out->table_ms)) ||
         (rc = span(10, 11, &out->scan_ms)) || (rc = span(11, 1, &out->sort_ms)))
         return rc;
+    // a kernel that did not run for this event has no time of its own (its span is only the gap
+    // between two event records)
+    if (!c->cleared) out->clear_ms = 0.f;
+    if (!c->compacted) out->compact_ms = 0.f;
     return HOUGH_OK;
 }
 
