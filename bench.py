@@ -969,7 +969,7 @@ def main():
         "config": {"workload": WORKLOAD_TEXT[args.workload], "hits": n, "votes_per_event": votes,
                    "candidates_per_event": plain["candidates"], "members_per_event": plain["members"],
                    "stage2_votes_per_event": plain["stage2_votes"],
-                   "mode": "plain: one event per step, hough_vote + hough_peaks + hough_stage2 (10 kernel launches)",
+                   "mode": "plain: one event per step, hough_vote + hough_peaks + hough_stage2 (7 kernel launches)",
                    "l2": "flushed before every timed step (256 MiB write)", "tiling": ctx.get_tiling(),
                    "tiling_from": "autotuner (one-event batch, 10 replays per configuration)" if plain_tune else "default"},
         "votes_per_s": votes * plain["events_per_s"],

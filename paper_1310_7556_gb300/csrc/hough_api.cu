@@ -248,8 +248,9 @@ Tiling default_tiling_impl(const Axes &ax)
     t.tile_phi = std::min(ax.n_phi, 256);
     while (ax.n_phi % t.tile_phi) t.tile_phi -= 64;
     t.tile_qpt = std::min(ax.n_qpt, 32);   // the scatter kernel's lanes take 32 rows
-    t.threads = 1024;                      // the scatter vote (every vote of layers whose hits lie at
-                                           // several radii): 32 row lanes x 32 warps sharing the hits
+    t.threads = 256;                       // the autotuner tries 512 and 1024 for the scatter vote (a
+                                           // per-vote detector runs it 2x faster at 1024; an empty
+                                           // launch over a batch's tiles costs 3x more at 1024)
     t.vote_mode = HOUGH_VOTE_GATHER;
     t.band_rows = 1;
     // with a d0 axis a band stages its rows in three slices: taller bands stage each row fewer times
