@@ -531,7 +531,8 @@ def measure_batched(env, args):
         table = kernel_table(wb, int(bhs[-1]), bst, args.smem_peak, args.hbm_peak, args.peaks_kind, BATCH_STEPS)
         dominant = max(table, key=lambda k: table[k]["ms"])
         out["kernels"] = table
-        out["roofline"] = headline_roofline(table, dominant, None)
+        out["roofline"] = headline_roofline(table, dominant,
+                                            measured_traffic(dominant, "batch_256", table[dominant]["source"]))
     if tune is not None:
         out["autotune"] = {"tiling": {f: getattr(tune.tiling, f) for f in binding.TILING_FIELDS},
                            "ms_per_batch": tune.ms, "default_ms_per_batch": tune.default_ms,
