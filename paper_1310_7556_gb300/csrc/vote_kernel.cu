@@ -161,7 +161,13 @@ template <int TPB, bool GENERAL_ONLY, int CELL>
 __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
 {
     constexpr bool COUNTS = CELL == 2;
-    pdl_enter();
+    // After the gather (GENERAL_ONLY) this kernel reads nothing its predecessor writes until its
+    // flush ORs its tile into the gathered accumulator: the layer records, tables, bucket offsets
+    // and sorted hits come from kernels that finished before the gather could launch.  So it checks
+    // for layers of several radii and casts their votes first, and waits for the gather only before
+    // the flush (or before returning with nothing to do), which keeps its completion behind the
+    // gather's.  Voting every layer, it follows the hit sort and waits at once.
+    if (!GENERAL_ONLY) pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_start[kMaxRanges], s_off[kMaxRanges];
     __shared__ int s_pre[kMaxRanges + 1];
@@ -210,7 +216,10 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     }
     __syncthreads();
     // in gather mode there is nothing to do unless some layer has hits at several radii
-    if (GENERAL_ONLY && s_gmask == 0u) return;
+    if (GENERAL_ONLY && s_gmask == 0u) {
+        pdl_enter();
+        return;
+    }
     const unsigned umask = s_umask;
 
     // clear the tile; stage this slab's table rows and FP32 q/pT centres
@@ -519,6 +528,7 @@ __global__ void __launch_bounds__(TPB) scatter_kernel(VoteParams p)
     }
     if (qn) flush_refines();
     if (refined) atomicAdd(&s_refined, refined);
+    if (GENERAL_ONLY) pdl_enter();   // the gathered accumulator is complete
     __syncthreads();
 
     // flush the tile: 8 cells of a row per thread, consecutive threads on consecutive rows (one
