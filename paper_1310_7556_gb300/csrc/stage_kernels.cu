@@ -465,11 +465,25 @@ __device__ __forceinline__ void sort_hit(const Axes &ax, const Workspace &w, int
 // Scatter every valid hit to its sorted position, completing its hot record with its voting rows.
 __global__ void __launch_bounds__(kStageThreads) hit_sort_kernel(Axes ax, Workspace w)
 {
-    pdl_enter();
     const int nkeys = n_keys(ax);
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     const int64_t total = hit_total(w);
     const HitInputs in = hit_inputs(w);
+    // The thread's first hit's own inputs -- its key, rank and record from the counting kernel,
+    // which finished before this grid could launch, and its coordinates -- are requested before
+    // waiting on the table and scan kernel, whose bucket offsets and layer records come after.
+    int k = -1, rank = 0;
+    HotHit hh{};
+    float rr = 0.f, ph = 0.f, zz = 0.f;
+    if (t0 < total) {
+        k = w.key[t0];
+        rank = w.rank[t0];
+        hh = w.hot_tmp[t0];
+        rr = in.r[t0];
+        ph = in.phi[t0];
+        zz = in.z[t0];
+    }
+    pdl_enter();
     // this thread's first (event, layer) pair of the one-radius vote counts: its inputs requested
     // now, counted after the hits, so the loads overlap the hits' own
     const int64_t npairs = (int64_t)w.n_events * ax.n_layers;
@@ -484,11 +498,15 @@ __global__ void __launch_bounds__(kStageThreads) hit_sort_kernel(Axes ax, Worksp
     }
     for (int64_t h = t0; h < total; h += nt) {
         // every load that does not depend on another first, then the bucket offset and layer
-        // record that do: two round trips a hit
-        const int k = w.key[h];
-        const int rank = w.rank[h];
-        const HotHit hh = w.hot_tmp[h];
-        const float rr = in.r[h], ph = in.phi[h], zz = in.z[h];
+        // record that do
+        if (h != t0) {
+            k = w.key[h];
+            rank = w.rank[h];
+            hh = w.hot_tmp[h];
+            rr = in.r[h];
+            ph = in.phi[h];
+            zz = in.z[h];
+        }
         const int e = event_of(w.hit_start, w.n_events, h);
         const int64_t start = w.hit_start[e];
         if (k >= 0) sort_hit(ax, w, h, e, start, start + w.offs[(int64_t)e * (nkeys + 1) + k] + rank, hh, rr, ph, zz);
