@@ -581,7 +581,7 @@ __device__ void vote_pairs(const Axes &ax, const Scratch<WPC, CAP, MAXP, NL> &S,
             const unsigned b0 = S.starts[q], b1 = q + 1 < MAXP / 32 ? S.starts[q + 1] : 0u;
             const int n0 = __popc(b0);
             vote(bw + lane, before + __popc(b0 & upto) - 1);
-            vote(bw + 32 + lane, before + n0 + __popc(b1 & upto) - 1);
+            if (bw + 32 < npairs) vote(bw + 32 + lane, before + n0 + __popc(b1 & upto) - 1);   // (warp-uniform)
             before += n0 + __popc(b1);
         }
     } else {
@@ -714,7 +714,7 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
                             gv = te.g;
                             if (side == 0) {
                                 S.zco[l] = zc;
-                                S.rb[l] = zc.z > 0.f ? __frcp_rn(zc.z) : 0.f;
+                                S.rb[l] = zc.z > 0.f ? __fdividef(1.f, zc.z) : 0.f;   // approximate suffices
                             }
                         }
                     }
