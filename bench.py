@@ -597,8 +597,7 @@ def measure_served(env, args):
     max_event_hits = max(e.n_hits for e in pool_events)
     loads = [float(x) for x in args.serve_loads.split(",") if x]
     # batches of up to 16 events, three launches in flight: the latency setting; batches of up to
-    # 64 events, two in flight: the throughput setting (about 12% more events/s at saturation,
-    # about twice the tail latency at 5k events/s offered)
+    # 64 events, two in flight: the throughput setting (larger launches, a longer tail)
     modes = {"continuous_batching": dict(lanes=4, max_in_flight=3, max_batch_events=16,
                                          max_batch_hits=max(16 * 60_000, max_event_hits)),
              "continuous_batching_large": dict(lanes=3, max_in_flight=2, max_batch_events=64,
