@@ -56,3 +56,37 @@ def test_kernel_table_leaves_out_kernels_that_did_not_run():
 def test_every_workload_named_on_the_command_line_exists():
     for name in bench.WORKLOAD_TEXT:
         assert name in eg.WORKLOADS
+
+
+def _profile_commands():
+    """Every ncu command line of the committed profile summaries (continuation lines joined)."""
+    out = []
+    pdir = os.path.join(ROOT, "profiles")
+    for name in sorted(os.listdir(pdir)):
+        text = open(os.path.join(pdir, name)).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            k = line.find("ncu --")
+            if k >= 0 and ("--metrics" in line or "--set" in line) and "python " in line[k:]:
+                out.append((name, line[k:].strip()))
+    assert out
+    return out
+
+
+def test_profile_recipes_keep_clocks_and_one_kernel_per_full_capture():
+    """Each ncu command in profiles/ leaves the GPU clocks alone, and a capture that collects more
+    than the launch time targets one kernel (-k) and at most three launches (-c)."""
+    for name, cmd in _profile_commands():
+        assert "--clock-control none" in cmd, (name, cmd)
+        if "--set" in cmd or "dram__" in cmd or "smsp__" in cmd:
+            assert " -k " in cmd, (name, cmd)
+            c = cmd.split(" -c ")[1].split()[0]
+            assert int(c) <= 3, (name, cmd)
+
+
+def test_profile_recipes_run_committed_files_only():
+    """The commands behind the profiles run bench.py with its own options, nothing from a working folder."""
+    for name, cmd in _profile_commands():
+        assert "_work" not in cmd, (name, cmd)
+        for tok in cmd.split():
+            if tok.endswith(".py"):
+                assert os.path.exists(os.path.join(ROOT, tok)), (name, tok)
