@@ -41,7 +41,8 @@
 // A candidate with more members than the list holds (kBatchCap, kEventCap), or whose runs hold more
 // pairs than a chunk votes at a time, is done in chunks, the membership pass repeated for each,
 // all chunks voting into the one grid.  The member lists are kept for contexts (hough_get_members
-// reads them), in the event's member pool; a batch keeps none.  The event's member and stage-2
+// reads them), in the event's member pool, where a slot is reserved once the membership pass has
+// counted the members and step 3 stores each member as it reads it; a batch keeps none.  The event's member and stage-2
 // vote counters are summed per group and added once per event a group visits.
 #include <atomic>
 #include <climits>
@@ -494,9 +495,10 @@ struct ChunkOut {
 // while their pairs fit MAXP: par is rewritten in place from slot 0 (a slot never lies past the
 // entry it comes from, and a round's entries are all read before any is written), and the bit of
 // each kept member's first pair is set in starts.  rlo / rhi widen to the rows the runs cover.
-template <int WPC, int CAP, int MAXP, int NL, bool GEN>
+// pool (contexts): the member list, whose first `written` ranks are stored as the entries are read.
+template <int WPC, int CAP, int MAXP, int NL, bool GEN, bool KEEP>
 __device__ ChunkOut chunk_runs(const Axes &ax, Scratch<WPC, CAP, MAXP, NL> &S, const ColdHit *cold, int i, int m, int &rlo,
-                               int &rhi)
+                               int &rhi, int32_t *pool, int rank0, int written)
 {
     const int tid = group_tid<WPC>();
     const int G = 32 * WPC;
@@ -507,6 +509,9 @@ __device__ ChunkOut chunk_runs(const Axes &ax, Scratch<WPC, CAP, MAXP, NL> &S, c
         const bool valid = idx < m;
         int4 e = make_int4(0, 0, 0, 0);
         if (valid) e = S.par[idx];
+        // a context lists the member (rank rank0 + idx, its staged position) in its pool slot; a
+        // member a later chunk lists again writes the same value
+        if (KEEP && valid && rank0 + idx < written) pool[rank0 + idx] = e.x;
         group_sync<WPC>();   // the round's entries are read (and starts cleared) before any write
         // every lane forms coefficients (a lane past the list from entry 0's zeros) and the run is
         // dropped where not valid: no divergent branch on the table path
@@ -631,15 +636,15 @@ __device__ int block_excl_scan(const int32_t *counts, int n, int *out)
 
 // Membership and stage 2 of every candidate a group takes.  GEN: some layer's hits lie at several
 // radii (their votes are redone per hit, partly in FP64); without it that code is left out, which
-// spares the common path its registers.
-template <int WPC, int CAP, int MAXP, int NL, bool P10, bool GEN>
+// spares the common path its registers.  KEEP: the member lists may be kept (Workspace::keep_members
+// decides; single events only), code the batches' one-warp kernels leave out for the same reason.
+template <int WPC, int CAP, int MAXP, int NL, bool P10, bool GEN, bool KEEP>
 __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, float s32, float refine_eps,
                                             Scratch<WPC, CAP, MAXP, NL> &S, uint32_t *grid, const LayerInfo *s_info,
                                             int ngroups, int gidx, int total, const int *band_offs)
 {
     const int tid = group_tid<WPC>(), lane = threadIdx.x & 31, wg = group_warp<WPC>();
     const int L = ax.n_layers, nphi = ax.n_phi, nkeys = L * nphi;
-    const bool keep = w.keep_members != 0;
     // the event's counters, summed by the group's first thread over the event's candidates it takes
     int acc_e = -1;
     unsigned acc_members = 0u;
@@ -758,20 +763,11 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
         };
         const int n = scan_members<WPC, CAP, MAXP, NL, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
                                                              to_chunk);
-        while (lo < n) {
-            if (lo > 0) {
-                group_sync<WPC>();   // the previous chunk's votes have read its members
-                scan_members<WPC, CAP, MAXP, NL, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, to_chunk);
-            }
-            group_sync<WPC>();   // the chunk's list is complete
-            const ChunkOut co = chunk_runs<WPC, CAP, MAXP, NL, GEN>(ax, S, cold, i, min(n - lo, CAP), rlo, rhi);
-            group_sync<WPC>();   // its runs and start bits are complete
-            vote_pairs<WPC, CAP, MAXP, NL, P10>(ax, S, grid, co.npairs, best, votes);
-            lo += co.consumed;
-        }
-        int written = n;
-        if (keep) {
-            // the event's member pool is shared by all its candidates: reserve, then list the members
+        int written = n, listed = 0;   // members in the pool slot / written by step 3
+        int32_t *pool = nullptr;
+        if (KEEP && w.keep_members) {
+            // the event's member pool is shared by all its candidates: the count known, a slot is
+            // reserved now, and the runs' pass lists each member as it reads the member's entry
             if (tid == 0) {
                 const unsigned reserved = n ? atomicAdd(&w.stats[ev].pool_used, (unsigned)n) : 0u;
                 const long long room = (long long)w.max_members - (long long)reserved;
@@ -781,18 +777,24 @@ __device__ __forceinline__ void confirm_all(const Axes &ax, const Workspace &w, 
             group_sync<WPC>();
             const int base = S.pool_base;
             written = S.pool_written;
-            group_sync<WPC>();
             if (tid == 0) {
                 w.mem_start[(int64_t)ev * w.max_cand + c] = base;
                 w.mem_count[(int64_t)ev * w.max_cand + c] = written;
             }
-            if (written > 0) {
-                int32_t *pool = w.mem_pool + (int64_t)ev * w.max_members + base;
-                scan_members<WPC, CAP, MAXP, NL, GEN, false>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps,
-                                                         [&](int r, int p, unsigned, float) {
-                                                             if (r < written) pool[r] = p;
-                                                         });
+            pool = w.mem_pool + (int64_t)ev * w.max_members + base;
+            listed = written;
+        }
+        while (lo < n) {
+            if (lo > 0) {
+                group_sync<WPC>();   // the previous chunk's votes have read its members
+                scan_members<WPC, CAP, MAXP, NL, GEN, true>(ax, w, S, hot, fsort, zsort, cold, i, j, s32, refine_eps, to_chunk);
             }
+            group_sync<WPC>();   // the chunk's list is complete
+            const ChunkOut co = chunk_runs<WPC, CAP, MAXP, NL, GEN, KEEP>(ax, S, cold, i, min(n - lo, CAP), rlo, rhi, pool,
+                                                                          lo, listed);
+            group_sync<WPC>();   // its runs and start bits are complete
+            vote_pairs<WPC, CAP, MAXP, NL, P10>(ax, S, grid, co.npairs, best, votes);
+            lo += co.consumed;
         }
         // step 5: the group's best key and votes, the final mask of its cell, the touched rows cleared
         best = __reduce_max_sync(0xFFFFFFFFu, best);
@@ -912,11 +914,11 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
             __syncthreads();
             if (g >= many_groups) return;
             if (s_general)
-                confirm_all<1, kBatchCap, kBatchPairs, NL, P10, true>(ax, w, s32, refine_eps, s1, grid1, s_info, many_groups,
-                                                                      g, total, band_offs);
+                confirm_all<1, kBatchCap, kBatchPairs, NL, P10, true, true>(ax, w, s32, refine_eps, s1, grid1, s_info,
+                                                                            many_groups, g, total, band_offs);
             else
-                confirm_all<1, kBatchCap, kBatchPairs, NL, P10, false>(ax, w, s32, refine_eps, s1, grid1, s_info,
-                                                                       many_groups, g, total, band_offs);
+                confirm_all<1, kBatchCap, kBatchPairs, NL, P10, false, true>(ax, w, s32, refine_eps, s1, grid1, s_info,
+                                                                             many_groups, g, total, band_offs);
             return;
         }
     }
@@ -932,10 +934,13 @@ __global__ void __launch_bounds__(WPC == 1 ? 32 * kBatchGroups : 32 * WPC, WPC =
         s_general = g;
     }
     __syncthreads();
+    // (one-warp kernels run batches, which keep no member lists)
     if (s_general)
-        confirm_all<WPC, CAP, MAXP, NL, P10, true>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
+        confirm_all<WPC, CAP, MAXP, NL, P10, true, (WPC > 1)>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total,
+                                                              band_offs);
     else
-        confirm_all<WPC, CAP, MAXP, NL, P10, false>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total, band_offs);
+        confirm_all<WPC, CAP, MAXP, NL, P10, false, (WPC > 1)>(ax, w, s32, refine_eps, S, grid, s_info, ngroups, gidx, total,
+                                                               band_offs);
 }
 
 __global__ void member_index_kernel(Workspace w, int32_t *idx_out, int64_t total)
@@ -1023,6 +1028,7 @@ cudaError_t launch_stage2(const Axes &ax, const Workspace &w, int sms, float ref
                           cudaEvent_t between)
 {
     const float s32 = (float)(ax.n_phi * kInvTwoPi);
+    if (w.keep_members && w.n_events != 1) return cudaErrorInvalidValue;   // only single events keep member lists
     cudaError_t err;
     if (w.n_events == 1) {
         // one event: a few hundred candidates, each a chain of dependent steps, so four warps share one
