@@ -319,10 +319,13 @@ class HoughContext:
         _check(self._lib.hough_get_accumulator(self._h, _ptr(out), HOST, _stream(stream)))
         return out
 
-    def members(self, n_candidates: int, hit_cap: int = 1 << 22, stream=None):
+    def members(self, n_candidates: int, hit_cap: int = 1 << 22, stream=None, allow_truncated: bool = False):
+        """(offsets, hit indices) of each candidate's members; with allow_truncated, lists cut by
+        max_members or hit_cap (HOUGH_ETRUNC) are returned as they are."""
         offsets = np.zeros(n_candidates + 1, dtype=np.int64)
         hits = np.zeros(max(hit_cap, 1), dtype=np.int32)
-        _check(self._lib.hough_get_members(self._h, _ptr(offsets), _ptr(hits), hit_cap, HOST, _stream(stream)))
+        _check(self._lib.hough_get_members(self._h, _ptr(offsets), _ptr(hits), hit_cap, HOST, _stream(stream)),
+               allow=(ETRUNC,) if allow_truncated else ())
         return offsets, hits[: offsets[-1]].copy()
 
     def stats(self, stream=None, allow_device_error=False) -> Stats:

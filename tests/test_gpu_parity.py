@@ -237,6 +237,43 @@ def test_candidate_capacity_truncates_in_raster_order(binding):
             [(int(c["iq"]), int(c["jphi"])) for c in ref["candidates"][:10]]
 
 
+@pytest.mark.parametrize("name, max_members", [("pileup_100k", 5000), ("paper_5000", 20000)])
+def test_member_pool_overflow(binding, name, max_members):
+    """A member pool smaller than the event's members (a candidate of four warps on the pileup
+    event; a warp per candidate, lists in chunks, on the paper's 5,000-track event): stage 2 is
+    unchanged, the pool is filled exactly, and every candidate's list is either whole or flagged
+    (flags bit 1) and a subset of the whole one."""
+    w = eg.paper_workload(5000) if name == "paper_5000" else eg.WORKLOADS[name]
+    ev = w.event(0)
+
+    def run(mm):
+        with binding.HoughContext(w.geometry, w.binning, max_hits=ev.n_hits, max_candidates=1 << 18,
+                                  max_members=mm) as ctx:
+            ctx.vote_event(ev)
+            ctx.peaks()
+            ctx.stage2()
+            cands = ctx.candidates()
+            off, mem = ctx.members(len(cands), allow_truncated=True)
+        return cands, off, mem
+
+    cb, ob, mb = run(1 << 22)
+    cs, os_, ms = run(max_members)
+    assert int(ob[-1]) == int(cb["n_members"].sum()) > max_members
+    for f in ("iq", "jphi", "mask", "n_members", "icot", "jz0", "mask2"):
+        assert np.array_equal(cs[f], cb[f]), f
+    assert np.array_equal(cs["flags"] & 1, cb["flags"] & 1) and not (cb["flags"] & 2).any()
+    counts = np.diff(os_)
+    assert int(counts.sum()) == max_members
+    cut = (cs["flags"] & 2) != 0
+    assert cut.any() and np.array_equal(cut, counts < cs["n_members"])
+    for q in range(len(cs)):
+        got, full = ms[os_[q]:os_[q + 1]], mb[ob[q]:ob[q + 1]]
+        if cut[q]:
+            assert np.isin(got, full).all()
+        else:
+            assert np.array_equal(got, full)
+
+
 def test_bad_hits(binding):
     """Host buffers: a bad hit is rejected with HOUGH_EINVAL before any work.  Device buffers: it
     is dropped on the device, flagged in device_error, and the other hits vote as usual."""
