@@ -395,12 +395,20 @@ int settle_list(hough_ctx *c, cudaStream_t s)
     return HOUGH_OK;
 }
 
+// The member pool's reservations exceed max_members exactly when some candidate's list was cut:
+// reported with the device's bits (the kernels count the reservations, the host compares).
+void note_member_cut(hough_ctx *c)
+{
+    if (c->stats_host->pool_used > (unsigned)c->w.max_members) c->stats_host->device_error |= HOUGH_DEVERR_MEMBERS;
+}
+
 int read_stats(hough_ctx *c, cudaStream_t s)
 {
     int rc = settle_list(c, s);
     if (rc) return rc;
     CU(cudaMemcpyAsync(c->stats_host, c->w.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, s), "copy stats");
     CU(cudaStreamSynchronize(s), "synchronise");
+    note_member_cut(c);
     return HOUGH_OK;
 }
 
@@ -718,6 +726,7 @@ int hough_process(hough_ctx *c, const float *r, const float *phi, const float *z
     g_launches += 1;
     CU(cudaStreamSynchronize(s), "synchronise");
     *c->stats_host = *c->stats_mapped;   // hough_get_stats and friends read the last event's copy
+    note_member_cut(c);
     const DevStats &d = *c->stats_host;
     if (d.device_error & (HOUGH_DEVERR_LAYER | HOUGH_DEVERR_RADIUS))
         return fail(HOUGH_EINVAL, "a hit had layer >= n_layers, r <= 0, |phi| > 1000 or a non-finite coordinate");

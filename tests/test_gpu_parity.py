@@ -241,8 +241,8 @@ def test_candidate_capacity_truncates_in_raster_order(binding):
 def test_member_pool_overflow(binding, name, max_members):
     """A member pool smaller than the event's members (a candidate of four warps on the pileup
     event; a warp per candidate, lists in chunks, on the paper's 5,000-track event): stage 2 is
-    unchanged, the pool is filled exactly, and every candidate's list is either whole or flagged
-    (flags bit 1) and a subset of the whole one."""
+    unchanged, the pool is filled exactly, every candidate's list is either whole or flagged
+    (flags bit 1) and a subset of the whole one, and the event reports HOUGH_DEVERR_MEMBERS."""
     w = eg.paper_workload(5000) if name == "paper_5000" else eg.WORKLOADS[name]
     ev = w.event(0)
 
@@ -254,10 +254,12 @@ def test_member_pool_overflow(binding, name, max_members):
             ctx.stage2()
             cands = ctx.candidates()
             off, mem = ctx.members(len(cands), allow_truncated=True)
-        return cands, off, mem
+            err = ctx.stats(allow_device_error=True).device_error
+        return cands, off, mem, err
 
-    cb, ob, mb = run(1 << 22)
-    cs, os_, ms = run(max_members)
+    cb, ob, mb, eb = run(1 << 22)
+    cs, os_, ms, es = run(max_members)
+    assert eb == 0 and es == 8   # HOUGH_DEVERR_MEMBERS: the lists were cut
     assert int(ob[-1]) == int(cb["n_members"].sum()) > max_members
     for f in ("iq", "jphi", "mask", "n_members", "icot", "jz0", "mask2"):
         assert np.array_equal(cs[f], cb[f]), f
