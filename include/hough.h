@@ -223,8 +223,10 @@ int hough_get_accumulator(hough_ctx *ctx, uint16_t *out, int where, void *stream
 /*
  * Copy the member lists of the last stage 2: offsets[n_cand + 1] (int64) and
  * hits[offsets[n_cand]] (int32 hit indices of the event, increasing within each
- * candidate).  `hit_cap` bounds `hits`; HOUGH_ETRUNC when it is too small.
- * Synchronises `stream`.
+ * candidate).  `hit_cap` bounds `hits`; HOUGH_ETRUNC when it is too small, or when
+ * the event had more member hits than max_members (HOUGH_DEVERR_MEMBERS; a cut
+ * list is a subset of the candidate's members, flagged in its record), the lists
+ * being copied as far as they go.  Synchronises `stream`.
  */
 int hough_get_members(hough_ctx *ctx, int64_t *offsets, int32_t *hits, int64_t hit_cap,
                       int where, void *stream);
