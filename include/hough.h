@@ -181,10 +181,13 @@ void hough_destroy(hough_ctx *ctx);
  * Stage-1 vote of one event (Sec. 4, first step).  Hits are four parallel
  * arrays of n_hits entries: r (cm, > 0), phi (rad, |phi| <= 1000; it is reduced
  * modulo 2 pi), z (cm, finite), layer (< n_layers).  With HOUGH_HOST the arrays
- * are checked on the host (HOUGH_EINVAL on a bad hit) and copied; with
- * HOUGH_DEVICE a bad hit is dropped on the device and reported through
- * hough_stats.device_error.  n_hits may be 0.  Replaces the context's previous
- * event.  HOUGH_ECAPACITY when n_hits > max_hits.  Asynchronous on `stream`.
+ * are checked on the host (HOUGH_EINVAL on a bad hit) and copied, except pinned
+ * arrays (cudaHostAlloc, cudaHostRegister), which the staging kernels read in
+ * place over the host link: their contents must stay unchanged until the vote
+ * has run on `stream`.  With HOUGH_DEVICE a bad hit is dropped on the device
+ * and reported through hough_stats.device_error.  n_hits may be 0.  Replaces
+ * the context's previous event.  HOUGH_ECAPACITY when n_hits > max_hits.
+ * Asynchronous on `stream`.
  */
 int hough_vote(hough_ctx *ctx, const float *r, const float *phi, const float *z,
                const uint8_t *layer, int64_t n_hits, int where, void *stream);
