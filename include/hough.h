@@ -348,14 +348,15 @@ int hough_microbench_smem_or(int device, int pattern, double ms, double *atomics
 /*
  * Batched processing: many events of uneven size through the whole path (vote, peaks, membership,
  * stage 2) in one launch sequence, captured into a CUDA graph on the first call for a given
- * number of events and replayed afterwards.  Each event keeps its own accumulator, candidate list
- * and member pool, with the limits below applying per event (max_hits: over the whole batch).
+ * number of events and replayed afterwards.  Each event keeps its own accumulator and candidate
+ * list, with the limits below applying per event (max_hits: over the whole batch); the candidate
+ * records carry their member counts, but a batch keeps no member lists.
  */
 typedef struct hough_batch_limits {
     int32_t max_events;       /* events per batch, >= 1 */
     int32_t max_candidates;   /* candidates kept per event, >= 1 */
     int64_t max_hits;         /* hits per batch, 1 .. 2^31 - 1 */
-    int32_t max_members;      /* member hits kept per event, >= 1 */
+    int32_t max_members;      /* >= 1 (no member lists are kept in batches) */
     int32_t reserved;         /* must be 0 */
 } hough_batch_limits;
 
@@ -443,8 +444,8 @@ int hough_tune_lookup(const char *cache_path, const hough_geometry *geometry, co
  * hough_batch path: one replayed graph) as soon as fewer than max_in_flight batches are on the
  * GPU, so events that arrive while others run join the next launch, and launches of different
  * lanes overlap on the device, one stream each.  A lane is one batch's device buffers
- * (accumulators, candidate lists, member pools for max_batch_events events, allocated once and
- * kept resident) plus pinned host staging for its hits and results.  Lanes are created within
+ * (accumulators and candidate lists for max_batch_events events, allocated once and kept
+ * resident) plus pinned host staging for its hits and results.  Lanes are created within
  * memory_budget; admission is bounded by them: when the filling batch is full and no lane is free,
  * a new event is refused with HOUGH_EBUSY (dead time), never queued without bound.
  *
@@ -457,7 +458,7 @@ typedef struct hough_serve_config {
     int32_t max_batch_events;  /* events per launch, >= 1 */
     int32_t max_candidates;    /* candidates kept per event, >= 1 */
     int64_t max_batch_hits;    /* hits per launch (and per event), 1 .. 2^31 - 1 */
-    int32_t max_members;       /* member hits kept per event, >= 1 */
+    int32_t max_members;       /* >= 1 (served events keep no member lists) */
     int32_t reserved;          /* must be 0 */
     int64_t memory_budget;     /* device bytes all lanes may hold; 0 = no budget */
     int64_t lane_timeout_us;   /* watchdog: a launch not finished after this fails with HOUGH_ETIMEDOUT and
